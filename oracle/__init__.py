@@ -1,0 +1,287 @@
+"""FP64 CPU oracle of the BSS/DQMC sweep (ALF 1.0 documentation, arXiv:1704.00131).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline legs of ``bench.py`` may import this package.  The CUDA library of
+``paper_1704_00131_gb300`` never imports, links or calls it, and the two share no
+code: the oracle is plain C (``dqmc_oracle.c``) built with gcc, loaded here with
+ctypes, and every array crossing this wrapper is a plain numpy array.
+
+Parity unpinned: nothing here is unpinned; see the tests under ``tests/`` that
+pin each routine (closed forms, exact diagonalisation, symmetries, brute force).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dqmc_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+FIELD_ISING = 1
+FIELD_HS4 = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable C99, no architecture flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [
+        ("n_sites", ctypes.c_int32),
+        ("n_flavors", ctypes.c_int32),
+        ("n_vertices", ctypes.c_int32),
+        ("field_type", ctypes.c_int32),
+        ("L", ctypes.c_int32),
+        ("n_wrap", ctypes.c_int32),
+        ("dtau", ctypes.c_double),
+        ("U", ctypes.c_double),
+        ("hopping", ctypes.POINTER(ctypes.c_double)),
+        ("vertex_site", ctypes.POINTER(ctypes.c_int32)),
+        ("vertex_sign", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("proposals", ctypes.c_int64),
+        ("accepted", ctypes.c_int64),
+        ("prec_green_mean", ctypes.c_double),
+        ("prec_green_max", ctypes.c_double),
+        ("prec_phase_max", ctypes.c_double),
+        ("mean_sign", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        d, i32, u32, u64, vp = ctypes.c_double, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+        _lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
+        _lib.orc_u01.argtypes = [u32, u32]
+        _lib.orc_u01.restype = d
+        _lib.orc_init_fields.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u64, u32, vp]
+        _lib.orc_field_coupling.argtypes = [ctypes.c_int, d, d, ctypes.c_int]
+        _lib.orc_field_coupling.restype = d
+        _lib.orc_field_gamma.argtypes = [ctypes.c_int, ctypes.c_int]
+        _lib.orc_field_gamma.restype = d
+        _lib.orc_ising_lambda.argtypes = [d, d]
+        _lib.orc_ising_lambda.restype = d
+        _lib.orc_eig_sym.argtypes = [ctypes.c_int, vp, vp, vp]
+        _lib.orc_expm_sym.argtypes = [ctypes.c_int, vp, d, vp]
+        _lib.orc_logdet.argtypes = [ctypes.c_int, vp, vp, vp]
+        _lib.orc_green_plain.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        _lib.orc_green_udv.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        _lib.orc_energy.argtypes = [vp, vp, vp]
+        _lib.orc_chain_new.argtypes = [vp, vp, u64, u32, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        _lib.orc_chain_new.restype = vp
+        _lib.orc_chain_free.argtypes = [vp]
+        _lib.orc_chain_sweep.argtypes = [vp, ctypes.c_int, vp]
+        _lib.orc_chain_green.argtypes = [vp, ctypes.c_int, vp]
+        _lib.orc_chain_fields.argtypes = [vp, vp, vp, vp]
+        _lib.orc_chain_measure.argtypes = [vp, vp, vp, vp]
+        _lib.orc_logdet_grad.argtypes = [vp, vp, vp, vp, vp, vp]
+        del i32
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Model:
+    """A Hubbard-type model: hopping per flavor, single-site vertices, one field type."""
+
+    hopping: np.ndarray          # [n_flavors, N, N] float64, symmetric, includes -mu
+    vertex_site: np.ndarray      # [M_V] int32
+    vertex_sign: np.ndarray      # [n_flavors, M_V] float64 (sigma_s)
+    U: float
+    dtau: float
+    L: int
+    n_wrap: int
+    field_type: int = FIELD_ISING
+
+    def __post_init__(self):
+        self.hopping = np.ascontiguousarray(self.hopping, dtype=np.float64)
+        if self.hopping.ndim == 2:
+            self.hopping = np.ascontiguousarray(np.stack([self.hopping, self.hopping]))
+        self.vertex_site = np.ascontiguousarray(self.vertex_site, dtype=np.int32)
+        self.vertex_sign = np.ascontiguousarray(self.vertex_sign, dtype=np.float64)
+        self._c = _Model(
+            self.N, self.n_flavors, self.n_vertices, int(self.field_type), int(self.L), int(self.n_wrap),
+            float(self.dtau), float(self.U),
+            self.hopping.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            self.vertex_site.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            self.vertex_sign.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        )
+
+    @property
+    def N(self) -> int:
+        return int(self.hopping.shape[-1])
+
+    @property
+    def n_flavors(self) -> int:
+        return int(self.hopping.shape[0])
+
+    @property
+    def n_vertices(self) -> int:
+        return int(self.vertex_site.shape[0])
+
+    def cref(self):
+        return ctypes.byref(self._c)
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def u01(hi: int, lo: int) -> float:
+    return lib().orc_u01(hi, lo)
+
+
+def init_fields(field_type: int, L: int, MV: int, seed: int, chain: int) -> np.ndarray:
+    f = np.zeros((L, MV), dtype=np.int8)
+    lib().orc_init_fields(field_type, L, MV, seed, chain, _ptr(f))
+    return f
+
+
+def field_coupling(field_type: int, dtau: float, U: float, f: int) -> float:
+    return lib().orc_field_coupling(field_type, dtau, U, f)
+
+
+def field_gamma(field_type: int, f: int) -> float:
+    return lib().orc_field_gamma(field_type, f)
+
+
+def ising_lambda(dtau: float, U: float) -> float:
+    return lib().orc_ising_lambda(dtau, U)
+
+
+def eig_sym(A: np.ndarray):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n))
+    lib().orc_eig_sym(n, _ptr(A), _ptr(w), _ptr(V))
+    return w, V
+
+
+def expm_sym(K: np.ndarray, t: float) -> np.ndarray:
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    E = np.zeros_like(K)
+    lib().orc_expm_sym(K.shape[0], _ptr(K), t, _ptr(E))
+    return E
+
+
+def logdet(A: np.ndarray):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    ld = ctypes.c_double()
+    sg = ctypes.c_int()
+    _check(lib().orc_logdet(A.shape[0], _ptr(A), ctypes.byref(ld), ctypes.byref(sg)), "logdet")
+    return ld.value, sg.value
+
+
+def _green(fn, model: Model, fields: np.ndarray, flavor: int, tau: int):
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    G = np.zeros((model.N, model.N))
+    ld = ctypes.c_double()
+    sg = ctypes.c_int()
+    _check(fn(model.cref(), _ptr(f), flavor, tau, _ptr(G), ctypes.byref(ld), ctypes.byref(sg)), "green")
+    return G, ld.value, sg.value
+
+
+def green_plain(model: Model, fields: np.ndarray, flavor: int, tau: int = 0):
+    """G(tau) = (1 + B(tau,0) B(beta,tau))^-1 by the plain product and LU."""
+    return _green(lib().orc_green_plain, model, fields, flavor, tau)
+
+
+def green_udv(model: Model, fields: np.ndarray, flavor: int, tau: int = 0):
+    """G(tau) through the QR-stabilised UDV chains (chunks of n_wrap slices)."""
+    return _green(lib().orc_green_udv, model, fields, flavor, tau)
+
+
+def energy(model: Model, G: np.ndarray) -> np.ndarray:
+    """(Kin, Pot, Part, Ener) of one configuration from G[n_flavors, N, N]."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    out = np.zeros(4)
+    _check(lib().orc_energy(model.cref(), _ptr(G), _ptr(out)), "energy")
+    return out
+
+
+class Chain:
+    """One Markov chain of the oracle (plain Sherman-Morrison updates, FP64)."""
+
+    def __init__(self, model: Model, fields=None, seed: int = 0, chain: int = 0, measure: bool = False,
+                 meas_first: int = 0, meas_last: int | None = None):
+        self.model = model
+        self._fields_in = None if fields is None else np.ascontiguousarray(fields, dtype=np.int8)
+        ml = model.L if meas_last is None else meas_last
+        self._h = lib().orc_chain_new(model.cref(), None if self._fields_in is None else _ptr(self._fields_in),
+                                      seed, chain, int(measure), meas_first, ml)
+        if not self._h:
+            raise RuntimeError("oracle chain creation failed")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_chain_free(h)
+            self._h = None
+
+    def sweep(self, n: int = 1) -> Stats:
+        st = Stats()
+        _check(lib().orc_chain_sweep(self._h, n, ctypes.byref(st)), "sweep")
+        return st
+
+    def green(self, flavor: int) -> np.ndarray:
+        G = np.zeros((self.model.N, self.model.N))
+        _check(lib().orc_chain_green(self._h, flavor, _ptr(G)), "chain_green")
+        return G
+
+    def fields(self):
+        f = np.zeros((self.model.L, self.model.n_vertices), dtype=np.int8)
+        sw = ctypes.c_uint64()
+        sg = ctypes.c_int()
+        _check(lib().orc_chain_fields(self._h, _ptr(f), ctypes.byref(sw), ctypes.byref(sg)), "fields")
+        return f, sw.value, sg.value
+
+    def measure(self):
+        out = np.zeros(4)
+        ss = ctypes.c_double()
+        nm = ctypes.c_int64()
+        _check(lib().orc_chain_measure(self._h, _ptr(out), ctypes.byref(ss), ctypes.byref(nm)), "measure")
+        return out, ss.value, nm.value
+
+
+def logdet_grad(model: Model, fields: np.ndarray):
+    """Per flavor: log|det(1+B(beta,0))|, its sign, d/dK (symmetric pairs) and d/dU."""
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    nfl, N = model.n_flavors, model.N
+    ld = np.zeros(nfl)
+    sg = np.zeros(nfl, dtype=np.int32)
+    gK = np.zeros((nfl, N, N))
+    gU = np.zeros(nfl)
+    _check(lib().orc_logdet_grad(model.cref(), _ptr(f), _ptr(ld), _ptr(sg), _ptr(gK), _ptr(gU)), "logdet_grad")
+    return ld, sg, gK, gU

@@ -1,0 +1,1021 @@
+/*
+ * dqmc_oracle.c -- plain FP64 CPU oracle for the BSS/DQMC sweep of the ALF 1.0
+ * documentation (Assaad et al., arXiv:1704.00131).
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and the CPU
+ * baseline legs of bench.py load this library.  It shares no code, header or
+ * table with the CUDA path of paper_1704_00131_gb300 and is never called by it.
+ *
+ * Everything is row-major double precision, written to be read against the
+ * paper rather than to be fast: naive triple-loop products, cyclic Jacobi for
+ * the symmetric eigenproblem, LU with partial pivoting, Householder QR with
+ * column pivoting.  Each routine names the passage it follows.
+ *
+ * Notation (Sec. 2.1, Eqs. of the partition function and of G):
+ *   N        lattice sites, L Trotter slices, beta = L * dtau
+ *   K^s      hopping matrix of flavor s (includes -mu on the diagonal)
+ *   E^s      = exp(-dtau K^s)                       (Op_T with g = -dtau)
+ *   v^s_i,t  = sigma^s_k * c(field_k,t), site i = site(k)
+ *   B^s_t    = E^s exp(V^s_t)                        (one-slice propagator)
+ *   B(t2,t1) = B_t2 ... B_t1+1
+ *   G^s(t)   = (1 + B^s(t,0) B^s(beta,t))^-1          (equal-time Green function)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ESING 2
+
+#define FIELD_ISING 1
+#define FIELD_HS4 2
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11 "Parallel random numbers: */
+/* as easy as 1, 2, 3"): 10 rounds of the 4x32 S-box with key schedule.      */
+/* ------------------------------------------------------------------------ */
+static void philox_round(uint32_t x[4], const uint32_t k[2]) {
+  const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x[0];
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x[2];
+  const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+  const uint32_t y0 = hi1 ^ x[1] ^ k[0];
+  const uint32_t y1 = lo1;
+  const uint32_t y2 = hi0 ^ x[3] ^ k[1];
+  const uint32_t y3 = lo0;
+  x[0] = y0; x[1] = y1; x[2] = y2; x[3] = y3;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  uint32_t k[2] = {key[0], key[1]};
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k[0] += 0x9E3779B9u; k[1] += 0xBB67AE85u; }
+    philox_round(x, k);
+  }
+  out[0] = x[0]; out[1] = x[1]; out[2] = x[2]; out[3] = x[3];
+}
+
+/* 53-bit uniform in [0,1) from two 32-bit words (high word first). */
+double orc_u01(uint32_t hi, uint32_t lo) {
+  const uint64_t w = ((uint64_t)hi << 32) | (uint64_t)lo;
+  return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* The random words of one proposal: counter (sweep_lo, 2*tau+dir, k, sweep_hi),
+ * key (seed_lo, seed_hi ^ chain).  u1 drives the proposal, u2 the acceptance. */
+static void proposal_uniforms(uint64_t seed, uint32_t chain, uint64_t sweep, int tau,
+                              int dir, int k, double* u1, double* u2) {
+  uint32_t ctr[4] = {(uint32_t)sweep, (uint32_t)(2 * tau + dir), (uint32_t)k,
+                     (uint32_t)(sweep >> 32)};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ chain};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  *u1 = orc_u01(o[0], o[1]);
+  *u2 = orc_u01(o[2], o[3]);
+}
+
+/* Initial fields: counter domain (0xFFFFFFFF, tau, k, 0xFFFFFFFF).  Ising: -1 if
+ * u1 < 1/2 else +1.  HS4: l = (-2,-1,1,2)[floor(4 u1)]. */
+void orc_init_fields(int field_type, int L, int MV, uint64_t seed, uint32_t chain,
+                     int8_t* fields /*[L][MV]*/) {
+  static const int8_t hs4[4] = {-2, -1, 1, 2};
+  for (int t = 0; t < L; ++t)
+    for (int k = 0; k < MV; ++k) {
+      uint32_t ctr[4] = {0xFFFFFFFFu, (uint32_t)(t + 1), (uint32_t)k, 0xFFFFFFFFu};
+      uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ chain};
+      uint32_t o[4];
+      orc_philox4x32_10(ctr, key, o);
+      const double u = orc_u01(o[0], o[1]);
+      if (field_type == FIELD_ISING)
+        fields[t * MV + k] = (u < 0.5) ? -1 : 1;
+      else {
+        int idx = (int)floor(4.0 * u);
+        if (idx > 3) idx = 3;
+        fields[t * MV + k] = hs4[idx];
+      }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Field couplings.                                                           */
+/*  Ising (type 1, the Ising-coupled term exp(-dtau s I) of the partition     */
+/*  function): exact two-valued decoupling of exp(-dtau U (n_up-1/2)(n_dn-1/2))*/
+/*  with cosh(lambda) = exp(dtau U / 2); c(s) = lambda * s, weight 1.          */
+/*  HS4 (type 2, the four-valued transform of Sec. 2.1 with M_z couplings     */
+/*  g = sqrt(dtau U / 2), Sec. 6.2): c(l) = g * eta(l), weight gamma(l).       */
+/* ------------------------------------------------------------------------ */
+static double hs_eta(int l) {
+  const double s6 = sqrt(6.0);
+  switch (l) {
+    case 1: return sqrt(2.0 * (3.0 - s6));
+    case -1: return -sqrt(2.0 * (3.0 - s6));
+    case 2: return sqrt(2.0 * (3.0 + s6));
+    case -2: return -sqrt(2.0 * (3.0 + s6));
+  }
+  return NAN;
+}
+static double hs_gamma(int l) {
+  const double s6 = sqrt(6.0);
+  if (l == 1 || l == -1) return 1.0 + s6 / 3.0;
+  if (l == 2 || l == -2) return 1.0 - s6 / 3.0;
+  return NAN;
+}
+
+double orc_ising_lambda(double dtau, double U) { return acosh(exp(0.5 * dtau * U)); }
+
+double orc_field_coupling(int field_type, double dtau, double U, int f) {
+  if (field_type == FIELD_ISING) return orc_ising_lambda(dtau, U) * (double)f;
+  return sqrt(0.5 * dtau * U) * hs_eta(f);
+}
+
+double orc_field_gamma(int field_type, int f) {
+  if (field_type == FIELD_ISING) return 1.0;
+  return hs_gamma(f);
+}
+
+/* d c(f) / dU */
+static double field_coupling_dU(int field_type, double dtau, double U, int f) {
+  if (field_type == FIELD_ISING) {
+    const double lam = orc_ising_lambda(dtau, U);
+    return 0.5 * dtau * exp(0.5 * dtau * U) / sinh(lam) * (double)f;
+  }
+  return dtau / (4.0 * sqrt(0.5 * dtau * U)) * hs_eta(f);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense linear algebra (row-major n x n).                                    */
+/* ------------------------------------------------------------------------ */
+static double* dalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
+
+static void mat_mul(int n, const double* A, const double* B, double* C) {
+  double* tmp = dalloc((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += A[i * n + k] * B[k * n + j];
+      tmp[i * n + j] = s;
+    }
+  memcpy(C, tmp, sizeof(double) * n * n);
+  free(tmp);
+}
+
+static void mat_transpose(int n, const double* A, double* At) {
+  double* tmp = dalloc((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) tmp[j * n + i] = A[i * n + j];
+  memcpy(At, tmp, sizeof(double) * n * n);
+  free(tmp);
+}
+
+static void mat_identity(int n, double* A) {
+  memset(A, 0, sizeof(double) * n * n);
+  for (int i = 0; i < n; ++i) A[i * n + i] = 1.0;
+}
+
+/* Symmetric eigendecomposition A = V diag(w) V^T by the cyclic Jacobi method
+ * (Golub & Van Loan, Sec. 8.5).  Used for Op_set's exponentials (Table of the
+ * Operator type: eigenvalues E and unitary U). */
+int orc_eig_sym(int n, const double* A_in, double* w, double* V) {
+  double* A = dalloc((size_t)n * n);
+  memcpy(A, A_in, sizeof(double) * n * n);
+  mat_identity(n, V);
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  /* columns p,q of A */
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  /* rows p,q of A */
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+  free(A);
+  return ORC_OK;
+}
+
+/* E = exp(t K) for symmetric K through K = V diag(w) V^T (Op_set). */
+int orc_expm_sym(int n, const double* K, double t, double* E) {
+  double* w = dalloc(n);
+  double* V = dalloc((size_t)n * n);
+  orc_eig_sym(n, K, w, V);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += V[i * n + k] * exp(t * w[k]) * V[j * n + k];
+      E[i * n + j] = s;
+    }
+  free(w);
+  free(V);
+  return ORC_OK;
+}
+
+/* LU with partial pivoting, in place.  Returns log|det| and sign; piv[n]. */
+static int lu_factor(int n, double* A, int* piv, double* logdet, int* sign) {
+  double ld = 0.0;
+  int sg = 1;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = fabs(A[k * n + k]);
+    for (int i = k + 1; i < n; ++i)
+      if (fabs(A[i * n + k]) > best) { best = fabs(A[i * n + k]); p = i; }
+    piv[k] = p;
+    if (best == 0.0) return ORC_ESING;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) {
+        const double t = A[k * n + j];
+        A[k * n + j] = A[p * n + j];
+        A[p * n + j] = t;
+      }
+      sg = -sg;
+    }
+    const double d = A[k * n + k];
+    ld += log(fabs(d));
+    if (d < 0) sg = -sg;
+    for (int i = k + 1; i < n; ++i) {
+      const double l = A[i * n + k] / d;
+      A[i * n + k] = l;
+      for (int j = k + 1; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+    }
+  }
+  *logdet = ld;
+  *sign = sg;
+  return ORC_OK;
+}
+
+/* Solve (LU) X = B for n right-hand sides stored as the columns of B (in place). */
+static void lu_solve(int n, const double* LU, const int* piv, double* B) {
+  for (int k = 0; k < n; ++k)
+    if (piv[k] != k)
+      for (int j = 0; j < n; ++j) {
+        const double t = B[k * n + j];
+        B[k * n + j] = B[piv[k] * n + j];
+        B[piv[k] * n + j] = t;
+      }
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) {
+      double s = B[i * n + j];
+      for (int k = 0; k < i; ++k) s -= LU[i * n + k] * B[k * n + j];
+      B[i * n + j] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = B[i * n + j];
+      for (int k = i + 1; k < n; ++k) s -= LU[i * n + k] * B[k * n + j];
+      B[i * n + j] = s / LU[i * n + i];
+    }
+  }
+}
+
+/* log|det A| and sign by LU (brute force, used by tests for determinant ratios). */
+int orc_logdet(int n, const double* A_in, double* logdet, int* sign) {
+  double* A = dalloc((size_t)n * n);
+  int* piv = (int*)calloc(n ? n : 1, sizeof(int));
+  memcpy(A, A_in, sizeof(double) * n * n);
+  int st = lu_factor(n, A, piv, logdet, sign);
+  free(A);
+  free(piv);
+  return st;
+}
+
+/* Householder QR with column pivoting (Businger-Golub): A P = Q R.
+ * Pivot: the remaining column of largest 2-norm, ties to the lowest index.
+ * Q is formed explicitly (n x n), R is returned in A's upper triangle,
+ * perm[k] = original column placed at position k, detQ = (-1)^reflections.
+ * This is the "QR with pivoting" default of the stabilisation (Sec. 2.3). */
+static void qr_pivoted(int n, double* A, double* Q, int* perm, int* detQ) {
+  double* vs = dalloc((size_t)n * n); /* Householder vectors, row k = v_k */
+  double* betas = dalloc(n);
+  int dq = 1;
+  for (int j = 0; j < n; ++j) perm[j] = j;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = -1.0;
+    for (int j = k; j < n; ++j) {
+      double s = 0.0;
+      for (int i = k; i < n; ++i) s += A[i * n + j] * A[i * n + j];
+      if (s > best) { best = s; p = j; }
+    }
+    if (p != k) {
+      for (int i = 0; i < n; ++i) {
+        const double t = A[i * n + k];
+        A[i * n + k] = A[i * n + p];
+        A[i * n + p] = t;
+      }
+      const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+    }
+    double nrm = 0.0;
+    for (int i = k; i < n; ++i) nrm += A[i * n + k] * A[i * n + k];
+    nrm = sqrt(nrm);
+    double* v = vs + (size_t)k * n;
+    betas[k] = 0.0;
+    if (nrm == 0.0) continue;
+    const double x0 = A[k * n + k];
+    const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+    for (int i = 0; i < n; ++i) v[i] = 0.0;
+    v[k] = x0 - alpha;
+    for (int i = k + 1; i < n; ++i) v[i] = A[i * n + k];
+    double vtv = 0.0;
+    for (int i = k; i < n; ++i) vtv += v[i] * v[i];
+    if (vtv == 0.0) continue;
+    betas[k] = 2.0 / vtv;
+    dq = -dq;
+    for (int j = k; j < n; ++j) {
+      double s = 0.0;
+      for (int i = k; i < n; ++i) s += v[i] * A[i * n + j];
+      s *= betas[k];
+      for (int i = k; i < n; ++i) A[i * n + j] -= s * v[i];
+    }
+    A[k * n + k] = alpha;
+    for (int i = k + 1; i < n; ++i) A[i * n + k] = 0.0;
+  }
+  /* Q = H_0 H_1 ... H_{n-1}, accumulated backwards onto the identity. */
+  mat_identity(n, Q);
+  for (int k = n - 1; k >= 0; --k) {
+    if (betas[k] == 0.0) continue;
+    const double* v = vs + (size_t)k * n;
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int i = k; i < n; ++i) s += v[i] * Q[i * n + j];
+      s *= betas[k];
+      for (int i = k; i < n; ++i) Q[i * n + j] -= s * v[i];
+    }
+  }
+  *detQ = dq;
+  free(vs);
+  free(betas);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Model.                                                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t n_sites, n_flavors, n_vertices, field_type, L, n_wrap;
+  double dtau, U;
+  const double* hopping;      /* [n_flavors][N][N] */
+  const int32_t* vertex_site; /* [M_V] */
+  const double* vertex_sign;  /* [n_flavors][M_V] */
+} orc_model;
+
+typedef struct {
+  int N, nfl, MV, ft, L, nw;
+  double dtau, U;
+  double* K;     /* [nfl][N][N] */
+  double* E;     /* exp(-dtau K) */
+  double* Einv;  /* exp(+dtau K) */
+  double* ET;    /* E^T */
+  int* site;     /* [MV] */
+  double* sgn;   /* [nfl][MV] */
+} model_t;
+
+static int model_load(const orc_model* m, model_t* M) {
+  if (!m || m->n_sites <= 0 || m->n_flavors < 1 || m->n_flavors > 2 || m->n_vertices < 0 ||
+      m->n_vertices > m->n_sites || m->L <= 0 || m->n_wrap <= 0 || m->L % m->n_wrap != 0 ||
+      (m->field_type != FIELD_ISING && m->field_type != FIELD_HS4) || !(m->dtau > 0.0) ||
+      m->U < 0.0)
+    return ORC_EINVAL;
+  const int N = m->n_sites;
+  M->N = N; M->nfl = m->n_flavors; M->MV = m->n_vertices; M->ft = m->field_type;
+  M->L = m->L; M->nw = m->n_wrap; M->dtau = m->dtau; M->U = m->U;
+  const size_t nn = (size_t)N * N;
+  M->K = dalloc(nn * M->nfl);
+  M->E = dalloc(nn * M->nfl);
+  M->Einv = dalloc(nn * M->nfl);
+  M->ET = dalloc(nn * M->nfl);
+  M->site = (int*)calloc(M->MV ? M->MV : 1, sizeof(int));
+  M->sgn = dalloc((size_t)M->nfl * (M->MV ? M->MV : 1));
+  memcpy(M->K, m->hopping, sizeof(double) * nn * M->nfl);
+  for (int s = 0; s < M->nfl; ++s) {
+    orc_expm_sym(N, M->K + s * nn, -M->dtau, M->E + s * nn);
+    orc_expm_sym(N, M->K + s * nn, +M->dtau, M->Einv + s * nn);
+    mat_transpose(N, M->E + s * nn, M->ET + s * nn);
+  }
+  for (int k = 0; k < M->MV; ++k) M->site[k] = m->vertex_site[k];
+  for (int i = 0; i < M->nfl * M->MV; ++i) M->sgn[i] = m->vertex_sign[i];
+  return ORC_OK;
+}
+
+static void model_free(model_t* M) {
+  free(M->K); free(M->E); free(M->Einv); free(M->ET); free(M->site); free(M->sgn);
+}
+
+/* v^s at every site for slice tau (1-based), from fields [L][MV]. */
+static void slice_potential(const model_t* M, const int8_t* fields, int s, int tau, double* v) {
+  for (int i = 0; i < M->N; ++i) v[i] = 0.0;
+  for (int k = 0; k < M->MV; ++k)
+    v[M->site[k]] += M->sgn[s * M->MV + k] *
+                     orc_field_coupling(M->ft, M->dtau, M->U, fields[(tau - 1) * M->MV + k]);
+}
+
+/* X <- B_tau X = E exp(V_tau) X */
+static void apply_B_left(const model_t* M, const int8_t* f, int s, int tau, double* X) {
+  const int N = M->N;
+  double* v = dalloc(N);
+  slice_potential(M, f, s, tau, v);
+  for (int i = 0; i < N; ++i) {
+    const double e = exp(v[i]);
+    for (int j = 0; j < N; ++j) X[i * N + j] *= e;
+  }
+  mat_mul(N, M->E + (size_t)s * N * N, X, X);
+  free(v);
+}
+
+/* X <- B_tau^T X = exp(V_tau) E^T X */
+static void apply_BT_left(const model_t* M, const int8_t* f, int s, int tau, double* X) {
+  const int N = M->N;
+  double* v = dalloc(N);
+  slice_potential(M, f, s, tau, v);
+  mat_mul(N, M->ET + (size_t)s * N * N, X, X);
+  for (int i = 0; i < N; ++i) {
+    const double e = exp(v[i]);
+    for (int j = 0; j < N; ++j) X[i * N + j] *= e;
+  }
+  free(v);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact result on fixed fields, by definition: G(tau) = (1 + B(tau,0)B(beta,tau))^-1 */
+/* with the product formed plainly and the inverse by LU.  Valid while the    */
+/* product is well conditioned (small beta * bandwidth).                      */
+/* ------------------------------------------------------------------------ */
+int orc_green_plain(const orc_model* m, const int8_t* fields, int s, int tau, double* G,
+                    double* logdet, int* sign) {
+  model_t M;
+  int st = model_load(m, &M);
+  if (st) return st;
+  if (s < 0 || s >= M.nfl || tau < 0 || tau > M.L) { model_free(&M); return ORC_EINVAL; }
+  const int N = M.N;
+  double* A = dalloc((size_t)N * N);
+  mat_identity(N, A);
+  /* A = B(tau,0) B(beta,tau) = B_tau ... B_1 B_L ... B_tau+1: apply from the right end. */
+  for (int t = tau + 1; t <= M.L; ++t) apply_B_left(&M, fields, s, t, A);
+  for (int t = 1; t <= tau; ++t) apply_B_left(&M, fields, s, t, A);
+  for (int i = 0; i < N; ++i) A[i * N + i] += 1.0;
+  int* piv = (int*)calloc(N, sizeof(int));
+  st = lu_factor(N, A, piv, logdet, sign);
+  if (!st) {
+    mat_identity(N, G);
+    lu_solve(N, A, piv, G);
+  }
+  free(piv);
+  free(A);
+  model_free(&M);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* UDV chains (Sec. 2.3, Eq. green_stable and the three-step update):        */
+/*   given A_{j-1} = Q D T,  M_j = (Bcal_j Q) D,  M_j P = Q' R,  D' = |diag R|, */
+/*   T' = D'^-1 R P^T T.                                                       */
+/* Right chain: B(tau,0) = Q_R D_R T_R.  Left chain: B(beta,tau)^T = Q_L D_L T_L. */
+/* ------------------------------------------------------------------------ */
+typedef struct { double *Q, *D, *T; int detQ; } udv_t;
+
+static void udv_alloc(int N, udv_t* u) {
+  u->Q = dalloc((size_t)N * N); u->D = dalloc(N); u->T = dalloc((size_t)N * N); u->detQ = 1;
+}
+static void udv_free(udv_t* u) { free(u->Q); free(u->D); free(u->T); }
+static void udv_identity(int N, udv_t* u) {
+  mat_identity(N, u->Q); mat_identity(N, u->T);
+  for (int i = 0; i < N; ++i) u->D[i] = 1.0;
+  u->detQ = 1;
+}
+static void udv_copy(int N, const udv_t* a, udv_t* b) {
+  memcpy(b->Q, a->Q, sizeof(double) * N * N);
+  memcpy(b->T, a->T, sizeof(double) * N * N);
+  memcpy(b->D, a->D, sizeof(double) * N);
+  b->detQ = a->detQ;
+}
+
+/* Given X = Bcal Q (already formed), finish the three steps in place on u. */
+static void udv_finish(int N, double* X, udv_t* u) {
+  /* M = X D (column scaling) */
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) X[i * N + j] *= u->D[j];
+  int* perm = (int*)calloc(N, sizeof(int));
+  double* Qn = dalloc((size_t)N * N);
+  int dq;
+  qr_pivoted(N, X, Qn, perm, &dq);
+  /* D' = |diag R|;  T' = D'^-1 R P^T T  where (P^T T) row k = T row perm[k]. */
+  double* Dn = dalloc(N);
+  for (int k = 0; k < N; ++k) Dn[k] = fabs(X[k * N + k]);
+  double* PT = dalloc((size_t)N * N);
+  for (int k = 0; k < N; ++k) memcpy(PT + (size_t)k * N, u->T + (size_t)perm[k] * N, sizeof(double) * N);
+  double* Tn = dalloc((size_t)N * N);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double acc = 0.0;
+      for (int k = i; k < N; ++k) acc += X[i * N + k] * PT[k * N + j];
+      Tn[i * N + j] = (Dn[i] > 0.0) ? acc / Dn[i] : 0.0;
+    }
+  memcpy(u->Q, Qn, sizeof(double) * N * N);
+  memcpy(u->T, Tn, sizeof(double) * N * N);
+  memcpy(u->D, Dn, sizeof(double) * N);
+  u->detQ = dq;
+  free(perm); free(Qn); free(Dn); free(PT); free(Tn);
+}
+
+/* Right chain step: B(t1,0) -> B(t2,0) = B_t2 ... B_t1+1 B(t1,0). */
+static void udv_right_step(const model_t* M, const int8_t* f, int s, int t1, int t2, udv_t* u) {
+  const int N = M->N;
+  double* X = dalloc((size_t)N * N);
+  memcpy(X, u->Q, sizeof(double) * N * N);
+  for (int t = t1 + 1; t <= t2; ++t) apply_B_left(M, f, s, t, X);
+  udv_finish(N, X, u);
+  free(X);
+}
+
+/* Left chain step: B(beta,t2)^T -> B(beta,t1)^T = B_t1+1^T ... B_t2^T B(beta,t2)^T. */
+static void udv_left_step(const model_t* M, const int8_t* f, int s, int t1, int t2, udv_t* u) {
+  const int N = M->N;
+  double* X = dalloc((size_t)N * N);
+  memcpy(X, u->Q, sizeof(double) * N * N);
+  for (int t = t2; t >= t1 + 1; --t) apply_BT_left(M, f, s, t, X);
+  udv_finish(N, X, u);
+  free(X);
+}
+
+/* G = (1 + Q_R D_R T_R T_L^T D_L Q_L^T)^-1 by scale separation:
+ *   D = Db * Ds, Db = max(D,1), Ds = min(D,1)
+ *   Mid = Db_R^-1 Q_R^T Q_L Db_L^-1 + Ds_R (T_R T_L^T) Ds_L
+ *   G   = Q_L Db_L^-1 Mid^-1 Db_R^-1 Q_R^T
+ *   log|det G^-1| = sum log Db_R + sum log Db_L + log|det Mid|. */
+static int green_from_udv(int N, const udv_t* R, const udv_t* Lf, double* G, double* logdet,
+                          int* sign) {
+  double* QRt = dalloc((size_t)N * N);
+  double* QRtQL = dalloc((size_t)N * N);
+  double* TLt = dalloc((size_t)N * N);
+  double* TRTLt = dalloc((size_t)N * N);
+  double* Mid = dalloc((size_t)N * N);
+  double* X = dalloc((size_t)N * N);
+  double *dbR = dalloc(N), *dsR = dalloc(N), *dbL = dalloc(N), *dsL = dalloc(N);
+  for (int i = 0; i < N; ++i) {
+    dbR[i] = R->D[i] > 1.0 ? R->D[i] : 1.0;
+    dsR[i] = R->D[i] > 1.0 ? 1.0 : R->D[i];
+    dbL[i] = Lf->D[i] > 1.0 ? Lf->D[i] : 1.0;
+    dsL[i] = Lf->D[i] > 1.0 ? 1.0 : Lf->D[i];
+  }
+  mat_transpose(N, R->Q, QRt);
+  mat_mul(N, QRt, Lf->Q, QRtQL);
+  mat_transpose(N, Lf->T, TLt);
+  mat_mul(N, R->T, TLt, TRTLt);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j)
+      Mid[i * N + j] = QRtQL[i * N + j] / (dbR[i] * dbL[j]) + dsR[i] * TRTLt[i * N + j] * dsL[j];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) X[i * N + j] = QRt[i * N + j] / dbR[i];
+  int* piv = (int*)calloc(N, sizeof(int));
+  double ldm;
+  int sm;
+  int st = lu_factor(N, Mid, piv, &ldm, &sm);
+  if (!st) {
+    lu_solve(N, Mid, piv, X); /* X = Mid^-1 Db_R^-1 Q_R^T */
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) X[i * N + j] /= dbL[i];
+    mat_mul(N, Lf->Q, X, G);
+    double ld = ldm;
+    for (int i = 0; i < N; ++i) ld += log(dbR[i]) + log(dbL[i]);
+    *logdet = ld;
+    *sign = sm * R->detQ * Lf->detQ;
+  }
+  free(piv); free(QRt); free(QRtQL); free(TLt); free(TRTLt); free(Mid); free(X);
+  free(dbR); free(dsR); free(dbL); free(dsL);
+  return st;
+}
+
+/* G(tau) from fixed fields through the two UDV chains, chunked every n_wrap
+ * slices (right chain 0 -> tau, left chain beta -> tau); a partial chunk
+ * closes each chain when tau is not a stabilisation point. */
+int orc_green_udv(const orc_model* m, const int8_t* fields, int s, int tau, double* G,
+                  double* logdet, int* sign) {
+  model_t M;
+  int st = model_load(m, &M);
+  if (st) return st;
+  if (s < 0 || s >= M.nfl || tau < 0 || tau > M.L) { model_free(&M); return ORC_EINVAL; }
+  const int N = M.N, nw = M.nw;
+  udv_t R, Lf;
+  udv_alloc(N, &R); udv_alloc(N, &Lf);
+  udv_identity(N, &R); udv_identity(N, &Lf);
+  for (int t = 0; t < tau; t += nw) udv_right_step(&M, fields, s, t, (t + nw < tau) ? t + nw : tau, &R);
+  for (int t = M.L; t > tau; t -= nw) udv_left_step(&M, fields, s, (t - nw > tau) ? t - nw : tau, t, &Lf);
+  st = green_from_udv(N, &R, &Lf, G, logdet, sign);
+  udv_free(&R); udv_free(&Lf);
+  model_free(&M);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Energy estimator (Sec. 6.1 observables, in the U n_up n_dn form):          */
+/*   Kin  = sum_s sum_xy K^s_xy (delta_xy - G^s_yx)                          */
+/*   Pot  = U sum_i (1 - G^up_ii)(1 - G^dn_ii)       (two flavors)           */
+/*   Part = sum_s sum_i (1 - G^s_ii),   Ener = Kin + Pot.                    */
+/* ------------------------------------------------------------------------ */
+static void energy_terms(const model_t* M, double* const* G, double out[4]) {
+  const int N = M->N;
+  double kin = 0.0, pot = 0.0, part = 0.0;
+  for (int s = 0; s < M->nfl; ++s) {
+    const double* K = M->K + (size_t)s * N * N;
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) kin += K[x * N + y] * ((x == y ? 1.0 : 0.0) - G[s][y * N + x]);
+    for (int i = 0; i < N; ++i) part += 1.0 - G[s][i * N + i];
+  }
+  if (M->nfl == 2)
+    for (int i = 0; i < N; ++i) pot += M->U * (1.0 - G[0][i * N + i]) * (1.0 - G[1][i * N + i]);
+  out[0] = kin; out[1] = pot; out[2] = part; out[3] = kin + pot;
+}
+
+int orc_energy(const orc_model* m, const double* G_all /*[nfl][N][N]*/, double* out4) {
+  model_t M;
+  int st = model_load(m, &M);
+  if (st) return st;
+  double* G[2] = {(double*)G_all, (double*)G_all + (size_t)M.N * M.N * (M.nfl - 1)};
+  energy_terms(&M, G, out4);
+  model_free(&M);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The Markov chain (Algorithm 1 with the default sequential single-field    */
+/* updates of Sec. 2.2.1).                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t proposals, accepted;
+  double prec_green_mean, prec_green_max, prec_phase_max, mean_sign;
+} orc_stats;
+
+typedef struct {
+  model_t M;
+  uint64_t seed;
+  uint32_t chain;
+  uint64_t sweep;      /* sweeps done so far (Philox counter) */
+  int8_t* fields;      /* [L][MV] */
+  double* G[2];        /* current G (at tau = 0 between sweeps) */
+  udv_t* slot[2];      /* [nst+1] per flavor */
+  int sign;            /* sign of the current weight */
+  int measure, meas_first, meas_last;
+  double meas[4], sign_sum;
+  int64_t n_meas;
+  /* precision monitor of the last orc_chain_sweep call */
+  double prec_sum, prec_max, phase_max;
+  int64_t prec_events;
+  int64_t proposals, accepted;
+} orc_chain;
+
+static void green_fresh(orc_chain* c, int s, int j_right, int j_left, double* G, double* ld,
+                        int* sg) {
+  /* j_right: slot index of the right chain (-1 = identity); j_left likewise. */
+  const int N = c->M.N;
+  udv_t I;
+  udv_alloc(N, &I);
+  udv_identity(N, &I);
+  const udv_t* R = (j_right < 0) ? &I : &c->slot[s][j_right];
+  const udv_t* Lf = (j_left < 0) ? &I : &c->slot[s][j_left];
+  green_from_udv(N, R, Lf, G, ld, sg);
+  udv_free(&I);
+}
+
+orc_chain* orc_chain_new(const orc_model* m, const int8_t* fields_or_null, uint64_t seed,
+                         uint32_t chain, int measure, int meas_first, int meas_last) {
+  orc_chain* c = (orc_chain*)calloc(1, sizeof(orc_chain));
+  if (model_load(m, &c->M)) { free(c); return NULL; }
+  const int N = c->M.N, L = c->M.L, MV = c->M.MV, nst = L / c->M.nw;
+  c->seed = seed; c->chain = chain; c->sweep = 0;
+  c->measure = measure; c->meas_first = meas_first; c->meas_last = meas_last;
+  c->fields = (int8_t*)calloc((size_t)L * (MV ? MV : 1), 1);
+  if (fields_or_null) memcpy(c->fields, fields_or_null, (size_t)L * MV);
+  else orc_init_fields(c->M.ft, L, MV, seed, chain, c->fields);
+  /* Fill the storage with the left chain (the wrapul loop of Algorithm 1). */
+  c->sign = 1;
+  for (int s = 0; s < c->M.nfl; ++s) {
+    c->G[s] = dalloc((size_t)N * N);
+    c->slot[s] = (udv_t*)calloc(nst + 1, sizeof(udv_t));
+    for (int j = 0; j <= nst; ++j) udv_alloc(N, &c->slot[s][j]);
+    udv_identity(N, &c->slot[s][nst]);
+    for (int j = nst - 1; j >= 0; --j) {
+      udv_copy(N, &c->slot[s][j + 1], &c->slot[s][j]);
+      udv_left_step(&c->M, c->fields, s, j * c->M.nw, (j + 1) * c->M.nw, &c->slot[s][j]);
+    }
+    double ld;
+    int sg;
+    green_fresh(c, s, -1, 0, c->G[s], &ld, &sg);
+    c->sign *= sg;
+  }
+  return c;
+}
+
+void orc_chain_free(orc_chain* c) {
+  if (!c) return;
+  const int nst = c->M.L / c->M.nw;
+  for (int s = 0; s < c->M.nfl; ++s) {
+    free(c->G[s]);
+    for (int j = 0; j <= nst; ++j) udv_free(&c->slot[s][j]);
+    free(c->slot[s]);
+  }
+  free(c->fields);
+  model_free(&c->M);
+  free(c);
+}
+
+/* G <- exp(a V_tau) G exp(-a V_tau), a = +1 (V-wrap) or -1 (V-unwrap). */
+static void v_wrap(orc_chain* c, int s, int tau, double a) {
+  const int N = c->M.N;
+  double* v = dalloc(N);
+  slice_potential(&c->M, c->fields, s, tau, v);
+  for (int x = 0; x < N; ++x)
+    for (int y = 0; y < N; ++y) c->G[s][x * N + y] *= exp(a * (v[x] - v[y]));
+  free(v);
+}
+
+/* G <- X G Y (the hopping wrap: (E, E^-1) up, (E^-1, E) down). */
+static void t_wrap(orc_chain* c, int s, int up) {
+  const int N = c->M.N;
+  const size_t nn = (size_t)N * N;
+  if (up) {
+    mat_mul(N, c->M.E + s * nn, c->G[s], c->G[s]);
+    mat_mul(N, c->G[s], c->M.Einv + s * nn, c->G[s]);
+  } else {
+    mat_mul(N, c->M.Einv + s * nn, c->G[s], c->G[s]);
+    mat_mul(N, c->G[s], c->M.E + s * nn, c->G[s]);
+  }
+}
+
+/* One proposal at vertex k of slice tau (direction dir: 0 up, 1 down). */
+static void propose(orc_chain* c, int tau, int dir, int k) {
+  const model_t* M = &c->M;
+  const int N = M->N, i = M->site[k];
+  double u1, u2;
+  proposal_uniforms(c->seed, c->chain, c->sweep, tau, dir, k, &u1, &u2);
+  const int f = c->fields[(tau - 1) * M->MV + k];
+  int fn;
+  if (M->ft == FIELD_ISING) fn = -f;
+  else {
+    /* the three other values of (-2,-1,1,2), ascending, index floor(3 u1) */
+    int others[3], n = 0;
+    const int all[4] = {-2, -1, 1, 2};
+    for (int q = 0; q < 4; ++q) if (all[q] != f) others[n++] = all[q];
+    int idx = (int)floor(3.0 * u1);
+    if (idx > 2) idx = 2;
+    fn = others[idx];
+  }
+  const double dc = orc_field_coupling(M->ft, M->dtau, M->U, fn) -
+                    orc_field_coupling(M->ft, M->dtau, M->U, f);
+  double delta[2], Rs[2];
+  double R = orc_field_gamma(M->ft, fn) / orc_field_gamma(M->ft, f);
+  for (int s = 0; s < M->nfl; ++s) {
+    delta[s] = exp(M->sgn[s * M->MV + k] * dc) - 1.0;
+    Rs[s] = 1.0 + delta[s] * (1.0 - c->G[s][i * N + i]);
+    R *= Rs[s];
+  }
+  c->proposals++;
+  const double absR = fabs(R);
+  if (u2 < (absR < 1.0 ? absR : 1.0)) {
+    c->accepted++;
+    c->fields[(tau - 1) * M->MV + k] = (int8_t)fn;
+    if (R < 0) c->sign = -c->sign;
+    /* Sherman-Morrison: G <- G - (delta/R_s) G[:,i] (e_i - G[i,:])^T */
+    double* col = dalloc(N);
+    double* row = dalloc(N);
+    for (int s = 0; s < M->nfl; ++s) {
+      double* G = c->G[s];
+      const double fac = delta[s] / Rs[s];
+      for (int x = 0; x < N; ++x) col[x] = G[x * N + i];
+      for (int y = 0; y < N; ++y) row[y] = ((y == i) ? 1.0 : 0.0) - G[i * N + y];
+      for (int x = 0; x < N; ++x)
+        for (int y = 0; y < N; ++y) G[x * N + y] -= fac * col[x] * row[y];
+    }
+    free(col);
+    free(row);
+  }
+}
+
+/* One stabilisation event of flavor s (the cgr + control_precisionG steps of
+ * Algorithm 1): G fresh from the right chain R and the left chain Lf replaces
+ * the wrapped G; |G_wrap - G_fresh| feeds the precision monitor. */
+static void fresh_replace(orc_chain* c, int s, const udv_t* R, const udv_t* Lf, int* fresh_sign) {
+  const int N = c->M.N;
+  double* Gf = dalloc((size_t)N * N);
+  double ld, mx = 0.0, sm = 0.0;
+  int sg = 1;
+  green_from_udv(N, R, Lf, Gf, &ld, &sg);
+  for (int x = 0; x < N * N; ++x) {
+    const double d = fabs(Gf[x] - c->G[s][x]);
+    sm += d;
+    if (d > mx) mx = d;
+  }
+  memcpy(c->G[s], Gf, sizeof(double) * N * N);
+  free(Gf);
+  c->prec_sum += sm / ((double)N * N * c->M.nfl);
+  if (mx > c->prec_max) c->prec_max = mx;
+  *fresh_sign *= sg;
+}
+
+/* Close an event: the tracked sign is compared with the fresh one and replaced. */
+static void close_event(orc_chain* c, int fresh_sign) {
+  const double ph = fabs((double)fresh_sign - (double)c->sign);
+  if (ph > c->phase_max) c->phase_max = ph;
+  c->sign = fresh_sign;
+  c->prec_events++;
+}
+
+static void measure_now(orc_chain* c, int tau) {
+  if (!c->measure || tau < c->meas_first || tau > c->meas_last) return;
+  double e[4];
+  energy_terms(&c->M, c->G, e);
+  for (int q = 0; q < 4; ++q) c->meas[q] += (double)c->sign * e[q];
+  c->sign_sum += (double)c->sign;
+  c->n_meas++;
+}
+
+/* One sweep: every field visited twice, tau = 1..L then L..1 (Sec. 2.4).
+ * Upward slice tau:   V-wrap, proposals at vertices 0..MV-1, T-wrap to G(tau),
+ *                     at tau = j*nw: right chain to tau, fresh G with the left
+ *                     chain of slot j, slot j <- right chain.
+ * Downward slice tau: T-unwrap, proposals at vertices MV-1..0, V-unwrap to
+ *                     G(tau-1), at tau-1 = j*nw: left chain to tau-1, fresh G
+ *                     with the right chain of slot j, slot j <- left chain. */
+static void one_sweep(orc_chain* c) {
+  const model_t* M = &c->M;
+  const int N = M->N, L = M->L, nw = M->nw, nst = L / nw, nfl = M->nfl, MV = M->MV;
+  udv_t chain, ident;
+  udv_alloc(N, &chain);
+  udv_alloc(N, &ident);
+  udv_identity(N, &ident);
+  for (int tau = 1; tau <= L; ++tau) {
+    for (int s = 0; s < nfl; ++s) v_wrap(c, s, tau, +1.0);
+    for (int k = 0; k < MV; ++k) propose(c, tau, 0, k);
+    for (int s = 0; s < nfl; ++s) t_wrap(c, s, 1);
+    if (tau % nw == 0) {
+      const int j = tau / nw;
+      int fs = 1;
+      for (int s = 0; s < nfl; ++s) {
+        udv_copy(N, (j == 1) ? &ident : &c->slot[s][j - 1], &chain);
+        udv_right_step(M, c->fields, s, tau - nw, tau, &chain);
+        fresh_replace(c, s, &chain, (j == nst) ? &ident : &c->slot[s][j], &fs);
+        udv_copy(N, &chain, &c->slot[s][j]);
+      }
+      close_event(c, fs);
+    }
+    measure_now(c, tau);
+  }
+  for (int tau = L; tau >= 1; --tau) {
+    for (int s = 0; s < nfl; ++s) t_wrap(c, s, 0);
+    for (int k = MV - 1; k >= 0; --k) propose(c, tau, 1, k);
+    for (int s = 0; s < nfl; ++s) v_wrap(c, s, tau, -1.0);
+    const int t0 = tau - 1;
+    if (t0 % nw == 0) {
+      const int j = t0 / nw;
+      int fs = 1;
+      for (int s = 0; s < nfl; ++s) {
+        udv_copy(N, (j + 1 == nst) ? &ident : &c->slot[s][j + 1], &chain);
+        udv_left_step(M, c->fields, s, t0, t0 + nw, &chain);
+        fresh_replace(c, s, (j == 0) ? &ident : &c->slot[s][j], &chain, &fs);
+        udv_copy(N, &chain, &c->slot[s][j]);
+      }
+      close_event(c, fs);
+    }
+    measure_now(c, t0);
+  }
+  udv_free(&chain);
+  udv_free(&ident);
+  c->sweep++;
+}
+
+int orc_chain_sweep(orc_chain* c, int n_sweeps, orc_stats* st) {
+  if (!c || n_sweeps < 0) return ORC_EINVAL;
+  c->prec_sum = 0.0; c->prec_max = 0.0; c->phase_max = 0.0; c->prec_events = 0;
+  c->proposals = 0; c->accepted = 0;
+  double sgn_sum = 0.0;
+  for (int n = 0; n < n_sweeps; ++n) {
+    one_sweep(c);
+    sgn_sum += (double)c->sign;
+  }
+  if (st) {
+    st->proposals = c->proposals;
+    st->accepted = c->accepted;
+    st->prec_green_mean = c->prec_events ? c->prec_sum / (double)c->prec_events : 0.0;
+    st->prec_green_max = c->prec_max;
+    st->prec_phase_max = c->phase_max;
+    st->mean_sign = n_sweeps ? sgn_sum / n_sweeps : 0.0;
+  }
+  return ORC_OK;
+}
+
+int orc_chain_green(const orc_chain* c, int s, double* G) {
+  if (!c || s < 0 || s >= c->M.nfl) return ORC_EINVAL;
+  memcpy(G, c->G[s], sizeof(double) * c->M.N * c->M.N);
+  return ORC_OK;
+}
+
+int orc_chain_fields(const orc_chain* c, int8_t* out, uint64_t* sweep_counter, int* sign) {
+  if (!c) return ORC_EINVAL;
+  memcpy(out, c->fields, (size_t)c->M.L * c->M.MV);
+  if (sweep_counter) *sweep_counter = c->sweep;
+  if (sign) *sign = c->sign;
+  return ORC_OK;
+}
+
+int orc_chain_measure(const orc_chain* c, double* out4, double* sign_sum, int64_t* n_meas) {
+  if (!c) return ORC_EINVAL;
+  for (int q = 0; q < 4; ++q) out4[q] = c->meas[q];
+  *sign_sum = c->sign_sum;
+  *n_meas = c->n_meas;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Derivative of log|det(1 + B^s(beta,0))| on fixed fields.                  */
+/* From G = (1 + B(beta,0))^-1 and d log det(1+B) = Tr[G dB]:                 */
+/*   d log|det| = sum_tau Tr[(1 - G(tau-1)) B_tau^-1 dB_tau],                 */
+/*   B_tau^-1 dB_tau = e^{-V} E^-1 dE e^{V} + dV,                            */
+/* so with Gt_tau = e^{V_tau} G(tau-1) e^{-V_tau} and S = sum_tau (1 - Gt_tau): */
+/*   hopping part: Tr[S E^-1 dE], dE the Frechet derivative of exp(-dtau K)  */
+/*   in K's eigenbasis (Daleckii-Krein divided differences);                  */
+/*   coupling part: sum_tau sum_k (1 - G(tau-1))_ii sigma_k dc(f_k,tau)/dU.    */
+/* grad_K[s][x][y] = d/dK^s_xy with K_xy and K_yx varied together (x != y).   */
+/* Each G(tau-1) is computed fresh through the UDV chains.                    */
+/* ------------------------------------------------------------------------ */
+int orc_logdet_grad(const orc_model* m, const int8_t* fields, double* logdet_out /*[nfl]*/,
+                    int* sign_out /*[nfl]*/, double* grad_K /*[nfl][N][N]*/,
+                    double* grad_U /*[nfl]*/) {
+  model_t M;
+  int st = model_load(m, &M);
+  if (st) return st;
+  const int N = M.N, L = M.L;
+  const size_t nn = (size_t)N * N;
+  double* G = dalloc(nn);
+  double* S = dalloc(nn);
+  double* v = dalloc(N);
+  double* w = dalloc(N);
+  double* V = dalloc(nn);
+  double* A = dalloc(nn);
+  double* Z = dalloc(nn);
+  double* tmp = dalloc(nn);
+  for (int s = 0; s < M.nfl; ++s) {
+    memset(S, 0, sizeof(double) * nn);
+    double gU = 0.0;
+    for (int tau = 1; tau <= L; ++tau) {
+      double ld;
+      int sg;
+      st = orc_green_udv(m, fields, s, tau - 1, G, &ld, &sg);
+      if (st) goto done;
+      if (tau == 1) { logdet_out[s] = ld; sign_out[s] = sg; }
+      slice_potential(&M, fields, s, tau, v);
+      for (int x = 0; x < N; ++x)
+        for (int y = 0; y < N; ++y)
+          S[x * N + y] += ((x == y) ? 1.0 : 0.0) - exp(v[x] - v[y]) * G[x * N + y];
+      for (int k = 0; k < M.MV; ++k) {
+        const int i = M.site[k];
+        gU += (1.0 - G[i * N + i]) * M.sgn[s * M.MV + k] *
+              field_coupling_dU(M.ft, M.dtau, M.U, fields[(tau - 1) * M.MV + k]);
+      }
+    }
+    grad_U[s] = gU;
+    /* A = S E^-1;  g = V [F o (V^T A^T V)] V^T;  F_ab divided differences of exp(-dtau x). */
+    mat_mul(N, S, M.Einv + s * nn, A);
+    orc_eig_sym(N, M.K + s * nn, w, V);
+    mat_transpose(N, A, tmp);       /* A^T */
+    mat_mul(N, tmp, V, Z);          /* A^T V */
+    mat_transpose(N, V, tmp);       /* V^T */
+    mat_mul(N, tmp, Z, Z);          /* V^T A^T V */
+    for (int a = 0; a < N; ++a)
+      for (int b = 0; b < N; ++b) {
+        double F;
+        const double la = w[a], lb = w[b];
+        if (fabs(la - lb) > 1e-9 * (1.0 + fabs(la) + fabs(lb)))
+          F = (exp(-M.dtau * la) - exp(-M.dtau * lb)) / (la - lb);
+        else
+          F = -M.dtau * exp(-M.dtau * 0.5 * (la + lb));
+        Z[a * N + b] *= F;
+      }
+    mat_mul(N, V, Z, Z);
+    mat_mul(N, Z, tmp, Z);          /* V Z V^T */
+    double* g = grad_K + s * nn;
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) g[x * N + y] = (x == y) ? Z[x * N + y] : Z[x * N + y] + Z[y * N + x];
+  }
+done:
+  free(G); free(S); free(v); free(w); free(V); free(A); free(Z); free(tmp);
+  model_free(&M);
+  return st;
+}

@@ -1,0 +1,425 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU (no GPU marker).  Each one is chosen so that a
+plausible mistake in the oracle (a dropped term, a wrong sign or index, a
+transposed operand) fails it:
+
+* Philox4x32-10 known-answer vectors (published with the generator);
+* the discrete HS constants of Sec. 2.1 and the exact Ising decoupling;
+* U = 0 closed forms: G(tau) = (1 + exp(-beta K))^-1 at every tau, log det and
+  kinetic energy from the lattice dispersion;
+* exact enumeration of every field configuration of 2- and 4-site clusters
+  against the Fock-space trace of the Trotterised density matrix (ED);
+* particle-hole symmetry at half filling on bipartite lattices;
+* the UDV chain against the plain product, and n_wrap independence;
+* the fast-updated, wrapped G against the freshly stabilised one;
+* central finite differences of log|det(1 + B(beta,0))|;
+* Monte Carlo estimates of the sampler against ED within 3 sigma.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+from paper_1704_00131_gb300 import workloads as W
+from tests.fock_ed import Fock
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def make_model(orc, K, U, dtau, L, nwrap, ft=1, nfl=2):
+    N = K.shape[-1]
+    H = K if K.ndim == 3 else np.stack([K] * nfl)
+    sign = np.stack([np.ones(N), -np.ones(N)])[:nfl]
+    return orc.Model(H, np.arange(N, dtype=np.int32), sign, U, dtau, L, nwrap, ft)
+
+
+# --------------------------------------------------------------------------- RNG
+def test_philox_known_answers(orc):
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        assert list(orc.philox4x32_10(w[0:4], w[4:6])) == w[6:10]
+        n += 1
+    assert n == 3
+
+
+def test_uniform_mapping(orc):
+    assert orc.u01(0, 0) == 0.0
+    assert orc.u01(0x80000000, 0) == 0.5
+    assert orc.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -53
+    # 53 bits: the 11 lowest bits of the low word are dropped
+    assert orc.u01(0, 0x7FF) == 0.0 and orc.u01(0, 0x800) == 2.0 ** -53
+
+
+def test_init_fields_distribution(orc):
+    f = orc.init_fields(1, 200, 50, seed=7, chain=3)
+    assert set(np.unique(f)) == {-1, 1}
+    assert abs(f.mean()) < 0.05
+    g = orc.init_fields(2, 200, 50, seed=7, chain=3)
+    assert set(np.unique(g)) == {-2, -1, 1, 2}
+    for v in (-2, -1, 1, 2):
+        assert abs((g == v).mean() - 0.25) < 0.02
+    assert not np.array_equal(f, orc.init_fields(1, 200, 50, seed=7, chain=4))
+
+
+# ------------------------------------------------------------ HS transformations
+def test_hs4_constants_match_paper_identity(orc):
+    """(1/4) sum_l gamma(l) exp(a eta(l) A) = exp(a^2 A^2) + O(a^8) (Sec. 2.1, Eq. HS_squares,
+    with the 1/4 normalisation of the weights; a^2 = dtau*lambda, so the error is O(dtau^4))."""
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+    s6 = math.sqrt(6.0)
+    assert gam[1] == pytest.approx(1 + s6 / 3, rel=1e-15) and gam[-2] == pytest.approx(1 - s6 / 3, rel=1e-15)
+    # eta(l) from the coupling with dtau*U/2 = 1, i.e. g = 1
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    assert eta[1] == pytest.approx(math.sqrt(2 * (3 - s6)), rel=1e-15)
+    assert eta[-2] == pytest.approx(-math.sqrt(2 * (3 + s6)), rel=1e-15)
+    for A in (0.0, 1.0, 2.0):
+        errs = []
+        for a in (0.1, 0.05):
+            lhs = sum(gam[l] * math.exp(a * eta[l] * A) for l in gam) / 4.0
+            errs.append(abs(lhs - math.exp(a * a * A * A)))
+        if A == 0.0:
+            assert max(errs) < 1e-15
+        else:
+            # O(a^8): halving a divides the error by ~2^8
+            assert errs[1] < errs[0] / 150.0
+
+
+def test_ising_decoupling_is_exact(orc):
+    """(1/2) e^{-dtau U/4} sum_s e^{lambda s (n_up - n_dn)} = e^{-dtau U (n_up-1/2)(n_dn-1/2)}."""
+    for dtau, U in ((0.1, 4.0), (0.05, 2.0), (0.2, 6.0)):
+        lam = orc.ising_lambda(dtau, U)
+        assert orc.field_coupling(1, dtau, U, 1) == pytest.approx(lam, rel=1e-15)
+        for nu, nd in itertools.product((0, 1), (0, 1)):
+            lhs = 0.5 * math.exp(-dtau * U / 4) * sum(math.exp(lam * s * (nu - nd)) for s in (1, -1))
+            rhs = math.exp(-dtau * U * (nu - 0.5) * (nd - 0.5))
+            assert lhs == pytest.approx(rhs, rel=1e-14)
+
+
+# ------------------------------------------------------------------ dense algebra
+def test_eig_and_expm_against_library(orc):
+    rng = np.random.default_rng(1)
+    for n in (1, 5, 16):
+        A = rng.standard_normal((n, n))
+        A = A + A.T
+        w, V = orc.eig_sym(A)
+        assert np.allclose(np.sort(w), np.linalg.eigvalsh(A), atol=1e-12)
+        assert np.allclose(V @ np.diag(w) @ V.T, A, atol=1e-12)
+        assert np.allclose(orc.expm_sym(A, -0.3), expm(-0.3 * A), rtol=1e-12, atol=1e-13)
+
+
+def test_logdet_against_library(orc):
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((9, 9))
+    ld, sg = orc.logdet(A)
+    s2, l2 = np.linalg.slogdet(A)
+    assert ld == pytest.approx(l2, rel=1e-13) and sg == int(s2)
+
+
+# ---------------------------------------------------------------- U = 0 closed form
+def square_dispersion(Lx, Ly, t, tp, mu):
+    e = []
+    for ny in range(Ly):
+        for nx in range(Lx):
+            kx, ky = 2 * np.pi * nx / Lx, 2 * np.pi * ny / Ly
+            e.append(-2 * t * (np.cos(kx) + np.cos(ky)) - 4 * tp * np.cos(kx) * np.cos(ky) - mu)
+    return np.sort(np.array(e))
+
+
+def honeycomb_dispersion(L1, L2, t, mu):
+    a1 = np.array([1.0, 0.0])
+    a2 = np.array([0.5, np.sqrt(3) / 2])
+    # reciprocal vectors g_i with a_i . g_j = 2 pi delta_ij
+    Amat = np.stack([a1, a2])
+    G = 2 * np.pi * np.linalg.inv(Amat).T
+    e = []
+    for n2 in range(L2):
+        for n1 in range(L1):
+            k = n1 / L1 * G[0] + n2 / L2 * G[1]
+            f = 1 + np.exp(1j * k @ (a1 - a2)) + np.exp(-1j * k @ a2)
+            e += [t * abs(f) - mu, -t * abs(f) - mu]
+    return np.sort(np.array(e))
+
+
+@pytest.mark.parametrize("lattice", ["square4x4", "square4x4_tp_mu", "honeycomb3x3"])
+def test_free_fermion_closed_form(orc, lattice):
+    if lattice == "square4x4":
+        K, eps, dtau, L = W.square_lattice(4, 4), square_dispersion(4, 4, 1.0, 0.0, 0.0), 0.1, 20
+    elif lattice == "square4x4_tp_mu":
+        K, eps, dtau, L = (W.square_lattice(4, 4, 1.0, -0.2, -0.5), square_dispersion(4, 4, 1.0, -0.2, -0.5), 0.05, 40)
+    else:
+        K, eps, dtau, L = W.honeycomb_lattice(3, 3), honeycomb_dispersion(3, 3, 1.0, 0.0), 0.1, 30
+    beta = dtau * L
+    # the lattice builder reproduces the analytic band structure
+    assert np.allclose(np.linalg.eigvalsh(K), eps, atol=1e-12)
+    m = make_model(orc, K, 0.0, dtau, L, 10)
+    N = K.shape[0]
+    fields = W.random_fields(1, L, N, seed=3)  # irrelevant at U = 0
+    w, V = np.linalg.eigh(K)
+    Gexact = V @ np.diag(1.0 / (1.0 + np.exp(-beta * w))) @ V.T
+    ld_exact = np.sum(np.log1p(np.exp(-beta * eps)))
+    for tau in (0, 7, L):
+        for fn in (orc.green_plain, orc.green_udv):
+            G, ld, sg = fn(m, fields, 0, tau)
+            assert np.allclose(G, Gexact, atol=1e-12), (fn.__name__, tau)
+            assert ld == pytest.approx(ld_exact, rel=1e-12, abs=1e-12) and sg == 1
+    kin_exact = 2 * np.sum(eps / (1.0 + np.exp(beta * eps)))
+    e = orc.energy(m, np.stack([Gexact, Gexact]))
+    assert e[0] == pytest.approx(kin_exact, rel=1e-12, abs=1e-12)
+    n_exact = 2 * np.sum(1.0 / (1.0 + np.exp(beta * eps)))
+    assert e[2] == pytest.approx(n_exact, rel=1e-12)
+    # a chain at U = 0 accepts every proposal and its G never leaves the closed form
+    ch = orc.Chain(m, fields, seed=5, measure=True)
+    st = ch.sweep(1)
+    assert st.accepted == st.proposals == 2 * L * N
+    assert np.allclose(ch.green(1), Gexact, atol=1e-12)
+    assert st.prec_green_max < 1e-12
+    meas, ssum, nm = ch.measure()
+    assert nm == 2 * L and ssum == nm
+    assert meas[0] / nm == pytest.approx(kin_exact, rel=1e-11, abs=1e-11)
+
+
+def test_free_fermion_logdet_gradient_closed_form(orc):
+    """At U = 0, log det(1 + e^{-beta K}) has d/dK_xy = -beta (1 - G)_yx exactly."""
+    K = W.square_lattice(4, 4)
+    L, dtau = 10, 0.1
+    m = make_model(orc, K, 0.0, dtau, L, 5)
+    fields = W.random_fields(1, L, 16, seed=1)
+    ld, sg, gK, gU = orc.logdet_grad(m, fields)
+    w, V = np.linalg.eigh(K)
+    G = V @ np.diag(1.0 / (1.0 + np.exp(-L * dtau * w))) @ V.T
+    g = -L * dtau * (np.eye(16) - G).T
+    gsym = g + g.T - np.diag(np.diag(g))
+    for s in range(2):
+        assert np.allclose(gK[s], gsym, atol=1e-11)
+
+
+# ----------------------------------------------------- exact enumeration vs ED
+def enumerate_ising(orc, K, U, dtau, L):
+    N = K.shape[0]
+    m = make_model(orc, K, U, dtau, L, L)
+    pref = (0.5 * math.exp(-dtau * U / 4.0)) ** (N * L)
+    Z = 0.0
+    num = np.zeros(4)
+    for bits in itertools.product((-1, 1), repeat=N * L):
+        f = np.array(bits, dtype=np.int8).reshape(L, N)
+        G0, ld0, s0 = orc.green_plain(m, f, 0, 0)
+        G1, ld1, s1 = orc.green_plain(m, f, 1, 0)
+        w = pref * s0 * s1 * math.exp(ld0 + ld1)
+        Z += w
+        num += w * orc.energy(m, np.stack([G0, G1]))
+    return Z, num / Z
+
+
+@pytest.mark.parametrize("cluster", ["dimer", "plaquette"])
+def test_enumeration_equals_fock_trace_ising(orc, cluster):
+    if cluster == "dimer":
+        K, U, dtau, L = W.chain_lattice(2, t=1.0, mu=0.3), 3.0, 0.25, 4
+    else:
+        K, U, dtau, L = W.square_lattice(2, 2, t=1.0), 4.0, 0.3, 4
+    Z, e = enumerate_ising(orc, K, U, dtau, L)
+    F = Fock(K.shape[0])
+    rho = F.trotter_ising(K, U, dtau, L)
+    Zed = np.trace(rho)
+    assert Z == pytest.approx(Zed, rel=1e-11)
+    HT = F.hopping(K)
+    Hn = F.hubbard_nn(U)
+    # estimators evaluated at the boundary tau = 0 of the trace
+    assert e[0] == pytest.approx(np.trace(HT @ rho) / Zed, rel=1e-10, abs=1e-12)
+    assert e[1] == pytest.approx(np.trace(Hn @ rho) / Zed, rel=1e-10, abs=1e-12)
+    Nop = sum(F.n(s, i) for s in range(2) for i in range(K.shape[0]))
+    assert e[2] == pytest.approx(np.trace(Nop @ rho) / Zed, rel=1e-10)
+
+
+def test_enumeration_equals_fock_trace_hs4(orc):
+    K, U, dtau, L = W.chain_lattice(2, t=1.0, mu=-0.2), 4.0, 0.2, 4
+    N = 2
+    m = make_model(orc, K, U, dtau, L, 2, ft=2)
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    Z = 0.0
+    for ls in itertools.product((-2, -1, 1, 2), repeat=N * L):
+        f = np.array(ls, dtype=np.int8).reshape(L, N)
+        _, ld0, s0 = orc.green_plain(m, f, 0, 0)
+        _, ld1, s1 = orc.green_plain(m, f, 1, 0)
+        w = np.prod([gam[l] / 4.0 for l in ls]) * s0 * s1 * math.exp(ld0 + ld1)
+        Z += w
+    F = Fock(N)
+    Zed = np.trace(F.trotter_hs4(K, U, dtau, L, eta, gam))
+    assert Z == pytest.approx(Zed, rel=1e-11)
+
+
+# ------------------------------------------------------------------ symmetries
+@pytest.mark.parametrize("lat", ["square", "honeycomb"])
+def test_particle_hole_symmetry(orc, lat):
+    if lat == "square":
+        K, D = W.square_lattice(4, 4), W.sublattice_signs_square(4, 4)
+    else:
+        K, D = W.honeycomb_lattice(2, 3), W.sublattice_signs_honeycomb(2, 3)
+    N = K.shape[0]
+    L, dtau, U = 20, 0.1, 4.0
+    m = make_model(orc, K, U, dtau, L, 10)
+    f = W.random_fields(1, L, N, seed=11)
+    lam = orc.ising_lambda(dtau, U)
+    for tau in (0, 10, 13):
+        Gu, ldu, su = orc.green_udv(m, f, 0, tau)
+        Gd, ldd, sd = orc.green_udv(m, f, 1, tau)
+        assert np.allclose(Gd, np.diag(D) @ (np.eye(N) - Gu.T) @ np.diag(D), atol=1e-12)
+        assert ldd == pytest.approx(ldu - lam * f.sum(), rel=1e-12, abs=1e-10)
+        assert su == sd == 1
+
+
+def test_udv_agrees_with_plain_product(orc):
+    K = W.square_lattice(4, 4)
+    m = make_model(orc, K, 4.0, 0.1, 20, 10)
+    f = W.random_fields(1, 20, 16, seed=4)
+    for tau in (0, 3, 10, 17, 20):
+        for s in (0, 1):
+            Gp, lp, sp = orc.green_plain(m, f, s, tau)
+            Gu, lu, su = orc.green_udv(m, f, s, tau)
+            # the plain inverse carries eps * cond(1 + B(beta,0)) (Sec. 2.3): ~1e4 here
+            assert np.abs(Gp - Gu).max() < 5e-11
+            assert lu == pytest.approx(lp, rel=1e-12) and su == sp
+
+
+def test_udv_independent_of_nwrap_at_low_temperature(orc):
+    """beta = 10, U = 4: the plain product is hopeless, chunk sizes must agree."""
+    K = W.square_lattice(4, 4)
+    L = 100
+    f = W.random_fields(1, L, 16, seed=9)
+    ref = None
+    for nw in (10, 5, 2):
+        m = make_model(orc, K, 4.0, 0.1, L, nw)
+        G, ld, sg = orc.green_udv(m, f, 0, 40)
+        if ref is None:
+            ref = (G, ld)
+        else:
+            assert np.abs(G - ref[0]).max() < 1e-9
+            assert ld == pytest.approx(ref[1], rel=1e-11)
+    # cyclicity: log det(1 + B(tau,0)B(beta,tau)) does not depend on tau
+    m = make_model(orc, K, 4.0, 0.1, L, 10)
+    lds = [orc.green_udv(m, f, 0, t)[1] for t in (0, 30, 55, 100)]
+    assert max(lds) - min(lds) < 1e-9 * abs(lds[0])
+
+
+# -------------------------------------------------------- fast updates vs fresh G
+@pytest.mark.parametrize("ft", [1, 2])
+def test_wrapped_sherman_morrison_matches_fresh(orc, ft):
+    """With n_wrap = L the only stabilisations are at tau = L (up) and 0 (down): the
+    monitor then compares G after L slices of Sherman-Morrison updates and wraps with
+    the exact G on the updated fields.  Round-off grows exponentially with the number
+    of unstabilised slices (Sec. 2.3), so a weak coupling keeps it measurable."""
+    K = W.square_lattice(4, 4)
+    m = make_model(orc, K, 2.0, 0.1, 10, 10, ft=ft)
+    ch = orc.Chain(m, None, seed=123, chain=1)
+    st = ch.sweep(3)
+    assert 0 < st.accepted < st.proposals
+    assert st.prec_green_max < 1e-10
+    f, nsw, sign = ch.fields()
+    assert nsw == 3
+    for s in (0, 1):
+        Gp, _, _ = orc.green_plain(m, f, s, 0)
+        assert np.abs(ch.green(s) - Gp).max() < 1e-12
+
+
+def test_trajectory_independent_of_stabilisation_interval(orc):
+    """Accept/reject decisions depend on G only through the ratios, which must not change
+    (beyond round-off) with the stabilisation interval: same fields for n_wrap = 1..10."""
+    K = W.square_lattice(4, 4)
+    ref = None
+    for nw in (1, 2, 5, 10):
+        m = make_model(orc, K, 4.0, 0.1, 20, nw)
+        ch = orc.Chain(m, None, seed=99, chain=2)
+        st = ch.sweep(3)
+        f, _, _ = ch.fields()
+        if ref is None:
+            ref = (f, st.accepted)
+        else:
+            assert np.array_equal(f, ref[0]) and st.accepted == ref[1]
+
+
+def test_precision_monitor_low_temperature(orc):
+    """4x4, U/t = 4, beta t = 10 (the paper's precision example size): the wrapped and
+    the fresh G agree to well below the recommended 1e-8 mean."""
+    K = W.square_lattice(4, 4)
+    m = make_model(orc, K, 4.0, 0.1, 100, 10)
+    ch = orc.Chain(m, None, seed=1, chain=0)
+    st = ch.sweep(2)
+    assert st.prec_green_mean < 1e-8
+    assert st.prec_green_max < 1e-5
+    assert st.prec_phase_max == 0.0 and st.mean_sign == 1.0
+
+
+# ---------------------------------------------------------------- derivatives
+def test_logdet_gradient_finite_differences(orc):
+    K = W.square_lattice(3, 2, t=1.0, tp=0.0, mu=0.2)
+    N = K.shape[0]
+    L, dtau, U = 8, 0.1, 3.0
+    f = W.random_fields(1, L, N, seed=21)
+    m = make_model(orc, K, U, dtau, L, 4)
+    ld, sg, gK, gU = orc.logdet_grad(m, f)
+    h = 1e-5
+
+    def ld_of(Kp, Up):
+        mm = make_model(orc, Kp, Up, dtau, L, 4)
+        return np.array([orc.green_udv(mm, f, s, 0)[1] for s in (0, 1)])
+
+    assert np.allclose(ld, ld_of(K, U), rtol=1e-12)
+    for (x, y) in ((0, 1), (2, 2), (1, 4), (0, 3)):
+        Kp = K.copy(); Km = K.copy()
+        Kp[x, y] += h; Km[x, y] -= h
+        if x != y:
+            Kp[y, x] += h; Km[y, x] -= h
+        fd = (ld_of(Kp, U) - ld_of(Km, U)) / (2 * h)
+        assert np.allclose(gK[:, x, y], fd, rtol=1e-6, atol=1e-8), (x, y)
+    fdU = (ld_of(K, U + h) - ld_of(K, U - h)) / (2 * h)
+    assert np.allclose(gU, fdU, rtol=1e-6, atol=1e-8)
+
+
+# ----------------------------------------------------------- sampler statistics
+def jackknife(x):
+    x = np.asarray(x)
+    n = len(x)
+    loo = (x.sum() - x) / (n - 1)
+    mean = loo.mean()
+    err = math.sqrt((n - 1) / n * np.sum((loo - mean) ** 2))
+    return mean, err
+
+
+@pytest.mark.parametrize("ft", [1, 2])
+def test_sampler_reproduces_exact_energies(orc, ft):
+    """Monte Carlo estimates on the 2x2 Hubbard plaquette agree with ED within 3 sigma."""
+    K = W.square_lattice(2, 2, t=1.0)
+    U, dtau, L = 4.0, 0.125, 8
+    m = make_model(orc, K, U, dtau, L, 4, ft=ft)
+    F = Fock(4)
+    if ft == 1:
+        rho = F.trotter_ising(K, U, dtau, L)
+    else:
+        gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+        eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+        rho = F.trotter_hs4(K, U, dtau, L, eta, gam)
+    Z = np.trace(rho)
+    kin_ed = np.trace(F.hopping(K) @ rho) / Z
+    pot_ed = np.trace(F.hubbard_nn(U) @ rho) / Z
+    bins_k, bins_p = [], []
+    ch = orc.Chain(m, None, seed=77, chain=0, measure=True, meas_first=0, meas_last=L)
+    ch.sweep(20)  # warm-up (measured too; discarded through the differences below)
+    prev, _, prev_n = ch.measure()
+    for b in range(40):
+        ch.sweep(50)
+        cur, _, cur_n = ch.measure()
+        d = (cur - prev) / (cur_n - prev_n)
+        bins_k.append(d[0])
+        bins_p.append(d[1])
+        prev, prev_n = cur, cur_n
+    mk, ek = jackknife(bins_k)
+    mp, ep = jackknife(bins_p)
+    assert abs(mk - kin_ed) < 3 * ek + 1e-12, (mk, ek, kin_ed)
+    assert abs(mp - pot_ed) < 3 * ep + 1e-12, (mp, ep, pot_ed)
