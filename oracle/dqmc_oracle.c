@@ -1000,13 +1000,12 @@ int orc_logdet_grad(const orc_model* m, const int8_t* fields, double* logdet_out
     mat_mul(N, tmp, Z, Z);          /* V^T A^T V */
     for (int a = 0; a < N; ++a)
       for (int b = 0; b < N; ++b) {
-        double F;
+        /* divided difference (e^{-t la} - e^{-t lb})/(la - lb), written without
+         * cancellation: -t e^{-t(la+lb)/2} sinh(x)/x with x = t(la-lb)/2 */
         const double la = w[a], lb = w[b];
-        if (fabs(la - lb) > 1e-9 * (1.0 + fabs(la) + fabs(lb)))
-          F = (exp(-M.dtau * la) - exp(-M.dtau * lb)) / (la - lb);
-        else
-          F = -M.dtau * exp(-M.dtau * 0.5 * (la + lb));
-        Z[a * N + b] *= F;
+        const double x = 0.5 * M.dtau * (la - lb);
+        const double shc = (x == 0.0) ? 1.0 : sinh(x) / x;
+        Z[a * N + b] *= -M.dtau * exp(-0.5 * M.dtau * (la + lb)) * shc;
       }
     mat_mul(N, V, Z, Z);
     mat_mul(N, Z, tmp, Z);          /* V Z V^T */
