@@ -1,0 +1,172 @@
+/*
+ * dqmc.h -- C ABI of the GB300 (sm_103a) library for the finite-temperature
+ * auxiliary-field (BSS / DQMC) sweep documented in the ALF 1.0 paper
+ * (Assaad et al., arXiv:1704.00131).
+ *
+ * The library runs Markov chains of Hubbard-type models on one GPU.  For a
+ * field configuration C the weight is prod_s det(1 + B^s(beta,0)) (Sec. 2.1,
+ * Eq. partition_2), with the one-slice propagator
+ *     B^s_tau = exp(-dtau K^s) exp(V^s_tau),   V^s_tau = diag(v^s_i,tau),
+ *     v^s_i,tau = sigma^s_k c(field_k,tau)  at site i = vertex_site[k],
+ * and the equal-time Green function G^s(tau) = (1 + B^s(tau,0) B^s(beta,tau))^-1
+ * (Eq. Green_eq).  Field types:
+ *     DQMC_FIELD_ISING (paper type 1): fields +-1, c(s) = lambda s with
+ *         cosh(lambda) = exp(dtau U / 2): the exact two-valued decoupling of
+ *         exp(-dtau U (n_up - 1/2)(n_dn - 1/2)) for sigma = (+1, -1);
+ *     DQMC_FIELD_HS4 (paper type 2, Sec. 2.1): fields -2,-1,1,2,
+ *         c(l) = sqrt(dtau U / 2) eta(l) with weights gamma(l) (M_z Hubbard,
+ *         Sec. 6.2).
+ * A sweep visits every field twice, tau = 1..L then L..1 (Sec. 2.4,
+ * Algorithm 1), proposes single-field changes accepted with
+ * min(1, |W'/W|) (Sec. 2.2.1), wraps G between slices and recomputes it
+ * from a QR-stabilised UDV chain every n_wrap slices (Sec. 2.3).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major, dense, double precision on the host unless the
+ *     argument says otherwise.
+ *   - The library owns the context and every device buffer; inputs are copied
+ *     at the call.  Outputs go to caller buffers.
+ *   - Work is enqueued on the CUDA stream given at dqmc_init; a call that
+ *     returns host data synchronises that stream before returning.
+ *   - Errors are reported by the returned status only (no exceptions, no
+ *     abort, no device trap); dqmc_last_error(ctx) gives a message.
+ *   - One context per host thread.
+ *   - No CPU fallback: every step of the sweep runs in the library's CUDA
+ *     kernels; without a usable GPU dqmc_init returns DQMC_ECUDA.
+ */
+#ifndef DQMC_H_
+#define DQMC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dqmc_ctx dqmc_ctx; /* opaque, library-owned */
+
+typedef enum {
+  DQMC_OK = 0,
+  DQMC_EINVAL = 1,    /* an argument is out of range or inconsistent          */
+  DQMC_ENOMEM = 2,    /* device or host allocation failed                      */
+  DQMC_ECUDA = 3,     /* a CUDA call failed (message in dqmc_last_error)       */
+  DQMC_EUNSTABLE = 4, /* stabilisation failed, or max|G_wrap - G_fresh|
+                         exceeded dqmc_run_opts.unstable_threshold             */
+  DQMC_ETIMEOUT = 5,  /* reserved: a bounded device wait gave up               */
+  DQMC_ESTATE = 6     /* the call is not valid in the context's state          */
+} dqmc_status;
+
+typedef enum { DQMC_FIELD_ISING = 1, DQMC_FIELD_HS4 = 2 } dqmc_field_type;
+
+/* Arithmetic of the working Green function, wraps and delayed updates.  The
+ * stabilisation (B-chain products, pivoted QR, T update, (1 + UDV)^-1 and
+ * log|det|) is FP64 in both modes. */
+typedef enum { DQMC_PREC_FP64 = 0, DQMC_PREC_MIXED = 1 } dqmc_precision;
+
+/* One model: a lattice with its couplings (Sec. 3.1, the Operator type with
+ * hopping Op_T, g = -dtau, and single-site vertices Op_V).  Chains refer to a
+ * model by index; every model of one context has the same n_flavors. */
+typedef struct {
+  int32_t n_sites;            /* N >= 1                                            */
+  int32_t n_flavors;          /* 1 or 2 (2 = spin up, spin down)                   */
+  const double* hopping;      /* [n_flavors][N][N], symmetric, -mu on the diagonal */
+  int32_t n_vertices;         /* M_V, 1 <= M_V <= N                                */
+  const int32_t* vertex_site; /* [M_V] distinct sites in [0, N)                    */
+  const double* vertex_sign;  /* [n_flavors][M_V] sigma^s_k (+1 / -1 for M_z)      */
+  double U;                   /* >= 0                                              */
+  int32_t field_type;         /* dqmc_field_type                                   */
+  double dtau;                /* > 0; beta = L dtau                                */
+  int32_t L;                  /* Trotter slices >= 1                               */
+  int32_t n_wrap;             /* stabilisation interval; L % n_wrap == 0 (Sec. 2.3)*/
+} dqmc_model_desc;
+
+typedef struct {
+  int32_t precision;          /* dqmc_precision                                    */
+  int32_t delay_k;            /* accepted flips per delayed rank-k flush, 1..64    */
+  int32_t measure;            /* nonzero: accumulate the energy estimator          */
+  int32_t meas_first;         /* measure G(tau) for meas_first <= tau <= meas_last */
+  int32_t meas_last;          /*   (upward tau = 1..L, downward tau-1 = L-1..0)    */
+  uint64_t seed;              /* Philox key (seed_lo, seed_hi ^ chain)             */
+  double unstable_threshold;  /* > 0: DQMC_EUNSTABLE when prec_green_max exceeds it*/
+  int64_t spin_limit;         /* reserved, 0                                       */
+} dqmc_run_opts;
+
+/* Statistics of one dqmc_sweep call, over all chains (Sec. 4.5 "info" file:
+ * "Precision Green" mean and max, "Precision Phase", acceptance). */
+typedef struct {
+  int64_t proposals;          /* 2 L M_V per chain per sweep                       */
+  int64_t accepted;
+  double prec_green_mean;     /* mean over events of mean_ij |G_wrap - G_fresh|    */
+  double prec_green_max;      /* max over events of max_ij |G_wrap - G_fresh|      */
+  double prec_phase_max;      /* max |sign_tracked - sign_fresh|                   */
+  double mean_sign;           /* mean over chains and sweeps of the end-of-sweep sign */
+  float ms_total;             /* device time of the call (CUDA events)             */
+} dqmc_sweep_stats;
+
+/* Create a context with n_chains chains; chain c uses models[chain_model[c]].
+ * fields_or_null: packed per chain [L_c][M_V_c] (int8, host); NULL draws them
+ * i.i.d. from Philox (counter (0xFFFFFFFF, tau, k, 0xFFFFFFFF)).  The initial
+ * left chain and G(0) are computed before return (Algorithm 1, first loop).
+ * cuda_stream: a cudaStream_t, or NULL for the default stream.
+ * Errors: DQMC_EINVAL (bad model or options), DQMC_ENOMEM, DQMC_ECUDA,
+ * DQMC_EUNSTABLE (the initial stabilisation hit a singular matrix).  On an
+ * error *out may still receive a context that only carries the message for
+ * dqmc_last_error; the caller destroys it with dqmc_destroy. */
+dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int32_t* chain_model,
+                      int32_t n_chains, const int8_t* fields_or_null, const dqmc_run_opts* opts,
+                      void* cuda_stream, dqmc_ctx** out);
+
+/* Run n_sweeps sweeps of every chain (Algorithm 1).  With stats_or_null == NULL
+ * the call only enqueues work and returns immediately; otherwise it waits for
+ * the sweeps and fills *stats_or_null.  Errors: DQMC_EINVAL (n_sweeps < 0),
+ * DQMC_ECUDA, DQMC_EUNSTABLE. */
+dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats_or_null);
+
+/* Equal-time Green function G^flavor(0) of one chain between sweeps (Eq.
+ * Green_eq).  fresh = 0: the library's working G (FP64 or the mixed path's FP32
+ * values widened); fresh = 1: recomputed from the fields through the FP64 UDV
+ * chain (Sec. 2.3).  out: N x N doubles, host (out_is_device = 0) or device.
+ * logdet_out / sign_out (nullable): log|det(1 + B(beta,0))| and its sign from
+ * the last stable recompute of that flavor. */
+dqmc_status dqmc_greens(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t fresh, double* out,
+                        int32_t out_is_device, double* logdet_out, int32_t* sign_out);
+
+/* Sign-weighted sums of the energy estimator since dqmc_init (Sec. 6.1
+ * observables in the U n_up n_dn form):
+ *     out[c][0] = sum sign * Kin,  Kin  = sum_s sum_xy K^s_xy (delta_xy - G^s_yx)
+ *     out[c][1] = sum sign * Pot,  Pot  = U sum_i (1 - G^up_ii)(1 - G^dn_ii)
+ *     out[c][2] = sum sign * Part, Part = sum_s sum_i (1 - G^s_ii)
+ *     out[c][3] = sum sign * (Kin + Pot)
+ * sign_sum[c] = sum of signs, n_meas[c] = number of measurements (host arrays). */
+dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas);
+
+/* Derivatives of log|det(1 + B^s(beta,0))| on fixed field configurations of
+ * model `model_index` (FP64):
+ *     d log|det| = sum_tau Tr[(1 - G(tau-1)) B_tau^-1 dB_tau]
+ * (from Eq. Green_eq by d log det(1 + B) = Tr[(1 + B)^-1 dB]).
+ * fields: [n_cfg][L][M_V] int8 host.  Outputs (host):
+ *     logdet  [n_cfg][n_flavors]
+ *     grad_K  [n_cfg][n_flavors][N][N]: d/dK^s_xy with K_xy and K_yx varied
+ *             together (x != y); d/dK_xx on the diagonal
+ *     grad_U  [n_cfg][n_flavors]: d/dU through the couplings c(field). */
+dqmc_status dqmc_logdet_backward(dqmc_ctx* ctx, int32_t model_index, const int8_t* fields, int32_t n_cfg,
+                                 double* logdet, double* grad_K, double* grad_U);
+
+/* Checkpoint: fields of every chain, packed [c][L_c][M_V_c] (host), and the
+ * Philox sweep counter (confout / confin of Algorithm 1). */
+dqmc_status dqmc_get_fields(dqmc_ctx* ctx, int8_t* out, uint64_t* rng_counter);
+/* Resume: replaces the fields and the sweep counter and recomputes the left
+ * chain and G(0) of every chain. */
+dqmc_status dqmc_set_fields(dqmc_ctx* ctx, const int8_t* in, uint64_t rng_counter);
+
+/* Per-context message of the last failing call; valid until the next call. */
+const char* dqmc_last_error(const dqmc_ctx* ctx);
+
+/* Frees every resource of the context; NULL-safe. */
+void dqmc_destroy(dqmc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQMC_H_ */

@@ -1,0 +1,654 @@
+// Host side of the C ABI declared in include/dqmc.h: validation, model set-up
+// (the exponentials exp(-+dtau K) of Sec. 3.1, Op_set), the device arena of
+// every chain, and the launches of the kernels in dqmc_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/dqmc.h"
+#include "dqmc_internal.h"
+
+using dqmc::ChainDev;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Symmetric eigendecomposition A = V diag(w) V^T (host, FP64): Jacobi
+// rotations with the classical threshold strategy (Rutishauser), sweeping the
+// upper triangle until every off-diagonal element is below the threshold.
+// ---------------------------------------------------------------------------
+void symmetric_eigen(int n, const std::vector<double>& A_in, std::vector<double>& w, std::vector<double>& V) {
+  std::vector<double> a(A_in);
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  auto at = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
+  double scale = 0.0;
+  for (double x : a) scale = std::max(scale, std::fabs(x));
+  if (scale == 0.0) scale = 1.0;
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off = std::max(off, std::fabs(at(i, j)));
+    if (off <= 1e-17 * scale) break;
+    const double thresh = (sweep < 4) ? 0.2 * off : 0.0;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = at(p, q);
+        if (std::fabs(apq) <= thresh || apq == 0.0) continue;
+        const double h = at(q, q) - at(p, p);
+        double t;
+        if (std::fabs(h) + std::fabs(apq) * 1e18 == std::fabs(apq) * 1e18) {
+          t = apq / h;
+        } else {
+          const double theta = 0.5 * h / apq;
+          t = 1.0 / (std::fabs(theta) + std::sqrt(1.0 + theta * theta));
+          if (theta < 0.0) t = -t;
+        }
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        // A <- J^T A J with J the rotation in the (p, q) plane
+        for (int k = 0; k < n; ++k) {
+          const double akp = at(k, p), akq = at(k, q);
+          at(k, p) = c * akp - s * akq;
+          at(k, q) = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = at(p, k), aqk = at(q, k);
+          at(p, k) = c * apk - s * aqk;
+          at(q, k) = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double& vkp = V[(size_t)k * n + p];
+          double& vkq = V[(size_t)k * n + q];
+          const double x = vkp, y = vkq;
+          vkp = c * x - s * y;
+          vkq = s * x + c * y;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = at(i, i);
+}
+
+// exp(t K) through the eigendecomposition of K.
+std::vector<double> expm_symmetric(int n, const std::vector<double>& w, const std::vector<double>& V, double t) {
+  std::vector<double> E((size_t)n * n, 0.0);
+  std::vector<double> ex(n);
+  for (int k = 0; k < n; ++k) ex[k] = std::exp(t * w[k]);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < n; ++k) acc += V[(size_t)i * n + k] * ex[k] * V[(size_t)j * n + k];
+      E[(size_t)i * n + j] = acc;
+    }
+  return E;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct ModelHost {
+  dqmc_model_desc d;
+  int ld = 0;
+  double cscale = 0.0;
+  std::vector<double> hopping, vsign;
+  std::vector<int> site;
+  std::vector<double> eigval[dqmc::kMaxFlavors], eigvec[dqmc::kMaxFlavors];
+  // device
+  double *K = nullptr, *E = nullptr, *Einv = nullptr, *ident = nullptr, *vsign_d = nullptr;
+  float *E32 = nullptr, *Einv32 = nullptr;
+  int* site_d = nullptr;
+};
+
+}  // namespace
+
+struct dqmc_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  dqmc_run_opts opts{};
+  int nfl = 0;
+  std::vector<ModelHost> models;
+  std::vector<int> chain_model;
+  std::vector<ChainDev> chains_h;
+  ChainDev* chains_d = nullptr;
+  int* order_d = nullptr;
+  unsigned char* arena = nullptr;
+  std::vector<void*> model_allocs;
+  size_t smem = 0;
+  uint64_t sweep_counter = 0;
+  int maxN = 0, maxld = 0, maxMV = 0;
+  double* scratch = nullptr;  // [nfl][maxN][maxN] FP64 for dqmc_greens
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+dqmc_status fail(dqmc_ctx* ctx, dqmc_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+#define CUDA_TRY(ctx, expr)                                                                      \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess) return fail(ctx, DQMC_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+dqmc_status validate_model(dqmc_ctx* ctx, const dqmc_model_desc& m, int idx) {
+  if (m.n_sites < 1 || m.n_flavors < 1 || m.n_flavors > dqmc::kMaxFlavors)
+    return fail(ctx, DQMC_EINVAL, "model %d: n_sites must be >= 1 and n_flavors 1 or 2", idx);
+  if (!m.hopping || !m.vertex_site || !m.vertex_sign) return fail(ctx, DQMC_EINVAL, "model %d: null array", idx);
+  if (m.n_vertices < 1 || m.n_vertices > m.n_sites)
+    return fail(ctx, DQMC_EINVAL, "model %d: n_vertices must be in [1, n_sites]", idx);
+  if (m.field_type != DQMC_FIELD_ISING && m.field_type != DQMC_FIELD_HS4)
+    return fail(ctx, DQMC_EINVAL, "model %d: unknown field_type %d", idx, m.field_type);
+  if (!(m.dtau > 0.0) || !std::isfinite(m.dtau)) return fail(ctx, DQMC_EINVAL, "model %d: dtau must be > 0", idx);
+  if (!(m.U >= 0.0) || !std::isfinite(m.U)) return fail(ctx, DQMC_EINVAL, "model %d: U must be >= 0", idx);
+  if (m.L < 1 || m.n_wrap < 1 || m.L % m.n_wrap != 0)
+    return fail(ctx, DQMC_EINVAL, "model %d: L must be a positive multiple of n_wrap", idx);
+  const int N = m.n_sites;
+  std::vector<char> seen(N, 0);
+  for (int k = 0; k < m.n_vertices; ++k) {
+    const int s = m.vertex_site[k];
+    if (s < 0 || s >= N || seen[s]) return fail(ctx, DQMC_EINVAL, "model %d: vertex sites must be distinct in [0,N)", idx);
+    seen[s] = 1;
+  }
+  for (int f = 0; f < m.n_flavors; ++f) {
+    const double* K = m.hopping + (size_t)f * N * N;
+    double mx = 0.0;
+    for (int i = 0; i < N * N; ++i) {
+      if (!std::isfinite(K[i])) return fail(ctx, DQMC_EINVAL, "model %d: non-finite hopping", idx);
+      mx = std::max(mx, std::fabs(K[i]));
+    }
+    for (int i = 0; i < N; ++i)
+      for (int j = i + 1; j < N; ++j)
+        if (std::fabs(K[(size_t)i * N + j] - K[(size_t)j * N + i]) > 1e-12 * (1.0 + mx))
+          return fail(ctx, DQMC_EINVAL, "model %d: hopping matrix of flavor %d is not symmetric", idx, f);
+    for (int k = 0; k < m.n_vertices; ++k)
+      if (!std::isfinite(m.vertex_sign[(size_t)f * m.n_vertices + k]))
+        return fail(ctx, DQMC_EINVAL, "model %d: non-finite vertex_sign", idx);
+  }
+  return DQMC_OK;
+}
+
+template <typename T>
+dqmc_status upload(dqmc_ctx* ctx, T** dst, const T* src, size_t n) {
+  void* p = nullptr;
+  CUDA_TRY(ctx, cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)));
+  ctx->model_allocs.push_back(p);
+  if (n) CUDA_TRY(ctx, cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  *dst = (T*)p;
+  return DQMC_OK;
+}
+
+dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
+  const dqmc_model_desc& d = M.d;
+  const int N = d.n_sites, nfl = d.n_flavors;
+  const int ld = (int)align_up(N, 4);
+  M.ld = ld;
+  M.cscale = (d.field_type == DQMC_FIELD_ISING) ? std::acosh(std::exp(0.5 * d.dtau * d.U)) : std::sqrt(0.5 * d.dtau * d.U);
+  M.hopping.assign(d.hopping, d.hopping + (size_t)nfl * N * N);
+  M.vsign.assign(d.vertex_sign, d.vertex_sign + (size_t)nfl * d.n_vertices);
+  M.site.assign(d.vertex_site, d.vertex_site + d.n_vertices);
+  M.d.hopping = nullptr;
+  M.d.vertex_site = nullptr;
+  M.d.vertex_sign = nullptr;
+  std::vector<double> K((size_t)nfl * N * ld, 0.0), E((size_t)nfl * N * ld, 0.0), Ei((size_t)nfl * N * ld, 0.0);
+  std::vector<float> E32((size_t)nfl * N * ld, 0.f), Ei32((size_t)nfl * N * ld, 0.f);
+  for (int f = 0; f < nfl; ++f) {
+    std::vector<double> Kf(M.hopping.begin() + (size_t)f * N * N, M.hopping.begin() + (size_t)(f + 1) * N * N);
+    symmetric_eigen(N, Kf, M.eigval[f], M.eigvec[f]);
+    const std::vector<double> Ef = expm_symmetric(N, M.eigval[f], M.eigvec[f], -d.dtau);
+    const std::vector<double> Eif = expm_symmetric(N, M.eigval[f], M.eigvec[f], +d.dtau);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        const size_t o = (size_t)f * N * ld + (size_t)i * ld + j;
+        K[o] = Kf[(size_t)i * N + j];
+        E[o] = Ef[(size_t)i * N + j];
+        Ei[o] = Eif[(size_t)i * N + j];
+        E32[o] = (float)E[o];
+        Ei32[o] = (float)Ei[o];
+      }
+  }
+  std::vector<double> ident((size_t)2 * N * ld + ld, 0.0);
+  for (int i = 0; i < N; ++i) {
+    ident[(size_t)i * ld + i] = 1.0;
+    ident[(size_t)N * ld + (size_t)i * ld + i] = 1.0;
+    ident[(size_t)2 * N * ld + i] = 1.0;
+  }
+  dqmc_status st;
+  if ((st = upload(ctx, &M.K, K.data(), K.size()))) return st;
+  if ((st = upload(ctx, &M.E, E.data(), E.size()))) return st;
+  if ((st = upload(ctx, &M.Einv, Ei.data(), Ei.size()))) return st;
+  if ((st = upload(ctx, &M.E32, E32.data(), E32.size()))) return st;
+  if ((st = upload(ctx, &M.Einv32, Ei32.data(), Ei32.size()))) return st;
+  if ((st = upload(ctx, &M.ident, ident.data(), ident.size()))) return st;
+  if ((st = upload(ctx, &M.site_d, M.site.data(), M.site.size()))) return st;
+  if ((st = upload(ctx, &M.vsign_d, M.vsign.data(), M.vsign.size()))) return st;
+  return DQMC_OK;
+}
+
+// Per-chain device memory, carved from one arena.  Returns the bytes needed
+// (ptrs filled when base != nullptr).
+size_t chain_layout(const ModelHost& M, int precision, int delay_k, unsigned char* base, ChainDev* C) {
+  const int N = M.d.n_sites, ld = M.ld, nfl = M.d.n_flavors, nst = M.d.L / M.d.n_wrap;
+  const size_t rs = precision == DQMC_PREC_FP64 ? sizeof(double) : sizeof(float);
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> unsigned char* {
+    off = align_up(off, 256);
+    unsigned char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  unsigned char* p = take((size_t)M.d.L * M.d.n_vertices);
+  if (C) C->fields = (int8_t*)p;
+  for (int s = 0; s < nfl; ++s) {
+    p = take((size_t)N * ld * rs);
+    if (C) C->G[s] = p;
+    p = take((size_t)N * ld * rs);
+    if (C) C->Gtmp[s] = p;
+    p = take((size_t)delay_k * ld * rs);
+    if (C) C->dA[s] = p;
+    p = take((size_t)delay_k * ld * rs);
+    if (C) C->dB[s] = p;
+    p = take((size_t)(nst + 1) * dqmc::slot_stride(N, ld) * sizeof(double));
+    if (C) C->slots[s] = (double*)p;
+    p = take((size_t)(nst + 1) * sizeof(int));
+    if (C) C->slot_detq[s] = (int*)p;
+    p = take(dqmc::work_elems(N, ld) * sizeof(double));
+    if (C) C->work[s] = (double*)p;
+    p = take((size_t)2 * ld * sizeof(int));
+    if (C) C->iwork[s] = (int*)p;
+  }
+  return align_up(off, 256);
+}
+
+void fill_model_fields(const ModelHost& M, ChainDev& C) {
+  const dqmc_model_desc& d = M.d;
+  C.N = d.n_sites;
+  C.ld = M.ld;
+  C.nfl = d.n_flavors;
+  C.MV = d.n_vertices;
+  C.L = d.L;
+  C.nw = d.n_wrap;
+  C.ft = d.field_type;
+  C.dtau = d.dtau;
+  C.U = d.U;
+  C.cscale = M.cscale;
+  const size_t mat = (size_t)d.n_sites * M.ld;
+  for (int s = 0; s < d.n_flavors; ++s) {
+    C.K[s] = M.K + s * mat;
+    C.E[s] = M.E + s * mat;
+    C.Einv[s] = M.Einv + s * mat;
+    C.E32[s] = M.E32 + s * mat;
+    C.Einv32[s] = M.Einv32 + s * mat;
+  }
+  C.site = M.site_d;
+  C.vsign = M.vsign_d;
+  C.ident = M.ident;
+}
+
+dqmc_status sync_check(dqmc_ctx* ctx) {
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return DQMC_OK;
+}
+
+dqmc_status download_chains(dqmc_ctx* ctx) {
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->chains_h.data(), ctx->chains_d, sizeof(ChainDev) * ctx->chains_h.size(),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+  return sync_check(ctx);
+}
+
+// Fields in place -> left chain, G(0), sign of every chain.
+dqmc_status initial_fill(dqmc_ctx* ctx) {
+  const int n = (int)ctx->chains_h.size();
+  dqmc::set_smem_bytes(ctx->smem);
+  CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, n, ctx->nfl, ctx->opts.precision, 1, nullptr, -1, ctx->stream));
+  CUDA_TRY(ctx, dqmc::launch_finalize_init(ctx->chains_d, n, ctx->stream));
+  dqmc_status st = download_chains(ctx);
+  if (st) return st;
+  for (const ChainDev& C : ctx->chains_h)
+    if (C.error) return fail(ctx, DQMC_EUNSTABLE, "chain %u: singular matrix in the stabilisation", C.chain_id);
+  return DQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int32_t* chain_model, int32_t n_chains,
+                      const int8_t* fields_or_null, const dqmc_run_opts* opts, void* cuda_stream, dqmc_ctx** out) {
+  if (!out) return DQMC_EINVAL;
+  *out = nullptr;
+  std::unique_ptr<dqmc_ctx> ctx(new dqmc_ctx());
+  dqmc_ctx* c = ctx.get();
+  if (!models || n_models < 1 || !chain_model || n_chains < 1 || !opts) {
+    *out = ctx.release();
+    return fail(*out, DQMC_EINVAL, "null argument or empty model/chain list");
+  }
+  c->opts = *opts;
+  if (opts->precision != DQMC_PREC_FP64 && opts->precision != DQMC_PREC_MIXED) {
+    *out = ctx.release();
+    return fail(*out, DQMC_EINVAL, "unknown precision %d", opts->precision);
+  }
+  if (opts->delay_k < 1 || opts->delay_k > 64) {
+    *out = ctx.release();
+    return fail(*out, DQMC_EINVAL, "delay_k must be in [1, 64]");
+  }
+  c->stream = (cudaStream_t)cuda_stream;
+  dqmc_status st = DQMC_OK;
+  for (int m = 0; m < n_models && !st; ++m) st = validate_model(c, models[m], m);
+  for (int m = 1; m < n_models && !st; ++m)
+    if (models[m].n_flavors != models[0].n_flavors) st = fail(c, DQMC_EINVAL, "all models need the same n_flavors");
+  for (int i = 0; i < n_chains && !st; ++i)
+    if (chain_model[i] < 0 || chain_model[i] >= n_models) st = fail(c, DQMC_EINVAL, "chain_model[%d] out of range", i);
+  if (st) {
+    *out = ctx.release();
+    return st;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    *out = ctx.release();
+    return fail(*out, DQMC_ECUDA, "no CUDA device available (the library has no CPU path)");
+  }
+  c->nfl = models[0].n_flavors;
+  c->models.resize(n_models);
+  for (int m = 0; m < n_models && !st; ++m) {
+    c->models[m].d = models[m];
+    st = setup_model(c, c->models[m]);
+    c->maxN = std::max(c->maxN, models[m].n_sites);
+    c->maxld = std::max(c->maxld, c->models[m].ld);
+    c->maxMV = std::max(c->maxMV, models[m].n_vertices);
+  }
+  if (st) {
+    *out = ctx.release();
+    return st;
+  }
+  c->chain_model.assign(chain_model, chain_model + n_chains);
+  // arena
+  std::vector<size_t> offs(n_chains);
+  size_t total = 0;
+  for (int i = 0; i < n_chains; ++i) {
+    offs[i] = total;
+    total += chain_layout(c->models[chain_model[i]], opts->precision, opts->delay_k, nullptr, nullptr);
+  }
+  if (cudaMalloc((void**)&c->arena, total) != cudaSuccess) {
+    *out = ctx.release();
+    return fail(*out, DQMC_ENOMEM, "device arena of %zu bytes", total);
+  }
+  cudaMemsetAsync(c->arena, 0, total, c->stream);
+  c->chains_h.assign(n_chains, ChainDev{});
+  size_t foff = 0;
+  for (int i = 0; i < n_chains; ++i) {
+    ChainDev& C = c->chains_h[i];
+    const ModelHost& M = c->models[chain_model[i]];
+    chain_layout(M, opts->precision, opts->delay_k, c->arena + offs[i], &C);
+    fill_model_fields(M, C);
+    C.chain_id = (uint32_t)i;
+    C.sign = 1;
+    if (fields_or_null) {
+      const size_t nf = (size_t)M.d.L * M.d.n_vertices;
+      for (size_t q = 0; q < nf; ++q) {
+        const int8_t f = fields_or_null[foff + q];
+        const bool ok = (M.d.field_type == DQMC_FIELD_ISING) ? (f == 1 || f == -1)
+                                                             : (f == 1 || f == -1 || f == 2 || f == -2);
+        if (!ok) {
+          *out = ctx.release();
+          return fail(*out, DQMC_EINVAL, "chain %d: invalid field value %d", i, (int)f);
+        }
+      }
+      cudaMemcpyAsync(C.fields, fields_or_null + foff, nf, cudaMemcpyHostToDevice, c->stream);
+      foff += nf;
+    }
+  }
+  *out = ctx.release();
+  c = *out;
+  CUDA_TRY(c, cudaMalloc((void**)&c->chains_d, sizeof(ChainDev) * n_chains));
+  CUDA_TRY(c, cudaMemcpyAsync(c->chains_d, c->chains_h.data(), sizeof(ChainDev) * n_chains, cudaMemcpyHostToDevice,
+                              c->stream));
+  // heavy chains first (cost ~ L N^3)
+  std::vector<int> order(n_chains);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const auto& A = c->chains_h[a];
+    const auto& B = c->chains_h[b];
+    return (double)A.L * A.N * A.N * A.N > (double)B.L * B.N * B.N * B.N;
+  });
+  CUDA_TRY(c, cudaMalloc((void**)&c->order_d, sizeof(int) * n_chains));
+  CUDA_TRY(c, cudaMemcpyAsync(c->order_d, order.data(), sizeof(int) * n_chains, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMalloc((void**)&c->scratch, sizeof(double) * c->nfl * c->maxN * c->maxN));
+  CUDA_TRY(c, cudaEventCreate(&c->ev0));
+  CUDA_TRY(c, cudaEventCreate(&c->ev1));
+  c->smem = dqmc::sweep_smem_bytes(c->maxN, c->maxld, c->maxMV, opts->delay_k, opts->precision);
+  if (!fields_or_null) CUDA_TRY(c, dqmc::launch_init_fields(c->chains_d, n_chains, opts->seed, 0, 0, c->stream));
+  return initial_fill(c);
+}
+
+dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats) {
+  if (!ctx) return DQMC_EINVAL;
+  if (n_sweeps < 0) return fail(ctx, DQMC_EINVAL, "n_sweeps < 0");
+  const int n = (int)ctx->chains_h.size();
+  CUDA_TRY(ctx, dqmc::launch_reset_stats(ctx->chains_d, n, ctx->stream));
+  if (stats) CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+  dqmc::SweepParams P{};
+  P.seed = ctx->opts.seed;
+  P.delay_k = ctx->opts.delay_k;
+  P.measure = ctx->opts.measure;
+  P.meas_first = ctx->opts.meas_first;
+  P.meas_last = ctx->opts.meas_last;
+  P.n_chains = n;
+  P.order = ctx->order_d;
+  for (int i = 0; i < n_sweeps; ++i) {
+    P.sweep = ctx->sweep_counter++;
+    CUDA_TRY(ctx, dqmc::launch_sweep(ctx->chains_d, P, ctx->nfl, ctx->opts.precision, ctx->smem, ctx->stream));
+  }
+  if (!stats) return DQMC_OK;
+  CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+  dqmc_status st = download_chains(ctx);
+  if (st) return st;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  dqmc_sweep_stats S{};
+  double prec_sum = 0.0, sign_sum = 0.0;
+  int64_t events = 0;
+  int err = 0;
+  for (const ChainDev& C : ctx->chains_h) {
+    S.proposals += C.proposals;
+    S.accepted += C.accepted;
+    for (int s = 0; s < C.nfl; ++s) {
+      prec_sum += C.prec_sum[s];
+      S.prec_green_max = std::max(S.prec_green_max, C.prec_max[s]);
+    }
+    events += C.prec_events;
+    S.prec_phase_max = std::max(S.prec_phase_max, C.phase_max);
+    sign_sum += C.sweep_sign_sum;
+    err |= C.error;
+  }
+  S.prec_green_mean = events ? prec_sum / (double)events : 0.0;
+  S.mean_sign = n_sweeps ? sign_sum / ((double)n_sweeps * n) : 0.0;
+  S.ms_total = ms;
+  *stats = S;
+  if (err) return fail(ctx, DQMC_EUNSTABLE, "singular matrix in the stabilisation");
+  if (ctx->opts.unstable_threshold > 0.0 && S.prec_green_max > ctx->opts.unstable_threshold)
+    return fail(ctx, DQMC_EUNSTABLE, "max|G_wrap - G_fresh| = %.3e exceeds %.3e", S.prec_green_max,
+                ctx->opts.unstable_threshold);
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_greens(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t fresh, double* out,
+                        int32_t out_is_device, double* logdet_out, int32_t* sign_out) {
+  if (!ctx) return DQMC_EINVAL;
+  if (chain < 0 || chain >= (int)ctx->chains_h.size() || flavor < 0 || flavor >= ctx->nfl || !out)
+    return fail(ctx, DQMC_EINVAL, "chain or flavor out of range, or null output");
+  const int N = ctx->chains_h[chain].N;
+  double* src;
+  if (fresh) {
+    dqmc::set_smem_bytes(ctx->smem);
+    CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, (int)ctx->chains_h.size(), ctx->nfl, ctx->opts.precision, 0,
+                                           ctx->scratch, chain, ctx->stream));
+    src = ctx->scratch + (size_t)flavor * N * N;
+  } else {
+    CUDA_TRY(ctx, dqmc::launch_copy_green(ctx->chains_d, chain, flavor, ctx->opts.precision, ctx->scratch, ctx->stream));
+    src = ctx->scratch;
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(out, src, sizeof(double) * N * N,
+                                out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  dqmc_status st = download_chains(ctx);
+  if (st) return st;
+  const ChainDev& C = ctx->chains_h[chain];
+  if (C.error) return fail(ctx, DQMC_EUNSTABLE, "singular matrix in the stabilisation");
+  if (logdet_out) *logdet_out = C.logdet[flavor];
+  if (sign_out) *sign_out = C.fresh_sign[flavor];
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas) {
+  if (!ctx) return DQMC_EINVAL;
+  if (!out || !sign_sum || !n_meas) return fail(ctx, DQMC_EINVAL, "null output");
+  dqmc_status st = download_chains(ctx);
+  if (st) return st;
+  for (size_t c = 0; c < ctx->chains_h.size(); ++c) {
+    const ChainDev& C = ctx->chains_h[c];
+    for (int q = 0; q < 4; ++q) out[c * 4 + q] = C.meas[q];
+    sign_sum[c] = C.meas_sign;
+    n_meas[c] = C.n_meas;
+  }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_get_fields(dqmc_ctx* ctx, int8_t* out, uint64_t* rng_counter) {
+  if (!ctx) return DQMC_EINVAL;
+  if (!out) return fail(ctx, DQMC_EINVAL, "null output");
+  size_t off = 0;
+  for (const ChainDev& C : ctx->chains_h) {
+    const size_t nf = (size_t)C.L * C.MV;
+    CUDA_TRY(ctx, cudaMemcpyAsync(out + off, C.fields, nf, cudaMemcpyDeviceToHost, ctx->stream));
+    off += nf;
+  }
+  if (rng_counter) *rng_counter = ctx->sweep_counter;
+  return sync_check(ctx);
+}
+
+dqmc_status dqmc_set_fields(dqmc_ctx* ctx, const int8_t* in, uint64_t rng_counter) {
+  if (!ctx) return DQMC_EINVAL;
+  if (!in) return fail(ctx, DQMC_EINVAL, "null input");
+  size_t off = 0;
+  for (const ChainDev& C : ctx->chains_h) {
+    const size_t nf = (size_t)C.L * C.MV;
+    for (size_t q = 0; q < nf; ++q) {
+      const int8_t f = in[off + q];
+      const bool ok = (C.ft == DQMC_FIELD_ISING) ? (f == 1 || f == -1) : (f == 1 || f == -1 || f == 2 || f == -2);
+      if (!ok) return fail(ctx, DQMC_EINVAL, "chain %u: invalid field value %d", C.chain_id, (int)f);
+    }
+    CUDA_TRY(ctx, cudaMemcpyAsync(C.fields, in + off, nf, cudaMemcpyHostToDevice, ctx->stream));
+    off += nf;
+  }
+  ctx->sweep_counter = rng_counter;
+  return initial_fill(ctx);
+}
+
+dqmc_status dqmc_logdet_backward(dqmc_ctx* ctx, int32_t model_index, const int8_t* fields, int32_t n_cfg,
+                                 double* logdet, double* grad_K, double* grad_U) {
+  if (!ctx) return DQMC_EINVAL;
+  if (model_index < 0 || model_index >= (int)ctx->models.size() || !fields || n_cfg < 1 || !logdet || !grad_K ||
+      !grad_U)
+    return fail(ctx, DQMC_EINVAL, "bad model index, empty configuration list or null output");
+  const ModelHost& M = ctx->models[model_index];
+  const int N = M.d.n_sites, nfl = M.d.n_flavors, MV = M.d.n_vertices, L = M.d.L;
+  for (size_t q = 0; q < (size_t)n_cfg * L * MV; ++q) {
+    const int8_t f = fields[q];
+    const bool ok = (M.d.field_type == DQMC_FIELD_ISING) ? (f == 1 || f == -1) : (f == 1 || f == -1 || f == 2 || f == -2);
+    if (!ok) return fail(ctx, DQMC_EINVAL, "invalid field value %d", (int)f);
+  }
+  const size_t per = chain_layout(M, DQMC_PREC_FP64, 1, nullptr, nullptr);
+  unsigned char* arena = nullptr;
+  if (cudaMalloc((void**)&arena, per * n_cfg) != cudaSuccess)
+    return fail(ctx, DQMC_ENOMEM, "gradient workspace of %zu bytes", per * n_cfg);
+  std::vector<ChainDev> ch(n_cfg, ChainDev{});
+  for (int c = 0; c < n_cfg; ++c) {
+    chain_layout(M, DQMC_PREC_FP64, 1, arena + per * c, &ch[c]);
+    fill_model_fields(M, ch[c]);
+    ch[c].chain_id = (uint32_t)c;
+    ch[c].sign = 1;
+  }
+  ChainDev* ch_d = nullptr;
+  double *V_d = nullptr, *w_d = nullptr, *gK_d = nullptr, *gU_d = nullptr;
+  std::vector<double> Vh((size_t)nfl * N * N), wh((size_t)nfl * N);
+  for (int s = 0; s < nfl; ++s) {
+    std::copy(M.eigvec[s].begin(), M.eigvec[s].end(), Vh.begin() + (size_t)s * N * N);
+    std::copy(M.eigval[s].begin(), M.eigval[s].end(), wh.begin() + (size_t)s * N);
+  }
+  dqmc_status st = DQMC_OK;
+  auto cleanup = [&]() {
+    cudaFree(arena);
+    cudaFree(ch_d);
+    cudaFree(V_d);
+    cudaFree(w_d);
+    cudaFree(gK_d);
+    cudaFree(gU_d);
+  };
+#define GRAD_TRY(expr)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      st = fail(ctx, DQMC_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));             \
+      cleanup();                                                                       \
+      return st;                                                                       \
+    }                                                                                  \
+  } while (0)
+  GRAD_TRY(cudaMemsetAsync(arena, 0, per * n_cfg, ctx->stream));
+  for (int c = 0; c < n_cfg; ++c)
+    GRAD_TRY(cudaMemcpyAsync(ch[c].fields, fields + (size_t)c * L * MV, (size_t)L * MV, cudaMemcpyHostToDevice,
+                             ctx->stream));
+  GRAD_TRY(cudaMalloc((void**)&ch_d, sizeof(ChainDev) * n_cfg));
+  GRAD_TRY(cudaMemcpyAsync(ch_d, ch.data(), sizeof(ChainDev) * n_cfg, cudaMemcpyHostToDevice, ctx->stream));
+  GRAD_TRY(cudaMalloc((void**)&V_d, sizeof(double) * Vh.size()));
+  GRAD_TRY(cudaMalloc((void**)&w_d, sizeof(double) * wh.size()));
+  GRAD_TRY(cudaMalloc((void**)&gK_d, sizeof(double) * (size_t)n_cfg * nfl * N * N));
+  GRAD_TRY(cudaMalloc((void**)&gU_d, sizeof(double) * (size_t)n_cfg * nfl));
+  GRAD_TRY(cudaMemcpyAsync(V_d, Vh.data(), sizeof(double) * Vh.size(), cudaMemcpyHostToDevice, ctx->stream));
+  GRAD_TRY(cudaMemcpyAsync(w_d, wh.data(), sizeof(double) * wh.size(), cudaMemcpyHostToDevice, ctx->stream));
+  dqmc::set_smem_bytes(dqmc::sweep_smem_bytes(N, M.ld, MV, 1, 0));
+  GRAD_TRY(dqmc::launch_logdet_grad(ch_d, n_cfg, nfl, V_d, w_d, gK_d, gU_d, nullptr, ctx->stream));
+  GRAD_TRY(cudaMemcpyAsync(grad_K, gK_d, sizeof(double) * (size_t)n_cfg * nfl * N * N, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  GRAD_TRY(cudaMemcpyAsync(grad_U, gU_d, sizeof(double) * (size_t)n_cfg * nfl, cudaMemcpyDeviceToHost, ctx->stream));
+  GRAD_TRY(cudaMemcpyAsync(ch.data(), ch_d, sizeof(ChainDev) * n_cfg, cudaMemcpyDeviceToHost, ctx->stream));
+  GRAD_TRY(cudaStreamSynchronize(ctx->stream));
+#undef GRAD_TRY
+  for (int c = 0; c < n_cfg; ++c) {
+    if (ch[c].error) st = fail(ctx, DQMC_EUNSTABLE, "configuration %d: singular matrix in the stabilisation", c);
+    for (int s = 0; s < nfl; ++s) logdet[(size_t)c * nfl + s] = ch[c].logdet[s];
+  }
+  cleanup();
+  return st;
+}
+
+const char* dqmc_last_error(const dqmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void dqmc_destroy(dqmc_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->arena);
+  cudaFree(ctx->chains_d);
+  cudaFree(ctx->order_d);
+  cudaFree(ctx->scratch);
+  for (void* p : ctx->model_allocs) cudaFree(p);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+}
+
+}  // extern "C"

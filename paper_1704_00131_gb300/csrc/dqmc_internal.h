@@ -1,0 +1,86 @@
+// Internal declarations shared by the host side (dqmc_api.cu) and the kernels
+// (dqmc_kernels.cu) of the GB300 DQMC library.  Not part of the public C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dqmc {
+
+constexpr int kThreads = 256;      // threads per CTA of every kernel
+constexpr int kMaxFlavors = 2;
+
+// Device-resident description and state of one Markov chain.  One CTA per
+// (chain, flavor) works on it; the CTAs of a chain form one thread-block
+// cluster.  All matrices are row-major with leading dimension `ld`.
+struct ChainDev {
+  // model
+  int N, ld, nfl, MV, L, nw, ft;  // ft: 1 Ising, 2 four-valued HS
+  double dtau, U, cscale;         // cscale = lambda (Ising) or g (HS4)
+  const double* K[kMaxFlavors];   // hopping [N][ld]
+  const double* E[kMaxFlavors];   // exp(-dtau K) [N][ld]
+  const double* Einv[kMaxFlavors];
+  const float* E32[kMaxFlavors];  // FP32 copies for the mixed path
+  const float* Einv32[kMaxFlavors];
+  const int* site;                // [MV]
+  const double* vsign;            // [nfl][MV]
+  const double* ident;            // identity UDV: Q=I [N][ld], T=I [N][ld], D=1 [ld]
+  // state
+  int8_t* fields;                 // [L][MV]
+  void* G[kMaxFlavors];           // working G (Real) [N][ld]
+  void* Gtmp[kMaxFlavors];        // Real [N][ld] scratch for the wraps
+  void* dA[kMaxFlavors];          // Real [k][ld] delayed vectors a_m
+  void* dB[kMaxFlavors];          // Real [k][ld] delayed vectors b_m
+  double* slots[kMaxFlavors];     // FP64 [nst+1] x {Q [N][ld], T [N][ld], D [ld]}
+  int* slot_detq[kMaxFlavors];    // [nst+1]
+  double* work[kMaxFlavors];      // FP64 stabilisation workspace, kWorkMats matrices + vectors
+  int* iwork[kMaxFlavors];        // [2*ld]
+  uint32_t chain_id;
+  int sign;                       // sign of the current weight (written by rank 0)
+  // statistics of the current dqmc_sweep call, per flavor
+  double prec_sum[kMaxFlavors], prec_max[kMaxFlavors];
+  double phase_max;
+  int64_t prec_events;
+  int64_t proposals, accepted;
+  double sweep_sign_sum;
+  // measurement accumulators (sign-weighted) kin, pot, part, ener
+  double meas[4];
+  double meas_sign;
+  int64_t n_meas;
+  // last fresh log|det| and sign per flavor (written by greens/init kernels)
+  double logdet[kMaxFlavors];
+  int fresh_sign[kMaxFlavors];
+  int error;                      // nonzero: a numerical failure was detected
+};
+
+constexpr int kWorkMats = 10;     // N x ld FP64 matrices per flavor in `work`
+
+__host__ __device__ inline size_t slot_stride(int N, int ld) { return (size_t)2 * N * ld + ld; }
+__host__ __device__ inline size_t work_elems(int N, int ld) { return (size_t)kWorkMats * N * ld + 8 * (size_t)ld; }
+
+struct SweepParams {
+  uint64_t seed;
+  uint64_t sweep;        // Philox sweep counter of this sweep
+  int delay_k;
+  int measure, meas_first, meas_last;
+  int n_chains;
+  const int* order;      // chain index for cluster c (heavy chains first)
+};
+
+// launchers (dqmc_kernels.cu)
+cudaError_t launch_init_fields(ChainDev* chains, int n_chains, uint64_t seed, int maxL, int maxMV,
+                               cudaStream_t st);
+cudaError_t launch_fresh_green(ChainDev* chains, int n_chains, int nfl, int precision, int write_working,
+                               double* out, int out_chain, cudaStream_t st);
+cudaError_t launch_sweep(ChainDev* chains, const SweepParams& p, int nfl, int precision, size_t smem,
+                         cudaStream_t st);
+size_t sweep_smem_bytes(int maxN, int maxld, int maxMV, int delay_k, int precision);
+cudaError_t launch_copy_green(ChainDev* chains, int chain, int flavor, int precision, double* out,
+                              cudaStream_t st);
+void set_smem_bytes(size_t bytes);
+cudaError_t launch_finalize_init(ChainDev* chains, int n_chains, cudaStream_t st);
+cudaError_t launch_reset_stats(ChainDev* chains, int n_chains, cudaStream_t st);
+cudaError_t launch_logdet_grad(ChainDev* chains, int n_cfg, int nfl, const double* eigvec,
+                               const double* eigval, double* gK, double* gU, double* Sacc,
+                               cudaStream_t st);
+
+}  // namespace dqmc

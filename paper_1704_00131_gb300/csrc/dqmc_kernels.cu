@@ -1,0 +1,1280 @@
+// GB300 (sm_103a) kernels of the BSS/DQMC sweep.
+//
+// Work decomposition: one thread-block cluster per Markov chain, one CTA per
+// flavor (spin up / spin down of the spin-z decoupling).  The flavors are
+// independent except in the acceptance ratio R = gamma * prod_s R_s, which the
+// CTAs exchange through distributed shared memory; every other step (wraps,
+// delayed updates, the FP64 QR/UDV stabilisation, the stable recompute of G)
+// runs in the flavor's own CTA.
+//
+// Precision: the working Green function, the wraps and the delayed updates are
+// templated on `Real` (double for the plain FP64 path, float for the mixed
+// path); the stabilisation chain (B-products, pivoted QR, T update, the stable
+// (1 + UDV)^-1 and log|det|) is always FP64.
+//
+// Method (ALF 1.0 documentation, arXiv:1704.00131):
+//   B_tau = exp(-dtau K) exp(V_tau)                       Sec. 2.1, Eq. of B_tau
+//   G(tau) = (1 + B(tau,0) B(beta,tau))^-1               Eq. Green_eq
+//   sequential single-field updates, Metropolis         Sec. 2.2.1
+//   QR-stabilised chain every n_wrap slices             Sec. 2.3, Eq. green_stable
+//   sweep: tau = 1..L up, L..1 down                     Algorithm 1, Sec. 2.4
+#include <cooperative_groups.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "dqmc_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace dqmc {
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): the counter-based generator that
+// draws the proposal (u1) and acceptance (u2) uniforms of every proposal.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
+__device__ __forceinline__ double uniform53(uint32_t hi, uint32_t lo) {
+  const uint64_t w = ((uint64_t)hi << 32) | lo;
+  return (double)(w >> 11) * 0x1.0p-53;
+}
+
+// --------------------------------------------------------------------------
+// Field couplings: Ising (type 1) c(s) = lambda s; four-valued HS (type 2)
+// c(l) = g eta(l) with weight gamma(l) (Sec. 2.1, the discrete HS transform).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double hs_eta(int l) {
+  const double a = sqrt(2.0 * (3.0 - sqrt(6.0))), b = sqrt(2.0 * (3.0 + sqrt(6.0)));
+  return l == 1 ? a : l == -1 ? -a : l == 2 ? b : -b;
+}
+__device__ __forceinline__ double hs_gamma(int l) {
+  return (l == 1 || l == -1) ? 1.0 + sqrt(6.0) / 3.0 : 1.0 - sqrt(6.0) / 3.0;
+}
+__device__ __forceinline__ double coupling(int ft, double cscale, int f) {
+  return ft == 1 ? cscale * (double)f : cscale * hs_eta(f);
+}
+__device__ __forceinline__ double field_weight(int ft, int f) { return ft == 1 ? 1.0 : hs_gamma(f); }
+// Proposal: Ising flips; HS picks one of the three other values of
+// (-2,-1,1,2), in ascending order, with index floor(3 u1).
+__device__ __forceinline__ int propose_field(int ft, int f, double u1) {
+  if (ft == 1) return -f;
+  int idx = (int)floor(3.0 * u1);
+  idx = idx > 2 ? 2 : idx;
+  const int vals[4] = {-2, -1, 1, 2};
+  int n = 0, out = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (vals[q] != f) {
+      if (n == idx) out = vals[q];
+      ++n;
+    }
+  return out;
+}
+__device__ __forceinline__ double coupling_dU(int ft, double dtau, double U, double cscale, int f) {
+  if (ft == 1) return 0.5 * dtau * exp(0.5 * dtau * U) / sinh(cscale) * (double)f;
+  return dtau / (4.0 * cscale) * hs_eta(f);
+}
+
+// --------------------------------------------------------------------------
+// Block-wide reductions (deterministic order).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) r += red[w];
+  return r;
+}
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = red[0];
+#pragma unroll
+  for (int w = 1; w < kThreads / 32; ++w) r = fmax(r, red[w]);
+  return r;
+}
+__device__ __forceinline__ int block_min_int(int v, int* ired) {
+  v = __reduce_min_sync(0xffffffffu, v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) ired[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int r = ired[0];
+#pragma unroll
+  for (int w = 1; w < kThreads / 32; ++w) r = min(r, ired[w]);
+  return r;
+}
+// argmax of v over the block, ties to the lowest index; returns the index.
+__device__ __forceinline__ int block_argmax(double v, int idx, double* red, int* ired) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = v; ired[threadIdx.x >> 5] = idx; }
+  __syncthreads();
+  double bv = red[0];
+  int bi = ired[0];
+#pragma unroll
+  for (int w = 1; w < kThreads / 32; ++w)
+    if (red[w] > bv || (red[w] == bv && ired[w] < bi)) { bv = red[w]; bi = ired[w]; }
+  return bi;
+}
+
+// --------------------------------------------------------------------------
+// CTA-level dense product C = op(A) op(B), row-major, generic pointers
+// (global or shared).  64x64 output tiles, 16-deep K panels staged in shared
+// memory, 4x4 outputs per thread.  C must not alias A or B.
+// --------------------------------------------------------------------------
+template <typename T, bool TA, bool TB>
+__device__ void cta_gemm(int M, int Nc, int Kd, const T* __restrict__ A, int lda, const T* __restrict__ B,
+                         int ldb, T* __restrict__ C, int ldc, T* sm) {
+  T* As = sm;            // [16][64]
+  T* Bs = sm + 16 * 64;  // [16][64]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += 64)
+    for (int n0 = 0; n0 < Nc; n0 += 64) {
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+        for (int e = tid; e < 1024; e += kThreads) {
+          int r, kk;
+          if (!TA) { r = e >> 4; kk = e & 15; } else { kk = e >> 6; r = e & 63; }
+          const int gm = m0 + r, gk = k0 + kk;
+          T val = T(0);
+          if (gm < M && gk < Kd) val = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+          As[kk * 64 + r] = val;
+        }
+#pragma unroll
+        for (int e = tid; e < 1024; e += kThreads) {
+          int kk, c;
+          if (!TB) { kk = e >> 6; c = e & 63; } else { c = e >> 4; kk = e & 15; }
+          const int gk = k0 + kk, gn = n0 + c;
+          T val = T(0);
+          if (gk < Kd && gn < Nc) val = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+          Bs[kk * 64 + c] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          T a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + ty * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + tx * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+          if (gm < M && gn < Nc) C[(size_t)gm * ldc + gn] = acc[i][j];
+        }
+    }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void cta_copy(int N, int ld, const T* src, T* dst) {
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    dst[(size_t)x * ld + y] = src[(size_t)x * ld + y];
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------
+// Shared-memory layout of the sweep kernel.
+// --------------------------------------------------------------------------
+struct Smem {
+  double* gemm;     // 2*16*64 doubles (also used by float GEMMs)
+  double* v;        // [ld] slice potential / exp factors
+  double* ev;       // [ld]
+  double* d;        // [ld] current diagonal of the effective G
+  double* hv;       // [ld] Householder vector
+  double* u2;       // [MV]
+  double* delta;    // [MV]
+  double* gam;      // [MV]
+  double* Rs;       // [2][MV] own-flavor ratios, double buffered (read by the peer CTA)
+  double* xdiag;    // [ld] exchange: diagonal of G for the potential energy
+  double* xs;       // [8]  exchange: scalars
+  double* red;      // [32]
+  int* ired;        // [32]
+  int* qsite;       // [MV]
+  int8_t* fnew;     // [MV]
+  int8_t* fslice;   // [MV] fields of the current slice
+};
+
+__host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
+  size_t b = 0;
+  b += 2 * 16 * 64 * 8;
+  b += 6 * (size_t)ld * 8;        // v, ev, d, hv, xdiag, spare
+  b += 5 * (size_t)MV * 8;        // u2, delta, gam, Rs[2]
+  b += 8 * 8 + 32 * 8 + 32 * 4;   // xs, red, ired
+  b += (size_t)MV * 4;            // qsite
+  b += 2 * (size_t)MV + 16;       // fnew, fslice
+  return b;
+}
+
+__device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
+  Smem s;
+  double* p = reinterpret_cast<double*>(base);
+  s.gemm = p; p += 2 * 16 * 64;
+  s.v = p; p += ld;
+  s.ev = p; p += ld;
+  s.d = p; p += ld;
+  s.hv = p; p += ld;
+  s.xdiag = p; p += ld;
+  p += ld;
+  s.u2 = p; p += MV;
+  s.delta = p; p += MV;
+  s.gam = p; p += MV;
+  s.Rs = p; p += 2 * MV;
+  s.xs = p; p += 8;
+  s.red = p; p += 32;
+  int* ip = reinterpret_cast<int*>(p);
+  s.ired = ip; ip += 32;
+  s.qsite = ip; ip += MV;
+  int8_t* bp = reinterpret_cast<int8_t*>(ip);
+  s.fnew = bp; bp += MV;
+  s.fslice = bp;
+  return s;
+}
+
+// Slice potential v^s_i of slice tau (1-based) from global fields.
+__device__ void slice_potential_global(const ChainDev& C, int s, int tau, double* v) {
+  for (int x = threadIdx.x; x < C.N; x += kThreads) v[x] = 0.0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < C.MV; k += kThreads)
+    v[C.site[k]] = C.vsign[s * C.MV + k] * coupling(C.ft, C.cscale, C.fields[(size_t)(tau - 1) * C.MV + k]);
+  __syncthreads();
+}
+
+// Slice potential from the shared-memory copy of the slice's fields.
+__device__ void slice_potential_smem(const ChainDev& C, int s, const int8_t* fsl, double* v) {
+  for (int x = threadIdx.x; x < C.N; x += kThreads) v[x] = 0.0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < C.MV; k += kThreads)
+    v[C.site[k]] = C.vsign[s * C.MV + k] * coupling(C.ft, C.cscale, fsl[k]);
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------
+// FP64 stabilisation building blocks (Sec. 2.3).
+// --------------------------------------------------------------------------
+struct UDV {
+  const double* Q;
+  const double* D;
+  const double* T;
+  int detq;
+};
+
+__device__ inline double* wmat(const ChainDev& C, int s, int m) {
+  return C.work[s] + (size_t)m * C.N * C.ld;
+}
+__device__ inline double* wvec(const ChainDev& C, int s, int v) {
+  return C.work[s] + (size_t)kWorkMats * C.N * C.ld + (size_t)v * C.ld;
+}
+__device__ inline UDV ident_udv(const ChainDev& C) {
+  UDV u;
+  u.Q = C.ident;
+  u.T = C.ident + (size_t)C.N * C.ld;
+  u.D = C.ident + (size_t)2 * C.N * C.ld;
+  u.detq = 1;
+  return u;
+}
+__device__ inline double* slot_base(const ChainDev& C, int s, int j) {
+  return C.slots[s] + (size_t)j * slot_stride(C.N, C.ld);
+}
+__device__ inline UDV slot_udv(const ChainDev& C, int s, int j) {
+  UDV u;
+  double* b = slot_base(C, s, j);
+  u.Q = b;
+  u.T = b + (size_t)C.N * C.ld;
+  u.D = b + (size_t)2 * C.N * C.ld;
+  u.detq = C.slot_detq[s][j];
+  return u;
+}
+
+// Householder QR with column pivoting of M (N x N, in place): on return the
+// upper triangle holds R, the strict lower triangle the Householder vectors
+// (their leading entries in vk0), beta[k] the reflector coefficients,
+// perm[k] the original column at position k.  Returns det(Q) = (-1)^#reflectors.
+// Pivot = remaining column of largest norm (ties to the lowest index); norms
+// are downdated and recomputed when cancellation sets in (LAPACK xGEQP3 rule).
+__device__ int qr_pivoted(int N, int ld, double* M, double* beta, double* vk0, double* cn, double* cn0,
+                          int* perm, Smem& S) {
+  const int tid = threadIdx.x;
+  for (int j = tid; j < N; j += kThreads) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc = fma(M[(size_t)i * ld + j], M[(size_t)i * ld + j], acc);
+    cn[j] = sqrt(acc);
+    cn0[j] = cn[j];
+    perm[j] = j;
+  }
+  __syncthreads();
+  const double tol3z = sqrt(2.220446049250313e-16);
+  int detq = 1;
+  for (int k = 0; k < N; ++k) {
+    // pivot
+    double bv = -1.0;
+    int bi = N;
+    for (int j = k + tid; j < N; j += kThreads)
+      if (cn[j] > bv) { bv = cn[j]; bi = j; }
+    int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N) p = k;  // no finite candidate (NaN input): keep the column order
+    if (p != k) {
+      for (int i = tid; i < N; i += kThreads) {
+        const double t = M[(size_t)i * ld + k];
+        M[(size_t)i * ld + k] = M[(size_t)i * ld + p];
+        M[(size_t)i * ld + p] = t;
+      }
+      if (tid == 0) {
+        const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
+        double t = cn[k]; cn[k] = cn[p]; cn[p] = t;
+        t = cn0[k]; cn0[k] = cn0[p]; cn0[p] = t;
+      }
+      __syncthreads();
+    }
+    // reflector from column k, rows k..N-1
+    double part = 0.0;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const double x = M[(size_t)i * ld + k];
+      part = fma(x, x, part);
+      S.hv[i] = x;
+    }
+    const double xn2 = block_sum(part, S.red);
+    const double xnorm = sqrt(xn2);
+    const double x0 = S.hv[k];
+    double bk = 0.0;
+    double alpha = 0.0;
+    if (xnorm > 0.0) {
+      alpha = (x0 >= 0.0) ? -xnorm : xnorm;
+      const double v0 = x0 - alpha;
+      const double vtv = xn2 - x0 * x0 + v0 * v0;
+      bk = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+      __syncthreads();
+      if (tid == 0) S.hv[k] = v0;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      beta[k] = bk;
+      vk0[k] = S.hv[k];
+    }
+    if (bk != 0.0) detq = -detq;
+    // apply H = I - bk v v^T to the trailing columns j > k
+    if (bk != 0.0) {
+      for (int j = k + 1 + tid; j < N; j += kThreads) {
+        double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+        int i = k;
+        for (; i + 3 < N; i += 4) {
+          w0 = fma(S.hv[i], M[(size_t)i * ld + j], w0);
+          w1 = fma(S.hv[i + 1], M[(size_t)(i + 1) * ld + j], w1);
+          w2 = fma(S.hv[i + 2], M[(size_t)(i + 2) * ld + j], w2);
+          w3 = fma(S.hv[i + 3], M[(size_t)(i + 3) * ld + j], w3);
+        }
+        for (; i < N; ++i) w0 = fma(S.hv[i], M[(size_t)i * ld + j], w0);
+        const double w = bk * ((w0 + w1) + (w2 + w3));
+        for (int r = k; r < N; ++r) M[(size_t)r * ld + j] -= w * S.hv[r];
+      }
+    }
+    __syncthreads();
+    if (tid == 0) M[(size_t)k * ld + k] = (xnorm > 0.0) ? alpha : x0;
+    // downdate the trailing column norms
+    for (int j = k + 1 + tid; j < N; j += kThreads) {
+      if (cn[j] != 0.0) {
+        double t = fabs(M[(size_t)k * ld + j]) / cn[j];
+        t = fmax(0.0, (1.0 + t) * (1.0 - t));
+        const double r = cn[j] / cn0[j];
+        if (t * r * r <= tol3z) {
+          double acc = 0.0;
+          for (int i = k + 1; i < N; ++i) acc = fma(M[(size_t)i * ld + j], M[(size_t)i * ld + j], acc);
+          cn[j] = sqrt(acc);
+          cn0[j] = cn[j];
+        } else {
+          cn[j] *= sqrt(t);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return detq;
+}
+
+// Q = H_0 H_1 ... H_{N-1} from the reflectors left in M by qr_pivoted.
+__device__ void form_q(int N, int ld, const double* M, const double* beta, const double* vk0, double* Q,
+                       Smem& S) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    Q[(size_t)x * ld + y] = (x == y) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = N - 1; k >= 0; --k) {
+    const double bk = beta[k];
+    if (bk == 0.0) continue;
+    for (int i = k + tid; i < N; i += kThreads) S.hv[i] = (i == k) ? vk0[k] : M[(size_t)i * ld + k];
+    __syncthreads();
+    for (int j = k + tid; j < N; j += kThreads) {
+      double w0 = 0.0, w1 = 0.0;
+      int i = k;
+      for (; i + 1 < N; i += 2) {
+        w0 = fma(S.hv[i], Q[(size_t)i * ld + j], w0);
+        w1 = fma(S.hv[i + 1], Q[(size_t)(i + 1) * ld + j], w1);
+      }
+      for (; i < N; ++i) w0 = fma(S.hv[i], Q[(size_t)i * ld + j], w0);
+      const double w = bk * (w0 + w1);
+      for (int r = k; r < N; ++r) Q[(size_t)r * ld + j] -= w * S.hv[r];
+    }
+    __syncthreads();
+  }
+}
+
+// One step of a UDV chain (Sec. 2.3): X = Bcal Q_src, M = X D_src, M P = Q R,
+// D = |diag R|, T = D^-1 R P^T T_src.  Right chain (left == false): Bcal =
+// B_t2 ... B_t1+1.  Left chain: Bcal = B_t1+1^T ... B_t2^T.  Result in
+// (W2, wvec 0, W5); returns det(Q).
+__device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  double* X = wmat(C, s, 0);
+  double* Y = wmat(C, s, 1);
+  cta_copy(N, ld, src.Q, X);
+  const double* E = C.E[s];
+  if (!left) {
+    for (int t = t1 + 1; t <= t2; ++t) {
+      slice_potential_global(C, s, t, S.v);
+      for (int x = threadIdx.x; x < N; x += kThreads) S.ev[x] = exp(S.v[x]);
+      __syncthreads();
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        X[(size_t)x * ld + y] *= S.ev[x];
+      }
+      __syncthreads();
+      cta_gemm<double, false, false>(N, N, N, E, ld, X, ld, Y, ld, S.gemm);
+      double* t_ = X; X = Y; Y = t_;
+    }
+  } else {
+    for (int t = t2; t >= t1 + 1; --t) {
+      cta_gemm<double, true, false>(N, N, N, E, ld, X, ld, Y, ld, S.gemm);
+      slice_potential_global(C, s, t, S.v);
+      for (int x = threadIdx.x; x < N; x += kThreads) S.ev[x] = exp(S.v[x]);
+      __syncthreads();
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        Y[(size_t)x * ld + y] *= S.ev[x];
+      }
+      __syncthreads();
+      double* t_ = X; X = Y; Y = t_;
+    }
+  }
+  // M = X D_src
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    X[(size_t)x * ld + y] *= src.D[y];
+  }
+  __syncthreads();
+  double* Dn = wvec(C, s, 0);
+  double* beta = wvec(C, s, 1);
+  double* vk0 = wvec(C, s, 2);
+  int* perm = C.iwork[s];
+  const int detq = qr_pivoted(N, ld, X, beta, vk0, wvec(C, s, 3), wvec(C, s, 4), perm, S);
+  double* Qn = wmat(C, s, 2);
+  form_q(N, ld, X, beta, vk0, Qn, S);
+  double* PT = wmat(C, s, 3);
+  double* Rt = wmat(C, s, 4);
+  for (int x = threadIdx.x; x < N; x += kThreads) Dn[x] = fabs(X[(size_t)x * ld + x]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    PT[(size_t)x * ld + y] = src.T[(size_t)perm[x] * ld + y];
+    Rt[(size_t)x * ld + y] = (y >= x && Dn[x] > 0.0) ? X[(size_t)x * ld + y] / Dn[x] : 0.0;
+  }
+  __syncthreads();
+  cta_gemm<double, false, false>(N, N, N, Rt, ld, PT, ld, wmat(C, s, 5), ld, S.gemm);
+  return detq;
+}
+
+// LU with partial pivoting in place (rows swapped whole).  Returns 0 or 1 if singular.
+__device__ int lu_factor(int N, int ld, double* A, int* piv, double& logdet, int& sign, Smem& S) {
+  const int tid = threadIdx.x;
+  double ld_ = 0.0;
+  int sg = 1;
+  for (int k = 0; k < N; ++k) {
+    double bv = -1.0;
+    int bi = N;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const double a = fabs(A[(size_t)i * ld + k]);
+      if (a > bv) { bv = a; bi = i; }
+    }
+    const int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N) return 1;  // no finite pivot candidate
+    if (tid == 0) piv[k] = p;
+    const double pv = A[(size_t)p * ld + k];
+    if (!(pv != 0.0)) return 1;
+    if (p != k) {
+      for (int j = tid; j < N; j += kThreads) {
+        const double t = A[(size_t)k * ld + j];
+        A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
+        A[(size_t)p * ld + j] = t;
+      }
+      sg = -sg;
+    }
+    __syncthreads();
+    const double d = A[(size_t)k * ld + k];
+    ld_ += log(fabs(d));
+    if (d < 0.0) sg = -sg;
+    for (int i = k + 1 + tid; i < N; i += kThreads) A[(size_t)i * ld + k] /= d;
+    __syncthreads();
+    const int rem = N - k - 1;
+    for (int e = tid; e < rem * rem; e += kThreads) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      A[(size_t)i * ld + j] -= A[(size_t)i * ld + k] * A[(size_t)k * ld + j];
+    }
+    __syncthreads();
+  }
+  logdet = ld_;
+  sign = sg;
+  return 0;
+}
+
+// Solve (LU) Y = B for all columns of B (in place), rows permuted by piv first.
+__device__ void lu_solve(int N, int ld, const double* LU, const int* piv, double* B) {
+  const int tid = threadIdx.x;
+  for (int k = 0; k < N; ++k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int j = tid; j < N; j += kThreads) {
+        const double t = B[(size_t)k * ld + j];
+        B[(size_t)k * ld + j] = B[(size_t)p * ld + j];
+        B[(size_t)p * ld + j] = t;
+      }
+    __syncthreads();
+  }
+  for (int i = 1; i < N; ++i) {
+    for (int j = tid; j < N; j += kThreads) {
+      double acc = B[(size_t)i * ld + j];
+      for (int k = 0; k < i; ++k) acc -= LU[(size_t)i * ld + k] * B[(size_t)k * ld + j];
+      B[(size_t)i * ld + j] = acc;
+    }
+    __syncthreads();
+  }
+  for (int i = N - 1; i >= 0; --i) {
+    for (int j = tid; j < N; j += kThreads) {
+      double acc = B[(size_t)i * ld + j];
+      for (int k = i + 1; k < N; ++k) acc -= LU[(size_t)i * ld + k] * B[(size_t)k * ld + j];
+      B[(size_t)i * ld + j] = acc / LU[(size_t)i * ld + i];
+    }
+    __syncthreads();
+  }
+}
+
+// Stable G from a right chain R (B(tau,0) = Q_R D_R T_R) and a left chain Lf
+// (B(beta,tau)^T = Q_L D_L T_L) by scale separation, D = Db Ds with
+// Db = max(D,1), Ds = min(D,1):
+//   Mid = Db_R^-1 Q_R^T Q_L Db_L^-1 + Ds_R (T_R T_L^T) Ds_L
+//   G   = Q_L Db_L^-1 Mid^-1 Db_R^-1 Q_R^T
+//   log|det G^-1| = sum log Db_R + sum log Db_L + log|det Mid|.
+// Uses W0, W1; the result goes to Gout.  Returns nonzero if Mid is singular.
+__device__ int green_from_udv(const ChainDev& C, int s, UDV R, UDV Lf, double* Gout, double& logdet,
+                              int& sign, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  double* W0 = wmat(C, s, 0);
+  double* W1 = wmat(C, s, 1);
+  cta_gemm<double, true, false>(N, N, N, R.Q, ld, Lf.Q, ld, W0, ld, S.gemm);
+  cta_gemm<double, false, true>(N, N, N, R.T, ld, Lf.T, ld, W1, ld, S.gemm);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dR = R.D[i], dL = Lf.D[j];
+    const double dbR = dR > 1.0 ? dR : 1.0, dsR = dR > 1.0 ? 1.0 : dR;
+    const double dbL = dL > 1.0 ? dL : 1.0, dsL = dL > 1.0 ? 1.0 : dL;
+    W0[(size_t)i * ld + j] = W0[(size_t)i * ld + j] / (dbR * dbL) + dsR * W1[(size_t)i * ld + j] * dsL;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dR = R.D[i];
+    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] / (dR > 1.0 ? dR : 1.0);
+  }
+  __syncthreads();
+  double ldm;
+  int sm;
+  int* piv = C.iwork[s] + ld;
+  if (lu_factor(N, ld, W0, piv, ldm, sm, S)) return 1;
+  lu_solve(N, ld, W0, piv, W1);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dL = Lf.D[i];
+    W1[(size_t)i * ld + j] /= (dL > 1.0 ? dL : 1.0);
+  }
+  __syncthreads();
+  cta_gemm<double, false, false>(N, N, N, Lf.Q, ld, W1, ld, Gout, ld, S.gemm);
+  double part = 0.0;
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    const double dR = R.D[i], dL = Lf.D[i];
+    part += log(dR > 1.0 ? dR : 1.0) + log(dL > 1.0 ? dL : 1.0);
+  }
+  logdet = ldm + block_sum(part, S.red);
+  sign = sm * R.detq * Lf.detq;
+  return 0;
+}
+
+__device__ void copy_udv_to_slot(const ChainDev& C, int s, int j, int detq) {
+  const int N = C.N, ld = C.ld;
+  double* b = slot_base(C, s, j);
+  cta_copy(N, ld, (const double*)wmat(C, s, 2), b);
+  cta_copy(N, ld, (const double*)wmat(C, s, 5), b + (size_t)N * ld);
+  const double* Dn = wvec(C, s, 0);
+  for (int x = threadIdx.x; x < N; x += kThreads) b[(size_t)2 * N * ld + x] = Dn[x];
+  if (threadIdx.x == 0) C.slot_detq[s][j] = detq;
+  __syncthreads();
+}
+
+__device__ inline UDV work_udv(const ChainDev& C, int s, int detq) {
+  UDV u;
+  u.Q = wmat(C, s, 2);
+  u.T = wmat(C, s, 5);
+  u.D = wvec(C, s, 0);
+  u.detq = detq;
+  return u;
+}
+
+// Fill the storage with the left chain (Algorithm 1, the loop before the bins)
+// and compute G(0) into W6.
+__device__ int fill_left_chain(const ChainDev& C, int s, Smem& S, double& logdet, int& sign) {
+  const int nst = C.L / C.nw;
+  for (int j = nst - 1; j >= 0; --j) {
+    const UDV src = (j + 1 == nst) ? ident_udv(C) : slot_udv(C, s, j + 1);
+    const int dq = chain_step(C, s, j * C.nw, (j + 1) * C.nw, true, src, S);
+    copy_udv_to_slot(C, s, j, dq);
+  }
+  return green_from_udv(C, s, ident_udv(C), slot_udv(C, s, 0), wmat(C, s, 6), logdet, sign, S);
+}
+
+// --------------------------------------------------------------------------
+// Kernels.
+// --------------------------------------------------------------------------
+__global__ void init_fields_kernel(ChainDev* chains, int n_chains, uint64_t seed) {
+  const int c = blockIdx.x;
+  if (c >= n_chains) return;
+  const ChainDev& C = chains[c];
+  for (int e = threadIdx.x; e < C.L * C.MV; e += kThreads) {
+    const int t = e / C.MV, k = e - t * C.MV;
+    uint32_t ctr[4] = {0xFFFFFFFFu, (uint32_t)(t + 1), (uint32_t)k, 0xFFFFFFFFu};
+    philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32) ^ C.chain_id);
+    const double u = uniform53(ctr[0], ctr[1]);
+    int8_t f;
+    if (C.ft == 1) {
+      f = u < 0.5 ? -1 : 1;
+    } else {
+      int idx = (int)floor(4.0 * u);
+      idx = idx > 3 ? 3 : idx;
+      const int8_t vals[4] = {-2, -1, 1, 2};
+      f = vals[idx];
+    }
+    C.fields[e] = f;
+  }
+}
+
+// Fresh G(0) for every (chain, flavor): the left chain is (re)computed into the
+// storage slots, G(0) lands in W6.  mode 0: also write the working G, the
+// fresh log|det| and the sign (initialisation); mode 1: copy G(0) of chain
+// `out_chain` to `out` (FP64, [nfl][N][N]).
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains, int n_chains, int mode,
+                                                               double* out, int out_chain) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nfl = chains[0].nfl;
+  const int c = blockIdx.x / nfl, s = blockIdx.x % nfl;
+  if (c >= n_chains) return;
+  if (mode == 1 && c != out_chain) return;
+  ChainDev& C = chains[c];
+  Smem S = carve_smem(smem_raw, C.ld, C.MV);
+  double logdet;
+  int sign;
+  if (fill_left_chain(C, s, S, logdet, sign)) {
+    if (threadIdx.x == 0) C.error = 1;
+    return;
+  }
+  const double* Gf = wmat(C, s, 6);
+  if (mode == 0) {
+    Real* G = (Real*)C.G[s];
+    for (int e = threadIdx.x; e < C.N * C.N; e += kThreads) {
+      const int x = e / C.N, y = e - x * C.N;
+      G[(size_t)x * C.ld + y] = (Real)Gf[(size_t)x * C.ld + y];
+    }
+  } else {
+    for (int e = threadIdx.x; e < C.N * C.N; e += kThreads) {
+      const int x = e / C.N, y = e - x * C.N;
+      out[(size_t)s * C.N * C.N + e] = Gf[(size_t)x * C.ld + y];
+    }
+  }
+  if (threadIdx.x == 0) {
+    C.logdet[s] = logdet;
+    C.fresh_sign[s] = sign;
+  }
+}
+
+template <typename Real>
+__global__ void copy_green_kernel(ChainDev* chains, int chain, int flavor, double* out) {
+  const ChainDev& C = chains[chain];
+  const Real* G = (const Real*)C.G[flavor];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.N * C.N; e += gridDim.x * blockDim.x) {
+    const int x = e / C.N, y = e - x * C.N;
+    out[e] = (double)G[(size_t)x * C.ld + y];
+  }
+}
+
+__global__ void reset_stats_kernel(ChainDev* chains, int n_chains) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chains) return;
+  ChainDev& C = chains[c];
+  for (int s = 0; s < kMaxFlavors; ++s) { C.prec_sum[s] = 0.0; C.prec_max[s] = 0.0; }
+  C.phase_max = 0.0;
+  C.prec_events = 0;
+  C.proposals = 0;
+  C.accepted = 0;
+  C.sweep_sign_sum = 0.0;
+}
+
+// ---- pieces of the sweep --------------------------------------------------
+
+// G <- diag(ev) G diag(1/ev)  with ev = exp(a v)
+template <typename Real>
+__device__ void v_wrap(const ChainDev& C, Real* G, const double* v, double a, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    S.ev[x] = exp(a * v[x]);
+    S.hv[x] = exp(-a * v[x]);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    G[(size_t)x * ld + y] = G[(size_t)x * ld + y] * ((Real)S.ev[x] * (Real)S.hv[y]);
+  }
+  __syncthreads();
+}
+
+// Hopping wrap: up  G <- E G E^-1;  down  G <- E^-1 G E.
+template <typename Real>
+__device__ void t_wrap(const ChainDev& C, int s, Real* G, Real* Gt, bool up, Smem& S);
+
+template <>
+__device__ void t_wrap<double>(const ChainDev& C, int s, double* G, double* Gt, bool up, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  const double* X = up ? C.E[s] : C.Einv[s];
+  const double* Y = up ? C.Einv[s] : C.E[s];
+  cta_gemm<double, false, false>(N, N, N, X, ld, G, ld, Gt, ld, S.gemm);
+  cta_gemm<double, false, false>(N, N, N, Gt, ld, Y, ld, G, ld, S.gemm);
+}
+template <>
+__device__ void t_wrap<float>(const ChainDev& C, int s, float* G, float* Gt, bool up, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  const float* X = up ? C.E32[s] : C.Einv32[s];
+  const float* Y = up ? C.Einv32[s] : C.E32[s];
+  float* sm = reinterpret_cast<float*>(S.gemm);
+  cta_gemm<float, false, false>(N, N, N, X, ld, G, ld, Gt, ld, sm);
+  cta_gemm<float, false, false>(N, N, N, Gt, ld, Y, ld, G, ld, sm);
+}
+
+// G <- G + sum_m a_m b_m^T  (flush of the delayed rank-k update)
+template <typename Real>
+__device__ void flush_delayed(const ChainDev& C, Real* G, const Real* A, const Real* B, int nacc) {
+  const int N = C.N, ld = C.ld;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    Real acc = G[(size_t)x * ld + y];
+    for (int m = 0; m < nacc; ++m) acc = fma(A[(size_t)m * ld + x], B[(size_t)m * ld + y], acc);
+    G[(size_t)x * ld + y] = acc;
+  }
+  __syncthreads();
+}
+
+// Sequential single-field updates of one slice (Sec. 2.2.1) for this CTA's
+// flavor.  The ratios of every remaining position are evaluated in parallel
+// from the current diagonal of G; the first accepted position in visiting
+// order is found by a block reduction, which is exactly the sequential
+// Metropolis chain because rejected proposals leave G unchanged.  Accepted
+// flips are applied as delayed rank-1 updates (flushed every k accepts):
+//   a = -(delta/R_s) G_eff[:,i],  b = e_i - G_eff[i,:],  G_eff += a b^T.
+template <typename Real>
+__device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepParams& P, Smem& S,
+                             cg::cluster_group& cl, Real* G, Real* A, Real* B, int& sign, int& buf) {
+  const int N = C.N, ld = C.ld, MV = C.MV, nfl = C.nfl, tid = threadIdx.x;
+  const uint32_t key0 = (uint32_t)P.seed, key1 = (uint32_t)(P.seed >> 32) ^ C.chain_id;
+  for (int q = tid; q < MV; q += kThreads) {
+    const int k = dir ? MV - 1 - q : q;
+    uint32_t ctr[4] = {(uint32_t)P.sweep, (uint32_t)(2 * tau + dir), (uint32_t)k, (uint32_t)(P.sweep >> 32)};
+    philox4x32_10(ctr, key0, key1);
+    const double u1 = uniform53(ctr[0], ctr[1]);
+    S.u2[q] = uniform53(ctr[2], ctr[3]);
+    const int f = S.fslice[k];
+    const int fn = propose_field(C.ft, f, u1);
+    const double dc = coupling(C.ft, C.cscale, fn) - coupling(C.ft, C.cscale, f);
+    S.delta[q] = exp(C.vsign[s * MV + k] * dc) - 1.0;
+    S.gam[q] = field_weight(C.ft, fn) / field_weight(C.ft, f);
+    S.fnew[q] = (int8_t)fn;
+    S.qsite[q] = C.site[k];
+  }
+  for (int x = tid; x < N; x += kThreads) S.d[x] = (double)G[(size_t)x * ld + x];
+  __syncthreads();
+  int pos = 0, nacc = 0;
+  int64_t n_acc_slice = 0;
+  const int kdel = P.delay_k;
+  while (true) {
+    double* Rs = S.Rs + buf * MV;
+    for (int q = pos + tid; q < MV; q += kThreads) Rs[q] = 1.0 + S.delta[q] * (1.0 - S.d[S.qsite[q]]);
+    cl.sync();
+    const double* Rr[kMaxFlavors];
+    for (int r = 0; r < nfl; ++r) Rr[r] = (r == s) ? Rs : cl.map_shared_rank(Rs, r);
+    int first = MV;
+    for (int q = pos + tid; q < MV; q += kThreads) {
+      double R = S.gam[q];
+      for (int r = 0; r < nfl; ++r) R *= Rr[r][q];
+      const double aR = fabs(R);
+      if (S.u2[q] < (aR < 1.0 ? aR : 1.0)) { first = q; break; }
+    }
+    first = block_min_int(first, S.ired);
+    if (first >= MV) { buf ^= 1; break; }
+    double R = S.gam[first];
+    for (int r = 0; r < nfl; ++r) R *= Rr[r][first];
+    if (R < 0.0) sign = -sign;
+    const int k = dir ? MV - 1 - first : first;
+    const int i = S.qsite[first];
+    const double fac = S.delta[first] / Rs[first];
+    Real* a = A + (size_t)nacc * ld;
+    Real* b = B + (size_t)nacc * ld;
+    for (int x = tid; x < N; x += kThreads) {
+      Real cx = G[(size_t)x * ld + i], ry = G[(size_t)i * ld + x];
+      for (int m = 0; m < nacc; ++m) {
+        cx = fma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
+        ry = fma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
+      }
+      a[x] = (Real)(-fac) * cx;
+      b[x] = (x == i ? Real(1) : Real(0)) - ry;
+    }
+    __syncthreads();
+    for (int x = tid; x < N; x += kThreads) S.d[x] += (double)a[x] * (double)b[x];
+    if (tid == 0) S.fslice[k] = S.fnew[first];
+    ++nacc;
+    ++n_acc_slice;
+    if (nacc == kdel) {
+      __syncthreads();
+      flush_delayed(C, G, A, B, nacc);
+      nacc = 0;
+    }
+    pos = first + 1;
+    buf ^= 1;
+    __syncthreads();
+  }
+  if (nacc) flush_delayed(C, G, A, B, nacc);
+  if (s == 0 && tid == 0) {
+    C.proposals += MV;
+    C.accepted += n_acc_slice;
+  }
+}
+
+// Stabilisation event of this CTA's flavor at slice tau: new chain, fresh G,
+// precision monitor, working G replaced, storage slot j written.
+template <typename Real>
+__device__ void stabilise(ChainDev& C, int s, int j, bool up, Real* G, Smem& S, double& ev_max,
+                          double& ev_sum, int& fresh_sign) {
+  const int N = C.N, ld = C.ld, nst = C.L / C.nw, nw = C.nw;
+  int dq;
+  UDV R, Lf;
+  if (up) {
+    const UDV src = (j == 1) ? ident_udv(C) : slot_udv(C, s, j - 1);
+    dq = chain_step(C, s, (j - 1) * nw, j * nw, false, src, S);
+    R = work_udv(C, s, dq);
+    Lf = (j == nst) ? ident_udv(C) : slot_udv(C, s, j);
+  } else {
+    const UDV src = (j + 1 == nst) ? ident_udv(C) : slot_udv(C, s, j + 1);
+    dq = chain_step(C, s, j * nw, (j + 1) * nw, true, src, S);
+    Lf = work_udv(C, s, dq);
+    R = (j == 0) ? ident_udv(C) : slot_udv(C, s, j);
+  }
+  double* Gf = wmat(C, s, 6);
+  double logdet;
+  int sg;
+  if (green_from_udv(C, s, R, Lf, Gf, logdet, sg, S)) {
+    if (threadIdx.x == 0) C.error = 1;
+    sg = 1;
+  }
+  double mx = 0.0, sm = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double gf = Gf[(size_t)x * ld + y];
+    const double dd = fabs(gf - (double)G[(size_t)x * ld + y]);
+    mx = fmax(mx, dd);
+    sm += dd;
+    G[(size_t)x * ld + y] = (Real)gf;
+  }
+  ev_max = block_max(mx, S.red);
+  ev_sum = block_sum(sm, S.red);
+  fresh_sign = sg;
+  if (threadIdx.x == 0) {
+    C.logdet[s] = logdet;
+    C.fresh_sign[s] = sg;
+  }
+  copy_udv_to_slot(C, s, j, dq);
+}
+
+// Energy estimator at the current G (Sec. 6 observables, U n_up n_dn form).
+template <typename Real>
+__device__ void measure(ChainDev& C, int s, const Real* G, Smem& S, cg::cluster_group& cl, int sign) {
+  const int N = C.N, ld = C.ld;
+  const double* K = C.K[s];
+  double kin = 0.0, part = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    kin += K[(size_t)x * ld + y] * ((x == y ? 1.0 : 0.0) - (double)G[(size_t)y * ld + x]);
+  }
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    const double gxx = (double)G[(size_t)x * ld + x];
+    part += 1.0 - gxx;
+    S.xdiag[x] = gxx;
+  }
+  kin = block_sum(kin, S.red);
+  part = block_sum(part, S.red);
+  if (threadIdx.x == 0) { S.xs[0] = kin; S.xs[1] = part; }
+  cl.sync();
+  if (s == 0) {
+    double pot = 0.0;
+    if (C.nfl == 2) {
+      const double* pd = cl.map_shared_rank(S.xdiag, 1);
+      for (int x = threadIdx.x; x < N; x += kThreads) pot += C.U * (1.0 - S.xdiag[x]) * (1.0 - pd[x]);
+    }
+    pot = block_sum(pot, S.red);
+    double kin_t = S.xs[0], part_t = S.xs[1];
+    if (C.nfl == 2) {
+      const double* px = cl.map_shared_rank(S.xs, 1);
+      kin_t += px[0];
+      part_t += px[1];
+    }
+    if (threadIdx.x == 0) {
+      const double sg = (double)sign;
+      C.meas[0] += sg * kin_t;
+      C.meas[1] += sg * pot;
+      C.meas[2] += sg * part_t;
+      C.meas[3] += sg * (kin_t + pot);
+      C.meas_sign += sg;
+      C.n_meas += 1;
+    }
+  }
+  cl.sync();
+}
+
+// Exchange this flavor's fresh sign and precision figures; returns the product
+// of the fresh signs.  Rank 0 books the event.
+__device__ int close_event(ChainDev& C, int s, Smem& S, cg::cluster_group& cl, double ev_max, double ev_sum,
+                           int fresh_sign, int sign) {
+  if (threadIdx.x == 0) S.xs[2] = (double)fresh_sign;
+  cl.sync();
+  int prod = 1;
+  for (int r = 0; r < C.nfl; ++r) {
+    const double* px = (r == s) ? S.xs : cl.map_shared_rank(S.xs, r);
+    prod *= (px[2] < 0.0) ? -1 : 1;
+  }
+  if (threadIdx.x == 0) {
+    C.prec_sum[s] += ev_sum / ((double)C.N * C.N * C.nfl);
+    C.prec_max[s] = fmax(C.prec_max[s], ev_max);
+    if (s == 0) {
+      C.phase_max = fmax(C.phase_max, fabs((double)prod - (double)sign));
+      C.prec_events += 1;
+    }
+  }
+  cl.sync();
+  return prod;
+}
+
+// One sweep of every chain (Algorithm 1, upward then downward).
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) sweep_kernel(ChainDev* chains, SweepParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int nfl = (int)cl.num_blocks();
+  const int s = (int)cl.block_rank();
+  const int c = P.order[blockIdx.x / nfl];
+  ChainDev& C = chains[c];
+  Smem S = carve_smem(smem_raw, C.ld, C.MV);
+  Real* G = (Real*)C.G[s];
+  Real* Gt = (Real*)C.Gtmp[s];
+  Real* A = (Real*)C.dA[s];
+  Real* B = (Real*)C.dB[s];
+  const int L = C.L, nw = C.nw, MV = C.MV;
+  int sign = C.sign;
+  int buf = 0;
+  for (int tau = 1; tau <= L; ++tau) {
+    for (int k = threadIdx.x; k < MV; k += kThreads) S.fslice[k] = C.fields[(size_t)(tau - 1) * MV + k];
+    __syncthreads();
+    slice_potential_smem(C, s, S.fslice, S.v);
+    v_wrap<Real>(C, G, S.v, +1.0, S);
+    update_slice<Real>(C, s, tau, 0, P, S, cl, G, A, B, sign, buf);
+    if (s == 0)
+      for (int k = threadIdx.x; k < MV; k += kThreads) C.fields[(size_t)(tau - 1) * MV + k] = S.fslice[k];
+    t_wrap<Real>(C, s, G, Gt, true, S);
+    if (tau % nw == 0) {
+      cl.sync();
+      double mx, sm;
+      int fs;
+      stabilise<Real>(C, s, tau / nw, true, G, S, mx, sm, fs);
+      sign = close_event(C, s, S, cl, mx, sm, fs, sign);
+    }
+    if (P.measure && tau >= P.meas_first && tau <= P.meas_last) measure<Real>(C, s, G, S, cl, sign);
+  }
+  for (int tau = L; tau >= 1; --tau) {
+    for (int k = threadIdx.x; k < MV; k += kThreads) S.fslice[k] = C.fields[(size_t)(tau - 1) * MV + k];
+    __syncthreads();
+    t_wrap<Real>(C, s, G, Gt, false, S);
+    update_slice<Real>(C, s, tau, 1, P, S, cl, G, A, B, sign, buf);
+    if (s == 0)
+      for (int k = threadIdx.x; k < MV; k += kThreads) C.fields[(size_t)(tau - 1) * MV + k] = S.fslice[k];
+    slice_potential_smem(C, s, S.fslice, S.v);
+    v_wrap<Real>(C, G, S.v, -1.0, S);
+    const int t0 = tau - 1;
+    if (t0 % nw == 0) {
+      cl.sync();
+      double mx, sm;
+      int fs;
+      stabilise<Real>(C, s, t0 / nw, false, G, S, mx, sm, fs);
+      sign = close_event(C, s, S, cl, mx, sm, fs, sign);
+    }
+    if (P.measure && t0 >= P.meas_first && t0 <= P.meas_last) measure<Real>(C, s, G, S, cl, sign);
+  }
+  cl.sync();
+  if (s == 0 && threadIdx.x == 0) {
+    C.sign = sign;
+    C.sweep_sign_sum += (double)sign;
+  }
+}
+
+// d log|det(1 + B^s(beta,0))| on fixed fields: walk tau upwards with wraps
+// and fresh recomputes at the stabilisation points, accumulating
+//   S = sum_tau (1 - Gt_tau),  Gt_tau = e^{V_tau} G(tau-1) e^{-V_tau},
+//   gU = sum_tau sum_k (1 - Gt_tau)_ii sigma_k dc(f_k,tau)/dU,
+// then grad_K = V [F o (V^T (S E^-1)^T V)] V^T with the divided differences
+// F of exp(-dtau x) over the eigenvalues of K (Frechet derivative).
+__global__ void __launch_bounds__(kThreads) logdet_grad_kernel(ChainDev* chains, int n_cfg, const double* V,
+                                                               const double* w, double* gK, double* gU) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nfl = chains[0].nfl;
+  const int c = blockIdx.x / nfl, s = blockIdx.x % nfl;
+  if (c >= n_cfg) return;
+  ChainDev& C = chains[c];
+  Smem S = carve_smem(smem_raw, C.ld, C.MV);
+  const int N = C.N, ld = C.ld, L = C.L, nw = C.nw, nst = L / nw;
+  double logdet;
+  int sign;
+  if (fill_left_chain(C, s, S, logdet, sign)) {
+    if (threadIdx.x == 0) C.error = 1;
+    return;
+  }
+  if (threadIdx.x == 0) { C.logdet[s] = logdet; C.fresh_sign[s] = sign; }
+  double* Gc = wmat(C, s, 7);
+  double* Sacc = wmat(C, s, 8);
+  double* Wt = wmat(C, s, 9);
+  cta_copy(N, ld, (const double*)wmat(C, s, 6), Gc);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    Sacc[(size_t)x * ld + y] = 0.0;
+  }
+  __syncthreads();
+  double gu = 0.0;
+  for (int tau = 1; tau <= L; ++tau) {
+    slice_potential_global(C, s, tau, S.v);
+    for (int x = threadIdx.x; x < N; x += kThreads) S.ev[x] = exp(S.v[x]);
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * N; e += kThreads) {
+      const int x = e / N, y = e - x * N;
+      const double gt = Gc[(size_t)x * ld + y] * (S.ev[x] / S.ev[y]);
+      Gc[(size_t)x * ld + y] = gt;
+      Sacc[(size_t)x * ld + y] += (x == y ? 1.0 : 0.0) - gt;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < C.MV; k += kThreads) {
+      const int i = C.site[k];
+      gu += (1.0 - Gc[(size_t)i * ld + i]) * C.vsign[s * C.MV + k] *
+            coupling_dU(C.ft, C.dtau, C.U, C.cscale, C.fields[(size_t)(tau - 1) * C.MV + k]);
+    }
+    cta_gemm<double, false, false>(N, N, N, C.E[s], ld, Gc, ld, Wt, ld, S.gemm);
+    cta_gemm<double, false, false>(N, N, N, Wt, ld, C.Einv[s], ld, Gc, ld, S.gemm);
+    if (tau % nw == 0 && tau < L) {
+      const int j = tau / nw;
+      const UDV src = (j == 1) ? ident_udv(C) : slot_udv(C, s, j - 1);
+      const int dq = chain_step(C, s, (j - 1) * nw, j * nw, false, src, S);
+      const UDV Lf = (j == nst) ? ident_udv(C) : slot_udv(C, s, j);
+      double ldt;
+      int sgt;
+      if (green_from_udv(C, s, work_udv(C, s, dq), Lf, wmat(C, s, 6), ldt, sgt, S)) {
+        if (threadIdx.x == 0) C.error = 1;
+        return;
+      }
+      cta_copy(N, ld, (const double*)wmat(C, s, 6), Gc);
+      copy_udv_to_slot(C, s, j, dq);
+    }
+  }
+  gu = block_sum(gu, S.red);
+  if (threadIdx.x == 0) gU[(size_t)c * nfl + s] = gu;
+  // A = S E^-1 -> W0;  W1 = A^T V;  W2 = V^T W1;  F o W2;  W1 = V W2;  W3 = W1 V^T
+  double* W0 = wmat(C, s, 0);
+  double* W1 = wmat(C, s, 1);
+  double* W2 = wmat(C, s, 2);
+  double* W3 = wmat(C, s, 3);
+  const double* Vs = V + (size_t)s * N * N;
+  const double* ws = w + (size_t)s * N;
+  cta_gemm<double, false, false>(N, N, N, Sacc, ld, C.Einv[s], ld, W0, ld, S.gemm);
+  // V is dense [N][N] (ld = N); use a copy with the chain's ld
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    W3[(size_t)x * ld + y] = Vs[e];
+  }
+  __syncthreads();
+  cta_gemm<double, true, false>(N, N, N, W0, ld, W3, ld, W1, ld, S.gemm);
+  cta_gemm<double, true, false>(N, N, N, W3, ld, W1, ld, W2, ld, S.gemm);
+  const double dt = C.dtau;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int a = e / N, b = e - a * N;
+    const double la = ws[a], lb = ws[b];
+    const double x = 0.5 * dt * (la - lb);
+    const double shc = (x == 0.0) ? 1.0 : sinh(x) / x;
+    W2[(size_t)a * ld + b] *= -dt * exp(-0.5 * dt * (la + lb)) * shc;
+  }
+  __syncthreads();
+  cta_gemm<double, false, false>(N, N, N, W3, ld, W2, ld, W1, ld, S.gemm);
+  cta_gemm<double, false, true>(N, N, N, W1, ld, W3, ld, W0, ld, S.gemm);
+  double* out = gK + ((size_t)c * nfl + s) * N * N;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double gxy = W0[(size_t)x * ld + y];
+    out[e] = (x == y) ? gxy : gxy + W0[(size_t)y * ld + x];
+  }
+}
+
+// After an initial fill: sign of the weight = product of the flavors' fresh signs.
+__global__ void finalize_init_kernel(ChainDev* chains, int n_chains) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chains) return;
+  ChainDev& C = chains[c];
+  int sg = 1;
+  for (int s = 0; s < C.nfl; ++s) sg *= C.fresh_sign[s];
+  C.sign = sg;
+}
+
+// --------------------------------------------------------------------------
+// Launchers.
+// --------------------------------------------------------------------------
+size_t sweep_smem_bytes(int maxN, int maxld, int maxMV, int delay_k, int precision) {
+  (void)maxN; (void)delay_k; (void)precision;
+  return smem_bytes_for(maxld, maxMV);
+}
+
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_init_fields(ChainDev* chains, int n_chains, uint64_t seed, int, int, cudaStream_t st) {
+  init_fields_kernel<<<n_chains, kThreads, 0, st>>>(chains, n_chains, seed);
+  return cudaGetLastError();
+}
+
+static size_t g_smem_bytes = 0;
+
+cudaError_t launch_fresh_green(ChainDev* chains, int n_chains, int nfl, int precision, int write_working,
+                               double* out, int out_chain, cudaStream_t st) {
+  const size_t smem = g_smem_bytes;
+  const int mode = write_working ? 0 : 1;
+  if (precision == 0) {
+    cudaError_t e = set_smem((const void*)fresh_green_kernel<double>, smem);
+    if (e != cudaSuccess) return e;
+    fresh_green_kernel<double><<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, mode, out, out_chain);
+  } else {
+    cudaError_t e = set_smem((const void*)fresh_green_kernel<float>, smem);
+    if (e != cudaSuccess) return e;
+    fresh_green_kernel<float><<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, mode, out, out_chain);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_green(ChainDev* chains, int chain, int flavor, int precision, double* out,
+                              cudaStream_t st) {
+  if (precision == 0)
+    copy_green_kernel<double><<<16, 256, 0, st>>>(chains, chain, flavor, out);
+  else
+    copy_green_kernel<float><<<16, 256, 0, st>>>(chains, chain, flavor, out);
+  return cudaGetLastError();
+}
+
+void set_smem_bytes(size_t b) { g_smem_bytes = b; }
+
+cudaError_t launch_finalize_init(ChainDev* chains, int n_chains, cudaStream_t st) {
+  finalize_init_kernel<<<(n_chains + 127) / 128, 128, 0, st>>>(chains, n_chains);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_stats(ChainDev* chains, int n_chains, cudaStream_t st) {
+  reset_stats_kernel<<<(n_chains + 127) / 128, 128, 0, st>>>(chains, n_chains);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+static cudaError_t launch_sweep_t(ChainDev* chains, const SweepParams& p, int nfl, size_t smem,
+                                  cudaStream_t st) {
+  cudaError_t e = set_smem((const void*)sweep_kernel<Real>, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.n_chains * nfl, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nfl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sweep_kernel<Real>, chains, p);
+}
+
+cudaError_t launch_sweep(ChainDev* chains, const SweepParams& p, int nfl, int precision, size_t smem,
+                         cudaStream_t st) {
+  return precision == 0 ? launch_sweep_t<double>(chains, p, nfl, smem, st)
+                        : launch_sweep_t<float>(chains, p, nfl, smem, st);
+}
+
+cudaError_t launch_logdet_grad(ChainDev* chains, int n_cfg, int nfl, const double* eigvec, const double* eigval,
+                               double* gK, double* gU, double*, cudaStream_t st) {
+  const size_t smem = g_smem_bytes;
+  cudaError_t e = set_smem((const void*)logdet_grad_kernel, smem);
+  if (e != cudaSuccess) return e;
+  logdet_grad_kernel<<<n_cfg * nfl, kThreads, smem, st>>>(chains, n_cfg, eigvec, eigval, gK, gU);
+  return cudaGetLastError();
+}
+
+}  // namespace dqmc

@@ -1,0 +1,243 @@
+"""ctypes binding of the C ABI in include/dqmc.h (argument marshalling only).
+
+Every step of the sweep runs in the CUDA kernels of libdqmc.so; this module
+only packs numpy/torch arguments into the C structs and unpacks results.  It
+raises if the library is missing: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from .workloads import ModelSpec
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libdqmc.so")
+
+DQMC_OK, DQMC_EINVAL, DQMC_ENOMEM, DQMC_ECUDA, DQMC_EUNSTABLE, DQMC_ETIMEOUT, DQMC_ESTATE = range(7)
+PREC = {"fp64": 0, "mixed": 1}
+
+EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_logdet_backward",
+            "dqmc_get_fields", "dqmc_set_fields", "dqmc_last_error", "dqmc_destroy"]
+
+
+class DqmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dqmc status {status}: {msg}")
+        self.status = status
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_sites", ctypes.c_int32),
+        ("n_flavors", ctypes.c_int32),
+        ("hopping", ctypes.POINTER(ctypes.c_double)),
+        ("n_vertices", ctypes.c_int32),
+        ("vertex_site", ctypes.POINTER(ctypes.c_int32)),
+        ("vertex_sign", ctypes.POINTER(ctypes.c_double)),
+        ("U", ctypes.c_double),
+        ("field_type", ctypes.c_int32),
+        ("dtau", ctypes.c_double),
+        ("L", ctypes.c_int32),
+        ("n_wrap", ctypes.c_int32),
+    ]
+
+
+class RunOpts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("delay_k", ctypes.c_int32),
+        ("measure", ctypes.c_int32),
+        ("meas_first", ctypes.c_int32),
+        ("meas_last", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("unstable_threshold", ctypes.c_double),
+        ("spin_limit", ctypes.c_int64),
+    ]
+
+
+class SweepStats(ctypes.Structure):
+    _fields_ = [
+        ("proposals", ctypes.c_int64),
+        ("accepted", ctypes.c_int64),
+        ("prec_green_mean", ctypes.c_double),
+        ("prec_green_max", ctypes.c_double),
+        ("prec_phase_max", ctypes.c_double),
+        ("mean_sign", ctypes.c_double),
+        ("ms_total", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load libdqmc.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with paper_1704_00131_gb300.build_ext.build()")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, i32, i64, u64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    L.dqmc_init.argtypes = [vp, i32, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]
+    L.dqmc_init.restype = ctypes.c_int
+    L.dqmc_sweep.argtypes = [vp, i32, vp]
+    L.dqmc_sweep.restype = ctypes.c_int
+    L.dqmc_greens.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp]
+    L.dqmc_greens.restype = ctypes.c_int
+    L.dqmc_measure.argtypes = [vp, vp, vp, vp]
+    L.dqmc_measure.restype = ctypes.c_int
+    L.dqmc_logdet_backward.argtypes = [vp, i32, vp, i32, vp, vp, vp]
+    L.dqmc_logdet_backward.restype = ctypes.c_int
+    L.dqmc_get_fields.argtypes = [vp, vp, vp]
+    L.dqmc_get_fields.restype = ctypes.c_int
+    L.dqmc_set_fields.argtypes = [vp, vp, u64]
+    L.dqmc_set_fields.restype = ctypes.c_int
+    L.dqmc_last_error.argtypes = [vp]
+    L.dqmc_last_error.restype = ctypes.c_char_p
+    L.dqmc_destroy.argtypes = [vp]
+    L.dqmc_destroy.restype = None
+    del i64, d
+    _lib = L
+    return L
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Ensemble:
+    """A set of Markov chains on one GPU (one dqmc_ctx)."""
+
+    def __init__(self, models: list[ModelSpec], chain_model, fields=None, precision: str = "fp64",
+                 delay_k: int = 16, seed: int = 0, measure: bool = False, meas_first: int = 0,
+                 meas_last: int | None = None, unstable_threshold: float = 0.0, stream=None):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        self.models = list(models)
+        self.chain_model = np.ascontiguousarray(chain_model, dtype=np.int32)
+        self.precision = precision
+        self._keep = []
+        descs = (ModelDesc * len(self.models))()
+        for i, m in enumerate(self.models):
+            H = np.ascontiguousarray(m.hopping, dtype=np.float64)
+            vs = np.ascontiguousarray(m.vertex_site, dtype=np.int32)
+            sg = np.ascontiguousarray(m.vertex_sign, dtype=np.float64)
+            self._keep += [H, vs, sg]
+            descs[i] = ModelDesc(m.N, H.shape[0], H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(vs),
+                                 vs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 sg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(m.U), int(m.field_type),
+                                 float(m.dtau), int(m.L), int(m.n_wrap))
+        self._descs = descs
+        ml = max(m.L for m in self.models) if meas_last is None else meas_last
+        self.opts = RunOpts(PREC[precision], int(delay_k), int(measure), int(meas_first), int(ml), int(seed),
+                            float(unstable_threshold), 0)
+        fptr = None
+        if fields is not None:
+            packed = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int8).ravel() for f in fields]))
+            self._keep.append(packed)
+            fptr = _p(packed)
+        st_ptr = None
+        if stream is not None:
+            st_ptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        st = self._lib.dqmc_init(ctypes.cast(descs, ctypes.c_void_p), len(self.models), _p(self.chain_model),
+                                 len(self.chain_model), fptr, ctypes.byref(self.opts), st_ptr, ctypes.byref(self._h))
+        if st != DQMC_OK:
+            msg = self._lib.dqmc_last_error(self._h).decode() if self._h else "dqmc_init failed"
+            self.close()
+            raise DqmcError(st, msg)
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, st: int):
+        if st != DQMC_OK:
+            raise DqmcError(st, self._lib.dqmc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.dqmc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_chains(self) -> int:
+        return int(len(self.chain_model))
+
+    def model_of(self, c: int) -> ModelSpec:
+        return self.models[int(self.chain_model[c])]
+
+    # --------------------------------------------------------------------- API
+    def sweep(self, n: int = 1, stats: bool = True):
+        if not stats:
+            self._check(self._lib.dqmc_sweep(self._h, int(n), None))
+            return None
+        s = SweepStats()
+        self._check(self._lib.dqmc_sweep(self._h, int(n), ctypes.byref(s)))
+        return s.as_dict()
+
+    def greens(self, chain: int, flavor: int, fresh: bool = False, out=None):
+        """G^flavor(0) of a chain as a numpy array (or into a CUDA torch tensor `out`)."""
+        N = self.model_of(chain).N
+        ld = ctypes.c_double()
+        sg = ctypes.c_int32()
+        if out is None:
+            G = np.zeros((N, N))
+            self._check(self._lib.dqmc_greens(self._h, chain, flavor, int(fresh), _p(G), 0, ctypes.byref(ld),
+                                              ctypes.byref(sg)))
+            return G, ld.value, sg.value
+        self._check(self._lib.dqmc_greens(self._h, chain, flavor, int(fresh), ctypes.c_void_p(out.data_ptr()), 1,
+                                          ctypes.byref(ld), ctypes.byref(sg)))
+        return out, ld.value, sg.value
+
+    def measure(self):
+        n = self.n_chains
+        out = np.zeros((n, 4))
+        ss = np.zeros(n)
+        nm = np.zeros(n, dtype=np.int64)
+        self._check(self._lib.dqmc_measure(self._h, _p(out), _p(ss), _p(nm)))
+        return out, ss, nm
+
+    def get_fields(self):
+        sizes = [self.model_of(c).L * self.model_of(c).n_vertices for c in range(self.n_chains)]
+        buf = np.zeros(sum(sizes), dtype=np.int8)
+        ctr = ctypes.c_uint64()
+        self._check(self._lib.dqmc_get_fields(self._h, _p(buf), ctypes.byref(ctr)))
+        out, off = [], 0
+        for c, sz in enumerate(sizes):
+            m = self.model_of(c)
+            out.append(buf[off:off + sz].reshape(m.L, m.n_vertices).copy())
+            off += sz
+        return out, ctr.value
+
+    def set_fields(self, fields, rng_counter: int):
+        packed = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int8).ravel() for f in fields]))
+        self._check(self._lib.dqmc_set_fields(self._h, _p(packed), int(rng_counter)))
+
+    def logdet_backward(self, model_index: int, fields: np.ndarray):
+        """Per configuration and flavor: log|det(1+B(beta,0))|, d/dK (symmetric pairs), d/dU."""
+        m = self.models[model_index]
+        f = np.ascontiguousarray(fields, dtype=np.int8)
+        if f.ndim == 2:
+            f = f[None]
+        n_cfg = f.shape[0]
+        nfl = m.hopping.shape[0]
+        ldv = np.zeros((n_cfg, nfl))
+        gK = np.zeros((n_cfg, nfl, m.N, m.N))
+        gU = np.zeros((n_cfg, nfl))
+        self._check(self._lib.dqmc_logdet_backward(self._h, int(model_index), _p(f), n_cfg, _p(ldv), _p(gK), _p(gU)))
+        return ldv, gK, gU

@@ -1,0 +1,70 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for sm_103a,
+loads, exports every entry point that include/dqmc.h declares, and refuses to
+run without a CUDA device instead of falling back to the CPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1704_00131_gb300 import build_ext, dqmc
+from paper_1704_00131_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_ext.build()
+    return dqmc.load()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(dqmc_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+def test_header_declares_the_named_entry_points():
+    names = declared_symbols()
+    for n in ("dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_logdet_backward"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+
+
+def test_no_cpu_fallback_without_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = W.ModelSpec(W.square_lattice(2, 2), U=2.0, dtau=0.1, L=4, n_wrap=2)
+    with pytest.raises(dqmc.DqmcError) as e:
+        dqmc.Ensemble([m], [0])
+    assert e.value.status == dqmc.DQMC_ECUDA
+
+
+def test_invalid_model_rejected_before_any_device_work(lib):
+    m = W.ModelSpec(W.square_lattice(2, 2), U=2.0, dtau=0.1, L=5, n_wrap=2)  # L % n_wrap != 0
+    with pytest.raises(dqmc.DqmcError) as e:
+        dqmc.Ensemble([m], [0])
+    assert e.value.status == dqmc.DQMC_EINVAL
+    K = W.square_lattice(2, 2)
+    K[0, 1] += 0.5  # not symmetric
+    with pytest.raises(dqmc.DqmcError) as e:
+        dqmc.Ensemble([W.ModelSpec(K, U=2.0, dtau=0.1, L=4, n_wrap=2)], [0])
+    assert e.value.status == dqmc.DQMC_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(dqmc, "_lib", None)
+    monkeypatch.setattr(dqmc, "_LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(ImportError):
+        dqmc.load()

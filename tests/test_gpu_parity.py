@@ -1,0 +1,215 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (from the arithmetic):
+* FP64 path: G and log|det| within 1e-10 (relative for log|det|, absolute on the
+  O(1) entries of G); fields, Philox-driven decisions and acceptance counts
+  bit-exact (the two sides compute each ratio in FP64 from the same uniforms;
+  a decision can differ only at a near-tie |u - |R|| ~ 1e-15, absent here).
+* Mixed path: the working G is FP32 between stabilisations; every stable
+  recompute is FP64, so G(0) after a sweep matches the oracle on the same
+  final fields to FP32 rounding (1e-6 absolute).
+"""
+import numpy as np
+import pytest
+
+from paper_1704_00131_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00131_gb300 import build_ext, dqmc
+    build_ext.build()
+    return dqmc
+
+
+def omodel(orc, m: W.ModelSpec):
+    return orc.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+
+
+def square(L_, U=4.0, dtau=0.1, L=20, nw=10, ft=1, tp=0.0, mu=0.0):
+    return W.ModelSpec(W.square_lattice(L_, L_, 1.0, tp, mu), U=U, dtau=dtau, L=L, n_wrap=nw, field_type=ft)
+
+
+# ------------------------------------------------------------------ fresh G(0)
+@pytest.mark.parametrize("case", ["square4x4", "honeycomb6x6", "square12x12_hs4", "chain13_ragged", "square8x8_tp_mu"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fresh_green_matches_oracle(dq, orc, case, precision):
+    if case == "square4x4":
+        m = square(4)
+    elif case == "honeycomb6x6":
+        m = W.ModelSpec(W.honeycomb_lattice(6, 6), U=4.0, dtau=0.1, L=20, n_wrap=10)
+    elif case == "square12x12_hs4":
+        m = square(12, L=20, nw=5, ft=2)
+    elif case == "chain13_ragged":
+        m = W.ModelSpec(W.chain_lattice(13, mu=0.3, periodic=True), U=3.0, dtau=0.125, L=12, n_wrap=4)
+    else:
+        m = square(8, U=4.0, dtau=0.05, L=40, tp=-0.2, mu=-0.5)
+    f = W.random_fields(m.field_type, m.L, m.n_vertices, seed=5)
+    ens = dq.Ensemble([m], [0], fields=[f], precision=precision)
+    om = omodel(orc, m)
+    for s in (0, 1):
+        Gg, ldg, sgg = ens.greens(0, s, fresh=True)
+        Go, ldo, sgo = orc.green_udv(om, f, s, 0)
+        assert np.abs(Gg - Go).max() < 1e-10, (case, s)
+        assert ldg == pytest.approx(ldo, rel=1e-10, abs=1e-10) and sgg == sgo
+        Gw, _, _ = ens.greens(0, s, fresh=False)
+        tol = 1e-10 if precision == "fp64" else 1e-6
+        assert np.abs(Gw - Go).max() < tol
+    ens.close()
+
+
+def test_init_fields_bitexact(dq, orc):
+    m1, m2 = square(4, L=20), W.ModelSpec(W.honeycomb_lattice(3, 3), U=2.0, dtau=0.1, L=10, n_wrap=5, field_type=2)
+    ens = dq.Ensemble([m1, m2], [0, 1, 0], seed=1234)
+    fields, ctr = ens.get_fields()
+    assert ctr == 0
+    for c, m in enumerate([m1, m2, m1]):
+        assert np.array_equal(fields[c], orc.init_fields(m.field_type, m.L, m.n_vertices, 1234, c))
+
+
+# ----------------------------------------------------------- trajectory parity
+@pytest.mark.parametrize("ft,delay", [(1, 1), (1, 16), (2, 8)])
+def test_sweep_trajectory_fp64(dq, orc, ft, delay):
+    m = square(4, U=4.0, L=20, nw=10, ft=ft)
+    seed = 20170401
+    ens = dq.Ensemble([m], [0], precision="fp64", delay_k=delay, seed=seed, measure=True)
+    f0, _ = ens.get_fields()
+    och = orc.Chain(omodel(orc, m), f0[0], seed=seed, chain=0, measure=True)
+    for rep in range(3):
+        sg = ens.sweep(2)
+        so = och.sweep(2)
+        fg, ctr = ens.get_fields()
+        fo, nsw, sign = och.fields()
+        assert ctr == nsw == 2 * (rep + 1)
+        assert np.array_equal(fg[0], fo), f"fields differ after sweep {2 * (rep + 1)}"
+        assert sg["accepted"] == so.accepted and sg["proposals"] == so.proposals
+        assert sg["mean_sign"] == so.mean_sign
+        assert sg["prec_green_max"] < 1e-8
+        for s in (0, 1):
+            Gg, _, _ = ens.greens(0, s)
+            assert np.abs(Gg - och.green(s)).max() < 1e-10
+    mg, ssg, nmg = ens.measure()
+    mo, sso, nmo = och.measure()
+    assert nmg[0] == nmo and ssg[0] == sso
+    assert np.allclose(mg[0], mo, rtol=1e-10, atol=1e-9)
+
+
+def test_batched_uneven_chains_fp64(dq, orc):
+    """Chains of different lattices and lengths in one launch: each follows its own oracle chain."""
+    models = [square(4, U=4.0, L=20, nw=10),
+              W.ModelSpec(W.honeycomb_lattice(3, 3), U=3.0, dtau=0.1, L=10, n_wrap=5),
+              W.ModelSpec(W.chain_lattice(7, periodic=True), U=2.0, dtau=0.1, L=8, n_wrap=4, field_type=2)]
+    cm = [0, 1, 2, 1, 0]
+    seed = 77
+    ens = dq.Ensemble(models, cm, precision="fp64", delay_k=4, seed=seed)
+    f0, _ = ens.get_fields()
+    ochs = [orc.Chain(omodel(orc, models[cm[c]]), f0[c], seed=seed, chain=c) for c in range(len(cm))]
+    st = ens.sweep(2)
+    tot = 0
+    for c, och in enumerate(ochs):
+        so = och.sweep(2)
+        tot += so.accepted
+    fg, _ = ens.get_fields()
+    for c, och in enumerate(ochs):
+        assert np.array_equal(fg[c], och.fields()[0]), c
+        for s in (0, 1):
+            assert np.abs(ens.greens(c, s)[0] - och.green(s)).max() < 1e-10
+    assert st["accepted"] == tot
+
+
+def test_large_lattice_fp64_one_sweep(dq, orc):
+    """Honeycomb 6x6 (N = 72, two 64-wide tiles with a ragged tail), short beta."""
+    m = W.ModelSpec(W.honeycomb_lattice(6, 6), U=4.0, dtau=0.1, L=10, n_wrap=10)
+    seed = 3
+    ens = dq.Ensemble([m], [0], precision="fp64", delay_k=16, seed=seed)
+    f0, _ = ens.get_fields()
+    och = orc.Chain(omodel(orc, m), f0[0], seed=seed, chain=0)
+    ens.sweep(1)
+    och.sweep(1)
+    assert np.array_equal(ens.get_fields()[0][0], och.fields()[0])
+    for s in (0, 1):
+        assert np.abs(ens.greens(0, s)[0] - och.green(s)).max() < 1e-10
+
+
+# ------------------------------------------------------------------ mixed path
+def test_mixed_precision_green_after_sweeps(dq, orc):
+    m = square(8, U=4.0, L=40, nw=10)
+    ens = dq.Ensemble([m, square(4, U=2.0, L=20)], [0, 1, 0], precision="mixed", delay_k=16, seed=11)
+    st = ens.sweep(2)
+    assert 0 < st["accepted"] < st["proposals"]
+    # drift of the FP32 working G between FP64 recomputes (precision monitor)
+    assert st["prec_green_max"] < 1e-3
+    fg, _ = ens.get_fields()
+    for c in range(3):
+        mm = ens.model_of(c)
+        for s in (0, 1):
+            Go, _, _ = orc.green_udv(omodel(orc, mm), fg[c], s, 0)
+            assert np.abs(ens.greens(c, s)[0] - Go).max() < 1e-6
+
+
+# -------------------------------------------------------- checkpoint / resume
+def test_checkpoint_resume_bitexact(dq):
+    m = square(4, U=4.0, L=20)
+    a = dq.Ensemble([m], [0, 0], precision="fp64", seed=9)
+    a.sweep(2)
+    f, ctr = a.get_fields()
+    a.sweep(2)
+    fa, ca = a.get_fields()
+    b = dq.Ensemble([m], [0, 0], precision="fp64", seed=9)
+    b.set_fields(f, ctr)
+    b.sweep(2)
+    fb, cb = b.get_fields()
+    assert ca == cb == 4
+    for c in range(2):
+        assert np.array_equal(fa[c], fb[c])
+        assert np.array_equal(a.greens(c, 0)[0], b.greens(c, 0)[0])
+
+
+# ------------------------------------------------------------------ gradients
+def test_logdet_gradient_matches_oracle(dq, orc):
+    m = W.ModelSpec(W.square_lattice(4, 4, 1.0, 0.0, 0.1), U=3.0, dtau=0.1, L=10, n_wrap=5)
+    fs = np.stack([W.random_fields(1, m.L, m.n_vertices, seed=s) for s in (1, 2)])
+    ens = dq.Ensemble([m], [0], precision="fp64")
+    ld, gK, gU = ens.logdet_backward(0, fs)
+    om = omodel(orc, m)
+    for c in range(2):
+        ldo, sgo, gKo, gUo = orc.logdet_grad(om, fs[c])
+        assert np.allclose(ld[c], ldo, rtol=1e-10)
+        assert np.allclose(gK[c], gKo, rtol=1e-8, atol=1e-9)
+        assert np.allclose(gU[c], gUo, rtol=1e-8, atol=1e-9)
+
+
+# --------------------------------------------------------------- edge cases
+def test_degenerate_sizes(dq, orc):
+    """N = 1, partial vertex sets, n_wrap = 1 and n_wrap = L."""
+    cases = [
+        W.ModelSpec(np.zeros((1, 1)), U=2.0, dtau=0.1, L=6, n_wrap=1),
+        W.ModelSpec(W.chain_lattice(5), U=2.0, dtau=0.1, L=6, n_wrap=6, vertex_site=np.array([0, 2, 4], np.int32)),
+    ]
+    for m in cases:
+        ens = dq.Ensemble([m], [0], precision="fp64", seed=4)
+        f0, _ = ens.get_fields()
+        och = orc.Chain(omodel(orc, m), f0[0], seed=4, chain=0)
+        ens.sweep(2)
+        och.sweep(2)
+        assert np.array_equal(ens.get_fields()[0][0], och.fields()[0])
+        for s in (0, 1):
+            assert np.abs(ens.greens(0, s)[0] - och.green(s)).max() < 1e-10
+
+
+def test_invalid_arguments_are_rejected(dq):
+    bad = W.ModelSpec(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=20, n_wrap=7)
+    with pytest.raises(dq.DqmcError) as e:
+        dq.Ensemble([bad], [0])
+    assert e.value.status == dq.DQMC_EINVAL
+    m = square(4)
+    with pytest.raises(dq.DqmcError):
+        dq.Ensemble([m], [0], fields=[np.full((20, 16), 3, np.int8)])
+    ens = dq.Ensemble([m], [0])
+    with pytest.raises(dq.DqmcError):
+        ens.greens(5, 0)
