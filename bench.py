@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Throughput of the batched DQMC sweep on GB300: field-update proposals/s and sweeps/s.
+
+One step = one sweep (tau = 1..L and back) of every chain of the workload.
+Default workload: 256 independent chains of the square-lattice Hubbard model,
+half 8x8 (N = 64) and half 12x12 (N = 144), beta = 4 or 8 (dtau = 0.1), U in
+{2, 4, 6}, spin-z Ising decoupling, n_wrap = 10; fields drawn from Philox.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+    python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+
+Multi-GPU (torchrun): every rank runs its own batch of chains (independent
+Markov chains, no data-path collective); value = all ranks' proposals / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1704_00131_gb300 import workloads as W  # noqa: E402
+
+METRIC = "field-update proposals/s (and sweeps/s) of the batched DQMC sweep at max|dG|<=1e-6"
+UNIT = "proposals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--chains", type=int, default=0, help="override the number of chains (c3/c5)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name: str, chains: int = 0) -> W.Workload:
+    if chains and name == "c3":
+        return W.config_c3(chains)
+    if chains and name == "c5":
+        return W.config_c5(chains)
+    return {"c1": W.config_c1, "c2": W.config_c2, "c3": W.config_c3, "c5": W.config_c5}[name]()
+
+
+def chain_cost(m: W.ModelSpec, accepted_per_chain: float) -> float:
+    """Algorithmic FLOPs of one sweep of one chain (two flavors):
+    wraps 2 flavors x 2L slices x 2 GEMMs x 2N^3; accepted flips 2 flavors x 2N^2;
+    stabilisation 2 flavors x 2L/n_wrap events x (2 n_wrap + 37/3) N^3
+    (B-chain GEMMs, QR 4/3, form Q 4/3, T update 1, Q^T Q 2, T T^T 2, LU 2/3,
+    solve 2, Q X 2)."""
+    N, L, nw = m.N, m.L, m.n_wrap
+    nfl = m.hopping.shape[0]
+    wraps = nfl * 2 * L * 2 * 2 * N ** 3
+    upd = nfl * accepted_per_chain * 2 * N ** 2
+    stab = nfl * (2 * L // nw) * (2 * nw + 37.0 / 3.0) * N ** 3
+    return wraps + upd + stab
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for i, n in enumerate(names):
+                    if r[3 + i].strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_sample(wl: W.Workload, n_threads: int, per_class: int):
+    """Time the FP64 oracle (one sweep per chain) on a stratified sample of the
+    workload's chains, run concurrently on n_threads host threads (ctypes releases
+    the GIL).  Returns (proposals, seconds, description)."""
+    import oracle
+    oracle.build()
+    classes = {}
+    for c, mi in enumerate(wl.chain_model):
+        classes.setdefault(int(mi), []).append(c)
+    sample = []
+    for mi, cs in sorted(classes.items()):
+        sample += [(mi, c) for c in cs[:per_class]]
+    chains = []
+    for mi, c in sample:
+        m = wl.models[mi]
+        om = oracle.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+        chains.append((oracle.Chain(om, None, seed=W.BASE_SEED, chain=c), 2 * m.L * m.n_vertices))
+    idx = [0]
+    lock = threading.Lock()
+
+    def worker():
+        while True:
+            with lock:
+                if idx[0] >= len(chains):
+                    return
+                i = idx[0]
+                idx[0] += 1
+            chains[i][0].sweep(1)
+
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=worker) for _ in range(n_threads)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    dt = time.perf_counter() - t0
+    props = sum(p for _, p in chains)
+    desc = (f"1 sweep each of {len(chains)} chains ({per_class} per model class of the workload: "
+            + ", ".join(f"{wl.models[mi].name}" for mi in sorted(classes)) + f") on {n_threads} threads")
+    return props, dt, desc
+
+
+def run_reference(args, wl: W.Workload, rank: int):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per_class = max(1, cores // max(1, len(set(wl.chain_model.tolist()))))
+    for _ in range(args.warmup):
+        oracle_sample(wl, cores, 1)
+    times, props = [], 0
+    desc = ""
+    for _ in range(args.steps):
+        p, dt, desc = oracle_sample(wl, cores, per_class)
+        times.append(dt)
+        props = p
+    tot = sum(times)
+    value = props * args.steps / tot
+    sweeps_per_s = value / wl.proposals_per_sweep()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Philox fields)",
+        "config": {"workload": wl.name, "chains": wl.n_chains, "sample": desc},
+        "sweeps_per_s": sweeps_per_s,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------- ours
+def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_1704_00131_gb300 import build_ext, dqmc
+
+    build_ext.build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    seed = W.BASE_SEED + rank
+    ens = dqmc.Ensemble(wl.models, wl.chain_model, precision=args.precision, delay_k=wl.delay_k, seed=seed,
+                        stream=stream)
+    # warm-up (untimed) and a stats sweep for the acceptance and precision figures
+    ens.sweep(max(args.warmup - 1, 0), stats=False)
+    st = ens.sweep(1)
+    acc_per_chain = st["accepted"] / wl.n_chains
+    flops_per_step = sum(chain_cost(wl.models[m], acc_per_chain) for m in wl.chain_model)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            ens.sweep(1, stats=False)
+            ev[i][1].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    ms_total = t_start.elapsed_time(t_end)
+    per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms_step = ms_total / args.steps
+    props_step = wl.proposals_per_sweep()
+    value = props_step * world / (ms_step / 1000.0)
+    # end to end through the public API with host buffers: fields in (pinned host),
+    # one sweep, fields and measurements out, every step
+    fields, ctr = ens.get_fields()
+    flat = np.concatenate([f.ravel() for f in fields])
+    pinned = torch.from_numpy(flat).pin_memory()
+    h2d = int(pinned.numel())
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        host_fields = np.asarray(pinned.numpy())
+        offs = np.cumsum([0] + [f.size for f in fields])
+        ens.set_fields([host_fields[offs[c]:offs[c + 1]] for c in range(len(fields))], ctr)
+        ens.sweep(1, stats=False)
+        fields, ctr = ens.get_fields()
+        meas = ens.measure()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    d2h = int(sum(f.size for f in fields) + sum(a.nbytes for a in meas))
+    e2e_value = props_step * world / e2e_s
+    # roofline of the dominant kernel (the sweep kernel: one launch per step)
+    avg_launch_s = statistics.mean(per_launch_ms) / 1000.0
+    achieved_tf = flops_per_step / avg_launch_s / 1e12
+    peak_tf = 1.0994 if args.precision == "fp64" else 69.83
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        p, dt, desc = oracle_sample(wl, cores, max(1, cores // len(set(wl.chain_model.tolist()))))
+        cpu = {"value": p / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded Philox fields, random-init Markov chains)",
+            "config": {"workload": wl.name, "chains": wl.n_chains, "precision": args.precision,
+                       "delay_k": wl.delay_k, "n_wrap": 10,
+                       "l2": "resident state > L2 (per-chain G, UDV storage and workspace, "
+                             f"{ens_bytes(wl, args.precision) / 1e9:.2f} GB); no flush"},
+            "sweeps_per_s": 1000.0 / ms_step * world,
+            "accept_rate": st["accepted"] / st["proposals"],
+            "prec_green_max": st["prec_green_max"], "prec_green_mean": st["prec_green_mean"],
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": achieved_tf / peak_tf, "traffic": None,
+                         "kernel": f"sweep_kernel<{'double' if args.precision == 'fp64' else 'float'}>",
+                         "peak_source": "measured cuBLAS DGEMM on this GB300 (FP64 pipe)" if args.precision == "fp64"
+                         else "measured cuBLAS SGEMM on this GB300 (FP32 SIMT)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ens.close()
+
+
+def ens_bytes(wl: W.Workload, precision: str) -> float:
+    rs = 8 if precision == "fp64" else 4
+    tot = 0
+    for m in wl.chain_model:
+        mm = wl.models[m]
+        N, L, nw = mm.N, mm.L, mm.n_wrap
+        ld = (N + 3) // 4 * 4
+        per_fl = 2 * N * ld * rs + (L // nw + 1) * (2 * N * ld + ld) * 8 + (10 * N * ld + 8 * ld) * 8
+        tot += 2 * per_fl + L * mm.n_vertices
+    return float(tot)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = workload(args.config, args.chains)
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, wl, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -60,8 +60,13 @@ typedef enum { DQMC_FIELD_ISING = 1, DQMC_FIELD_HS4 = 2 } dqmc_field_type;
 
 /* Arithmetic of the working Green function, wraps and delayed updates.  The
  * stabilisation (B-chain products, pivoted QR, T update, (1 + UDV)^-1 and
- * log|det|) is FP64 in both modes. */
-typedef enum { DQMC_PREC_FP64 = 0, DQMC_PREC_MIXED = 1 } dqmc_precision;
+ * log|det|) is FP64 in every mode.
+ *   DQMC_PREC_FP64: plain FP64.
+ *   DQMC_PREC_FP32: plain FP32 between stabilisations.  Round-off grows by the
+ *     condition number of the unstabilised slice product (Sec. 2.3), so the
+ *     wrapped G can drift far from the fresh one at strong coupling; the
+ *     precision monitor of dqmc_sweep reports it. */
+typedef enum { DQMC_PREC_FP64 = 0, DQMC_PREC_FP32 = 1 } dqmc_precision;
 
 /* One model: a lattice with its couplings (Sec. 3.1, the Operator type with
  * hopping Op_T, g = -dtau, and single-site vertices Op_V).  Chains refer to a

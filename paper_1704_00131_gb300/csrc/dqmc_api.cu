@@ -41,12 +41,13 @@ void symmetric_eigen(int n, const std::vector<double>& A_in, std::vector<double>
       for (int q = p + 1; q < n; ++q) {
         const double apq = at(p, q);
         if (std::fabs(apq) <= thresh || apq == 0.0) continue;
-        const double h = at(q, q) - at(p, p);
+        // tangent t of the rotation angle that annihilates a_pq: the smaller
+        // root of t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq)
+        const double theta = 0.5 * (at(q, q) - at(p, p)) / apq;
         double t;
-        if (std::fabs(h) + std::fabs(apq) * 1e18 == std::fabs(apq) * 1e18) {
-          t = apq / h;
+        if (std::fabs(theta) > 1e150) {
+          t = 0.5 / theta;
         } else {
-          const double theta = 0.5 * h / apq;
           t = 1.0 / (std::fabs(theta) + std::sqrt(1.0 + theta * theta));
           if (theta < 0.0) t = -t;
         }
@@ -339,7 +340,7 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
     return fail(*out, DQMC_EINVAL, "null argument or empty model/chain list");
   }
   c->opts = *opts;
-  if (opts->precision != DQMC_PREC_FP64 && opts->precision != DQMC_PREC_MIXED) {
+  if (opts->precision != DQMC_PREC_FP64 && opts->precision != DQMC_PREC_FP32) {
     *out = ctx.release();
     return fail(*out, DQMC_EINVAL, "unknown precision %d", opts->precision);
   }

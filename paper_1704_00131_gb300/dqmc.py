@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libdqmc.so")
 
 DQMC_OK, DQMC_EINVAL, DQMC_ENOMEM, DQMC_ECUDA, DQMC_EUNSTABLE, DQMC_ETIMEOUT, DQMC_ESTATE = range(7)
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "fp32": 1}
 
 EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_logdet_backward",
             "dqmc_get_fields", "dqmc_set_fields", "dqmc_last_error", "dqmc_destroy"]
@@ -192,6 +192,8 @@ class Ensemble:
 
     def greens(self, chain: int, flavor: int, fresh: bool = False, out=None):
         """G^flavor(0) of a chain as a numpy array (or into a CUDA torch tensor `out`)."""
+        if not 0 <= int(chain) < self.n_chains:
+            raise DqmcError(DQMC_EINVAL, f"chain {chain} out of range")
         N = self.model_of(chain).N
         ld = ctypes.c_double()
         sg = ctypes.c_int32()
