@@ -164,6 +164,33 @@ dqmc_status dqmc_get_fields(dqmc_ctx* ctx, int8_t* out, uint64_t* rng_counter);
  * chain and G(0) of every chain. */
 dqmc_status dqmc_set_fields(dqmc_ctx* ctx, const int8_t* in, uint64_t rng_counter);
 
+/* Allocation-free computation of G^s(0) for every flavor (no counterpart in
+ * the paper; it is a service of this library).  For callers that cannot
+ * allocate device memory where they need G: code running under an allocator
+ * that owns all device memory, or a context that must not call cudaMalloc.
+ * It allocates nothing and needs no dqmc_ctx: all inputs and outputs are the
+ * caller's device buffers, and its scratch is one device array of this library
+ * (about 1 MiB, held by every GPU that loads the library until exit).
+ *   Inputs (device): E_dev [n_flavors][N][N] = exp(-dtau K^s) row-major;
+ *     vertex_site_dev [M_V]; vertex_sign_dev [n_flavors][M_V];
+ *     fields_dev [L][M_V] int8 (+-1, or -2,-1,1,2 for DQMC_FIELD_HS4).
+ *   Outputs (device): G_out_dev [n_flavors][N][N]; logdet_out_dev [n_flavors]
+ *     and sign_out_dev [n_flavors] (nullable; sign 0 marks a singular
+ *     stabilisation).
+ * Limits: N <= 64, n_flavors <= 2; larger sizes return DQMC_EINVAL before any
+ * device work.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The work is enqueued on cuda_stream (NULL: the
+ * default stream) and the call returns without waiting.  Every call shares the
+ * one array, so calls that overlap on the GPU (different streams, or different
+ * host threads on the same device) race and give wrong results: serialise them.
+ * Errors: DQMC_EINVAL, DQMC_ECUDA. */
+dqmc_status dqmc_green_fresh_noalloc(int32_t n_sites, int32_t n_flavors, const double* E_dev, int32_t n_vertices,
+                                     const int32_t* vertex_site_dev, const double* vertex_sign_dev, double U,
+                                     int32_t field_type, double dtau, int32_t L, int32_t n_wrap,
+                                     const int8_t* fields_dev, double* G_out_dev, double* logdet_out_dev,
+                                     int32_t* sign_out_dev, void* cuda_stream);
+
 /* Per-context message of the last failing call; valid until the next call. */
 const char* dqmc_last_error(const dqmc_ctx* ctx);
 
