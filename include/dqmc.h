@@ -65,8 +65,11 @@ typedef enum { DQMC_FIELD_ISING = 1, DQMC_FIELD_HS4 = 2 } dqmc_field_type;
  *   DQMC_PREC_FP32: plain FP32 between stabilisations.  Round-off grows by the
  *     condition number of the unstabilised slice product (Sec. 2.3), so the
  *     wrapped G can drift far from the fresh one at strong coupling; the
- *     precision monitor of dqmc_sweep reports it. */
-typedef enum { DQMC_PREC_FP64 = 0, DQMC_PREC_FP32 = 1 } dqmc_precision;
+ *     precision monitor of dqmc_sweep reports it.
+ *   DQMC_PREC_MIXED: the working G and the update vectors are float pairs
+ *     (hi + lo, about 48 significant bits) computed with error-free
+ *     transformations on the FP32 pipes; the stabilisation is FP64. */
+typedef enum { DQMC_PREC_FP64 = 0, DQMC_PREC_FP32 = 1, DQMC_PREC_MIXED = 2 } dqmc_precision;
 
 /* One model: a lattice with its couplings (Sec. 3.1, the Operator type with
  * hopping Op_T, g = -dtau, and single-site vertices Op_V).  Chains refer to a

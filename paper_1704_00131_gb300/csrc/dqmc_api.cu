@@ -102,6 +102,7 @@ struct ModelHost {
   // device
   double *K = nullptr, *E = nullptr, *Einv = nullptr, *ident = nullptr, *vsign_d = nullptr;
   float *E32 = nullptr, *Einv32 = nullptr;
+  float *Edd = nullptr, *Einvdd = nullptr;  // (hi, lo) pairs
   int* site_d = nullptr;
 };
 
@@ -207,6 +208,7 @@ dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
   M.d.vertex_sign = nullptr;
   std::vector<double> K((size_t)nfl * N * ld, 0.0), E((size_t)nfl * N * ld, 0.0), Ei((size_t)nfl * N * ld, 0.0);
   std::vector<float> E32((size_t)nfl * N * ld, 0.f), Ei32((size_t)nfl * N * ld, 0.f);
+  std::vector<float> Edd((size_t)2 * nfl * N * ld, 0.f), Eidd((size_t)2 * nfl * N * ld, 0.f);
   for (int f = 0; f < nfl; ++f) {
     std::vector<double> Kf(M.hopping.begin() + (size_t)f * N * N, M.hopping.begin() + (size_t)(f + 1) * N * N);
     symmetric_eigen(N, Kf, M.eigval[f], M.eigvec[f]);
@@ -220,6 +222,10 @@ dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
         Ei[o] = Eif[(size_t)i * N + j];
         E32[o] = (float)E[o];
         Ei32[o] = (float)Ei[o];
+        Edd[2 * o] = E32[o];
+        Edd[2 * o + 1] = (float)(E[o] - (double)E32[o]);
+        Eidd[2 * o] = Ei32[o];
+        Eidd[2 * o + 1] = (float)(Ei[o] - (double)Ei32[o]);
       }
   }
   std::vector<double> ident((size_t)2 * N * ld + ld, 0.0);
@@ -234,6 +240,8 @@ dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
   if ((st = upload(ctx, &M.Einv, Ei.data(), Ei.size()))) return st;
   if ((st = upload(ctx, &M.E32, E32.data(), E32.size()))) return st;
   if ((st = upload(ctx, &M.Einv32, Ei32.data(), Ei32.size()))) return st;
+  if ((st = upload(ctx, &M.Edd, Edd.data(), Edd.size()))) return st;
+  if ((st = upload(ctx, &M.Einvdd, Eidd.data(), Eidd.size()))) return st;
   if ((st = upload(ctx, &M.ident, ident.data(), ident.size()))) return st;
   if ((st = upload(ctx, &M.site_d, M.site.data(), M.site.size()))) return st;
   if ((st = upload(ctx, &M.vsign_d, M.vsign.data(), M.vsign.size()))) return st;
@@ -244,7 +252,7 @@ dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
 // (ptrs filled when base != nullptr).
 size_t chain_layout(const ModelHost& M, int precision, int delay_k, unsigned char* base, ChainDev* C) {
   const int N = M.d.n_sites, ld = M.ld, nfl = M.d.n_flavors, nst = M.d.L / M.d.n_wrap;
-  const size_t rs = precision == DQMC_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t rs = precision == DQMC_PREC_FP32 ? sizeof(float) : sizeof(double);  // FP64 or float pairs
   size_t off = 0;
   auto take = [&](size_t bytes) -> unsigned char* {
     off = align_up(off, 256);
@@ -294,6 +302,8 @@ void fill_model_fields(const ModelHost& M, ChainDev& C) {
     C.Einv[s] = M.Einv + s * mat;
     C.E32[s] = M.E32 + s * mat;
     C.Einv32[s] = M.Einv32 + s * mat;
+    C.Edd[s] = M.Edd + 2 * s * mat;
+    C.Einvdd[s] = M.Einvdd + 2 * s * mat;
   }
   C.site = M.site_d;
   C.vsign = M.vsign_d;
@@ -340,7 +350,7 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
     return fail(*out, DQMC_EINVAL, "null argument or empty model/chain list");
   }
   c->opts = *opts;
-  if (opts->precision != DQMC_PREC_FP64 && opts->precision != DQMC_PREC_FP32) {
+  if (opts->precision != DQMC_PREC_FP64 && opts->precision != DQMC_PREC_FP32 && opts->precision != DQMC_PREC_MIXED) {
     *out = ctx.release();
     return fail(*out, DQMC_EINVAL, "unknown precision %d", opts->precision);
   }

@@ -21,6 +21,8 @@ struct ChainDev {
   const double* Einv[kMaxFlavors];
   const float* E32[kMaxFlavors];  // FP32 copies for the mixed path
   const float* Einv32[kMaxFlavors];
+  const void* Edd[kMaxFlavors];   // float-float (hi, lo) copies for the mixed path
+  const void* Einvdd[kMaxFlavors];
   const int* site;                // [MV]
   const double* vsign;            // [nfl][MV]
   const double* ident;            // identity UDV: Q=I [N][ld], T=I [N][ld], D=1 [ld]

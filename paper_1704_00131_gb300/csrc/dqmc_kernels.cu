@@ -141,6 +141,70 @@ __device__ __forceinline__ int block_argmax(double v, int idx, double* red, int*
 }
 
 // --------------------------------------------------------------------------
+// Float-float ("double-word") numbers: x = hi + lo with |lo| <= ulp(hi)/2,
+// about 48 significant bits on the FP32 pipes, which run 64x faster than FP64
+// on this GPU.  Error-free transformations: TwoSum (Knuth), FastTwoSum
+// (Dekker), TwoProd with an FMA (Joldes, Muller, Popescu, ACM TOMS 2017).
+// The working Green function of the mixed path is stored in this format.
+// --------------------------------------------------------------------------
+struct dd {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dd two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dd fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  const dd s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+// c + a * b
+__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  const dd s = two_sum(c.hi, p);
+  return fast_two_sum(s.hi, s.lo + (c.lo + e));
+}
+
+// Arithmetic adapters of the working precision (double, float, dd).
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(dd x) { return (double)x.hi + (double)x.lo; }
+template <typename R>
+__device__ __forceinline__ R from_d(double x);
+template <>
+__device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+template <>
+__device__ __forceinline__ dd from_d<dd>(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ dd rfma(dd a, dd b, dd c) { return dd_fma(a, b, c); }
+__device__ __forceinline__ double rmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float rmul(float a, float b) { return a * b; }
+__device__ __forceinline__ dd rmul(dd a, dd b) { return dd_mul(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return a - b; }
+__device__ __forceinline__ float rsub(float a, float b) { return a - b; }
+__device__ __forceinline__ dd rsub(dd a, dd b) { return dd_add(a, {-b.hi, -b.lo}); }
+
+// --------------------------------------------------------------------------
 // CTA-level dense product C = op(A) op(B), row-major, generic pointers
 // (global or shared).  64x64 output tiles, 16-deep K panels staged in shared
 // memory, 4x4 outputs per thread.  C must not alias A or B.
@@ -198,6 +262,75 @@ __device__ void cta_gemm(int M, int Nc, int Kd, const T* __restrict__ A, int lda
         for (int j = 0; j < 4; ++j) {
           const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
           if (gm < M && gn < Nc) C[(size_t)gm * ldc + gn] = acc[i][j];
+        }
+    }
+  __syncthreads();
+}
+
+// The same tiling for float-float operands: every product hi*hi is split
+// exactly (TwoProd), its high part summed with TwoSum into the accumulator's
+// high word, the rounding errors and the hi*lo, lo*hi cross terms gathered in
+// the low word and renormalised once per output.
+__device__ void cta_gemm_dd(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B,
+                            int ldb, dd* __restrict__ C, int ldc, dd* sm) {
+  dd* As = sm;            // [16][64]
+  dd* Bs = sm + 16 * 64;  // [16][64]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += 64)
+    for (int n0 = 0; n0 < Nc; n0 += 64) {
+      float ah[4][4], al[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { ah[i][j] = 0.f; al[i][j] = 0.f; }
+      for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+        for (int e = tid; e < 1024; e += kThreads) {
+          const int r = e >> 4, kk = e & 15;
+          const int gm = m0 + r, gk = k0 + kk;
+          dd val = {0.f, 0.f};
+          if (gm < M && gk < Kd) val = A[(size_t)gm * lda + gk];
+          As[kk * 64 + r] = val;
+        }
+#pragma unroll
+        for (int e = tid; e < 1024; e += kThreads) {
+          const int kk = e >> 6, c = e & 63;
+          const int gk = k0 + kk, gn = n0 + c;
+          dd val = {0.f, 0.f};
+          if (gk < Kd && gn < Nc) val = B[(size_t)gk * ldb + gn];
+          Bs[kk * 64 + c] = val;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+          dd a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + ty * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + tx * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const float p = a[i].hi * b[j].hi;
+              const float pe = fmaf(a[i].hi, b[j].hi, -p);
+              const float s = ah[i][j] + p;
+              const float bb = s - ah[i][j];
+              const float se = (ah[i][j] - (s - bb)) + (p - bb);
+              ah[i][j] = s;
+              float lo = al[i][j] + (se + pe);
+              lo = fmaf(a[i].hi, b[j].lo, lo);
+              al[i][j] = fmaf(a[i].lo, b[j].hi, lo);
+            }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+          if (gm < M && gn < Nc) C[(size_t)gm * ldc + gn] = fast_two_sum(ah[i][j], al[i][j]);
         }
     }
   __syncthreads();
@@ -729,7 +862,7 @@ __global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains,
     Real* G = (Real*)C.G[s];
     for (int e = threadIdx.x; e < C.N * C.N; e += kThreads) {
       const int x = e / C.N, y = e - x * C.N;
-      G[(size_t)x * C.ld + y] = (Real)Gf[(size_t)x * C.ld + y];
+      G[(size_t)x * C.ld + y] = from_d<Real>(Gf[(size_t)x * C.ld + y]);
     }
   } else {
     for (int e = threadIdx.x; e < C.N * C.N; e += kThreads) {
@@ -749,7 +882,7 @@ __global__ void copy_green_kernel(ChainDev* chains, int chain, int flavor, doubl
   const Real* G = (const Real*)C.G[flavor];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.N * C.N; e += gridDim.x * blockDim.x) {
     const int x = e / C.N, y = e - x * C.N;
-    out[e] = (double)G[(size_t)x * C.ld + y];
+    out[e] = to_d(G[(size_t)x * C.ld + y]);
   }
 }
 
@@ -771,14 +904,16 @@ __global__ void reset_stats_kernel(ChainDev* chains, int n_chains) {
 template <typename Real>
 __device__ void v_wrap(const ChainDev& C, Real* G, const double* v, double a, Smem& S) {
   const int N = C.N, ld = C.ld;
+  Real* evr = reinterpret_cast<Real*>(S.ev);
+  Real* evi = reinterpret_cast<Real*>(S.hv);
   for (int x = threadIdx.x; x < N; x += kThreads) {
-    S.ev[x] = exp(a * v[x]);
-    S.hv[x] = exp(-a * v[x]);
+    evr[x] = from_d<Real>(exp(a * v[x]));
+    evi[x] = from_d<Real>(exp(-a * v[x]));
   }
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int x = e / N, y = e - x * N;
-    G[(size_t)x * ld + y] = G[(size_t)x * ld + y] * ((Real)S.ev[x] * (Real)S.hv[y]);
+    G[(size_t)x * ld + y] = rmul(rmul(G[(size_t)x * ld + y], evr[x]), evi[y]);
   }
   __syncthreads();
 }
@@ -805,6 +940,16 @@ __device__ void t_wrap<float>(const ChainDev& C, int s, float* G, float* Gt, boo
   cta_gemm<float, false, false>(N, N, N, Gt, ld, Y, ld, G, ld, sm);
 }
 
+template <>
+__device__ void t_wrap<dd>(const ChainDev& C, int s, dd* G, dd* Gt, bool up, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  const dd* X = (const dd*)(up ? C.Edd[s] : C.Einvdd[s]);
+  const dd* Y = (const dd*)(up ? C.Einvdd[s] : C.Edd[s]);
+  dd* sm = reinterpret_cast<dd*>(S.gemm);
+  cta_gemm_dd(N, N, N, X, ld, G, ld, Gt, ld, sm);
+  cta_gemm_dd(N, N, N, Gt, ld, Y, ld, G, ld, sm);
+}
+
 // G <- G + sum_m a_m b_m^T  (flush of the delayed rank-k update)
 template <typename Real>
 __device__ void flush_delayed(const ChainDev& C, Real* G, const Real* A, const Real* B, int nacc) {
@@ -812,7 +957,7 @@ __device__ void flush_delayed(const ChainDev& C, Real* G, const Real* A, const R
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int x = e / N, y = e - x * N;
     Real acc = G[(size_t)x * ld + y];
-    for (int m = 0; m < nacc; ++m) acc = fma(A[(size_t)m * ld + x], B[(size_t)m * ld + y], acc);
+    for (int m = 0; m < nacc; ++m) acc = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + y], acc);
     G[(size_t)x * ld + y] = acc;
   }
   __syncthreads();
@@ -844,7 +989,7 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     S.fnew[q] = (int8_t)fn;
     S.qsite[q] = C.site[k];
   }
-  for (int x = tid; x < N; x += kThreads) S.d[x] = (double)G[(size_t)x * ld + x];
+  for (int x = tid; x < N; x += kThreads) S.d[x] = to_d(G[(size_t)x * ld + x]);
   __syncthreads();
   int pos = 0, nacc = 0;
   int64_t n_acc_slice = 0;
@@ -872,17 +1017,18 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     const double fac = S.delta[first] / Rs[first];
     Real* a = A + (size_t)nacc * ld;
     Real* b = B + (size_t)nacc * ld;
+    const Real mfac = from_d<Real>(-fac);
     for (int x = tid; x < N; x += kThreads) {
       Real cx = G[(size_t)x * ld + i], ry = G[(size_t)i * ld + x];
       for (int m = 0; m < nacc; ++m) {
-        cx = fma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
-        ry = fma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
+        cx = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
+        ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
       }
-      a[x] = (Real)(-fac) * cx;
-      b[x] = (x == i ? Real(1) : Real(0)) - ry;
+      a[x] = rmul(mfac, cx);
+      b[x] = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
     }
     __syncthreads();
-    for (int x = tid; x < N; x += kThreads) S.d[x] += (double)a[x] * (double)b[x];
+    for (int x = tid; x < N; x += kThreads) S.d[x] += to_d(a[x]) * to_d(b[x]);
     if (tid == 0) S.fslice[k] = S.fnew[first];
     ++nacc;
     ++n_acc_slice;
@@ -932,10 +1078,10 @@ __device__ void stabilise(ChainDev& C, int s, int j, bool up, Real* G, Smem& S, 
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int x = e / N, y = e - x * N;
     const double gf = Gf[(size_t)x * ld + y];
-    const double dd = fabs(gf - (double)G[(size_t)x * ld + y]);
-    mx = fmax(mx, dd);
-    sm += dd;
-    G[(size_t)x * ld + y] = (Real)gf;
+    const double dg = fabs(gf - to_d(G[(size_t)x * ld + y]));
+    mx = fmax(mx, dg);
+    sm += dg;
+    G[(size_t)x * ld + y] = from_d<Real>(gf);
   }
   ev_max = block_max(mx, S.red);
   ev_sum = block_sum(sm, S.red);
@@ -955,10 +1101,10 @@ __device__ void measure(ChainDev& C, int s, const Real* G, Smem& S, cg::cluster_
   double kin = 0.0, part = 0.0;
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int x = e / N, y = e - x * N;
-    kin += K[(size_t)x * ld + y] * ((x == y ? 1.0 : 0.0) - (double)G[(size_t)y * ld + x]);
+    kin += K[(size_t)x * ld + y] * ((x == y ? 1.0 : 0.0) - to_d(G[(size_t)y * ld + x]));
   }
   for (int x = threadIdx.x; x < N; x += kThreads) {
-    const double gxx = (double)G[(size_t)x * ld + x];
+    const double gxx = to_d(G[(size_t)x * ld + x]);
     part += 1.0 - gxx;
     S.xdiag[x] = gxx;
   }
@@ -1215,10 +1361,14 @@ cudaError_t launch_fresh_green(ChainDev* chains, int n_chains, int nfl, int prec
     cudaError_t e = set_smem((const void*)fresh_green_kernel<double>, smem);
     if (e != cudaSuccess) return e;
     fresh_green_kernel<double><<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, mode, out, out_chain);
-  } else {
+  } else if (precision == 1) {
     cudaError_t e = set_smem((const void*)fresh_green_kernel<float>, smem);
     if (e != cudaSuccess) return e;
     fresh_green_kernel<float><<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, mode, out, out_chain);
+  } else {
+    cudaError_t e = set_smem((const void*)fresh_green_kernel<dd>, smem);
+    if (e != cudaSuccess) return e;
+    fresh_green_kernel<dd><<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, mode, out, out_chain);
   }
   return cudaGetLastError();
 }
@@ -1227,8 +1377,10 @@ cudaError_t launch_copy_green(ChainDev* chains, int chain, int flavor, int preci
                               cudaStream_t st) {
   if (precision == 0)
     copy_green_kernel<double><<<16, 256, 0, st>>>(chains, chain, flavor, out);
-  else
+  else if (precision == 1)
     copy_green_kernel<float><<<16, 256, 0, st>>>(chains, chain, flavor, out);
+  else
+    copy_green_kernel<dd><<<16, 256, 0, st>>>(chains, chain, flavor, out);
   return cudaGetLastError();
 }
 
@@ -1266,8 +1418,9 @@ static cudaError_t launch_sweep_t(ChainDev* chains, const SweepParams& p, int nf
 
 cudaError_t launch_sweep(ChainDev* chains, const SweepParams& p, int nfl, int precision, size_t smem,
                          cudaStream_t st) {
-  return precision == 0 ? launch_sweep_t<double>(chains, p, nfl, smem, st)
-                        : launch_sweep_t<float>(chains, p, nfl, smem, st);
+  if (precision == 0) return launch_sweep_t<double>(chains, p, nfl, smem, st);
+  if (precision == 1) return launch_sweep_t<float>(chains, p, nfl, smem, st);
+  return launch_sweep_t<dd>(chains, p, nfl, smem, st);
 }
 
 cudaError_t launch_logdet_grad(ChainDev* chains, int n_cfg, int nfl, const double* eigvec, const double* eigval,
