@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c5"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--chains", type=int, default=0, help="override the number of chains (c3/c5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -282,6 +282,7 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
             "sweeps_per_s": 1000.0 / ms_step * world,
             "accept_rate": st["accepted"] / st["proposals"],
             "prec_green_max": st["prec_green_max"], "prec_green_mean": st["prec_green_mean"],
+            "critical_chain_ms": {k: round(st[k], 3) for k in ("ms_update", "ms_wrap", "ms_stab", "ms_measure")},
             "gpu_launches": 2 * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                          "frac": achieved_tf / peak_tf, "traffic": None,

@@ -109,6 +109,10 @@ typedef struct {
   double prec_phase_max;      /* max |sign_tracked - sign_fresh|                   */
   double mean_sign;           /* mean over chains and sweeps of the end-of-sweep sign */
   float ms_total;             /* device time of the call (CUDA events)             */
+  float ms_update;            /* the slowest chain's time in the updates (a4, a5), */
+  float ms_wrap;              /*   the wraps (a3, a6), the stabilisation (a7-a10)  */
+  float ms_stab;              /*   and the measurement (a12), from SM cycle        */
+  float ms_measure;           /*   counters at the device's clock rate             */
 } dqmc_sweep_stats;
 
 /* Create a context with n_chains chains; chain c uses models[chain_model[c]].

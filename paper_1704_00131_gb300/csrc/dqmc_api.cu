@@ -120,7 +120,9 @@ struct dqmc_ctx {
   int* order_d = nullptr;
   unsigned char* arena = nullptr;
   std::vector<void*> model_allocs;
-  size_t smem = 0;
+  size_t smem = 0;        // dynamic shared memory of the fresh-G / gradient kernels
+  size_t smem_sweep = 0;  // ... of the sweep kernel (plus the delayed vectors when they fit)
+  int ab_smem = 0;
   uint64_t sweep_counter = 0;
   int maxN = 0, maxld = 0, maxMV = 0;
   double* scratch = nullptr;  // [nfl][maxN][maxN] FP64 for dqmc_greens
@@ -443,6 +445,13 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
   CUDA_TRY(c, cudaEventCreate(&c->ev0));
   CUDA_TRY(c, cudaEventCreate(&c->ev1));
   c->smem = dqmc::sweep_smem_bytes(c->maxN, c->maxld, c->maxMV, opts->delay_k, opts->precision);
+  {
+    // delayed vectors A, B in shared memory when they fit beside the rest
+    const size_t rs = opts->precision == DQMC_PREC_FP32 ? sizeof(float) : sizeof(double);
+    const size_t ab = (size_t)2 * opts->delay_k * c->maxld * rs;
+    c->ab_smem = (c->smem + ab <= 200 * 1024) ? 1 : 0;
+    c->smem_sweep = c->smem + (c->ab_smem ? ab : 0);
+  }
   if (!fields_or_null) CUDA_TRY(c, dqmc::launch_init_fields(c->chains_d, n_chains, opts->seed, 0, 0, c->stream));
   return initial_fill(c);
 }
@@ -460,10 +469,11 @@ dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats)
   P.meas_first = ctx->opts.meas_first;
   P.meas_last = ctx->opts.meas_last;
   P.n_chains = n;
+  P.ab_smem = ctx->ab_smem;
   P.order = ctx->order_d;
   for (int i = 0; i < n_sweeps; ++i) {
     P.sweep = ctx->sweep_counter++;
-    CUDA_TRY(ctx, dqmc::launch_sweep(ctx->chains_d, P, ctx->nfl, ctx->opts.precision, ctx->smem, ctx->stream));
+    CUDA_TRY(ctx, dqmc::launch_sweep(ctx->chains_d, P, ctx->nfl, ctx->opts.precision, ctx->smem_sweep, ctx->stream));
   }
   if (!stats) return DQMC_OK;
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
@@ -486,6 +496,25 @@ dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats)
     S.prec_phase_max = std::max(S.prec_phase_max, C.phase_max);
     sign_sum += C.sweep_sign_sum;
     err |= C.error;
+  }
+  // per-phase times of the slowest chain (the critical path of the launch)
+  {
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    const double per_ms = khz > 0 ? (double)khz : 1.0;
+    double best = -1.0;
+    for (const ChainDev& C : ctx->chains_h)
+      for (int s = 0; s < C.nfl; ++s) {
+        const double tot = (double)(C.cyc[s][0] + C.cyc[s][1] + C.cyc[s][2] + C.cyc[s][3]);
+        if (tot > best) {
+          best = tot;
+          S.ms_update = (float)(C.cyc[s][0] / per_ms);
+          S.ms_wrap = (float)(C.cyc[s][1] / per_ms);
+          S.ms_stab = (float)(C.cyc[s][2] / per_ms);
+          S.ms_measure = (float)(C.cyc[s][3] / per_ms);
+        }
+      }
   }
   S.prec_green_mean = events ? prec_sum / (double)events : 0.0;
   S.mean_sign = n_sweeps ? sign_sum / ((double)n_sweeps * n) : 0.0;

@@ -52,6 +52,9 @@ struct ChainDev {
   double logdet[kMaxFlavors];
   int fresh_sign[kMaxFlavors];
   int error;                      // nonzero: a numerical failure was detected
+  // SM cycles spent per phase during the current dqmc_sweep call, per flavor:
+  // 0 updates, 1 wraps (V and T), 2 stabilisation, 3 measurement
+  int64_t cyc[kMaxFlavors][4];
 };
 
 constexpr int kWorkMats = 10;     // N x ld FP64 matrices per flavor in `work`
@@ -65,6 +68,7 @@ struct SweepParams {
   int delay_k;
   int measure, meas_first, meas_last;
   int n_chains;
+  int ab_smem;           // delayed vectors in shared memory (else in the chain's arena)
   const int* order;      // chain index for cluster c (heavy chains first)
 };
 

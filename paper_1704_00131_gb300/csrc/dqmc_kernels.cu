@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <type_traits>
 
 #include "../../include/dqmc.h"
 #include "dqmc_internal.h"
@@ -206,112 +207,139 @@ __device__ __forceinline__ dd rsub(dd a, dd b) { return dd_add(a, {-b.hi, -b.lo}
 
 // --------------------------------------------------------------------------
 // CTA-level dense product C = op(A) op(B), row-major, generic pointers
-// (global or shared).  64x64 output tiles, 16-deep K panels staged in shared
-// memory, 4x4 outputs per thread.  C must not alias A or B.
+// (global or shared).  Output tiles of 16R x 16R (R = 3, 4, 5 outputs per
+// thread and dimension; R is picked per size so that N = 144 or 400 need no
+// padding), 16-deep K panels staged in shared memory.  C must not alias A or B.
 // --------------------------------------------------------------------------
-template <typename T, bool TA, bool TB>
-__device__ void cta_gemm(int M, int Nc, int Kd, const T* __restrict__ A, int lda, const T* __restrict__ B,
-                         int ldb, T* __restrict__ C, int ldc, T* sm) {
-  T* As = sm;            // [16][64]
-  T* Bs = sm + 16 * 64;  // [16][64]
+constexpr int kGemmMaxTile = 80;  // 16 * 5
+
+__host__ __device__ inline int gemm_pick_r(int n) {
+  int best_r = 4, best = 1 << 30;
+  for (int r = 5; r >= 3; --r) {
+    const int t = 16 * r;
+    const int padded = ((n + t - 1) / t) * t;
+    if (padded < best) { best = padded; best_r = r; }
+  }
+  return best_r;
+}
+
+template <typename T, bool TA, bool TB, int R>
+__device__ void cta_gemm_r(int M, int Nc, int Kd, const T* __restrict__ A, int lda, const T* __restrict__ B,
+                           int ldb, T* __restrict__ C, int ldc, T* sm) {
+  constexpr int TT = 16 * R;
+  T* As = sm;            // [16][TT]
+  T* Bs = sm + 16 * TT;  // [16][TT]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int m0 = 0; m0 < M; m0 += 64)
-    for (int n0 = 0; n0 < Nc; n0 += 64) {
-      T acc[4][4];
+  for (int m0 = 0; m0 < M; m0 += TT)
+    for (int n0 = 0; n0 < Nc; n0 += TT) {
+      T acc[R][R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        for (int j = 0; j < R; ++j) acc[i][j] = T(0);
       for (int k0 = 0; k0 < Kd; k0 += 16) {
 #pragma unroll
-        for (int e = tid; e < 1024; e += kThreads) {
+        for (int e = tid; e < 16 * TT; e += kThreads) {
           int r, kk;
-          if (!TA) { r = e >> 4; kk = e & 15; } else { kk = e >> 6; r = e & 63; }
+          if (!TA) { r = e >> 4; kk = e & 15; } else { kk = e / TT; r = e - kk * TT; }
           const int gm = m0 + r, gk = k0 + kk;
           T val = T(0);
           if (gm < M && gk < Kd) val = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-          As[kk * 64 + r] = val;
+          As[kk * TT + r] = val;
         }
 #pragma unroll
-        for (int e = tid; e < 1024; e += kThreads) {
+        for (int e = tid; e < 16 * TT; e += kThreads) {
           int kk, c;
-          if (!TB) { kk = e >> 6; c = e & 63; } else { c = e >> 4; kk = e & 15; }
+          if (!TB) { kk = e / TT; c = e - kk * TT; } else { c = e >> 4; kk = e & 15; }
           const int gk = k0 + kk, gn = n0 + c;
           T val = T(0);
           if (gk < Kd && gn < Nc) val = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-          Bs[kk * 64 + c] = val;
+          Bs[kk * TT + c] = val;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-          T a[4], b[4];
+          T a[R], b[R];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + ty * 4 + i];
+          for (int i = 0; i < R; ++i) a[i] = As[kk * TT + ty * R + i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + tx * 4 + j];
+          for (int j = 0; j < R; ++j) b[j] = Bs[kk * TT + tx * R + j];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < R; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+        for (int j = 0; j < R; ++j) {
+          const int gm = m0 + ty * R + i, gn = n0 + tx * R + j;
           if (gm < M && gn < Nc) C[(size_t)gm * ldc + gn] = acc[i][j];
         }
     }
   __syncthreads();
 }
 
+template <typename T, bool TA, bool TB>
+__device__ void cta_gemm(int M, int Nc, int Kd, const T* __restrict__ A, int lda, const T* __restrict__ B,
+                         int ldb, T* __restrict__ C, int ldc, T* sm) {
+  const int r = gemm_pick_r(M > Nc ? M : Nc);
+  if (r == 3) cta_gemm_r<T, TA, TB, 3>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+  else if (r == 5) cta_gemm_r<T, TA, TB, 5>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+  else cta_gemm_r<T, TA, TB, 4>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+}
+
 // The same tiling for float-float operands: every product hi*hi is split
 // exactly (TwoProd), its high part summed with TwoSum into the accumulator's
 // high word, the rounding errors and the hi*lo, lo*hi cross terms gathered in
 // the low word and renormalised once per output.
-__device__ void cta_gemm_dd(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B,
-                            int ldb, dd* __restrict__ C, int ldc, dd* sm) {
-  dd* As = sm;            // [16][64]
-  dd* Bs = sm + 16 * 64;  // [16][64]
+template <bool TA, bool TB, int R>
+__device__ void cta_gemm_dd_r(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B,
+                              int ldb, dd* __restrict__ C, int ldc, dd* sm) {
+  constexpr int TT = 16 * R;
+  dd* As = sm;            // [16][TT]
+  dd* Bs = sm + 16 * TT;  // [16][TT]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int m0 = 0; m0 < M; m0 += 64)
-    for (int n0 = 0; n0 < Nc; n0 += 64) {
-      float ah[4][4], al[4][4];
+  for (int m0 = 0; m0 < M; m0 += TT)
+    for (int n0 = 0; n0 < Nc; n0 += TT) {
+      float ah[R][R], al[R][R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { ah[i][j] = 0.f; al[i][j] = 0.f; }
+        for (int j = 0; j < R; ++j) { ah[i][j] = 0.f; al[i][j] = 0.f; }
       for (int k0 = 0; k0 < Kd; k0 += 16) {
 #pragma unroll
-        for (int e = tid; e < 1024; e += kThreads) {
-          const int r = e >> 4, kk = e & 15;
+        for (int e = tid; e < 16 * TT; e += kThreads) {
+          int r, kk;
+          if (!TA) { r = e >> 4; kk = e & 15; } else { kk = e / TT; r = e - kk * TT; }
           const int gm = m0 + r, gk = k0 + kk;
           dd val = {0.f, 0.f};
-          if (gm < M && gk < Kd) val = A[(size_t)gm * lda + gk];
-          As[kk * 64 + r] = val;
+          if (gm < M && gk < Kd) val = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+          As[kk * TT + r] = val;
         }
 #pragma unroll
-        for (int e = tid; e < 1024; e += kThreads) {
-          const int kk = e >> 6, c = e & 63;
+        for (int e = tid; e < 16 * TT; e += kThreads) {
+          int kk, c;
+          if (!TB) { kk = e / TT; c = e - kk * TT; } else { c = e >> 4; kk = e & 15; }
           const int gk = k0 + kk, gn = n0 + c;
           dd val = {0.f, 0.f};
-          if (gk < Kd && gn < Nc) val = B[(size_t)gk * ldb + gn];
-          Bs[kk * 64 + c] = val;
+          if (gk < Kd && gn < Nc) val = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+          Bs[kk * TT + c] = val;
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < 16; ++kk) {
-          dd a[4], b[4];
+          dd a[R], b[R];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = As[kk * 64 + ty * 4 + i];
+          for (int i = 0; i < R; ++i) a[i] = As[kk * TT + ty * R + i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = Bs[kk * 64 + tx * 4 + j];
+          for (int j = 0; j < R; ++j) b[j] = Bs[kk * TT + tx * R + j];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < R; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < R; ++j) {
               const float p = a[i].hi * b[j].hi;
               const float pe = fmaf(a[i].hi, b[j].hi, -p);
               const float s = ah[i][j] + p;
@@ -326,14 +354,25 @@ __device__ void cta_gemm_dd(int M, int Nc, int Kd, const dd* __restrict__ A, int
         __syncthreads();
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+        for (int j = 0; j < R; ++j) {
+          const int gm = m0 + ty * R + i, gn = n0 + tx * R + j;
           if (gm < M && gn < Nc) C[(size_t)gm * ldc + gn] = fast_two_sum(ah[i][j], al[i][j]);
         }
     }
   __syncthreads();
+}
+
+template <bool TA, bool TB>
+__device__ void cta_gemm_dd(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B,
+                            int ldb, dd* __restrict__ C, int ldc, dd* sm) {
+  // float pairs double the accumulator registers: tiles of 48 or 64 only, so
+  // that two CTAs fit on an SM
+  const int n = M > Nc ? M : Nc;
+  const int p3 = (n + 47) / 48 * 48, p4 = (n + 63) / 64 * 64;
+  if (p3 < p4) cta_gemm_dd_r<TA, TB, 3>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+  else cta_gemm_dd_r<TA, TB, 4>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
 }
 
 template <typename T>
@@ -349,7 +388,7 @@ __device__ __forceinline__ void cta_copy(int N, int ld, const T* src, T* dst) {
 // Shared-memory layout of the sweep kernel.
 // --------------------------------------------------------------------------
 struct Smem {
-  double* gemm;     // 2*16*64 doubles (also used by float GEMMs)
+  double* gemm;     // 2*16*kGemmMaxTile doubles (also used by float / float-pair GEMMs)
   double* v;        // [ld] slice potential / exp factors
   double* ev;       // [ld]
   double* d;        // [ld] current diagonal of the effective G
@@ -365,23 +404,27 @@ struct Smem {
   int* qsite;       // [MV]
   int8_t* fnew;     // [MV]
   int8_t* fslice;   // [MV] fields of the current slice
+  double* ab;       // delayed vectors A, B [2][k][ld] when they fit in shared memory
+  double* qred;     // [8][128] partial sums of the QR trailing update
 };
 
 __host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
   size_t b = 0;
-  b += 2 * 16 * 64 * 8;
+  b += 2 * 16 * kGemmMaxTile * 8;
   b += 6 * (size_t)ld * 8;        // v, ev, d, hv, xdiag, spare
   b += 5 * (size_t)MV * 8;        // u2, delta, gam, Rs[2]
   b += 8 * 8 + 32 * 8 + 32 * 4;   // xs, red, ired
   b += (size_t)MV * 4;            // qsite
   b += 2 * (size_t)MV + 16;       // fnew, fslice
+  b = (b + 15) / 16 * 16;
+  b += 8 * 128 * 8;               // qred
   return b;
 }
 
 __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   Smem s;
   double* p = reinterpret_cast<double*>(base);
-  s.gemm = p; p += 2 * 16 * 64;
+  s.gemm = p; p += 2 * 16 * kGemmMaxTile;
   s.v = p; p += ld;
   s.ev = p; p += ld;
   s.d = p; p += ld;
@@ -399,7 +442,10 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   s.qsite = ip; ip += MV;
   int8_t* bp = reinterpret_cast<int8_t*>(ip);
   s.fnew = bp; bp += MV;
-  s.fslice = bp;
+  s.fslice = bp; bp += MV + 16;
+  const size_t off = ((size_t)(bp - reinterpret_cast<int8_t*>(base)) + 15) / 16 * 16;
+  s.qred = reinterpret_cast<double*>(base + off);
+  s.ab = s.qred + 8 * 128;
   return s;
 }
 
@@ -456,6 +502,47 @@ __device__ inline UDV slot_udv(const ChainDev& C, int s, int j) {
   u.D = b + (size_t)2 * C.N * C.ld;
   u.detq = C.slot_detq[s][j];
   return u;
+}
+
+// M[k:, j] -= bk v (v^T M[k:, j]) for the columns j0 <= j < N, v = hv[k:].
+// 8 row groups x 32 columns: rows are read coalesced along j; the partial dot
+// products of the row groups are summed in shared memory in a fixed order.
+__device__ void householder_apply(int N, int ld, double* M, int k, int j0, double bk, const double* hv,
+                                  double* qred) {
+  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
+  for (int c0 = j0; c0 < N; c0 += 128) {
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = k + rg; i < N; i += 8) {
+      const double vi = hv[i];
+      const double* row = M + (size_t)i * ld;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < N) w[q] = fma(vi, row[j], w[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
+    __syncthreads();
+    double wt[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double t = 0.0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) t += qred[r * 128 + lane + 32 * q];
+      wt[q] = bk * t;
+    }
+    for (int i = k + rg; i < N; i += 8) {
+      const double vi = hv[i];
+      double* row = M + (size_t)i * ld;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < N) row[j] -= wt[q] * vi;
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // Householder QR with column pivoting of M (N x N, in place): on return the
@@ -525,21 +612,7 @@ __device__ int qr_pivoted(int N, int ld, double* M, double* beta, double* vk0, d
     }
     if (bk != 0.0) detq = -detq;
     // apply H = I - bk v v^T to the trailing columns j > k
-    if (bk != 0.0) {
-      for (int j = k + 1 + tid; j < N; j += kThreads) {
-        double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
-        int i = k;
-        for (; i + 3 < N; i += 4) {
-          w0 = fma(S.hv[i], M[(size_t)i * ld + j], w0);
-          w1 = fma(S.hv[i + 1], M[(size_t)(i + 1) * ld + j], w1);
-          w2 = fma(S.hv[i + 2], M[(size_t)(i + 2) * ld + j], w2);
-          w3 = fma(S.hv[i + 3], M[(size_t)(i + 3) * ld + j], w3);
-        }
-        for (; i < N; ++i) w0 = fma(S.hv[i], M[(size_t)i * ld + j], w0);
-        const double w = bk * ((w0 + w1) + (w2 + w3));
-        for (int r = k; r < N; ++r) M[(size_t)r * ld + j] -= w * S.hv[r];
-      }
-    }
+    if (bk != 0.0) householder_apply(N, ld, M, k, k + 1, bk, S.hv, S.qred);
     __syncthreads();
     if (tid == 0) M[(size_t)k * ld + k] = (xnorm > 0.0) ? alpha : x0;
     // downdate the trailing column norms
@@ -577,18 +650,7 @@ __device__ void form_q(int N, int ld, const double* M, const double* beta, const
     if (bk == 0.0) continue;
     for (int i = k + tid; i < N; i += kThreads) S.hv[i] = (i == k) ? vk0[k] : M[(size_t)i * ld + k];
     __syncthreads();
-    for (int j = k + tid; j < N; j += kThreads) {
-      double w0 = 0.0, w1 = 0.0;
-      int i = k;
-      for (; i + 1 < N; i += 2) {
-        w0 = fma(S.hv[i], Q[(size_t)i * ld + j], w0);
-        w1 = fma(S.hv[i + 1], Q[(size_t)(i + 1) * ld + j], w1);
-      }
-      for (; i < N; ++i) w0 = fma(S.hv[i], Q[(size_t)i * ld + j], w0);
-      const double w = bk * (w0 + w1);
-      for (int r = k; r < N; ++r) Q[(size_t)r * ld + j] -= w * S.hv[r];
-    }
-    __syncthreads();
+    householder_apply(N, ld, Q, k, k, bk, S.hv, S.qred);
   }
 }
 
@@ -700,8 +762,11 @@ __device__ int lu_factor(int N, int ld, double* A, int* piv, double& logdet, int
 }
 
 // Solve (LU) Y = B for all columns of B (in place), rows permuted by piv first.
-__device__ void lu_solve(int N, int ld, const double* LU, const int* piv, double* B) {
-  const int tid = threadIdx.x;
+// Each row of the forward and backward substitution is one row-vector times
+// matrix product, computed with 8 row groups x 32 columns and a fixed-order
+// shared-memory reduction (rows of B read coalesced).
+__device__ void lu_solve(int N, int ld, const double* LU, const int* piv, double* B, double* qred) {
+  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
   for (int k = 0; k < N; ++k) {
     const int p = piv[k];
     if (p != k)
@@ -712,21 +777,41 @@ __device__ void lu_solve(int N, int ld, const double* LU, const int* piv, double
       }
     __syncthreads();
   }
-  for (int i = 1; i < N; ++i) {
-    for (int j = tid; j < N; j += kThreads) {
-      double acc = B[(size_t)i * ld + j];
-      for (int k = 0; k < i; ++k) acc -= LU[(size_t)i * ld + k] * B[(size_t)k * ld + j];
-      B[(size_t)i * ld + j] = acc;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int ii = (pass == 0 ? 1 : N - 1); pass == 0 ? ii < N : ii >= 0; ii += (pass == 0 ? 1 : -1)) {
+      const int klo = pass == 0 ? 0 : ii + 1, khi = pass == 0 ? ii : N;
+      const double* lrow = LU + (size_t)ii * ld;
+      for (int c0 = 0; c0 < N; c0 += 128) {
+        double w[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = klo + rg; k < khi; k += 8) {
+          const double l = lrow[k];
+          const double* brow = B + (size_t)k * ld;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = c0 + lane + 32 * q;
+            if (j < N) w[q] = fma(l, brow[j], w[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
+        __syncthreads();
+        if (rg == 0) {
+          const double dinv = pass == 1 ? 1.0 / lrow[ii] : 1.0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = c0 + lane + 32 * q;
+            double t = 0.0;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) t += qred[r * 128 + lane + 32 * q];
+            if (j < N) {
+              const double v = B[(size_t)ii * ld + j] - t;
+              B[(size_t)ii * ld + j] = pass == 1 ? v * dinv : v;
+            }
+          }
+        }
+        __syncthreads();
+      }
     }
-    __syncthreads();
-  }
-  for (int i = N - 1; i >= 0; --i) {
-    for (int j = tid; j < N; j += kThreads) {
-      double acc = B[(size_t)i * ld + j];
-      for (int k = i + 1; k < N; ++k) acc -= LU[(size_t)i * ld + k] * B[(size_t)k * ld + j];
-      B[(size_t)i * ld + j] = acc / LU[(size_t)i * ld + i];
-    }
-    __syncthreads();
   }
 }
 
@@ -762,7 +847,7 @@ __device__ int green_from_udv(const ChainDev& C, int s, UDV R, UDV Lf, double* G
   int sm;
   int* piv = C.iwork[s] + ld;
   if (lu_factor(N, ld, W0, piv, ldm, sm, S)) return 1;
-  lu_solve(N, ld, W0, piv, W1);
+  lu_solve(N, ld, W0, piv, W1, S.qred);
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
     const double dL = Lf.D[i];
@@ -890,7 +975,11 @@ __global__ void reset_stats_kernel(ChainDev* chains, int n_chains) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_chains) return;
   ChainDev& C = chains[c];
-  for (int s = 0; s < kMaxFlavors; ++s) { C.prec_sum[s] = 0.0; C.prec_max[s] = 0.0; }
+  for (int s = 0; s < kMaxFlavors; ++s) {
+    C.prec_sum[s] = 0.0;
+    C.prec_max[s] = 0.0;
+    for (int q = 0; q < 4; ++q) C.cyc[s][q] = 0;
+  }
   C.phase_max = 0.0;
   C.prec_events = 0;
   C.proposals = 0;
@@ -946,8 +1035,8 @@ __device__ void t_wrap<dd>(const ChainDev& C, int s, dd* G, dd* Gt, bool up, Sme
   const dd* X = (const dd*)(up ? C.Edd[s] : C.Einvdd[s]);
   const dd* Y = (const dd*)(up ? C.Einvdd[s] : C.Edd[s]);
   dd* sm = reinterpret_cast<dd*>(S.gemm);
-  cta_gemm_dd(N, N, N, X, ld, G, ld, Gt, ld, sm);
-  cta_gemm_dd(N, N, N, Gt, ld, Y, ld, G, ld, sm);
+  cta_gemm_dd<false, false>(N, N, N, X, ld, G, ld, Gt, ld, sm);
+  cta_gemm_dd<false, false>(N, N, N, Gt, ld, Y, ld, G, ld, sm);
 }
 
 // G <- G + sum_m a_m b_m^T  (flush of the delayed rank-k update)
@@ -1018,14 +1107,18 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     Real* a = A + (size_t)nacc * ld;
     Real* b = B + (size_t)nacc * ld;
     const Real mfac = from_d<Real>(-fac);
-    for (int x = tid; x < N; x += kThreads) {
-      Real cx = G[(size_t)x * ld + i], ry = G[(size_t)i * ld + x];
-      for (int m = 0; m < nacc; ++m) {
-        cx = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
-        ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
+    // column i of G_eff (tasks 0..N-1) and row i (tasks N..2N-1)
+    for (int t = tid; t < 2 * N; t += kThreads) {
+      if (t < N) {
+        Real cx = G[(size_t)t * ld + i];
+        for (int m = 0; m < nacc; ++m) cx = rfma(A[(size_t)m * ld + t], B[(size_t)m * ld + i], cx);
+        a[t] = rmul(mfac, cx);
+      } else {
+        const int x = t - N;
+        Real ry = G[(size_t)i * ld + x];
+        for (int m = 0; m < nacc; ++m) ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
+        b[x] = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
       }
-      a[x] = rmul(mfac, cx);
-      b[x] = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
     }
     __syncthreads();
     for (int x = tid; x < N; x += kThreads) S.d[x] += to_d(a[x]) * to_d(b[x]);
@@ -1048,6 +1141,152 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
   }
 }
 
+// ---- stabilisation with float-float products (mixed path) ----------------
+// Same steps as chain_step / green_from_udv; the dense products (the B chain,
+// T = D^-1 R P^T T, Q_R^T Q_L, T_R T_L^T, Q_L Y) run as float-float GEMMs on the
+// FP32 pipes, the pivoted QR, Q accumulation, LU and triangular solves stay
+// FP64.  Storage matrices (Q, T) remain FP64.
+__device__ inline void to_dd_mat(int N, int ld, const double* src, dd* dst) {
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    dst[(size_t)x * ld + y] = from_d<dd>(src[(size_t)x * ld + y]);
+  }
+  __syncthreads();
+}
+
+// dd -> double in place (same 8-byte slot)
+__device__ inline void dd_to_d_inplace(int N, int ld, void* buf) {
+  dd* a = reinterpret_cast<dd*>(buf);
+  double* b = reinterpret_cast<double*>(buf);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const dd v = a[(size_t)x * ld + y];
+    b[(size_t)x * ld + y] = to_d(v);
+  }
+  __syncthreads();
+}
+
+__device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  dd* X = reinterpret_cast<dd*>(wmat(C, s, 0));
+  dd* Y = reinterpret_cast<dd*>(wmat(C, s, 1));
+  dd* sm = reinterpret_cast<dd*>(S.gemm);
+  dd* evr = reinterpret_cast<dd*>(S.ev);
+  to_dd_mat(N, ld, src.Q, X);
+  const dd* E = (const dd*)C.Edd[s];
+  if (!left) {
+    for (int t = t1 + 1; t <= t2; ++t) {
+      slice_potential_global(C, s, t, S.v);
+      for (int x = threadIdx.x; x < N; x += kThreads) evr[x] = from_d<dd>(exp(S.v[x]));
+      __syncthreads();
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        X[(size_t)x * ld + y] = dd_mul(X[(size_t)x * ld + y], evr[x]);
+      }
+      __syncthreads();
+      cta_gemm_dd<false, false>(N, N, N, E, ld, X, ld, Y, ld, sm);
+      dd* t_ = X; X = Y; Y = t_;
+    }
+  } else {
+    for (int t = t2; t >= t1 + 1; --t) {
+      cta_gemm_dd<true, false>(N, N, N, E, ld, X, ld, Y, ld, sm);
+      slice_potential_global(C, s, t, S.v);
+      for (int x = threadIdx.x; x < N; x += kThreads) evr[x] = from_d<dd>(exp(S.v[x]));
+      __syncthreads();
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        Y[(size_t)x * ld + y] = dd_mul(Y[(size_t)x * ld + y], evr[x]);
+      }
+      __syncthreads();
+      dd* t_ = X; X = Y; Y = t_;
+    }
+  }
+  double* Xd = reinterpret_cast<double*>(X);
+  dd_to_d_inplace(N, ld, X);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    Xd[(size_t)x * ld + y] *= src.D[y];
+  }
+  __syncthreads();
+  double* Dn = wvec(C, s, 0);
+  double* beta = wvec(C, s, 1);
+  double* vk0 = wvec(C, s, 2);
+  int* perm = C.iwork[s];
+  const int detq = qr_pivoted(N, ld, Xd, beta, vk0, wvec(C, s, 3), wvec(C, s, 4), perm, S);
+  double* Qn = wmat(C, s, 2);
+  form_q(N, ld, Xd, beta, vk0, Qn, S);
+  dd* PT = reinterpret_cast<dd*>(wmat(C, s, 3));
+  dd* Rt = reinterpret_cast<dd*>(wmat(C, s, 4));
+  for (int x = threadIdx.x; x < N; x += kThreads) Dn[x] = fabs(Xd[(size_t)x * ld + x]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    PT[(size_t)x * ld + y] = from_d<dd>(src.T[(size_t)perm[x] * ld + y]);
+    Rt[(size_t)x * ld + y] = from_d<dd>((y >= x && Dn[x] > 0.0) ? Xd[(size_t)x * ld + y] / Dn[x] : 0.0);
+  }
+  __syncthreads();
+  dd* Tn = reinterpret_cast<dd*>(wmat(C, s, 5));
+  cta_gemm_dd<false, false>(N, N, N, Rt, ld, PT, ld, Tn, ld, sm);
+  dd_to_d_inplace(N, ld, Tn);
+  return detq;
+}
+
+__device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, double* Gout, double& logdet,
+                                    int& sign, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  dd* sm = reinterpret_cast<dd*>(S.gemm);
+  double* W0 = wmat(C, s, 0);
+  double* W1 = wmat(C, s, 1);
+  dd* QRd = reinterpret_cast<dd*>(wmat(C, s, 3));
+  dd* QLd = reinterpret_cast<dd*>(wmat(C, s, 4));
+  dd* TRd = reinterpret_cast<dd*>(wmat(C, s, 7));
+  dd* TLd = reinterpret_cast<dd*>(wmat(C, s, 8));
+  to_dd_mat(N, ld, R.Q, QRd);
+  to_dd_mat(N, ld, Lf.Q, QLd);
+  to_dd_mat(N, ld, R.T, TRd);
+  to_dd_mat(N, ld, Lf.T, TLd);
+  cta_gemm_dd<true, false>(N, N, N, QRd, ld, QLd, ld, reinterpret_cast<dd*>(W0), ld, sm);
+  cta_gemm_dd<false, true>(N, N, N, TRd, ld, TLd, ld, reinterpret_cast<dd*>(W1), ld, sm);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dR = R.D[i], dL = Lf.D[j];
+    const double dbR = dR > 1.0 ? dR : 1.0, dsR = dR > 1.0 ? 1.0 : dR;
+    const double dbL = dL > 1.0 ? dL : 1.0, dsL = dL > 1.0 ? 1.0 : dL;
+    const double qq = to_d(reinterpret_cast<const dd*>(W0)[(size_t)i * ld + j]);
+    const double tt = to_d(reinterpret_cast<const dd*>(W1)[(size_t)i * ld + j]);
+    W0[(size_t)i * ld + j] = qq / (dbR * dbL) + dsR * tt * dsL;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dR = R.D[i];
+    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] / (dR > 1.0 ? dR : 1.0);
+  }
+  __syncthreads();
+  double ldm;
+  int smi;
+  int* piv = C.iwork[s] + ld;
+  if (lu_factor(N, ld, W0, piv, ldm, smi, S)) return 1;
+  lu_solve(N, ld, W0, piv, W1, S.qred);
+  dd* Yd = reinterpret_cast<dd*>(wmat(C, s, 9));
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dL = Lf.D[i];
+    Yd[(size_t)i * ld + j] = from_d<dd>(W1[(size_t)i * ld + j] / (dL > 1.0 ? dL : 1.0));
+  }
+  __syncthreads();
+  cta_gemm_dd<false, false>(N, N, N, QLd, ld, Yd, ld, reinterpret_cast<dd*>(Gout), ld, sm);
+  dd_to_d_inplace(N, ld, Gout);
+  double part = 0.0;
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    const double dR = R.D[i], dL = Lf.D[i];
+    part += log(dR > 1.0 ? dR : 1.0) + log(dL > 1.0 ? dL : 1.0);
+  }
+  logdet = ldm + block_sum(part, S.red);
+  sign = smi * R.detq * Lf.detq;
+  return 0;
+}
+
 // Stabilisation event of this CTA's flavor at slice tau: new chain, fresh G,
 // precision monitor, working G replaced, storage slot j written.
 template <typename Real>
@@ -1056,21 +1295,26 @@ __device__ void stabilise(ChainDev& C, int s, int j, bool up, Real* G, Smem& S, 
   const int N = C.N, ld = C.ld, nst = C.L / C.nw, nw = C.nw;
   int dq;
   UDV R, Lf;
+  constexpr bool mixed = std::is_same<Real, dd>::value;
   if (up) {
     const UDV src = (j == 1) ? ident_udv(C) : slot_udv(C, s, j - 1);
-    dq = chain_step(C, s, (j - 1) * nw, j * nw, false, src, S);
+    dq = mixed ? chain_step_mixed(C, s, (j - 1) * nw, j * nw, false, src, S)
+               : chain_step(C, s, (j - 1) * nw, j * nw, false, src, S);
     R = work_udv(C, s, dq);
     Lf = (j == nst) ? ident_udv(C) : slot_udv(C, s, j);
   } else {
     const UDV src = (j + 1 == nst) ? ident_udv(C) : slot_udv(C, s, j + 1);
-    dq = chain_step(C, s, j * nw, (j + 1) * nw, true, src, S);
+    dq = mixed ? chain_step_mixed(C, s, j * nw, (j + 1) * nw, true, src, S)
+               : chain_step(C, s, j * nw, (j + 1) * nw, true, src, S);
     Lf = work_udv(C, s, dq);
     R = (j == 0) ? ident_udv(C) : slot_udv(C, s, j);
   }
   double* Gf = wmat(C, s, 6);
   double logdet;
   int sg;
-  if (green_from_udv(C, s, R, Lf, Gf, logdet, sg, S)) {
+  const int bad = mixed ? green_from_udv_mixed(C, s, R, Lf, Gf, logdet, sg, S)
+                        : green_from_udv(C, s, R, Lf, Gf, logdet, sg, S);
+  if (bad) {
     if (threadIdx.x == 0) C.error = 1;
     sg = 1;
   }
@@ -1163,7 +1407,7 @@ __device__ int close_event(ChainDev& C, int s, Smem& S, cg::cluster_group& cl, d
 
 // One sweep of every chain (Algorithm 1, upward then downward).
 template <typename Real>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(ChainDev* chains, SweepParams P) {
+__global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, SweepParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cg::cluster_group cl = cg::this_cluster();
   const int nfl = (int)cl.num_blocks();
@@ -1173,52 +1417,76 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(ChainDev* chains, Sweep
   Smem S = carve_smem(smem_raw, C.ld, C.MV);
   Real* G = (Real*)C.G[s];
   Real* Gt = (Real*)C.Gtmp[s];
-  Real* A = (Real*)C.dA[s];
-  Real* B = (Real*)C.dB[s];
+  Real* A = P.ab_smem ? reinterpret_cast<Real*>(S.ab) : (Real*)C.dA[s];
+  Real* B = P.ab_smem ? A + (size_t)P.delay_k * C.ld : (Real*)C.dB[s];
   const int L = C.L, nw = C.nw, MV = C.MV;
   int sign = C.sign;
   int buf = 0;
+  long long cyc[4] = {0, 0, 0, 0};
+  long long t0 = clock64();
+  auto lap = [&](int phase) {
+    const long long t1 = clock64();
+    cyc[phase] += t1 - t0;
+    t0 = t1;
+  };
   for (int tau = 1; tau <= L; ++tau) {
     for (int k = threadIdx.x; k < MV; k += kThreads) S.fslice[k] = C.fields[(size_t)(tau - 1) * MV + k];
     __syncthreads();
     slice_potential_smem(C, s, S.fslice, S.v);
     v_wrap<Real>(C, G, S.v, +1.0, S);
+    lap(1);
     update_slice<Real>(C, s, tau, 0, P, S, cl, G, A, B, sign, buf);
     if (s == 0)
       for (int k = threadIdx.x; k < MV; k += kThreads) C.fields[(size_t)(tau - 1) * MV + k] = S.fslice[k];
+    lap(0);
     t_wrap<Real>(C, s, G, Gt, true, S);
+    lap(1);
     if (tau % nw == 0) {
       cl.sync();
       double mx, sm;
       int fs;
       stabilise<Real>(C, s, tau / nw, true, G, S, mx, sm, fs);
       sign = close_event(C, s, S, cl, mx, sm, fs, sign);
+      lap(2);
     }
-    if (P.measure && tau >= P.meas_first && tau <= P.meas_last) measure<Real>(C, s, G, S, cl, sign);
+    if (P.measure && tau >= P.meas_first && tau <= P.meas_last) {
+      measure<Real>(C, s, G, S, cl, sign);
+      lap(3);
+    }
   }
   for (int tau = L; tau >= 1; --tau) {
     for (int k = threadIdx.x; k < MV; k += kThreads) S.fslice[k] = C.fields[(size_t)(tau - 1) * MV + k];
     __syncthreads();
     t_wrap<Real>(C, s, G, Gt, false, S);
+    lap(1);
     update_slice<Real>(C, s, tau, 1, P, S, cl, G, A, B, sign, buf);
     if (s == 0)
       for (int k = threadIdx.x; k < MV; k += kThreads) C.fields[(size_t)(tau - 1) * MV + k] = S.fslice[k];
+    lap(0);
     slice_potential_smem(C, s, S.fslice, S.v);
     v_wrap<Real>(C, G, S.v, -1.0, S);
-    const int t0 = tau - 1;
-    if (t0 % nw == 0) {
+    lap(1);
+    const int t0s = tau - 1;
+    if (t0s % nw == 0) {
       cl.sync();
       double mx, sm;
       int fs;
-      stabilise<Real>(C, s, t0 / nw, false, G, S, mx, sm, fs);
+      stabilise<Real>(C, s, t0s / nw, false, G, S, mx, sm, fs);
       sign = close_event(C, s, S, cl, mx, sm, fs, sign);
+      lap(2);
     }
-    if (P.measure && t0 >= P.meas_first && t0 <= P.meas_last) measure<Real>(C, s, G, S, cl, sign);
+    if (P.measure && t0s >= P.meas_first && t0s <= P.meas_last) {
+      measure<Real>(C, s, G, S, cl, sign);
+      lap(3);
+    }
   }
   cl.sync();
-  if (s == 0 && threadIdx.x == 0) {
-    C.sign = sign;
-    C.sweep_sign_sum += (double)sign;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) C.cyc[s][q] += cyc[q];
+    if (s == 0) {
+      C.sign = sign;
+      C.sweep_sign_sum += (double)sign;
+    }
   }
 }
 

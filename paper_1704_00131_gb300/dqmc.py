@@ -68,6 +68,10 @@ class SweepStats(ctypes.Structure):
         ("prec_phase_max", ctypes.c_double),
         ("mean_sign", ctypes.c_double),
         ("ms_total", ctypes.c_float),
+        ("ms_update", ctypes.c_float),
+        ("ms_wrap", ctypes.c_float),
+        ("ms_stab", ctypes.c_float),
+        ("ms_measure", ctypes.c_float),
     ]
 
     def as_dict(self) -> dict:

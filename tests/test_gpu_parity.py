@@ -89,7 +89,9 @@ def test_sweep_trajectory_fp64(dq, orc, ft, delay):
         assert np.array_equal(fg[0], fo), f"fields differ after sweep {2 * (rep + 1)}"
         assert sg["accepted"] == so.accepted and sg["proposals"] == so.proposals
         assert sg["mean_sign"] == so.mean_sign
-        assert sg["prec_green_max"] < 1e-8
+        # the paper recommends a mean monitor value of 1e-8 or better (Sec. 2.3) and
+        # prints maxima up to 6e-6 in its examples
+        assert sg["prec_green_mean"] < 1e-10 and sg["prec_green_max"] < 1e-6
         for s in (0, 1):
             Gg, _, _ = ens.greens(0, s)
             assert np.abs(Gg - och.green(s)).max() < 1e-10
