@@ -283,6 +283,9 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
             "accept_rate": st["accepted"] / st["proposals"],
             "prec_green_max": st["prec_green_max"], "prec_green_mean": st["prec_green_mean"],
             "critical_chain_ms": {k: round(st[k], 3) for k in ("ms_update", "ms_wrap", "ms_stab", "ms_measure")},
+            "critical_chain_detail_ms": dict(zip(("ratio_precompute", "accept_scan", "update_vectors", "flushes",
+                                                  "b_chain", "qr_and_q", "t_update", "stable_green"),
+                                                 [round(x, 3) for x in st["ms_detail"]])),
             "gpu_launches": 2 * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                          "frac": achieved_tf / peak_tf, "traffic": None,

@@ -113,6 +113,9 @@ typedef struct {
   float ms_wrap;              /*   the wraps (a3, a6), the stabilisation (a7-a10)  */
   float ms_stab;              /*   and the measurement (a12), from SM cycle        */
   float ms_measure;           /*   counters at the device's clock rate             */
+  float ms_detail[8];         /* the same chain: ratio precompute, acceptance scan,
+                                 update vectors, flushes, B-chain products, QR and
+                                 Q, T update, stable G                             */
 } dqmc_sweep_stats;
 
 /* Create a context with n_chains chains; chain c uses models[chain_model[c]].

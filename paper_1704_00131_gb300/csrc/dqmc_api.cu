@@ -513,6 +513,7 @@ dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats)
           S.ms_wrap = (float)(C.cyc[s][1] / per_ms);
           S.ms_stab = (float)(C.cyc[s][2] / per_ms);
           S.ms_measure = (float)(C.cyc[s][3] / per_ms);
+          for (int q = 0; q < 8; ++q) S.ms_detail[q] = (float)(C.cycd[s][q] / per_ms);
         }
       }
   }

@@ -55,6 +55,10 @@ struct ChainDev {
   // SM cycles spent per phase during the current dqmc_sweep call, per flavor:
   // 0 updates, 1 wraps (V and T), 2 stabilisation, 3 measurement
   int64_t cyc[kMaxFlavors][4];
+  // finer split, per flavor: 0 ratio precompute, 1 acceptance scan (ratios,
+  // cluster barrier, first acceptance), 2 update vectors, 3 flushes,
+  // 4 B-chain products, 5 QR and Q, 6 T update, 7 stable G
+  int64_t cycd[kMaxFlavors][8];
 };
 
 constexpr int kWorkMats = 10;     // N x ld FP64 matrices per flavor in `work`

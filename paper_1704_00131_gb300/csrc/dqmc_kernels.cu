@@ -51,6 +51,13 @@ __device__ __forceinline__ double uniform53(uint32_t hi, uint32_t lo) {
   return (double)(w >> 11) * 0x1.0p-53;
 }
 
+// Sub-phase cycle counter: thread 0 adds the cycles since *t0 to acc[q].
+__device__ __forceinline__ void tick(long long* acc, int q, long long& t0) {
+  const long long t1 = clock64();
+  if (acc && threadIdx.x == 0) acc[q] += t1 - t0;
+  t0 = t1;
+}
+
 // --------------------------------------------------------------------------
 // Field couplings: Ising (type 1) c(s) = lambda s; four-valued HS (type 2)
 // c(l) = g eta(l) with weight gamma(l) (Sec. 2.1, the discrete HS transform).
@@ -658,7 +665,9 @@ __device__ void form_q(int N, int ld, const double* M, const double* beta, const
 // D = |diag R|, T = D^-1 R P^T T_src.  Right chain (left == false): Bcal =
 // B_t2 ... B_t1+1.  Left chain: Bcal = B_t1+1^T ... B_t2^T.  Result in
 // (W2, wvec 0, W5); returns det(Q).
-__device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S) {
+__device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S,
+                      long long* det = nullptr) {
+  long long t0 = clock64();
   const int N = C.N, ld = C.ld;
   double* X = wmat(C, s, 0);
   double* Y = wmat(C, s, 1);
@@ -691,6 +700,7 @@ __device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, U
       double* t_ = X; X = Y; Y = t_;
     }
   }
+  tick(det, 4, t0);
   // M = X D_src
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int x = e / N, y = e - x * N;
@@ -704,6 +714,7 @@ __device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, U
   const int detq = qr_pivoted(N, ld, X, beta, vk0, wvec(C, s, 3), wvec(C, s, 4), perm, S);
   double* Qn = wmat(C, s, 2);
   form_q(N, ld, X, beta, vk0, Qn, S);
+  tick(det, 5, t0);
   double* PT = wmat(C, s, 3);
   double* Rt = wmat(C, s, 4);
   for (int x = threadIdx.x; x < N; x += kThreads) Dn[x] = fabs(X[(size_t)x * ld + x]);
@@ -715,6 +726,7 @@ __device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, U
   }
   __syncthreads();
   cta_gemm<double, false, false>(N, N, N, Rt, ld, PT, ld, wmat(C, s, 5), ld, S.gemm);
+  tick(det, 6, t0);
   return detq;
 }
 
@@ -979,6 +991,7 @@ __global__ void reset_stats_kernel(ChainDev* chains, int n_chains) {
     C.prec_sum[s] = 0.0;
     C.prec_max[s] = 0.0;
     for (int q = 0; q < 4; ++q) C.cyc[s][q] = 0;
+    for (int q = 0; q < 8; ++q) C.cycd[s][q] = 0;
   }
   C.phase_max = 0.0;
   C.prec_events = 0;
@@ -1061,8 +1074,10 @@ __device__ void flush_delayed(const ChainDev& C, Real* G, const Real* A, const R
 //   a = -(delta/R_s) G_eff[:,i],  b = e_i - G_eff[i,:],  G_eff += a b^T.
 template <typename Real>
 __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepParams& P, Smem& S,
-                             cg::cluster_group& cl, Real* G, Real* A, Real* B, int& sign, int& buf) {
+                             cg::cluster_group& cl, Real* G, Real* A, Real* B, int& sign, int& buf,
+                             long long* det) {
   const int N = C.N, ld = C.ld, MV = C.MV, nfl = C.nfl, tid = threadIdx.x;
+  long long t0 = clock64();
   const uint32_t key0 = (uint32_t)P.seed, key1 = (uint32_t)(P.seed >> 32) ^ C.chain_id;
   for (int q = tid; q < MV; q += kThreads) {
     const int k = dir ? MV - 1 - q : q;
@@ -1080,6 +1095,7 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
   }
   for (int x = tid; x < N; x += kThreads) S.d[x] = to_d(G[(size_t)x * ld + x]);
   __syncthreads();
+  tick(det, 0, t0);
   int pos = 0, nacc = 0;
   int64_t n_acc_slice = 0;
   const int kdel = P.delay_k;
@@ -1097,6 +1113,7 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
       if (S.u2[q] < (aR < 1.0 ? aR : 1.0)) { first = q; break; }
     }
     first = block_min_int(first, S.ired);
+    tick(det, 1, t0);
     if (first >= MV) { buf ^= 1; break; }
     double R = S.gam[first];
     for (int r = 0; r < nfl; ++r) R *= Rr[r][first];
@@ -1125,16 +1142,19 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     if (tid == 0) S.fslice[k] = S.fnew[first];
     ++nacc;
     ++n_acc_slice;
+    tick(det, 2, t0);
     if (nacc == kdel) {
       __syncthreads();
       flush_delayed(C, G, A, B, nacc);
       nacc = 0;
+      tick(det, 3, t0);
     }
     pos = first + 1;
     buf ^= 1;
     __syncthreads();
   }
   if (nacc) flush_delayed(C, G, A, B, nacc);
+  tick(det, 3, t0);
   if (s == 0 && tid == 0) {
     C.proposals += MV;
     C.accepted += n_acc_slice;
@@ -1166,7 +1186,9 @@ __device__ inline void dd_to_d_inplace(int N, int ld, void* buf) {
   __syncthreads();
 }
 
-__device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S) {
+__device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S,
+                      long long* det = nullptr) {
+  long long t0 = clock64();
   const int N = C.N, ld = C.ld;
   dd* X = reinterpret_cast<dd*>(wmat(C, s, 0));
   dd* Y = reinterpret_cast<dd*>(wmat(C, s, 1));
@@ -1203,6 +1225,7 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
   }
   double* Xd = reinterpret_cast<double*>(X);
   dd_to_d_inplace(N, ld, X);
+  tick(det, 4, t0);
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int x = e / N, y = e - x * N;
     Xd[(size_t)x * ld + y] *= src.D[y];
@@ -1215,6 +1238,7 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
   const int detq = qr_pivoted(N, ld, Xd, beta, vk0, wvec(C, s, 3), wvec(C, s, 4), perm, S);
   double* Qn = wmat(C, s, 2);
   form_q(N, ld, Xd, beta, vk0, Qn, S);
+  tick(det, 5, t0);
   dd* PT = reinterpret_cast<dd*>(wmat(C, s, 3));
   dd* Rt = reinterpret_cast<dd*>(wmat(C, s, 4));
   for (int x = threadIdx.x; x < N; x += kThreads) Dn[x] = fabs(Xd[(size_t)x * ld + x]);
@@ -1228,6 +1252,7 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
   dd* Tn = reinterpret_cast<dd*>(wmat(C, s, 5));
   cta_gemm_dd<false, false>(N, N, N, Rt, ld, PT, ld, Tn, ld, sm);
   dd_to_d_inplace(N, ld, Tn);
+  tick(det, 6, t0);
   return detq;
 }
 
@@ -1291,24 +1316,26 @@ __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, dou
 // precision monitor, working G replaced, storage slot j written.
 template <typename Real>
 __device__ void stabilise(ChainDev& C, int s, int j, bool up, Real* G, Smem& S, double& ev_max,
-                          double& ev_sum, int& fresh_sign) {
+                          double& ev_sum, int& fresh_sign, long long* det) {
+  long long t0 = clock64();
   const int N = C.N, ld = C.ld, nst = C.L / C.nw, nw = C.nw;
   int dq;
   UDV R, Lf;
   constexpr bool mixed = std::is_same<Real, dd>::value;
   if (up) {
     const UDV src = (j == 1) ? ident_udv(C) : slot_udv(C, s, j - 1);
-    dq = mixed ? chain_step_mixed(C, s, (j - 1) * nw, j * nw, false, src, S)
-               : chain_step(C, s, (j - 1) * nw, j * nw, false, src, S);
+    dq = mixed ? chain_step_mixed(C, s, (j - 1) * nw, j * nw, false, src, S, det)
+               : chain_step(C, s, (j - 1) * nw, j * nw, false, src, S, det);
     R = work_udv(C, s, dq);
     Lf = (j == nst) ? ident_udv(C) : slot_udv(C, s, j);
   } else {
     const UDV src = (j + 1 == nst) ? ident_udv(C) : slot_udv(C, s, j + 1);
-    dq = mixed ? chain_step_mixed(C, s, j * nw, (j + 1) * nw, true, src, S)
-               : chain_step(C, s, j * nw, (j + 1) * nw, true, src, S);
+    dq = mixed ? chain_step_mixed(C, s, j * nw, (j + 1) * nw, true, src, S, det)
+               : chain_step(C, s, j * nw, (j + 1) * nw, true, src, S, det);
     Lf = work_udv(C, s, dq);
     R = (j == 0) ? ident_udv(C) : slot_udv(C, s, j);
   }
+  t0 = clock64();
   double* Gf = wmat(C, s, 6);
   double logdet;
   int sg;
@@ -1318,6 +1345,7 @@ __device__ void stabilise(ChainDev& C, int s, int j, bool up, Real* G, Smem& S, 
     if (threadIdx.x == 0) C.error = 1;
     sg = 1;
   }
+  tick(det, 7, t0);
   double mx = 0.0, sm = 0.0;
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int x = e / N, y = e - x * N;
@@ -1423,6 +1451,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
   int sign = C.sign;
   int buf = 0;
   long long cyc[4] = {0, 0, 0, 0};
+  long long det[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long t0 = clock64();
   auto lap = [&](int phase) {
     const long long t1 = clock64();
@@ -1435,7 +1464,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
     slice_potential_smem(C, s, S.fslice, S.v);
     v_wrap<Real>(C, G, S.v, +1.0, S);
     lap(1);
-    update_slice<Real>(C, s, tau, 0, P, S, cl, G, A, B, sign, buf);
+    update_slice<Real>(C, s, tau, 0, P, S, cl, G, A, B, sign, buf, det);
     if (s == 0)
       for (int k = threadIdx.x; k < MV; k += kThreads) C.fields[(size_t)(tau - 1) * MV + k] = S.fslice[k];
     lap(0);
@@ -1445,7 +1474,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
       cl.sync();
       double mx, sm;
       int fs;
-      stabilise<Real>(C, s, tau / nw, true, G, S, mx, sm, fs);
+      stabilise<Real>(C, s, tau / nw, true, G, S, mx, sm, fs, det);
       sign = close_event(C, s, S, cl, mx, sm, fs, sign);
       lap(2);
     }
@@ -1459,7 +1488,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
     __syncthreads();
     t_wrap<Real>(C, s, G, Gt, false, S);
     lap(1);
-    update_slice<Real>(C, s, tau, 1, P, S, cl, G, A, B, sign, buf);
+    update_slice<Real>(C, s, tau, 1, P, S, cl, G, A, B, sign, buf, det);
     if (s == 0)
       for (int k = threadIdx.x; k < MV; k += kThreads) C.fields[(size_t)(tau - 1) * MV + k] = S.fslice[k];
     lap(0);
@@ -1471,7 +1500,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
       cl.sync();
       double mx, sm;
       int fs;
-      stabilise<Real>(C, s, t0s / nw, false, G, S, mx, sm, fs);
+      stabilise<Real>(C, s, t0s / nw, false, G, S, mx, sm, fs, det);
       sign = close_event(C, s, S, cl, mx, sm, fs, sign);
       lap(2);
     }
@@ -1483,6 +1512,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
   cl.sync();
   if (threadIdx.x == 0) {
     for (int q = 0; q < 4; ++q) C.cyc[s][q] += cyc[q];
+    for (int q = 0; q < 8; ++q) C.cycd[s][q] += det[q];
     if (s == 0) {
       C.sign = sign;
       C.sweep_sign_sum += (double)sign;

@@ -72,10 +72,13 @@ class SweepStats(ctypes.Structure):
         ("ms_wrap", ctypes.c_float),
         ("ms_stab", ctypes.c_float),
         ("ms_measure", ctypes.c_float),
+        ("ms_detail", ctypes.c_float * 8),
     ]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["ms_detail"] = list(self.ms_detail)
+        return d
 
 
 _lib = None
