@@ -6,7 +6,7 @@ Default workload: 256 independent chains of the square-lattice Hubbard model,
 half 8x8 (N = 64) and half 12x12 (N = 144), beta = 4 or 8 (dtau = 0.1), U in
 {2, 4, 6}, spin-z Ising decoupling, n_wrap = 10; fields drawn from Philox.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64|fp32]
     python bench.py --impl reference     # the FP64 CPU oracle on the host cores
 
 Multi-GPU (torchrun): every rank runs its own batch of chains (independent
@@ -42,9 +42,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c5"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--chains", type=int, default=0, help="override the number of chains (c3/c5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 path")
+    ap.add_argument("--peaks", action="store_true", help="measure the matmul peaks used as roofline denominators")
+    ap.add_argument("--no-oracle-check", action="store_true", help="skip the max|dG| check against the oracle")
     return ap.parse_args()
 
 
@@ -197,27 +200,26 @@ def run_reference(args, wl: W.Workload, rank: int):
 
 
 # ---------------------------------------------------------------------- ours
-def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
+FP64_PEAK_TF = 1.0994   # cuBLAS DGEMM measured on this GB300 (profiles/peaks_gb300_measured.md)
+FP32_PEAK_TF = 69.83    # cuBLAS SGEMM (FP32 SIMT) measured on the same part
+# one double-word (float pair) multiply-add costs 12 FP32-pipe operations
+DW_PEAK_TF = FP32_PEAK_TF / 12.0 * 1.0
+
+
+def time_path(wl, precision, args, stream, seed, world, local_rank):
+    """Warm up, then time args.steps sweeps of every chain with CUDA events."""
     import torch
 
-    from paper_1704_00131_gb300 import build_ext, dqmc
-
-    build_ext.build()
-    torch.cuda.set_device(local_rank)
-    stream = torch.cuda.current_stream()
-    seed = W.BASE_SEED + rank
-    ens = dqmc.Ensemble(wl.models, wl.chain_model, precision=args.precision, delay_k=wl.delay_k, seed=seed,
+    from paper_1704_00131_gb300 import dqmc
+    ens = dqmc.Ensemble(wl.models, wl.chain_model, precision=precision, delay_k=wl.delay_k, seed=seed,
                         stream=stream)
-    # warm-up (untimed) and a stats sweep for the acceptance and precision figures
     ens.sweep(max(args.warmup - 1, 0), stats=False)
     st = ens.sweep(1)
     acc_per_chain = st["accepted"] / wl.n_chains
     flops_per_step = sum(chain_cost(wl.models[m], acc_per_chain) for m in wl.chain_model)
-    dist = None
+    torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
-    torch.cuda.synchronize()
-    if dist:
         dist.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local_rank) as clk:
@@ -232,26 +234,94 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
     ms_total = t_start.elapsed_time(t_end)
     per_launch_ms = [a.elapsed_time(b) for a, b in ev]
-    if dist:
+    if world > 1:
+        import torch.distributed as dist
         t = torch.tensor([ms_total], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = float(t.item())
         dist.barrier()
     ms_step = ms_total / args.steps
+    value = wl.proposals_per_sweep() * world / (ms_step / 1000.0)
+    avg_launch_s = statistics.mean(per_launch_ms) / 1000.0
+    achieved = flops_per_step / avg_launch_s / 1e12
+    if precision == "fp64":
+        peak, src, kern = FP64_PEAK_TF, "measured cuBLAS DGEMM on this GB300 (FP64 pipe)", "sweep_kernel<double>"
+    elif precision == "fp32":
+        peak, src, kern = FP32_PEAK_TF, "measured cuBLAS SGEMM on this GB300 (FP32 SIMT)", "sweep_kernel<float>"
+    else:
+        peak, src, kern = DW_PEAK_TF, ("double-word arithmetic on the FP32 pipes: measured SGEMM rate / 12 "
+                                       "FP32 operations per float-pair multiply-add (the FP64 share of the "
+                                       "stabilisation runs at the 1.10 TFLOP/s FP64 rate)"), "sweep_kernel<dd>"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kern, "peak_source": src}
+    return {"ens": ens, "st": st, "ms_step": ms_step, "value": value, "roofline": roof, "clocks": clk.summary(),
+            "algorithmic_tflop_per_step": flops_per_step / 1e12}
+
+
+def oracle_dg(wl, ens, n_threads):
+    """max |G_GPU(0) - G_oracle(0)| on the GPU's current fields, one chain per model
+    class of the workload (flavor up), computed by the FP64 oracle on the host."""
+    import oracle
+    oracle.build()
+    fields, _ = ens.get_fields()
+    picks = {}
+    for c, mi in enumerate(wl.chain_model):
+        picks.setdefault(int(mi), c)
+    jobs = []
+    for mi, c in sorted(picks.items()):
+        m = wl.models[mi]
+        om = oracle.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+        jobs.append((om, fields[c], c))
+    res = [None] * len(jobs)
+
+    def work(i):
+        om, f, c = jobs[i]
+        Go, _, _ = oracle.green_udv(om, f, 0, 0)
+        res[i] = Go
+
+    ths = []
+    for i in range(len(jobs)):
+        t = threading.Thread(target=work, args=(i,))
+        t.start()
+        ths.append(t)
+        if len(ths) >= n_threads:
+            for t in ths:
+                t.join()
+            ths = []
+    for t in ths:
+        t.join()
+    worst = 0.0
+    for i, (_, _, c) in enumerate(jobs):
+        Gg, _, _ = ens.greens(c, 0)
+        worst = max(worst, float(np.abs(Gg - res[i]).max()))
+    return worst, len(jobs)
+
+
+def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_1704_00131_gb300 import build_ext
+
+    build_ext.build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    seed = W.BASE_SEED + rank
+    main_prec = args.precision
+    r = time_path(wl, main_prec, args, stream, seed, world, local_rank)
+    ens, st = r["ens"], r["st"]
     props_step = wl.proposals_per_sweep()
-    value = props_step * world / (ms_step / 1000.0)
     # end to end through the public API with host buffers: fields in (pinned host),
     # one sweep, fields and measurements out, every step
     fields, ctr = ens.get_fields()
     flat = np.concatenate([f.ravel() for f in fields])
     pinned = torch.from_numpy(flat).pin_memory()
     h2d = int(pinned.numel())
+    offs = np.cumsum([0] + [f.size for f in fields])
     torch.cuda.synchronize()
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         host_fields = np.asarray(pinned.numpy())
-        offs = np.cumsum([0] + [f.size for f in fields])
         ens.set_fields([host_fields[offs[c]:offs[c + 1]] for c in range(len(fields))], ctr)
         ens.sweep(1, stats=False)
         fields, ctr = ens.get_fields()
@@ -260,48 +330,56 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     d2h = int(sum(f.size for f in fields) + sum(a.nbytes for a in meas))
     e2e_value = props_step * world / e2e_s
-    # roofline of the dominant kernel (the sweep kernel: one launch per step)
-    avg_launch_s = statistics.mean(per_launch_ms) / 1000.0
-    achieved_tf = flops_per_step / avg_launch_s / 1e12
-    peak_tf = 1.0994 if args.precision == "fp64" else 69.83
+    dg = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and not args.no_oracle_check:
+        worst, n = oracle_dg(wl, ens, cores)
+        dg = {"max_abs_dG_vs_oracle": worst, "chains_checked": n,
+              "what": "working G(0) after the timed sweeps vs the FP64 oracle's G(0) on the same fields"}
+    ens.close()
+    fp64 = None
+    if main_prec != "fp64" and not args.no_fp64_compare:
+        rf = time_path(wl, "fp64", args, stream, seed, world, local_rank)
+        rf["ens"].close()
+        fp64 = {"value": rf["value"], "unit": UNIT, "ms_per_step": rf["ms_step"], "roofline": rf["roofline"],
+                "critical_chain_ms": {k: round(rf["st"][k], 3) for k in ("ms_update", "ms_wrap", "ms_stab")},
+                "prec_green_max": rf["st"]["prec_green_max"], "prec_green_mean": rf["st"]["prec_green_mean"]}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cores = os.cpu_count() or 1
         p, dt, desc = oracle_sample(wl, cores, max(1, cores // len(set(wl.chain_model.tolist()))))
         cpu = {"value": p / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "mixed": "f32x2+f64"}[main_prec],
             "data": "synthetic (seeded Philox fields, random-init Markov chains)",
-            "config": {"workload": wl.name, "chains": wl.n_chains, "precision": args.precision,
+            "config": {"workload": wl.name, "chains": wl.n_chains, "precision": main_prec,
                        "delay_k": wl.delay_k, "n_wrap": 10,
                        "l2": "resident state > L2 (per-chain G, UDV storage and workspace, "
-                             f"{ens_bytes(wl, args.precision) / 1e9:.2f} GB); no flush"},
-            "sweeps_per_s": 1000.0 / ms_step * world,
+                             f"{ens_bytes(wl, main_prec) / 1e9:.2f} GB); no flush"},
+            "sweeps_per_s": 1000.0 / r["ms_step"] * world,
             "accept_rate": st["accepted"] / st["proposals"],
+            "accuracy": dg,
             "prec_green_max": st["prec_green_max"], "prec_green_mean": st["prec_green_mean"],
             "critical_chain_ms": {k: round(st[k], 3) for k in ("ms_update", "ms_wrap", "ms_stab", "ms_measure")},
             "critical_chain_detail_ms": dict(zip(("ratio_precompute", "accept_scan", "update_vectors", "flushes",
                                                   "b_chain", "qr_and_q", "t_update", "stable_green"),
                                                  [round(x, 3) for x in st["ms_detail"]])),
+            "algorithmic_tflop_per_step": r["algorithmic_tflop_per_step"],
             "gpu_launches": 2 * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                         "frac": achieved_tf / peak_tf, "traffic": None,
-                         "kernel": f"sweep_kernel<{'double' if args.precision == 'fp64' else 'float'}>",
-                         "peak_source": "measured cuBLAS DGEMM on this GB300 (FP64 pipe)" if args.precision == "fp64"
-                         else "measured cuBLAS SGEMM on this GB300 (FP32 SIMT)"},
+            "roofline": r["roofline"],
+            "fp64_path": fp64,
+            "speedup_vs_fp64_path": (r["value"] / fp64["value"]) if fp64 else None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "clocks": clk.summary(),
+            "clocks": r["clocks"],
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    ens.close()
 
 
 def ens_bytes(wl: W.Workload, precision: str) -> float:
-    rs = 8 if precision == "fp64" else 4
+    rs = 4 if precision == "fp32" else 8
     tot = 0
     for m in wl.chain_model:
         mm = wl.models[m]
@@ -312,8 +390,39 @@ def ens_bytes(wl: W.Workload, precision: str) -> float:
     return float(tot)
 
 
+def measure_peaks():
+    """cuBLAS matmul rates (torch) of this GPU: the roofline denominators."""
+    import torch
+    res = {}
+
+    def rate(dtype, n, tf32=False, iters=10):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(3):
+            a @ b
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(iters):
+            a @ b
+        s1.record()
+        torch.cuda.synchronize()
+        return 2 * n ** 3 / (s0.elapsed_time(s1) / iters * 1e-3) / 1e12
+
+    res["fp64_tflops"] = rate(torch.float64, 8192, iters=5)
+    res["fp32_simt_tflops"] = rate(torch.float32, 8192)
+    res["tf32_tflops"] = rate(torch.float32, 8192, tf32=True)
+    res["bf16_tflops"] = rate(torch.bfloat16, 8192)
+    res["device"] = torch.cuda.get_device_name(0)
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
+    if args.peaks:
+        measure_peaks()
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
