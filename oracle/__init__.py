@@ -94,6 +94,8 @@ def lib():
         _lib.orc_chain_fields.argtypes = [vp, vp, vp, vp]
         _lib.orc_chain_measure.argtypes = [vp, vp, vp, vp]
         _lib.orc_logdet_grad.argtypes = [vp, vp, vp, vp, vp, vp]
+        _lib.orc_green_displaced.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+        _lib.orc_energy_grad.argtypes = [vp, vp, vp, vp, vp]
         del i32
     return _lib
 
@@ -285,3 +287,22 @@ def logdet_grad(model: Model, fields: np.ndarray):
     gU = np.zeros(nfl)
     _check(lib().orc_logdet_grad(model.cref(), _ptr(f), _ptr(ld), _ptr(sg), _ptr(gK), _ptr(gU)), "logdet_grad")
     return ld, sg, gK, gU
+
+
+def green_displaced(model: Model, fields: np.ndarray, flavor: int, tau: int):
+    """G(tau,0) and G(0,tau) through the UDV chains."""
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    Gt0 = np.zeros((model.N, model.N))
+    G0t = np.zeros((model.N, model.N))
+    _check(lib().orc_green_displaced(model.cref(), _ptr(f), flavor, tau, _ptr(Gt0), _ptr(G0t)), "green_displaced")
+    return Gt0, G0t
+
+
+def energy_grad(model: Model, fields: np.ndarray):
+    """(Kin, Pot, Part, Ener) at G(0), dEner/dK^s (symmetric pairs) and dEner/dU."""
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    e = np.zeros(4)
+    gK = np.zeros((model.n_flavors, model.N, model.N))
+    gU = np.zeros(1)
+    _check(lib().orc_energy_grad(model.cref(), _ptr(f), _ptr(e), _ptr(gK), _ptr(gU)), "energy_grad")
+    return e, gK, float(gU[0])

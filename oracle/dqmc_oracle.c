@@ -1018,3 +1018,196 @@ done:
   model_free(&M);
   return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Time-displaced Green functions on fixed fields (the equal-time G of Eq.   */
+/* Green_eq extended to two times, Sec. 2.1 Observables):                    */
+/*   G(tau,0) = B(tau,0) G(0) = (B(tau,0)^-1 + B(beta,tau))^-1                */
+/*   G(0,tau) = -(1 - G(0)) B(tau,0)^-1 = -(B(tau,0) + B(beta,tau)^-1)^-1     */
+/* From the two UDV chains, with the same middle matrix as the stable G:     */
+/*   G(tau,0) = Q_L Db_L^-1 Mid^-1 Ds_R T_R                                   */
+/*   G(0,tau) = -T_L^T Ds_L Mid^-1 Db_R^-1 Q_R^T                              */
+/* ------------------------------------------------------------------------ */
+static int displaced_from_udv(int N, const udv_t* R, const udv_t* Lf, double* Gt0, double* G0t) {
+  double* QRt = dalloc((size_t)N * N);
+  double* Mid = dalloc((size_t)N * N);
+  double* TLt = dalloc((size_t)N * N);
+  double* TT = dalloc((size_t)N * N);
+  double* MI = dalloc((size_t)N * N);
+  double* X = dalloc((size_t)N * N);
+  mat_transpose(N, R->Q, QRt);
+  mat_mul(N, QRt, Lf->Q, Mid);
+  mat_transpose(N, Lf->T, TLt);
+  mat_mul(N, R->T, TLt, TT);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      const double dR = R->D[i], dL = Lf->D[j];
+      const double dbR = dR > 1.0 ? dR : 1.0, dsR = dR > 1.0 ? 1.0 : dR;
+      const double dbL = dL > 1.0 ? dL : 1.0, dsL = dL > 1.0 ? 1.0 : dL;
+      Mid[i * N + j] = Mid[i * N + j] / (dbR * dbL) + dsR * TT[i * N + j] * dsL;
+    }
+  int* piv = (int*)calloc(N, sizeof(int));
+  double ld;
+  int sg;
+  int st = lu_factor(N, Mid, piv, &ld, &sg);
+  if (!st) {
+    mat_identity(N, MI);
+    lu_solve(N, Mid, piv, MI); /* Mid^-1 */
+    /* G(tau,0) = Q_L Db_L^-1 MI Ds_R T_R */
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        const double dL = Lf->D[i];
+        X[i * N + j] = MI[i * N + j] / (dL > 1.0 ? dL : 1.0);
+      }
+    mat_mul(N, Lf->Q, X, X);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < N; ++k) {
+          const double dR = R->D[k];
+          acc += X[i * N + k] * (dR > 1.0 ? 1.0 : dR) * R->T[k * N + j];
+        }
+        Gt0[i * N + j] = acc;
+      }
+    /* G(0,tau) = -T_L^T Ds_L MI Db_R^-1 Q_R^T */
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        const double dL = Lf->D[i];
+        X[i * N + j] = (dL > 1.0 ? 1.0 : dL) * MI[i * N + j];
+      }
+    mat_mul(N, TLt, X, X);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < N; ++k) {
+          const double dR = R->D[k];
+          acc += X[i * N + k] / (dR > 1.0 ? dR : 1.0) * QRt[k * N + j];
+        }
+        G0t[i * N + j] = -acc;
+      }
+  }
+  free(QRt); free(Mid); free(TLt); free(TT); free(MI); free(X); free(piv);
+  return st;
+}
+
+int orc_green_displaced(const orc_model* m, const int8_t* fields, int s, int tau, double* Gt0, double* G0t) {
+  model_t M;
+  int st = model_load(m, &M);
+  if (st) return st;
+  if (s < 0 || s >= M.nfl || tau < 0 || tau > M.L) { model_free(&M); return ORC_EINVAL; }
+  const int N = M.N, nw = M.nw;
+  udv_t R, Lf;
+  udv_alloc(N, &R); udv_alloc(N, &Lf);
+  udv_identity(N, &R); udv_identity(N, &Lf);
+  for (int t = 0; t < tau; t += nw) udv_right_step(&M, fields, s, t, (t + nw < tau) ? t + nw : tau, &R);
+  for (int t = M.L; t > tau; t -= nw) udv_left_step(&M, fields, s, (t - nw > tau) ? t - nw : tau, t, &Lf);
+  st = displaced_from_udv(N, &R, &Lf, Gt0, G0t);
+  udv_free(&R); udv_free(&Lf);
+  model_free(&M);
+  return st;
+}
+
+/* Derivative of the energy estimator E(G(0)) (the U n_up n_dn form above) on
+ * fixed fields.  With Gamma^s = dE/dG^s = -(K^s)^T - diag(U (1 - G^sbar_ii)):
+ *   dE = (explicit terms at fixed G) + sum_s Tr[Gamma^s^T dG^s],
+ *   dG = -G dB(beta,0) G,  dB(beta,0) = sum_tau B(beta,tau) dB_tau B(tau-1,0),
+ *   and B(tau-1,0) G = G(tau-1,0), G B(beta,tau) = -G(0,tau), so
+ *   sum_s Tr[Gamma^T dG] = sum_s sum_tau Tr[Z_tau dB_tau],
+ *   Z_tau = G(tau-1,0) Gamma^T G(0,tau),  dB_tau = dE e^{V} + E e^{V} dV.
+ * Hopping part: Tr[e^{V} Z dE] through the Frechet derivative of exp(-dtau K)
+ * (divided differences); coupling part: sum_i (Z E e^{V})_ii dv_i/dU.
+ * energy_out = (Kin, Pot, Part, Ener) at G(0); grad_K[s] = dEner/dK^s with
+ * K_xy and K_yx varied together (x != y); grad_U = dEner/dU. */
+int orc_energy_grad(const orc_model* m, const int8_t* fields, double* energy_out, double* grad_K,
+                    double* grad_U) {
+  model_t M;
+  int st = model_load(m, &M);
+  if (st) return st;
+  const int N = M.N, L = M.L, nfl = M.nfl;
+  const size_t nn = (size_t)N * N;
+  double* G0[2] = {dalloc(nn), dalloc(nn)};
+  for (int s = 0; s < nfl; ++s) {
+    double ld;
+    int sg;
+    st = orc_green_udv(m, fields, s, 0, G0[s], &ld, &sg);
+    if (st) goto out;
+  }
+  energy_terms(&M, G0, energy_out);
+  {
+    double gu = 0.0;
+    if (nfl == 2)
+      for (int i = 0; i < N; ++i) gu += (1.0 - G0[0][i * N + i]) * (1.0 - G0[1][i * N + i]);
+    double* Gam = dalloc(nn);
+    double* Gt0 = dalloc(nn);
+    double* G0t = dalloc(nn);
+    double* Z = dalloc(nn);
+    double* SE = dalloc(nn);
+    double* T1 = dalloc(nn);
+    double* v = dalloc(N);
+    double* w = dalloc(N);
+    double* V = dalloc(nn);
+    for (int s = 0; s < nfl; ++s) {
+      const double* K = M.K + s * nn;
+      const double* E = M.E + s * nn;
+      /* Gamma^T */
+      for (int x = 0; x < N; ++x)
+        for (int y = 0; y < N; ++y) {
+          double g = -K[x * N + y]; /* (Gamma^T)_xy = Gamma_yx = -K_xy */
+          if (x == y && nfl == 2) g -= M.U * (1.0 - G0[1 - s][x * N + x]);
+          Gam[x * N + y] = g;
+        }
+      memset(SE, 0, sizeof(double) * nn);
+      for (int tau = 1; tau <= L; ++tau) {
+        st = orc_green_displaced(m, fields, s, tau - 1, Gt0, T1); /* G(tau-1,0); T1 unused */
+        if (st) break;
+        st = orc_green_displaced(m, fields, s, tau, T1, G0t);     /* G(0,tau);   T1 unused */
+        if (st) break;
+        mat_mul(N, Gt0, Gam, T1);  /* G(tau-1,0) Gamma^T */
+        mat_mul(N, T1, G0t, Z);    /* Z_tau */
+        slice_potential(&M, fields, s, tau, v);
+        for (int x = 0; x < N; ++x)
+          for (int y = 0; y < N; ++y) SE[x * N + y] += exp(v[x]) * Z[x * N + y];
+        /* (Z E e^V)_ii dv_i/dU */
+        for (int k = 0; k < M.MV; ++k) {
+          const int i = M.site[k];
+          double acc = 0.0;
+          for (int q = 0; q < N; ++q) acc += Z[i * N + q] * E[q * N + i];
+          acc *= exp(v[i]);
+          gu += acc * M.sgn[s * M.MV + k] *
+                field_coupling_dU(M.ft, M.dtau, M.U, fields[(tau - 1) * M.MV + k]);
+        }
+      }
+      if (st) break;
+      /* hopping: Tr[SE dE] -> V [F o (V^T SE^T V)] V^T, plus the explicit delta - G^T */
+      orc_eig_sym(N, K, w, V);
+      double* A = T1;
+      mat_transpose(N, SE, A);         /* SE^T */
+      mat_mul(N, A, V, Z);             /* SE^T V */
+      mat_transpose(N, V, A);          /* V^T */
+      mat_mul(N, A, Z, Z);             /* V^T SE^T V */
+      for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+          const double x = 0.5 * M.dtau * (w[a] - w[b]);
+          const double shc = (x == 0.0) ? 1.0 : sinh(x) / x;
+          Z[a * N + b] *= -M.dtau * exp(-0.5 * M.dtau * (w[a] + w[b])) * shc;
+        }
+      mat_mul(N, V, Z, Z);
+      mat_mul(N, Z, A, Z);             /* V Z V^T: d/dK_xy of the implicit part */
+      double* g = grad_K + s * nn;
+      for (int x = 0; x < N; ++x)
+        for (int y = 0; y < N; ++y) {
+          /* explicit: d Kin / dK_xy = delta_xy - G_yx */
+          const double ex = ((x == y) ? 1.0 : 0.0) - G0[s][y * N + x];
+          const double exT = ((x == y) ? 1.0 : 0.0) - G0[s][x * N + y];
+          if (x == y) g[x * N + y] = Z[x * N + y] + ex;
+          else g[x * N + y] = Z[x * N + y] + Z[y * N + x] + ex + exT;
+        }
+    }
+    *grad_U = gu;
+    free(Gam); free(Gt0); free(G0t); free(Z); free(SE); free(T1); free(v); free(w); free(V);
+  }
+out:
+  free(G0[0]); free(G0[1]);
+  model_free(&M);
+  return st;
+}

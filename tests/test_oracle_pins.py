@@ -423,3 +423,52 @@ def test_sampler_reproduces_exact_energies(orc, ft):
     mp, ep = jackknife(bins_p)
     assert abs(mk - kin_ed) < 3 * ek + 1e-12, (mk, ek, kin_ed)
     assert abs(mp - pot_ed) < 3 * ep + 1e-12, (mp, ep, pot_ed)
+
+
+# ----------------------------------------------------------- energy adjoint
+def test_displaced_green_against_plain_products(orc):
+    """G(tau,0) = B(tau,0) G(0) and G(0,tau) = -(1 - G(0)) B(tau,0)^-1 by plain products
+    at small beta, against the UDV-chain formulas."""
+    K = W.square_lattice(2, 3, 1.0, 0.0, 0.2)
+    N, L, dtau, U = 6, 8, 0.1, 3.0
+    m = make_model(orc, K, U, dtau, L, 4)
+    f = W.random_fields(1, L, N, seed=31)
+    E = expm(-dtau * K)
+    lam = orc.ising_lambda(dtau, U)
+    for s, sig in ((0, 1.0), (1, -1.0)):
+        G0, _, _ = orc.green_plain(m, f, s, 0)
+        for tau in (0, 3, 4, 8):
+            B = np.eye(N)
+            for t in range(1, tau + 1):
+                B = E @ np.diag(np.exp(sig * lam * f[t - 1])) @ B
+            Gt0, G0t = orc.green_displaced(m, f, s, tau)
+            assert np.allclose(Gt0, B @ G0, atol=1e-12)
+            assert np.allclose(G0t, -(np.eye(N) - G0) @ np.linalg.inv(B), atol=1e-12)
+
+
+def test_energy_gradient_finite_differences(orc):
+    K = W.square_lattice(3, 2, t=1.0, tp=0.0, mu=0.2)
+    N = K.shape[0]
+    L, dtau, U = 8, 0.1, 3.0
+    for ft in (1, 2):
+        f = W.random_fields(ft, L, N, seed=41 + ft)
+        m = make_model(orc, K, U, dtau, L, 4, ft=ft)
+        e, gK, gU = orc.energy_grad(m, f)
+        h = 1e-5
+
+        def ener(Kp, Up):
+            mm = make_model(orc, Kp, Up, dtau, L, 4, ft=ft)
+            G = np.stack([orc.green_udv(mm, f, s, 0)[0] for s in (0, 1)])
+            return orc.energy(mm, G)[3]
+
+        assert e[3] == pytest.approx(ener(K, U), rel=1e-12)
+        for (x, y) in ((0, 1), (2, 2), (1, 4), (0, 3)):
+            Kp = K.copy(); Km = K.copy()
+            Kp[x, y] += h; Km[x, y] -= h
+            if x != y:
+                Kp[y, x] += h; Km[y, x] -= h
+            fd = (ener(Kp, U) - ener(Km, U)) / (2 * h)
+            # one K shared by both flavors: the total derivative is the sum over flavors
+            assert gK[:, x, y].sum() == pytest.approx(fd, rel=1e-6, abs=1e-8), (ft, x, y)
+        fdU = (ener(K, U + h) - ener(K, U - h)) / (2 * h)
+        assert gU == pytest.approx(fdU, rel=1e-6, abs=1e-8)
