@@ -167,6 +167,19 @@ dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* 
 dqmc_status dqmc_logdet_backward(dqmc_ctx* ctx, int32_t model_index, const int8_t* fields, int32_t n_cfg,
                                  double* logdet, double* grad_K, double* grad_U);
 
+/* Derivatives of the energy estimator at tau = 0 (the Kin + Pot of dqmc_measure,
+ * evaluated at G(0) = (1 + B(beta,0))^-1) on fixed field configurations of model
+ * `model_index` (FP64).  With Gamma = dE/dG:
+ *     dE = (explicit, at fixed G) + sum_s sum_tau Tr[G(tau-1,0) Gamma^T G(0,tau) dB_tau]
+ * (dG = -G dB(beta,0) G with the time-displaced Green functions G(tau,0) =
+ * B(tau,0) G(0) and G(0,tau) = -(1 - G(0)) B(tau,0)^-1, both computed stably
+ * from the UDV chains).  fields: [n_cfg][L][M_V] int8 host.  Outputs (host):
+ *     energy  [n_cfg][4] = Kin, Pot, Part, Ener of each configuration
+ *     grad_K  [n_cfg][n_flavors][N][N]: dEner/dK^s_xy, K_xy and K_yx varied together
+ *     grad_U  [n_cfg]: dEner/dU (explicit U and the couplings c(field)). */
+dqmc_status dqmc_energy_backward(dqmc_ctx* ctx, int32_t model_index, const int8_t* fields, int32_t n_cfg,
+                                 double* energy, double* grad_K, double* grad_U);
+
 /* Checkpoint: fields of every chain, packed [c][L_c][M_V_c] (host), and the
  * Philox sweep counter (confout / confin of Algorithm 1). */
 dqmc_status dqmc_get_fields(dqmc_ctx* ctx, int8_t* out, uint64_t* rng_counter);

@@ -677,6 +677,102 @@ dqmc_status dqmc_logdet_backward(dqmc_ctx* ctx, int32_t model_index, const int8_
   return st;
 }
 
+dqmc_status dqmc_energy_backward(dqmc_ctx* ctx, int32_t model_index, const int8_t* fields, int32_t n_cfg,
+                                 double* energy, double* grad_K, double* grad_U) {
+  if (!ctx) return DQMC_EINVAL;
+  if (model_index < 0 || model_index >= (int)ctx->models.size() || !fields || n_cfg < 1 || !energy || !grad_K ||
+      !grad_U)
+    return fail(ctx, DQMC_EINVAL, "bad model index, empty configuration list or null output");
+  const ModelHost& M = ctx->models[model_index];
+  const int N = M.d.n_sites, nfl = M.d.n_flavors, MV = M.d.n_vertices, L = M.d.L, ld = M.ld;
+  for (size_t q = 0; q < (size_t)n_cfg * L * MV; ++q) {
+    const int8_t f = fields[q];
+    const bool ok = (M.d.field_type == DQMC_FIELD_ISING) ? (f == 1 || f == -1) : (f == 1 || f == -1 || f == 2 || f == -2);
+    if (!ok) return fail(ctx, DQMC_EINVAL, "invalid field value %d", (int)f);
+  }
+  const size_t per = chain_layout(M, DQMC_PREC_FP64, 1, nullptr, nullptr);
+  const size_t mat = (size_t)N * ld;
+  std::vector<ChainDev> ch(n_cfg, ChainDev{});
+  unsigned char* arena = nullptr;
+  ChainDev* ch_d = nullptr;
+  double *V_d = nullptr, *w_d = nullptr, *G0_d = nullptr, *ew_d = nullptr, *gK_d = nullptr, *gU_d = nullptr,
+         *ep_d = nullptr;
+  dqmc_status st = DQMC_OK;
+  auto cleanup = [&]() {
+    cudaFree(arena);
+    cudaFree(ch_d);
+    cudaFree(V_d);
+    cudaFree(w_d);
+    cudaFree(G0_d);
+    cudaFree(ew_d);
+    cudaFree(gK_d);
+    cudaFree(gU_d);
+    cudaFree(ep_d);
+  };
+#define EGRAD_TRY(expr)                                                                \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      st = fail(ctx, DQMC_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));             \
+      cleanup();                                                                       \
+      return st;                                                                       \
+    }                                                                                  \
+  } while (0)
+  EGRAD_TRY(cudaMalloc((void**)&arena, per * n_cfg));
+  EGRAD_TRY(cudaMemsetAsync(arena, 0, per * n_cfg, ctx->stream));
+  for (int c = 0; c < n_cfg; ++c) {
+    chain_layout(M, DQMC_PREC_FP64, 1, arena + per * c, &ch[c]);
+    fill_model_fields(M, ch[c]);
+    ch[c].chain_id = (uint32_t)c;
+    ch[c].sign = 1;
+    EGRAD_TRY(cudaMemcpyAsync(ch[c].fields, fields + (size_t)c * L * MV, (size_t)L * MV, cudaMemcpyHostToDevice,
+                              ctx->stream));
+  }
+  std::vector<double> Vh((size_t)nfl * N * N), wh((size_t)nfl * N);
+  for (int s = 0; s < nfl; ++s) {
+    std::copy(M.eigvec[s].begin(), M.eigvec[s].end(), Vh.begin() + (size_t)s * N * N);
+    std::copy(M.eigval[s].begin(), M.eigval[s].end(), wh.begin() + (size_t)s * N);
+  }
+  EGRAD_TRY(cudaMalloc((void**)&ch_d, sizeof(ChainDev) * n_cfg));
+  EGRAD_TRY(cudaMemcpyAsync(ch_d, ch.data(), sizeof(ChainDev) * n_cfg, cudaMemcpyHostToDevice, ctx->stream));
+  EGRAD_TRY(cudaMalloc((void**)&V_d, sizeof(double) * Vh.size()));
+  EGRAD_TRY(cudaMalloc((void**)&w_d, sizeof(double) * wh.size()));
+  EGRAD_TRY(cudaMemcpyAsync(V_d, Vh.data(), sizeof(double) * Vh.size(), cudaMemcpyHostToDevice, ctx->stream));
+  EGRAD_TRY(cudaMemcpyAsync(w_d, wh.data(), sizeof(double) * wh.size(), cudaMemcpyHostToDevice, ctx->stream));
+  EGRAD_TRY(cudaMalloc((void**)&G0_d, sizeof(double) * (size_t)n_cfg * nfl * N * N));
+  EGRAD_TRY(cudaMalloc((void**)&ew_d, sizeof(double) * (size_t)n_cfg * nfl * 6 * mat));
+  EGRAD_TRY(cudaMalloc((void**)&gK_d, sizeof(double) * (size_t)n_cfg * nfl * N * N));
+  EGRAD_TRY(cudaMalloc((void**)&gU_d, sizeof(double) * (size_t)n_cfg * nfl));
+  EGRAD_TRY(cudaMalloc((void**)&ep_d, sizeof(double) * (size_t)n_cfg * nfl * 3));
+  dqmc::set_smem_bytes(dqmc::sweep_smem_bytes(N, ld, MV, 1, 0));
+  EGRAD_TRY(dqmc::launch_energy_grad(ch_d, n_cfg, nfl, V_d, w_d, G0_d, ew_d, gK_d, gU_d, ep_d, ctx->stream));
+  std::vector<double> gU((size_t)n_cfg * nfl), ep((size_t)n_cfg * nfl * 3);
+  EGRAD_TRY(cudaMemcpyAsync(grad_K, gK_d, sizeof(double) * (size_t)n_cfg * nfl * N * N, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  EGRAD_TRY(cudaMemcpyAsync(gU.data(), gU_d, sizeof(double) * gU.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  EGRAD_TRY(cudaMemcpyAsync(ep.data(), ep_d, sizeof(double) * ep.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  EGRAD_TRY(cudaMemcpyAsync(ch.data(), ch_d, sizeof(ChainDev) * n_cfg, cudaMemcpyDeviceToHost, ctx->stream));
+  EGRAD_TRY(cudaStreamSynchronize(ctx->stream));
+#undef EGRAD_TRY
+  for (int c = 0; c < n_cfg; ++c) {
+    if (ch[c].error) st = fail(ctx, DQMC_EUNSTABLE, "configuration %d: singular matrix in the stabilisation", c);
+    double kin = 0.0, part = 0.0, pot = 0.0, gu = 0.0;
+    for (int s = 0; s < nfl; ++s) {
+      kin += ep[((size_t)c * nfl + s) * 3 + 0];
+      part += ep[((size_t)c * nfl + s) * 3 + 1];
+      pot += ep[((size_t)c * nfl + s) * 3 + 2];
+      gu += gU[(size_t)c * nfl + s];
+    }
+    energy[(size_t)c * 4 + 0] = kin;
+    energy[(size_t)c * 4 + 1] = pot;
+    energy[(size_t)c * 4 + 2] = part;
+    energy[(size_t)c * 4 + 3] = kin + pot;
+    grad_U[c] = gu;
+  }
+  cleanup();
+  return st;
+}
+
 const char* dqmc_last_error(const dqmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 void dqmc_destroy(dqmc_ctx* ctx) {

@@ -87,6 +87,9 @@ size_t sweep_smem_bytes(int maxN, int maxld, int maxMV, int delay_k, int precisi
 cudaError_t launch_copy_green(ChainDev* chains, int chain, int flavor, int precision, double* out,
                               cudaStream_t st);
 void set_smem_bytes(size_t bytes);
+cudaError_t launch_energy_grad(ChainDev* chains, int n_cfg, int nfl, const double* eigvec, const double* eigval,
+                               double* G0all, double* ework, double* gK, double* gU, double* eparts,
+                               cudaStream_t st);
 cudaError_t launch_finalize_init(ChainDev* chains, int n_chains, cudaStream_t st);
 cudaError_t launch_reset_stats(ChainDev* chains, int n_chains, cudaStream_t st);
 cudaError_t launch_logdet_grad(ChainDev* chains, int n_cfg, int nfl, const double* eigvec,

@@ -107,6 +107,8 @@ def load() -> ctypes.CDLL:
     L.dqmc_measure.restype = ctypes.c_int
     L.dqmc_logdet_backward.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     L.dqmc_logdet_backward.restype = ctypes.c_int
+    L.dqmc_energy_backward.argtypes = [vp, i32, vp, i32, vp, vp, vp]
+    L.dqmc_energy_backward.restype = ctypes.c_int
     L.dqmc_get_fields.argtypes = [vp, vp, vp]
     L.dqmc_get_fields.restype = ctypes.c_int
     L.dqmc_set_fields.argtypes = [vp, vp, u64]
@@ -250,3 +252,17 @@ class Ensemble:
         gU = np.zeros((n_cfg, nfl))
         self._check(self._lib.dqmc_logdet_backward(self._h, int(model_index), _p(f), n_cfg, _p(ldv), _p(gK), _p(gU)))
         return ldv, gK, gU
+
+    def energy_backward(self, model_index: int, fields: np.ndarray):
+        """Per configuration: (Kin, Pot, Part, Ener), dEner/dK^s (symmetric pairs) and dEner/dU."""
+        m = self.models[model_index]
+        f = np.ascontiguousarray(fields, dtype=np.int8)
+        if f.ndim == 2:
+            f = f[None]
+        n_cfg = f.shape[0]
+        nfl = m.hopping.shape[0]
+        e = np.zeros((n_cfg, 4))
+        gK = np.zeros((n_cfg, nfl, m.N, m.N))
+        gU = np.zeros(n_cfg)
+        self._check(self._lib.dqmc_energy_backward(self._h, int(model_index), _p(f), n_cfg, _p(e), _p(gK), _p(gU)))
+        return e, gK, gU

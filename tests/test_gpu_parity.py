@@ -249,6 +249,68 @@ def test_logdet_gradient_matches_oracle(dq, orc):
         assert np.allclose(gU[c], gUo, rtol=1e-8, atol=1e-9)
 
 
+@pytest.mark.parametrize("ft", [1, 2])
+def test_energy_gradient_matches_oracle(dq, orc, ft):
+    m = W.ModelSpec(W.square_lattice(3, 3, 1.0, 0.0, 0.15), U=3.0, dtau=0.1, L=12, n_wrap=4, field_type=ft)
+    fs = np.stack([W.random_fields(ft, m.L, m.n_vertices, seed=s) for s in (3, 4)])
+    ens = dq.Ensemble([m], [0], precision="fp64")
+    e, gK, gU = ens.energy_backward(0, fs)
+    om = omodel(orc, m)
+    for c in range(2):
+        eo, gKo, gUo = orc.energy_grad(om, fs[c])
+        assert np.allclose(e[c], eo, rtol=1e-10, atol=1e-10)
+        assert np.allclose(gK[c], gKo, rtol=1e-8, atol=1e-9)
+        assert gU[c] == pytest.approx(gUo, rel=1e-8, abs=1e-9)
+
+
+def test_gradients_square8x8_beta4(dq, orc):
+    """The gradient workload's shape: 8x8, beta = 4 (L = 40), U = 4, one configuration."""
+    m = W.ModelSpec(W.square_lattice(8, 8), U=4.0, dtau=0.1, L=40, n_wrap=10)
+    f = W.random_fields(1, m.L, m.n_vertices, seed=1)[None]
+    ens = dq.Ensemble([m], [0], precision="fp64")
+    ld, gKl, gUl = ens.logdet_backward(0, f)
+    e, gKe, gUe = ens.energy_backward(0, f)
+    om = omodel(orc, m)
+    ldo, _, gKlo, gUlo = orc.logdet_grad(om, f[0])
+    eo, gKeo, gUeo = orc.energy_grad(om, f[0])
+    assert np.allclose(ld[0], ldo, rtol=1e-10)
+    assert np.allclose(gKl[0], gKlo, rtol=1e-8, atol=1e-8)
+    assert np.allclose(gUl[0], gUlo, rtol=1e-8)
+    assert np.allclose(e[0], eo, rtol=1e-10, atol=1e-10)
+    assert np.allclose(gKe[0], gKeo, rtol=1e-7, atol=1e-8)
+    assert gUe[0] == pytest.approx(gUeo, rel=1e-8)
+
+
+def test_autograd_function_against_finite_differences(dq):
+    import torch
+    from paper_1704_00131_gb300.autograd import logdet_energy
+    K0 = W.square_lattice(2, 3, 1.0, 0.0, 0.1)
+    L, dtau, nw = 8, 0.1, 4
+    fs = np.stack([W.random_fields(1, L, 6, seed=s) for s in (1, 2)])
+    K = torch.tensor(K0, dtype=torch.float64, requires_grad=True)
+    U = torch.tensor(2.5, dtype=torch.float64, requires_grad=True)
+    ld, en = logdet_energy(K, U, fs, dtau, L, nw)
+    loss = ld.sum() + 0.5 * en.sum()
+    loss.backward()
+    h = 1e-5
+
+    def f(Kn, Un):
+        with torch.no_grad():
+            a, b = logdet_energy(torch.tensor(Kn), torch.tensor(Un), fs, dtau, L, nw)
+        return float(a.sum() + 0.5 * b.sum())
+
+    for (x, y) in ((0, 1), (1, 1), (2, 5)):
+        Kp, Km = K0.copy(), K0.copy()
+        Kp[x, y] += h; Km[x, y] -= h
+        if x != y:
+            Kp[y, x] += h; Km[y, x] -= h
+        fd = (f(Kp, 2.5) - f(Km, 2.5)) / (2 * h)
+        g = K.grad[x, y] + (K.grad[y, x] if x != y else 0.0)
+        assert float(g) == pytest.approx(fd, rel=1e-6, abs=1e-8)
+    fdU = (f(K0, 2.5 + h) - f(K0, 2.5 - h)) / (2 * h)
+    assert float(U.grad) == pytest.approx(fdU, rel=1e-6, abs=1e-8)
+
+
 # --------------------------------------------------------------- edge cases
 def test_degenerate_sizes(dq, orc):
     """N = 1, partial vertex sets, n_wrap = 1 and n_wrap = L."""
