@@ -296,7 +296,8 @@ def test_autograd_function_against_finite_differences(dq):
 
     def f(Kn, Un):
         with torch.no_grad():
-            a, b = logdet_energy(torch.tensor(Kn), torch.tensor(Un), fs, dtau, L, nw)
+            a, b = logdet_energy(torch.tensor(Kn, dtype=torch.float64), torch.tensor(Un, dtype=torch.float64),
+                                 fs, dtau, L, nw)
         return float(a.sum() + 0.5 * b.sum())
 
     for (x, y) in ((0, 1), (1, 1), (2, 5)):
