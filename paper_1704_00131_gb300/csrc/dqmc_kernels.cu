@@ -230,7 +230,7 @@ __host__ __device__ inline int gemm_pick_r(int n) {
   return best_r;
 }
 
-template <typename T, bool TA, bool TB, int R>
+template <typename T, bool TA, bool TB, int R, bool ACC = false>
 __device__ void cta_gemm_r(int M, int Nc, int Kd, const T* __restrict__ A, int lda, const T* __restrict__ B,
                            int ldb, T* __restrict__ C, int ldc, T* sm) {
   constexpr int TT = 16 * R;
@@ -283,7 +283,10 @@ __device__ void cta_gemm_r(int M, int Nc, int Kd, const T* __restrict__ A, int l
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           const int gm = m0 + ty * R + i, gn = n0 + tx * R + j;
-          if (gm < M && gn < Nc) C[(size_t)gm * ldc + gn] = acc[i][j];
+          if (gm < M && gn < Nc) {
+            if (ACC) C[(size_t)gm * ldc + gn] += acc[i][j];
+            else C[(size_t)gm * ldc + gn] = acc[i][j];
+          }
         }
     }
   __syncthreads();
@@ -302,7 +305,7 @@ __device__ void cta_gemm(int M, int Nc, int Kd, const T* __restrict__ A, int lda
 // exactly (TwoProd), its high part summed with TwoSum into the accumulator's
 // high word, the rounding errors and the hi*lo, lo*hi cross terms gathered in
 // the low word and renormalised once per output.
-template <bool TA, bool TB, int R>
+template <bool TA, bool TB, int R, bool ACC = false>
 __device__ void cta_gemm_dd_r(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B,
                               int ldb, dd* __restrict__ C, int ldc, dd* sm) {
   constexpr int TT = 16 * R;
@@ -365,7 +368,10 @@ __device__ void cta_gemm_dd_r(int M, int Nc, int Kd, const dd* __restrict__ A, i
 #pragma unroll
         for (int j = 0; j < R; ++j) {
           const int gm = m0 + ty * R + i, gn = n0 + tx * R + j;
-          if (gm < M && gn < Nc) C[(size_t)gm * ldc + gn] = fast_two_sum(ah[i][j], al[i][j]);
+          if (gm < M && gn < Nc) {
+            const dd r = fast_two_sum(ah[i][j], al[i][j]);
+            C[(size_t)gm * ldc + gn] = ACC ? dd_add(C[(size_t)gm * ldc + gn], r) : r;
+          }
         }
     }
   __syncthreads();
@@ -404,6 +410,7 @@ struct Smem {
   double* delta;    // [MV]
   double* gam;      // [MV]
   double* Rs;       // [2][MV] own-flavor ratios, double buffered (read by the peer CTA)
+  double* Rp;       // [MV] full ratio of the position a thread found accepted
   double* xdiag;    // [ld] exchange: diagonal of G for the potential energy
   double* xs;       // [8]  exchange: scalars
   double* red;      // [32]
@@ -419,7 +426,7 @@ __host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
   size_t b = 0;
   b += 2 * 16 * kGemmMaxTile * 8;
   b += 6 * (size_t)ld * 8;        // v, ev, d, hv, xdiag, spare
-  b += 5 * (size_t)MV * 8;        // u2, delta, gam, Rs[2]
+  b += 6 * (size_t)MV * 8;        // u2, delta, gam, Rs[2], Rp
   b += 8 * 8 + 32 * 8 + 32 * 4;   // xs, red, ired
   b += (size_t)MV * 4;            // qsite
   b += 2 * (size_t)MV + 16;       // fnew, fslice
@@ -442,6 +449,7 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   s.delta = p; p += MV;
   s.gam = p; p += MV;
   s.Rs = p; p += 2 * MV;
+  s.Rp = p; p += MV;
   s.xs = p; p += 8;
   s.red = p; p += 32;
   int* ip = reinterpret_cast<int*>(p);
@@ -1052,17 +1060,37 @@ __device__ void t_wrap<dd>(const ChainDev& C, int s, dd* G, dd* Gt, bool up, Sme
   cta_gemm_dd<false, false>(N, N, N, Gt, ld, Y, ld, G, ld, sm);
 }
 
-// G <- G + sum_m a_m b_m^T  (flush of the delayed rank-k update)
+// G <- G + sum_m a_m b_m^T  (flush of the delayed rank-k update), a register-
+// blocked product G += A^T B with A, B stored as rows a_m, b_m.
 template <typename Real>
-__device__ void flush_delayed(const ChainDev& C, Real* G, const Real* A, const Real* B, int nacc) {
+__device__ void flush_delayed(const ChainDev& C, Real* G, const Real* A, const Real* B, int nacc, Smem& S);
+
+template <>
+__device__ void flush_delayed<double>(const ChainDev& C, double* G, const double* A, const double* B, int nacc,
+                                      Smem& S) {
   const int N = C.N, ld = C.ld;
-  for (int e = threadIdx.x; e < N * N; e += kThreads) {
-    const int x = e / N, y = e - x * N;
-    Real acc = G[(size_t)x * ld + y];
-    for (int m = 0; m < nacc; ++m) acc = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + y], acc);
-    G[(size_t)x * ld + y] = acc;
-  }
-  __syncthreads();
+  const int r = gemm_pick_r(N);
+  if (r == 3) cta_gemm_r<double, true, false, 3, true>(N, N, nacc, A, ld, B, ld, G, ld, S.gemm);
+  else if (r == 5) cta_gemm_r<double, true, false, 5, true>(N, N, nacc, A, ld, B, ld, G, ld, S.gemm);
+  else cta_gemm_r<double, true, false, 4, true>(N, N, nacc, A, ld, B, ld, G, ld, S.gemm);
+}
+template <>
+__device__ void flush_delayed<float>(const ChainDev& C, float* G, const float* A, const float* B, int nacc,
+                                     Smem& S) {
+  const int N = C.N, ld = C.ld;
+  float* sm = reinterpret_cast<float*>(S.gemm);
+  const int r = gemm_pick_r(N);
+  if (r == 3) cta_gemm_r<float, true, false, 3, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
+  else if (r == 5) cta_gemm_r<float, true, false, 5, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
+  else cta_gemm_r<float, true, false, 4, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
+}
+template <>
+__device__ void flush_delayed<dd>(const ChainDev& C, dd* G, const dd* A, const dd* B, int nacc, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  dd* sm = reinterpret_cast<dd*>(S.gemm);
+  const int p3 = (N + 47) / 48 * 48, p4 = (N + 63) / 64 * 64;
+  if (p3 < p4) cta_gemm_dd_r<true, false, 3, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
+  else cta_gemm_dd_r<true, false, 4, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
 }
 
 // Sequential single-field updates of one slice (Sec. 2.2.1) for this CTA's
@@ -1110,13 +1138,16 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
       double R = S.gam[q];
       for (int r = 0; r < nfl; ++r) R *= Rr[r][q];
       const double aR = fabs(R);
-      if (S.u2[q] < (aR < 1.0 ? aR : 1.0)) { first = q; break; }
+      if (S.u2[q] < (aR < 1.0 ? aR : 1.0)) {
+        S.Rp[q] = R;
+        first = q;
+        break;
+      }
     }
     first = block_min_int(first, S.ired);
     tick(det, 1, t0);
     if (first >= MV) { buf ^= 1; break; }
-    double R = S.gam[first];
-    for (int r = 0; r < nfl; ++r) R *= Rr[r][first];
+    const double R = S.Rp[first];
     if (R < 0.0) sign = -sign;
     const int k = dir ? MV - 1 - first : first;
     const int i = S.qsite[first];
@@ -1145,7 +1176,7 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     tick(det, 2, t0);
     if (nacc == kdel) {
       __syncthreads();
-      flush_delayed(C, G, A, B, nacc);
+      flush_delayed<Real>(C, G, A, B, nacc, S);
       nacc = 0;
       tick(det, 3, t0);
     }
@@ -1153,7 +1184,7 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     buf ^= 1;
     __syncthreads();
   }
-  if (nacc) flush_delayed(C, G, A, B, nacc);
+  if (nacc) flush_delayed<Real>(C, G, A, B, nacc, S);
   tick(det, 3, t0);
   if (s == 0 && tid == 0) {
     C.proposals += MV;
