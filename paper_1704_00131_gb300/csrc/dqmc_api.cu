@@ -281,6 +281,14 @@ size_t chain_layout(const ModelHost& M, int precision, int delay_k, unsigned cha
     if (C) C->work[s] = (double*)p;
     p = take((size_t)2 * ld * sizeof(int));
     if (C) C->iwork[s] = (int*)p;
+    if (precision == DQMC_PREC_MIXED) {
+      // BF16 digit planes: kDig x (roundup(N,64) + roundup(N,32)) x roundup(max(N,k),16)
+      const int kmax = N > delay_k ? N : delay_k;
+      const size_t kp = (size_t)((kmax + 15) / 16 * 16);
+      const size_t elems = (size_t)7 * (size_t)(((N + 63) / 64) * 64 + ((N + 31) / 32) * 32) * kp;
+      p = take(elems * 2);
+      if (C) C->planes[s] = p;
+    }
   }
   return align_up(off, 256);
 }

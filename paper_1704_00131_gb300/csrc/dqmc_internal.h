@@ -35,6 +35,7 @@ struct ChainDev {
   double* slots[kMaxFlavors];     // FP64 [nst+1] x {Q [N][ld], T [N][ld], D [ld]}
   int* slot_detq[kMaxFlavors];    // [nst+1]
   double* work[kMaxFlavors];      // FP64 stabilisation workspace, kWorkMats matrices + vectors
+  void* planes[kMaxFlavors];      // BF16 digit planes of the split tensor-core products (mixed path)
   int* iwork[kMaxFlavors];        // [2*ld]
   uint32_t chain_id;
   int sign;                       // sign of the current weight (written by rank 0)

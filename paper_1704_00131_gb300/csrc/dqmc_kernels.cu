@@ -19,6 +19,7 @@
 //   QR-stabilised chain every n_wrap slices             Sec. 2.3, Eq. green_stable
 //   sweep: tau = 1..L up, L..1 down                     Algorithm 1, Sec. 2.4
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -377,15 +378,151 @@ __device__ void cta_gemm_dd_r(int M, int Nc, int Kd, const dd* __restrict__ A, i
   __syncthreads();
 }
 
-template <bool TA, bool TB>
-__device__ void cta_gemm_dd(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B,
-                            int ldb, dd* __restrict__ C, int ldc, dd* sm) {
-  // float pairs double the accumulator registers: tiles of 48 or 64 only, so
-  // that two CTAs fit on an SM
+
+// --------------------------------------------------------------------------
+// Exact-split BF16 tensor-core products for float-pair operands (the scheme of
+// Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 2012, on BF16 tensor cores).
+// Each row of op(A) and each column of op(B) is scaled by a power of two and
+// cut into kDig balanced 8-bit digits, x = 2^e sum_t q_t 2^-8(t+1), |q_t| <= 128,
+// each exactly a BF16 number.  Digit products are integers of at most 2^14;
+// the pairs (t,u) with t + u = d share one FP32 accumulator, exact as long as
+// (d + 1) K 2^14 <= 2^24, i.e. for K segments of at most 144.  The kDig
+// partial sums of a segment are recombined in float-float arithmetic and
+// scaled back.  Digits t + u >= kDig (relative weight 2^-64) are dropped.
+// Products run on mma.sync.m16n8k16 (BF16 in, FP32 accumulate); the digit
+// planes live in a per-CTA global scratch (L2-resident).
+// --------------------------------------------------------------------------
+constexpr int kDig = 7;
+constexpr int kKSeg = 144;
+
+__host__ __device__ inline int tc_pad(int n, int q) { return (n + q - 1) / q * q; }
+// bf16 elements of the digit planes of one CTA for sizes up to n and K up to kmax
+__host__ __device__ inline size_t tc_plane_elems(int n, int kmax) {
+  const int Kp = tc_pad(kmax, 16);
+  return (size_t)kDig * ((size_t)tc_pad(n, 64) + (size_t)tc_pad(n, 32)) * Kp;
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// |x| < 2^(e-1) for every element of a row or column whose largest |hi| is amax
+__device__ __forceinline__ int tc_exponent(float amax) { return amax > 0.f ? ilogbf(amax) + 2 : 0; }
+
+__device__ __forceinline__ void tc_digits(dd x, int e, __nv_bfloat16* out, size_t stride) {
+  float h = ldexpf(x.hi, -e), l = ldexpf(x.lo, -e);
+#pragma unroll
+  for (int t = 0; t < kDig; ++t) {
+    h *= 256.f;
+    l *= 256.f;
+    const float q = rintf(h);
+    out[(size_t)t * stride] = __float2bfloat16_rn(q);
+    const dd r = two_sum(h - q, l);
+    h = r.hi;
+    l = r.lo;
+  }
+}
+
+// C (+)= op(A) op(B), M x Nc, inner dimension Kd; float-pair operands.
+template <bool TA, bool TB, bool ACC>
+__device__ void gemm_tc(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B, int ldb,
+                        dd* __restrict__ C, int ldc, __nv_bfloat16* planes, int* expA, int* expB) {
+  const int Mp = tc_pad(M, 64), Np = tc_pad(Nc, 32), Kp = tc_pad(Kd, 16);
+  __nv_bfloat16* PA = planes;
+  __nv_bfloat16* PB = planes + (size_t)kDig * Mp * Kp;
+  const size_t sA = (size_t)Mp * Kp, sB = (size_t)Np * Kp;
+  const int tid = threadIdx.x;
+  // scale exponents: rows of op(A), columns of op(B)
+  for (int m = tid; m < Mp; m += kThreads) {
+    float amax = 0.f;
+    if (m < M)
+      for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(TA ? A[(size_t)k * lda + m].hi : A[(size_t)m * lda + k].hi));
+    expA[m] = tc_exponent(amax);
+  }
+  for (int n = tid; n < Np; n += kThreads) {
+    float amax = 0.f;
+    if (n < Nc)
+      for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(TB ? B[(size_t)n * ldb + k].hi : B[(size_t)k * ldb + n].hi));
+    expB[n] = tc_exponent(amax);
+  }
+  __syncthreads();
+  // digit planes: PA[t][m][k], PB[t][n][k] (k contiguous), zero padded
+  for (size_t e = tid; e < sA; e += kThreads) {
+    const int m = (int)(e / Kp), k = (int)(e - (size_t)m * Kp);
+    dd x = {0.f, 0.f};
+    if (m < M && k < Kd) x = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+    tc_digits(x, expA[m], PA + e, sA);
+  }
+  for (size_t e = tid; e < sB; e += kThreads) {
+    const int n = (int)(e / Kp), k = (int)(e - (size_t)n * Kp);
+    dd x = {0.f, 0.f};
+    if (n < Nc && k < Kd) x = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+    tc_digits(x, expB[n], PB + e, sB);
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, cq = lane & 3;
+  const int wm = warp & 3, wn = warp >> 2;
+  for (int m0 = 0; m0 < Mp; m0 += 64)
+    for (int n0 = 0; n0 < Np; n0 += 32)
+      for (int nt = 0; nt < 2; ++nt) {
+        const int r0 = m0 + wm * 16, c0 = n0 + wn * 16 + nt * 8;
+        for (int ks = 0; ks < Kp; ks += kKSeg) {
+          float acc[kDig][4];
+#pragma unroll
+          for (int d = 0; d < kDig; ++d)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[d][q] = 0.f;
+          const int ke = min(Kp, ks + kKSeg);
+          for (int k0 = ks; k0 < ke; k0 += 16) {
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) {
+              const __nv_bfloat16* pa = PA + (size_t)t * sA + (size_t)(r0 + g) * Kp + k0 + 2 * cq;
+              const uint32_t a0 = *reinterpret_cast<const uint32_t*>(pa);
+              const uint32_t a1 = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp);
+              const uint32_t a2 = *reinterpret_cast<const uint32_t*>(pa + 8);
+              const uint32_t a3 = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp + 8);
+#pragma unroll
+              for (int u = 0; t + u < kDig; ++u) {
+                const __nv_bfloat16* pb = PB + (size_t)u * sB + (size_t)(c0 + g) * Kp + k0 + 2 * cq;
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(pb);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(pb + 8);
+                mma_bf16_16816(acc[t + u], a0, a1, a2, a3, b0, b1);
+              }
+            }
+          }
+          // recombine the digit diagonals of this segment and add into C
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = r0 + g + (q >= 2 ? 8 : 0);
+            const int j = c0 + 2 * cq + (q & 1);
+            if (i < M && j < Nc) {
+              dd sum = {0.f, 0.f};
+#pragma unroll
+              for (int d = kDig - 1; d >= 0; --d) sum = dd_add(sum, {ldexpf(acc[d][q], -8 * (d + 2)), 0.f});
+              const int e = expA[i] + expB[j];
+              sum.hi = ldexpf(sum.hi, e);
+              sum.lo = ldexpf(sum.lo, e);
+              dd* cp = C + (size_t)i * ldc + j;
+              *cp = (ACC || ks > 0) ? dd_add(*cp, sum) : sum;
+            }
+          }
+        }
+      }
+  __syncthreads();
+}
+
+template <bool TA, bool TB, bool ACC>
+__device__ void gemm_dd_tiles(int M, int Nc, int Kd, const dd* A, int lda, const dd* B, int ldb, dd* C, int ldc,
+                              dd* sm) {
   const int n = M > Nc ? M : Nc;
   const int p3 = (n + 47) / 48 * 48, p4 = (n + 63) / 64 * 64;
-  if (p3 < p4) cta_gemm_dd_r<TA, TB, 3>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
-  else cta_gemm_dd_r<TA, TB, 4>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+  if (p3 < p4) cta_gemm_dd_r<TA, TB, 3, ACC>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+  else cta_gemm_dd_r<TA, TB, 4, ACC>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
 }
 
 template <typename T>
@@ -418,7 +555,10 @@ struct Smem {
   int* qsite;       // [MV]
   int8_t* fnew;     // [MV]
   int8_t* fslice;   // [MV] fields of the current slice
+  int* expA;        // [roundup(ld,64)] row exponents of the split tensor-core products
+  int* expB;        // [roundup(ld,64)] column exponents
   double* ab;       // delayed vectors A, B [2][k][ld] when they fit in shared memory
+  int flavor;       // the CTA's flavor
   double* qred;     // [8][128] partial sums of the QR trailing update
 };
 
@@ -432,6 +572,7 @@ __host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
   b += 2 * (size_t)MV + 16;       // fnew, fslice
   b = (b + 15) / 16 * 16;
   b += 8 * 128 * 8;               // qred
+  b += 2 * (size_t)((ld + 63) / 64 * 64) * 4;  // expA, expB
   return b;
 }
 
@@ -460,8 +601,22 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   s.fslice = bp; bp += MV + 16;
   const size_t off = ((size_t)(bp - reinterpret_cast<int8_t*>(base)) + 15) / 16 * 16;
   s.qred = reinterpret_cast<double*>(base + off);
-  s.ab = s.qred + 8 * 128;
+  const int le = (ld + 63) / 64 * 64;
+  s.expA = reinterpret_cast<int*>(s.qred + 8 * 128);
+  s.expB = s.expA + le;
+  s.ab = reinterpret_cast<double*>(s.expB + le);
   return s;
+}
+
+// Float-pair product of the mixed path: exact-split tensor-core products when
+// the chain has digit-plane scratch, the float-pair SIMT tiles otherwise.
+template <bool TA, bool TB, bool ACC>
+__device__ void gemm_dd(const ChainDev& C, int s, Smem& S, int M, int Nc, int Kd, const dd* A, int lda, const dd* B,
+                        int ldb, dd* Cm, int ldc) {
+  if (C.planes[s])
+    gemm_tc<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, (__nv_bfloat16*)C.planes[s], S.expA, S.expB);
+  else
+    gemm_dd_tiles<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, reinterpret_cast<dd*>(S.gemm));
 }
 
 // Slice potential v^s_i of slice tau (1-based) from global fields.
@@ -1055,9 +1210,8 @@ __device__ void t_wrap<dd>(const ChainDev& C, int s, dd* G, dd* Gt, bool up, Sme
   const int N = C.N, ld = C.ld;
   const dd* X = (const dd*)(up ? C.Edd[s] : C.Einvdd[s]);
   const dd* Y = (const dd*)(up ? C.Einvdd[s] : C.Edd[s]);
-  dd* sm = reinterpret_cast<dd*>(S.gemm);
-  cta_gemm_dd<false, false>(N, N, N, X, ld, G, ld, Gt, ld, sm);
-  cta_gemm_dd<false, false>(N, N, N, Gt, ld, Y, ld, G, ld, sm);
+  gemm_dd<false, false, false>(C, s, S, N, N, N, X, ld, G, ld, Gt, ld);
+  gemm_dd<false, false, false>(C, s, S, N, N, N, Gt, ld, Y, ld, G, ld);
 }
 
 // G <- G + sum_m a_m b_m^T  (flush of the delayed rank-k update), a register-
@@ -1087,10 +1241,7 @@ __device__ void flush_delayed<float>(const ChainDev& C, float* G, const float* A
 template <>
 __device__ void flush_delayed<dd>(const ChainDev& C, dd* G, const dd* A, const dd* B, int nacc, Smem& S) {
   const int N = C.N, ld = C.ld;
-  dd* sm = reinterpret_cast<dd*>(S.gemm);
-  const int p3 = (N + 47) / 48 * 48, p4 = (N + 63) / 64 * 64;
-  if (p3 < p4) cta_gemm_dd_r<true, false, 3, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
-  else cta_gemm_dd_r<true, false, 4, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
+  gemm_dd<true, false, true>(C, S.flavor, S, N, N, nacc, A, ld, B, ld, G, ld);
 }
 
 // Sequential single-field updates of one slice (Sec. 2.2.1) for this CTA's
@@ -1223,7 +1374,6 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
   const int N = C.N, ld = C.ld;
   dd* X = reinterpret_cast<dd*>(wmat(C, s, 0));
   dd* Y = reinterpret_cast<dd*>(wmat(C, s, 1));
-  dd* sm = reinterpret_cast<dd*>(S.gemm);
   dd* evr = reinterpret_cast<dd*>(S.ev);
   to_dd_mat(N, ld, src.Q, X);
   const dd* E = (const dd*)C.Edd[s];
@@ -1237,12 +1387,12 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
         X[(size_t)x * ld + y] = dd_mul(X[(size_t)x * ld + y], evr[x]);
       }
       __syncthreads();
-      cta_gemm_dd<false, false>(N, N, N, E, ld, X, ld, Y, ld, sm);
+      gemm_dd<false, false, false>(C, s, S, N, N, N, E, ld, X, ld, Y, ld);
       dd* t_ = X; X = Y; Y = t_;
     }
   } else {
     for (int t = t2; t >= t1 + 1; --t) {
-      cta_gemm_dd<true, false>(N, N, N, E, ld, X, ld, Y, ld, sm);
+      gemm_dd<true, false, false>(C, s, S, N, N, N, E, ld, X, ld, Y, ld);
       slice_potential_global(C, s, t, S.v);
       for (int x = threadIdx.x; x < N; x += kThreads) evr[x] = from_d<dd>(exp(S.v[x]));
       __syncthreads();
@@ -1281,7 +1431,7 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
   }
   __syncthreads();
   dd* Tn = reinterpret_cast<dd*>(wmat(C, s, 5));
-  cta_gemm_dd<false, false>(N, N, N, Rt, ld, PT, ld, Tn, ld, sm);
+  gemm_dd<false, false, false>(C, s, S, N, N, N, Rt, ld, PT, ld, Tn, ld);
   dd_to_d_inplace(N, ld, Tn);
   tick(det, 6, t0);
   return detq;
@@ -1290,7 +1440,6 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
 __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, double* Gout, double& logdet,
                                     int& sign, Smem& S) {
   const int N = C.N, ld = C.ld;
-  dd* sm = reinterpret_cast<dd*>(S.gemm);
   double* W0 = wmat(C, s, 0);
   double* W1 = wmat(C, s, 1);
   dd* QRd = reinterpret_cast<dd*>(wmat(C, s, 3));
@@ -1301,8 +1450,8 @@ __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, dou
   to_dd_mat(N, ld, Lf.Q, QLd);
   to_dd_mat(N, ld, R.T, TRd);
   to_dd_mat(N, ld, Lf.T, TLd);
-  cta_gemm_dd<true, false>(N, N, N, QRd, ld, QLd, ld, reinterpret_cast<dd*>(W0), ld, sm);
-  cta_gemm_dd<false, true>(N, N, N, TRd, ld, TLd, ld, reinterpret_cast<dd*>(W1), ld, sm);
+  gemm_dd<true, false, false>(C, s, S, N, N, N, QRd, ld, QLd, ld, reinterpret_cast<dd*>(W0), ld);
+  gemm_dd<false, true, false>(C, s, S, N, N, N, TRd, ld, TLd, ld, reinterpret_cast<dd*>(W1), ld);
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
     const double dR = R.D[i], dL = Lf.D[j];
@@ -1331,7 +1480,7 @@ __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, dou
     Yd[(size_t)i * ld + j] = from_d<dd>(W1[(size_t)i * ld + j] / (dL > 1.0 ? dL : 1.0));
   }
   __syncthreads();
-  cta_gemm_dd<false, false>(N, N, N, QLd, ld, Yd, ld, reinterpret_cast<dd*>(Gout), ld, sm);
+  gemm_dd<false, false, false>(C, s, S, N, N, N, QLd, ld, Yd, ld, reinterpret_cast<dd*>(Gout), ld);
   dd_to_d_inplace(N, ld, Gout);
   double part = 0.0;
   for (int i = threadIdx.x; i < N; i += kThreads) {
@@ -1474,6 +1623,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
   const int c = P.order[blockIdx.x / nfl];
   ChainDev& C = chains[c];
   Smem S = carve_smem(smem_raw, C.ld, C.MV);
+  S.flavor = s;
   Real* G = (Real*)C.G[s];
   Real* Gt = (Real*)C.Gtmp[s];
   Real* A = P.ab_smem ? reinterpret_cast<Real*>(S.ab) : (Real*)C.dA[s];
