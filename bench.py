@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c5"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed", "mixed_tc"])
     ap.add_argument("--chains", type=int, default=0, help="override the number of chains (c3/c5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 path")
@@ -248,6 +248,9 @@ def time_path(wl, precision, args, stream, seed, world, local_rank):
         peak, src, kern = FP64_PEAK_TF, "measured cuBLAS DGEMM on this GB300 (FP64 pipe)", "sweep_kernel<double>"
     elif precision == "fp32":
         peak, src, kern = FP32_PEAK_TF, "measured cuBLAS SGEMM on this GB300 (FP32 SIMT)", "sweep_kernel<float>"
+    elif precision == "mixed_tc":
+        peak, src, kern = DW_PEAK_TF, ("double-word peak of the FP32 pipes (SGEMM / 12); the N^3 products run as "
+                                       "exact-split BF16 tensor-core products"), "sweep_kernel<dd> (split-BF16 mma)"
     else:
         peak, src, kern = DW_PEAK_TF, ("double-word arithmetic on the FP32 pipes: measured SGEMM rate / 12 "
                                        "FP32 operations per float-pair multiply-add (the FP64 share of the "
@@ -352,7 +355,7 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "mixed": "f32x2+f64"}[main_prec],
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "mixed": "f32x2+f64", "mixed_tc": "bf16-split+f32x2+f64"}[main_prec],
             "data": "synthetic (seeded Philox fields, random-init Markov chains)",
             "config": {"workload": wl.name, "chains": wl.n_chains, "precision": main_prec,
                        "delay_k": wl.delay_k, "n_wrap": 10,

@@ -68,8 +68,20 @@ typedef enum { DQMC_FIELD_ISING = 1, DQMC_FIELD_HS4 = 2 } dqmc_field_type;
  *     precision monitor of dqmc_sweep reports it.
  *   DQMC_PREC_MIXED: the working G and the update vectors are float pairs
  *     (hi + lo, about 48 significant bits) computed with error-free
- *     transformations on the FP32 pipes; the stabilisation is FP64. */
-typedef enum { DQMC_PREC_FP64 = 0, DQMC_PREC_FP32 = 1, DQMC_PREC_MIXED = 2 } dqmc_precision;
+ *     transformations on the FP32 pipes; the dense products of the
+ *     stabilisation (B chain, T update, Q^T Q, T T^T, Q Y) are float-pair
+ *     products; the pivoted QR, the LU and the solves are FP64.
+ *   DQMC_PREC_MIXED_TC: as DQMC_PREC_MIXED, with the N x N x N products (wraps
+ *     and the stabilisation products) as exact-split BF16 tensor-core products
+ *     (seven 8-bit digits per operand, digit diagonals accumulated exactly in
+ *     FP32, recombined in float pairs).  Needs extra device memory for the
+ *     digit planes. */
+typedef enum {
+  DQMC_PREC_FP64 = 0,
+  DQMC_PREC_FP32 = 1,
+  DQMC_PREC_MIXED = 2,
+  DQMC_PREC_MIXED_TC = 3
+} dqmc_precision;
 
 /* One model: a lattice with its couplings (Sec. 3.1, the Operator type with
  * hopping Op_T, g = -dtau, and single-site vertices Op_V).  Chains refer to a

@@ -120,6 +120,7 @@ struct dqmc_ctx {
   int* order_d = nullptr;
   unsigned char* arena = nullptr;
   std::vector<void*> model_allocs;
+  int kprec = 0;          // kernel instantiation: 0 double, 1 float, 2 float pairs
   size_t smem = 0;        // dynamic shared memory of the fresh-G / gradient kernels
   size_t smem_sweep = 0;  // ... of the sweep kernel (plus the delayed vectors when they fit)
   int ab_smem = 0;
@@ -281,7 +282,7 @@ size_t chain_layout(const ModelHost& M, int precision, int delay_k, unsigned cha
     if (C) C->work[s] = (double*)p;
     p = take((size_t)2 * ld * sizeof(int));
     if (C) C->iwork[s] = (int*)p;
-    if (precision == DQMC_PREC_MIXED) {
+    if (precision == DQMC_PREC_MIXED_TC) {
       // BF16 digit planes: kDig x (roundup(N,64) + roundup(N,32)) x roundup(max(N,k),16)
       const int kmax = N > delay_k ? N : delay_k;
       const size_t kp = (size_t)((kmax + 15) / 16 * 16);
@@ -336,7 +337,7 @@ dqmc_status download_chains(dqmc_ctx* ctx) {
 dqmc_status initial_fill(dqmc_ctx* ctx) {
   const int n = (int)ctx->chains_h.size();
   dqmc::set_smem_bytes(ctx->smem);
-  CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, n, ctx->nfl, ctx->opts.precision, 1, nullptr, -1, ctx->stream));
+  CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, n, ctx->nfl, ctx->kprec, 1, nullptr, -1, ctx->stream));
   CUDA_TRY(ctx, dqmc::launch_finalize_init(ctx->chains_d, n, ctx->stream));
   dqmc_status st = download_chains(ctx);
   if (st) return st;
@@ -360,7 +361,8 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
     return fail(*out, DQMC_EINVAL, "null argument or empty model/chain list");
   }
   c->opts = *opts;
-  if (opts->precision != DQMC_PREC_FP64 && opts->precision != DQMC_PREC_FP32 && opts->precision != DQMC_PREC_MIXED) {
+  c->kprec = opts->precision == DQMC_PREC_MIXED_TC ? DQMC_PREC_MIXED : opts->precision;
+  if (opts->precision < DQMC_PREC_FP64 || opts->precision > DQMC_PREC_MIXED_TC) {
     *out = ctx.release();
     return fail(*out, DQMC_EINVAL, "unknown precision %d", opts->precision);
   }
@@ -455,7 +457,7 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
   c->smem = dqmc::sweep_smem_bytes(c->maxN, c->maxld, c->maxMV, opts->delay_k, opts->precision);
   {
     // delayed vectors A, B in shared memory when they fit beside the rest
-    const size_t rs = opts->precision == DQMC_PREC_FP32 ? sizeof(float) : sizeof(double);
+    const size_t rs = c->kprec == DQMC_PREC_FP32 ? sizeof(float) : sizeof(double);
     const size_t ab = (size_t)2 * opts->delay_k * c->maxld * rs;
     c->ab_smem = (c->smem + ab <= 200 * 1024) ? 1 : 0;
     c->smem_sweep = c->smem + (c->ab_smem ? ab : 0);
@@ -481,7 +483,7 @@ dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats)
   P.order = ctx->order_d;
   for (int i = 0; i < n_sweeps; ++i) {
     P.sweep = ctx->sweep_counter++;
-    CUDA_TRY(ctx, dqmc::launch_sweep(ctx->chains_d, P, ctx->nfl, ctx->opts.precision, ctx->smem_sweep, ctx->stream));
+    CUDA_TRY(ctx, dqmc::launch_sweep(ctx->chains_d, P, ctx->nfl, ctx->kprec, ctx->smem_sweep, ctx->stream));
   }
   if (!stats) return DQMC_OK;
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
@@ -545,11 +547,11 @@ dqmc_status dqmc_greens(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t fr
   double* src;
   if (fresh) {
     dqmc::set_smem_bytes(ctx->smem);
-    CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, (int)ctx->chains_h.size(), ctx->nfl, ctx->opts.precision, 0,
+    CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, (int)ctx->chains_h.size(), ctx->nfl, ctx->kprec, 0,
                                            ctx->scratch, chain, ctx->stream));
     src = ctx->scratch + (size_t)flavor * N * N;
   } else {
-    CUDA_TRY(ctx, dqmc::launch_copy_green(ctx->chains_d, chain, flavor, ctx->opts.precision, ctx->scratch, ctx->stream));
+    CUDA_TRY(ctx, dqmc::launch_copy_green(ctx->chains_d, chain, flavor, ctx->kprec, ctx->scratch, ctx->stream));
     src = ctx->scratch;
   }
   CUDA_TRY(ctx, cudaMemcpyAsync(out, src, sizeof(double) * N * N,

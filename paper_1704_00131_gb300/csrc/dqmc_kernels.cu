@@ -1240,8 +1240,9 @@ __device__ void flush_delayed<float>(const ChainDev& C, float* G, const float* A
 }
 template <>
 __device__ void flush_delayed<dd>(const ChainDev& C, dd* G, const dd* A, const dd* B, int nacc, Smem& S) {
-  const int N = C.N, ld = C.ld;
-  gemm_dd<true, false, true>(C, S.flavor, S, N, N, nacc, A, ld, B, ld, G, ld);
+  // a rank-k update (k <= 64): the float-pair SIMT tiles beat the split
+  // tensor-core product, whose digit split and recombination cost O(N^2 k_dig)
+  gemm_dd_tiles<true, false, true>(C.N, C.N, nacc, A, C.ld, B, C.ld, G, C.ld, reinterpret_cast<dd*>(S.gemm));
 }
 
 // Sequential single-field updates of one slice (Sec. 2.2.1) for this CTA's
@@ -1343,6 +1344,162 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
   }
 }
 
+// ---- float-pair Householder QR with FP64 column scales (mixed path) -------
+// M = X diag(dsc) with X the float-pair product Bcal Q (entries O(1)) and dsc
+// the FP64 scales D of the previous decomposition, which may exceed the float
+// range.  Householder reflections act on rows and commute with the column
+// scaling, so the pivoted QR of M is the QR of X with the pivot chosen by the
+// scaled norm dsc_j ||X[k:, j]|| (Businger-Golub on M); R_M = R_X diag(dsc[perm]).
+__device__ void householder_apply_dd(int N, int ld, dd* M, int k, int j0, dd bk, const dd* hv, dd* qred) {
+  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
+  for (int c0 = j0; c0 < N; c0 += 128) {
+    dd w[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int i = k + rg; i < N; i += 8) {
+      const dd vi = hv[i];
+      const dd* row = M + (size_t)i * ld;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < N) w[q] = dd_fma(vi, row[j], w[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
+    __syncthreads();
+    dd wt[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dd t = {0.f, 0.f};
+#pragma unroll
+      for (int r = 0; r < 8; ++r) t = dd_add(t, qred[r * 128 + lane + 32 * q]);
+      const dd bw = dd_mul(bk, t);
+      wt[q] = {-bw.hi, -bw.lo};
+    }
+    for (int i = k + rg; i < N; i += 8) {
+      const dd vi = hv[i];
+      dd* row = M + (size_t)i * ld;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < N) row[j] = dd_fma(wt[q], vi, row[j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ int qr_pivoted_dd(int N, int ld, dd* X, double* dsc, double* beta, dd* vk0, double* cn, double* cn0,
+                             int* perm, Smem& S) {
+  const int tid = threadIdx.x;
+  dd* hv = reinterpret_cast<dd*>(S.hv);
+  dd* qred = reinterpret_cast<dd*>(S.qred);
+  for (int j = tid; j < N; j += kThreads) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double x = to_d(X[(size_t)i * ld + j]);
+      acc = fma(x, x, acc);
+    }
+    cn[j] = sqrt(acc);
+    cn0[j] = cn[j];
+    perm[j] = j;
+  }
+  __syncthreads();
+  const double tol3z = sqrt(2.220446049250313e-16);
+  int detq = 1;
+  for (int k = 0; k < N; ++k) {
+    double bv = -1.0;
+    int bi = N;
+    for (int j = k + tid; j < N; j += kThreads) {
+      const double sn = dsc[j] * cn[j];
+      if (sn > bv) { bv = sn; bi = j; }
+    }
+    int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N) p = k;
+    if (p != k) {
+      for (int i = tid; i < N; i += kThreads) {
+        const dd t = X[(size_t)i * ld + k];
+        X[(size_t)i * ld + k] = X[(size_t)i * ld + p];
+        X[(size_t)i * ld + p] = t;
+      }
+      if (tid == 0) {
+        const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
+        double t = cn[k]; cn[k] = cn[p]; cn[p] = t;
+        t = cn0[k]; cn0[k] = cn0[p]; cn0[p] = t;
+        t = dsc[k]; dsc[k] = dsc[p]; dsc[p] = t;
+      }
+      __syncthreads();
+    }
+    double part = 0.0;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const dd x = X[(size_t)i * ld + k];
+      const double xd = to_d(x);
+      part = fma(xd, xd, part);
+      hv[i] = x;
+    }
+    const double xn2 = block_sum(part, S.red);
+    const double xnorm = sqrt(xn2);
+    const dd x0 = hv[k];
+    double bk = 0.0, alpha = 0.0;
+    if (xnorm > 0.0) {
+      const double x0d = to_d(x0);
+      alpha = (x0d >= 0.0) ? -xnorm : xnorm;
+      const dd v0 = dd_add(x0, from_d<dd>(-alpha));
+      const double v0d = to_d(v0);
+      const double vtv = xn2 - x0d * x0d + v0d * v0d;
+      bk = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+      __syncthreads();
+      if (tid == 0) hv[k] = v0;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      beta[k] = bk;
+      vk0[k] = hv[k];
+    }
+    if (bk != 0.0) detq = -detq;
+    if (bk != 0.0) householder_apply_dd(N, ld, X, k, k + 1, from_d<dd>(bk), hv, qred);
+    __syncthreads();
+    if (tid == 0) X[(size_t)k * ld + k] = (xnorm > 0.0) ? from_d<dd>(alpha) : x0;
+    for (int j = k + 1 + tid; j < N; j += kThreads) {
+      if (cn[j] != 0.0) {
+        double t = fabs(to_d(X[(size_t)k * ld + j])) / cn[j];
+        t = fmax(0.0, (1.0 + t) * (1.0 - t));
+        const double r = cn[j] / cn0[j];
+        if (t * r * r <= tol3z) {
+          double acc = 0.0;
+          for (int i = k + 1; i < N; ++i) {
+            const double x = to_d(X[(size_t)i * ld + j]);
+            acc = fma(x, x, acc);
+          }
+          cn[j] = sqrt(acc);
+          cn0[j] = cn[j];
+        } else {
+          cn[j] *= sqrt(t);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return detq;
+}
+
+__device__ void form_q_dd(int N, int ld, const dd* X, const double* beta, const dd* vk0, dd* Q, Smem& S) {
+  const int tid = threadIdx.x;
+  dd* hv = reinterpret_cast<dd*>(S.hv);
+  dd* qred = reinterpret_cast<dd*>(S.qred);
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    Q[(size_t)x * ld + y] = {(x == y) ? 1.f : 0.f, 0.f};
+  }
+  __syncthreads();
+  for (int k = N - 1; k >= 0; --k) {
+    const double bk = beta[k];
+    if (bk == 0.0) continue;
+    for (int i = k + tid; i < N; i += kThreads) hv[i] = (i == k) ? vk0[k] : X[(size_t)i * ld + k];
+    __syncthreads();
+    householder_apply_dd(N, ld, Q, k, k, from_d<dd>(bk), hv, qred);
+  }
+}
+
 // ---- stabilisation with float-float products (mixed path) ----------------
 // Same steps as chain_step / green_from_udv; the dense products (the B chain,
 // T = D^-1 R P^T T, Q_R^T Q_L, T_R T_L^T, Q_L Y) run as float-float GEMMs on the
@@ -1404,30 +1561,35 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
       dd* t_ = X; X = Y; Y = t_;
     }
   }
-  double* Xd = reinterpret_cast<double*>(X);
-  dd_to_d_inplace(N, ld, X);
   tick(det, 4, t0);
-  for (int e = threadIdx.x; e < N * N; e += kThreads) {
-    const int x = e / N, y = e - x * N;
-    Xd[(size_t)x * ld + y] *= src.D[y];
-  }
-  __syncthreads();
   double* Dn = wvec(C, s, 0);
   double* beta = wvec(C, s, 1);
-  double* vk0 = wvec(C, s, 2);
+  dd* vk0 = reinterpret_cast<dd*>(wvec(C, s, 2));
+  double* dsc = wvec(C, s, 5);
+  double* invr = wvec(C, s, 6);
   int* perm = C.iwork[s];
-  const int detq = qr_pivoted(N, ld, Xd, beta, vk0, wvec(C, s, 3), wvec(C, s, 4), perm, S);
-  double* Qn = wmat(C, s, 2);
-  form_q(N, ld, Xd, beta, vk0, Qn, S);
+  for (int j = threadIdx.x; j < N; j += kThreads) dsc[j] = src.D[j];
+  __syncthreads();
+  const int detq = qr_pivoted_dd(N, ld, X, dsc, beta, vk0, wvec(C, s, 3), wvec(C, s, 4), perm, S);
+  dd* Qd = reinterpret_cast<dd*>(wmat(C, s, 2));
+  form_q_dd(N, ld, X, beta, vk0, Qd, S);
+  dd_to_d_inplace(N, ld, Qd);
   tick(det, 5, t0);
   dd* PT = reinterpret_cast<dd*>(wmat(C, s, 3));
   dd* Rt = reinterpret_cast<dd*>(wmat(C, s, 4));
-  for (int x = threadIdx.x; x < N; x += kThreads) Dn[x] = fabs(Xd[(size_t)x * ld + x]);
+  // D = |diag R_M| = |R_X,kk| dsc_k;  R~_ij = R_X,ij dsc_j / (|R_X,ii| dsc_i), |R~_ij| <= 1
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    const double rkk = fabs(to_d(X[(size_t)x * ld + x]));
+    Dn[x] = rkk * dsc[x];
+    invr[x] = (rkk > 0.0 && dsc[x] > 0.0) ? 1.0 / (rkk * dsc[x]) : 0.0;
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int x = e / N, y = e - x * N;
     PT[(size_t)x * ld + y] = from_d<dd>(src.T[(size_t)perm[x] * ld + y]);
-    Rt[(size_t)x * ld + y] = from_d<dd>((y >= x && Dn[x] > 0.0) ? Xd[(size_t)x * ld + y] / Dn[x] : 0.0);
+    dd r = {0.f, 0.f};
+    if (y >= x) r = dd_mul(X[(size_t)x * ld + y], from_d<dd>(invr[x] * dsc[y]));
+    Rt[(size_t)x * ld + y] = r;
   }
   __syncthreads();
   dd* Tn = reinterpret_cast<dd*>(wmat(C, s, 5));

@@ -18,7 +18,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libdqmc.so")
 
 DQMC_OK, DQMC_EINVAL, DQMC_ENOMEM, DQMC_ECUDA, DQMC_EUNSTABLE, DQMC_ETIMEOUT, DQMC_ESTATE = range(7)
-PREC = {"fp64": 0, "fp32": 1, "mixed": 2}
+PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tc": 3}
 
 EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_logdet_backward",
             "dqmc_get_fields", "dqmc_set_fields", "dqmc_last_error", "dqmc_destroy"]

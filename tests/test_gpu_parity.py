@@ -157,14 +157,15 @@ def test_fp32_path_green_after_sweeps(dq, orc):
 
 
 # ------------------------------------------------------------------ mixed path
+@pytest.mark.parametrize("precision", ["mixed", "mixed_tc"])
 @pytest.mark.parametrize("ft", [1, 2])
-def test_sweep_trajectory_mixed(dq, orc, ft):
+def test_sweep_trajectory_mixed(dq, orc, ft, precision):
     """Mixed path (float-pair G, FP64 stabilisation): the ratios agree with FP64 to
     ~1e-13 relative, so every accept/reject decision and every field matches the
     oracle's trajectory, and G after each sweep matches to 1e-10."""
     m = square(4, U=4.0, L=20, nw=10, ft=ft)
     seed = 20170401
-    ens = dq.Ensemble([m], [0], precision="mixed", delay_k=16, seed=seed)
+    ens = dq.Ensemble([m], [0], precision=precision, delay_k=16, seed=seed)
     f0, _ = ens.get_fields()
     och = orc.Chain(omodel(orc, m), f0[0], seed=seed, chain=0)
     for rep in range(3):
@@ -177,14 +178,15 @@ def test_sweep_trajectory_mixed(dq, orc, ft):
             assert np.abs(ens.greens(0, s)[0] - och.green(s)).max() < 1e-10
 
 
-def test_mixed_path_drift_and_batch(dq, orc):
+@pytest.mark.parametrize("precision", ["mixed", "mixed_tc"])
+def test_mixed_path_drift_and_batch(dq, orc, precision):
     """Batched uneven chains on the mixed path: each chain follows its FP64 oracle
     chain, and the wrapped G stays within 1e-6 of the fresh G (precision monitor)."""
     models = [square(8, U=4.0, L=40, nw=10), square(4, U=6.0, L=20, nw=10),
               W.ModelSpec(W.honeycomb_lattice(3, 3), U=4.0, dtau=0.1, L=20, n_wrap=10)]
     cm = [0, 1, 2, 0]
     seed = 5
-    ens = dq.Ensemble(models, cm, precision="mixed", delay_k=16, seed=seed)
+    ens = dq.Ensemble(models, cm, precision=precision, delay_k=16, seed=seed)
     f0, _ = ens.get_fields()
     ochs = [orc.Chain(omodel(orc, models[cm[c]]), f0[c], seed=seed, chain=c) for c in range(len(cm))]
     st = ens.sweep(2)
