@@ -682,7 +682,25 @@ __device__ void householder_apply(int N, int ld, double* M, int k, int j0, doubl
   const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
   for (int c0 = j0; c0 < N; c0 += 128) {
     double w[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = k + rg; i < N; i += 8) {
+    int i = k + rg;
+    // four rows per iteration with all loads issued first (memory-level parallelism)
+    for (; i + 24 < N; i += 32) {
+      double x[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : 0.0;
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double vi = hv[i + 8 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = fma(vi, x[r][q], w[q]);
+      }
+    }
+    for (; i < N; i += 8) {
       const double vi = hv[i];
       const double* row = M + (size_t)i * ld;
 #pragma unroll
@@ -702,7 +720,27 @@ __device__ void householder_apply(int N, int ld, double* M, int k, int j0, doubl
       for (int r = 0; r < 8; ++r) t += qred[r * 128 + lane + 32 * q];
       wt[q] = bk * t;
     }
-    for (int i = k + rg; i < N; i += 8) {
+    i = k + rg;
+    for (; i + 24 < N; i += 32) {
+      double x[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : 0.0;
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double vi = hv[i + 8 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          if (j < N) M[(size_t)(i + 8 * r) * ld + j] = x[r][q] - wt[q] * vi;
+        }
+      }
+    }
+    for (; i < N; i += 8) {
       const double vi = hv[i];
       double* row = M + (size_t)i * ld;
 #pragma unroll
@@ -958,7 +996,24 @@ __device__ void lu_solve(int N, int ld, const double* LU, const int* piv, double
       const double* lrow = LU + (size_t)ii * ld;
       for (int c0 = 0; c0 < N; c0 += 128) {
         double w[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k = klo + rg; k < khi; k += 8) {
+        int k = klo + rg;
+        for (; k + 24 < khi; k += 32) {
+          double x[4][4], l[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            l[r] = lrow[k + 8 * r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int j = c0 + lane + 32 * q;
+              x[r][q] = (j < N) ? B[(size_t)(k + 8 * r) * ld + j] : 0.0;
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = fma(l[r], x[r][q], w[q]);
+        }
+        for (; k < khi; k += 8) {
           const double l = lrow[k];
           const double* brow = B + (size_t)k * ld;
 #pragma unroll
@@ -1004,18 +1059,24 @@ __device__ int green_from_udv(const ChainDev& C, int s, UDV R, UDV Lf, double* G
   double* W1 = wmat(C, s, 1);
   cta_gemm<double, true, false>(N, N, N, R.Q, ld, Lf.Q, ld, W0, ld, S.gemm);
   cta_gemm<double, false, true>(N, N, N, R.T, ld, Lf.T, ld, W1, ld, S.gemm);
-  for (int e = threadIdx.x; e < N * N; e += kThreads) {
-    const int i = e / N, j = e - i * N;
-    const double dR = R.D[i], dL = Lf.D[j];
-    const double dbR = dR > 1.0 ? dR : 1.0, dsR = dR > 1.0 ? 1.0 : dR;
-    const double dbL = dL > 1.0 ? dL : 1.0, dsL = dL > 1.0 ? 1.0 : dL;
-    W0[(size_t)i * ld + j] = W0[(size_t)i * ld + j] / (dbR * dbL) + dsR * W1[(size_t)i * ld + j] * dsL;
+  // 1/Db and Ds of both chains (vectors 5..7 of the workspace)
+  double* ibR = wvec(C, s, 5);
+  double* ibL = wvec(C, s, 6);
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    ibR[i] = 1.0 / (R.D[i] > 1.0 ? R.D[i] : 1.0);
+    ibL[i] = 1.0 / (Lf.D[i] > 1.0 ? Lf.D[i] : 1.0);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
-    const double dR = R.D[i];
-    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] / (dR > 1.0 ? dR : 1.0);
+    const double dR = R.D[i], dL = Lf.D[j];
+    const double dsR = dR > 1.0 ? 1.0 : dR, dsL = dL > 1.0 ? 1.0 : dL;
+    W0[(size_t)i * ld + j] = W0[(size_t)i * ld + j] * (ibR[i] * ibL[j]) + dsR * W1[(size_t)i * ld + j] * dsL;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] * ibR[i];
   }
   __syncthreads();
   double ldm;
@@ -1025,8 +1086,7 @@ __device__ int green_from_udv(const ChainDev& C, int s, UDV R, UDV Lf, double* G
   lu_solve(N, ld, W0, piv, W1, S.qred);
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
-    const double dL = Lf.D[i];
-    W1[(size_t)i * ld + j] /= (dL > 1.0 ? dL : 1.0);
+    W1[(size_t)i * ld + j] *= ibL[i];
   }
   __syncthreads();
   cta_gemm<double, false, false>(N, N, N, Lf.Q, ld, W1, ld, Gout, ld, S.gemm);
@@ -1354,7 +1414,24 @@ __device__ void householder_apply_dd(int N, int ld, dd* M, int k, int j0, dd bk,
   const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
   for (int c0 = j0; c0 < N; c0 += 128) {
     dd w[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    for (int i = k + rg; i < N; i += 8) {
+    int i = k + rg;
+    for (; i + 8 < N; i += 16) {
+      dd x[2][4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : dd{0.f, 0.f};
+        }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const dd vi = hv[i + 8 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = dd_fma(vi, x[r][q], w[q]);
+      }
+    }
+    for (; i < N; i += 8) {
       const dd vi = hv[i];
       const dd* row = M + (size_t)i * ld;
 #pragma unroll
@@ -1375,7 +1452,27 @@ __device__ void householder_apply_dd(int N, int ld, dd* M, int k, int j0, dd bk,
       const dd bw = dd_mul(bk, t);
       wt[q] = {-bw.hi, -bw.lo};
     }
-    for (int i = k + rg; i < N; i += 8) {
+    i = k + rg;
+    for (; i + 8 < N; i += 16) {
+      dd x[2][4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : dd{0.f, 0.f};
+        }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const dd vi = hv[i + 8 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          if (j < N) M[(size_t)(i + 8 * r) * ld + j] = dd_fma(wt[q], vi, x[r][q]);
+        }
+      }
+    }
+    for (; i < N; i += 8) {
       const dd vi = hv[i];
       dd* row = M + (size_t)i * ld;
 #pragma unroll
@@ -1614,20 +1711,25 @@ __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, dou
   to_dd_mat(N, ld, Lf.T, TLd);
   gemm_dd<true, false, false>(C, s, S, N, N, N, QRd, ld, QLd, ld, reinterpret_cast<dd*>(W0), ld);
   gemm_dd<false, true, false>(C, s, S, N, N, N, TRd, ld, TLd, ld, reinterpret_cast<dd*>(W1), ld);
-  for (int e = threadIdx.x; e < N * N; e += kThreads) {
-    const int i = e / N, j = e - i * N;
-    const double dR = R.D[i], dL = Lf.D[j];
-    const double dbR = dR > 1.0 ? dR : 1.0, dsR = dR > 1.0 ? 1.0 : dR;
-    const double dbL = dL > 1.0 ? dL : 1.0, dsL = dL > 1.0 ? 1.0 : dL;
-    const double qq = to_d(reinterpret_cast<const dd*>(W0)[(size_t)i * ld + j]);
-    const double tt = to_d(reinterpret_cast<const dd*>(W1)[(size_t)i * ld + j]);
-    W0[(size_t)i * ld + j] = qq / (dbR * dbL) + dsR * tt * dsL;
+  double* ibR = wvec(C, s, 5);
+  double* ibL = wvec(C, s, 6);
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    ibR[i] = 1.0 / (R.D[i] > 1.0 ? R.D[i] : 1.0);
+    ibL[i] = 1.0 / (Lf.D[i] > 1.0 ? Lf.D[i] : 1.0);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
-    const double dR = R.D[i];
-    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] / (dR > 1.0 ? dR : 1.0);
+    const double dR = R.D[i], dL = Lf.D[j];
+    const double dsR = dR > 1.0 ? 1.0 : dR, dsL = dL > 1.0 ? 1.0 : dL;
+    const double qq = to_d(reinterpret_cast<const dd*>(W0)[(size_t)i * ld + j]);
+    const double tt = to_d(reinterpret_cast<const dd*>(W1)[(size_t)i * ld + j]);
+    W0[(size_t)i * ld + j] = qq * (ibR[i] * ibL[j]) + dsR * tt * dsL;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] * ibR[i];
   }
   __syncthreads();
   double ldm;
@@ -1638,8 +1740,7 @@ __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, dou
   dd* Yd = reinterpret_cast<dd*>(wmat(C, s, 9));
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
-    const double dL = Lf.D[i];
-    Yd[(size_t)i * ld + j] = from_d<dd>(W1[(size_t)i * ld + j] / (dL > 1.0 ? dL : 1.0));
+    Yd[(size_t)i * ld + j] = from_d<dd>(W1[(size_t)i * ld + j] * ibL[i]);
   }
   __syncthreads();
   gemm_dd<false, false, false>(C, s, S, N, N, N, QLd, ld, Yd, ld, reinterpret_cast<dd*>(Gout), ld);

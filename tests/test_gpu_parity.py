@@ -160,9 +160,10 @@ def test_fp32_path_green_after_sweeps(dq, orc):
 @pytest.mark.parametrize("precision", ["mixed", "mixed_tc"])
 @pytest.mark.parametrize("ft", [1, 2])
 def test_sweep_trajectory_mixed(dq, orc, ft, precision):
-    """Mixed path (float-pair G, FP64 stabilisation): the ratios agree with FP64 to
-    ~1e-13 relative, so every accept/reject decision and every field matches the
-    oracle's trajectory, and G after each sweep matches to 1e-10."""
+    """Mixed paths (float-pair G and stabilisation products, FP64 scales and LU): the
+    ratios agree with FP64 to ~1e-12 relative, so every accept/reject decision and
+    every field matches the oracle's trajectory; G after each sweep matches to the
+    float-pair round-off times the conditioning (bar 1e-7, reduced-precision target 1e-6)."""
     m = square(4, U=4.0, L=20, nw=10, ft=ft)
     seed = 20170401
     ens = dq.Ensemble([m], [0], precision=precision, delay_k=16, seed=seed)
@@ -196,7 +197,9 @@ def test_mixed_path_drift_and_batch(dq, orc, precision):
     for c, och in enumerate(ochs):
         assert np.array_equal(fg[c], och.fields()[0]), c
         for s in (0, 1):
-            assert np.abs(ens.greens(c, s)[0] - och.green(s)).max() < 1e-10
+            # float-pair stabilisation products and QR (unit round-off ~2^-44) times the
+            # conditioning of the middle matrix: ~1e-9 here; the reduced-precision bar is 1e-6
+            assert np.abs(ens.greens(c, s)[0] - och.green(s)).max() < 1e-7
     assert st["prec_green_max"] < 1e-6, st
 
 
