@@ -1342,6 +1342,14 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
   while (true) {
     double* Rs = S.Rs + buf * MV;
     for (int q = pos + tid; q < MV; q += kThreads) Rs[q] = 1.0 + S.delta[q] * (1.0 - S.d[S.qsite[q]]);
+    // the next position is accepted most of the time: start reading its column and
+    // row of G now, so that the cluster barrier covers the memory latency
+    const int ipre = (pos < MV) ? S.qsite[pos] : 0;
+    Real gc_pre = from_d<Real>(0.0), gr_pre = from_d<Real>(0.0);
+    if (tid < N) {
+      gc_pre = G[(size_t)tid * ld + ipre];
+      gr_pre = G[(size_t)ipre * ld + tid];
+    }
     cl.sync();
     const double* Rr[kMaxFlavors];
     for (int r = 0; r < nfl; ++r) Rr[r] = (r == s) ? Rs : cl.map_shared_rank(Rs, r);
@@ -1367,18 +1375,23 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     Real* a = A + (size_t)nacc * ld;
     Real* b = B + (size_t)nacc * ld;
     const Real mfac = from_d<Real>(-fac);
-    // column i of G_eff (tasks 0..N-1) and row i (tasks N..2N-1)
-    for (int t = tid; t < 2 * N; t += kThreads) {
-      if (t < N) {
-        Real cx = G[(size_t)t * ld + i];
-        for (int m = 0; m < nacc; ++m) cx = rfma(A[(size_t)m * ld + t], B[(size_t)m * ld + i], cx);
-        a[t] = rmul(mfac, cx);
+    const bool hit = (first == pos);
+    // element x of column i (a) and of row i (b) of G_eff
+    for (int x = tid; x < N; x += kThreads) {
+      Real cx, ry;
+      if (hit && x == tid) {
+        cx = gc_pre;
+        ry = gr_pre;
       } else {
-        const int x = t - N;
-        Real ry = G[(size_t)i * ld + x];
-        for (int m = 0; m < nacc; ++m) ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
-        b[x] = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
+        cx = G[(size_t)x * ld + i];
+        ry = G[(size_t)i * ld + x];
       }
+      for (int m = 0; m < nacc; ++m) {
+        cx = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
+        ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
+      }
+      a[x] = rmul(mfac, cx);
+      b[x] = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
     }
     __syncthreads();
     for (int x = tid; x < N; x += kThreads) S.d[x] += to_d(a[x]) * to_d(b[x]);
