@@ -199,6 +199,28 @@ def run_reference(args, wl: W.Workload, rank: int):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- rank helpers
+def rank_seed(rank: int) -> int:
+    """Each rank runs its own independent chains (the paper's one walker per task)."""
+    return W.BASE_SEED + rank
+
+
+def max_over_ranks(ms: float, device="cuda") -> float:
+    """The slowest rank sets the time of a step (the only collective, outside the data path)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(proposals_per_step: int, world: int, ms_step: float) -> float:
+    """Proposals of all ranks per second of the slowest rank."""
+    return proposals_per_step * world / (ms_step / 1000.0)
+
+
 # ---------------------------------------------------------------------- ours
 FP64_PEAK_TF = 1.0994   # cuBLAS DGEMM measured on this GB300 (profiles/peaks_gb300_measured.md)
 FP32_PEAK_TF = 69.83    # cuBLAS SGEMM (FP32 SIMT) measured on the same part
@@ -234,14 +256,12 @@ def time_path(wl, precision, args, stream, seed, world, local_rank):
         torch.cuda.synchronize()
     ms_total = t_start.elapsed_time(t_end)
     per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_total = max_over_ranks(ms_total)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
         dist.barrier()
     ms_step = ms_total / args.steps
-    value = wl.proposals_per_sweep() * world / (ms_step / 1000.0)
+    value = whole_job_value(wl.proposals_per_sweep(), world, ms_step)
     avg_launch_s = statistics.mean(per_launch_ms) / 1000.0
     achieved = flops_per_step / avg_launch_s / 1e12
     if precision == "fp64":
@@ -308,7 +328,7 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
     build_ext.build()
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
-    seed = W.BASE_SEED + rank
+    seed = rank_seed(rank)
     main_prec = args.precision
     r = time_path(wl, main_prec, args, stream, seed, world, local_rank)
     ens, st = r["ens"], r["st"]

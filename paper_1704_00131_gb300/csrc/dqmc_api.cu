@@ -217,6 +217,9 @@ dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
     symmetric_eigen(N, Kf, M.eigval[f], M.eigvec[f]);
     const std::vector<double> Ef = expm_symmetric(N, M.eigval[f], M.eigvec[f], -d.dtau);
     const std::vector<double> Eif = expm_symmetric(N, M.eigval[f], M.eigvec[f], +d.dtau);
+    for (size_t q = 0; q < Ef.size(); ++q)
+      if (!std::isfinite(Ef[q]) || !std::isfinite(Eif[q]))
+        return fail(ctx, DQMC_EINVAL, "exp(-+dtau K) of flavor %d is not finite (dtau * |K| too large)", f);
     for (int i = 0; i < N; ++i)
       for (int j = 0; j < N; ++j) {
         const size_t o = (size_t)f * N * ld + (size_t)i * ld + j;

@@ -348,3 +348,51 @@ def test_invalid_arguments_are_rejected(dq):
     ens = dq.Ensemble([m], [0])
     with pytest.raises(dq.DqmcError):
         ens.greens(5, 0)
+
+
+# ------------------------------------------------------- failure handling
+def test_unstable_threshold_reports_eunstable(dq):
+    """The precision monitor turns an excursion above the user threshold into DQMC_EUNSTABLE."""
+    m = square(4, U=6.0, L=20, nw=10)
+    ens = dq.Ensemble([m], [0], precision="fp32", unstable_threshold=1e-30, seed=3)
+    with pytest.raises(dq.DqmcError) as e:
+        ens.sweep(1)
+    assert e.value.status == dq.DQMC_EUNSTABLE
+    # the context stays usable: a second sweep runs and reports the same way
+    with pytest.raises(dq.DqmcError):
+        ens.sweep(1)
+
+
+def test_non_finite_propagator_rejected(dq):
+    K = 1.0e5 * W.square_lattice(2, 2)
+    with pytest.raises(dq.DqmcError) as e:
+        dq.Ensemble([W.ModelSpec(K, U=2.0, dtau=0.1, L=4, n_wrap=2)], [0])
+    assert e.value.status == dq.DQMC_EINVAL
+
+
+# ------------------------------------------------- the sampler against ED
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gpu_sampler_matches_exact_diagonalisation(dq, precision):
+    """64 independent GPU chains on the 2x2 Hubbard plaquette: Kin and Pot from the
+    library's own measurements agree with the Fock-space trace of the Trotterised
+    density matrix within 3 sigma (errors from the spread over chains)."""
+    from tests.fock_ed import Fock
+    K = W.square_lattice(2, 2, t=1.0)
+    U, dtau, L = 4.0, 0.125, 8
+    m = W.ModelSpec(K, U=U, dtau=dtau, L=L, n_wrap=4)
+    F = Fock(4)
+    rho = F.trotter_ising(K, U, dtau, L)
+    Z = np.trace(rho)
+    kin_ed = np.trace(F.hopping(K) @ rho) / Z
+    pot_ed = np.trace(F.hubbard_nn(U) @ rho) / Z
+    n = 64
+    ens = dq.Ensemble([m], [0] * n, precision=precision, seed=2024, measure=True, meas_first=0, meas_last=L)
+    ens.sweep(20, stats=False)
+    m0, s0, n0 = ens.measure()
+    ens.sweep(300, stats=False)
+    m1, s1, n1 = ens.measure()
+    per_chain = (m1 - m0) / (n1 - n0)[:, None]
+    for q, ref in ((0, kin_ed), (1, pot_ed)):
+        x = per_chain[:, q]
+        mean, err = x.mean(), x.std(ddof=1) / np.sqrt(n)
+        assert abs(mean - ref) < 3 * err + 1e-12, (q, mean, err, ref)
