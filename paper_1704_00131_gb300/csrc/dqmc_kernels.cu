@@ -437,18 +437,42 @@ __device__ void gemm_tc(int M, int Nc, int Kd, const dd* __restrict__ A, int lda
   __nv_bfloat16* PB = planes + (size_t)kDig * Mp * Kp;
   const size_t sA = (size_t)Mp * Kp, sB = (size_t)Np * Kp;
   const int tid = threadIdx.x;
-  // scale exponents: rows of op(A), columns of op(B)
-  for (int m = tid; m < Mp; m += kThreads) {
-    float amax = 0.f;
-    if (m < M)
-      for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(TA ? A[(size_t)k * lda + m].hi : A[(size_t)m * lda + k].hi));
-    expA[m] = tc_exponent(amax);
+  // scale exponents: rows of op(A), columns of op(B); a warp per contiguous row,
+  // a thread per strided column, so that every read is coalesced
+  const int warp_id = tid >> 5, lane_id = tid & 31;
+  if (!TA) {
+    for (int m = warp_id; m < Mp; m += kThreads / 32) {
+      float amax = 0.f;
+      if (m < M)
+        for (int k = lane_id; k < Kd; k += 32) amax = fmaxf(amax, fabsf(A[(size_t)m * lda + k].hi));
+#pragma unroll
+      for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if (lane_id == 0) expA[m] = tc_exponent(amax);
+    }
+  } else {
+    for (int m = tid; m < Mp; m += kThreads) {
+      float amax = 0.f;
+      if (m < M)
+        for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(A[(size_t)k * lda + m].hi));
+      expA[m] = tc_exponent(amax);
+    }
   }
-  for (int n = tid; n < Np; n += kThreads) {
-    float amax = 0.f;
-    if (n < Nc)
-      for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(TB ? B[(size_t)n * ldb + k].hi : B[(size_t)k * ldb + n].hi));
-    expB[n] = tc_exponent(amax);
+  if (TB) {
+    for (int n = warp_id; n < Np; n += kThreads / 32) {
+      float amax = 0.f;
+      if (n < Nc)
+        for (int k = lane_id; k < Kd; k += 32) amax = fmaxf(amax, fabsf(B[(size_t)n * ldb + k].hi));
+#pragma unroll
+      for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if (lane_id == 0) expB[n] = tc_exponent(amax);
+    }
+  } else {
+    for (int n = tid; n < Np; n += kThreads) {
+      float amax = 0.f;
+      if (n < Nc)
+        for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(B[(size_t)k * ldb + n].hi));
+      expB[n] = tc_exponent(amax);
+    }
   }
   __syncthreads();
   // digit planes: PA[t][m][k], PB[t][n][k] (k contiguous), zero padded
@@ -479,21 +503,24 @@ __device__ void gemm_tc(int M, int Nc, int Kd, const dd* __restrict__ A, int lda
             for (int q = 0; q < 4; ++q) acc[d][q] = 0.f;
           const int ke = min(Kp, ks + kKSeg);
           for (int k0 = ks; k0 < ke; k0 += 16) {
+            // all fragments of this k-step first, then the 28 digit-pair products
+            uint32_t af[kDig][4], bf[kDig][2];
 #pragma unroll
             for (int t = 0; t < kDig; ++t) {
               const __nv_bfloat16* pa = PA + (size_t)t * sA + (size_t)(r0 + g) * Kp + k0 + 2 * cq;
-              const uint32_t a0 = *reinterpret_cast<const uint32_t*>(pa);
-              const uint32_t a1 = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp);
-              const uint32_t a2 = *reinterpret_cast<const uint32_t*>(pa + 8);
-              const uint32_t a3 = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp + 8);
-#pragma unroll
-              for (int u = 0; t + u < kDig; ++u) {
-                const __nv_bfloat16* pb = PB + (size_t)u * sB + (size_t)(c0 + g) * Kp + k0 + 2 * cq;
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(pb);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(pb + 8);
-                mma_bf16_16816(acc[t + u], a0, a1, a2, a3, b0, b1);
-              }
+              af[t][0] = *reinterpret_cast<const uint32_t*>(pa);
+              af[t][1] = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp);
+              af[t][2] = *reinterpret_cast<const uint32_t*>(pa + 8);
+              af[t][3] = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp + 8);
+              const __nv_bfloat16* pb = PB + (size_t)t * sB + (size_t)(c0 + g) * Kp + k0 + 2 * cq;
+              bf[t][0] = *reinterpret_cast<const uint32_t*>(pb);
+              bf[t][1] = *reinterpret_cast<const uint32_t*>(pb + 8);
             }
+#pragma unroll
+            for (int t = 0; t < kDig; ++t)
+#pragma unroll
+              for (int u = 0; t + u < kDig; ++u)
+                mma_bf16_16816(acc[t + u], af[t][0], af[t][1], af[t][2], af[t][3], bf[u][0], bf[u][1]);
           }
           // recombine the digit diagonals of this segment and add into C
 #pragma unroll
