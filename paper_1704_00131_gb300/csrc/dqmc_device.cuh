@@ -1,0 +1,2027 @@
+// GB300 (sm_103a) kernels of the BSS/DQMC sweep.
+//
+// Work decomposition: one thread-block cluster per Markov chain, one CTA per
+// flavor (spin up / spin down of the spin-z decoupling).  The flavors are
+// independent except in the acceptance ratio R = gamma * prod_s R_s, which the
+// CTAs exchange through distributed shared memory; every other step (wraps,
+// delayed updates, the FP64 QR/UDV stabilisation, the stable recompute of G)
+// runs in the flavor's own CTA.
+//
+// Precision: the working Green function, the wraps and the delayed updates are
+// templated on `Real` (double for the plain FP64 path, float for the mixed
+// path); the stabilisation chain (B-products, pivoted QR, T update, the stable
+// (1 + UDV)^-1 and log|det|) is always FP64.
+//
+// Method (ALF 1.0 documentation, arXiv:1704.00131):
+//   B_tau = exp(-dtau K) exp(V_tau)                       Sec. 2.1, Eq. of B_tau
+//   G(tau) = (1 + B(tau,0) B(beta,tau))^-1               Eq. Green_eq
+//   sequential single-field updates, Metropolis         Sec. 2.2.1
+//   QR-stabilised chain every n_wrap slices             Sec. 2.3, Eq. green_stable
+//   sweep: tau = 1..L up, L..1 down                     Algorithm 1, Sec. 2.4
+#pragma once
+//
+// This header holds the device code shared by the kernel translation units:
+// the per-precision sweep units (dqmc_sweep_fp64.cu, dqmc_sweep_fp32.cu,
+// dqmc_sweep_mixed.cu) instantiate the sweep and fresh-G kernels for one
+// working precision each, so that nvcc compiles them in parallel;
+// dqmc_kernels.cu holds the precision-independent kernels and the dispatch.
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <type_traits>
+
+#include "../../include/dqmc.h"
+#include "dqmc_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace dqmc {
+// Internal linkage: every translation unit that includes this header gets its
+// own copy of the device code it instantiates.
+namespace {
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): the counter-based generator that
+// draws the proposal (u1) and acceptance (u2) uniforms of every proposal.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
+__device__ __forceinline__ double uniform53(uint32_t hi, uint32_t lo) {
+  const uint64_t w = ((uint64_t)hi << 32) | lo;
+  return (double)(w >> 11) * 0x1.0p-53;
+}
+
+// Sub-phase cycle counter: thread 0 adds the cycles since *t0 to acc[q].
+__device__ __forceinline__ void tick(long long* acc, int q, long long& t0) {
+  const long long t1 = clock64();
+  if (acc && threadIdx.x == 0) acc[q] += t1 - t0;
+  t0 = t1;
+}
+
+// --------------------------------------------------------------------------
+// Field couplings: Ising (type 1) c(s) = lambda s; four-valued HS (type 2)
+// c(l) = g eta(l) with weight gamma(l) (Sec. 2.1, the discrete HS transform).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double hs_eta(int l) {
+  const double a = sqrt(2.0 * (3.0 - sqrt(6.0))), b = sqrt(2.0 * (3.0 + sqrt(6.0)));
+  return l == 1 ? a : l == -1 ? -a : l == 2 ? b : -b;
+}
+__device__ __forceinline__ double hs_gamma(int l) {
+  return (l == 1 || l == -1) ? 1.0 + sqrt(6.0) / 3.0 : 1.0 - sqrt(6.0) / 3.0;
+}
+__device__ __forceinline__ double coupling(int ft, double cscale, int f) {
+  return ft == 1 ? cscale * (double)f : cscale * hs_eta(f);
+}
+__device__ __forceinline__ double field_weight(int ft, int f) { return ft == 1 ? 1.0 : hs_gamma(f); }
+// Proposal: Ising flips; HS picks one of the three other values of
+// (-2,-1,1,2), in ascending order, with index floor(3 u1).
+__device__ __forceinline__ int propose_field(int ft, int f, double u1) {
+  if (ft == 1) return -f;
+  int idx = (int)floor(3.0 * u1);
+  idx = idx > 2 ? 2 : idx;
+  const int vals[4] = {-2, -1, 1, 2};
+  int n = 0, out = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (vals[q] != f) {
+      if (n == idx) out = vals[q];
+      ++n;
+    }
+  return out;
+}
+__device__ __forceinline__ double coupling_dU(int ft, double dtau, double U, double cscale, int f) {
+  if (ft == 1) return 0.5 * dtau * exp(0.5 * dtau * U) / sinh(cscale) * (double)f;
+  return dtau / (4.0 * cscale) * hs_eta(f);
+}
+
+// --------------------------------------------------------------------------
+// Block-wide reductions (deterministic order).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) r += red[w];
+  return r;
+}
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = red[0];
+#pragma unroll
+  for (int w = 1; w < kThreads / 32; ++w) r = fmax(r, red[w]);
+  return r;
+}
+__device__ __forceinline__ int block_min_int(int v, int* ired) {
+  v = __reduce_min_sync(0xffffffffu, v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) ired[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int r = ired[0];
+#pragma unroll
+  for (int w = 1; w < kThreads / 32; ++w) r = min(r, ired[w]);
+  return r;
+}
+// argmax of v over the block, ties to the lowest index; returns the index.
+__device__ __forceinline__ int block_argmax(double v, int idx, double* red, int* ired) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = v; ired[threadIdx.x >> 5] = idx; }
+  __syncthreads();
+  double bv = red[0];
+  int bi = ired[0];
+#pragma unroll
+  for (int w = 1; w < kThreads / 32; ++w)
+    if (red[w] > bv || (red[w] == bv && ired[w] < bi)) { bv = red[w]; bi = ired[w]; }
+  return bi;
+}
+
+// --------------------------------------------------------------------------
+// Float-float ("double-word") numbers: x = hi + lo with |lo| <= ulp(hi)/2,
+// about 48 significant bits on the FP32 pipes, which run 64x faster than FP64
+// on this GPU.  Error-free transformations: TwoSum (Knuth), FastTwoSum
+// (Dekker), TwoProd with an FMA (Joldes, Muller, Popescu, ACM TOMS 2017).
+// The working Green function of the mixed path is stored in this format.
+// --------------------------------------------------------------------------
+struct dd {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dd two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dd fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  const dd s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return fast_two_sum(p, e);
+}
+// c + a * b
+__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  const dd s = two_sum(c.hi, p);
+  return fast_two_sum(s.hi, s.lo + (c.lo + e));
+}
+
+// Arithmetic adapters of the working precision (double, float, dd).
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(dd x) { return (double)x.hi + (double)x.lo; }
+template <typename R>
+__device__ __forceinline__ R from_d(double x);
+template <>
+__device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+template <>
+__device__ __forceinline__ dd from_d<dd>(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ dd rfma(dd a, dd b, dd c) { return dd_fma(a, b, c); }
+__device__ __forceinline__ double rmul(double a, double b) { return a * b; }
+__device__ __forceinline__ float rmul(float a, float b) { return a * b; }
+__device__ __forceinline__ dd rmul(dd a, dd b) { return dd_mul(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return a - b; }
+__device__ __forceinline__ float rsub(float a, float b) { return a - b; }
+__device__ __forceinline__ dd rsub(dd a, dd b) { return dd_add(a, {-b.hi, -b.lo}); }
+
+// --------------------------------------------------------------------------
+// CTA-level dense product C = op(A) op(B), row-major, generic pointers
+// (global or shared).  Output tiles of 16R x 16R (R = 3, 4, 5 outputs per
+// thread and dimension; R is picked per size so that N = 144 or 400 need no
+// padding), 16-deep K panels staged in shared memory.  C must not alias A or B.
+// --------------------------------------------------------------------------
+constexpr int kGemmMaxTile = 80;  // 16 * 5
+
+__host__ __device__ inline int gemm_pick_r(int n) {
+  int best_r = 4, best = 1 << 30;
+  for (int r = 5; r >= 3; --r) {
+    const int t = 16 * r;
+    const int padded = ((n + t - 1) / t) * t;
+    if (padded < best) { best = padded; best_r = r; }
+  }
+  return best_r;
+}
+
+template <typename T, bool TA, bool TB, int R, bool ACC = false>
+__device__ void cta_gemm_r(int M, int Nc, int Kd, const T* __restrict__ A, int lda, const T* __restrict__ B,
+                           int ldb, T* __restrict__ C, int ldc, T* sm) {
+  constexpr int TT = 16 * R;
+  T* As = sm;            // [16][TT]
+  T* Bs = sm + 16 * TT;  // [16][TT]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += TT)
+    for (int n0 = 0; n0 < Nc; n0 += TT) {
+      T acc[R][R];
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[i][j] = T(0);
+      for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+        for (int e = tid; e < 16 * TT; e += kThreads) {
+          int r, kk;
+          if (!TA) { r = e >> 4; kk = e & 15; } else { kk = e / TT; r = e - kk * TT; }
+          const int gm = m0 + r, gk = k0 + kk;
+          T val = T(0);
+          if (gm < M && gk < Kd) val = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+          As[kk * TT + r] = val;
+        }
+#pragma unroll
+        for (int e = tid; e < 16 * TT; e += kThreads) {
+          int kk, c;
+          if (!TB) { kk = e / TT; c = e - kk * TT; } else { c = e >> 4; kk = e & 15; }
+          const int gk = k0 + kk, gn = n0 + c;
+          T val = T(0);
+          if (gk < Kd && gn < Nc) val = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+          Bs[kk * TT + c] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          T a[R], b[R];
+#pragma unroll
+          for (int i = 0; i < R; ++i) a[i] = As[kk * TT + ty * R + i];
+#pragma unroll
+          for (int j = 0; j < R; ++j) b[j] = Bs[kk * TT + tx * R + j];
+#pragma unroll
+          for (int i = 0; i < R; ++i)
+#pragma unroll
+            for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int gm = m0 + ty * R + i, gn = n0 + tx * R + j;
+          if (gm < M && gn < Nc) {
+            if (ACC) C[(size_t)gm * ldc + gn] += acc[i][j];
+            else C[(size_t)gm * ldc + gn] = acc[i][j];
+          }
+        }
+    }
+  __syncthreads();
+}
+
+template <typename T, bool TA, bool TB>
+__device__ void cta_gemm(int M, int Nc, int Kd, const T* __restrict__ A, int lda, const T* __restrict__ B,
+                         int ldb, T* __restrict__ C, int ldc, T* sm) {
+  const int r = gemm_pick_r(M > Nc ? M : Nc);
+  if (r == 3) cta_gemm_r<T, TA, TB, 3>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+  else if (r == 5) cta_gemm_r<T, TA, TB, 5>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+  else cta_gemm_r<T, TA, TB, 4>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+}
+
+// The same tiling for float-float operands: every product hi*hi is split
+// exactly (TwoProd), its high part summed with TwoSum into the accumulator's
+// high word, the rounding errors and the hi*lo, lo*hi cross terms gathered in
+// the low word and renormalised once per output.
+template <bool TA, bool TB, int R, bool ACC = false>
+__device__ void cta_gemm_dd_r(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B,
+                              int ldb, dd* __restrict__ C, int ldc, dd* sm) {
+  constexpr int TT = 16 * R;
+  dd* As = sm;            // [16][TT]
+  dd* Bs = sm + 16 * TT;  // [16][TT]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < M; m0 += TT)
+    for (int n0 = 0; n0 < Nc; n0 += TT) {
+      float ah[R][R], al[R][R];
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) { ah[i][j] = 0.f; al[i][j] = 0.f; }
+      for (int k0 = 0; k0 < Kd; k0 += 16) {
+#pragma unroll
+        for (int e = tid; e < 16 * TT; e += kThreads) {
+          int r, kk;
+          if (!TA) { r = e >> 4; kk = e & 15; } else { kk = e / TT; r = e - kk * TT; }
+          const int gm = m0 + r, gk = k0 + kk;
+          dd val = {0.f, 0.f};
+          if (gm < M && gk < Kd) val = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+          As[kk * TT + r] = val;
+        }
+#pragma unroll
+        for (int e = tid; e < 16 * TT; e += kThreads) {
+          int kk, c;
+          if (!TB) { kk = e / TT; c = e - kk * TT; } else { c = e >> 4; kk = e & 15; }
+          const int gk = k0 + kk, gn = n0 + c;
+          dd val = {0.f, 0.f};
+          if (gk < Kd && gn < Nc) val = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+          Bs[kk * TT + c] = val;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+          dd a[R], b[R];
+#pragma unroll
+          for (int i = 0; i < R; ++i) a[i] = As[kk * TT + ty * R + i];
+#pragma unroll
+          for (int j = 0; j < R; ++j) b[j] = Bs[kk * TT + tx * R + j];
+#pragma unroll
+          for (int i = 0; i < R; ++i)
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              const float p = a[i].hi * b[j].hi;
+              const float pe = fmaf(a[i].hi, b[j].hi, -p);
+              const float s = ah[i][j] + p;
+              const float bb = s - ah[i][j];
+              const float se = (ah[i][j] - (s - bb)) + (p - bb);
+              ah[i][j] = s;
+              float lo = al[i][j] + (se + pe);
+              lo = fmaf(a[i].hi, b[j].lo, lo);
+              al[i][j] = fmaf(a[i].lo, b[j].hi, lo);
+            }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int gm = m0 + ty * R + i, gn = n0 + tx * R + j;
+          if (gm < M && gn < Nc) {
+            const dd r = fast_two_sum(ah[i][j], al[i][j]);
+            C[(size_t)gm * ldc + gn] = ACC ? dd_add(C[(size_t)gm * ldc + gn], r) : r;
+          }
+        }
+    }
+  __syncthreads();
+}
+
+
+// --------------------------------------------------------------------------
+// Exact-split BF16 tensor-core products for float-pair operands (the scheme of
+// Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 2012, on BF16 tensor cores).
+// Each row of op(A) and each column of op(B) is scaled by a power of two and
+// cut into kDig balanced 8-bit digits, x = 2^e sum_t q_t 2^-8(t+1), |q_t| <= 128,
+// each exactly a BF16 number.  Digit products are integers of at most 2^14;
+// the pairs (t,u) with t + u = d share one FP32 accumulator, exact as long as
+// (d + 1) K 2^14 <= 2^24, i.e. for K segments of at most 144.  The kDig
+// partial sums of a segment are recombined in float-float arithmetic and
+// scaled back.  Digits t + u >= kDig (relative weight 2^-64) are dropped.
+// Products run on mma.sync.m16n8k16 (BF16 in, FP32 accumulate); the digit
+// planes live in a per-CTA global scratch (L2-resident).
+// --------------------------------------------------------------------------
+constexpr int kDig = 7;
+constexpr int kKSeg = 144;
+
+__host__ __device__ inline int tc_pad(int n, int q) { return (n + q - 1) / q * q; }
+// bf16 elements of the digit planes of one CTA for sizes up to n and K up to kmax
+__host__ __device__ inline size_t tc_plane_elems(int n, int kmax) {
+  const int Kp = tc_pad(kmax, 16);
+  return (size_t)kDig * ((size_t)tc_pad(n, 64) + (size_t)tc_pad(n, 32)) * Kp;
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// |x| < 2^(e-1) for every element of a row or column whose largest |hi| is amax
+__device__ __forceinline__ int tc_exponent(float amax) { return amax > 0.f ? ilogbf(amax) + 2 : 0; }
+
+__device__ __forceinline__ void tc_digits(dd x, int e, __nv_bfloat16* out, size_t stride) {
+  float h = ldexpf(x.hi, -e), l = ldexpf(x.lo, -e);
+#pragma unroll
+  for (int t = 0; t < kDig; ++t) {
+    h *= 256.f;
+    l *= 256.f;
+    const float q = rintf(h);
+    out[(size_t)t * stride] = __float2bfloat16_rn(q);
+    const dd r = two_sum(h - q, l);
+    h = r.hi;
+    l = r.lo;
+  }
+}
+
+// C (+)= op(A) op(B), M x Nc, inner dimension Kd; float-pair operands.
+template <bool TA, bool TB, bool ACC>
+__device__ void gemm_tc(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B, int ldb,
+                        dd* __restrict__ C, int ldc, __nv_bfloat16* planes, int* expA, int* expB) {
+  const int Mp = tc_pad(M, 64), Np = tc_pad(Nc, 32), Kp = tc_pad(Kd, 16);
+  __nv_bfloat16* PA = planes;
+  __nv_bfloat16* PB = planes + (size_t)kDig * Mp * Kp;
+  const size_t sA = (size_t)Mp * Kp, sB = (size_t)Np * Kp;
+  const int tid = threadIdx.x;
+  // scale exponents: rows of op(A), columns of op(B); a warp per contiguous row,
+  // a thread per strided column, so that every read is coalesced
+  const int warp_id = tid >> 5, lane_id = tid & 31;
+  if (!TA) {
+    for (int m = warp_id; m < Mp; m += kThreads / 32) {
+      float amax = 0.f;
+      if (m < M)
+        for (int k = lane_id; k < Kd; k += 32) amax = fmaxf(amax, fabsf(A[(size_t)m * lda + k].hi));
+#pragma unroll
+      for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if (lane_id == 0) expA[m] = tc_exponent(amax);
+    }
+  } else {
+    for (int m = tid; m < Mp; m += kThreads) {
+      float amax = 0.f;
+      if (m < M)
+        for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(A[(size_t)k * lda + m].hi));
+      expA[m] = tc_exponent(amax);
+    }
+  }
+  if (TB) {
+    for (int n = warp_id; n < Np; n += kThreads / 32) {
+      float amax = 0.f;
+      if (n < Nc)
+        for (int k = lane_id; k < Kd; k += 32) amax = fmaxf(amax, fabsf(B[(size_t)n * ldb + k].hi));
+#pragma unroll
+      for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if (lane_id == 0) expB[n] = tc_exponent(amax);
+    }
+  } else {
+    for (int n = tid; n < Np; n += kThreads) {
+      float amax = 0.f;
+      if (n < Nc)
+        for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(B[(size_t)k * ldb + n].hi));
+      expB[n] = tc_exponent(amax);
+    }
+  }
+  __syncthreads();
+  // digit planes: PA[t][m][k], PB[t][n][k] (k contiguous), zero padded
+  for (size_t e = tid; e < sA; e += kThreads) {
+    const int m = (int)(e / Kp), k = (int)(e - (size_t)m * Kp);
+    dd x = {0.f, 0.f};
+    if (m < M && k < Kd) x = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+    tc_digits(x, expA[m], PA + e, sA);
+  }
+  for (size_t e = tid; e < sB; e += kThreads) {
+    const int n = (int)(e / Kp), k = (int)(e - (size_t)n * Kp);
+    dd x = {0.f, 0.f};
+    if (n < Nc && k < Kd) x = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+    tc_digits(x, expB[n], PB + e, sB);
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, cq = lane & 3;
+  const int wm = warp & 3, wn = warp >> 2;
+  for (int m0 = 0; m0 < Mp; m0 += 64)
+    for (int n0 = 0; n0 < Np; n0 += 32)
+      for (int nt = 0; nt < 2; ++nt) {
+        const int r0 = m0 + wm * 16, c0 = n0 + wn * 16 + nt * 8;
+        for (int ks = 0; ks < Kp; ks += kKSeg) {
+          float acc[kDig][4];
+#pragma unroll
+          for (int d = 0; d < kDig; ++d)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[d][q] = 0.f;
+          const int ke = min(Kp, ks + kKSeg);
+          for (int k0 = ks; k0 < ke; k0 += 16) {
+            // all fragments of this k-step first, then the 28 digit-pair products
+            uint32_t af[kDig][4], bf[kDig][2];
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) {
+              const __nv_bfloat16* pa = PA + (size_t)t * sA + (size_t)(r0 + g) * Kp + k0 + 2 * cq;
+              af[t][0] = *reinterpret_cast<const uint32_t*>(pa);
+              af[t][1] = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp);
+              af[t][2] = *reinterpret_cast<const uint32_t*>(pa + 8);
+              af[t][3] = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp + 8);
+              const __nv_bfloat16* pb = PB + (size_t)t * sB + (size_t)(c0 + g) * Kp + k0 + 2 * cq;
+              bf[t][0] = *reinterpret_cast<const uint32_t*>(pb);
+              bf[t][1] = *reinterpret_cast<const uint32_t*>(pb + 8);
+            }
+#pragma unroll
+            for (int t = 0; t < kDig; ++t)
+#pragma unroll
+              for (int u = 0; t + u < kDig; ++u)
+                mma_bf16_16816(acc[t + u], af[t][0], af[t][1], af[t][2], af[t][3], bf[u][0], bf[u][1]);
+          }
+          // recombine the digit diagonals of this segment and add into C
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = r0 + g + (q >= 2 ? 8 : 0);
+            const int j = c0 + 2 * cq + (q & 1);
+            if (i < M && j < Nc) {
+              dd sum = {0.f, 0.f};
+#pragma unroll
+              for (int d = kDig - 1; d >= 0; --d) sum = dd_add(sum, {ldexpf(acc[d][q], -8 * (d + 2)), 0.f});
+              const int e = expA[i] + expB[j];
+              sum.hi = ldexpf(sum.hi, e);
+              sum.lo = ldexpf(sum.lo, e);
+              dd* cp = C + (size_t)i * ldc + j;
+              *cp = (ACC || ks > 0) ? dd_add(*cp, sum) : sum;
+            }
+          }
+        }
+      }
+  __syncthreads();
+}
+
+template <bool TA, bool TB, bool ACC>
+__device__ void gemm_dd_tiles(int M, int Nc, int Kd, const dd* A, int lda, const dd* B, int ldb, dd* C, int ldc,
+                              dd* sm) {
+  const int n = M > Nc ? M : Nc;
+  const int p3 = (n + 47) / 48 * 48, p4 = (n + 63) / 64 * 64;
+  if (p3 < p4) cta_gemm_dd_r<TA, TB, 3, ACC>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+  else cta_gemm_dd_r<TA, TB, 4, ACC>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+}
+
+template <typename T>
+__device__ __forceinline__ void cta_copy(int N, int ld, const T* src, T* dst) {
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    dst[(size_t)x * ld + y] = src[(size_t)x * ld + y];
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------
+// Shared-memory layout of the sweep kernel.
+// --------------------------------------------------------------------------
+struct Smem {
+  double* gemm;     // 2*16*kGemmMaxTile doubles (also used by float / float-pair GEMMs)
+  double* v;        // [ld] slice potential / exp factors
+  double* ev;       // [ld]
+  double* d;        // [ld] current diagonal of the effective G
+  double* hv;       // [ld] Householder vector
+  double* u2;       // [MV]
+  double* delta;    // [MV]
+  double* gam;      // [MV]
+  double* Rs;       // [2][MV] own-flavor ratios, double buffered (read by the peer CTA)
+  double* Rp;       // [MV] full ratio of the position a thread found accepted
+  double* xdiag;    // [ld] exchange: diagonal of G for the potential energy
+  double* xs;       // [8]  exchange: scalars
+  double* red;      // [32]
+  int* ired;        // [32]
+  int* qsite;       // [MV]
+  int8_t* fnew;     // [MV]
+  int8_t* fslice;   // [MV] fields of the current slice
+  int* expA;        // [roundup(ld,64)] row exponents of the split tensor-core products
+  int* expB;        // [roundup(ld,64)] column exponents
+  double* ab;       // delayed vectors A, B [2][k][ld] when they fit in shared memory
+  int flavor;       // the CTA's flavor
+  double* qred;     // [8][128] partial sums of the QR trailing update
+};
+
+__host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
+  size_t b = 0;
+  b += 2 * 16 * kGemmMaxTile * 8;
+  b += 6 * (size_t)ld * 8;        // v, ev, d, hv, xdiag, spare
+  b += 6 * (size_t)MV * 8;        // u2, delta, gam, Rs[2], Rp
+  b += 8 * 8 + 32 * 8 + 32 * 4;   // xs, red, ired
+  b += (size_t)MV * 4;            // qsite
+  b += 2 * (size_t)MV + 16;       // fnew, fslice
+  b = (b + 15) / 16 * 16;
+  b += 8 * 128 * 8;               // qred
+  b += 2 * (size_t)((ld + 63) / 64 * 64) * 4;  // expA, expB
+  return b;
+}
+
+__device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
+  Smem s;
+  double* p = reinterpret_cast<double*>(base);
+  s.gemm = p; p += 2 * 16 * kGemmMaxTile;
+  s.v = p; p += ld;
+  s.ev = p; p += ld;
+  s.d = p; p += ld;
+  s.hv = p; p += ld;
+  s.xdiag = p; p += ld;
+  p += ld;
+  s.u2 = p; p += MV;
+  s.delta = p; p += MV;
+  s.gam = p; p += MV;
+  s.Rs = p; p += 2 * MV;
+  s.Rp = p; p += MV;
+  s.xs = p; p += 8;
+  s.red = p; p += 32;
+  int* ip = reinterpret_cast<int*>(p);
+  s.ired = ip; ip += 32;
+  s.qsite = ip; ip += MV;
+  int8_t* bp = reinterpret_cast<int8_t*>(ip);
+  s.fnew = bp; bp += MV;
+  s.fslice = bp; bp += MV + 16;
+  const size_t off = ((size_t)(bp - reinterpret_cast<int8_t*>(base)) + 15) / 16 * 16;
+  s.qred = reinterpret_cast<double*>(base + off);
+  const int le = (ld + 63) / 64 * 64;
+  s.expA = reinterpret_cast<int*>(s.qred + 8 * 128);
+  s.expB = s.expA + le;
+  s.ab = reinterpret_cast<double*>(s.expB + le);
+  return s;
+}
+
+// Float-pair product of the mixed path: exact-split tensor-core products when
+// the chain has digit-plane scratch, the float-pair SIMT tiles otherwise.
+template <bool TA, bool TB, bool ACC>
+__device__ void gemm_dd(const ChainDev& C, int s, Smem& S, int M, int Nc, int Kd, const dd* A, int lda, const dd* B,
+                        int ldb, dd* Cm, int ldc) {
+  if (C.planes[s])
+    gemm_tc<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, (__nv_bfloat16*)C.planes[s], S.expA, S.expB);
+  else
+    gemm_dd_tiles<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, reinterpret_cast<dd*>(S.gemm));
+}
+
+// Slice potential v^s_i of slice tau (1-based) from global fields.
+__device__ void slice_potential_global(const ChainDev& C, int s, int tau, double* v) {
+  for (int x = threadIdx.x; x < C.N; x += kThreads) v[x] = 0.0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < C.MV; k += kThreads)
+    v[C.site[k]] = C.vsign[s * C.MV + k] * coupling(C.ft, C.cscale, C.fields[(size_t)(tau - 1) * C.MV + k]);
+  __syncthreads();
+}
+
+// Slice potential from the shared-memory copy of the slice's fields.
+__device__ void slice_potential_smem(const ChainDev& C, int s, const int8_t* fsl, double* v) {
+  for (int x = threadIdx.x; x < C.N; x += kThreads) v[x] = 0.0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < C.MV; k += kThreads)
+    v[C.site[k]] = C.vsign[s * C.MV + k] * coupling(C.ft, C.cscale, fsl[k]);
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------
+// FP64 stabilisation building blocks (Sec. 2.3).
+// --------------------------------------------------------------------------
+struct UDV {
+  const double* Q;
+  const double* D;
+  const double* T;
+  int detq;
+};
+
+__device__ inline double* wmat(const ChainDev& C, int s, int m) {
+  return C.work[s] + (size_t)m * C.N * C.ld;
+}
+__device__ inline double* wvec(const ChainDev& C, int s, int v) {
+  return C.work[s] + (size_t)kWorkMats * C.N * C.ld + (size_t)v * C.ld;
+}
+__device__ inline UDV ident_udv(const ChainDev& C) {
+  UDV u;
+  u.Q = C.ident;
+  u.T = C.ident + (size_t)C.N * C.ld;
+  u.D = C.ident + (size_t)2 * C.N * C.ld;
+  u.detq = 1;
+  return u;
+}
+__device__ inline double* slot_base(const ChainDev& C, int s, int j) {
+  return C.slots[s] + (size_t)j * slot_stride(C.N, C.ld);
+}
+__device__ inline UDV slot_udv(const ChainDev& C, int s, int j) {
+  UDV u;
+  double* b = slot_base(C, s, j);
+  u.Q = b;
+  u.T = b + (size_t)C.N * C.ld;
+  u.D = b + (size_t)2 * C.N * C.ld;
+  u.detq = C.slot_detq[s][j];
+  return u;
+}
+
+// M[k:, j] -= bk v (v^T M[k:, j]) for the columns j0 <= j < N, v = hv[k:].
+// 8 row groups x 32 columns: rows are read coalesced along j; the partial dot
+// products of the row groups are summed in shared memory in a fixed order.
+__device__ void householder_apply(int N, int ld, double* M, int k, int j0, double bk, const double* hv,
+                                  double* qred) {
+  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
+  for (int c0 = j0; c0 < N; c0 += 128) {
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = k + rg;
+    // four rows per iteration with all loads issued first (memory-level parallelism)
+    for (; i + 24 < N; i += 32) {
+      double x[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : 0.0;
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double vi = hv[i + 8 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = fma(vi, x[r][q], w[q]);
+      }
+    }
+    for (; i < N; i += 8) {
+      const double vi = hv[i];
+      const double* row = M + (size_t)i * ld;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < N) w[q] = fma(vi, row[j], w[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
+    __syncthreads();
+    double wt[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double t = 0.0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) t += qred[r * 128 + lane + 32 * q];
+      wt[q] = bk * t;
+    }
+    i = k + rg;
+    for (; i + 24 < N; i += 32) {
+      double x[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : 0.0;
+        }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double vi = hv[i + 8 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          if (j < N) M[(size_t)(i + 8 * r) * ld + j] = x[r][q] - wt[q] * vi;
+        }
+      }
+    }
+    for (; i < N; i += 8) {
+      const double vi = hv[i];
+      double* row = M + (size_t)i * ld;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < N) row[j] -= wt[q] * vi;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Householder QR with column pivoting of M (N x N, in place): on return the
+// upper triangle holds R, the strict lower triangle the Householder vectors
+// (their leading entries in vk0), beta[k] the reflector coefficients,
+// perm[k] the original column at position k.  Returns det(Q) = (-1)^#reflectors.
+// Pivot = remaining column of largest norm (ties to the lowest index); norms
+// are downdated and recomputed when cancellation sets in (LAPACK xGEQP3 rule).
+__device__ int qr_pivoted(int N, int ld, double* M, double* beta, double* vk0, double* cn, double* cn0,
+                          int* perm, Smem& S) {
+  const int tid = threadIdx.x;
+  for (int j = tid; j < N; j += kThreads) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc = fma(M[(size_t)i * ld + j], M[(size_t)i * ld + j], acc);
+    cn[j] = sqrt(acc);
+    cn0[j] = cn[j];
+    perm[j] = j;
+  }
+  __syncthreads();
+  const double tol3z = sqrt(2.220446049250313e-16);
+  int detq = 1;
+  for (int k = 0; k < N; ++k) {
+    // pivot
+    double bv = -1.0;
+    int bi = N;
+    for (int j = k + tid; j < N; j += kThreads)
+      if (cn[j] > bv) { bv = cn[j]; bi = j; }
+    int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N) p = k;  // no finite candidate (NaN input): keep the column order
+    if (p != k) {
+      for (int i = tid; i < N; i += kThreads) {
+        const double t = M[(size_t)i * ld + k];
+        M[(size_t)i * ld + k] = M[(size_t)i * ld + p];
+        M[(size_t)i * ld + p] = t;
+      }
+      if (tid == 0) {
+        const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
+        double t = cn[k]; cn[k] = cn[p]; cn[p] = t;
+        t = cn0[k]; cn0[k] = cn0[p]; cn0[p] = t;
+      }
+      __syncthreads();
+    }
+    // reflector from column k, rows k..N-1
+    double part = 0.0;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const double x = M[(size_t)i * ld + k];
+      part = fma(x, x, part);
+      S.hv[i] = x;
+    }
+    const double xn2 = block_sum(part, S.red);
+    const double xnorm = sqrt(xn2);
+    const double x0 = S.hv[k];
+    double bk = 0.0;
+    double alpha = 0.0;
+    if (xnorm > 0.0) {
+      alpha = (x0 >= 0.0) ? -xnorm : xnorm;
+      const double v0 = x0 - alpha;
+      const double vtv = xn2 - x0 * x0 + v0 * v0;
+      bk = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+      __syncthreads();
+      if (tid == 0) S.hv[k] = v0;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      beta[k] = bk;
+      vk0[k] = S.hv[k];
+    }
+    if (bk != 0.0) detq = -detq;
+    // apply H = I - bk v v^T to the trailing columns j > k
+    if (bk != 0.0) householder_apply(N, ld, M, k, k + 1, bk, S.hv, S.qred);
+    __syncthreads();
+    if (tid == 0) M[(size_t)k * ld + k] = (xnorm > 0.0) ? alpha : x0;
+    // downdate the trailing column norms
+    for (int j = k + 1 + tid; j < N; j += kThreads) {
+      if (cn[j] != 0.0) {
+        double t = fabs(M[(size_t)k * ld + j]) / cn[j];
+        t = fmax(0.0, (1.0 + t) * (1.0 - t));
+        const double r = cn[j] / cn0[j];
+        if (t * r * r <= tol3z) {
+          double acc = 0.0;
+          for (int i = k + 1; i < N; ++i) acc = fma(M[(size_t)i * ld + j], M[(size_t)i * ld + j], acc);
+          cn[j] = sqrt(acc);
+          cn0[j] = cn[j];
+        } else {
+          cn[j] *= sqrt(t);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return detq;
+}
+
+// Q = H_0 H_1 ... H_{N-1} from the reflectors left in M by qr_pivoted.
+__device__ void form_q(int N, int ld, const double* M, const double* beta, const double* vk0, double* Q,
+                       Smem& S) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    Q[(size_t)x * ld + y] = (x == y) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = N - 1; k >= 0; --k) {
+    const double bk = beta[k];
+    if (bk == 0.0) continue;
+    for (int i = k + tid; i < N; i += kThreads) S.hv[i] = (i == k) ? vk0[k] : M[(size_t)i * ld + k];
+    __syncthreads();
+    householder_apply(N, ld, Q, k, k, bk, S.hv, S.qred);
+  }
+}
+
+// One step of a UDV chain (Sec. 2.3): X = Bcal Q_src, M = X D_src, M P = Q R,
+// D = |diag R|, T = D^-1 R P^T T_src.  Right chain (left == false): Bcal =
+// B_t2 ... B_t1+1.  Left chain: Bcal = B_t1+1^T ... B_t2^T.  Result in
+// (W2, wvec 0, W5); returns det(Q).
+__device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S,
+                      long long* det = nullptr) {
+  long long t0 = clock64();
+  const int N = C.N, ld = C.ld;
+  double* X = wmat(C, s, 0);
+  double* Y = wmat(C, s, 1);
+  cta_copy(N, ld, src.Q, X);
+  const double* E = C.E[s];
+  if (!left) {
+    for (int t = t1 + 1; t <= t2; ++t) {
+      slice_potential_global(C, s, t, S.v);
+      for (int x = threadIdx.x; x < N; x += kThreads) S.ev[x] = exp(S.v[x]);
+      __syncthreads();
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        X[(size_t)x * ld + y] *= S.ev[x];
+      }
+      __syncthreads();
+      cta_gemm<double, false, false>(N, N, N, E, ld, X, ld, Y, ld, S.gemm);
+      double* t_ = X; X = Y; Y = t_;
+    }
+  } else {
+    for (int t = t2; t >= t1 + 1; --t) {
+      cta_gemm<double, true, false>(N, N, N, E, ld, X, ld, Y, ld, S.gemm);
+      slice_potential_global(C, s, t, S.v);
+      for (int x = threadIdx.x; x < N; x += kThreads) S.ev[x] = exp(S.v[x]);
+      __syncthreads();
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        Y[(size_t)x * ld + y] *= S.ev[x];
+      }
+      __syncthreads();
+      double* t_ = X; X = Y; Y = t_;
+    }
+  }
+  tick(det, 4, t0);
+  // M = X D_src
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    X[(size_t)x * ld + y] *= src.D[y];
+  }
+  __syncthreads();
+  double* Dn = wvec(C, s, 0);
+  double* beta = wvec(C, s, 1);
+  double* vk0 = wvec(C, s, 2);
+  int* perm = C.iwork[s];
+  const int detq = qr_pivoted(N, ld, X, beta, vk0, wvec(C, s, 3), wvec(C, s, 4), perm, S);
+  double* Qn = wmat(C, s, 2);
+  form_q(N, ld, X, beta, vk0, Qn, S);
+  tick(det, 5, t0);
+  double* PT = wmat(C, s, 3);
+  double* Rt = wmat(C, s, 4);
+  for (int x = threadIdx.x; x < N; x += kThreads) Dn[x] = fabs(X[(size_t)x * ld + x]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    PT[(size_t)x * ld + y] = src.T[(size_t)perm[x] * ld + y];
+    Rt[(size_t)x * ld + y] = (y >= x && Dn[x] > 0.0) ? X[(size_t)x * ld + y] / Dn[x] : 0.0;
+  }
+  __syncthreads();
+  cta_gemm<double, false, false>(N, N, N, Rt, ld, PT, ld, wmat(C, s, 5), ld, S.gemm);
+  tick(det, 6, t0);
+  return detq;
+}
+
+// LU with partial pivoting in place (rows swapped whole).  Returns 0 or 1 if singular.
+__device__ int lu_factor(int N, int ld, double* A, int* piv, double& logdet, int& sign, Smem& S) {
+  const int tid = threadIdx.x;
+  double ld_ = 0.0;
+  int sg = 1;
+  for (int k = 0; k < N; ++k) {
+    double bv = -1.0;
+    int bi = N;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const double a = fabs(A[(size_t)i * ld + k]);
+      if (a > bv) { bv = a; bi = i; }
+    }
+    const int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N) return 1;  // no finite pivot candidate
+    if (tid == 0) piv[k] = p;
+    const double pv = A[(size_t)p * ld + k];
+    if (!(pv != 0.0)) return 1;
+    if (p != k) {
+      for (int j = tid; j < N; j += kThreads) {
+        const double t = A[(size_t)k * ld + j];
+        A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
+        A[(size_t)p * ld + j] = t;
+      }
+      sg = -sg;
+    }
+    __syncthreads();
+    const double d = A[(size_t)k * ld + k];
+    ld_ += log(fabs(d));
+    if (d < 0.0) sg = -sg;
+    for (int i = k + 1 + tid; i < N; i += kThreads) A[(size_t)i * ld + k] /= d;
+    __syncthreads();
+    const int rem = N - k - 1;
+    for (int e = tid; e < rem * rem; e += kThreads) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      A[(size_t)i * ld + j] -= A[(size_t)i * ld + k] * A[(size_t)k * ld + j];
+    }
+    __syncthreads();
+  }
+  logdet = ld_;
+  sign = sg;
+  return 0;
+}
+
+// Solve (LU) Y = B for all columns of B (in place), rows permuted by piv first.
+// Each row of the forward and backward substitution is one row-vector times
+// matrix product, computed with 8 row groups x 32 columns and a fixed-order
+// shared-memory reduction (rows of B read coalesced).
+__device__ void lu_solve(int N, int ld, const double* LU, const int* piv, double* B, double* qred) {
+  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
+  for (int k = 0; k < N; ++k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int j = tid; j < N; j += kThreads) {
+        const double t = B[(size_t)k * ld + j];
+        B[(size_t)k * ld + j] = B[(size_t)p * ld + j];
+        B[(size_t)p * ld + j] = t;
+      }
+    __syncthreads();
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int ii = (pass == 0 ? 1 : N - 1); pass == 0 ? ii < N : ii >= 0; ii += (pass == 0 ? 1 : -1)) {
+      const int klo = pass == 0 ? 0 : ii + 1, khi = pass == 0 ? ii : N;
+      const double* lrow = LU + (size_t)ii * ld;
+      for (int c0 = 0; c0 < N; c0 += 128) {
+        double w[4] = {0.0, 0.0, 0.0, 0.0};
+        int k = klo + rg;
+        for (; k + 24 < khi; k += 32) {
+          double x[4][4], l[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            l[r] = lrow[k + 8 * r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int j = c0 + lane + 32 * q;
+              x[r][q] = (j < N) ? B[(size_t)(k + 8 * r) * ld + j] : 0.0;
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = fma(l[r], x[r][q], w[q]);
+        }
+        for (; k < khi; k += 8) {
+          const double l = lrow[k];
+          const double* brow = B + (size_t)k * ld;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = c0 + lane + 32 * q;
+            if (j < N) w[q] = fma(l, brow[j], w[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
+        __syncthreads();
+        if (rg == 0) {
+          const double dinv = pass == 1 ? 1.0 / lrow[ii] : 1.0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = c0 + lane + 32 * q;
+            double t = 0.0;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) t += qred[r * 128 + lane + 32 * q];
+            if (j < N) {
+              const double v = B[(size_t)ii * ld + j] - t;
+              B[(size_t)ii * ld + j] = pass == 1 ? v * dinv : v;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// Stable G from a right chain R (B(tau,0) = Q_R D_R T_R) and a left chain Lf
+// (B(beta,tau)^T = Q_L D_L T_L) by scale separation, D = Db Ds with
+// Db = max(D,1), Ds = min(D,1):
+//   Mid = Db_R^-1 Q_R^T Q_L Db_L^-1 + Ds_R (T_R T_L^T) Ds_L
+//   G   = Q_L Db_L^-1 Mid^-1 Db_R^-1 Q_R^T
+//   log|det G^-1| = sum log Db_R + sum log Db_L + log|det Mid|.
+// Uses W0, W1; the result goes to Gout.  Returns nonzero if Mid is singular.
+__device__ int green_from_udv(const ChainDev& C, int s, UDV R, UDV Lf, double* Gout, double& logdet,
+                              int& sign, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  double* W0 = wmat(C, s, 0);
+  double* W1 = wmat(C, s, 1);
+  cta_gemm<double, true, false>(N, N, N, R.Q, ld, Lf.Q, ld, W0, ld, S.gemm);
+  cta_gemm<double, false, true>(N, N, N, R.T, ld, Lf.T, ld, W1, ld, S.gemm);
+  // 1/Db and Ds of both chains (vectors 5..7 of the workspace)
+  double* ibR = wvec(C, s, 5);
+  double* ibL = wvec(C, s, 6);
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    ibR[i] = 1.0 / (R.D[i] > 1.0 ? R.D[i] : 1.0);
+    ibL[i] = 1.0 / (Lf.D[i] > 1.0 ? Lf.D[i] : 1.0);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dR = R.D[i], dL = Lf.D[j];
+    const double dsR = dR > 1.0 ? 1.0 : dR, dsL = dL > 1.0 ? 1.0 : dL;
+    W0[(size_t)i * ld + j] = W0[(size_t)i * ld + j] * (ibR[i] * ibL[j]) + dsR * W1[(size_t)i * ld + j] * dsL;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] * ibR[i];
+  }
+  __syncthreads();
+  double ldm;
+  int sm;
+  int* piv = C.iwork[s] + ld;
+  if (lu_factor(N, ld, W0, piv, ldm, sm, S)) return 1;
+  lu_solve(N, ld, W0, piv, W1, S.qred);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    W1[(size_t)i * ld + j] *= ibL[i];
+  }
+  __syncthreads();
+  cta_gemm<double, false, false>(N, N, N, Lf.Q, ld, W1, ld, Gout, ld, S.gemm);
+  double part = 0.0;
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    const double dR = R.D[i], dL = Lf.D[i];
+    part += log(dR > 1.0 ? dR : 1.0) + log(dL > 1.0 ? dL : 1.0);
+  }
+  logdet = ldm + block_sum(part, S.red);
+  sign = sm * R.detq * Lf.detq;
+  return 0;
+}
+
+__device__ void copy_udv_to_slot(const ChainDev& C, int s, int j, int detq) {
+  const int N = C.N, ld = C.ld;
+  double* b = slot_base(C, s, j);
+  cta_copy(N, ld, (const double*)wmat(C, s, 2), b);
+  cta_copy(N, ld, (const double*)wmat(C, s, 5), b + (size_t)N * ld);
+  const double* Dn = wvec(C, s, 0);
+  for (int x = threadIdx.x; x < N; x += kThreads) b[(size_t)2 * N * ld + x] = Dn[x];
+  if (threadIdx.x == 0) C.slot_detq[s][j] = detq;
+  __syncthreads();
+}
+
+__device__ inline UDV work_udv(const ChainDev& C, int s, int detq) {
+  UDV u;
+  u.Q = wmat(C, s, 2);
+  u.T = wmat(C, s, 5);
+  u.D = wvec(C, s, 0);
+  u.detq = detq;
+  return u;
+}
+
+// Fill the storage with the left chain (Algorithm 1, the loop before the bins)
+// and compute G(0) into W6.
+__device__ int fill_left_chain(const ChainDev& C, int s, Smem& S, double& logdet, int& sign) {
+  const int nst = C.L / C.nw;
+  for (int j = nst - 1; j >= 0; --j) {
+    const UDV src = (j + 1 == nst) ? ident_udv(C) : slot_udv(C, s, j + 1);
+    const int dq = chain_step(C, s, j * C.nw, (j + 1) * C.nw, true, src, S);
+    copy_udv_to_slot(C, s, j, dq);
+  }
+  return green_from_udv(C, s, ident_udv(C), slot_udv(C, s, 0), wmat(C, s, 6), logdet, sign, S);
+}
+
+// --------------------------------------------------------------------------
+// Kernels templated on the working precision.
+// --------------------------------------------------------------------------
+// Fresh G(0) for every (chain, flavor): the left chain is (re)computed into the
+// storage slots, G(0) lands in W6.  mode 0: also write the working G, the
+// fresh log|det| and the sign (initialisation); mode 1: copy G(0) of chain
+// `out_chain` to `out` (FP64, [nfl][N][N]).
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains, int n_chains, int mode,
+                                                               double* out, int out_chain) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nfl = chains[0].nfl;
+  const int c = blockIdx.x / nfl, s = blockIdx.x % nfl;
+  if (c >= n_chains) return;
+  if (mode == 1 && c != out_chain) return;
+  ChainDev& C = chains[c];
+  Smem S = carve_smem(smem_raw, C.ld, C.MV);
+  double logdet;
+  int sign;
+  if (fill_left_chain(C, s, S, logdet, sign)) {
+    if (threadIdx.x == 0) C.error = 1;
+    return;
+  }
+  const double* Gf = wmat(C, s, 6);
+  if (mode == 0) {
+    Real* G = (Real*)C.G[s];
+    for (int e = threadIdx.x; e < C.N * C.N; e += kThreads) {
+      const int x = e / C.N, y = e - x * C.N;
+      G[(size_t)x * C.ld + y] = from_d<Real>(Gf[(size_t)x * C.ld + y]);
+    }
+  } else {
+    for (int e = threadIdx.x; e < C.N * C.N; e += kThreads) {
+      const int x = e / C.N, y = e - x * C.N;
+      out[(size_t)s * C.N * C.N + e] = Gf[(size_t)x * C.ld + y];
+    }
+  }
+  if (threadIdx.x == 0) {
+    C.logdet[s] = logdet;
+    C.fresh_sign[s] = sign;
+  }
+}
+
+template <typename Real>
+__global__ void copy_green_kernel(ChainDev* chains, int chain, int flavor, double* out) {
+  const ChainDev& C = chains[chain];
+  const Real* G = (const Real*)C.G[flavor];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.N * C.N; e += gridDim.x * blockDim.x) {
+    const int x = e / C.N, y = e - x * C.N;
+    out[e] = to_d(G[(size_t)x * C.ld + y]);
+  }
+}
+
+// ---- pieces of the sweep --------------------------------------------------
+
+// G <- diag(ev) G diag(1/ev)  with ev = exp(a v)
+template <typename Real>
+__device__ void v_wrap(const ChainDev& C, Real* G, const double* v, double a, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  Real* evr = reinterpret_cast<Real*>(S.ev);
+  Real* evi = reinterpret_cast<Real*>(S.hv);
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    evr[x] = from_d<Real>(exp(a * v[x]));
+    evi[x] = from_d<Real>(exp(-a * v[x]));
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    G[(size_t)x * ld + y] = rmul(rmul(G[(size_t)x * ld + y], evr[x]), evi[y]);
+  }
+  __syncthreads();
+}
+
+// Hopping wrap: up  G <- E G E^-1;  down  G <- E^-1 G E.
+template <typename Real>
+__device__ void t_wrap(const ChainDev& C, int s, Real* G, Real* Gt, bool up, Smem& S);
+
+template <>
+__device__ void t_wrap<double>(const ChainDev& C, int s, double* G, double* Gt, bool up, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  const double* X = up ? C.E[s] : C.Einv[s];
+  const double* Y = up ? C.Einv[s] : C.E[s];
+  cta_gemm<double, false, false>(N, N, N, X, ld, G, ld, Gt, ld, S.gemm);
+  cta_gemm<double, false, false>(N, N, N, Gt, ld, Y, ld, G, ld, S.gemm);
+}
+template <>
+__device__ void t_wrap<float>(const ChainDev& C, int s, float* G, float* Gt, bool up, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  const float* X = up ? C.E32[s] : C.Einv32[s];
+  const float* Y = up ? C.Einv32[s] : C.E32[s];
+  float* sm = reinterpret_cast<float*>(S.gemm);
+  cta_gemm<float, false, false>(N, N, N, X, ld, G, ld, Gt, ld, sm);
+  cta_gemm<float, false, false>(N, N, N, Gt, ld, Y, ld, G, ld, sm);
+}
+
+template <>
+__device__ void t_wrap<dd>(const ChainDev& C, int s, dd* G, dd* Gt, bool up, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  const dd* X = (const dd*)(up ? C.Edd[s] : C.Einvdd[s]);
+  const dd* Y = (const dd*)(up ? C.Einvdd[s] : C.Edd[s]);
+  gemm_dd<false, false, false>(C, s, S, N, N, N, X, ld, G, ld, Gt, ld);
+  gemm_dd<false, false, false>(C, s, S, N, N, N, Gt, ld, Y, ld, G, ld);
+}
+
+// G <- G + sum_m a_m b_m^T  (flush of the delayed rank-k update), a register-
+// blocked product G += A^T B with A, B stored as rows a_m, b_m.
+template <typename Real>
+__device__ void flush_delayed(const ChainDev& C, Real* G, const Real* A, const Real* B, int nacc, Smem& S);
+
+template <>
+__device__ void flush_delayed<double>(const ChainDev& C, double* G, const double* A, const double* B, int nacc,
+                                      Smem& S) {
+  const int N = C.N, ld = C.ld;
+  const int r = gemm_pick_r(N);
+  if (r == 3) cta_gemm_r<double, true, false, 3, true>(N, N, nacc, A, ld, B, ld, G, ld, S.gemm);
+  else if (r == 5) cta_gemm_r<double, true, false, 5, true>(N, N, nacc, A, ld, B, ld, G, ld, S.gemm);
+  else cta_gemm_r<double, true, false, 4, true>(N, N, nacc, A, ld, B, ld, G, ld, S.gemm);
+}
+template <>
+__device__ void flush_delayed<float>(const ChainDev& C, float* G, const float* A, const float* B, int nacc,
+                                     Smem& S) {
+  const int N = C.N, ld = C.ld;
+  float* sm = reinterpret_cast<float*>(S.gemm);
+  const int r = gemm_pick_r(N);
+  if (r == 3) cta_gemm_r<float, true, false, 3, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
+  else if (r == 5) cta_gemm_r<float, true, false, 5, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
+  else cta_gemm_r<float, true, false, 4, true>(N, N, nacc, A, ld, B, ld, G, ld, sm);
+}
+template <>
+__device__ void flush_delayed<dd>(const ChainDev& C, dd* G, const dd* A, const dd* B, int nacc, Smem& S) {
+  // a rank-k update (k <= 64): the float-pair SIMT tiles beat the split
+  // tensor-core product, whose digit split and recombination cost O(N^2 k_dig)
+  gemm_dd_tiles<true, false, true>(C.N, C.N, nacc, A, C.ld, B, C.ld, G, C.ld, reinterpret_cast<dd*>(S.gemm));
+}
+
+// Sequential single-field updates of one slice (Sec. 2.2.1) for this CTA's
+// flavor.  The ratios of every remaining position are evaluated in parallel
+// from the current diagonal of G; the first accepted position in visiting
+// order is found by a block reduction, which is exactly the sequential
+// Metropolis chain because rejected proposals leave G unchanged.  Accepted
+// flips are applied as delayed rank-1 updates (flushed every k accepts):
+//   a = -(delta/R_s) G_eff[:,i],  b = e_i - G_eff[i,:],  G_eff += a b^T.
+template <typename Real>
+__device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepParams& P, Smem& S,
+                             cg::cluster_group& cl, Real* G, Real* A, Real* B, int& sign, int& buf,
+                             long long* det) {
+  const int N = C.N, ld = C.ld, MV = C.MV, nfl = C.nfl, tid = threadIdx.x;
+  long long t0 = clock64();
+  const uint32_t key0 = (uint32_t)P.seed, key1 = (uint32_t)(P.seed >> 32) ^ C.chain_id;
+  for (int q = tid; q < MV; q += kThreads) {
+    const int k = dir ? MV - 1 - q : q;
+    uint32_t ctr[4] = {(uint32_t)P.sweep, (uint32_t)(2 * tau + dir), (uint32_t)k, (uint32_t)(P.sweep >> 32)};
+    philox4x32_10(ctr, key0, key1);
+    const double u1 = uniform53(ctr[0], ctr[1]);
+    S.u2[q] = uniform53(ctr[2], ctr[3]);
+    const int f = S.fslice[k];
+    const int fn = propose_field(C.ft, f, u1);
+    const double dc = coupling(C.ft, C.cscale, fn) - coupling(C.ft, C.cscale, f);
+    S.delta[q] = exp(C.vsign[s * MV + k] * dc) - 1.0;
+    S.gam[q] = field_weight(C.ft, fn) / field_weight(C.ft, f);
+    S.fnew[q] = (int8_t)fn;
+    S.qsite[q] = C.site[k];
+  }
+  for (int x = tid; x < N; x += kThreads) S.d[x] = to_d(G[(size_t)x * ld + x]);
+  __syncthreads();
+  tick(det, 0, t0);
+  int pos = 0, nacc = 0;
+  int64_t n_acc_slice = 0;
+  const int kdel = P.delay_k;
+  while (true) {
+    double* Rs = S.Rs + buf * MV;
+    for (int q = pos + tid; q < MV; q += kThreads) Rs[q] = 1.0 + S.delta[q] * (1.0 - S.d[S.qsite[q]]);
+    // the next position is accepted most of the time: start reading its column and
+    // row of G now, so that the cluster barrier covers the memory latency
+    const int ipre = (pos < MV) ? S.qsite[pos] : 0;
+    Real gc_pre = from_d<Real>(0.0), gr_pre = from_d<Real>(0.0);
+    if (tid < N) {
+      gc_pre = G[(size_t)tid * ld + ipre];
+      gr_pre = G[(size_t)ipre * ld + tid];
+    }
+    cl.sync();
+    const double* Rr[kMaxFlavors];
+    for (int r = 0; r < nfl; ++r) Rr[r] = (r == s) ? Rs : cl.map_shared_rank(Rs, r);
+    int first = MV;
+    for (int q = pos + tid; q < MV; q += kThreads) {
+      double R = S.gam[q];
+      for (int r = 0; r < nfl; ++r) R *= Rr[r][q];
+      const double aR = fabs(R);
+      if (S.u2[q] < (aR < 1.0 ? aR : 1.0)) {
+        S.Rp[q] = R;
+        first = q;
+        break;
+      }
+    }
+    first = block_min_int(first, S.ired);
+    tick(det, 1, t0);
+    if (first >= MV) { buf ^= 1; break; }
+    const double R = S.Rp[first];
+    if (R < 0.0) sign = -sign;
+    const int k = dir ? MV - 1 - first : first;
+    const int i = S.qsite[first];
+    const double fac = S.delta[first] / Rs[first];
+    Real* a = A + (size_t)nacc * ld;
+    Real* b = B + (size_t)nacc * ld;
+    const Real mfac = from_d<Real>(-fac);
+    const bool hit = (first == pos);
+    // element x of column i (a) and of row i (b) of G_eff
+    for (int x = tid; x < N; x += kThreads) {
+      Real cx, ry;
+      if (hit && x == tid) {
+        cx = gc_pre;
+        ry = gr_pre;
+      } else {
+        cx = G[(size_t)x * ld + i];
+        ry = G[(size_t)i * ld + x];
+      }
+      for (int m = 0; m < nacc; ++m) {
+        cx = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
+        ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
+      }
+      a[x] = rmul(mfac, cx);
+      b[x] = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
+    }
+    __syncthreads();
+    for (int x = tid; x < N; x += kThreads) S.d[x] += to_d(a[x]) * to_d(b[x]);
+    if (tid == 0) S.fslice[k] = S.fnew[first];
+    ++nacc;
+    ++n_acc_slice;
+    tick(det, 2, t0);
+    if (nacc == kdel) {
+      __syncthreads();
+      flush_delayed<Real>(C, G, A, B, nacc, S);
+      nacc = 0;
+      tick(det, 3, t0);
+    }
+    pos = first + 1;
+    buf ^= 1;
+    __syncthreads();
+  }
+  if (nacc) flush_delayed<Real>(C, G, A, B, nacc, S);
+  tick(det, 3, t0);
+  if (s == 0 && tid == 0) {
+    C.proposals += MV;
+    C.accepted += n_acc_slice;
+  }
+}
+
+// ---- float-pair Householder QR with FP64 column scales (mixed path) -------
+// M = X diag(dsc) with X the float-pair product Bcal Q (entries O(1)) and dsc
+// the FP64 scales D of the previous decomposition, which may exceed the float
+// range.  Householder reflections act on rows and commute with the column
+// scaling, so the pivoted QR of M is the QR of X with the pivot chosen by the
+// scaled norm dsc_j ||X[k:, j]|| (Businger-Golub on M); R_M = R_X diag(dsc[perm]).
+__device__ void householder_apply_dd(int N, int ld, dd* M, int k, int j0, dd bk, const dd* hv, dd* qred) {
+  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
+  for (int c0 = j0; c0 < N; c0 += 128) {
+    dd w[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    int i = k + rg;
+    for (; i + 8 < N; i += 16) {
+      dd x[2][4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : dd{0.f, 0.f};
+        }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const dd vi = hv[i + 8 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = dd_fma(vi, x[r][q], w[q]);
+      }
+    }
+    for (; i < N; i += 8) {
+      const dd vi = hv[i];
+      const dd* row = M + (size_t)i * ld;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < N) w[q] = dd_fma(vi, row[j], w[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
+    __syncthreads();
+    dd wt[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dd t = {0.f, 0.f};
+#pragma unroll
+      for (int r = 0; r < 8; ++r) t = dd_add(t, qred[r * 128 + lane + 32 * q]);
+      const dd bw = dd_mul(bk, t);
+      wt[q] = {-bw.hi, -bw.lo};
+    }
+    i = k + rg;
+    for (; i + 8 < N; i += 16) {
+      dd x[2][4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : dd{0.f, 0.f};
+        }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const dd vi = hv[i + 8 * r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = c0 + lane + 32 * q;
+          if (j < N) M[(size_t)(i + 8 * r) * ld + j] = dd_fma(wt[q], vi, x[r][q]);
+        }
+      }
+    }
+    for (; i < N; i += 8) {
+      const dd vi = hv[i];
+      dd* row = M + (size_t)i * ld;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < N) row[j] = dd_fma(wt[q], vi, row[j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ int qr_pivoted_dd(int N, int ld, dd* X, double* dsc, double* beta, dd* vk0, double* cn, double* cn0,
+                             int* perm, Smem& S) {
+  const int tid = threadIdx.x;
+  dd* hv = reinterpret_cast<dd*>(S.hv);
+  dd* qred = reinterpret_cast<dd*>(S.qred);
+  for (int j = tid; j < N; j += kThreads) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double x = to_d(X[(size_t)i * ld + j]);
+      acc = fma(x, x, acc);
+    }
+    cn[j] = sqrt(acc);
+    cn0[j] = cn[j];
+    perm[j] = j;
+  }
+  __syncthreads();
+  const double tol3z = sqrt(2.220446049250313e-16);
+  int detq = 1;
+  for (int k = 0; k < N; ++k) {
+    double bv = -1.0;
+    int bi = N;
+    for (int j = k + tid; j < N; j += kThreads) {
+      const double sn = dsc[j] * cn[j];
+      if (sn > bv) { bv = sn; bi = j; }
+    }
+    int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N) p = k;
+    if (p != k) {
+      for (int i = tid; i < N; i += kThreads) {
+        const dd t = X[(size_t)i * ld + k];
+        X[(size_t)i * ld + k] = X[(size_t)i * ld + p];
+        X[(size_t)i * ld + p] = t;
+      }
+      if (tid == 0) {
+        const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
+        double t = cn[k]; cn[k] = cn[p]; cn[p] = t;
+        t = cn0[k]; cn0[k] = cn0[p]; cn0[p] = t;
+        t = dsc[k]; dsc[k] = dsc[p]; dsc[p] = t;
+      }
+      __syncthreads();
+    }
+    double part = 0.0;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const dd x = X[(size_t)i * ld + k];
+      const double xd = to_d(x);
+      part = fma(xd, xd, part);
+      hv[i] = x;
+    }
+    const double xn2 = block_sum(part, S.red);
+    const double xnorm = sqrt(xn2);
+    const dd x0 = hv[k];
+    double bk = 0.0, alpha = 0.0;
+    if (xnorm > 0.0) {
+      const double x0d = to_d(x0);
+      alpha = (x0d >= 0.0) ? -xnorm : xnorm;
+      const dd v0 = dd_add(x0, from_d<dd>(-alpha));
+      const double v0d = to_d(v0);
+      const double vtv = xn2 - x0d * x0d + v0d * v0d;
+      bk = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+      __syncthreads();
+      if (tid == 0) hv[k] = v0;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      beta[k] = bk;
+      vk0[k] = hv[k];
+    }
+    if (bk != 0.0) detq = -detq;
+    if (bk != 0.0) householder_apply_dd(N, ld, X, k, k + 1, from_d<dd>(bk), hv, qred);
+    __syncthreads();
+    if (tid == 0) X[(size_t)k * ld + k] = (xnorm > 0.0) ? from_d<dd>(alpha) : x0;
+    for (int j = k + 1 + tid; j < N; j += kThreads) {
+      if (cn[j] != 0.0) {
+        double t = fabs(to_d(X[(size_t)k * ld + j])) / cn[j];
+        t = fmax(0.0, (1.0 + t) * (1.0 - t));
+        const double r = cn[j] / cn0[j];
+        if (t * r * r <= tol3z) {
+          double acc = 0.0;
+          for (int i = k + 1; i < N; ++i) {
+            const double x = to_d(X[(size_t)i * ld + j]);
+            acc = fma(x, x, acc);
+          }
+          cn[j] = sqrt(acc);
+          cn0[j] = cn[j];
+        } else {
+          cn[j] *= sqrt(t);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return detq;
+}
+
+__device__ void form_q_dd(int N, int ld, const dd* X, const double* beta, const dd* vk0, dd* Q, Smem& S) {
+  const int tid = threadIdx.x;
+  dd* hv = reinterpret_cast<dd*>(S.hv);
+  dd* qred = reinterpret_cast<dd*>(S.qred);
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    Q[(size_t)x * ld + y] = {(x == y) ? 1.f : 0.f, 0.f};
+  }
+  __syncthreads();
+  for (int k = N - 1; k >= 0; --k) {
+    const double bk = beta[k];
+    if (bk == 0.0) continue;
+    for (int i = k + tid; i < N; i += kThreads) hv[i] = (i == k) ? vk0[k] : X[(size_t)i * ld + k];
+    __syncthreads();
+    householder_apply_dd(N, ld, Q, k, k, from_d<dd>(bk), hv, qred);
+  }
+}
+
+// ---- stabilisation with float-float products (mixed path) ----------------
+// Same steps as chain_step / green_from_udv; the dense products (the B chain,
+// T = D^-1 R P^T T, Q_R^T Q_L, T_R T_L^T, Q_L Y) run as float-float GEMMs on the
+// FP32 pipes, the pivoted QR, Q accumulation, LU and triangular solves stay
+// FP64.  Storage matrices (Q, T) remain FP64.
+__device__ inline void to_dd_mat(int N, int ld, const double* src, dd* dst) {
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    dst[(size_t)x * ld + y] = from_d<dd>(src[(size_t)x * ld + y]);
+  }
+  __syncthreads();
+}
+
+// dd -> double in place (same 8-byte slot)
+__device__ inline void dd_to_d_inplace(int N, int ld, void* buf) {
+  dd* a = reinterpret_cast<dd*>(buf);
+  double* b = reinterpret_cast<double*>(buf);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const dd v = a[(size_t)x * ld + y];
+    b[(size_t)x * ld + y] = to_d(v);
+  }
+  __syncthreads();
+}
+
+__device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S,
+                      long long* det = nullptr) {
+  long long t0 = clock64();
+  const int N = C.N, ld = C.ld;
+  dd* X = reinterpret_cast<dd*>(wmat(C, s, 0));
+  dd* Y = reinterpret_cast<dd*>(wmat(C, s, 1));
+  dd* evr = reinterpret_cast<dd*>(S.ev);
+  to_dd_mat(N, ld, src.Q, X);
+  const dd* E = (const dd*)C.Edd[s];
+  if (!left) {
+    for (int t = t1 + 1; t <= t2; ++t) {
+      slice_potential_global(C, s, t, S.v);
+      for (int x = threadIdx.x; x < N; x += kThreads) evr[x] = from_d<dd>(exp(S.v[x]));
+      __syncthreads();
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        X[(size_t)x * ld + y] = dd_mul(X[(size_t)x * ld + y], evr[x]);
+      }
+      __syncthreads();
+      gemm_dd<false, false, false>(C, s, S, N, N, N, E, ld, X, ld, Y, ld);
+      dd* t_ = X; X = Y; Y = t_;
+    }
+  } else {
+    for (int t = t2; t >= t1 + 1; --t) {
+      gemm_dd<true, false, false>(C, s, S, N, N, N, E, ld, X, ld, Y, ld);
+      slice_potential_global(C, s, t, S.v);
+      for (int x = threadIdx.x; x < N; x += kThreads) evr[x] = from_d<dd>(exp(S.v[x]));
+      __syncthreads();
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        Y[(size_t)x * ld + y] = dd_mul(Y[(size_t)x * ld + y], evr[x]);
+      }
+      __syncthreads();
+      dd* t_ = X; X = Y; Y = t_;
+    }
+  }
+  tick(det, 4, t0);
+  double* Dn = wvec(C, s, 0);
+  double* beta = wvec(C, s, 1);
+  dd* vk0 = reinterpret_cast<dd*>(wvec(C, s, 2));
+  double* dsc = wvec(C, s, 5);
+  double* invr = wvec(C, s, 6);
+  int* perm = C.iwork[s];
+  for (int j = threadIdx.x; j < N; j += kThreads) dsc[j] = src.D[j];
+  __syncthreads();
+  const int detq = qr_pivoted_dd(N, ld, X, dsc, beta, vk0, wvec(C, s, 3), wvec(C, s, 4), perm, S);
+  dd* Qd = reinterpret_cast<dd*>(wmat(C, s, 2));
+  form_q_dd(N, ld, X, beta, vk0, Qd, S);
+  dd_to_d_inplace(N, ld, Qd);
+  tick(det, 5, t0);
+  dd* PT = reinterpret_cast<dd*>(wmat(C, s, 3));
+  dd* Rt = reinterpret_cast<dd*>(wmat(C, s, 4));
+  // D = |diag R_M| = |R_X,kk| dsc_k;  R~_ij = R_X,ij dsc_j / (|R_X,ii| dsc_i), |R~_ij| <= 1
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    const double rkk = fabs(to_d(X[(size_t)x * ld + x]));
+    Dn[x] = rkk * dsc[x];
+    invr[x] = (rkk > 0.0 && dsc[x] > 0.0) ? 1.0 / (rkk * dsc[x]) : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    PT[(size_t)x * ld + y] = from_d<dd>(src.T[(size_t)perm[x] * ld + y]);
+    dd r = {0.f, 0.f};
+    if (y >= x) r = dd_mul(X[(size_t)x * ld + y], from_d<dd>(invr[x] * dsc[y]));
+    Rt[(size_t)x * ld + y] = r;
+  }
+  __syncthreads();
+  dd* Tn = reinterpret_cast<dd*>(wmat(C, s, 5));
+  gemm_dd<false, false, false>(C, s, S, N, N, N, Rt, ld, PT, ld, Tn, ld);
+  dd_to_d_inplace(N, ld, Tn);
+  tick(det, 6, t0);
+  return detq;
+}
+
+__device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, double* Gout, double& logdet,
+                                    int& sign, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  double* W0 = wmat(C, s, 0);
+  double* W1 = wmat(C, s, 1);
+  dd* QRd = reinterpret_cast<dd*>(wmat(C, s, 3));
+  dd* QLd = reinterpret_cast<dd*>(wmat(C, s, 4));
+  dd* TRd = reinterpret_cast<dd*>(wmat(C, s, 7));
+  dd* TLd = reinterpret_cast<dd*>(wmat(C, s, 8));
+  to_dd_mat(N, ld, R.Q, QRd);
+  to_dd_mat(N, ld, Lf.Q, QLd);
+  to_dd_mat(N, ld, R.T, TRd);
+  to_dd_mat(N, ld, Lf.T, TLd);
+  gemm_dd<true, false, false>(C, s, S, N, N, N, QRd, ld, QLd, ld, reinterpret_cast<dd*>(W0), ld);
+  gemm_dd<false, true, false>(C, s, S, N, N, N, TRd, ld, TLd, ld, reinterpret_cast<dd*>(W1), ld);
+  double* ibR = wvec(C, s, 5);
+  double* ibL = wvec(C, s, 6);
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    ibR[i] = 1.0 / (R.D[i] > 1.0 ? R.D[i] : 1.0);
+    ibL[i] = 1.0 / (Lf.D[i] > 1.0 ? Lf.D[i] : 1.0);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dR = R.D[i], dL = Lf.D[j];
+    const double dsR = dR > 1.0 ? 1.0 : dR, dsL = dL > 1.0 ? 1.0 : dL;
+    const double qq = to_d(reinterpret_cast<const dd*>(W0)[(size_t)i * ld + j]);
+    const double tt = to_d(reinterpret_cast<const dd*>(W1)[(size_t)i * ld + j]);
+    W0[(size_t)i * ld + j] = qq * (ibR[i] * ibL[j]) + dsR * tt * dsL;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] * ibR[i];
+  }
+  __syncthreads();
+  double ldm;
+  int smi;
+  int* piv = C.iwork[s] + ld;
+  if (lu_factor(N, ld, W0, piv, ldm, smi, S)) return 1;
+  lu_solve(N, ld, W0, piv, W1, S.qred);
+  dd* Yd = reinterpret_cast<dd*>(wmat(C, s, 9));
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    Yd[(size_t)i * ld + j] = from_d<dd>(W1[(size_t)i * ld + j] * ibL[i]);
+  }
+  __syncthreads();
+  gemm_dd<false, false, false>(C, s, S, N, N, N, QLd, ld, Yd, ld, reinterpret_cast<dd*>(Gout), ld);
+  dd_to_d_inplace(N, ld, Gout);
+  double part = 0.0;
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    const double dR = R.D[i], dL = Lf.D[i];
+    part += log(dR > 1.0 ? dR : 1.0) + log(dL > 1.0 ? dL : 1.0);
+  }
+  logdet = ldm + block_sum(part, S.red);
+  sign = smi * R.detq * Lf.detq;
+  return 0;
+}
+
+// Stabilisation event of this CTA's flavor at slice tau: new chain, fresh G,
+// precision monitor, working G replaced, storage slot j written.
+template <typename Real>
+__device__ void stabilise(ChainDev& C, int s, int j, bool up, Real* G, Smem& S, double& ev_max,
+                          double& ev_sum, int& fresh_sign, long long* det) {
+  long long t0 = clock64();
+  const int N = C.N, ld = C.ld, nst = C.L / C.nw, nw = C.nw;
+  int dq;
+  UDV R, Lf;
+  constexpr bool mixed = std::is_same<Real, dd>::value;
+  if (up) {
+    const UDV src = (j == 1) ? ident_udv(C) : slot_udv(C, s, j - 1);
+    dq = mixed ? chain_step_mixed(C, s, (j - 1) * nw, j * nw, false, src, S, det)
+               : chain_step(C, s, (j - 1) * nw, j * nw, false, src, S, det);
+    R = work_udv(C, s, dq);
+    Lf = (j == nst) ? ident_udv(C) : slot_udv(C, s, j);
+  } else {
+    const UDV src = (j + 1 == nst) ? ident_udv(C) : slot_udv(C, s, j + 1);
+    dq = mixed ? chain_step_mixed(C, s, j * nw, (j + 1) * nw, true, src, S, det)
+               : chain_step(C, s, j * nw, (j + 1) * nw, true, src, S, det);
+    Lf = work_udv(C, s, dq);
+    R = (j == 0) ? ident_udv(C) : slot_udv(C, s, j);
+  }
+  t0 = clock64();
+  double* Gf = wmat(C, s, 6);
+  double logdet;
+  int sg;
+  const int bad = mixed ? green_from_udv_mixed(C, s, R, Lf, Gf, logdet, sg, S)
+                        : green_from_udv(C, s, R, Lf, Gf, logdet, sg, S);
+  if (bad) {
+    if (threadIdx.x == 0) C.error = 1;
+    sg = 1;
+  }
+  tick(det, 7, t0);
+  double mx = 0.0, sm = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double gf = Gf[(size_t)x * ld + y];
+    const double dg = fabs(gf - to_d(G[(size_t)x * ld + y]));
+    mx = fmax(mx, dg);
+    sm += dg;
+    G[(size_t)x * ld + y] = from_d<Real>(gf);
+  }
+  ev_max = block_max(mx, S.red);
+  ev_sum = block_sum(sm, S.red);
+  fresh_sign = sg;
+  if (threadIdx.x == 0) {
+    C.logdet[s] = logdet;
+    C.fresh_sign[s] = sg;
+  }
+  copy_udv_to_slot(C, s, j, dq);
+}
+
+// Energy estimator at the current G (Sec. 6 observables, U n_up n_dn form).
+template <typename Real>
+__device__ void measure(ChainDev& C, int s, const Real* G, Smem& S, cg::cluster_group& cl, int sign) {
+  const int N = C.N, ld = C.ld;
+  const double* K = C.K[s];
+  double kin = 0.0, part = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    kin += K[(size_t)x * ld + y] * ((x == y ? 1.0 : 0.0) - to_d(G[(size_t)y * ld + x]));
+  }
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    const double gxx = to_d(G[(size_t)x * ld + x]);
+    part += 1.0 - gxx;
+    S.xdiag[x] = gxx;
+  }
+  kin = block_sum(kin, S.red);
+  part = block_sum(part, S.red);
+  if (threadIdx.x == 0) { S.xs[0] = kin; S.xs[1] = part; }
+  cl.sync();
+  if (s == 0) {
+    double pot = 0.0;
+    if (C.nfl == 2) {
+      const double* pd = cl.map_shared_rank(S.xdiag, 1);
+      for (int x = threadIdx.x; x < N; x += kThreads) pot += C.U * (1.0 - S.xdiag[x]) * (1.0 - pd[x]);
+    }
+    pot = block_sum(pot, S.red);
+    double kin_t = S.xs[0], part_t = S.xs[1];
+    if (C.nfl == 2) {
+      const double* px = cl.map_shared_rank(S.xs, 1);
+      kin_t += px[0];
+      part_t += px[1];
+    }
+    if (threadIdx.x == 0) {
+      const double sg = (double)sign;
+      C.meas[0] += sg * kin_t;
+      C.meas[1] += sg * pot;
+      C.meas[2] += sg * part_t;
+      C.meas[3] += sg * (kin_t + pot);
+      C.meas_sign += sg;
+      C.n_meas += 1;
+    }
+  }
+  cl.sync();
+}
+
+// Exchange this flavor's fresh sign and precision figures; returns the product
+// of the fresh signs.  Rank 0 books the event.
+__device__ int close_event(ChainDev& C, int s, Smem& S, cg::cluster_group& cl, double ev_max, double ev_sum,
+                           int fresh_sign, int sign) {
+  if (threadIdx.x == 0) S.xs[2] = (double)fresh_sign;
+  cl.sync();
+  int prod = 1;
+  for (int r = 0; r < C.nfl; ++r) {
+    const double* px = (r == s) ? S.xs : cl.map_shared_rank(S.xs, r);
+    prod *= (px[2] < 0.0) ? -1 : 1;
+  }
+  if (threadIdx.x == 0) {
+    C.prec_sum[s] += ev_sum / ((double)C.N * C.N * C.nfl);
+    C.prec_max[s] = fmax(C.prec_max[s], ev_max);
+    if (s == 0) {
+      C.phase_max = fmax(C.phase_max, fabs((double)prod - (double)sign));
+      C.prec_events += 1;
+    }
+  }
+  cl.sync();
+  return prod;
+}
+
+// One sweep of every chain (Algorithm 1, upward then downward).
+template <typename Real>
+__global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, SweepParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int nfl = (int)cl.num_blocks();
+  const int s = (int)cl.block_rank();
+  const int c = P.order[blockIdx.x / nfl];
+  ChainDev& C = chains[c];
+  Smem S = carve_smem(smem_raw, C.ld, C.MV);
+  S.flavor = s;
+  Real* G = (Real*)C.G[s];
+  Real* Gt = (Real*)C.Gtmp[s];
+  Real* A = P.ab_smem ? reinterpret_cast<Real*>(S.ab) : (Real*)C.dA[s];
+  Real* B = P.ab_smem ? A + (size_t)P.delay_k * C.ld : (Real*)C.dB[s];
+  const int L = C.L, nw = C.nw, MV = C.MV;
+  int sign = C.sign;
+  int buf = 0;
+  long long cyc[4] = {0, 0, 0, 0};
+  long long det[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long t0 = clock64();
+  auto lap = [&](int phase) {
+    const long long t1 = clock64();
+    cyc[phase] += t1 - t0;
+    t0 = t1;
+  };
+  for (int tau = 1; tau <= L; ++tau) {
+    for (int k = threadIdx.x; k < MV; k += kThreads) S.fslice[k] = C.fields[(size_t)(tau - 1) * MV + k];
+    __syncthreads();
+    slice_potential_smem(C, s, S.fslice, S.v);
+    v_wrap<Real>(C, G, S.v, +1.0, S);
+    lap(1);
+    update_slice<Real>(C, s, tau, 0, P, S, cl, G, A, B, sign, buf, det);
+    if (s == 0)
+      for (int k = threadIdx.x; k < MV; k += kThreads) C.fields[(size_t)(tau - 1) * MV + k] = S.fslice[k];
+    lap(0);
+    t_wrap<Real>(C, s, G, Gt, true, S);
+    lap(1);
+    if (tau % nw == 0) {
+      cl.sync();
+      double mx, sm;
+      int fs;
+      stabilise<Real>(C, s, tau / nw, true, G, S, mx, sm, fs, det);
+      sign = close_event(C, s, S, cl, mx, sm, fs, sign);
+      lap(2);
+    }
+    if (P.measure && tau >= P.meas_first && tau <= P.meas_last) {
+      measure<Real>(C, s, G, S, cl, sign);
+      lap(3);
+    }
+  }
+  for (int tau = L; tau >= 1; --tau) {
+    for (int k = threadIdx.x; k < MV; k += kThreads) S.fslice[k] = C.fields[(size_t)(tau - 1) * MV + k];
+    __syncthreads();
+    t_wrap<Real>(C, s, G, Gt, false, S);
+    lap(1);
+    update_slice<Real>(C, s, tau, 1, P, S, cl, G, A, B, sign, buf, det);
+    if (s == 0)
+      for (int k = threadIdx.x; k < MV; k += kThreads) C.fields[(size_t)(tau - 1) * MV + k] = S.fslice[k];
+    lap(0);
+    slice_potential_smem(C, s, S.fslice, S.v);
+    v_wrap<Real>(C, G, S.v, -1.0, S);
+    lap(1);
+    const int t0s = tau - 1;
+    if (t0s % nw == 0) {
+      cl.sync();
+      double mx, sm;
+      int fs;
+      stabilise<Real>(C, s, t0s / nw, false, G, S, mx, sm, fs, det);
+      sign = close_event(C, s, S, cl, mx, sm, fs, sign);
+      lap(2);
+    }
+    if (P.measure && t0s >= P.meas_first && t0s <= P.meas_last) {
+      measure<Real>(C, s, G, S, cl, sign);
+      lap(3);
+    }
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) C.cyc[s][q] += cyc[q];
+    for (int q = 0; q < 8; ++q) C.cycd[s][q] += det[q];
+    if (s == 0) {
+      C.sign = sign;
+      C.sweep_sign_sum += (double)sign;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Launch helpers (instantiated once per precision unit).
+// --------------------------------------------------------------------------
+static inline cudaError_t set_smem(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename Real>
+static cudaError_t launch_fresh_green_t(ChainDev* chains, int n_chains, int nfl, size_t smem, int mode,
+                                        double* out, int out_chain, cudaStream_t st) {
+  cudaError_t e = set_smem((const void*)fresh_green_kernel<Real>, smem);
+  if (e != cudaSuccess) return e;
+  fresh_green_kernel<Real><<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, mode, out, out_chain);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+static cudaError_t launch_sweep_t(ChainDev* chains, const SweepParams& p, int nfl, size_t smem,
+                                  cudaStream_t st) {
+  cudaError_t e = set_smem((const void*)sweep_kernel<Real>, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.n_chains * nfl, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nfl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sweep_kernel<Real>, chains, p);
+}
+
+}  // namespace
+
+// One pair per precision unit: 0 = FP64, 1 = FP32, 2/3 = float-pair (mixed).
+cudaError_t launch_sweep_fp64(ChainDev* chains, const SweepParams& p, int nfl, size_t smem, cudaStream_t st);
+cudaError_t launch_sweep_fp32(ChainDev* chains, const SweepParams& p, int nfl, size_t smem, cudaStream_t st);
+cudaError_t launch_sweep_mixed(ChainDev* chains, const SweepParams& p, int nfl, size_t smem, cudaStream_t st);
+cudaError_t launch_fresh_green_fp64(ChainDev* chains, int n_chains, int nfl, size_t smem, int mode, double* out,
+                                    int out_chain, cudaStream_t st);
+cudaError_t launch_fresh_green_fp32(ChainDev* chains, int n_chains, int nfl, size_t smem, int mode, double* out,
+                                    int out_chain, cudaStream_t st);
+cudaError_t launch_fresh_green_mixed(ChainDev* chains, int n_chains, int nfl, size_t smem, int mode, double* out,
+                                     int out_chain, cudaStream_t st);
+
+}  // namespace dqmc

@@ -1,0 +1,15 @@
+// Sweep and fresh-G kernels instantiated for the FP64 working Green function.
+#include "dqmc_device.cuh"
+
+namespace dqmc {
+
+cudaError_t launch_sweep_fp64(ChainDev* chains, const SweepParams& p, int nfl, size_t smem, cudaStream_t st) {
+  return launch_sweep_t<double>(chains, p, nfl, smem, st);
+}
+
+cudaError_t launch_fresh_green_fp64(ChainDev* chains, int n_chains, int nfl, size_t smem, int mode, double* out,
+                                    int out_chain, cudaStream_t st) {
+  return launch_fresh_green_t<double>(chains, n_chains, nfl, smem, mode, out, out_chain, st);
+}
+
+}  // namespace dqmc
