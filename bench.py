@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 path")
     ap.add_argument("--peaks", action="store_true", help="measure the matmul peaks used as roofline denominators")
     ap.add_argument("--no-oracle-check", action="store_true", help="skip the max|dG| check against the oracle")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --precision and the workload's delay_k as given instead of tuning them")
     return ap.parse_args()
 
 
@@ -228,12 +230,12 @@ FP32_PEAK_TF = 69.83    # cuBLAS SGEMM (FP32 SIMT) measured on the same part
 DW_PEAK_TF = FP32_PEAK_TF / 12.0 * 1.0
 
 
-def time_path(wl, precision, args, stream, seed, world, local_rank):
+def time_path(wl, precision, args, stream, seed, world, local_rank, delay_k=None):
     """Warm up, then time args.steps sweeps of every chain with CUDA events."""
     import torch
 
     from paper_1704_00131_gb300 import dqmc
-    ens = dqmc.Ensemble(wl.models, wl.chain_model, precision=precision, delay_k=wl.delay_k, seed=seed,
+    ens = dqmc.Ensemble(wl.models, wl.chain_model, precision=precision, delay_k=delay_k or wl.delay_k, seed=seed,
                         stream=stream)
     ens.sweep(max(args.warmup - 1, 0), stats=False)
     st = ens.sweep(1)
@@ -329,8 +331,19 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
     seed = rank_seed(rank)
-    main_prec = args.precision
-    r = time_path(wl, main_prec, args, stream, seed, world, local_rank)
+    main_prec, k_main, k_fp64 = args.precision, wl.delay_k, wl.delay_k
+    tuned = None
+    if not args.no_autotune:
+        # untimed: pick the product family and the delayed-update rank on this GPU
+        from paper_1704_00131_gb300 import autotune
+        ch = autotune.tune(wl.models, wl.chain_model, args.precision, seed=seed, stream=stream, cache=None)
+        main_prec, k_main = ch.precision, ch.delay_k
+        tuned = {"main": ch.as_dict()}
+        if main_prec != "fp64" and not args.no_fp64_compare:
+            cf = autotune.tune(wl.models, wl.chain_model, "fp64", seed=seed, stream=stream, cache=None)
+            k_fp64 = cf.delay_k
+            tuned["fp64"] = cf.as_dict()
+    r = time_path(wl, main_prec, args, stream, seed, world, local_rank, delay_k=k_main)
     ens, st = r["ens"], r["st"]
     props_step = wl.proposals_per_sweep()
     # end to end through the public API with host buffers: fields in (pinned host),
@@ -362,9 +375,10 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
     ens.close()
     fp64 = None
     if main_prec != "fp64" and not args.no_fp64_compare:
-        rf = time_path(wl, "fp64", args, stream, seed, world, local_rank)
+        rf = time_path(wl, "fp64", args, stream, seed, world, local_rank, delay_k=k_fp64)
         rf["ens"].close()
-        fp64 = {"value": rf["value"], "unit": UNIT, "ms_per_step": rf["ms_step"], "roofline": rf["roofline"],
+        fp64 = {"value": rf["value"], "unit": UNIT, "ms_per_step": rf["ms_step"], "delay_k": k_fp64,
+                "roofline": rf["roofline"],
                 "critical_chain_ms": {k: round(rf["st"][k], 3) for k in ("ms_update", "ms_wrap", "ms_stab")},
                 "prec_green_max": rf["st"]["prec_green_max"], "prec_green_mean": rf["st"]["prec_green_mean"]}
     cpu = None
@@ -378,7 +392,7 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "mixed": "f32x2+f64", "mixed_tc": "bf16-split+f32x2+f64"}[main_prec],
             "data": "synthetic (seeded Philox fields, random-init Markov chains)",
             "config": {"workload": wl.name, "chains": wl.n_chains, "precision": main_prec,
-                       "delay_k": wl.delay_k, "n_wrap": 10,
+                       "delay_k": k_main, "n_wrap": 10, "autotune": tuned,
                        "l2": "resident state > L2 (per-chain G, UDV storage and workspace, "
                              f"{ens_bytes(wl, main_prec) / 1e9:.2f} GB); no flush"},
             "sweeps_per_s": 1000.0 / r["ms_step"] * world,
