@@ -96,6 +96,7 @@ def lib():
         _lib.orc_logdet_grad.argtypes = [vp, vp, vp, vp, vp, vp]
         _lib.orc_green_displaced.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         _lib.orc_energy_grad.argtypes = [vp, vp, vp, vp, vp]
+        _lib.orc_tau_observables.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp]
         del i32
     return _lib
 
@@ -296,6 +297,26 @@ def green_displaced(model: Model, fields: np.ndarray, flavor: int, tau: int):
     G0t = np.zeros((model.N, model.N))
     _check(lib().orc_green_displaced(model.cref(), _ptr(f), flavor, tau, _ptr(Gt0), _ptr(G0t)), "green_displaced")
     return Gt0, G0t
+
+
+def tau_observables(model: Model, fields: np.ndarray, n_tau: int, phase=None):
+    """Per displacement tau = 0..n_tau and flavor s: (a_s, c_s, p_s) =
+    (sum_x G(tau,0)_xx, -sum_xy ph_x ph_y G(0,tau)_yx G(tau,0)_xy, sum_x ph_x (1 - G(tau,tau)_xx)),
+    every Green function from scratch; returns (out[n_tau+1, nfl, 3], signs[nfl])."""
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    out = np.zeros((n_tau + 1, model.n_flavors, 3))
+    sg = np.zeros(model.n_flavors, dtype=np.int32)
+    ph = None if phase is None else np.ascontiguousarray(phase, dtype=np.float64)
+    _check(lib().orc_tau_observables(model.cref(), _ptr(f), n_tau, None if ph is None else _ptr(ph), _ptr(out),
+                                     _ptr(sg)), "tau_observables")
+    return out, sg
+
+
+def szz_from_tau(obs: np.ndarray) -> np.ndarray:
+    """sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)> of one configuration from the
+    two-flavor (a, c, p) sums (flavor 0 = spin up, flavor 1 = spin down)."""
+    m = obs[:, 0, 2] - obs[:, 1, 2]
+    return (m * m[0] + obs[:, 0, 1] + obs[:, 1, 1]) / 4.0
 
 
 def energy_grad(model: Model, fields: np.ndarray):

@@ -1211,3 +1211,53 @@ out:
   model_free(&M);
   return st;
 }
+
+/* Time-displaced measurement of one configuration (the tau_m step at the end
+ * of a sweep, Algorithm 1; the ObserT quantities of Sec. 5.2): for each
+ * displacement tau = 0..n_tau and flavor s, with G^s(tau,0), G^s(0,tau) and
+ * G^s(tau,tau) each computed from scratch through the UDV chains,
+ *   a_s(tau) = sum_x G^s(tau,0)_xx                        (local Green function)
+ *   c_s(tau) = -sum_xy ph_x ph_y G^s(0,tau)_yx G^s(tau,0)_xy
+ *              (Wick-connected part of sum_xy ph_x ph_y <n_xs(tau) n_ys(0)>)
+ *   p_s(tau) = sum_x ph_x (1 - G^s(tau,tau)_xx)          (phase-weighted density)
+ * out[(tau * nfl + s) * 3 + {0, 1, 2}] = (a_s, c_s, p_s); ph = NULL means 1.
+ * sign_out[s] = sign of det(1 + B^s(beta,0)).
+ * In one configuration the flavors are independent, so for two flavors
+ *   sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)> =
+ *     [(p_0(tau) - p_1(tau)) (p_0(0) - p_1(0)) + c_0(tau) + c_1(tau)] / 4. */
+int orc_tau_observables(const orc_model* m, const int8_t* fields, int n_tau, const double* ph, double* out,
+                        int* sign_out) {
+  model_t M;
+  int st = model_load(m, &M);
+  if (st) return st;
+  const int N = M.N, nfl = M.nfl;
+  if (n_tau < 0 || n_tau > M.L) { model_free(&M); return ORC_EINVAL; }
+  double* Gt0 = (double*)malloc(sizeof(double) * N * N);
+  double* G0t = (double*)malloc(sizeof(double) * N * N);
+  double* Gtt = (double*)malloc(sizeof(double) * N * N);
+  for (int s = 0; s < nfl && !st; ++s) {
+    for (int tau = 0; tau <= n_tau && !st; ++tau) {
+      double ld;
+      int sg;
+      st = orc_green_displaced(m, fields, s, tau, Gt0, G0t);
+      if (!st) st = orc_green_udv(m, fields, s, tau, Gtt, &ld, &sg);
+      if (st) break;
+      if (tau == 0) sign_out[s] = sg;
+      double a = 0.0, c = 0.0, p = 0.0;
+      for (int x = 0; x < N; ++x) {
+        const double px = ph ? ph[x] : 1.0;
+        a += Gt0[x * N + x];
+        p += px * (1.0 - Gtt[x * N + x]);
+        for (int y = 0; y < N; ++y) {
+          const double py = ph ? ph[y] : 1.0;
+          c -= px * py * G0t[y * N + x] * Gt0[x * N + y];
+        }
+      }
+      double* o = out + ((size_t)tau * nfl + s) * 3;
+      o[0] = a; o[1] = c; o[2] = p;
+    }
+  }
+  free(Gt0); free(G0t); free(Gtt);
+  model_free(&M);
+  return st;
+}
