@@ -167,6 +167,38 @@ dqmc_status dqmc_greens(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t fr
  * sign_sum[c] = sum of signs, n_meas[c] = number of measurements (host arrays). */
 dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas);
 
+/* Time-displaced Green functions of every chain's current configuration: the
+ * tau measurement at the end of a sweep (Algorithm 1), giving the quantities
+ * that ObserT receives (Sec. 5.2), with the "Precision tau" monitor of the
+ * wrapped against the recomputed time-displaced functions (Sec. 2.3, info file).
+ * From G(0) the library wraps, slice by slice,
+ *     G(tau,0) = B_tau G(tau-1,0),   G(0,tau) = G(0,tau-1) B_tau^-1,
+ *     G(tau,tau) = B_tau G(tau-1,tau-1) B_tau^-1,
+ * with G(0,0) = G(0), G(0,0^+) = -(1 - G(0)), and replaces all three by the
+ * stable recompute from the UDV chains at every tau = j n_wrap (FP64 throughout,
+ * whatever the sweep precision).  The fields, the working G and the stored
+ * chains of the ensemble are left as they are.
+ *     n_tau      chain c measures tau = 0 .. min(n_tau, L_c); 0 <= n_tau <= max L
+ *     site_phase host [sum over models of n_sites] (model order) phases ph_x,
+ *                or NULL for ph = 1
+ * Outputs (host):
+ *     out  [n_chains][n_tau + 1][n_flavors][3]:
+ *            a = sum_x G^s(tau,0)_xx,
+ *            c = -sum_xy ph_x ph_y G^s(0,tau)_yx G^s(tau,0)_xy,
+ *            p = sum_x ph_x (1 - G^s(tau,tau)_xx);  rows tau > L_c are 0.
+ *          For the spin-z decoupling (flavor 0 up, 1 down),
+ *            sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)> =
+ *              [(p_0(tau) - p_1(tau)) (p_0(0) - p_1(0)) + c_0(tau) + c_1(tau)] / 4
+ *          and the local Green function is (a_0 + a_1) / (n_flavors N).
+ *     sign [n_chains][n_flavors]: sign of det(1 + B^s(beta,0)) (multiply the
+ *          flavors for the configuration's sign)
+ *     prec [2] or NULL: mean over stabilisation points (chains, flavors) of the
+ *          element-mean |wrapped - recomputed| of G(tau,0) and G(0,tau), and the
+ *          largest element difference.
+ * DQMC_EUNSTABLE if a recompute meets a singular matrix. */
+dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_phase, double* out, int32_t* sign,
+                             double* prec);
+
 /* Derivatives of log|det(1 + B^s(beta,0))| on fixed field configurations of
  * model `model_index` (FP64):
  *     d log|det| = sum_tau Tr[(1 - G(tau-1)) B_tau^-1 dB_tau]

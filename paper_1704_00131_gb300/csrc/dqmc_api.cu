@@ -127,6 +127,7 @@ struct dqmc_ctx {
   uint64_t sweep_counter = 0;
   int maxN = 0, maxld = 0, maxMV = 0;
   double* scratch = nullptr;  // [nfl][maxN][maxN] FP64 for dqmc_greens
+  double* tau_work = nullptr;  // [n_chains][nfl][4][maxN][maxld] FP64 for dqmc_measure_tau (on first use)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -582,6 +583,83 @@ dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* 
   return DQMC_OK;
 }
 
+dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_phase, double* out, int32_t* sign,
+                             double* prec) {
+  if (!ctx) return DQMC_EINVAL;
+  int maxL = 0;
+  for (const ChainDev& C : ctx->chains_h) maxL = C.L > maxL ? C.L : maxL;
+  if (n_tau < 0 || n_tau > maxL || !out || !sign)
+    return fail(ctx, DQMC_EINVAL, "n_tau outside 0..%d, or null output", maxL);
+  const int nch = (int)ctx->chains_h.size(), nfl = ctx->nfl, pld = ctx->maxN;
+  std::vector<size_t> moff(ctx->models.size() + 1, 0);
+  for (size_t m = 0; m < ctx->models.size(); ++m) moff[m + 1] = moff[m] + ctx->models[m].d.n_sites;
+  std::vector<double> ph((size_t)nch * pld, 0.0);
+  for (int c = 0; c < nch; ++c) {
+    const int m = ctx->chain_model[c];
+    for (int x = 0; x < ctx->chains_h[c].N; ++x) {
+      const double v = site_phase ? site_phase[moff[m] + x] : 1.0;
+      if (!std::isfinite(v)) return fail(ctx, DQMC_EINVAL, "non-finite site phase");
+      ph[(size_t)c * pld + x] = v;
+    }
+  }
+  const size_t tw_stride = (size_t)4 * ctx->maxN * ctx->maxld;
+  if (!ctx->tau_work) {
+    if (cudaMalloc((void**)&ctx->tau_work, sizeof(double) * tw_stride * nch * nfl) != cudaSuccess) {
+      ctx->tau_work = nullptr;
+      cudaGetLastError();
+      return fail(ctx, DQMC_ENOMEM, "no device memory for the time-displaced workspace");
+    }
+  }
+  const size_t nobs = (size_t)nch * (n_tau + 1) * nfl * 3;
+  double *ph_d = nullptr, *obs_d = nullptr, *prec_d = nullptr;
+  int* sg_d = nullptr;
+  dqmc_status st = DQMC_OK;
+  auto cleanup = [&]() {
+    cudaFree(ph_d);
+    cudaFree(obs_d);
+    cudaFree(prec_d);
+    cudaFree(sg_d);
+  };
+  if (cudaMalloc((void**)&ph_d, sizeof(double) * ph.size()) != cudaSuccess ||
+      cudaMalloc((void**)&obs_d, sizeof(double) * nobs) != cudaSuccess ||
+      cudaMalloc((void**)&prec_d, sizeof(double) * nch * nfl * 3) != cudaSuccess ||
+      cudaMalloc((void**)&sg_d, sizeof(int) * nch * nfl) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, DQMC_ENOMEM, "no device memory for the time-displaced outputs");
+  }
+  std::vector<double> prec_h((size_t)nch * nfl * 3);
+  do {
+    if (cudaMemcpyAsync(ph_d, ph.data(), sizeof(double) * ph.size(), cudaMemcpyHostToDevice, ctx->stream) !=
+        cudaSuccess) { st = fail(ctx, DQMC_ECUDA, "phase upload failed"); break; }
+    dqmc::set_smem_bytes(ctx->smem);
+    cudaError_t e = dqmc::launch_tau_measure(ctx->chains_d, nch, nfl, n_tau, ph_d, pld, ctx->tau_work, tw_stride,
+                                             obs_d, prec_d, sg_d, ctx->stream);
+    if (e != cudaSuccess) { st = fail(ctx, DQMC_ECUDA, "tau measurement launch: %s", cudaGetErrorString(e)); break; }
+    if (cudaMemcpyAsync(out, obs_d, sizeof(double) * nobs, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(sign, sg_d, sizeof(int) * nch * nfl, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(prec_h.data(), prec_d, sizeof(double) * prec_h.size(), cudaMemcpyDeviceToHost,
+                        ctx->stream) != cudaSuccess) { st = fail(ctx, DQMC_ECUDA, "download failed"); break; }
+    st = download_chains(ctx);
+    if (st) break;
+    for (const ChainDev& C : ctx->chains_h)
+      if (C.error) { st = fail(ctx, DQMC_EUNSTABLE, "chain %u: singular matrix in the stabilisation", C.chain_id); break; }
+  } while (false);
+  cleanup();
+  if (st) return st;
+  if (prec) {
+    double sum = 0.0, mx = 0.0, ev = 0.0;
+    for (size_t q = 0; q < prec_h.size(); q += 3) {
+      sum += prec_h[q];
+      mx = prec_h[q + 1] > mx ? prec_h[q + 1] : mx;
+      ev += prec_h[q + 2];
+    }
+    prec[0] = ev > 0 ? sum / ev : 0.0;
+    prec[1] = mx;
+  }
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_get_fields(dqmc_ctx* ctx, int8_t* out, uint64_t* rng_counter) {
   if (!ctx) return DQMC_EINVAL;
   if (!out) return fail(ctx, DQMC_EINVAL, "null output");
@@ -795,6 +873,7 @@ void dqmc_destroy(dqmc_ctx* ctx) {
   cudaFree(ctx->chains_d);
   cudaFree(ctx->order_d);
   cudaFree(ctx->scratch);
+  cudaFree(ctx->tau_work);
   for (void* p : ctx->model_allocs) cudaFree(p);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);

@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(_PKG, "libdqmc.so")
 DQMC_OK, DQMC_EINVAL, DQMC_ENOMEM, DQMC_ECUDA, DQMC_EUNSTABLE, DQMC_ETIMEOUT, DQMC_ESTATE = range(7)
 PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tc": 3}
 
-EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_logdet_backward",
+EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_measure_tau", "dqmc_logdet_backward",
             "dqmc_get_fields", "dqmc_set_fields", "dqmc_last_error", "dqmc_destroy"]
 
 
@@ -105,6 +105,8 @@ def load() -> ctypes.CDLL:
     L.dqmc_greens.restype = ctypes.c_int
     L.dqmc_measure.argtypes = [vp, vp, vp, vp]
     L.dqmc_measure.restype = ctypes.c_int
+    L.dqmc_measure_tau.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.dqmc_measure_tau.restype = ctypes.c_int
     L.dqmc_logdet_backward.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     L.dqmc_logdet_backward.restype = ctypes.c_int
     L.dqmc_energy_backward.argtypes = [vp, i32, vp, i32, vp, vp, vp]
@@ -124,6 +126,13 @@ def load() -> ctypes.CDLL:
 
 def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def szz_tau(obs: np.ndarray) -> np.ndarray:
+    """sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)> per chain and tau from the two-flavor
+    sums of Ensemble.measure_tau (flavor 0 up, flavor 1 down)."""
+    m = obs[..., 0, 2] - obs[..., 1, 2]
+    return (m * m[..., :1] + obs[..., 0, 1] + obs[..., 1, 1]) / 4.0
 
 
 class Ensemble:
@@ -222,6 +231,27 @@ class Ensemble:
         nm = np.zeros(n, dtype=np.int64)
         self._check(self._lib.dqmc_measure(self._h, _p(out), _p(ss), _p(nm)))
         return out, ss, nm
+
+    def measure_tau(self, n_tau: int, site_phase=None):
+        """Time-displaced sums of every chain's current configuration.
+
+        Returns (obs, sign, prec): obs[c, tau, s] = (a, c, p) with
+        a = sum_x G(tau,0)_xx, c = -sum_xy ph_x ph_y G(0,tau)_yx G(tau,0)_xy,
+        p = sum_x ph_x (1 - G(tau,tau)_xx); sign[c, s] = sign of det(1 + B^s(beta,0));
+        prec = (mean, max) of |wrapped - recomputed| time-displaced G ("Precision tau").
+        site_phase: one array per model (or None for unit phases)."""
+        nfl = max(m.hopping.shape[0] for m in self.models)
+        obs = np.zeros((self.n_chains, int(n_tau) + 1, nfl, 3))
+        sg = np.zeros((self.n_chains, nfl), dtype=np.int32)
+        prec = np.zeros(2)
+        ph = None
+        if site_phase is not None:
+            ph = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in site_phase]))
+            if ph.size != sum(m.N for m in self.models):
+                raise DqmcError(DQMC_EINVAL, "site_phase must hold one phase per site of every model")
+        self._check(self._lib.dqmc_measure_tau(self._h, int(n_tau), None if ph is None else _p(ph), _p(obs), _p(sg),
+                                               _p(prec)))
+        return obs, sg, prec
 
     def get_fields(self):
         sizes = [self.model_of(c).L * self.model_of(c).n_vertices for c in range(self.n_chains)]

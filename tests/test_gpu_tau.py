@@ -1,0 +1,124 @@
+"""GPU parity of the time-displaced measurement (dqmc_measure_tau) against the oracle.
+
+The GPU wraps G(tau,0), G(0,tau), G(tau,tau) slice by slice between the
+stabilisation points; the oracle recomputes every one from scratch through the
+UDV chains.  Both are FP64, so each Green-function entry agrees to the 1e-10
+of the FP64 paths; the sums a (N terms), p (N terms) and c (N^2 products of
+O(1) entries) are compared at N * 1e-10, N * 1e-10 and 2 N^2 * 1e-10.
+"""
+import numpy as np
+import pytest
+
+from paper_1704_00131_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00131_gb300 import build_ext, dqmc
+    build_ext.build()
+    return dqmc
+
+
+def omodel(orc, m):
+    return orc.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+
+
+def check_chain(orc, m, fields, obs_c, sign_c, n_tau, ph):
+    om = omodel(orc, m)
+    ntc = min(n_tau, m.L)
+    ref, sg = orc.tau_observables(om, fields, ntc, ph)
+    N = m.N
+    tol = np.array([N * 1e-10, 2 * N * N * 1e-10, N * 1e-10])
+    d = np.abs(obs_c[:ntc + 1] - ref)
+    assert (d <= tol).all(), f"max diff per quantity {d.max(axis=(0, 1))}, tolerance {tol}"
+    assert np.all(obs_c[ntc + 1:] == 0.0)
+    assert list(sign_c) == list(sg)
+
+
+@pytest.mark.parametrize("ft", [1, 2])
+def test_tau_measure_single_chain(dq, orc, ft):
+    m = W.ModelSpec(W.square_lattice(4, 4, tp=-0.1, mu=-0.3), U=4.0, dtau=0.1, L=20, n_wrap=5, field_type=ft)
+    f = W.random_fields(ft, m.L, m.n_vertices, seed=17)
+    ens = dq.Ensemble([m], [0], fields=[f], precision="fp64")
+    ph = W.sublattice_signs_square(4, 4)
+    obs, sg, prec = ens.measure_tau(m.L, [ph])
+    check_chain(orc, m, f, obs[0], sg[0], m.L, ph)
+    assert 0.0 <= prec[0] < 1e-11 and prec[1] < 1e-9
+    # partial window
+    obs2, _, _ = ens.measure_tau(7, [ph])
+    assert np.abs(obs2[0] - obs[0, :8]).max() < 1e-12
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tau_measure_batch_leaves_the_chains_alone(dq, orc, precision):
+    """Uneven chains after a sweep: every chain matches the oracle on its current
+    fields, and a twin ensemble that is not measured continues bit for bit alike."""
+    models = [W.ModelSpec(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=20, n_wrap=10),
+              W.ModelSpec(W.honeycomb_lattice(3, 3), U=3.0, dtau=0.1, L=10, n_wrap=5),
+              W.ModelSpec(W.chain_lattice(13, mu=0.2, periodic=True), U=2.0, dtau=0.125, L=16, n_wrap=4,
+                          field_type=2)]
+    cm = [0, 1, 2, 0]
+    phases = [W.sublattice_signs_square(4, 4), W.sublattice_signs_honeycomb(3, 3),
+              np.cos(np.pi * np.arange(13) / 6.5)]
+    a = dq.Ensemble(models, cm, precision=precision, delay_k=8, seed=5)
+    b = dq.Ensemble(models, cm, precision=precision, delay_k=8, seed=5)
+    a.sweep(1)
+    b.sweep(1)
+    fa, _ = a.get_fields()
+    G_before = [a.greens(c, s)[0] for c in range(len(cm)) for s in (0, 1)]
+    n_tau = 20
+    obs, sg, prec = a.measure_tau(n_tau, phases)
+    for c in range(len(cm)):
+        mi = cm[c]
+        check_chain(orc, models[mi], fa[c], obs[c], sg[c], n_tau, phases[mi])
+    assert prec[1] < 1e-8
+    G_after = [a.greens(c, s)[0] for c in range(len(cm)) for s in (0, 1)]
+    assert all(np.array_equal(x, y) for x, y in zip(G_before, G_after))
+    a.sweep(2)
+    b.sweep(2)
+    fa2, ca = a.get_fields()
+    fb2, cb = b.get_fields()
+    assert ca == cb and all(np.array_equal(x, y) for x, y in zip(fa2, fb2))
+    for c in range(len(cm)):
+        for s in (0, 1):
+            assert np.array_equal(a.greens(c, s)[0], b.greens(c, s)[0])
+    a.close()
+    b.close()
+
+
+def test_tau_measure_spin_correlation_identity(dq):
+    """tau = 0 of the S^z S^z sum equals the equal-time value from G(0):
+    sum_xy ph_x ph_y <S^z_x S^z_y> with the same Wick rule at equal times."""
+    m = W.ModelSpec(W.square_lattice(6, 6), U=4.0, dtau=0.1, L=20, n_wrap=10)
+    ens = dq.Ensemble([m], [0], precision="fp64", seed=3)
+    ens.sweep(1)
+    ph = W.sublattice_signs_square(6, 6)
+    obs, _, _ = ens.measure_tau(4, [ph])
+    szz = dq.szz_tau(obs)[0]
+    G = [ens.greens(0, s, fresh=True)[0] for s in (0, 1)]
+    n = [1.0 - np.diag(g) for g in G]
+    mz = np.sum(ph * (n[0] - n[1]))
+    conn = sum(np.einsum("x,y,yx,xy->", ph, ph, np.eye(36) - g, g) for g in G)
+    assert szz[0] == pytest.approx((mz * mz + conn) / 4.0, rel=1e-10, abs=1e-10)
+    ens.close()
+
+
+def test_tau_measure_invalid_arguments(dq):
+    m = W.ModelSpec(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=20, n_wrap=10)
+    ens = dq.Ensemble([m], [0], precision="fp64", seed=1)
+    for bad in (-1, 21):
+        with pytest.raises(dq.DqmcError) as e:
+            ens.measure_tau(bad)
+        assert e.value.status == dq.DQMC_EINVAL
+    with pytest.raises(dq.DqmcError):
+        ens.measure_tau(4, [np.ones(3)])
+    with pytest.raises(dq.DqmcError) as e:
+        ens.measure_tau(4, [np.full(16, np.nan)])
+    assert e.value.status == dq.DQMC_EINVAL
+    ens.close()
