@@ -1082,6 +1082,125 @@ __device__ void lu_solve(int N, int ld, const double* LU, const int* piv, double
   }
 }
 
+// Float-pair versions of lu_factor / lu_solve for the mixed path's middle
+// matrix.  Every row of Mid has an entry of order one (for each i either
+// Db_R,i = 1 or Ds_R,i = 1, and likewise for the columns), so Mid, its LU
+// factors and the solution X = Mid^-1 Db_R^-1 Q_R^T stay inside the float
+// range; entries that underflow are below 1e-38 of their row and change G by
+// less than that in absolute value.  Pivots are chosen on |hi + lo| in FP64 and
+// divisions use the FP64 reciprocal of the pivot.
+__device__ int lu_factor_dd(int N, int ld, dd* A, int* piv, double& logdet, int& sign, Smem& S) {
+  const int tid = threadIdx.x;
+  double ld_ = 0.0;
+  int sg = 1;
+  for (int k = 0; k < N; ++k) {
+    double bv = -1.0;
+    int bi = N;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const double a = fabs(to_d(A[(size_t)i * ld + k]));
+      if (a > bv) { bv = a; bi = i; }
+    }
+    const int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N) return 1;
+    if (tid == 0) piv[k] = p;
+    const double pv = to_d(A[(size_t)p * ld + k]);
+    if (!(pv != 0.0)) return 1;
+    if (p != k) {
+      for (int j = tid; j < N; j += kThreads) {
+        const dd t = A[(size_t)k * ld + j];
+        A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
+        A[(size_t)p * ld + j] = t;
+      }
+      sg = -sg;
+    }
+    __syncthreads();
+    const double d = to_d(A[(size_t)k * ld + k]);
+    ld_ += log(fabs(d));
+    if (d < 0.0) sg = -sg;
+    const dd dinv = from_d<dd>(1.0 / d);
+    for (int i = k + 1 + tid; i < N; i += kThreads) A[(size_t)i * ld + k] = dd_mul(A[(size_t)i * ld + k], dinv);
+    __syncthreads();
+    const int rem = N - k - 1;
+    for (int e = tid; e < rem * rem; e += kThreads) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      const dd l = A[(size_t)i * ld + k];
+      A[(size_t)i * ld + j] = dd_fma({-l.hi, -l.lo}, A[(size_t)k * ld + j], A[(size_t)i * ld + j]);
+    }
+    __syncthreads();
+  }
+  logdet = ld_;
+  sign = sg;
+  return 0;
+}
+
+__device__ void lu_solve_dd(int N, int ld, const dd* LU, const int* piv, dd* B, dd* qred) {
+  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
+  for (int k = 0; k < N; ++k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int j = tid; j < N; j += kThreads) {
+        const dd t = B[(size_t)k * ld + j];
+        B[(size_t)k * ld + j] = B[(size_t)p * ld + j];
+        B[(size_t)p * ld + j] = t;
+      }
+    __syncthreads();
+  }
+  const dd zero = {0.f, 0.f};
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int ii = (pass == 0 ? 1 : N - 1); pass == 0 ? ii < N : ii >= 0; ii += (pass == 0 ? 1 : -1)) {
+      const int klo = pass == 0 ? 0 : ii + 1, khi = pass == 0 ? ii : N;
+      const dd* lrow = LU + (size_t)ii * ld;
+      for (int c0 = 0; c0 < N; c0 += 128) {
+        dd w[4] = {zero, zero, zero, zero};
+        int k = klo + rg;
+        for (; k + 8 < khi; k += 16) {
+          dd x[2][4], l[2];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            l[r] = lrow[k + 8 * r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int j = c0 + lane + 32 * q;
+              x[r][q] = (j < N) ? B[(size_t)(k + 8 * r) * ld + j] : zero;
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = dd_fma(l[r], x[r][q], w[q]);
+        }
+        for (; k < khi; k += 8) {
+          const dd l = lrow[k];
+          const dd* brow = B + (size_t)k * ld;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = c0 + lane + 32 * q;
+            if (j < N) w[q] = dd_fma(l, brow[j], w[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
+        __syncthreads();
+        if (rg == 0) {
+          const dd dinv = pass == 1 ? from_d<dd>(1.0 / to_d(lrow[ii])) : dd{1.f, 0.f};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = c0 + lane + 32 * q;
+            dd t = zero;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) t = dd_add(t, qred[r * 128 + lane + 32 * q]);
+            if (j < N) {
+              const dd v = rsub(B[(size_t)ii * ld + j], t);
+              B[(size_t)ii * ld + j] = pass == 1 ? dd_mul(v, dinv) : v;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
 // Stable G from a right chain R (B(tau,0) = Q_R D_R T_R) and a left chain Lf
 // (B(beta,tau)^T = Q_L D_L T_L) by scale separation, D = Db Ds with
 // Db = max(D,1), Ds = min(D,1):
@@ -1710,8 +1829,8 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
 __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, double* Gout, double& logdet,
                                     int& sign, Smem& S) {
   const int N = C.N, ld = C.ld;
-  double* W0 = wmat(C, s, 0);
-  double* W1 = wmat(C, s, 1);
+  dd* W0d = reinterpret_cast<dd*>(wmat(C, s, 0));
+  dd* W1d = reinterpret_cast<dd*>(wmat(C, s, 1));
   dd* QRd = reinterpret_cast<dd*>(wmat(C, s, 3));
   dd* QLd = reinterpret_cast<dd*>(wmat(C, s, 4));
   dd* TRd = reinterpret_cast<dd*>(wmat(C, s, 7));
@@ -1720,8 +1839,8 @@ __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, dou
   to_dd_mat(N, ld, Lf.Q, QLd);
   to_dd_mat(N, ld, R.T, TRd);
   to_dd_mat(N, ld, Lf.T, TLd);
-  gemm_dd<true, false, false>(C, s, S, N, N, N, QRd, ld, QLd, ld, reinterpret_cast<dd*>(W0), ld);
-  gemm_dd<false, true, false>(C, s, S, N, N, N, TRd, ld, TLd, ld, reinterpret_cast<dd*>(W1), ld);
+  gemm_dd<true, false, false>(C, s, S, N, N, N, QRd, ld, QLd, ld, W0d, ld);
+  gemm_dd<false, true, false>(C, s, S, N, N, N, TRd, ld, TLd, ld, W1d, ld);
   double* ibR = wvec(C, s, 5);
   double* ibL = wvec(C, s, 6);
   for (int i = threadIdx.x; i < N; i += kThreads) {
@@ -1729,29 +1848,30 @@ __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, dou
     ibL[i] = 1.0 / (Lf.D[i] > 1.0 ? Lf.D[i] : 1.0);
   }
   __syncthreads();
+  // Mid (float pairs, scale factors applied in FP64) in W0; right-hand side in W1
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
     const double dR = R.D[i], dL = Lf.D[j];
     const double dsR = dR > 1.0 ? 1.0 : dR, dsL = dL > 1.0 ? 1.0 : dL;
-    const double qq = to_d(reinterpret_cast<const dd*>(W0)[(size_t)i * ld + j]);
-    const double tt = to_d(reinterpret_cast<const dd*>(W1)[(size_t)i * ld + j]);
-    W0[(size_t)i * ld + j] = qq * (ibR[i] * ibL[j]) + dsR * tt * dsL;
+    const double qq = to_d(W0d[(size_t)i * ld + j]);
+    const double tt = to_d(W1d[(size_t)i * ld + j]);
+    W0d[(size_t)i * ld + j] = from_d<dd>(qq * (ibR[i] * ibL[j]) + dsR * tt * dsL);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
-    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] * ibR[i];
+    W1d[(size_t)i * ld + j] = from_d<dd>(R.Q[(size_t)j * ld + i] * ibR[i]);
   }
   __syncthreads();
   double ldm;
   int smi;
   int* piv = C.iwork[s] + ld;
-  if (lu_factor(N, ld, W0, piv, ldm, smi, S)) return 1;
-  lu_solve(N, ld, W0, piv, W1, S.qred);
+  if (lu_factor_dd(N, ld, W0d, piv, ldm, smi, S)) return 1;
+  lu_solve_dd(N, ld, W0d, piv, W1d, reinterpret_cast<dd*>(S.qred));
   dd* Yd = reinterpret_cast<dd*>(wmat(C, s, 9));
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
-    Yd[(size_t)i * ld + j] = from_d<dd>(W1[(size_t)i * ld + j] * ibL[i]);
+    Yd[(size_t)i * ld + j] = from_d<dd>(to_d(W1d[(size_t)i * ld + j]) * ibL[i]);
   }
   __syncthreads();
   gemm_dd<false, false, false>(C, s, S, N, N, N, QLd, ld, Yd, ld, reinterpret_cast<dd*>(Gout), ld);
