@@ -230,6 +230,15 @@ FP32_PEAK_TF = 69.83    # cuBLAS SGEMM (FP32 SIMT) measured on the same part
 DW_PEAK_TF = FP32_PEAK_TF / 12.0 * 1.0
 
 
+# DRAM bytes (read + write) per launch of the sweep kernel, from one ncu capture
+# of the full workload (profiles/dram_sweep_kernel_square256.md), keyed by
+# (precision, workload, delay_k); other cases report null.
+TRAFFIC_BYTES = {
+    ("mixed", "square 8x8/12x12 x256 chains", 16): 10356692224 + 26193950208,
+    ("fp64", "square 8x8/12x12 x256 chains", 16): 10076649728 + 21551729664,
+}
+
+
 def time_path(wl, precision, args, stream, seed, world, local_rank, delay_k=None):
     """Warm up, then time args.steps sweeps of every chain with CUDA events."""
     import torch
@@ -277,8 +286,10 @@ def time_path(wl, precision, args, stream, seed, world, local_rank, delay_k=None
         peak, src, kern = DW_PEAK_TF, ("double-word arithmetic on the FP32 pipes: measured SGEMM rate / 12 "
                                        "FP32 operations per float-pair multiply-add (the FP64 share of the "
                                        "stabilisation runs at the 1.10 TFLOP/s FP64 rate)"), "sweep_kernel<dd>"
+    traffic = TRAFFIC_BYTES.get((precision, wl.name, delay_k or wl.delay_k))
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": kern, "peak_source": src}
+            "traffic": traffic, "traffic_unit": "bytes per launch (DRAM read + write, ncu)" if traffic else None,
+            "kernel": kern, "peak_source": src}
     return {"ens": ens, "st": st, "ms_step": ms_step, "value": value, "roofline": roof, "clocks": clk.summary(),
             "algorithmic_tflop_per_step": flops_per_step / 1e12}
 
