@@ -968,237 +968,195 @@ __device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, U
   return detq;
 }
 
-// LU with partial pivoting in place (rows swapped whole).  Returns 0 or 1 if singular.
-__device__ int lu_factor(int N, int ld, double* A, int* piv, double& logdet, int& sign, Smem& S) {
+// LU and solves of the middle matrix, blocked, templated on double and float
+// pairs.  On the mixed path they run in float pairs on the FP32 pipes: every
+// row of Mid has an entry of order one (for each i either Db_R,i = 1 or
+// Ds_R,i = 1, and likewise for the columns), so Mid, its LU factors and the
+// solution X = Mid^-1 Db_R^-1 Q_R^T stay inside the float range; entries that
+// underflow are below 1e-38 of their row and change G by less than that in
+// absolute value.  Pivots are chosen on |hi + lo| in FP64 and divisions use the
+// FP64 reciprocal of the pivot.
+//
+// Blocking: a panel of PB columns (or a block of PB rows of the right-hand
+// sides) is staged in the shared GEMM buffer and finished there; everything
+// beyond it is updated by one accumulate-GEMM of depth PB.  PB is the largest
+// power of two <= 16 with PB (N + PB) elements fitting the buffer.
+__device__ __forceinline__ double rneg(double a) { return -a; }
+__device__ __forceinline__ dd rneg(dd a) { return {-a.hi, -a.lo}; }
+
+__device__ inline int lu_block_width(int N) {
+  const int cap = 2 * 16 * kGemmMaxTile;
+  int pb = 16;
+  while (pb > 1 && pb * (N + pb) > cap) pb >>= 1;
+  return pb;
+}
+
+// C += A B (row-major, no transposes) on the register-tiled CTA products.
+__device__ inline void gemm_acc(int M, int Nc, int Kd, const double* A, int lda, const double* B, int ldb, double* C,
+                                int ldc, Smem& S) {
+  const int r = gemm_pick_r(M > Nc ? M : Nc);
+  if (r == 3) cta_gemm_r<double, false, false, 3, true>(M, Nc, Kd, A, lda, B, ldb, C, ldc, S.gemm);
+  else if (r == 5) cta_gemm_r<double, false, false, 5, true>(M, Nc, Kd, A, lda, B, ldb, C, ldc, S.gemm);
+  else cta_gemm_r<double, false, false, 4, true>(M, Nc, Kd, A, lda, B, ldb, C, ldc, S.gemm);
+}
+__device__ inline void gemm_acc(int M, int Nc, int Kd, const dd* A, int lda, const dd* B, int ldb, dd* C, int ldc,
+                                Smem& S) {
+  gemm_dd_tiles<false, false, true>(M, Nc, Kd, A, lda, B, ldb, C, ldc, reinterpret_cast<dd*>(S.gemm));
+}
+
+// P A = L U in place (unit L below the diagonal, rows interchanged whole);
+// piv[k] = row interchanged with row k.  tmp: PB x N scratch (ld).  Returns 1 if
+// a pivot column has no finite nonzero entry.
+template <typename T>
+__device__ int lu_factor_blk(int N, int ld, T* A, int* piv, T* tmp, double& logdet, int& sign, Smem& S) {
   const int tid = threadIdx.x;
+  const int PB = lu_block_width(N);
+  T* P = reinterpret_cast<T*>(S.gemm);
   double ld_ = 0.0;
   int sg = 1;
-  for (int k = 0; k < N; ++k) {
-    double bv = -1.0;
-    int bi = N;
-    for (int i = k + tid; i < N; i += kThreads) {
-      const double a = fabs(A[(size_t)i * ld + k]);
-      if (a > bv) { bv = a; bi = i; }
+  for (int k0 = 0; k0 < N; k0 += PB) {
+    const int nb = (N - k0 < PB) ? N - k0 : PB, rows = N - k0, n2 = N - k0 - nb;
+    for (int e = tid; e < rows * nb; e += kThreads) {
+      const int r = e / nb, q = e - r * nb;
+      P[r * PB + q] = A[(size_t)(k0 + r) * ld + k0 + q];
     }
-    const int p = block_argmax(bv, bi, S.red, S.ired);
-    if (p >= N) return 1;  // no finite pivot candidate
-    if (tid == 0) piv[k] = p;
-    const double pv = A[(size_t)p * ld + k];
-    if (!(pv != 0.0)) return 1;
-    if (p != k) {
-      for (int j = tid; j < N; j += kThreads) {
-        const double t = A[(size_t)k * ld + j];
-        A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
-        A[(size_t)p * ld + j] = t;
+    __syncthreads();
+    for (int c = 0; c < nb; ++c) {
+      double bv = -1.0;
+      int bi = rows;
+      for (int r = c + tid; r < rows; r += kThreads) {
+        const double a = fabs(to_d(P[r * PB + c]));
+        if (a > bv) { bv = a; bi = r; }
       }
-      sg = -sg;
+      const int p = block_argmax(bv, bi, S.red, S.ired);
+      if (p >= rows) return 1;
+      if (tid == 0) piv[k0 + c] = k0 + p;
+      const double pv = to_d(P[p * PB + c]);
+      if (!(pv != 0.0)) return 1;
+      if (p != c) {
+        for (int q = tid; q < nb; q += kThreads) {
+          const T t = P[c * PB + q];
+          P[c * PB + q] = P[p * PB + q];
+          P[p * PB + q] = t;
+        }
+        sg = -sg;
+      }
+      __syncthreads();
+      const double d = to_d(P[c * PB + c]);
+      ld_ += log(fabs(d));
+      if (d < 0.0) sg = -sg;
+      const T dinv = from_d<T>(1.0 / d);
+      for (int r = c + 1 + tid; r < rows; r += kThreads) {
+        const T l = rmul(P[r * PB + c], dinv);
+        P[r * PB + c] = l;
+        const T ml = rneg(l);
+        for (int q = c + 1; q < nb; ++q) P[r * PB + q] = rfma(ml, P[c * PB + q], P[r * PB + q]);
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < rows * nb; e += kThreads) {
+      const int r = e / nb, q = e - r * nb;
+      A[(size_t)(k0 + r) * ld + k0 + q] = P[r * PB + q];
+    }
+    // the panel's interchanges on the columns outside it (one thread per column)
+    for (int j = tid; j < N; j += kThreads) {
+      if (j >= k0 && j < k0 + nb) continue;
+      for (int c = 0; c < nb; ++c) {
+        const int p = piv[k0 + c];
+        if (p != k0 + c) {
+          const T t = A[(size_t)(k0 + c) * ld + j];
+          A[(size_t)(k0 + c) * ld + j] = A[(size_t)p * ld + j];
+          A[(size_t)p * ld + j] = t;
+        }
+      }
     }
     __syncthreads();
-    const double d = A[(size_t)k * ld + k];
-    ld_ += log(fabs(d));
-    if (d < 0.0) sg = -sg;
-    for (int i = k + 1 + tid; i < N; i += kThreads) A[(size_t)i * ld + k] /= d;
-    __syncthreads();
-    const int rem = N - k - 1;
-    for (int e = tid; e < rem * rem; e += kThreads) {
-      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-      A[(size_t)i * ld + j] -= A[(size_t)i * ld + k] * A[(size_t)k * ld + j];
+    if (n2 > 0) {
+      // U12 = L11^-1 A12 column by column (L11 = P rows 0..nb-1, staging after it)
+      T* U = P + PB * PB;
+      for (int jj = tid; jj < n2; jj += kThreads) {
+        const int j = k0 + nb + jj;
+        for (int q = 0; q < nb; ++q) {
+          T u = A[(size_t)(k0 + q) * ld + j];
+          for (int p2 = 0; p2 < q; ++p2) u = rfma(rneg(P[q * PB + p2]), U[p2 * n2 + jj], u);
+          U[q * n2 + jj] = u;
+          A[(size_t)(k0 + q) * ld + j] = u;
+          tmp[(size_t)q * ld + jj] = rneg(u);
+        }
+      }
+      __syncthreads();
+      // A22 -= L21 U12
+      gemm_acc(rows - nb, n2, nb, A + (size_t)(k0 + nb) * ld + k0, ld, tmp, ld, A + (size_t)(k0 + nb) * ld + k0 + nb,
+               ld, S);
     }
-    __syncthreads();
   }
   logdet = ld_;
   sign = sg;
   return 0;
 }
 
-// Solve (LU) Y = B for all columns of B (in place), rows permuted by piv first.
-// Each row of the forward and backward substitution is one row-vector times
-// matrix product, computed with 8 row groups x 32 columns and a fixed-order
-// shared-memory reduction (rows of B read coalesced).
-__device__ void lu_solve(int N, int ld, const double* LU, const int* piv, double* B, double* qred) {
-  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
-  for (int k = 0; k < N; ++k) {
-    const int p = piv[k];
-    if (p != k)
-      for (int j = tid; j < N; j += kThreads) {
-        const double t = B[(size_t)k * ld + j];
-        B[(size_t)k * ld + j] = B[(size_t)p * ld + j];
-        B[(size_t)p * ld + j] = t;
-      }
-    __syncthreads();
-  }
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int ii = (pass == 0 ? 1 : N - 1); pass == 0 ? ii < N : ii >= 0; ii += (pass == 0 ? 1 : -1)) {
-      const int klo = pass == 0 ? 0 : ii + 1, khi = pass == 0 ? ii : N;
-      const double* lrow = LU + (size_t)ii * ld;
-      for (int c0 = 0; c0 < N; c0 += 128) {
-        double w[4] = {0.0, 0.0, 0.0, 0.0};
-        int k = klo + rg;
-        for (; k + 24 < khi; k += 32) {
-          double x[4][4], l[4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            l[r] = lrow[k + 8 * r];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int j = c0 + lane + 32 * q;
-              x[r][q] = (j < N) ? B[(size_t)(k + 8 * r) * ld + j] : 0.0;
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) w[q] = fma(l[r], x[r][q], w[q]);
-        }
-        for (; k < khi; k += 8) {
-          const double l = lrow[k];
-          const double* brow = B + (size_t)k * ld;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = c0 + lane + 32 * q;
-            if (j < N) w[q] = fma(l, brow[j], w[q]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
-        __syncthreads();
-        if (rg == 0) {
-          const double dinv = pass == 1 ? 1.0 / lrow[ii] : 1.0;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = c0 + lane + 32 * q;
-            double t = 0.0;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) t += qred[r * 128 + lane + 32 * q];
-            if (j < N) {
-              const double v = B[(size_t)ii * ld + j] - t;
-              B[(size_t)ii * ld + j] = pass == 1 ? v * dinv : v;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-  }
-}
-
-// Float-pair versions of lu_factor / lu_solve for the mixed path's middle
-// matrix.  Every row of Mid has an entry of order one (for each i either
-// Db_R,i = 1 or Ds_R,i = 1, and likewise for the columns), so Mid, its LU
-// factors and the solution X = Mid^-1 Db_R^-1 Q_R^T stay inside the float
-// range; entries that underflow are below 1e-38 of their row and change G by
-// less than that in absolute value.  Pivots are chosen on |hi + lo| in FP64 and
-// divisions use the FP64 reciprocal of the pivot.
-__device__ int lu_factor_dd(int N, int ld, dd* A, int* piv, double& logdet, int& sign, Smem& S) {
+// Solve (LU) X = B for all N columns of B, B already in interchanged row order
+// (B <- X).  Blocks of PB rows are solved in shared memory, one thread per
+// column; the rows beyond a block are updated by one accumulate-GEMM.  tmp: PB x N.
+template <typename T>
+__device__ void lu_solve_blk(int N, int ld, const T* LU, T* B, T* tmp, Smem& S) {
   const int tid = threadIdx.x;
-  double ld_ = 0.0;
-  int sg = 1;
-  for (int k = 0; k < N; ++k) {
-    double bv = -1.0;
-    int bi = N;
-    for (int i = k + tid; i < N; i += kThreads) {
-      const double a = fabs(to_d(A[(size_t)i * ld + k]));
-      if (a > bv) { bv = a; bi = i; }
-    }
-    const int p = block_argmax(bv, bi, S.red, S.ired);
-    if (p >= N) return 1;
-    if (tid == 0) piv[k] = p;
-    const double pv = to_d(A[(size_t)p * ld + k]);
-    if (!(pv != 0.0)) return 1;
-    if (p != k) {
-      for (int j = tid; j < N; j += kThreads) {
-        const dd t = A[(size_t)k * ld + j];
-        A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
-        A[(size_t)p * ld + j] = t;
+  const int PB = lu_block_width(N);
+  T* Lb = reinterpret_cast<T*>(S.gemm);  // [PB][PB] diagonal block
+  T* Y = Lb + PB * PB;                   // [PB][N] block of right-hand sides
+  for (int pass = 0; pass < 2; ++pass) {
+    const int nblk = (N + PB - 1) / PB;
+    for (int bi = 0; bi < nblk; ++bi) {
+      // forward: blocks top to bottom; backward: bottom to top
+      const int r0 = pass == 0 ? bi * PB : (nblk - 1 - bi) * PB;
+      const int nb = (N - r0 < PB) ? N - r0 : PB;
+      for (int e = tid; e < nb * nb; e += kThreads) {
+        const int q = e / nb, p2 = e - q * nb;
+        Lb[q * PB + p2] = LU[(size_t)(r0 + q) * ld + r0 + p2];
       }
-      sg = -sg;
+      for (int e = tid; e < nb * N; e += kThreads) {
+        const int q = e / N, j = e - q * N;
+        Y[q * N + j] = B[(size_t)(r0 + q) * ld + j];
+      }
+      __syncthreads();
+      for (int j = tid; j < N; j += kThreads) {
+        if (pass == 0) {
+          for (int q = 1; q < nb; ++q) {
+            T y = Y[q * N + j];
+            for (int p2 = 0; p2 < q; ++p2) y = rfma(rneg(Lb[q * PB + p2]), Y[p2 * N + j], y);
+            Y[q * N + j] = y;
+          }
+        } else {
+          for (int q = nb - 1; q >= 0; --q) {
+            T y = Y[q * N + j];
+            for (int p2 = q + 1; p2 < nb; ++p2) y = rfma(rneg(Lb[q * PB + p2]), Y[p2 * N + j], y);
+            Y[q * N + j] = rmul(y, from_d<T>(1.0 / to_d(Lb[q * PB + q])));
+          }
+        }
+        for (int q = 0; q < nb; ++q) {
+          const T y = Y[q * N + j];
+          B[(size_t)(r0 + q) * ld + j] = y;
+          tmp[(size_t)q * ld + j] = rneg(y);
+        }
+      }
+      __syncthreads();
+      if (pass == 0 && r0 + nb < N)
+        gemm_acc(N - r0 - nb, N, nb, LU + (size_t)(r0 + nb) * ld + r0, ld, tmp, ld, B + (size_t)(r0 + nb) * ld, ld, S);
+      if (pass == 1 && r0 > 0) gemm_acc(r0, N, nb, LU + r0, ld, tmp, ld, B, ld, S);
     }
-    __syncthreads();
-    const double d = to_d(A[(size_t)k * ld + k]);
-    ld_ += log(fabs(d));
-    if (d < 0.0) sg = -sg;
-    const dd dinv = from_d<dd>(1.0 / d);
-    for (int i = k + 1 + tid; i < N; i += kThreads) A[(size_t)i * ld + k] = dd_mul(A[(size_t)i * ld + k], dinv);
-    __syncthreads();
-    const int rem = N - k - 1;
-    for (int e = tid; e < rem * rem; e += kThreads) {
-      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-      const dd l = A[(size_t)i * ld + k];
-      A[(size_t)i * ld + j] = dd_fma({-l.hi, -l.lo}, A[(size_t)k * ld + j], A[(size_t)i * ld + j]);
-    }
-    __syncthreads();
   }
-  logdet = ld_;
-  sign = sg;
-  return 0;
 }
 
-__device__ void lu_solve_dd(int N, int ld, const dd* LU, const int* piv, dd* B, dd* qred) {
-  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
-  for (int k = 0; k < N; ++k) {
-    const int p = piv[k];
-    if (p != k)
-      for (int j = tid; j < N; j += kThreads) {
-        const dd t = B[(size_t)k * ld + j];
-        B[(size_t)k * ld + j] = B[(size_t)p * ld + j];
-        B[(size_t)p * ld + j] = t;
-      }
-    __syncthreads();
-  }
-  const dd zero = {0.f, 0.f};
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int ii = (pass == 0 ? 1 : N - 1); pass == 0 ? ii < N : ii >= 0; ii += (pass == 0 ? 1 : -1)) {
-      const int klo = pass == 0 ? 0 : ii + 1, khi = pass == 0 ? ii : N;
-      const dd* lrow = LU + (size_t)ii * ld;
-      for (int c0 = 0; c0 < N; c0 += 128) {
-        dd w[4] = {zero, zero, zero, zero};
-        int k = klo + rg;
-        for (; k + 8 < khi; k += 16) {
-          dd x[2][4], l[2];
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            l[r] = lrow[k + 8 * r];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int j = c0 + lane + 32 * q;
-              x[r][q] = (j < N) ? B[(size_t)(k + 8 * r) * ld + j] : zero;
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) w[q] = dd_fma(l[r], x[r][q], w[q]);
-        }
-        for (; k < khi; k += 8) {
-          const dd l = lrow[k];
-          const dd* brow = B + (size_t)k * ld;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = c0 + lane + 32 * q;
-            if (j < N) w[q] = dd_fma(l, brow[j], w[q]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) qred[rg * 128 + lane + 32 * q] = w[q];
-        __syncthreads();
-        if (rg == 0) {
-          const dd dinv = pass == 1 ? from_d<dd>(1.0 / to_d(lrow[ii])) : dd{1.f, 0.f};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = c0 + lane + 32 * q;
-            dd t = zero;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) t = dd_add(t, qred[r * 128 + lane + 32 * q]);
-            if (j < N) {
-              const dd v = rsub(B[(size_t)ii * ld + j], t);
-              B[(size_t)ii * ld + j] = pass == 1 ? dd_mul(v, dinv) : v;
-            }
-          }
-        }
-        __syncthreads();
-      }
+// Row map of the LU row interchanges: row i of P b is row rowof[i] of b.
+__device__ void lu_row_map(int N, const int* piv, int* rowof) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < N; ++i) rowof[i] = i;
+    for (int k = 0; k < N; ++k) {
+      const int p = piv[k];
+      const int t = rowof[k]; rowof[k] = rowof[p]; rowof[p] = t;
     }
   }
+  __syncthreads();
 }
 
 // Stable G from a right chain R (B(tau,0) = Q_R D_R T_R) and a left chain Lf
@@ -1230,16 +1188,20 @@ __device__ int green_from_udv(const ChainDev& C, int s, UDV R, UDV Lf, double* G
     W0[(size_t)i * ld + j] = W0[(size_t)i * ld + j] * (ibR[i] * ibL[j]) + dsR * W1[(size_t)i * ld + j] * dsL;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < N * N; e += kThreads) {
-    const int i = e / N, j = e - i * N;
-    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + i] * ibR[i];
-  }
-  __syncthreads();
   double ldm;
   int sm;
   int* piv = C.iwork[s] + ld;
-  if (lu_factor(N, ld, W0, piv, ldm, sm, S)) return 1;
-  lu_solve(N, ld, W0, piv, W1, S.qred);
+  double* tmp = wmat(C, s, 9);
+  if (lu_factor_blk(N, ld, W0, piv, tmp, ldm, sm, S)) return 1;
+  int* rowof = C.iwork[s];
+  lu_row_map(N, piv, rowof);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const int r = rowof[i];
+    W1[(size_t)i * ld + j] = R.Q[(size_t)j * ld + r] * ibR[r];
+  }
+  __syncthreads();
+  lu_solve_blk(N, ld, W0, W1, tmp, S);
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
     W1[(size_t)i * ld + j] *= ibL[i];
@@ -1858,16 +1820,21 @@ __device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, dou
     W0d[(size_t)i * ld + j] = from_d<dd>(qq * (ibR[i] * ibL[j]) + dsR * tt * dsL);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < N * N; e += kThreads) {
-    const int i = e / N, j = e - i * N;
-    W1d[(size_t)i * ld + j] = from_d<dd>(R.Q[(size_t)j * ld + i] * ibR[i]);
-  }
-  __syncthreads();
   double ldm;
   int smi;
   int* piv = C.iwork[s] + ld;
-  if (lu_factor_dd(N, ld, W0d, piv, ldm, smi, S)) return 1;
-  lu_solve_dd(N, ld, W0d, piv, W1d, reinterpret_cast<dd*>(S.qred));
+  dd* tmpd = reinterpret_cast<dd*>(wmat(C, s, 9));
+  if (lu_factor_blk(N, ld, W0d, piv, tmpd, ldm, smi, S)) return 1;
+  // right-hand side Db_R^-1 Q_R^T with the LU row interchanges applied
+  int* rowof = C.iwork[s];
+  lu_row_map(N, piv, rowof);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const int r = rowof[i];
+    W1d[(size_t)i * ld + j] = from_d<dd>(R.Q[(size_t)j * ld + r] * ibR[r]);
+  }
+  __syncthreads();
+  lu_solve_blk(N, ld, W0d, W1d, tmpd, S);
   dd* Yd = reinterpret_cast<dd*>(wmat(C, s, 9));
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;

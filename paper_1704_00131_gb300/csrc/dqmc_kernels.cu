@@ -176,14 +176,21 @@ __device__ int displaced_from_udv(const ChainDev& C, int s, UDV R, UDV Lf, doubl
     const double dbR = dR > 1.0 ? dR : 1.0, dsR = dR > 1.0 ? 1.0 : dR;
     const double dbL = dL > 1.0 ? dL : 1.0, dsL = dL > 1.0 ? 1.0 : dL;
     W0[(size_t)i * ld + j] = W0[(size_t)i * ld + j] / (dbR * dbL) + dsR * W1[(size_t)i * ld + j] * dsL;
-    W1[(size_t)i * ld + j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
   double ldm;
   int smi;
   int* piv = C.iwork[s] + ld;
-  if (lu_factor(N, ld, W0, piv, ldm, smi, S)) return 1;
-  lu_solve(N, ld, W0, piv, W1, S.qred);  // W1 = Mid^-1
+  double* tmp = wmat(C, s, 9);
+  if (lu_factor_blk(N, ld, W0, piv, tmp, ldm, smi, S)) return 1;
+  int* rowof = C.iwork[s];
+  lu_row_map(N, piv, rowof);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    W1[(size_t)i * ld + j] = (rowof[i] == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  lu_solve_blk(N, ld, W0, W1, tmp, S);  // W1 = Mid^-1
   for (int e = threadIdx.x; e < N * N; e += kThreads) {
     const int i = e / N, j = e - i * N;
     const double m = W1[(size_t)i * ld + j];
