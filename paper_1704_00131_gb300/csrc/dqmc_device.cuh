@@ -590,6 +590,7 @@ struct Smem {
   double* red;      // [32]
   int* ired;        // [32]
   int* qsite;       // [MV]
+  int* qinv;        // [ld] position in the slice's visiting order of the vertex on site x (-1: none)
   int8_t* fnew;     // [MV]
   int8_t* fslice;   // [MV] fields of the current slice
   int* expA;        // [roundup(ld,64)] row exponents of the split tensor-core products
@@ -606,6 +607,7 @@ __host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
   b += 6 * (size_t)MV * 8;        // u2, delta, gam, Rs[2], Rp
   b += 8 * 8 + 32 * 8 + 32 * 4;   // xs, red, ired
   b += (size_t)MV * 4;            // qsite
+  b += (size_t)ld * 4;            // qinv
   b += 2 * (size_t)MV + 16;       // fnew, fslice
   b = (b + 15) / 16 * 16;
   b += 8 * 128 * 8;               // qred
@@ -633,6 +635,7 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   int* ip = reinterpret_cast<int*>(p);
   s.ired = ip; ip += 32;
   s.qsite = ip; ip += MV;
+  s.qinv = ip; ip += ld;
   int8_t* bp = reinterpret_cast<int8_t*>(ip);
   s.fnew = bp; bp += MV;
   s.fslice = bp; bp += MV + 16;
@@ -1412,15 +1415,29 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     S.fnew[q] = (int8_t)fn;
     S.qsite[q] = C.site[k];
   }
-  for (int x = tid; x < N; x += kThreads) S.d[x] = to_d(G[(size_t)x * ld + x]);
+  for (int x = tid; x < N; x += kThreads) {
+    S.d[x] = to_d(G[(size_t)x * ld + x]);
+    S.qinv[x] = -1;
+  }
+  // first accepted position of the current scan (two slots, alternating)
+  int* first_slot = S.ired + 16;
+  if (tid == 0) first_slot[0] = first_slot[1] = MV;
+  __syncthreads();
+  for (int q = tid; q < MV; q += kThreads) {
+    S.qinv[S.qsite[q]] = q;
+    S.Rs[buf * MV + q] = 1.0 + S.delta[q] * (1.0 - S.d[S.qsite[q]]);
+  }
   __syncthreads();
   tick(det, 0, t0);
   int pos = 0, nacc = 0;
   int64_t n_acc_slice = 0;
   const int kdel = P.delay_k;
+  // Barriers per acceptance: the cluster barrier (ratios of both flavors) and one
+  // CTA barrier after the scan.  The thread that owns site x updates the
+  // diagonal d_x and the next ratio of the vertex on x itself, so neither needs
+  // a barrier of its own; the flush is preceded by one.
   while (true) {
     double* Rs = S.Rs + buf * MV;
-    for (int q = pos + tid; q < MV; q += kThreads) Rs[q] = 1.0 + S.delta[q] * (1.0 - S.d[S.qsite[q]]);
     // the next position is accepted most of the time: start reading its column and
     // row of G now, so that the cluster barrier covers the memory latency
     const int ipre = (pos < MV) ? S.qsite[pos] : 0;
@@ -1432,18 +1449,19 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     cl.sync();
     const double* Rr[kMaxFlavors];
     for (int r = 0; r < nfl; ++r) Rr[r] = (r == s) ? Rs : cl.map_shared_rank(Rs, r);
-    int first = MV;
     for (int q = pos + tid; q < MV; q += kThreads) {
       double R = S.gam[q];
       for (int r = 0; r < nfl; ++r) R *= Rr[r][q];
       const double aR = fabs(R);
       if (S.u2[q] < (aR < 1.0 ? aR : 1.0)) {
         S.Rp[q] = R;
-        first = q;
+        atomicMin(first_slot + buf, q);
         break;
       }
     }
-    first = block_min_int(first, S.ired);
+    __syncthreads();
+    const int first = first_slot[buf];
+    if (tid == 0) first_slot[buf ^ 1] = MV;
     tick(det, 1, t0);
     if (first >= MV) { buf ^= 1; break; }
     const double R = S.Rp[first];
@@ -1455,6 +1473,7 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     Real* b = B + (size_t)nacc * ld;
     const Real mfac = from_d<Real>(-fac);
     const bool hit = (first == pos);
+    double* Rs_next = S.Rs + (buf ^ 1) * MV;
     // element x of column i (a) and of row i (b) of G_eff
     for (int x = tid; x < N; x += kThreads) {
       Real cx, ry;
@@ -1469,11 +1488,15 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
         cx = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
         ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
       }
-      a[x] = rmul(mfac, cx);
-      b[x] = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
+      const Real ax = rmul(mfac, cx);
+      const Real bx = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
+      a[x] = ax;
+      b[x] = bx;
+      const double dx = S.d[x] + to_d(ax) * to_d(bx);
+      S.d[x] = dx;
+      const int qx = S.qinv[x];
+      if (qx >= 0) Rs_next[qx] = 1.0 + S.delta[qx] * (1.0 - dx);
     }
-    __syncthreads();
-    for (int x = tid; x < N; x += kThreads) S.d[x] += to_d(a[x]) * to_d(b[x]);
     if (tid == 0) S.fslice[k] = S.fnew[first];
     ++nacc;
     ++n_acc_slice;
@@ -1486,7 +1509,6 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
     }
     pos = first + 1;
     buf ^= 1;
-    __syncthreads();
   }
   if (nacc) flush_delayed<Real>(C, G, A, B, nacc, S);
   tick(det, 3, t0);
