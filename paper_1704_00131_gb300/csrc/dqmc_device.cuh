@@ -600,8 +600,12 @@ struct Smem {
   double* qred;     // [8][128] partial sums of the QR trailing update
 };
 
+// The first kSmemCounterBytes of the dynamic shared memory hold thread 0's
+// cycle counters of the sweep kernel (fixed addresses, no registers).
+constexpr int kSmemCounterBytes = 16 * 8;
+
 __host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
-  size_t b = 0;
+  size_t b = kSmemCounterBytes;
   b += 2 * 16 * kGemmMaxTile * 8;
   b += 6 * (size_t)ld * 8;        // v, ev, d, hv, xdiag, spare
   b += 6 * (size_t)MV * 8;        // u2, delta, gam, Rs[2], Rp
@@ -617,6 +621,7 @@ __host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
 
 __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   Smem s;
+  base += kSmemCounterBytes;
   double* p = reinterpret_cast<double*>(base);
   s.gemm = p; p += 2 * 16 * kGemmMaxTile;
   s.v = p; p += ld;
@@ -2014,12 +2019,15 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
   const int L = C.L, nw = C.nw, MV = C.MV;
   int sign = C.sign;
   int buf = 0;
-  long long cyc[4] = {0, 0, 0, 0};
-  long long det[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // thread 0's phase counters: cyc[0..3] per phase, det[0..7] per sub-phase
+  long long* cyc = reinterpret_cast<long long*>(smem_raw);
+  long long* det = cyc + 4;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 12; ++q) cyc[q] = 0;
   long long t0 = clock64();
   auto lap = [&](int phase) {
     const long long t1 = clock64();
-    cyc[phase] += t1 - t0;
+    if (threadIdx.x == 0) cyc[phase] += t1 - t0;
     t0 = t1;
   };
   for (int tau = 1; tau <= L; ++tau) {
