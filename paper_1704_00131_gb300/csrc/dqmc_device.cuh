@@ -219,6 +219,9 @@ __device__ __forceinline__ dd rfma(dd a, dd b, dd c) { return dd_fma(a, b, c); }
 __device__ __forceinline__ double rmul(double a, double b) { return a * b; }
 __device__ __forceinline__ float rmul(float a, float b) { return a * b; }
 __device__ __forceinline__ dd rmul(dd a, dd b) { return dd_mul(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return a + b; }
+__device__ __forceinline__ float radd(float a, float b) { return a + b; }
+__device__ __forceinline__ dd radd(dd a, dd b) { return dd_add(a, b); }
 __device__ __forceinline__ double rsub(double a, double b) { return a - b; }
 __device__ __forceinline__ float rsub(float a, float b) { return a - b; }
 __device__ __forceinline__ dd rsub(dd a, dd b) { return dd_add(a, {-b.hi, -b.lo}); }
@@ -1489,10 +1492,21 @@ __device__ void update_slice(ChainDev& C, int s, int tau, int dir, const SweepPa
         cx = G[(size_t)x * ld + i];
         ry = G[(size_t)i * ld + x];
       }
-      for (int m = 0; m < nacc; ++m) {
+      // two independent accumulation chains each (even and odd m)
+      Real cx1 = from_d<Real>(0.0), ry1 = from_d<Real>(0.0);
+      int m = 0;
+      for (; m + 1 < nacc; m += 2) {
+        cx = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
+        ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
+        cx1 = rfma(A[(size_t)(m + 1) * ld + x], B[(size_t)(m + 1) * ld + i], cx1);
+        ry1 = rfma(A[(size_t)(m + 1) * ld + i], B[(size_t)(m + 1) * ld + x], ry1);
+      }
+      if (m < nacc) {
         cx = rfma(A[(size_t)m * ld + x], B[(size_t)m * ld + i], cx);
         ry = rfma(A[(size_t)m * ld + i], B[(size_t)m * ld + x], ry);
       }
+      cx = radd(cx, cx1);
+      ry = radd(ry, ry1);
       const Real ax = rmul(mfac, cx);
       const Real bx = rsub(from_d<Real>(x == i ? 1.0 : 0.0), ry);
       a[x] = ax;
@@ -1534,17 +1548,17 @@ __device__ void householder_apply_dd(int N, int ld, dd* M, int k, int j0, dd bk,
   for (int c0 = j0; c0 < N; c0 += 128) {
     dd w[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     int i = k + rg;
-    for (; i + 8 < N; i += 16) {
-      dd x[2][4];
+    for (; i + 24 < N; i += 32) {
+      dd x[4][4];
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = c0 + lane + 32 * q;
           x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : dd{0.f, 0.f};
         }
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < 4; ++r) {
         const dd vi = hv[i + 8 * r];
 #pragma unroll
         for (int q = 0; q < 4; ++q) w[q] = dd_fma(vi, x[r][q], w[q]);
@@ -1572,17 +1586,17 @@ __device__ void householder_apply_dd(int N, int ld, dd* M, int k, int j0, dd bk,
       wt[q] = {-bw.hi, -bw.lo};
     }
     i = k + rg;
-    for (; i + 8 < N; i += 16) {
-      dd x[2][4];
+    for (; i + 24 < N; i += 32) {
+      dd x[4][4];
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int j = c0 + lane + 32 * q;
           x[r][q] = (j < N) ? M[(size_t)(i + 8 * r) * ld + j] : dd{0.f, 0.f};
         }
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < 4; ++r) {
         const dd vi = hv[i + 8 * r];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
