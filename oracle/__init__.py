@@ -97,6 +97,7 @@ def lib():
         _lib.orc_green_displaced.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         _lib.orc_energy_grad.argtypes = [vp, vp, vp, vp, vp]
         _lib.orc_tau_observables.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp]
+        _lib.orc_correlations.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp]
         del i32
     return _lib
 
@@ -310,6 +311,17 @@ def tau_observables(model: Model, fields: np.ndarray, n_tau: int, phase=None):
     _check(lib().orc_tau_observables(model.cref(), _ptr(f), n_tau, None if ph is None else _ptr(ph), _ptr(out),
                                      _ptr(sg)), "tau_observables")
     return out, sg
+
+
+def correlations(G: np.ndarray, pair_class: np.ndarray, n_class: int) -> np.ndarray:
+    """Equal-time (S^z S^z, n n, S^+ S^-, sum_s c^+ c) sums per pair class of one
+    configuration from its two-flavor Green functions G[2, N, N]; returns [n_class, 4]."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    N = G.shape[-1]
+    cls = np.ascontiguousarray(pair_class, dtype=np.int32).reshape(N, N)
+    out = np.zeros((n_class, 4))
+    _check(lib().orc_correlations(N, _ptr(G), _ptr(cls), int(n_class), _ptr(out)), "correlations")
+    return out
 
 
 def szz_from_tau(obs: np.ndarray) -> np.ndarray:

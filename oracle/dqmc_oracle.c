@@ -1261,3 +1261,40 @@ int orc_tau_observables(const orc_model* m, const int8_t* fields, int n_tau, con
   model_free(&M);
   return st;
 }
+
+/* Equal-time correlation functions of one configuration (the equal-time
+ * observables of Sec. 5.2 and 6, Obser_Latt), for the spin-z decoupling with
+ * two flavors (0 = up, 1 = down); G[s] is the equal-time Green function
+ * G^s_xy = <c_xs c^+_ys> of the configuration.  Flavors are independent in one
+ * configuration, so Wick's theorem gives, with rho_x = sum_s (1 - G^s_xx),
+ * m_x = (1 - G^0_xx) - (1 - G^1_xx) and X^s_xy = (delta_xy - G^s_yx) G^s_xy:
+ *   <S^z_x S^z_y> = [m_x m_y + X^0_xy + X^1_xy] / 4
+ *   <n_x n_y>     = rho_x rho_y + X^0_xy + X^1_xy
+ *   <S^+_x S^-_y> = (delta_xy - G^0_yx) G^1_xy
+ *   sum_s <c^+_xs c_ys> = sum_s (delta_xy - G^s_yx)
+ * out[c * 4 + {0, 1, 2, 3}] = sums of these over the pairs (x, y) with
+ * cls[x * N + y] == c (0 <= c < n_class; pairs with a negative class skipped). */
+int orc_correlations(int N, const double* G_all /*[2][N][N]*/, const int32_t* cls, int n_class, double* out) {
+  if (N < 1 || n_class < 1) return ORC_EINVAL;
+  const double* G0 = G_all;
+  const double* G1 = G_all + (size_t)N * N;
+  for (int q = 0; q < 4 * n_class; ++q) out[q] = 0.0;
+  for (int x = 0; x < N; ++x)
+    for (int y = 0; y < N; ++y) {
+      const int c = cls[x * N + y];
+      if (c < 0) continue;
+      if (c >= n_class) return ORC_EINVAL;
+      const double dxy = (x == y) ? 1.0 : 0.0;
+      const double rx = (1.0 - G0[x * N + x]) + (1.0 - G1[x * N + x]);
+      const double ry = (1.0 - G0[y * N + y]) + (1.0 - G1[y * N + y]);
+      const double mx = (1.0 - G0[x * N + x]) - (1.0 - G1[x * N + x]);
+      const double my = (1.0 - G0[y * N + y]) - (1.0 - G1[y * N + y]);
+      const double X0 = (dxy - G0[y * N + x]) * G0[x * N + y];
+      const double X1 = (dxy - G1[y * N + x]) * G1[x * N + y];
+      out[c * 4 + 0] += 0.25 * (mx * my + X0 + X1);
+      out[c * 4 + 1] += rx * ry + X0 + X1;
+      out[c * 4 + 2] += (dxy - G0[y * N + x]) * G1[x * N + y];
+      out[c * 4 + 3] += (dxy - G0[y * N + x]) + (dxy - G1[y * N + x]);
+    }
+  return ORC_OK;
+}

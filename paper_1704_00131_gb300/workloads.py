@@ -96,6 +96,41 @@ def sublattice_signs_honeycomb(L1: int, L2: int) -> np.ndarray:
     return np.array([1.0 if (i % 2 == 0) else -1.0 for i in range(2 * L1 * L2)])
 
 
+def translation_classes_square(Lx: int, Ly: int):
+    """Pair classes of the periodic square lattice by displacement: the pair
+    (i, j) belongs to class (dx mod Lx) + Lx (dy mod Ly), dx = x_j - x_i.
+    Returns (class map [N*N] int32, number of classes N, displacement r[N, 2])."""
+    N = Lx * Ly
+    cls = np.zeros((N, N), dtype=np.int32)
+    for i in range(N):
+        xi, yi = i % Lx, i // Lx
+        for j in range(N):
+            xj, yj = j % Lx, j // Lx
+            cls[i, j] = ((xj - xi) % Lx) + Lx * ((yj - yi) % Ly)
+    r = np.array([[c % Lx, c // Lx] for c in range(N)], dtype=np.float64)
+    return cls.ravel(), N, r
+
+
+def translation_classes_honeycomb(L1: int, L2: int):
+    """Pair classes of the periodic honeycomb lattice by cell displacement and
+    orbital pair: class = 4 ((d1 mod L1) + L1 (d2 mod L2)) + 2 o_i + o_j.
+    Returns (class map [N*N], number of classes 4 L1 L2, displacement r[n, 2] in
+    units of a1, a2 (cell part only))."""
+    ncell = L1 * L2
+    N = 2 * ncell
+    cls = np.zeros((N, N), dtype=np.int32)
+    for i in range(N):
+        ci, oi = divmod(i, 2)
+        n1i, n2i = ci % L1, ci // L1
+        for j in range(N):
+            cj, oj = divmod(j, 2)
+            n1j, n2j = cj % L1, cj // L1
+            d = ((n1j - n1i) % L1) + L1 * ((n2j - n2i) % L2)
+            cls[i, j] = 4 * d + 2 * oi + oj
+    r = np.array([[(c // 4) % L1, (c // 4) // L1] for c in range(4 * ncell)], dtype=np.float64)
+    return cls.ravel(), 4 * ncell, r
+
+
 @dataclass
 class ModelSpec:
     """One Hubbard model in the spin-z decoupling: flavors up (+1) and down (-1)."""
