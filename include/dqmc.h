@@ -199,6 +199,29 @@ dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* 
 dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_phase, double* out, int32_t* sign,
                              double* prec);
 
+/* Equal-time correlation functions of every chain's current configuration (the
+ * equal-time observables of Sec. 5.2 and the correlation functions of Sec. 6,
+ * collected per class of site pairs as Obser_Latt collects them per lattice
+ * displacement), from the working G(0) of the two flavors of the spin-z
+ * decoupling (flavor 0 up, flavor 1 down; two-flavor models only).  With
+ * X^s_xy = (delta_xy - G^s_yx) G^s_xy, Wick's theorem per configuration gives
+ *     <S^z_x S^z_y> = [m_x m_y + X^0_xy + X^1_xy] / 4,  m_x = G^1_xx - G^0_xx
+ *     <n_x n_y>     = rho_x rho_y + X^0_xy + X^1_xy,    rho_x = 2 - G^0_xx - G^1_xx
+ *     <S^+_x S^-_y> = (delta_xy - G^0_yx) G^1_xy
+ *     sum_s <c^+_xs c_ys> = sum_s (delta_xy - G^s_yx)
+ *     pair_class  host, per model [n_sites][n_sites] int32 (models concatenated):
+ *                 class of the pair (x, y) in [0, n_class[m]), or -1 to skip it
+ *     n_class     host [n_models], each >= 1
+ * Outputs (host):
+ *     out  [n_chains][max over models of n_class][4]: per class the sums over its
+ *          pairs of the four expectation values above (unweighted; rows beyond
+ *          the chain's model's n_class are 0)
+ *     sign [n_chains]: sign of the configuration's weight (multiply before averaging)
+ * The chains are left as they are.  DQMC_EINVAL for a one-flavor model or a
+ * class outside [-1, n_class). */
+dqmc_status dqmc_measure_corr(dqmc_ctx* ctx, const int32_t* pair_class, const int32_t* n_class, double* out,
+                              int32_t* sign);
+
 /* Derivatives of log|det(1 + B^s(beta,0))| on fixed field configurations of
  * model `model_index` (FP64):
  *     d log|det| = sum_tau Tr[(1 - G(tau-1)) B_tau^-1 dB_tau]

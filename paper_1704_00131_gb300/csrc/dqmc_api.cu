@@ -660,6 +660,86 @@ dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_ph
   return DQMC_OK;
 }
 
+dqmc_status dqmc_measure_corr(dqmc_ctx* ctx, const int32_t* pair_class, const int32_t* n_class, double* out,
+                              int32_t* sign) {
+  if (!ctx) return DQMC_EINVAL;
+  if (!pair_class || !n_class || !out || !sign) return fail(ctx, DQMC_EINVAL, "null argument");
+  if (ctx->nfl != 2) return fail(ctx, DQMC_EINVAL, "correlation functions need the two flavors of the spin-z decoupling");
+  const int nm = (int)ctx->models.size(), nch = (int)ctx->chains_h.size();
+  // per model: class offsets and the pairs sorted by class (then by x, y)
+  std::vector<int> csr, pairs, mcsr(nm), mpairs(nm);
+  int max_cls = 0;
+  size_t coff = 0;
+  for (int m = 0; m < nm; ++m) {
+    const int N = ctx->models[m].d.n_sites, nc = n_class[m];
+    if (nc < 1) return fail(ctx, DQMC_EINVAL, "model %d: n_class < 1", m);
+    max_cls = nc > max_cls ? nc : max_cls;
+    const int32_t* cl = pair_class + coff;
+    std::vector<int> cnt(nc + 1, 0);
+    for (int e = 0; e < N * N; ++e) {
+      if (cl[e] < -1 || cl[e] >= nc) return fail(ctx, DQMC_EINVAL, "model %d: pair class %d out of range", m, cl[e]);
+      if (cl[e] >= 0) ++cnt[cl[e] + 1];
+    }
+    for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
+    mcsr[m] = (int)csr.size();
+    mpairs[m] = (int)pairs.size();
+    csr.insert(csr.end(), cnt.begin(), cnt.end());
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    pairs.resize(pairs.size() + cnt[nc]);
+    for (int e = 0; e < N * N; ++e)
+      if (cl[e] >= 0) pairs[mpairs[m] + fill[cl[e]]++] = e;
+    coff += (size_t)N * N;
+  }
+  std::vector<int> ccsr(nch), cpairs(nch), cncls(nch);
+  for (int c = 0; c < nch; ++c) {
+    const int m = ctx->chain_model[c];
+    ccsr[c] = mcsr[m];
+    cpairs[c] = mpairs[m];
+    cncls[c] = n_class[m];
+  }
+  if (pairs.empty()) pairs.push_back(0);
+  int *csr_d = nullptr, *pairs_d = nullptr, *meta_d = nullptr;
+  double* out_d = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(csr_d);
+    cudaFree(pairs_d);
+    cudaFree(meta_d);
+    cudaFree(out_d);
+  };
+  const size_t nout = (size_t)nch * max_cls * 4;
+  if (cudaMalloc((void**)&csr_d, sizeof(int) * csr.size()) != cudaSuccess ||
+      cudaMalloc((void**)&pairs_d, sizeof(int) * pairs.size()) != cudaSuccess ||
+      cudaMalloc((void**)&meta_d, sizeof(int) * 3 * nch) != cudaSuccess ||
+      cudaMalloc((void**)&out_d, sizeof(double) * nout) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, DQMC_ENOMEM, "no device memory for the correlation functions");
+  }
+  dqmc_status st = DQMC_OK;
+  do {
+    if (cudaMemcpyAsync(csr_d, csr.data(), sizeof(int) * csr.size(), cudaMemcpyHostToDevice, ctx->stream) ||
+        cudaMemcpyAsync(pairs_d, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, ctx->stream) ||
+        cudaMemcpyAsync(meta_d, ccsr.data(), sizeof(int) * nch, cudaMemcpyHostToDevice, ctx->stream) ||
+        cudaMemcpyAsync(meta_d + nch, cpairs.data(), sizeof(int) * nch, cudaMemcpyHostToDevice, ctx->stream) ||
+        cudaMemcpyAsync(meta_d + 2 * nch, cncls.data(), sizeof(int) * nch, cudaMemcpyHostToDevice, ctx->stream)) {
+      st = fail(ctx, DQMC_ECUDA, "upload failed");
+      break;
+    }
+    cudaError_t e = dqmc::launch_corr(ctx->chains_d, nch, ctx->kprec, csr_d, pairs_d, meta_d, meta_d + nch,
+                                      meta_d + 2 * nch, max_cls, out_d, ctx->stream);
+    if (e != cudaSuccess) { st = fail(ctx, DQMC_ECUDA, "correlation launch: %s", cudaGetErrorString(e)); break; }
+    if (cudaMemcpyAsync(out, out_d, sizeof(double) * nout, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) {
+      st = fail(ctx, DQMC_ECUDA, "download failed");
+      break;
+    }
+    st = download_chains(ctx);
+  } while (false);
+  cleanup();
+  if (st) return st;
+  for (int c = 0; c < nch; ++c) sign[c] = ctx->chains_h[c].sign;
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_get_fields(dqmc_ctx* ctx, int8_t* out, uint64_t* rng_counter) {
   if (!ctx) return DQMC_EINVAL;
   if (!out) return fail(ctx, DQMC_EINVAL, "null output");

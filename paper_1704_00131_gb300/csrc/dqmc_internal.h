@@ -92,6 +92,9 @@ cudaError_t launch_energy_grad(ChainDev* chains, int n_cfg, int nfl, const doubl
                                double* G0all, double* ework, double* gK, double* gU, double* eparts,
                                cudaStream_t st);
 cudaError_t launch_finalize_init(ChainDev* chains, int n_chains, cudaStream_t st);
+cudaError_t launch_corr(ChainDev* chains, int n_chains, int precision, const int* csr_all, const int* pairs_all,
+                        const int* chain_csr, const int* chain_pairs, const int* chain_ncls, int max_cls,
+                        double* out, cudaStream_t st);
 cudaError_t launch_tau_measure(ChainDev* chains, int n_chains, int nfl, int n_tau, const double* phase,
                                int phase_ld, double* tw, size_t tw_stride, double* obs, double* prec, int* sign,
                                cudaStream_t st);

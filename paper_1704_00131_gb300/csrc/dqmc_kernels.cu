@@ -532,6 +532,56 @@ __global__ void __launch_bounds__(kThreads) tau_measure_kernel(ChainDev* chains,
   }
 }
 
+// Equal-time correlation functions of every chain's current configuration
+// (equal-time observables of Sec. 5.2 / 6, spin-z decoupling, flavor 0 up and
+// 1 down), from the working G(0) of both flavors.  Wick's theorem per
+// configuration (flavors independent), with X^s_xy = (delta_xy - G^s_yx) G^s_xy:
+//   <S^z_x S^z_y> = [m_x m_y + X^0_xy + X^1_xy] / 4,  m_x = G^1_xx - G^0_xx
+//   <n_x n_y>     = rho_x rho_y + X^0_xy + X^1_xy,    rho_x = 2 - G^0_xx - G^1_xx
+//   <S^+_x S^-_y> = (delta_xy - G^0_yx) G^1_xy
+//   sum_s <c^+_xs c_ys> = sum_s (delta_xy - G^s_yx)
+// summed over the pairs of each class.  One thread per class walks the class's
+// pairs in a fixed order (deterministic sums).  csr: per chain, class offsets
+// [n_class + 1] into the pair list (x * N + y); out [n_chains][max_class][4].
+template <typename Real>
+__global__ void corr_kernel(ChainDev* chains, int n_chains, const int* csr_all, const int* pairs_all,
+                            const int* chain_csr, const int* chain_pairs, const int* chain_ncls, int max_cls,
+                            double* out) {
+  const int c = blockIdx.x;
+  if (c >= n_chains) return;
+  const ChainDev& C = chains[c];
+  const int N = C.N, ld = C.ld, ncls = chain_ncls[c];
+  const int* off = csr_all + chain_csr[c];
+  const int* pairs = pairs_all + chain_pairs[c];
+  const Real* G0 = (const Real*)C.G[0];
+  const Real* G1 = (const Real*)C.G[1];
+  double* o = out + (size_t)c * max_cls * 4;
+  for (int k = threadIdx.x; k < max_cls; k += blockDim.x) {
+    double zz = 0.0, nn = 0.0, pm = 0.0, gf = 0.0;
+    if (k < ncls) {
+      for (int p = off[k]; p < off[k + 1]; ++p) {
+        const int x = pairs[p] / N, y = pairs[p] - (pairs[p] / N) * N;
+        const double dxy = (x == y) ? 1.0 : 0.0;
+        const double g0xx = to_d(G0[(size_t)x * ld + x]), g1xx = to_d(G1[(size_t)x * ld + x]);
+        const double g0yy = to_d(G0[(size_t)y * ld + y]), g1yy = to_d(G1[(size_t)y * ld + y]);
+        const double g0xy = to_d(G0[(size_t)x * ld + y]), g0yx = to_d(G0[(size_t)y * ld + x]);
+        const double g1xy = to_d(G1[(size_t)x * ld + y]), g1yx = to_d(G1[(size_t)y * ld + x]);
+        const double X0 = (dxy - g0yx) * g0xy, X1 = (dxy - g1yx) * g1xy;
+        const double mx = g1xx - g0xx, my = g1yy - g0yy;
+        const double rx = 2.0 - g0xx - g1xx, ry = 2.0 - g0yy - g1yy;
+        zz += 0.25 * (mx * my + X0 + X1);
+        nn += rx * ry + X0 + X1;
+        pm += (dxy - g0yx) * g1xy;
+        gf += (dxy - g0yx) + (dxy - g1yx);
+      }
+    }
+    o[k * 4 + 0] = zz;
+    o[k * 4 + 1] = nn;
+    o[k * 4 + 2] = pm;
+    o[k * 4 + 3] = gf;
+  }
+}
+
 // --------------------------------------------------------------------------
 // Launchers.
 // --------------------------------------------------------------------------
@@ -609,6 +659,21 @@ cudaError_t launch_tau_measure(ChainDev* chains, int n_chains, int nfl, int n_ta
   if (e != cudaSuccess) return e;
   tau_measure_kernel<<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, n_tau, phase, phase_ld, tw,
                                                              tw_stride, obs, prec, sign);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr(ChainDev* chains, int n_chains, int precision, const int* csr_all, const int* pairs_all,
+                        const int* chain_csr, const int* chain_pairs, const int* chain_ncls, int max_cls,
+                        double* out, cudaStream_t st) {
+  if (precision == 0)
+    corr_kernel<double><<<n_chains, 128, 0, st>>>(chains, n_chains, csr_all, pairs_all, chain_csr, chain_pairs,
+                                                  chain_ncls, max_cls, out);
+  else if (precision == 1)
+    corr_kernel<float><<<n_chains, 128, 0, st>>>(chains, n_chains, csr_all, pairs_all, chain_csr, chain_pairs,
+                                                 chain_ncls, max_cls, out);
+  else
+    corr_kernel<dd><<<n_chains, 128, 0, st>>>(chains, n_chains, csr_all, pairs_all, chain_csr, chain_pairs,
+                                              chain_ncls, max_cls, out);
   return cudaGetLastError();
 }
 

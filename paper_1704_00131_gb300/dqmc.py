@@ -20,7 +20,7 @@ _LIB_PATH = os.path.join(_PKG, "libdqmc.so")
 DQMC_OK, DQMC_EINVAL, DQMC_ENOMEM, DQMC_ECUDA, DQMC_EUNSTABLE, DQMC_ETIMEOUT, DQMC_ESTATE = range(7)
 PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tc": 3}
 
-EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_measure_tau", "dqmc_logdet_backward",
+EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_measure_tau", "dqmc_measure_corr", "dqmc_logdet_backward",
             "dqmc_get_fields", "dqmc_set_fields", "dqmc_last_error", "dqmc_destroy"]
 
 
@@ -107,6 +107,8 @@ def load() -> ctypes.CDLL:
     L.dqmc_measure.restype = ctypes.c_int
     L.dqmc_measure_tau.argtypes = [vp, i32, vp, vp, vp, vp]
     L.dqmc_measure_tau.restype = ctypes.c_int
+    L.dqmc_measure_corr.argtypes = [vp, vp, vp, vp, vp]
+    L.dqmc_measure_corr.restype = ctypes.c_int
     L.dqmc_logdet_backward.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     L.dqmc_logdet_backward.restype = ctypes.c_int
     L.dqmc_energy_backward.argtypes = [vp, i32, vp, i32, vp, vp, vp]
@@ -252,6 +254,20 @@ class Ensemble:
         self._check(self._lib.dqmc_measure_tau(self._h, int(n_tau), None if ph is None else _p(ph), _p(obs), _p(sg),
                                                _p(prec)))
         return obs, sg, prec
+
+    def measure_corr(self, pair_class, n_class):
+        """Equal-time correlation sums per pair class of every chain's current
+        configuration: out[c, k] = (S^z S^z, n n, S^+ S^-, sum_s c^+ c) summed over
+        the pairs of class k; sign[c] = the configuration's sign.  pair_class and
+        n_class: one entry per model (class map [N*N], number of classes)."""
+        cls = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.int32).ravel() for a in pair_class]))
+        nc = np.ascontiguousarray(n_class, dtype=np.int32)
+        if cls.size != sum(m.N * m.N for m in self.models) or nc.size != len(self.models):
+            raise DqmcError(DQMC_EINVAL, "one class map [N*N] and one class count per model")
+        out = np.zeros((self.n_chains, int(nc.max()), 4))
+        sg = np.zeros(self.n_chains, dtype=np.int32)
+        self._check(self._lib.dqmc_measure_corr(self._h, _p(cls), _p(nc), _p(out), _p(sg)))
+        return out, sg
 
     def get_fields(self):
         sizes = [self.model_of(c).L * self.model_of(c).n_vertices for c in range(self.n_chains)]
