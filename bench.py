@@ -234,8 +234,8 @@ DW_PEAK_TF = FP32_PEAK_TF / 12.0 * 1.0
 # of the full workload (profiles/dram_sweep_kernel_square256.md), keyed by
 # (precision, workload, delay_k); other cases report null.
 TRAFFIC_BYTES = {
-    ("mixed", "square 8x8/12x12 x256 chains", 16): 10356692224 + 26193950208,
-    ("fp64", "square 8x8/12x12 x256 chains", 16): 10076649728 + 21551729664,
+    ("mixed", "square 8x8/12x12 x256 chains", 16): 10183387136 + 26127431936,
+    ("fp64", "square 8x8/12x12 x256 chains", 16): 10456027392 + 22116251136,
 }
 
 
