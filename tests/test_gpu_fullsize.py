@@ -1,0 +1,83 @@
+"""Parity at the benchmark's full sizes, in the launch configurations bench.py times.
+
+* 256 chains of the square 8x8 / 12x12 workload (one launch per sweep, delayed
+  rank 16, mixed and FP64 paths): after one sweep of the whole batch, one chain of
+  each (N, beta) class is replayed by the FP64 oracle from the same initial fields
+  and seed.  Fields must agree bit for bit and G(0) to the path's tolerance (1e-10
+  FP64, 1e-7 float pairs: the reduced-precision bar is 1e-6).
+* 32 chains of the 20x20, beta = 10, L = 200 workload with the split-BF16
+  tensor-core products and rank 32 (the autotuner's choice at N = 400): the oracle
+  needs minutes per G there, so the checks are properties that hold at any size:
+  the working G(0) after the sweep equals the FP64 recompute from the chain's
+  fields to 1e-6, the precision monitor stays below 1e-4, fields stay +-1.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_1704_00131_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-7}
+
+
+@pytest.fixture(scope="module")
+def dq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00131_gb300 import build_ext, dqmc
+    build_ext.build()
+    return dqmc
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_256_chain_workload_sampled_chains_follow_the_oracle(dq, orc, precision):
+    wl = W.config_c3()
+    ens = dq.Ensemble(wl.models, wl.chain_model, precision=precision, delay_k=16, seed=W.BASE_SEED)
+    f0, _ = ens.get_fields()
+    st = ens.sweep(1)
+    assert st["proposals"] == wl.proposals_per_sweep()
+    f1, ctr = ens.get_fields()
+    assert ctr == 1
+    # one chain per (N, beta) class: c < 128 is 8x8, c even is beta = 4
+    sample = [0, 1, 128, 129]
+    res = {}
+
+    def replay(c):
+        m = wl.models[wl.chain_model[c]]
+        om = orc.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+        och = orc.Chain(om, f0[c], seed=W.BASE_SEED, chain=c)
+        och.sweep(1)
+        res[c] = (och.fields()[0], och.green(0), och.green(1))
+
+    th = [threading.Thread(target=replay, args=(c,)) for c in sample]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for c in sample:
+        fo, G0, G1 = res[c]
+        assert np.array_equal(f1[c], fo), c
+        assert np.abs(ens.greens(c, 0)[0] - G0).max() < TOL[precision], c
+        assert np.abs(ens.greens(c, 1)[0] - G1).max() < TOL[precision], c
+    ens.close()
+
+
+def test_20x20_workload_properties(dq):
+    wl = W.config_c5()
+    ens = dq.Ensemble(wl.models, wl.chain_model, precision="mixed_tc", delay_k=32, seed=W.BASE_SEED)
+    st = ens.sweep(1)
+    assert st["proposals"] == wl.proposals_per_sweep()
+    assert 0 < st["accepted"] < st["proposals"]
+    assert st["prec_green_max"] < 1e-4 and st["prec_green_mean"] < 1e-8
+    f, _ = ens.get_fields()
+    assert all(set(np.unique(x)) <= {-1, 1} for x in f)
+    for c in (0, 31):
+        for s in (0, 1):
+            Gw, _, _ = ens.greens(c, s)
+            Gf, _, _ = ens.greens(c, s, fresh=True)
+            assert np.abs(Gw - Gf).max() < 1e-6, (c, s)
+    ens.close()
