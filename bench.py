@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 path")
     ap.add_argument("--peaks", action="store_true", help="measure the matmul peaks used as roofline denominators")
     ap.add_argument("--no-oracle-check", action="store_true", help="skip the max|dG| check against the oracle")
+    ap.add_argument("--paper-example", action="store_true",
+                    help="precision monitors of the paper's 4x4, U=4, beta=10 spin-z example instead of the bench")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --precision and the workload's delay_k as given instead of tuning them")
     return ap.parse_args()
@@ -466,10 +468,42 @@ def measure_peaks():
     print(json.dumps(res), flush=True)
 
 
+def paper_example(args):
+    """The numerical-precision example the paper prints for the spin-z decoupling
+    (Sec. 6, 4x4 square lattice, U/t = 4, beta t = 10; here dtau = 0.1, n_wrap = 10):
+    the "Precision Green" and "Precision tau" monitors (mean, max) of the FP64 and
+    mixed paths over args.steps sweeps after args.warmup, with the time-displaced
+    functions measured after every sweep, next to the values of the paper's info file."""
+    from paper_1704_00131_gb300 import build_ext, dqmc
+    build_ext.build()
+    m = W.ModelSpec(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=100, n_wrap=10, name="square4x4_U4_b10")
+    out = {"workload": m.name, "sweeps": args.steps, "warmup": args.warmup,
+           "paper_info_file": {"precision_green_mean_max": [5.0823874429126405e-11, 5.8621144596315844e-06],
+                               "precision_tau_mean_max": [1.5929357848647394e-11, 1.0985132530727526e-05]}}
+    for prec in ("fp64", "mixed"):
+        ens = dqmc.Ensemble([m], [0], precision=prec, delay_k=16, seed=W.BASE_SEED)
+        ens.sweep(args.warmup, stats=False)
+        gm, gx, tm, tx = [], 0.0, [], 0.0
+        for _ in range(args.steps):
+            st = ens.sweep(1)
+            gm.append(st["prec_green_mean"])
+            gx = max(gx, st["prec_green_max"])
+            _, _, pt = ens.measure_tau(m.L)
+            tm.append(pt[0])
+            tx = max(tx, pt[1])
+        ens.close()
+        out[prec] = {"precision_green_mean_max": [float(np.mean(gm)), gx],
+                     "precision_tau_mean_max": [float(np.mean(tm)), tx]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.peaks:
         measure_peaks()
+        return
+    if args.paper_example:
+        paper_example(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
