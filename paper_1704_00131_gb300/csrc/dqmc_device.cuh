@@ -2142,7 +2142,63 @@ static cudaError_t launch_sweep_t(ChainDev* chains, const SweepParams& p, int nf
   return cudaLaunchKernelEx(&cfg, sweep_kernel<Real>, chains, p);
 }
 
+// Time-displaced Green functions from the two chains, sharing the middle
+// matrix of the stable G (Sec. 2.1 observables, two times):
+//   G(tau,0) = Q_L Db_L^-1 Mid^-1 Ds_R T_R,
+//   G(0,tau) = -T_L^T Ds_L Mid^-1 Db_R^-1 Q_R^T.
+// Uses W0, W1, W7, W8.  Returns nonzero if Mid is singular.
+__device__ int displaced_from_udv(const ChainDev& C, int s, UDV R, UDV Lf, double* Gt0, double* G0t, Smem& S) {
+  const int N = C.N, ld = C.ld;
+  double* W0 = wmat(C, s, 0);
+  double* W1 = wmat(C, s, 1);
+  double* W7 = wmat(C, s, 7);
+  double* W8 = wmat(C, s, 8);
+  cta_gemm<double, true, false>(N, N, N, R.Q, ld, Lf.Q, ld, W0, ld, S.gemm);
+  cta_gemm<double, false, true>(N, N, N, R.T, ld, Lf.T, ld, W1, ld, S.gemm);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double dR = R.D[i], dL = Lf.D[j];
+    const double dbR = dR > 1.0 ? dR : 1.0, dsR = dR > 1.0 ? 1.0 : dR;
+    const double dbL = dL > 1.0 ? dL : 1.0, dsL = dL > 1.0 ? 1.0 : dL;
+    W0[(size_t)i * ld + j] = W0[(size_t)i * ld + j] / (dbR * dbL) + dsR * W1[(size_t)i * ld + j] * dsL;
+  }
+  __syncthreads();
+  double ldm;
+  int smi;
+  int* piv = C.iwork[s] + ld;
+  double* tmp = wmat(C, s, 9);
+  if (lu_factor_blk(N, ld, W0, piv, tmp, ldm, smi, S)) return 1;
+  int* rowof = C.iwork[s];
+  lu_row_map(N, piv, rowof);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    W1[(size_t)i * ld + j] = (rowof[i] == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  lu_solve_blk(N, ld, W0, W1, tmp, S);  // W1 = Mid^-1
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double m = W1[(size_t)i * ld + j];
+    const double dLi = Lf.D[i], dRj = R.D[j];
+    W7[(size_t)i * ld + j] = m / (dLi > 1.0 ? dLi : 1.0) * (dRj > 1.0 ? 1.0 : dRj);
+    W8[(size_t)i * ld + j] = (dLi > 1.0 ? 1.0 : dLi) * m / (dRj > 1.0 ? dRj : 1.0);
+  }
+  __syncthreads();
+  cta_gemm<double, false, false>(N, N, N, Lf.Q, ld, W7, ld, W0, ld, S.gemm);
+  cta_gemm<double, false, false>(N, N, N, W0, ld, R.T, ld, Gt0, ld, S.gemm);
+  cta_gemm<double, true, false>(N, N, N, Lf.T, ld, W8, ld, W0, ld, S.gemm);
+  cta_gemm<double, false, true>(N, N, N, W0, ld, R.Q, ld, G0t, ld, S.gemm);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    G0t[(size_t)i * ld + j] = -G0t[(size_t)i * ld + j];
+  }
+  __syncthreads();
+  return 0;
+}
+
 }  // namespace
+
+size_t get_smem_bytes();  // dynamic shared memory of the fresh-G / adjoint / measurement kernels
 
 // One pair per precision unit: 0 = FP64, 1 = FP32, 2/3 = float-pair (mixed).
 cudaError_t launch_sweep_fp64(ChainDev* chains, const SweepParams& p, int nfl, size_t smem, cudaStream_t st);
