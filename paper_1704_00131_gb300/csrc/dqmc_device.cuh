@@ -1261,11 +1261,37 @@ __device__ int fill_left_chain(const ChainDev& C, int s, Smem& S, double& logdet
   return green_from_udv(C, s, ident_udv(C), slot_udv(C, s, 0), wmat(C, s, 6), logdet, sign, S);
 }
 
+// The float-pair stabilisation (defined with the mixed path below).
+__device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S,
+                                long long* det);
+__device__ int green_from_udv_mixed(const ChainDev& C, int s, UDV R, UDV Lf, double* Gout, double& logdet,
+                                    int& sign, Smem& S);
+
+// Left chain and G(0) with the stabilisation arithmetic of the working
+// precision: float pairs (FP64 scales) for the mixed paths, FP64 otherwise.
+// Used when a chain starts or restarts from fields, so that the stored chain is
+// the one the sweep itself would have left.
+template <typename Real>
+__device__ int fill_left_chain_working(const ChainDev& C, int s, Smem& S, double& logdet, int& sign) {
+  if constexpr (std::is_same<Real, dd>::value) {
+    const int nst = C.L / C.nw;
+    for (int j = nst - 1; j >= 0; --j) {
+      const UDV src = (j + 1 == nst) ? ident_udv(C) : slot_udv(C, s, j + 1);
+      const int dq = chain_step_mixed(C, s, j * C.nw, (j + 1) * C.nw, true, src, S, nullptr);
+      copy_udv_to_slot(C, s, j, dq);
+    }
+    return green_from_udv_mixed(C, s, ident_udv(C), slot_udv(C, s, 0), wmat(C, s, 6), logdet, sign, S);
+  } else {
+    return fill_left_chain(C, s, S, logdet, sign);
+  }
+}
+
 // --------------------------------------------------------------------------
 // Kernels templated on the working precision.
 // --------------------------------------------------------------------------
 // Fresh G(0) for every (chain, flavor): the left chain is (re)computed into the
-// storage slots, G(0) lands in W6.  mode 0: also write the working G, the
+// storage slots, G(0) lands in W6.  mode 0 (start from fields, in the working
+// precision's stabilisation arithmetic): also write the working G, the
 // fresh log|det| and the sign (initialisation); mode 1: copy G(0) of chain
 // `out_chain` to `out` (FP64, [nfl][N][N]).
 template <typename Real>
@@ -1280,7 +1306,9 @@ __global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains,
   Smem S = carve_smem(smem_raw, C.ld, C.MV);
   double logdet;
   int sign;
-  if (fill_left_chain(C, s, S, logdet, sign)) {
+  const int bad = (mode == 0) ? fill_left_chain_working<Real>(C, s, S, logdet, sign)
+                              : fill_left_chain(C, s, S, logdet, sign);
+  if (bad) {
     if (threadIdx.x == 0) C.error = 1;
     return;
   }
