@@ -76,3 +76,50 @@ class Fock:
             w = sum(gamma[l] * np.exp(g * eta[l] * A) for l in (-2, -1, 1, 2)) / 4.0
             W = W @ np.diag(w)
         return np.linalg.matrix_power(E @ W, L)
+
+
+def tau_observables(F, K, U, dtau, L, ph):
+    """Local Green function sum_s,x <c_xs(tau) c^+_xs(0)> and the phase-weighted
+    sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)> for tau = 0..L of the Trotterised
+    Ising-decoupled Hubbard model: <A(tau) B(0)> = Tr[T^{L-tau} A T^tau B] / Tr[T^L]
+    with T = exp(-dtau H_T) exp(-dtau H_U)."""
+    N = K.shape[0]
+    T = expm(-dtau * F.hopping(K)) @ expm(-dtau * F.hubbard_ph(U))
+    Z = np.trace(np.linalg.matrix_power(T, L))
+    Sz = [0.5 * (F.n(0, x) - F.n(1, x)) for x in range(N)]
+    SzP = sum(ph[x] * Sz[x] for x in range(N))
+    gl, szz = [], []
+    for tau in range(L + 1):
+        A = np.linalg.matrix_power(T, L - tau)
+        B = np.linalg.matrix_power(T, tau)
+        g = 0.0
+        for s in range(2):
+            for x in range(N):
+                c = F.c[F.mode(s, x)]
+                g += np.trace(A @ c @ B @ c.T)
+        gl.append(g / Z)
+        szz.append(np.trace(A @ SzP @ B @ SzP) / Z)
+    return np.array(gl), np.array(szz)
+
+
+def equal_time_correlations(F, K, U, dtau, L, cls, n_class):
+    """Per pair class: sums of <S^z_x S^z_y>, <n_x n_y>, <S^+_x S^-_y> and
+    sum_s <c^+_xs c_ys> in the Trotterised density matrix (trace boundary)."""
+    N = K.shape[0]
+    rho = F.trotter_ising(K, U, dtau, L)
+    Z = np.trace(rho)
+    out = np.zeros((n_class, 4))
+    cu = [F.c[F.mode(0, x)] for x in range(N)]
+    cd = [F.c[F.mode(1, x)] for x in range(N)]
+    for x in range(N):
+        for y in range(N):
+            c = cls[x * N + y]
+            szx = 0.5 * (F.n(0, x) - F.n(1, x))
+            szy = 0.5 * (F.n(0, y) - F.n(1, y))
+            nx = F.n(0, x) + F.n(1, x)
+            ny = F.n(0, y) + F.n(1, y)
+            spm = cu[x].T @ cd[x] @ cd[y].T @ cu[y]
+            hop = cu[x].T @ cu[y] + cd[x].T @ cd[y]
+            for q, O in enumerate((szx @ szy, nx @ ny, spm, hop)):
+                out[c, q] += np.trace(O @ rho) / Z
+    return out

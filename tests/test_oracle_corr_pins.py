@@ -18,35 +18,13 @@ import pytest
 
 from paper_1704_00131_gb300 import workloads as W
 
-from .fock_ed import Fock
+from .fock_ed import Fock, equal_time_correlations
 
 
 def make_model(orc, K, U, dtau, L, nwrap):
     N = K.shape[-1]
     sign = np.stack([np.ones(N), -np.ones(N)])
     return orc.Model(np.stack([K, K]), np.arange(N, dtype=np.int32), sign, U, dtau, L, nwrap, 1)
-
-
-def fock_correlations(K, U, dtau, L, cls, n_class):
-    N = K.shape[0]
-    F = Fock(N)
-    rho = F.trotter_ising(K, U, dtau, L)
-    Z = np.trace(rho)
-    out = np.zeros((n_class, 4))
-    cu = [F.c[F.mode(0, x)] for x in range(N)]
-    cd = [F.c[F.mode(1, x)] for x in range(N)]
-    for x in range(N):
-        for y in range(N):
-            c = cls[x * N + y]
-            szx = 0.5 * (F.n(0, x) - F.n(1, x))
-            szy = 0.5 * (F.n(0, y) - F.n(1, y))
-            nx = F.n(0, x) + F.n(1, x)
-            ny = F.n(0, y) + F.n(1, y)
-            spm = cu[x].T @ cd[x] @ cd[y].T @ cu[y]
-            hop = cu[x].T @ cu[y] + cd[x].T @ cd[y]
-            for q, O in enumerate((szx @ szy, nx @ ny, spm, hop)):
-                out[c, q] += np.trace(O @ rho) / Z
-    return out
 
 
 @pytest.mark.parametrize("cluster", ["dimer", "plaquette"])
@@ -70,7 +48,7 @@ def test_correlations_enumeration_equals_fock_trace(orc, cluster):
         w = s0 * s1 * math.exp(ld0 + ld1)
         Z += w
         acc += w * orc.correlations(np.stack([G0, G1]), cls, n_class)
-    ref = fock_correlations(K, U, dtau, L, cls, n_class)
+    ref = equal_time_correlations(Fock(N), K, U, dtau, L, cls, n_class)
     assert acc / Z == pytest.approx(ref, rel=1e-10, abs=1e-12)
 
 

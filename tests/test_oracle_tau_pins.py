@@ -16,11 +16,10 @@ import math
 
 import numpy as np
 import pytest
-from scipy.linalg import expm
 
 from paper_1704_00131_gb300 import workloads as W
 
-from .fock_ed import Fock
+from .fock_ed import Fock, tau_observables
 
 
 def make_model(orc, K, U, dtau, L, nwrap, ft=1):
@@ -80,26 +79,6 @@ def test_conserved_particle_number_per_configuration(orc):
     assert np.ptp(out2[:, 0, 1]) > 1e-3
 
 
-def _fock_tau(F, K, U, dtau, L, ph):
-    N = K.shape[0]
-    T = expm(-dtau * F.hopping(K)) @ expm(-dtau * F.hubbard_ph(U))
-    Z = np.trace(np.linalg.matrix_power(T, L))
-    Sz = [0.5 * (F.n(0, x) - F.n(1, x)) for x in range(N)]
-    SzP = sum(ph[x] * Sz[x] for x in range(N))
-    gl, szz = [], []
-    for tau in range(L + 1):
-        A = np.linalg.matrix_power(T, L - tau)
-        B = np.linalg.matrix_power(T, tau)
-        g = 0.0
-        for s in range(2):
-            for x in range(N):
-                c = F.c[F.mode(s, x)]
-                g += np.trace(A @ c @ B @ c.T)
-        gl.append(g / Z)
-        szz.append(np.trace(A @ SzP @ B @ SzP) / Z)
-    return np.array(gl), np.array(szz)
-
-
 @pytest.mark.parametrize("cluster", ["dimer", "chain3"])
 def test_tau_enumeration_equals_fock_trace(orc, cluster):
     if cluster == "dimer":
@@ -124,6 +103,6 @@ def test_tau_enumeration_equals_fock_trace(orc, cluster):
         gl += w * (out[:, 0, 0] + out[:, 1, 0])
         szz += w * orc.szz_from_tau(out)
     F = Fock(N)
-    gl_ed, szz_ed = _fock_tau(F, K, U, dtau, L, ph)
+    gl_ed, szz_ed = tau_observables(F, K, U, dtau, L, ph)
     assert gl / Z == pytest.approx(gl_ed, rel=1e-10, abs=1e-12)
     assert szz / Z == pytest.approx(szz_ed, rel=1e-10, abs=1e-12)
