@@ -130,16 +130,6 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   for (int w = 1; w < kThreads / 32; ++w) r = fmax(r, red[w]);
   return r;
 }
-__device__ __forceinline__ int block_min_int(int v, int* ired) {
-  v = __reduce_min_sync(0xffffffffu, v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) ired[threadIdx.x >> 5] = v;
-  __syncthreads();
-  int r = ired[0];
-#pragma unroll
-  for (int w = 1; w < kThreads / 32; ++w) r = min(r, ired[w]);
-  return r;
-}
 // argmax of v over the block, ties to the lowest index; returns the index.
 __device__ __forceinline__ int block_argmax(double v, int idx, double* red, int* ired) {
 #pragma unroll
