@@ -1,0 +1,115 @@
+"""Bins of sweeps and their analysis, the way the paper's main program runs a
+simulation (Sec. 5: NBin bins of NSweep sweeps, equal-time and time-displaced
+observables accumulated per bin, bin results analysed with the jackknife).
+
+The Markov chains of an `Ensemble` are independent walkers (the paper's one
+walker per MPI task); a bin pools the sign-weighted measurements of all chains
+over its sweeps.  Everything here is host bookkeeping over the library's
+measurement calls: `Ensemble.sweep`, `Ensemble.measure` (energy estimator over
+the measurement window), `Ensemble.measure_tau` and `Ensemble.measure_corr`
+(one sample per chain after each sweep).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import analysis
+
+
+@dataclass
+class Result:
+    """Jackknife mean and error over bins of each sign-reweighted observable."""
+
+    n_bins: int
+    sweeps_per_bin: int
+    mean_sign: float
+    mean: dict = field(default_factory=dict)
+    error: dict = field(default_factory=dict)
+
+
+class Simulation:
+    """Run `n_bins` bins of `sweeps_per_bin` sweeps after `warmup` sweeps.
+
+    tau:  (n_tau, site_phase per model) -> "gloc_tau" (sum_s,x G(tau,0)_xx per
+          site and flavor) and "szz_tau" (sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)>)
+    corr: (pair_class per model, n_class per model) -> "corr_zz", "corr_nn",
+          "corr_pm", "corr_gf" per class
+    The energy estimator ("kin", "pot", "part", "ener") comes from the ensemble's
+    own measurement window (the ensemble must be created with measure=True).
+    Chains of different models are pooled, so `tau` and `corr` need a single
+    model (or models with the same sizes).
+    """
+
+    def __init__(self, ensemble, n_bins: int, sweeps_per_bin: int, warmup: int = 0, tau=None, corr=None,
+                 energy: bool = True):
+        if n_bins < 2 or sweeps_per_bin < 1 or warmup < 0:
+            raise ValueError("need n_bins >= 2, sweeps_per_bin >= 1, warmup >= 0")
+        self.ens = ensemble
+        self.n_bins = n_bins
+        self.sweeps_per_bin = sweeps_per_bin
+        self.warmup = warmup
+        self.tau = tau
+        self.corr = corr
+        self.energy = energy
+
+    def _one_bin(self):
+        ens = self.ens
+        acc, s_acc = {}, 0.0
+        if self.energy:
+            e0, ss0, n0 = ens.measure()
+        for _ in range(self.sweeps_per_bin):
+            ens.sweep(1, stats=False)
+            sign = None
+            if self.tau is not None:
+                n_tau, phases = self.tau
+                obs, sg, _ = ens.measure_tau(n_tau, phases)
+                sign = np.prod(sg, axis=1).astype(np.float64)
+                n_sites = np.array([ens.model_of(c).N for c in range(ens.n_chains)], dtype=np.float64)
+                nfl = obs.shape[2]
+                gloc = obs[:, :, :, 0].sum(axis=2) / (nfl * n_sites[:, None])
+                m = obs[..., 0, 2] - obs[..., 1, 2]
+                szz = (m * m[..., :1] + obs[..., 0, 1] + obs[..., 1, 1]) / 4.0
+                acc["gloc_tau"] = acc.get("gloc_tau", 0.0) + (sign[:, None] * gloc).sum(axis=0)
+                acc["szz_tau"] = acc.get("szz_tau", 0.0) + (sign[:, None] * szz).sum(axis=0)
+            if self.corr is not None:
+                classes, n_class = self.corr
+                c, sgc = ens.measure_corr(classes, n_class)
+                sgc = sgc.astype(np.float64)
+                if sign is None:
+                    sign = sgc
+                for q, name in enumerate(("corr_zz", "corr_nn", "corr_pm", "corr_gf")):
+                    acc[name] = acc.get(name, 0.0) + (sgc[:, None] * c[:, :, q]).sum(axis=0)
+            if sign is not None:
+                s_acc += sign.sum()
+        out = {k: v / self.sweeps_per_bin for k, v in acc.items()}
+        s_bin = s_acc / self.sweeps_per_bin
+        if self.energy:
+            e1, ss1, n1 = ens.measure()
+            nm = float((n1 - n0).sum())
+            if nm > 0:
+                de = (e1 - e0).sum(axis=0) / nm                  # sum over chains of sign * O per measurement
+                ds = float((ss1 - ss0).sum()) / nm
+                for q, name in enumerate(("kin", "pot", "part", "ener")):
+                    out[name] = de[q]
+                out["_sign_energy"] = ds
+        return out, s_bin
+
+    def run(self) -> Result:
+        if self.warmup:
+            self.ens.sweep(self.warmup, stats=False)
+        bins = [self._one_bin() for _ in range(self.n_bins)]
+        res = Result(self.n_bins, self.sweeps_per_bin, 0.0)
+        names = sorted({k for b, _ in bins for k in b if not k.startswith("_")})
+        signs = np.array([s for _, s in bins])
+        e_signs = np.array([b.get("_sign_energy", np.nan) for b, _ in bins])
+        for k in names:
+            data = np.array([b[k] for b, _ in bins])
+            sg = e_signs if k in ("kin", "pot", "part", "ener") else signs
+            res.mean[k], res.error[k] = analysis.jackknife(data, sg)
+        if self.tau is not None or self.corr is not None:
+            res.mean_sign = float(signs.mean() / self.ens.n_chains)   # per chain and sweep
+        else:
+            res.mean_sign = float(np.nanmean(e_signs))                 # per measurement
+        return res

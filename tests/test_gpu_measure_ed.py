@@ -70,3 +70,27 @@ def test_measurements_match_exact_diagonalisation(dq, precision):
     # function measure the same staggered S^z S^z
     stag = np.array([ph[0] * ph[j] for j in range(4)])
     assert np.allclose(szz_sum[:, 0], (corr_sum[:, :, 0] * stag[None, :]).sum(axis=1), atol=1e-6)
+
+
+def test_simulation_driver_matches_exact_diagonalisation(dq):
+    """The bin driver over the same calls: energy (measurement window), local
+    G(tau) and the equal-time correlations, jackknife over 8 bins (whose error
+    bars are themselves uncertain by about a quarter), within 5 sigma."""
+    from paper_1704_00131_gb300.simulation import Simulation
+    K = W.square_lattice(2, 2, t=1.0)
+    U, dtau, L = 4.0, 0.125, 8
+    m = W.ModelSpec(K, U=U, dtau=dtau, L=L, n_wrap=4)
+    cls, ncls, _ = W.translation_classes_square(2, 2)
+    F = Fock(4)
+    gl_ed, _ = tau_observables(F, K, U, dtau, L, np.ones(4))
+    corr_ed = equal_time_correlations(F, K, U, dtau, L, cls, ncls)
+    rho = F.trotter_ising(K, U, dtau, L)
+    kin_ed = np.trace(F.hopping(K) @ rho) / np.trace(rho)
+    ens = dq.Ensemble([m], [0] * 32, precision="fp64", seed=404, measure=True, meas_first=0, meas_last=L)
+    res = Simulation(ens, n_bins=8, sweeps_per_bin=15, warmup=20, tau=(L, None), corr=([cls], [ncls])).run()
+    ens.close()
+    assert res.mean_sign == pytest.approx(1.0)
+    # per-chain averages: kin per measurement, gloc per site and flavor (8 = 2 x 4)
+    assert abs(res.mean["kin"] - kin_ed) < 5 * res.error["kin"] + 1e-12
+    assert (np.abs(res.mean["gloc_tau"] * 8 - gl_ed) < 5 * res.error["gloc_tau"] * 8 + 1e-12).all()
+    assert (np.abs(res.mean["corr_zz"] - corr_ed[:, 0]) < 5 * res.error["corr_zz"] + 1e-12).all()

@@ -1,0 +1,80 @@
+"""Bin bookkeeping of the Simulation driver, on a fake ensemble (no GPU)."""
+import numpy as np
+import pytest
+
+from paper_1704_00131_gb300.simulation import Simulation
+
+
+class _Model:
+    N = 4
+
+
+class FakeEnsemble:
+    """Deterministic stand-in with the measurement calls of dqmc.Ensemble."""
+
+    def __init__(self, n_chains=3, L=4, seed=0):
+        self.n_chains = n_chains
+        self.L = L
+        self.rng = np.random.default_rng(seed)
+        self.e = np.zeros((n_chains, 4))
+        self.ss = np.zeros(n_chains)
+        self.nm = np.zeros(n_chains, dtype=np.int64)
+        self.log = []                                   # (sign, obs, corr) per sweep
+
+    def model_of(self, c):
+        return _Model()
+
+    def sweep(self, n, stats=False):
+        for _ in range(n):
+            sg = np.where(self.rng.random((self.n_chains, 2)) < 0.9, 1, -1).astype(np.int32)
+            obs = self.rng.random((self.n_chains, self.L + 1, 2, 3))
+            corr = self.rng.random((self.n_chains, 2, 4))
+            en = self.rng.random((self.n_chains, 4))
+            s = np.prod(sg, axis=1)
+            self.e += 2 * s[:, None] * en                   # two measurements per sweep
+            self.ss += 2 * s
+            self.nm += 2
+            self.log.append((s.astype(float), obs, corr, en))
+            self.cur = (sg, obs, corr)
+
+    def measure(self):
+        return self.e.copy(), self.ss.copy(), self.nm.copy()
+
+    def measure_tau(self, n_tau, phases):
+        sg, obs, _ = self.cur
+        return obs, sg, np.zeros(2)
+
+    def measure_corr(self, classes, n_class):
+        sg, _, corr = self.cur
+        return corr, np.prod(sg, axis=1).astype(np.int32)
+
+
+def test_bins_pool_chains_and_reweight_by_sign():
+    ens = FakeEnsemble()
+    sim = Simulation(ens, n_bins=4, sweeps_per_bin=5, warmup=2, tau=(4, None), corr=([None], [2]))
+    res = sim.run()
+    log = ens.log[2:]                                   # after the warm-up
+    s = np.array([x[0] for x in log])                   # [sweeps, chains]
+    corr = np.array([x[2] for x in log])                # [sweeps, chains, class, 4]
+    en = np.array([x[3] for x in log])
+    want_zz = (s[:, :, None] * corr[:, :, :, 0]).sum(axis=(0, 1)) / s.sum()
+    assert res.mean["corr_zz"] == pytest.approx(want_zz, rel=1e-12)
+    want_kin = (s * en[:, :, 0]).sum() / s.sum()
+    assert res.mean["kin"] == pytest.approx(want_kin, rel=1e-12)
+    obs = np.array([x[1] for x in log])                 # [sweeps, chains, tau, fl, 3]
+    m = obs[..., 0, 2] - obs[..., 1, 2]
+    szz = (m * m[..., :1] + obs[..., 0, 1] + obs[..., 1, 1]) / 4.0
+    want_szz = (s[:, :, None] * szz).sum(axis=(0, 1)) / s.sum()
+    assert res.mean["szz_tau"] == pytest.approx(want_szz, rel=1e-12)
+    gl = obs[..., 0].sum(axis=3) / (2 * 4)
+    assert res.mean["gloc_tau"] == pytest.approx((s[:, :, None] * gl).sum(axis=(0, 1)) / s.sum(), rel=1e-12)
+    assert all(np.all(np.asarray(res.error[k]) > 0) for k in res.mean)
+    assert res.mean_sign == pytest.approx(s.mean(), rel=1e-12)
+    assert res.n_bins == 4 and res.sweeps_per_bin == 5
+
+
+def test_bad_parameters():
+    with pytest.raises(ValueError):
+        Simulation(FakeEnsemble(), n_bins=1, sweeps_per_bin=1)
+    with pytest.raises(ValueError):
+        Simulation(FakeEnsemble(), n_bins=2, sweeps_per_bin=0)
