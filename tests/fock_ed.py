@@ -69,22 +69,29 @@ class Fock:
     def trotter_hs4(self, K, U, dtau, L, eta, gamma):
         """(exp(-dtau H_T) W)^L with W = prod_i (1/4) sum_l gamma(l) exp(g eta(l) (n_up - n_dn))."""
         E = expm(-dtau * self.hopping(K))
-        g = np.sqrt(0.5 * dtau * U)
-        W = np.eye(self.dim)
-        for i in range(self.N):
-            A = np.diag(self.n(0, i)) - np.diag(self.n(1, i))
-            w = sum(gamma[l] * np.exp(g * eta[l] * A) for l in (-2, -1, 1, 2)) / 4.0
-            W = W @ np.diag(w)
-        return np.linalg.matrix_power(E @ W, L)
+        return np.linalg.matrix_power(E @ hs4_slice(self, U, dtau, eta, gamma), L)
 
 
-def tau_observables(F, K, U, dtau, L, ph):
+def hs4_slice(F, U, dtau, eta, gamma):
+    """prod_i (1/4) sum_l gamma(l) exp(g eta(l) (n_i,up - n_i,dn)), g = sqrt(dtau U / 2):
+    the interaction factor of one slice after summing the four-valued field."""
+    g = np.sqrt(0.5 * dtau * U)
+    W = np.eye(F.dim)
+    for i in range(F.N):
+        A = np.diag(F.n(0, i)) - np.diag(F.n(1, i))
+        W = W @ np.diag(sum(gamma[l] * np.exp(g * eta[l] * A) for l in (-2, -1, 1, 2)) / 4.0)
+    return W
+
+
+def tau_observables(F, K, U, dtau, L, ph, W=None):
     """Local Green function sum_s,x <c_xs(tau) c^+_xs(0)> and the phase-weighted
     sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)> for tau = 0..L of the Trotterised
-    Ising-decoupled Hubbard model: <A(tau) B(0)> = Tr[T^{L-tau} A T^tau B] / Tr[T^L]
-    with T = exp(-dtau H_T) exp(-dtau H_U)."""
+    Hubbard model: <A(tau) B(0)> = Tr[T^{L-tau} A T^tau B] / Tr[T^L] with
+    T = exp(-dtau H_T) W, W = exp(-dtau H_U) (exact Ising decoupling) unless given."""
     N = K.shape[0]
-    T = expm(-dtau * F.hopping(K)) @ expm(-dtau * F.hubbard_ph(U))
+    if W is None:
+        W = expm(-dtau * F.hubbard_ph(U))
+    T = expm(-dtau * F.hopping(K)) @ W
     Z = np.trace(np.linalg.matrix_power(T, L))
     Sz = [0.5 * (F.n(0, x) - F.n(1, x)) for x in range(N)]
     SzP = sum(ph[x] * Sz[x] for x in range(N))

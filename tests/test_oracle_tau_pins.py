@@ -19,7 +19,7 @@ import pytest
 
 from paper_1704_00131_gb300 import workloads as W
 
-from .fock_ed import Fock, tau_observables
+from .fock_ed import Fock, hs4_slice, tau_observables
 
 
 def make_model(orc, K, U, dtau, L, nwrap, ft=1):
@@ -104,5 +104,33 @@ def test_tau_enumeration_equals_fock_trace(orc, cluster):
         szz += w * orc.szz_from_tau(out)
     F = Fock(N)
     gl_ed, szz_ed = tau_observables(F, K, U, dtau, L, ph)
+    assert gl / Z == pytest.approx(gl_ed, rel=1e-10, abs=1e-12)
+    assert szz / Z == pytest.approx(szz_ed, rel=1e-10, abs=1e-12)
+
+
+def test_tau_enumeration_equals_fock_trace_hs4(orc):
+    """Four-valued HS fields of a dimer (4^(N L) = 4096 configurations), weighted
+    by prod gamma(l)/4 and the determinants: the time-displaced averages equal the
+    Fock trace with the summed HS4 slice factor inserted between hoppings."""
+    K, U, dtau, L = W.chain_lattice(2, t=1.0, mu=-0.2), 4.0, 0.2, 3
+    N = 2
+    ph = np.array([1.0, -1.0])
+    m = make_model(orc, K, U, dtau, L, L, ft=2)
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    Z = 0.0
+    gl = np.zeros(L + 1)
+    szz = np.zeros(L + 1)
+    for ls in itertools.product((-2, -1, 1, 2), repeat=N * L):
+        f = np.array(ls, dtype=np.int8).reshape(L, N)
+        _, ld0, s0 = orc.green_udv(m, f, 0, 0)
+        _, ld1, s1 = orc.green_udv(m, f, 1, 0)
+        w = np.prod([gam[l] / 4.0 for l in ls]) * s0 * s1 * math.exp(ld0 + ld1)
+        out, _ = orc.tau_observables(m, f, L, ph)
+        Z += w
+        gl += w * (out[:, 0, 0] + out[:, 1, 0])
+        szz += w * orc.szz_from_tau(out)
+    F = Fock(N)
+    gl_ed, szz_ed = tau_observables(F, K, U, dtau, L, ph, W=hs4_slice(F, U, dtau, eta, gam))
     assert gl / Z == pytest.approx(gl_ed, rel=1e-10, abs=1e-12)
     assert szz / Z == pytest.approx(szz_ed, rel=1e-10, abs=1e-12)
