@@ -162,6 +162,7 @@ def oracle_sample(wl: W.Workload, n_threads: int, per_class: int):
             chains[i][0].sweep(1)
 
     t0 = time.perf_counter()
+    n_threads = max(1, min(n_threads, len(chains)))       # threads that get work
     th = [threading.Thread(target=worker) for _ in range(n_threads)]
     for t in th:
         t.start()
@@ -171,20 +172,21 @@ def oracle_sample(wl: W.Workload, n_threads: int, per_class: int):
     props = sum(p for _, p in chains)
     desc = (f"1 sweep each of {len(chains)} chains ({per_class} per model class of the workload: "
             + ", ".join(f"{wl.models[mi].name}" for mi in sorted(classes)) + f") on {n_threads} threads")
-    return props, dt, desc
+    return props, dt, desc, n_threads
 
 
 def run_reference(args, wl: W.Workload, rank: int):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
-    per_class = max(1, cores // max(1, len(set(wl.chain_model.tolist()))))
+    n_cls = max(1, len(set(wl.chain_model.tolist())))
+    per_class = max(1, -(-cores // n_cls))                   # enough chains to give every core work
     for _ in range(args.warmup):
         oracle_sample(wl, cores, 1)
     times, props = [], 0
-    desc = ""
+    desc, used = "", cores
     for _ in range(args.steps):
-        p, dt, desc = oracle_sample(wl, cores, per_class)
+        p, dt, desc, used = oracle_sample(wl, cores, per_class)
         times.append(dt)
         props = p
     tot = sum(times)
@@ -197,7 +199,7 @@ def run_reference(args, wl: W.Workload, rank: int):
         "data": "synthetic (seeded Philox fields)",
         "config": {"workload": wl.name, "chains": wl.n_chains, "sample": desc},
         "sweeps_per_s": sweeps_per_s,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -396,8 +398,9 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
                 "prec_green_max": rf["st"]["prec_green_max"], "prec_green_mean": rf["st"]["prec_green_mean"]}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        p, dt, desc = oracle_sample(wl, cores, max(1, cores // len(set(wl.chain_model.tolist()))))
-        cpu = {"value": p / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        n_cls = max(1, len(set(wl.chain_model.tolist())))
+        p, dt, desc, used = oracle_sample(wl, cores, max(1, -(-cores // n_cls)))
+        cpu = {"value": p / dt, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc}
     if rank == 0:
         line = {
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
