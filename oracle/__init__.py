@@ -98,6 +98,7 @@ def lib():
         _lib.orc_energy_grad.argtypes = [vp, vp, vp, vp, vp]
         _lib.orc_tau_observables.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp]
         _lib.orc_correlations.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp]
+        _lib.orc_su2_plain.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         del i32
     return _lib
 
@@ -322,6 +323,22 @@ def correlations(G: np.ndarray, pair_class: np.ndarray, n_class: int) -> np.ndar
     out = np.zeros((n_class, 4))
     _check(lib().orc_correlations(N, _ptr(G), _ptr(cls), int(n_class), _ptr(out)), "correlations")
     return out
+
+
+def su2_plain(K: np.ndarray, dtau: float, U: float, fields: np.ndarray):
+    """SU(2) charge decoupling with complex coupling, plain product (small beta):
+    returns (G complex [N, N], log|det(1+B)|, arg det(1+B), phase -g sum eta,
+    Kin + i.., Pot + i.. of the configuration)."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    N = K.shape[0]
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    L = f.size // N
+    G = np.zeros((N, N, 2))
+    la, ar, ph = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    e = np.zeros(4)
+    _check(lib().orc_su2_plain(N, _ptr(K), float(dtau), float(U), L, _ptr(f), _ptr(G), ctypes.byref(la),
+                               ctypes.byref(ar), ctypes.byref(ph), _ptr(e)), "su2_plain")
+    return G[..., 0] + 1j * G[..., 1], la.value, ar.value, ph.value, complex(e[0], e[1]), complex(e[2], e[3])
 
 
 def szz_from_tau(obs: np.ndarray) -> np.ndarray:

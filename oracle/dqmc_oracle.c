@@ -20,6 +20,8 @@
  *   B(t2,t1) = B_t2 ... B_t1+1
  *   G^s(t)   = (1 + B^s(t,0) B^s(beta,t))^-1          (equal-time Green function)
  */
+#include <complex.h>
+#undef I /* the imaginary unit is written _Complex_I; I names a local below */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -1297,4 +1299,117 @@ int orc_correlations(int N, const double* G_all /*[2][N][N]*/, const int32_t* cl
       out[c * 4 + 3] += (dxy - G0[y * N + x]) + (dxy - G1[y * N + x]);
     }
   return ORC_OK;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* SU(2) charge decoupling with complex coupling (the paper's default         */
+/* Hubbard example, Sec. 6.1; the four-valued transform of Sec. 2.1 applied   */
+/* to exp(-dtau U/2 (n_i - 1)^2), n_i = n_i,up + n_i,dn, whose quadratic form */
+/* has the negative sign, hence the imaginary coupling):                      */
+/*   exp(-dtau U/2 (n_i - 1)^2) = sum_l gamma(l)/4 exp(i g eta(l) (n_i - 1))   */
+/*                                + O(dtau^4),   g = sqrt(dtau U / 2).        */
+/* Both spins (colors) see the same one-body propagator, so on fixed fields   */
+/*   B_tau = E exp(V_tau),  V_tau = diag(i g eta(l_tau,x)),  E = exp(-dtau K) */
+/*   weight = prod gamma(l)/4 * exp(-i g sum eta(l)) * det(1 + B(beta,0))^2.  */
+/* Plain product and complex LU with partial pivoting: valid for small        */
+/* beta * bandwidth (no stabilisation).  TEST INFRASTRUCTURE (next row).      */
+/* Outputs: G = (1 + B(beta,0))^-1 [N][N] complex (re, im interleaved),       */
+/* log|det(1+B)|, arg det(1+B), the phase -g sum eta(l), and the energy       */
+/* estimator per configuration (Wick, two colors):                            */
+/*   Kin = 2 sum_xy K_xy (delta_xy - G_yx)                                     */
+/*   Pot = U/2 sum_i <(n_i - 1)^2> = U/2 sum_i [2 (1-G_ii)^2 - 2 (1-G_ii) + 1] */
+/* energy[0..3] = Re Kin, Im Kin, Re Pot, Im Pot.                              */
+/* ------------------------------------------------------------------------ */
+int orc_su2_plain(int N, const double* K, double dtau, double U, int L, const int8_t* fields, double* G_out,
+                  double* logabs, double* arg, double* phase, double* energy) {
+  if (N < 1 || L < 1 || !(dtau > 0.0) || !(U >= 0.0)) return ORC_EINVAL;
+  for (int q = 0; q < L * N; ++q) {
+    const int l = fields[q];
+    if (l != 1 && l != -1 && l != 2 && l != -2) return ORC_EINVAL;
+  }
+  const size_t NN = (size_t)N * N;
+  double* E = dalloc(NN);
+  orc_expm_sym(N, K, -dtau, E);  /* exp(-dtau K) */
+  double complex* B = (double complex*)calloc(NN, sizeof(double complex));
+  double complex* T = (double complex*)calloc(NN, sizeof(double complex));
+  for (int x = 0; x < N; ++x) B[(size_t)x * N + x] = 1.0;
+  const double g = sqrt(0.5 * dtau * U);
+  double ph = 0.0;
+  /* B(beta,0) = B_L ... B_1: apply B_tau on the left for tau = 1..L */
+  for (int tau = 1; tau <= L; ++tau) {
+    for (int x = 0; x < N; ++x) {
+      const double th = g * hs_eta(fields[(size_t)(tau - 1) * N + x]);
+      ph -= th;
+      const double complex ev = cexp(_Complex_I * th);
+      for (int y = 0; y < N; ++y) B[(size_t)x * N + y] *= ev;
+    }
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) {
+        double complex acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += E[(size_t)x * N + k] * B[(size_t)k * N + y];
+        T[(size_t)x * N + y] = acc;
+      }
+    memcpy(B, T, NN * sizeof(double complex));
+  }
+  /* M = 1 + B; LU with partial pivoting; G = M^-1 column by column */
+  for (int x = 0; x < N; ++x) B[(size_t)x * N + x] += 1.0;
+  int* piv = (int*)malloc(sizeof(int) * N);
+  double la = 0.0, ar = 0.0;
+  int st = ORC_OK;
+  for (int k = 0; k < N && !st; ++k) {
+    int p = k;
+    for (int i = k + 1; i < N; ++i)
+      if (cabs(B[(size_t)i * N + k]) > cabs(B[(size_t)p * N + k])) p = i;
+    piv[k] = p;
+    if (cabs(B[(size_t)p * N + k]) == 0.0) { st = ORC_ESING; break; }
+    if (p != k) {
+      for (int j = 0; j < N; ++j) {
+        const double complex t = B[(size_t)k * N + j];
+        B[(size_t)k * N + j] = B[(size_t)p * N + j];
+        B[(size_t)p * N + j] = t;
+      }
+      ar += 3.14159265358979323846;
+    }
+    const double complex d = B[(size_t)k * N + k];
+    la += log(cabs(d));
+    ar += carg(d);
+    for (int i = k + 1; i < N; ++i) {
+      const double complex l = B[(size_t)i * N + k] / d;
+      B[(size_t)i * N + k] = l;
+      for (int j = k + 1; j < N; ++j) B[(size_t)i * N + j] -= l * B[(size_t)k * N + j];
+    }
+  }
+  if (!st) {
+    double complex* col = (double complex*)malloc(sizeof(double complex) * N);
+    double complex* G = (double complex*)malloc(sizeof(double complex) * NN);
+    for (int j = 0; j < N; ++j) {
+      for (int i = 0; i < N; ++i) col[i] = (i == j) ? 1.0 : 0.0;
+      for (int k = 0; k < N; ++k) {
+        const double complex t = col[k]; col[k] = col[piv[k]]; col[piv[k]] = t;
+      }
+      for (int i = 0; i < N; ++i)
+        for (int k = 0; k < i; ++k) col[i] -= B[(size_t)i * N + k] * col[k];
+      for (int i = N - 1; i >= 0; --i) {
+        for (int k = i + 1; k < N; ++k) col[i] -= B[(size_t)i * N + k] * col[k];
+        col[i] /= B[(size_t)i * N + i];
+      }
+      for (int i = 0; i < N; ++i) G[(size_t)i * N + j] = col[i];
+    }
+    double complex kin = 0.0, pot = 0.0;
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) kin += 2.0 * K[(size_t)x * N + y] * ((x == y ? 1.0 : 0.0) - G[(size_t)y * N + x]);
+    for (int i = 0; i < N; ++i) {
+      const double complex h = 1.0 - G[(size_t)i * N + i];
+      pot += 0.5 * U * (2.0 * h * h - 2.0 * h + 1.0);
+    }
+    for (size_t e = 0; e < NN; ++e) { G_out[2 * e] = creal(G[e]); G_out[2 * e + 1] = cimag(G[e]); }
+    *logabs = la;
+    *arg = remainder(ar, 2.0 * 3.14159265358979323846);
+    *phase = ph;
+    energy[0] = creal(kin); energy[1] = cimag(kin); energy[2] = creal(pot); energy[3] = cimag(pot);
+    free(col); free(G);
+  }
+  free(piv); free(E); free(B); free(T);
+  return st;
 }
