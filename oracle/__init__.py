@@ -99,6 +99,7 @@ def lib():
         _lib.orc_tau_observables.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp]
         _lib.orc_correlations.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp]
         _lib.orc_su2_plain.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+        _lib.orc_su2_sweep.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, vp, u64, u32, u64, vp, vp, vp]
         del i32
     return _lib
 
@@ -339,6 +340,29 @@ def su2_plain(K: np.ndarray, dtau: float, U: float, fields: np.ndarray):
     _check(lib().orc_su2_plain(N, _ptr(K), float(dtau), float(U), L, _ptr(f), _ptr(G), ctypes.byref(la),
                                ctypes.byref(ar), ctypes.byref(ph), _ptr(e)), "su2_plain")
     return G[..., 0] + 1j * G[..., 1], la.value, ar.value, ph.value, complex(e[0], e[1]), complex(e[2], e[3])
+
+
+class Su2Chain:
+    """A Markov chain of the SU(2) decoupling sampled with W = |Re e^{-S}| (plain
+    recomputes; small clusters only)."""
+
+    def __init__(self, K, dtau: float, U: float, fields, seed: int, chain: int):
+        self.K = np.ascontiguousarray(K, dtype=np.float64)
+        self.dtau, self.U = float(dtau), float(U)
+        self.fields = np.ascontiguousarray(fields, dtype=np.int8).copy()
+        self.L = self.fields.size // self.K.shape[0]
+        self.seed, self.chain, self.n_sweeps = int(seed), int(chain), 0
+        self.phase = np.zeros(2)
+
+    def sweep(self):
+        """One sweep; returns (sign * P / Re P * Ener (complex), sign, accepted)."""
+        obs = np.zeros(3)
+        acc = ctypes.c_int()
+        _check(lib().orc_su2_sweep(self.K.shape[0], _ptr(self.K), self.dtau, self.U, self.L, _ptr(self.fields),
+                                   self.seed, self.chain, self.n_sweeps, _ptr(self.phase), _ptr(obs),
+                                   ctypes.byref(acc)), "su2_sweep")
+        self.n_sweeps += 1
+        return complex(obs[0], obs[1]), obs[2], acc.value
 
 
 def szz_from_tau(obs: np.ndarray) -> np.ndarray:

@@ -1413,3 +1413,135 @@ int orc_su2_plain(int N, const double* K, double dtau, double U, int L, const in
   free(piv); free(E); free(B); free(T);
   return st;
 }
+
+/* G~ = (1 + e^{V_tau} B(tau-1,0) B(beta,tau) E)^-1 of the SU(2) decoupling at
+ * slice tau, from scratch (plain products): the Green function seen by the
+ * vertices of slice tau, whose change multiplies B_tau = E e^{V_tau} on the
+ * right of E.  Gt: [N][N] complex. */
+static int su2_green_at_vertex(int N, const double* E, double g, int L, const int8_t* fields, int tau,
+                               double complex* Gt) {
+  const size_t NN = (size_t)N * N;
+  double complex* A = (double complex*)calloc(NN, sizeof(double complex));
+  double complex* T = (double complex*)calloc(NN, sizeof(double complex));
+  for (int x = 0; x < N; ++x) A[(size_t)x * N + x] = 1.0;
+  /* A <- E, then left-multiply B_L ... B_tau+1, then B_tau-1 ... B_1, then e^{V_tau} */
+  for (int x = 0; x < N; ++x)
+    for (int y = 0; y < N; ++y) A[(size_t)x * N + y] = E[(size_t)x * N + y];
+  for (int step = 0; step < L - 1; ++step) {
+    const int t = (tau + 1 + step - 1) % L + 1;   /* tau+1, ..., L, 1, ..., tau-1 */
+    for (int x = 0; x < N; ++x) {
+      const double complex ev = cexp(_Complex_I * g * hs_eta(fields[(size_t)(t - 1) * N + x]));
+      for (int y = 0; y < N; ++y) A[(size_t)x * N + y] *= ev;
+    }
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) {
+        double complex acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += E[(size_t)x * N + k] * A[(size_t)k * N + y];
+        T[(size_t)x * N + y] = acc;
+      }
+    memcpy(A, T, NN * sizeof(double complex));
+  }
+  for (int x = 0; x < N; ++x) {
+    const double complex ev = cexp(_Complex_I * g * hs_eta(fields[(size_t)(tau - 1) * N + x]));
+    for (int y = 0; y < N; ++y) A[(size_t)x * N + y] *= ev;
+  }
+  /* Gt = (1 + A)^-1 by Gauss-Jordan with partial pivoting */
+  for (int x = 0; x < N; ++x) A[(size_t)x * N + x] += 1.0;
+  for (size_t e = 0; e < NN; ++e) Gt[e] = 0.0;
+  for (int x = 0; x < N; ++x) Gt[(size_t)x * N + x] = 1.0;
+  int st = ORC_OK;
+  for (int k = 0; k < N; ++k) {
+    int p = k;
+    for (int i = k + 1; i < N; ++i)
+      if (cabs(A[(size_t)i * N + k]) > cabs(A[(size_t)p * N + k])) p = i;
+    if (cabs(A[(size_t)p * N + k]) == 0.0) { st = ORC_ESING; break; }
+    for (int j = 0; j < N; ++j) {
+      double complex t = A[(size_t)k * N + j]; A[(size_t)k * N + j] = A[(size_t)p * N + j]; A[(size_t)p * N + j] = t;
+      t = Gt[(size_t)k * N + j]; Gt[(size_t)k * N + j] = Gt[(size_t)p * N + j]; Gt[(size_t)p * N + j] = t;
+    }
+    const double complex d = A[(size_t)k * N + k];
+    for (int j = 0; j < N; ++j) { A[(size_t)k * N + j] /= d; Gt[(size_t)k * N + j] /= d; }
+    for (int i = 0; i < N; ++i) {
+      if (i == k) continue;
+      const double complex f = A[(size_t)i * N + k];
+      for (int j = 0; j < N; ++j) {
+        A[(size_t)i * N + j] -= f * A[(size_t)k * N + j];
+        Gt[(size_t)i * N + j] -= f * Gt[(size_t)k * N + j];
+      }
+    }
+  }
+  free(A); free(T);
+  return st;
+}
+
+/* One sweep of a Markov chain of the SU(2) decoupling (the paper's sampling
+ * with complex weights: W(C) = |Re e^{-S(C)}| (Sec. 2.2), Metropolis on W).
+ * Order and random numbers as for the spin-z chains: up tau = 1..L with sites
+ * 0..N-1, down tau = L..1 with sites N-1..0; Philox counter (sweep_lo, 2 tau +
+ * dir, site, sweep_hi), key (seed_lo, seed_hi ^ chain); the proposal is one of
+ * the other three field values (ascending, index floor(3 u1)).  Per proposal,
+ * with Delta = e^{i g (eta' - eta)} - 1 and G~ from su2_green_at_vertex,
+ *   R = gamma(l')/gamma(l) * e^{-i g (eta' - eta)} * (1 + Delta (1 - G~_ii))^2,
+ * accepted when u2 < |Re(P R)| / |Re P|, P the phase of e^{-S(C)} (in/out as
+ * phase[0] + i phase[1]; on entry with phase[0] = phase[1] = 0 it is computed).
+ * After the sweep: energy estimator of the final configuration at tau = 0,
+ * reweighted as in Sec. 2.2: obs[0..1] = sign * (P / Re P) * (Kin + Pot)
+ * (re, im), obs[2] = sign.  accepted: number of accepted proposals. */
+int orc_su2_sweep(int N, const double* K, double dtau, double U, int L, int8_t* fields, uint64_t seed,
+                  uint32_t chain, uint64_t sweep, double* phase, double* obs, int* accepted) {
+  if (N < 1 || L < 1 || !(dtau > 0.0) || !(U >= 0.0)) return ORC_EINVAL;
+  const size_t NN = (size_t)N * N;
+  const double g = sqrt(0.5 * dtau * U);
+  double* E = dalloc(NN);
+  orc_expm_sym(N, K, -dtau, E);
+  double complex* Gt = (double complex*)malloc(NN * sizeof(double complex));
+  double* Gd = dalloc(2 * NN);
+  double la, ar, ph, en[4];
+  int st = ORC_OK;
+  double complex P = phase[0] + _Complex_I * phase[1];
+  if (phase[0] == 0.0 && phase[1] == 0.0) {
+    st = orc_su2_plain(N, K, dtau, U, L, fields, Gd, &la, &ar, &ph, en);
+    if (st) { free(E); free(Gt); free(Gd); return st; }
+    P = cexp(_Complex_I * (ph + 2.0 * ar));   /* prod gamma/4 > 0 and |det|^2 do not change the phase */
+  }
+  int acc = 0;
+  for (int dir = 0; dir < 2 && !st; ++dir) {
+    for (int step = 0; step < L && !st; ++step) {
+      const int tau = dir ? L - step : step + 1;
+      for (int q = 0; q < N; ++q) {
+        const int k = dir ? N - 1 - q : q;
+        double u1, u2;
+        proposal_uniforms(seed, chain, sweep, tau, dir, k, &u1, &u2);
+        const int f = fields[(size_t)(tau - 1) * N + k];
+        int others[3], n = 0;
+        const int all[4] = {-2, -1, 1, 2};
+        for (int a = 0; a < 4; ++a) if (all[a] != f) others[n++] = all[a];
+        int idx = (int)floor(3.0 * u1);
+        if (idx > 2) idx = 2;
+        const int fn = others[idx];
+        st = su2_green_at_vertex(N, E, g, L, fields, tau, Gt);
+        if (st) break;
+        const double dth = g * (hs_eta(fn) - hs_eta(f));
+        const double complex delta = cexp(_Complex_I * dth) - 1.0;
+        const double complex r1 = 1.0 + delta * (1.0 - Gt[(size_t)k * N + k]);
+        const double complex R = hs_gamma(fn) / hs_gamma(f) * cexp(-_Complex_I * dth) * r1 * r1;
+        const double ratio = fabs(creal(P * R)) / fabs(creal(P));
+        if (u2 < (ratio < 1.0 ? ratio : 1.0)) {
+          fields[(size_t)(tau - 1) * N + k] = (int8_t)fn;
+          P = P * R / cabs(P * R);
+          ++acc;
+        }
+      }
+    }
+  }
+  if (!st) st = orc_su2_plain(N, K, dtau, U, L, fields, Gd, &la, &ar, &ph, en);
+  if (!st) {
+    const double sgn = creal(P) >= 0.0 ? 1.0 : -1.0;
+    const double complex w = sgn * P / creal(P) * ((en[0] + _Complex_I * en[1]) + (en[2] + _Complex_I * en[3]));
+    obs[0] = creal(w); obs[1] = cimag(w); obs[2] = sgn;
+    phase[0] = creal(P); phase[1] = cimag(P);
+    *accepted = acc;
+  }
+  free(E); free(Gt); free(Gd);
+  return st;
+}

@@ -130,3 +130,20 @@ def equal_time_correlations(F, K, U, dtau, L, cls, n_class):
             for q, O in enumerate((szx @ szy, nx @ ny, spm, hop)):
                 out[c, q] += np.trace(O @ rho) / Z
     return out
+
+
+def su2_trotter(F, K, U, dtau, L, eta, gamma):
+    """Partition function and <H_T + U/2 sum_i (n_i - 1)^2> of the Trotter product
+    (exp(-dtau H_T) W)^L with the summed slice factor of the SU(2) charge
+    decoupling, W = prod_i sum_l gamma(l)/4 exp(i g eta(l) (n_i - 1)), g = sqrt(dtau U/2)."""
+    N = K.shape[0]
+    g = np.sqrt(0.5 * dtau * U)
+    Wd = np.ones(F.dim, dtype=complex)
+    for i in range(N):
+        ni = np.diag(F.n(0, i)) + np.diag(F.n(1, i))
+        Wd *= sum(gamma[l] / 4.0 * np.exp(1j * g * eta[l] * (ni - 1.0)) for l in (-2, -1, 1, 2))
+    rho = np.linalg.matrix_power(expm(-dtau * F.hopping(K)) @ np.diag(Wd), L)
+    I = np.eye(F.dim)
+    HU = sum(0.5 * U * (F.n(0, i) + F.n(1, i) - I) @ (F.n(0, i) + F.n(1, i) - I) for i in range(N))
+    Z = np.trace(rho)
+    return Z, np.trace((F.hopping(K) + HU) @ rho) / Z
