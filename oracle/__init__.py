@@ -100,6 +100,7 @@ def lib():
         _lib.orc_correlations.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp]
         _lib.orc_su2_plain.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         _lib.orc_su2_sweep.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, vp, u64, u32, u64, vp, vp, vp]
+        _lib.orc_su2_green_udv.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
         del i32
     return _lib
 
@@ -340,6 +341,20 @@ def su2_plain(K: np.ndarray, dtau: float, U: float, fields: np.ndarray):
     _check(lib().orc_su2_plain(N, _ptr(K), float(dtau), float(U), L, _ptr(f), _ptr(G), ctypes.byref(la),
                                ctypes.byref(ar), ctypes.byref(ph), _ptr(e)), "su2_plain")
     return G[..., 0] + 1j * G[..., 1], la.value, ar.value, ph.value, complex(e[0], e[1]), complex(e[2], e[3])
+
+
+def su2_green_udv(K: np.ndarray, dtau: float, U: float, n_wrap: int, fields: np.ndarray, tau: int = 0):
+    """G(tau) of one color of the SU(2) decoupling through the complex UDV chains:
+    (G complex [N, N], log|det(1 + B(beta,0))|, arg det(1 + B(beta,0)))."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    N = K.shape[0]
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    L = f.size // N
+    G = np.zeros((N, N, 2))
+    la, ar = ctypes.c_double(), ctypes.c_double()
+    _check(lib().orc_su2_green_udv(N, _ptr(K), float(dtau), float(U), L, int(n_wrap), _ptr(f), int(tau), _ptr(G),
+                                   ctypes.byref(la), ctypes.byref(ar)), "su2_green_udv")
+    return G[..., 0] + 1j * G[..., 1], la.value, ar.value
 
 
 class Su2Chain:

@@ -1545,3 +1545,208 @@ int orc_su2_sweep(int N, const double* K, double dtau, double U, int L, int8_t* 
   free(E); free(Gt); free(Gd);
   return st;
 }
+
+/* ---- complex UDV chain of the SU(2) decoupling (stable G at any beta) ----- */
+/* The steps of the real chain with complex arithmetic: Householder reflectors */
+/* H = 1 - 2 v v^H / (v^H v) (unitary, det -1), column pivoting on the norms,  */
+/* D = |diag R|, T = D^-1 R P^T T.  The left chain stores B(beta,tau)^H, so    */
+/*   1 + B(tau,0) B(beta,tau) = Q_R Db_R Mid Db_L Q_L^H,                        */
+/*   Mid = Db_R^-1 Q_R^H Q_L Db_L^-1 + Ds_R T_R T_L^H Ds_L,                     */
+/*   G = Q_L Db_L^-1 Mid^-1 Db_R^-1 Q_R^H,                                      */
+/*   det(1 + B) = det Q_R conj(det Q_L) prod Db_R prod Db_L det Mid.            */
+typedef struct { double complex *Q, *T; double* D; int detQ; } cudv_t;
+
+static void cudv_alloc(int N, cudv_t* u) {
+  u->Q = (double complex*)calloc((size_t)N * N, sizeof(double complex));
+  u->T = (double complex*)calloc((size_t)N * N, sizeof(double complex));
+  u->D = dalloc(N);
+  for (int i = 0; i < N; ++i) { u->Q[(size_t)i * N + i] = 1.0; u->T[(size_t)i * N + i] = 1.0; u->D[i] = 1.0; }
+  u->detQ = 1;
+}
+static void cudv_free(cudv_t* u) { free(u->Q); free(u->T); free(u->D); }
+
+static void cudv_finish(int N, double complex* X, cudv_t* u) {
+  const size_t NN = (size_t)N * N;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) X[(size_t)i * N + j] *= u->D[j];
+  int* perm = (int*)calloc(N, sizeof(int));
+  double complex* vs = (double complex*)calloc(NN, sizeof(double complex));
+  double* betas = dalloc(N);
+  int dq = 1;
+  for (int j = 0; j < N; ++j) perm[j] = j;
+  for (int k = 0; k < N; ++k) {
+    int p = k;
+    double best = -1.0;
+    for (int j = k; j < N; ++j) {
+      double s = 0.0;
+      for (int i = k; i < N; ++i) { const double a = cabs(X[(size_t)i * N + j]); s += a * a; }
+      if (s > best) { best = s; p = j; }
+    }
+    if (p != k) {
+      for (int i = 0; i < N; ++i) {
+        const double complex t = X[(size_t)i * N + k]; X[(size_t)i * N + k] = X[(size_t)i * N + p]; X[(size_t)i * N + p] = t;
+      }
+      const int t = perm[k]; perm[k] = perm[p]; perm[p] = t;
+    }
+    double nrm = 0.0;
+    for (int i = k; i < N; ++i) { const double a = cabs(X[(size_t)i * N + k]); nrm += a * a; }
+    nrm = sqrt(nrm);
+    betas[k] = 0.0;
+    if (nrm == 0.0) continue;
+    double complex* v = vs + (size_t)k * N;
+    const double complex x0 = X[(size_t)k * N + k];
+    const double complex alpha = (cabs(x0) > 0.0) ? -x0 / cabs(x0) * nrm : -nrm;
+    v[k] = x0 - alpha;
+    for (int i = k + 1; i < N; ++i) v[i] = X[(size_t)i * N + k];
+    double vhv = 0.0;
+    for (int i = k; i < N; ++i) { const double a = cabs(v[i]); vhv += a * a; }
+    if (vhv == 0.0) continue;
+    betas[k] = 2.0 / vhv;
+    dq = -dq;
+    for (int j = k; j < N; ++j) {
+      double complex s = 0.0;
+      for (int i = k; i < N; ++i) s += conj(v[i]) * X[(size_t)i * N + j];
+      s *= betas[k];
+      for (int i = k; i < N; ++i) X[(size_t)i * N + j] -= s * v[i];
+    }
+    X[(size_t)k * N + k] = alpha;
+    for (int i = k + 1; i < N; ++i) X[(size_t)i * N + k] = 0.0;
+  }
+  /* Q = H_0 ... H_{N-1} applied to the identity from the last reflector */
+  double complex* Qn = (double complex*)calloc(NN, sizeof(double complex));
+  for (int i = 0; i < N; ++i) Qn[(size_t)i * N + i] = 1.0;
+  for (int k = N - 1; k >= 0; --k) {
+    if (betas[k] == 0.0) continue;
+    const double complex* v = vs + (size_t)k * N;
+    for (int j = 0; j < N; ++j) {
+      double complex s = 0.0;
+      for (int i = k; i < N; ++i) s += conj(v[i]) * Qn[(size_t)i * N + j];
+      s *= betas[k];
+      for (int i = k; i < N; ++i) Qn[(size_t)i * N + j] -= s * v[i];
+    }
+  }
+  double* Dn = dalloc(N);
+  for (int k = 0; k < N; ++k) Dn[k] = cabs(X[(size_t)k * N + k]);
+  double complex* Tn = (double complex*)calloc(NN, sizeof(double complex));
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double complex acc = 0.0;
+      for (int k = i; k < N; ++k) acc += X[(size_t)i * N + k] * u->T[(size_t)perm[k] * N + j];
+      Tn[(size_t)i * N + j] = (Dn[i] > 0.0) ? acc / Dn[i] : 0.0;
+    }
+  memcpy(u->Q, Qn, NN * sizeof(double complex));
+  memcpy(u->T, Tn, NN * sizeof(double complex));
+  memcpy(u->D, Dn, (size_t)N * sizeof(double));
+  u->detQ = dq;
+  free(perm); free(vs); free(betas); free(Qn); free(Dn); free(Tn);
+}
+
+/* Right chain: X <- B_t X = E e^{i g eta} X for t = t1+1..t2.  Left chain:
+ * X <- B_t^H X = e^{-i g eta} E X for t = t2..t1+1. */
+static void cudv_step(int N, const double* E, double g, const int8_t* fields, int t1, int t2, int left,
+                      cudv_t* u) {
+  const size_t NN = (size_t)N * N;
+  double complex* X = (double complex*)malloc(NN * sizeof(double complex));
+  double complex* Y = (double complex*)malloc(NN * sizeof(double complex));
+  memcpy(X, u->Q, NN * sizeof(double complex));
+  for (int step = 0; step < t2 - t1; ++step) {
+    const int t = left ? t2 - step : t1 + 1 + step;
+    if (!left)
+      for (int x = 0; x < N; ++x) {
+        const double complex ev = cexp(_Complex_I * g * hs_eta(fields[(size_t)(t - 1) * N + x]));
+        for (int y = 0; y < N; ++y) X[(size_t)x * N + y] *= ev;
+      }
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) {
+        double complex acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += E[(size_t)x * N + k] * X[(size_t)k * N + y];
+        Y[(size_t)x * N + y] = acc;
+      }
+    memcpy(X, Y, NN * sizeof(double complex));
+    if (left)
+      for (int x = 0; x < N; ++x) {
+        const double complex ev = cexp(-_Complex_I * g * hs_eta(fields[(size_t)(t - 1) * N + x]));
+        for (int y = 0; y < N; ++y) X[(size_t)x * N + y] *= ev;
+      }
+  }
+  cudv_finish(N, X, u);
+  free(X); free(Y);
+}
+
+/* G(tau) of one color of the SU(2) decoupling through the complex UDV chains
+ * (chunks of n_wrap slices; a partial chunk closes each chain), with
+ * log|det(1 + B(beta,0))| and its argument.  G_out [N][N] complex (re, im). */
+int orc_su2_green_udv(int N, const double* K, double dtau, double U, int L, int n_wrap, const int8_t* fields,
+                      int tau, double* G_out, double* logabs, double* arg) {
+  if (N < 1 || L < 1 || n_wrap < 1 || tau < 0 || tau > L || !(dtau > 0.0) || !(U >= 0.0)) return ORC_EINVAL;
+  const size_t NN = (size_t)N * N;
+  const double g = sqrt(0.5 * dtau * U);
+  double* E = dalloc(NN);
+  orc_expm_sym(N, K, -dtau, E);
+  cudv_t R, Lf;
+  cudv_alloc(N, &R);
+  cudv_alloc(N, &Lf);
+  for (int t = 0; t < tau; t += n_wrap) cudv_step(N, E, g, fields, t, (t + n_wrap < tau) ? t + n_wrap : tau, 0, &R);
+  for (int t = L; t > tau; t -= n_wrap) cudv_step(N, E, g, fields, (t - n_wrap > tau) ? t - n_wrap : tau, t, 1, &Lf);
+  double complex* Mid = (double complex*)calloc(NN, sizeof(double complex));
+  double complex* X = (double complex*)calloc(NN, sizeof(double complex));
+  double *dbR = dalloc(N), *dsR = dalloc(N), *dbL = dalloc(N), *dsL = dalloc(N);
+  for (int i = 0; i < N; ++i) {
+    dbR[i] = R.D[i] > 1.0 ? R.D[i] : 1.0;  dsR[i] = R.D[i] > 1.0 ? 1.0 : R.D[i];
+    dbL[i] = Lf.D[i] > 1.0 ? Lf.D[i] : 1.0; dsL[i] = Lf.D[i] > 1.0 ? 1.0 : Lf.D[i];
+  }
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double complex qq = 0.0, tt = 0.0;
+      for (int k = 0; k < N; ++k) {
+        qq += conj(R.Q[(size_t)k * N + i]) * Lf.Q[(size_t)k * N + j];   /* Q_R^H Q_L */
+        tt += R.T[(size_t)i * N + k] * conj(Lf.T[(size_t)j * N + k]);   /* T_R T_L^H */
+      }
+      Mid[(size_t)i * N + j] = qq / (dbR[i] * dbL[j]) + dsR[i] * tt * dsL[j];
+      X[(size_t)i * N + j] = conj(R.Q[(size_t)j * N + i]) / dbR[i];    /* Db_R^-1 Q_R^H */
+    }
+  /* Gauss-Jordan: X <- Mid^-1 X, with the determinant of Mid */
+  double la = 0.0, ar = 0.0;
+  int st = ORC_OK;
+  for (int k = 0; k < N; ++k) {
+    int p = k;
+    for (int i = k + 1; i < N; ++i)
+      if (cabs(Mid[(size_t)i * N + k]) > cabs(Mid[(size_t)p * N + k])) p = i;
+    if (cabs(Mid[(size_t)p * N + k]) == 0.0) { st = ORC_ESING; break; }
+    if (p != k) {
+      for (int j = 0; j < N; ++j) {
+        double complex t = Mid[(size_t)k * N + j]; Mid[(size_t)k * N + j] = Mid[(size_t)p * N + j]; Mid[(size_t)p * N + j] = t;
+        t = X[(size_t)k * N + j]; X[(size_t)k * N + j] = X[(size_t)p * N + j]; X[(size_t)p * N + j] = t;
+      }
+      ar += 3.14159265358979323846;
+    }
+    const double complex d = Mid[(size_t)k * N + k];
+    la += log(cabs(d));
+    ar += carg(d);
+    for (int j = 0; j < N; ++j) { Mid[(size_t)k * N + j] /= d; X[(size_t)k * N + j] /= d; }
+    for (int i = 0; i < N; ++i) {
+      if (i == k) continue;
+      const double complex f = Mid[(size_t)i * N + k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < N; ++j) { Mid[(size_t)i * N + j] -= f * Mid[(size_t)k * N + j]; X[(size_t)i * N + j] -= f * X[(size_t)k * N + j]; }
+    }
+  }
+  if (!st) {
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) X[(size_t)i * N + j] /= dbL[i];
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        double complex acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += Lf.Q[(size_t)i * N + k] * X[(size_t)k * N + j];
+        G_out[2 * ((size_t)i * N + j)] = creal(acc);
+        G_out[2 * ((size_t)i * N + j) + 1] = cimag(acc);
+      }
+    for (int i = 0; i < N; ++i) la += log(dbR[i]) + log(dbL[i]);
+    if (R.detQ * Lf.detQ < 0) ar += 3.14159265358979323846;
+    *logabs = la;
+    *arg = remainder(ar, 2.0 * 3.14159265358979323846);
+  }
+  free(Mid); free(X); free(dbR); free(dsR); free(dbL); free(dsL); free(E);
+  cudv_free(&R); cudv_free(&Lf);
+  return st;
+}

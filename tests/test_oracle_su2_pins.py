@@ -9,6 +9,9 @@
 * At half filling on a bipartite lattice every configuration's weight is real
   and positive (no phase problem), away from it the weights are complex.
 * U = 0: G = (1 + exp(-beta K))^-1.
+* The complex UDV chain (orc_su2_green_udv) equals the plain product where both
+  hold (G, log|det|, arg det; G(tau) against the rotated field sequence) and is
+  independent of n_wrap at beta = 10.
 * The oracle's Markov chain, sampled with W = |Re e^{-S}| and reweighted by
   sign e^{-S} / Re e^{-S} (Sec. 2.2), reproduces the energy of the Trotter
   product within 4 sigma, at and away from half filling (the single-
@@ -91,3 +94,37 @@ def test_su2_sampler_matches_trotter_energy(orc, mu):
     mean_im, err_im = A.jackknife(os_.imag, ss)
     assert abs(mean_re - Ef.real) < 4 * err_re
     assert abs(mean_im) < 4 * err_im + 1e-12
+
+
+def _wrap_angle(a):
+    return (a + np.pi) % (2 * np.pi) - np.pi
+
+
+def test_su2_udv_chain_matches_plain_product(orc):
+    """The complex UDV chain (QR with pivoting, scale separation) against the plain
+    product where both hold (beta = 2): G, log|det| and arg det for several n_wrap,
+    and G(tau) against the plain product of the cyclically rotated fields."""
+    rng = np.random.default_rng(0)
+    K = W.square_lattice(4, 4, t=1.0, mu=0.2)
+    f = rng.choice([-2, -1, 1, 2], size=(20, 16)).astype(np.int8)
+    Gp, la, ar, _, _, _ = orc.su2_plain(K, 0.1, 4.0, f)
+    for nw in (1, 5, 20):
+        Gu, lu, au = orc.su2_green_udv(K, 0.1, 4.0, nw, f, 0)
+        assert np.abs(Gu - Gp).max() < 1e-12
+        assert lu == pytest.approx(la, rel=1e-12)
+        assert abs(_wrap_angle(au - ar)) < 1e-10
+    for tau in (3, 7, 20):
+        Gt, _, _ = orc.su2_green_udv(K, 0.1, 4.0, 5, f, tau)
+        rot = np.concatenate([f[tau:], f[:tau]])
+        Gr, _, _, _, _, _ = orc.su2_plain(K, 0.1, 4.0, rot)
+        assert np.abs(Gt - Gr).max() < 1e-12, tau
+
+
+def test_su2_udv_chain_is_independent_of_n_wrap_at_large_beta(orc):
+    rng = np.random.default_rng(1)
+    K = W.square_lattice(4, 4, t=1.0, mu=0.2)
+    f = rng.choice([-2, -1, 1, 2], size=(100, 16)).astype(np.int8)     # beta = 10
+    G5, l5, a5 = orc.su2_green_udv(K, 0.1, 4.0, 5, f, 0)
+    G10, l10, a10 = orc.su2_green_udv(K, 0.1, 4.0, 10, f, 0)
+    assert np.abs(G5 - G10).max() < 1e-10
+    assert l5 == pytest.approx(l10, rel=1e-12) and abs(_wrap_angle(a5 - a10)) < 1e-10
