@@ -85,6 +85,7 @@ def lib():
         _lib.orc_logdet.argtypes = [ctypes.c_int, vp, vp, vp]
         _lib.orc_green_plain.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         _lib.orc_green_udv.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        _lib.orc_green_udv_svd.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         _lib.orc_energy.argtypes = [vp, vp, vp]
         _lib.orc_chain_new.argtypes = [vp, vp, u64, u32, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         _lib.orc_chain_new.restype = vp
@@ -228,6 +229,12 @@ def green_plain(model: Model, fields: np.ndarray, flavor: int, tau: int = 0):
 def green_udv(model: Model, fields: np.ndarray, flavor: int, tau: int = 0):
     """G(tau) through the QR-stabilised UDV chains (chunks of n_wrap slices)."""
     return _green(lib().orc_green_udv, model, fields, flavor, tau)
+
+
+def green_udv_svd(model: Model, fields: np.ndarray, flavor: int, tau: int = 0):
+    """G(tau) through UDV chains decomposed by one-sided Jacobi SVD (the SVD
+    stabilisation option) instead of the pivoted QR."""
+    return _green(lib().orc_green_udv_svd, model, fields, flavor, tau)
 
 
 def energy(model: Model, G: np.ndarray) -> np.ndarray:

@@ -1750,3 +1750,96 @@ int orc_su2_green_udv(int N, const double* K, double dtau, double U, int L, int 
   cudv_free(&R); cudv_free(&Lf);
   return st;
 }
+
+/* ---- SVD stabilisation (the compile-time alternative of Sec. 5, -DSTAB1) -- */
+/* The same UDV chain with the decomposition M = X D = U S V^T by one-sided     */
+/* Jacobi rotations (Hestenes): column pairs of M are rotated until mutually    */
+/* orthogonal, S_j = |m_j|, U = M S^-1, and V accumulates the rotations; then   */
+/* Q = U, D = S, T = V^T T_old, det Q from an LU of U.  One-sided Jacobi keeps  */
+/* the relative accuracy of the small singular values of a column-scaled        */
+/* matrix, which is what the scale separation needs.                            */
+static void udv_finish_svd(int N, double* X, udv_t* u) {
+  const size_t NN = (size_t)N * N;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) X[i * N + j] *= u->D[j];
+  double* V = dalloc(NN);
+  mat_identity(N, V);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    int rotated = 0;
+    for (int p = 0; p < N - 1; ++p)
+      for (int q = p + 1; q < N; ++q) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int i = 0; i < N; ++i) {
+          a += X[i * N + p] * X[i * N + p];
+          b += X[i * N + q] * X[i * N + q];
+          c += X[i * N + p] * X[i * N + q];
+        }
+        if (c == 0.0 || fabs(c) <= 1e-15 * sqrt(a * b)) continue;
+        rotated = 1;
+        const double zeta = (b - a) / (2.0 * c);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int i = 0; i < N; ++i) {
+          const double xp = X[i * N + p], xq = X[i * N + q];
+          X[i * N + p] = cs * xp - sn * xq;
+          X[i * N + q] = sn * xp + cs * xq;
+          const double vp = V[i * N + p], vq = V[i * N + q];
+          V[i * N + p] = cs * vp - sn * vq;
+          V[i * N + q] = sn * vp + cs * vq;
+        }
+      }
+    if (!rotated) break;
+  }
+  double* S = dalloc(N);
+  for (int j = 0; j < N; ++j) {
+    double s2 = 0.0;
+    for (int i = 0; i < N; ++i) s2 += X[i * N + j] * X[i * N + j];
+    S[j] = sqrt(s2);
+    for (int i = 0; i < N; ++i) X[i * N + j] = (S[j] > 0.0) ? X[i * N + j] / S[j] : (i == j ? 1.0 : 0.0);
+  }
+  /* T' = V^T T */
+  double* Tn = dalloc(NN);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < N; ++k) acc += V[k * N + i] * u->T[k * N + j];
+      Tn[i * N + j] = acc;
+    }
+  double ld;
+  int sg;
+  orc_logdet(N, X, &ld, &sg);
+  memcpy(u->Q, X, NN * sizeof(double));
+  memcpy(u->T, Tn, NN * sizeof(double));
+  memcpy(u->D, S, (size_t)N * sizeof(double));
+  u->detQ = sg;
+  free(V); free(S); free(Tn);
+}
+
+/* G(tau) like orc_green_udv, every chain step decomposed by SVD. */
+int orc_green_udv_svd(const orc_model* m, const int8_t* fields, int s, int tau, double* G, double* logdet,
+                      int* sign) {
+  model_t M;
+  int st = model_load(m, &M);
+  if (st) return st;
+  if (s < 0 || s >= M.nfl || tau < 0 || tau > M.L) { model_free(&M); return ORC_EINVAL; }
+  const int N = M.N, nw = M.nw;
+  udv_t R, Lf;
+  udv_alloc(N, &R); udv_alloc(N, &Lf);
+  udv_identity(N, &R); udv_identity(N, &Lf);
+  double* X = dalloc((size_t)N * N);
+  for (int t = 0; t < tau; t += nw) {
+    memcpy(X, R.Q, sizeof(double) * N * N);
+    for (int u = t + 1; u <= ((t + nw < tau) ? t + nw : tau); ++u) apply_B_left(&M, fields, s, u, X);
+    udv_finish_svd(N, X, &R);
+  }
+  for (int t = M.L; t > tau; t -= nw) {
+    memcpy(X, Lf.Q, sizeof(double) * N * N);
+    for (int u = t; u >= ((t - nw > tau) ? t - nw : tau) + 1; --u) apply_BT_left(&M, fields, s, u, X);
+    udv_finish_svd(N, X, &Lf);
+  }
+  st = green_from_udv(N, &R, &Lf, G, logdet, sign);
+  free(X);
+  udv_free(&R); udv_free(&Lf);
+  model_free(&M);
+  return st;
+}
