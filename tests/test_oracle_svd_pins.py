@@ -1,7 +1,10 @@
 """Pins of the SVD-stabilised UDV chain (orc_green_udv_svd, the stabilisation
 option by singular value decomposition): G, log|det| and sign equal those of
 the column-pivoted QR chain at beta = 10 and U = 6, and the plain product at
-beta = 2 for an interior tau."""
+beta = 2 for an interior tau.  Two backward-stable routes to the same inverse
+agree to rounding times its conditioning, which grows with the size of G's
+entries (up to ~10 with the four-valued field at U = 6), so the comparison is
+relative to max(1, max|G|)."""
 import numpy as np
 import pytest
 
@@ -21,7 +24,7 @@ def test_svd_chain_equals_qr_chain_at_large_beta(orc, ft):
         for tau in (0, 37):
             Gq, lq, sq = orc.green_udv(om, f, s, tau)
             Gs, ls, ss = orc.green_udv_svd(om, f, s, tau)
-            assert np.abs(Gq - Gs).max() < 1e-10, (s, tau)
+            assert np.abs(Gq - Gs).max() < 1e-10 * max(1.0, np.abs(Gq).max()), (s, tau)
             assert ls == pytest.approx(lq, rel=1e-12) and ss == sq
 
 
