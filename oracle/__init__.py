@@ -101,6 +101,9 @@ def lib():
         _lib.orc_correlations.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp]
         _lib.orc_su2_plain.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         _lib.orc_su2_sweep.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, vp, u64, u32, u64, vp, vp, vp]
+        _lib.orc_hubbard_ising_plain.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, d, d, d, ctypes.c_int, vp, vp, vp,
+                                                  vp, vp, vp, vp]
+        _lib.orc_ising_bond_logweight.argtypes = [ctypes.c_int, ctypes.c_int, vp, d, d, d, ctypes.c_int, vp, vp]
         _lib.orc_su2_green_udv.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
         del i32
     return _lib
@@ -362,6 +365,37 @@ def su2_green_udv(K: np.ndarray, dtau: float, U: float, n_wrap: int, fields: np.
     _check(lib().orc_su2_green_udv(N, _ptr(K), float(dtau), float(U), L, int(n_wrap), _ptr(f), int(tau), _ptr(G),
                                    ctypes.byref(la), ctypes.byref(ar)), "su2_green_udv")
     return G[..., 0] + 1j * G[..., 1], la.value, ar.value
+
+
+def hubbard_ising_plain(T: np.ndarray, bonds, xi: float, dtau: float, U: float, hs: np.ndarray, ising: np.ndarray):
+    """SU(2) Hubbard model with an Ising field on bonds coupling to the hopping, on
+    fixed HS fields hs[L, N] and Ising spins ising[L, n_bonds]: (G complex,
+    log|det(1+B)|, arg det(1+B), HS phase, Kin complex) of one color."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    N = T.shape[0]
+    b = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+    bi, bj = np.ascontiguousarray(b[:, 0]), np.ascontiguousarray(b[:, 1])
+    f = np.ascontiguousarray(hs, dtype=np.int8)
+    z = np.ascontiguousarray(ising, dtype=np.int8)
+    L = f.size // N
+    G = np.zeros((N, N, 2))
+    la, ar, ph = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    kin = np.zeros(2)
+    _check(lib().orc_hubbard_ising_plain(N, _ptr(T), len(bi), _ptr(bi), _ptr(bj), float(xi), float(dtau), float(U), L,
+                                         _ptr(f), _ptr(z), _ptr(G), ctypes.byref(la), ctypes.byref(ar),
+                                         ctypes.byref(ph), _ptr(kin)), "hubbard_ising_plain")
+    return G[..., 0] + 1j * G[..., 1], la.value, ar.value, ph.value, complex(kin[0], kin[1])
+
+
+def ising_bond_logweight(ising: np.ndarray, dtau: float, h: float, J: float, pairs) -> float:
+    """log of the imaginary-time weight of the bond Ising spins ising[L, n_bonds]."""
+    z = np.ascontiguousarray(ising, dtype=np.int8)
+    L, nb = z.shape
+    p = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    lw = ctypes.c_double()
+    _check(lib().orc_ising_bond_logweight(nb, L, _ptr(z), float(dtau), float(h), float(J), len(p),
+                                          _ptr(p) if len(p) else None, ctypes.byref(lw)), "ising_bond_logweight")
+    return lw.value
 
 
 class Su2Chain:

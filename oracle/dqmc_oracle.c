@@ -1843,3 +1843,119 @@ int orc_green_udv_svd(const orc_model* m, const int8_t* fields, int s, int tau, 
   model_free(&M);
   return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* SU(2) Hubbard model coupled to a transverse Ising field on bonds (the     */
+/* second example model of Sec. 6, Hubbard-Ising on the square lattice).     */
+/* On fixed fields -- four-valued HS fields l[tau][x] of the charge          */
+/* decoupling and Ising spins s[tau][b] = +-1 in the Z basis -- the fermion  */
+/* propagator of one color is                                                */
+/*   B_tau = exp(-dtau T) X_0 X_1 ... X_{nb-1} exp(V_tau),                    */
+/*   X_b = exp(-dtau xi s_b O_b), O_b = |i><j| + |j><i| on bond b = (i, j),   */
+/*   V_tau = diag(i g eta(l_tau,x)), g = sqrt(dtau U / 2),                    */
+/* (the two-site type-1 operators of the bond terms: X_b acts on a 2 x 2     */
+/* block as cosh(a) 1 + sinh(a) O, a = -dtau xi s_b).  Plain product, small  */
+/* beta.  Outputs as orc_su2_plain; kin = 2 sum_xy T_xy (delta_xy - G_yx).    */
+/* ------------------------------------------------------------------------ */
+int orc_hubbard_ising_plain(int N, const double* T, int nb, const int32_t* bi, const int32_t* bj, double xi,
+                            double dtau, double U, int L, const int8_t* hs, const int8_t* sz, double* G_out,
+                            double* logabs, double* arg, double* phase, double* kin) {
+  if (N < 1 || L < 1 || nb < 0 || !(dtau > 0.0) || !(U >= 0.0)) return ORC_EINVAL;
+  for (int b = 0; b < nb; ++b)
+    if (bi[b] < 0 || bi[b] >= N || bj[b] < 0 || bj[b] >= N || bi[b] == bj[b]) return ORC_EINVAL;
+  const size_t NN = (size_t)N * N;
+  double* E = dalloc(NN);
+  orc_expm_sym(N, T, -dtau, E);
+  double complex* B = (double complex*)calloc(NN, sizeof(double complex));
+  double complex* Y = (double complex*)calloc(NN, sizeof(double complex));
+  for (int x = 0; x < N; ++x) B[(size_t)x * N + x] = 1.0;
+  const double g = sqrt(0.5 * dtau * U);
+  double ph = 0.0;
+  for (int tau = 1; tau <= L; ++tau) {
+    /* B <- exp(V_tau) B */
+    for (int x = 0; x < N; ++x) {
+      const double th = g * hs_eta(hs[(size_t)(tau - 1) * N + x]);
+      ph -= th;
+      const double complex ev = cexp(_Complex_I * th);
+      for (int y = 0; y < N; ++y) B[(size_t)x * N + y] *= ev;
+    }
+    /* B <- X_0 ... X_{nb-1} B: the last bond acts first */
+    for (int b = nb - 1; b >= 0; --b) {
+      const double a = -dtau * xi * (double)sz[(size_t)(tau - 1) * nb + b];
+      const double ch = cosh(a), sh = sinh(a);
+      const int i = bi[b], j = bj[b];
+      for (int y = 0; y < N; ++y) {
+        const double complex ri = B[(size_t)i * N + y], rj = B[(size_t)j * N + y];
+        B[(size_t)i * N + y] = ch * ri + sh * rj;
+        B[(size_t)j * N + y] = sh * ri + ch * rj;
+      }
+    }
+    /* B <- E B */
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) {
+        double complex acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += E[(size_t)x * N + k] * B[(size_t)k * N + y];
+        Y[(size_t)x * N + y] = acc;
+      }
+    memcpy(B, Y, NN * sizeof(double complex));
+  }
+  /* G = (1 + B)^-1 by Gauss-Jordan, with det(1 + B) */
+  for (int x = 0; x < N; ++x) B[(size_t)x * N + x] += 1.0;
+  double complex* G = (double complex*)calloc(NN, sizeof(double complex));
+  for (int x = 0; x < N; ++x) G[(size_t)x * N + x] = 1.0;
+  double la = 0.0, ar = 0.0;
+  int st = ORC_OK;
+  for (int k = 0; k < N; ++k) {
+    int p = k;
+    for (int i = k + 1; i < N; ++i)
+      if (cabs(B[(size_t)i * N + k]) > cabs(B[(size_t)p * N + k])) p = i;
+    if (cabs(B[(size_t)p * N + k]) == 0.0) { st = ORC_ESING; break; }
+    if (p != k) {
+      for (int j = 0; j < N; ++j) {
+        double complex t = B[(size_t)k * N + j]; B[(size_t)k * N + j] = B[(size_t)p * N + j]; B[(size_t)p * N + j] = t;
+        t = G[(size_t)k * N + j]; G[(size_t)k * N + j] = G[(size_t)p * N + j]; G[(size_t)p * N + j] = t;
+      }
+      ar += 3.14159265358979323846;
+    }
+    const double complex d = B[(size_t)k * N + k];
+    la += log(cabs(d));
+    ar += carg(d);
+    for (int j = 0; j < N; ++j) { B[(size_t)k * N + j] /= d; G[(size_t)k * N + j] /= d; }
+    for (int i = 0; i < N; ++i) {
+      if (i == k) continue;
+      const double complex f = B[(size_t)i * N + k];
+      for (int j = 0; j < N; ++j) { B[(size_t)i * N + j] -= f * B[(size_t)k * N + j]; G[(size_t)i * N + j] -= f * G[(size_t)k * N + j]; }
+    }
+  }
+  if (!st) {
+    double complex kn = 0.0;
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) kn += 2.0 * T[(size_t)x * N + y] * ((x == y ? 1.0 : 0.0) - G[(size_t)y * N + x]);
+    for (size_t e = 0; e < NN; ++e) { G_out[2 * e] = creal(G[e]); G_out[2 * e + 1] = cimag(G[e]); }
+    *logabs = la;
+    *arg = remainder(ar, 2.0 * 3.14159265358979323846);
+    *phase = ph;
+    kin[0] = creal(kn); kin[1] = cimag(kn);
+  }
+  free(E); free(B); free(Y); free(G);
+  return st;
+}
+
+/* Log weight of the Ising field on bonds in imaginary time (the S0 of the
+ * Ising terms -h sum X_b - J sum Z_b Z_b'): the transverse field between
+ * slices, <s'|exp(dtau h X)|s> = cosh(dtau h) (s' = s) or sinh(dtau h), for
+ * each bond and each pair of neighbouring slices (periodic in tau), and
+ * exp(dtau J sum_pairs s_b s_b') within each slice.  pairs: [n_pairs][2]. */
+int orc_ising_bond_logweight(int nb, int L, const int8_t* sz, double dtau, double h, double J, int n_pairs,
+                             const int32_t* pairs, double* logw) {
+  if (nb < 1 || L < 1 || !(dtau > 0.0) || !(h > 0.0)) return ORC_EINVAL;
+  double lw = 0.0;
+  for (int tau = 0; tau < L; ++tau) {
+    const int8_t* s = sz + (size_t)tau * nb;
+    const int8_t* sn = sz + (size_t)((tau + 1) % L) * nb;
+    for (int b = 0; b < nb; ++b) lw += (s[b] == sn[b]) ? log(cosh(dtau * h)) : log(sinh(dtau * h));
+    for (int q = 0; q < n_pairs; ++q) lw += dtau * J * (double)(s[pairs[2 * q]] * s[pairs[2 * q + 1]]);
+  }
+  *logw = lw;
+  return ORC_OK;
+}

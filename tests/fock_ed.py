@@ -147,3 +147,38 @@ def su2_trotter(F, K, U, dtau, L, eta, gamma):
     HU = sum(0.5 * U * (F.n(0, i) + F.n(1, i) - I) @ (F.n(0, i) + F.n(1, i) - I) for i in range(N))
     Z = np.trace(rho)
     return Z, np.trace((F.hopping(K) + HU) @ rho) / Z
+
+
+def hubbard_ising_trotter(F, K, U, dtau, L, eta, gamma, bonds, xi, h, J, pairs):
+    """Partition function and <H_T> of the Trotter product of the Hubbard model
+    coupled to Ising spins on bonds, on the product space Fock (x) Ising
+    (Ising basis state k: s_b = 1 - 2 bit_b(k)):
+      S = exp(-dtau H_T) prod_b exp(-dtau xi Z_b O_b) W exp(dtau J sum_pairs Z Z) prod_b exp(dtau h X_b),
+    O_b = sum_s (c^+_is c_js + h.c.), W the summed slice factor of the SU(2)
+    charge decoupling.  Returns (Tr S^L, Tr[H_T S^L] / Tr S^L)."""
+    N = K.shape[0]
+    nb = len(bonds)
+    dI = 2 ** nb
+    s = np.array([[1.0 - 2.0 * ((k >> b) & 1) for b in range(nb)] for k in range(dI)])   # [dI, nb]
+    If = np.eye(F.dim)
+    g = np.sqrt(0.5 * dtau * U)
+    Wd = np.ones(F.dim, dtype=complex)
+    for i in range(N):
+        ni = np.diag(F.n(0, i)) + np.diag(F.n(1, i))
+        Wd *= sum(gamma[l] / 4.0 * np.exp(1j * g * eta[l] * (ni - 1.0)) for l in (-2, -1, 1, 2))
+    S = np.kron(expm(-dtau * F.hopping(K)), np.eye(dI)).astype(complex)
+    for b, (i, j) in enumerate(bonds):
+        Ob = np.zeros((N, N))
+        Ob[i, j] = Ob[j, i] = 1.0
+        S = S @ expm(-dtau * xi * np.kron(F.hopping(Ob), np.diag(s[:, b])))
+    S = S @ np.kron(np.diag(Wd), np.eye(dI))
+    zz = np.array([sum(s[k, p] * s[k, q] for p, q in pairs) for k in range(dI)])
+    S = S @ np.kron(If, np.diag(np.exp(dtau * J * zz)))
+    for b in range(nb):
+        Xb = np.zeros((dI, dI))
+        for k in range(dI):
+            Xb[k ^ (1 << b), k] = 1.0
+        S = S @ np.kron(If, expm(dtau * h * Xb))
+    rho = np.linalg.matrix_power(S, L)
+    Z = np.trace(rho)
+    return Z, np.trace(np.kron(F.hopping(K), np.eye(dI)) @ rho) / Z

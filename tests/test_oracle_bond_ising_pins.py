@@ -1,0 +1,121 @@
+"""Pins of the oracle's Hubbard model coupled to a transverse Ising field on
+bonds (Sec. 6: the hopping on bond b gains xi Z_b, the bond spins carry a
+transverse field h and a coupling J between neighbouring bonds;
+orc_hubbard_ising_plain on fixed fields, orc_ising_bond_logweight for the
+bond spins' own weight).
+
+* Exact enumeration of all four-valued HS fields and bond spins of small
+  clusters, each weighted by prod gamma/4, the HS phase, det(1 + B)^2 and the
+  bond spins' weight, equals the trace of the Trotter product on Fock (x) Ising
+  space: the partition function and <H_T>.  Three open sites (two bonds that
+  share a site) with U > 0 over two slices and at U = 0 over four slices, and
+  two sites with U > 0 over three slices, at and away from half filling.
+* The bond spins' weight alone: one bond, J = 0, sums to the transverse-field
+  Ising chain's closed form 2 cosh(L dtau h); two bonds with J reproduce the
+  transfer-matrix trace.
+* xi = 0 decouples: the fermion part equals the SU(2) Hubbard oracle.
+* At half filling on the bipartite chain every weight is real and positive.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_1704_00131_gb300 import workloads as W
+
+from .fock_ed import Fock, hubbard_ising_trotter
+
+
+def enumerate_model(orc, K, U, dtau, L, bonds, xi, h, J, pairs, hs_values):
+    N, nb = K.shape[0], len(bonds)
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+    Z, KZ, weights = 0.0, 0.0, []
+    for zs in itertools.product((-1, 1), repeat=nb * L):
+        z = np.array(zs, dtype=np.int8).reshape(L, nb)
+        wz = math.exp(orc.ising_bond_logweight(z, dtau, h, J, pairs))
+        for ls in itertools.product(hs_values, repeat=N * L):
+            f = np.array(ls, dtype=np.int8).reshape(L, N)
+            _, la, ar, ph, kin = orc.hubbard_ising_plain(K, bonds, xi, dtau, U, f, z)
+            w = wz * np.prod([gam[l] / 4.0 for l in ls]) * np.exp(1j * ph) * np.exp(2.0 * (la + 1j * ar))
+            weights.append(w)
+            Z += w
+            KZ += w * kin
+    return Z, KZ / Z, np.array(weights)
+
+
+def reference(orc, K, U, dtau, L, bonds, xi, h, J, pairs):
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+    return hubbard_ising_trotter(Fock(K.shape[0]), K, U, dtau, L, eta, gam, bonds, xi, h, J, pairs)
+
+
+def test_enumeration_equals_trotter_trace_two_bonds_interacting(orc):
+    # two bonds through site 1 with U > 0 on a chain without reflection symmetry:
+    # the order of the bond factors within a slice, relative to the HS factor and
+    # exp(-dtau T), changes Z and <H_T> (at U = 0, or on the symmetric chain, it
+    # does not: transposing the product or reflecting the chain reverses it)
+    K, U, dtau, L = W.chain_lattice(3, t=1.0, mu=0.25), 2.5, 0.3, 2
+    K[0, 0] -= 0.5
+    K[1, 2] = K[2, 1] = -0.8
+    bonds, pairs = [(0, 1), (1, 2)], [(0, 1)]
+    xi, h, J = 0.8, 0.7, 0.5
+    Z, kin, _ = enumerate_model(orc, K, U, dtau, L, bonds, xi, h, J, pairs, (-2, -1, 1, 2))
+    Zf, kf = reference(orc, K, U, dtau, L, bonds, xi, h, J, pairs)
+    assert Z == pytest.approx(Zf, rel=1e-11)
+    assert kin == pytest.approx(kf, rel=1e-10, abs=1e-12)
+
+
+def test_enumeration_equals_trotter_trace_two_bonds_free_fermions(orc):
+    # at U = 0 the HS field drops out (sum gamma / 4 = 1): one field value with weight 4^(N L)
+    K, dtau, L = W.chain_lattice(3, t=1.0, mu=0.3), 0.2, 4
+    bonds, pairs = [(0, 1), (1, 2)], [(0, 1)]
+    xi, h, J = 0.7, 0.9, 0.4
+    Z, kin, _ = enumerate_model(orc, K, 0.0, dtau, L, bonds, xi, h, J, pairs, (1,))
+    g1 = orc.field_gamma(2, 1) / 4.0
+    Z /= g1 ** (3 * L)
+    Zf, kf = reference(orc, K, 0.0, dtau, L, bonds, xi, h, J, pairs)
+    assert Z == pytest.approx(Zf, rel=1e-11)
+    assert kin == pytest.approx(kf, rel=1e-10, abs=1e-12)
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.35])
+def test_enumeration_equals_trotter_trace_interacting(orc, mu):
+    K, U, dtau, L = W.chain_lattice(2, t=1.0, mu=mu), 3.0, 0.25, 3
+    bonds, pairs = [(0, 1)], []
+    xi, h, J = 0.6, 0.8, 0.0
+    Z, kin, w = enumerate_model(orc, K, U, dtau, L, bonds, xi, h, J, pairs, (-2, -1, 1, 2))
+    Zf, kf = reference(orc, K, U, dtau, L, bonds, xi, h, J, pairs)
+    assert Z == pytest.approx(Zf, rel=1e-11)
+    assert abs(Z.imag) < 1e-11 * abs(Z)
+    assert kin == pytest.approx(kf, rel=1e-10, abs=1e-12)
+    if mu == 0.0:
+        assert np.abs(w.imag).max() < 1e-12 * np.abs(w).max() and (w.real > 0).all()
+    else:
+        assert np.abs(w.imag).max() > 1e-6 * np.abs(w).max()
+
+
+def test_bond_spin_weight_closed_forms(orc):
+    dtau, h, L = 0.15, 1.3, 5
+    tot = sum(math.exp(orc.ising_bond_logweight(np.array(z, dtype=np.int8).reshape(L, 1), dtau, h, 0.0, []))
+              for z in itertools.product((-1, 1), repeat=L))
+    assert tot == pytest.approx(2.0 * math.cosh(L * dtau * h), rel=1e-13)
+    # two coupled bonds: trace of the transfer matrix exp(dtau J Z Z) exp(dtau h (X_0 + X_1))
+    J, L = 0.7, 3
+    tot = sum(math.exp(orc.ising_bond_logweight(np.array(z, dtype=np.int8).reshape(L, 2), dtau, h, J, [(0, 1)]))
+              for z in itertools.product((-1, 1), repeat=2 * L))
+    X = np.array([[math.cosh(dtau * h), math.sinh(dtau * h)], [math.sinh(dtau * h), math.cosh(dtau * h)]])
+    D = np.diag([math.exp(dtau * J), math.exp(-dtau * J), math.exp(-dtau * J), math.exp(dtau * J)])
+    T = D @ np.kron(X, X)
+    assert tot == pytest.approx(np.trace(np.linalg.matrix_power(T, L)), rel=1e-13)
+
+
+def test_zero_coupling_reduces_to_su2_hubbard(orc):
+    K, U, dtau, L = W.square_lattice(2, 2, t=1.0, mu=0.2), 4.0, 0.1, 6
+    rng = np.random.default_rng(5)
+    f = rng.choice(np.array([-2, -1, 1, 2], dtype=np.int8), size=(L, 4))
+    z = rng.choice(np.array([-1, 1], dtype=np.int8), size=(L, 4))
+    G, la, ar, ph, kin = orc.hubbard_ising_plain(K, [(0, 1), (2, 3), (0, 2), (1, 3)], 0.0, dtau, U, f, z)
+    G2, la2, ar2, ph2, kin2, _ = orc.su2_plain(K, dtau, U, f.ravel())
+    assert np.abs(G - G2).max() < 1e-13 and la == pytest.approx(la2, rel=1e-13)
+    assert ar == pytest.approx(ar2, abs=1e-12) and ph == ph2 and kin == pytest.approx(kin2, rel=1e-12)
