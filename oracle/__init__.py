@@ -104,6 +104,11 @@ def lib():
         _lib.orc_hubbard_ising_plain.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, d, d, d, ctypes.c_int, vp, vp, vp,
                                                   vp, vp, vp, vp]
         _lib.orc_ising_bond_logweight.argtypes = [ctypes.c_int, ctypes.c_int, vp, d, d, d, ctypes.c_int, vp, vp]
+        _lib.orc_hubbard_ising_green_at.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, d, d, d, ctypes.c_int, vp,
+                                                     vp, ctypes.c_int, ctypes.c_int, vp]
+        _lib.orc_bond_rank2_update.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+        _lib.orc_hubbard_ising_sweep.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, d, d, d, ctypes.c_int, vp, d, d,
+                                                 ctypes.c_int, vp, vp, u64, u32, u64, vp, vp, vp]
         _lib.orc_su2_green_udv.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
         del i32
     return _lib
@@ -396,6 +401,68 @@ def ising_bond_logweight(ising: np.ndarray, dtau: float, h: float, J: float, pai
     _check(lib().orc_ising_bond_logweight(nb, L, _ptr(z), float(dtau), float(h), float(J), len(p),
                                           _ptr(p) if len(p) else None, ctypes.byref(lw)), "ising_bond_logweight")
     return lw.value
+
+
+def _bond_arrays(bonds):
+    b = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+    return np.ascontiguousarray(b[:, 0]), np.ascontiguousarray(b[:, 1])
+
+
+def hubbard_ising_green_at(T: np.ndarray, bonds, xi: float, dtau: float, U: float, hs: np.ndarray,
+                           ising: np.ndarray, tau: int, part: int) -> np.ndarray:
+    """Green function (complex [N, N]) seen by the factor (tau, part) of the bond
+    model: part 0 = the HS factor of slice tau, 1..n_bonds = bonds n_bonds-1..0,
+    n_bonds+1 = exp(-dtau T)."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    N = T.shape[0]
+    bi, bj = _bond_arrays(bonds)
+    f = np.ascontiguousarray(hs, dtype=np.int8)
+    z = np.ascontiguousarray(ising, dtype=np.int8)
+    G = np.zeros((N, N, 2))
+    _check(lib().orc_hubbard_ising_green_at(N, _ptr(T), len(bi), _ptr(bi), _ptr(bj), float(xi), float(dtau),
+                                            float(U), f.size // N, _ptr(f), _ptr(z), int(tau), int(part), _ptr(G)),
+           "hubbard_ising_green_at")
+    return G[..., 0] + 1j * G[..., 1]
+
+
+def bond_rank2_update(G: np.ndarray, i: int, j: int, delta: np.ndarray):
+    """(G', det ratio) of the rank-2 change (1 + Delta) on the rows/columns {i, j}."""
+    N = G.shape[0]
+    Gi = np.ascontiguousarray(np.stack([G.real, G.imag], axis=-1), dtype=np.float64)
+    d = np.asarray(delta, dtype=complex)
+    dd = np.ascontiguousarray(np.stack([d.real, d.imag], axis=-1), dtype=np.float64)
+    r = np.zeros(2)
+    _check(lib().orc_bond_rank2_update(N, _ptr(Gi), int(i), int(j), _ptr(dd), _ptr(r)), "bond_rank2_update")
+    return Gi[..., 0] + 1j * Gi[..., 1], complex(r[0], r[1])
+
+
+class HubbardIsingChain:
+    """A Markov chain of the Hubbard-Ising bond model (HS fields and bond spins),
+    sampled with W = |Re e^{-S}| (plain recomputes; small clusters only)."""
+
+    def __init__(self, T, bonds, xi, h, J, pairs, dtau, U, hs, ising, seed: int, chain: int):
+        self.T = np.ascontiguousarray(T, dtype=np.float64)
+        self.bi, self.bj = _bond_arrays(bonds)
+        self.xi, self.h, self.J = float(xi), float(h), float(J)
+        self.pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        self.dtau, self.U = float(dtau), float(U)
+        self.hs = np.ascontiguousarray(hs, dtype=np.int8).copy()
+        self.ising = np.ascontiguousarray(ising, dtype=np.int8).copy()
+        self.L = self.hs.size // self.T.shape[0]
+        self.seed, self.chain, self.n_sweeps = int(seed), int(chain), 0
+        self.phase = np.zeros(2)
+
+    def sweep(self):
+        """One sweep; returns (reweighted Kin, sign, reweighted (sum_b s_b)^2 / n_bonds, accepted)."""
+        obs = np.zeros(5)
+        acc = ctypes.c_int()
+        _check(lib().orc_hubbard_ising_sweep(self.T.shape[0], _ptr(self.T), len(self.bi), _ptr(self.bi),
+                                             _ptr(self.bj), self.xi, self.h, self.J, len(self.pairs),
+                                             _ptr(self.pairs) if len(self.pairs) else None, self.dtau, self.U, self.L,
+                                             _ptr(self.hs), _ptr(self.ising), self.seed, self.chain, self.n_sweeps,
+                                             _ptr(self.phase), _ptr(obs), ctypes.byref(acc)), "hubbard_ising_sweep")
+        self.n_sweeps += 1
+        return complex(obs[0], obs[1]), obs[2], complex(obs[3], obs[4]), acc.value
 
 
 class Su2Chain:

@@ -1959,3 +1959,279 @@ int orc_ising_bond_logweight(int nb, int L, const int8_t* sz, double dtau, doubl
   *logw = lw;
   return ORC_OK;
 }
+
+/* ---- Markov chain of the Hubbard-Ising bond model (rank-2 bond updates) --- */
+/* The propagator of orc_hubbard_ising_plain as a cyclic list of elementary    */
+/* factors in the order they act: per slice tau = 1..L, part 0 = exp(V_tau)     */
+/* (all HS sites, diagonal), parts 1..nb = the bond factors X_{nb-1}, ..., X_0, */
+/* part nb+1 = exp(-dtau T).  The Green function seen by a vertex is the one    */
+/* just after its factor acted:                                                */
+/*   G~ = (1 + F_p F_{p-1} ... F_0 F_{n-1} ... F_{p+1})^-1,                      */
+/* so that changing F_p -> (1 + Delta) F_p multiplies det(1 + B) by            */
+/* det(1 + Delta (1 - G~)), restricted to the rows Delta touches.              */
+typedef struct {
+  int N, nb, L;
+  const int32_t *bi, *bj;
+  const double* E;
+  double g, a0; /* HS coupling sqrt(dtau U / 2); bond coupling -dtau xi */
+  const int8_t *hs, *sz;
+} hi_model_t;
+
+/* A <- F A for the factor of slice tau (1-based), part p. */
+static void hi_apply_factor(const hi_model_t* m, int tau, int part, double complex* A, double complex* T) {
+  const int N = m->N;
+  if (part == 0) {
+    for (int x = 0; x < N; ++x) {
+      const double complex ev = cexp(_Complex_I * m->g * hs_eta(m->hs[(size_t)(tau - 1) * N + x]));
+      for (int y = 0; y < N; ++y) A[(size_t)x * N + y] *= ev;
+    }
+  } else if (part <= m->nb) {
+    const int b = m->nb - part;
+    const double a = m->a0 * (double)m->sz[(size_t)(tau - 1) * m->nb + b];
+    const double ch = cosh(a), sh = sinh(a);
+    const int i = m->bi[b], j = m->bj[b];
+    for (int y = 0; y < N; ++y) {
+      const double complex ri = A[(size_t)i * N + y], rj = A[(size_t)j * N + y];
+      A[(size_t)i * N + y] = ch * ri + sh * rj;
+      A[(size_t)j * N + y] = sh * ri + ch * rj;
+    }
+  } else {
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) {
+        double complex acc = 0.0;
+        for (int k = 0; k < N; ++k) acc += m->E[(size_t)x * N + k] * A[(size_t)k * N + y];
+        T[(size_t)x * N + y] = acc;
+      }
+    memcpy(A, T, (size_t)N * N * sizeof(double complex));
+  }
+}
+
+/* G = (1 + A)^-1 by Gauss-Jordan with partial pivoting (A is destroyed). */
+static int c_inverse_one_plus(int N, double complex* A, double complex* G) {
+  for (int x = 0; x < N; ++x) A[(size_t)x * N + x] += 1.0;
+  for (size_t e = 0; e < (size_t)N * N; ++e) G[e] = 0.0;
+  for (int x = 0; x < N; ++x) G[(size_t)x * N + x] = 1.0;
+  for (int k = 0; k < N; ++k) {
+    int p = k;
+    for (int i = k + 1; i < N; ++i)
+      if (cabs(A[(size_t)i * N + k]) > cabs(A[(size_t)p * N + k])) p = i;
+    if (cabs(A[(size_t)p * N + k]) == 0.0) return ORC_ESING;
+    for (int j = 0; j < N; ++j) {
+      double complex t = A[(size_t)k * N + j]; A[(size_t)k * N + j] = A[(size_t)p * N + j]; A[(size_t)p * N + j] = t;
+      t = G[(size_t)k * N + j]; G[(size_t)k * N + j] = G[(size_t)p * N + j]; G[(size_t)p * N + j] = t;
+    }
+    const double complex d = A[(size_t)k * N + k];
+    for (int j = 0; j < N; ++j) { A[(size_t)k * N + j] /= d; G[(size_t)k * N + j] /= d; }
+    for (int i = 0; i < N; ++i) {
+      if (i == k) continue;
+      const double complex f = A[(size_t)i * N + k];
+      for (int j = 0; j < N; ++j) { A[(size_t)i * N + j] -= f * A[(size_t)k * N + j]; G[(size_t)i * N + j] -= f * G[(size_t)k * N + j]; }
+    }
+  }
+  return ORC_OK;
+}
+
+static int hi_green_at(const hi_model_t* m, int tau, int part, double complex* G) {
+  const int N = m->N, P = m->nb + 2, nF = m->L * P;
+  const size_t NN = (size_t)N * N;
+  double complex* A = (double complex*)calloc(NN, sizeof(double complex));
+  double complex* T = (double complex*)calloc(NN, sizeof(double complex));
+  for (int x = 0; x < N; ++x) A[(size_t)x * N + x] = 1.0;
+  const int f = (tau - 1) * P + part;
+  for (int step = 1; step <= nF; ++step) {
+    const int idx = (f + step) % nF;
+    hi_apply_factor(m, idx / P + 1, idx % P, A, T);
+  }
+  const int st = c_inverse_one_plus(N, A, G);
+  free(A); free(T);
+  return st;
+}
+
+static int hi_model_init(hi_model_t* m, int N, const double* T, int nb, const int32_t* bi, const int32_t* bj,
+                         double xi, double dtau, double U, int L, const int8_t* hs, const int8_t* sz) {
+  if (N < 1 || L < 1 || nb < 0 || !(dtau > 0.0) || !(U >= 0.0)) return ORC_EINVAL;
+  for (int b = 0; b < nb; ++b)
+    if (bi[b] < 0 || bi[b] >= N || bj[b] < 0 || bj[b] >= N || bi[b] == bj[b]) return ORC_EINVAL;
+  double* E = dalloc((size_t)N * N);
+  orc_expm_sym(N, T, -dtau, E);
+  m->N = N; m->nb = nb; m->L = L; m->bi = bi; m->bj = bj; m->E = E;
+  m->g = sqrt(0.5 * dtau * U); m->a0 = -dtau * xi; m->hs = hs; m->sz = sz;
+  return ORC_OK;
+}
+
+/* The Green function seen by the factor (tau, part) of the bond model, from
+ * scratch (plain products).  G_out: [N][N] complex (re, im interleaved). */
+int orc_hubbard_ising_green_at(int N, const double* T, int nb, const int32_t* bi, const int32_t* bj, double xi,
+                               double dtau, double U, int L, const int8_t* hs, const int8_t* sz, int tau, int part,
+                               double* G_out) {
+  if (tau < 1 || tau > L || part < 0 || part > nb + 1) return ORC_EINVAL;
+  hi_model_t m;
+  int st = hi_model_init(&m, N, T, nb, bi, bj, xi, dtau, U, L, hs, sz);
+  if (st) return st;
+  double complex* G = (double complex*)malloc((size_t)N * N * sizeof(double complex));
+  st = hi_green_at(&m, tau, part, G);
+  if (!st)
+    for (size_t e = 0; e < (size_t)N * N; ++e) { G_out[2 * e] = creal(G[e]); G_out[2 * e + 1] = cimag(G[e]); }
+  free(G); free((void*)m.E);
+  return st;
+}
+
+/* Rank-2 update of G~ when the factor seen by G~ changes by F -> (1 + Delta) F,
+ * Delta nonzero only on the rows and columns {i, j} (the 2 x 2 block delta):
+ * with (1 - G~)_PP the 2 x 2 block of 1 - G~ on {i, j} and (1 - G~)_P: its rows,
+ *   ratio = det(1 + delta (1 - G~)_PP),
+ *   G~' = G~ - G~_:P (1 + delta (1 - G~)_PP)^-1 delta (1 - G~)_P:
+ * (Woodbury, with B (1 + B)^-1 = 1 - G~).  G: [N][N] complex in/out, delta:
+ * 2 x 2 complex (re, im interleaved), ratio: re, im. */
+int orc_bond_rank2_update(int N, double* G, int i, int j, const double* delta, double* ratio) {
+  if (N < 2 || i < 0 || j < 0 || i >= N || j >= N || i == j) return ORC_EINVAL;
+  const int P[2] = {i, j};
+  double complex d[4], h[4], S[4], Si[4];
+  for (int e = 0; e < 4; ++e) d[e] = delta[2 * e] + _Complex_I * delta[2 * e + 1];
+#define GC(x, y) (G[2 * ((size_t)(x) * N + (y))] + _Complex_I * G[2 * ((size_t)(x) * N + (y)) + 1])
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) h[2 * a + b] = (a == b ? 1.0 : 0.0) - GC(P[a], P[b]);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) S[2 * a + b] = (a == b ? 1.0 : 0.0) + d[2 * a] * h[b] + d[2 * a + 1] * h[2 + b];
+  const double complex det = S[0] * S[3] - S[1] * S[2];
+  ratio[0] = creal(det); ratio[1] = cimag(det);
+  if (cabs(det) == 0.0) return ORC_ESING;
+  Si[0] = S[3] / det; Si[1] = -S[1] / det; Si[2] = -S[2] / det; Si[3] = S[0] / det;
+  /* W = S^-1 delta (2 x 2); rows of (1 - G~) on P: R[a][y] = delta_{P_a y} - G~_{P_a y} */
+  double complex Wm[4];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) Wm[2 * a + b] = Si[2 * a] * d[b] + Si[2 * a + 1] * d[2 + b];
+  double complex* R = (double complex*)malloc(2 * (size_t)N * sizeof(double complex));
+  double complex* C = (double complex*)malloc(2 * (size_t)N * sizeof(double complex));
+  for (int a = 0; a < 2; ++a)
+    for (int y = 0; y < N; ++y) {
+      R[(size_t)a * N + y] = (P[a] == y ? 1.0 : 0.0) - GC(P[a], y);
+      C[(size_t)a * N + y] = GC(y, P[a]);   /* column P_a of G~, stored as a row */
+    }
+  for (int x = 0; x < N; ++x)
+    for (int y = 0; y < N; ++y) {
+      double complex acc = 0.0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) acc += C[(size_t)a * N + x] * Wm[2 * a + b] * R[(size_t)b * N + y];
+      const size_t e = (size_t)x * N + y;
+      G[2 * e] -= creal(acc);
+      G[2 * e + 1] -= cimag(acc);
+    }
+#undef GC
+  free(R); free(C);
+  return ORC_OK;
+}
+
+/* One sweep of a Markov chain of the bond model: the four-valued HS fields and
+ * the bond Ising spins are both updated, with W(C) = |Re e^{-S(C)}| (Sec. 2.2)
+ * including the bond spins' own weight (the ratio S0 of Sec. 6 on a flip).
+ * Order: up tau = 1..L, within a slice the factors in the order they act
+ * (sites 0..N-1, then bonds nb-1..0); down tau = L..1 in the reverse order.
+ * Random numbers as orc_su2_sweep, vertex index x for site x and N + b for
+ * bond b (a bond proposal is the flip s -> -s and uses u2 only).  Ratios, G~
+ * recomputed from scratch at each vertex:
+ *   site:  gamma(l')/gamma(l) e^{-i g (eta'-eta)} (1 + Delta (1 - G~_xx))^2
+ *   bond:  det(1 + delta (1 - G~)_PP)^2 * e^{logw(s') - logw(s)},
+ *          delta = X_b(-2a) - 1 on the bond's 2 x 2 block, a = -dtau xi s_b.
+ * After the sweep, with sign and P as orc_su2_sweep: obs[0..1] = reweighted
+ * Kin (re, im), obs[2] = sign, obs[3..4] = reweighted (sum_b s_b)^2 / nb
+ * averaged over slices (re, im). */
+int orc_hubbard_ising_sweep(int N, const double* T, int nb, const int32_t* bi, const int32_t* bj, double xi, double h,
+                            double J, int n_pairs, const int32_t* pairs, double dtau, double U, int L, int8_t* hs,
+                            int8_t* sz, uint64_t seed, uint32_t chain, uint64_t sweep, double* phase, double* obs,
+                            int* accepted) {
+  if (nb < 1 || !(h > 0.0)) return ORC_EINVAL;
+  hi_model_t m;
+  int st = hi_model_init(&m, N, T, nb, bi, bj, xi, dtau, U, L, hs, sz);
+  if (st) return st;
+  const size_t NN = (size_t)N * N;
+  double complex* Gt = (double complex*)malloc(NN * sizeof(double complex));
+  double* Gd = dalloc(2 * NN);
+  double la, ar, ph, kin[2];
+  double complex P = phase[0] + _Complex_I * phase[1];
+  if (phase[0] == 0.0 && phase[1] == 0.0) {
+    st = orc_hubbard_ising_plain(N, T, nb, bi, bj, xi, dtau, U, L, hs, sz, Gd, &la, &ar, &ph, kin);
+    P = cexp(_Complex_I * (ph + 2.0 * ar));
+  }
+  int acc = 0;
+  const int nv = N + nb;
+  for (int dir = 0; dir < 2 && !st; ++dir) {
+    for (int step = 0; step < L && !st; ++step) {
+      const int tau = dir ? L - step : step + 1;
+      for (int q = 0; q < nv && !st; ++q) {
+        const int v = dir ? nv - 1 - q : q;          /* position in the order the factors act */
+        double u1, u2;
+        double complex R;
+        if (v < N) {
+          const int x = v;
+          proposal_uniforms(seed, chain, sweep, tau, dir, x, &u1, &u2);
+          const int f = hs[(size_t)(tau - 1) * N + x];
+          int others[3], n = 0;
+          const int all[4] = {-2, -1, 1, 2};
+          for (int a = 0; a < 4; ++a) if (all[a] != f) others[n++] = all[a];
+          int idx = (int)floor(3.0 * u1);
+          if (idx > 2) idx = 2;
+          const int fn = others[idx];
+          st = hi_green_at(&m, tau, 0, Gt);
+          if (st) break;
+          const double dth = m.g * (hs_eta(fn) - hs_eta(f));
+          const double complex r1 = 1.0 + (cexp(_Complex_I * dth) - 1.0) * (1.0 - Gt[(size_t)x * N + x]);
+          R = hs_gamma(fn) / hs_gamma(f) * cexp(-_Complex_I * dth) * r1 * r1;
+          const double rr = fabs(creal(P * R)) / fabs(creal(P));
+          if (u2 < (rr < 1.0 ? rr : 1.0)) {
+            hs[(size_t)(tau - 1) * N + x] = (int8_t)fn;
+            P = P * R / cabs(P * R);
+            ++acc;
+          }
+        } else {
+          const int b = nb - 1 - (v - N);            /* parts 1..nb act as bonds nb-1..0 */
+          proposal_uniforms(seed, chain, sweep, tau, dir, N + b, &u1, &u2);
+          st = hi_green_at(&m, tau, v - N + 1, Gt);
+          if (st) break;
+          int8_t* s = &sz[(size_t)(tau - 1) * nb + b];
+          const double a = m.a0 * (double)(*s);
+          const double delta[8] = {cosh(2.0 * a) - 1.0, 0.0, -sinh(2.0 * a), 0.0,
+                                   -sinh(2.0 * a), 0.0, cosh(2.0 * a) - 1.0, 0.0};
+          double* Gi = dalloc(2 * NN);
+          for (size_t e = 0; e < NN; ++e) { Gi[2 * e] = creal(Gt[e]); Gi[2 * e + 1] = cimag(Gt[e]); }
+          double r1[2];
+          st = orc_bond_rank2_update(N, Gi, bi[b], bj[b], delta, r1);
+          free(Gi);
+          if (st == ORC_ESING) st = ORC_OK;            /* a zero ratio is a rejected proposal */
+          if (st) break;
+          double lw0, lw1;
+          orc_ising_bond_logweight(nb, L, sz, dtau, h, J, n_pairs, pairs, &lw0);
+          *s = (int8_t)(-*s);
+          orc_ising_bond_logweight(nb, L, sz, dtau, h, J, n_pairs, pairs, &lw1);
+          *s = (int8_t)(-*s);
+          const double complex rf = r1[0] + _Complex_I * r1[1];
+          R = rf * rf * exp(lw1 - lw0);
+          const double rr = fabs(creal(P * R)) / fabs(creal(P));
+          if (u2 < (rr < 1.0 ? rr : 1.0)) {
+            *s = (int8_t)(-*s);
+            P = P * R / cabs(P * R);
+            ++acc;
+          }
+        }
+      }
+    }
+  }
+  if (!st) st = orc_hubbard_ising_plain(N, T, nb, bi, bj, xi, dtau, U, L, hs, sz, Gd, &la, &ar, &ph, kin);
+  if (!st) {
+    const double sgn = creal(P) >= 0.0 ? 1.0 : -1.0;
+    const double complex rw = sgn * P / creal(P);
+    const double complex wk = rw * (kin[0] + _Complex_I * kin[1]);
+    double m2 = 0.0;
+    for (int tau = 0; tau < L; ++tau) {
+      double mt = 0.0;
+      for (int b = 0; b < nb; ++b) mt += (double)sz[(size_t)tau * nb + b];
+      m2 += mt * mt / (double)nb;
+    }
+    const double complex wm = rw * (m2 / (double)L);
+    obs[0] = creal(wk); obs[1] = cimag(wk); obs[2] = sgn; obs[3] = creal(wm); obs[4] = cimag(wm);
+    phase[0] = creal(P); phase[1] = cimag(P);
+    *accepted = acc;
+  }
+  free(Gt); free(Gd); free((void*)m.E);
+  return st;
+}

@@ -149,13 +149,14 @@ def su2_trotter(F, K, U, dtau, L, eta, gamma):
     return Z, np.trace((F.hopping(K) + HU) @ rho) / Z
 
 
-def hubbard_ising_trotter(F, K, U, dtau, L, eta, gamma, bonds, xi, h, J, pairs):
+def hubbard_ising_trotter(F, K, U, dtau, L, eta, gamma, bonds, xi, h, J, pairs, with_m2=False):
     """Partition function and <H_T> of the Trotter product of the Hubbard model
     coupled to Ising spins on bonds, on the product space Fock (x) Ising
     (Ising basis state k: s_b = 1 - 2 bit_b(k)):
       S = exp(-dtau H_T) prod_b exp(-dtau xi Z_b O_b) W exp(dtau J sum_pairs Z Z) prod_b exp(dtau h X_b),
     O_b = sum_s (c^+_is c_js + h.c.), W the summed slice factor of the SU(2)
-    charge decoupling.  Returns (Tr S^L, Tr[H_T S^L] / Tr S^L)."""
+    charge decoupling.  Returns (Tr S^L, Tr[H_T S^L] / Tr S^L) and, with
+    with_m2, <(sum_b Z_b)^2> / n_bonds as a third value."""
     N = K.shape[0]
     nb = len(bonds)
     dI = 2 ** nb
@@ -181,4 +182,8 @@ def hubbard_ising_trotter(F, K, U, dtau, L, eta, gamma, bonds, xi, h, J, pairs):
         S = S @ np.kron(If, expm(dtau * h * Xb))
     rho = np.linalg.matrix_power(S, L)
     Z = np.trace(rho)
-    return Z, np.trace(np.kron(F.hopping(K), np.eye(dI)) @ rho) / Z
+    kin = np.trace(np.kron(F.hopping(K), np.eye(dI)) @ rho) / Z
+    if not with_m2:
+        return Z, kin
+    m2 = np.kron(np.ones(F.dim), s.sum(axis=1) ** 2 / nb)
+    return Z, kin, np.trace(np.diag(m2) @ rho) / Z
