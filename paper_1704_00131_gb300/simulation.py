@@ -8,9 +8,17 @@ over its sweeps.  Everything here is host bookkeeping over the library's
 measurement calls: `Ensemble.sweep`, `Ensemble.measure` (energy estimator over
 the measurement window), `Ensemble.measure_tau` and `Ensemble.measure_corr`
 (one sample per chain after each sweep).
+
+Chained jobs (the paper's configuration files and CPU_MAX): `run` can write a
+checkpoint after every bin -- the fields and random-number counter of every
+chain and the bins done so far -- and stop once a wall-clock budget is spent; a
+later `run` with the same checkpoint on a fresh ensemble of the same models
+resumes from it and ends with the same bins as an uninterrupted run.
 """
 from __future__ import annotations
 
+import os
+import time
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -27,6 +35,7 @@ class Result:
     mean_sign: float
     mean: dict = field(default_factory=dict)
     error: dict = field(default_factory=dict)
+    complete: bool = True          # False when a time budget stopped the run early
 
 
 class Simulation:
@@ -96,11 +105,57 @@ class Simulation:
                 out["_sign_energy"] = ds
         return out, s_bin
 
-    def run(self) -> Result:
-        if self.warmup:
-            self.ens.sweep(self.warmup, stats=False)
-        bins = [self._one_bin() for _ in range(self.n_bins)]
-        res = Result(self.n_bins, self.sweeps_per_bin, 0.0)
+    def _save(self, path: str, bins) -> None:
+        fields, ctr = self.ens.get_fields()
+        data = {"meta": np.array([self.n_bins, self.sweeps_per_bin, self.ens.n_chains, ctr], dtype=np.uint64),
+                "signs": np.array([s for _, s in bins], dtype=np.float64)}
+        for k in sorted({k for b, _ in bins for k in b}):
+            data["bin__" + k] = np.array([b[k] for b, _ in bins])
+        for c, f in enumerate(fields):
+            data[f"fields__{c}"] = np.asarray(f, dtype=np.int8)
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "wb") as fh:
+            np.savez(fh, **data)
+        os.replace(tmp, path)                  # a crash leaves the previous checkpoint intact
+
+    def _load(self, path: str):
+        with np.load(path) as z:
+            n_bins, spb, n_chains, ctr = (int(v) for v in z["meta"])
+            if (n_bins, spb, n_chains) != (self.n_bins, self.sweeps_per_bin, self.ens.n_chains):
+                raise ValueError(f"checkpoint {path} is for {n_bins} bins of {spb} sweeps over {n_chains} chains")
+            signs = z["signs"]
+            keys = [k[5:] for k in z.files if k.startswith("bin__")]
+            cols = {k: z["bin__" + k] for k in keys}
+            bins = [({k: cols[k][i] for k in keys}, float(signs[i])) for i in range(len(signs))]
+            fields = [z[f"fields__{c}"] for c in range(n_chains)]
+        self.ens.set_fields(fields, ctr)
+        return bins
+
+    def run(self, checkpoint: str | None = None, max_seconds: float | None = None) -> Result:
+        """Warm up, then run the bins.  checkpoint: path of a file written after
+        every bin; if it exists when the run starts, the run resumes from it (no
+        warm-up).  max_seconds: stop after the first bin that ends past this
+        wall-clock budget; the result covers the bins done (complete=False;
+        with fewer than two bins its mean and error stay empty)."""
+        t0 = time.monotonic()
+        if checkpoint is not None and os.path.exists(checkpoint):
+            bins = self._load(checkpoint)
+        else:
+            bins = []
+            if self.warmup:
+                self.ens.sweep(self.warmup, stats=False)
+        while len(bins) < self.n_bins:
+            bins.append(self._one_bin())
+            if checkpoint is not None:
+                self._save(checkpoint, bins)
+            if max_seconds is not None and time.monotonic() - t0 >= max_seconds and len(bins) < self.n_bins:
+                break
+        return self._analyse(bins)
+
+    def _analyse(self, bins) -> Result:
+        res = Result(self.n_bins, self.sweeps_per_bin, 0.0, complete=len(bins) == self.n_bins)
+        if len(bins) < 2:
+            return res
         names = sorted({k for b, _ in bins for k in b if not k.startswith("_")})
         signs = np.array([s for _, s in bins])
         e_signs = np.array([b.get("_sign_energy", np.nan) for b, _ in bins])

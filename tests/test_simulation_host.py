@@ -15,7 +15,9 @@ class FakeEnsemble:
     def __init__(self, n_chains=3, L=4, seed=0):
         self.n_chains = n_chains
         self.L = L
-        self.rng = np.random.default_rng(seed)
+        self.seed = seed
+        self.counter = 0                                # sweeps done: the random numbers follow from it
+        self.fields = [np.ones((L, 4), dtype=np.int8) for _ in range(n_chains)]
         self.e = np.zeros((n_chains, 4))
         self.ss = np.zeros(n_chains)
         self.nm = np.zeros(n_chains, dtype=np.int64)
@@ -24,12 +26,23 @@ class FakeEnsemble:
     def model_of(self, c):
         return _Model()
 
+    def get_fields(self):
+        return [f.copy() for f in self.fields], self.counter
+
+    def set_fields(self, fields, counter):
+        self.fields = [np.asarray(f, dtype=np.int8).copy() for f in fields]
+        self.counter = counter
+
     def sweep(self, n, stats=False):
         for _ in range(n):
-            sg = np.where(self.rng.random((self.n_chains, 2)) < 0.9, 1, -1).astype(np.int32)
-            obs = self.rng.random((self.n_chains, self.L + 1, 2, 3))
-            corr = self.rng.random((self.n_chains, 2, 4))
-            en = self.rng.random((self.n_chains, 4))
+            rng = np.random.default_rng([self.seed, self.counter])
+            self.counter += 1
+            for f in self.fields:
+                f[rng.integers(self.L), rng.integers(4)] *= -1
+            sg = np.where(rng.random((self.n_chains, 2)) < 0.9, 1, -1).astype(np.int32)
+            obs = rng.random((self.n_chains, self.L + 1, 2, 3))
+            corr = rng.random((self.n_chains, 2, 4))
+            en = rng.random((self.n_chains, 4))
             s = np.prod(sg, axis=1)
             self.e += 2 * s[:, None] * en                   # two measurements per sweep
             self.ss += 2 * s
@@ -78,3 +91,37 @@ def test_bad_parameters():
         Simulation(FakeEnsemble(), n_bins=1, sweeps_per_bin=1)
     with pytest.raises(ValueError):
         Simulation(FakeEnsemble(), n_bins=2, sweeps_per_bin=0)
+
+
+def test_checkpoint_resume_equals_uninterrupted_run(tmp_path):
+    kw = dict(n_bins=5, sweeps_per_bin=3, warmup=2, tau=(4, None), corr=([None], [2]))
+    full = Simulation(FakeEnsemble(seed=7), **kw).run()
+    path = str(tmp_path / "run.npz")
+    part = Simulation(FakeEnsemble(seed=7), **kw).run(checkpoint=path, max_seconds=0.0)
+    assert not part.complete and part.mean == {}         # stopped after the first bin
+    ens = FakeEnsemble(seed=7)
+    resumed = Simulation(ens, **kw).run(checkpoint=path)
+    assert resumed.complete and ens.counter == 2 + 5 * 3
+    assert resumed.mean_sign == full.mean_sign
+    for k in full.mean:
+        if k in ("kin", "pot", "part", "ener"):
+            # differences of running sums that restart from zero on the fresh ensemble: equal to rounding
+            assert resumed.mean[k] == pytest.approx(full.mean[k], rel=1e-12), k
+            assert resumed.error[k] == pytest.approx(full.error[k], rel=1e-12), k
+        else:
+            assert np.array_equal(resumed.mean[k], full.mean[k]) and np.array_equal(resumed.error[k], full.error[k]), k
+    # a finished checkpoint resumes to the same result without sweeping
+    ens2 = FakeEnsemble(seed=7)
+    again = Simulation(ens2, **kw).run(checkpoint=path)
+    assert ens2.counter == 2 + 5 * 3 and np.array_equal(again.mean["corr_zz"], full.mean["corr_zz"])
+    f_end, _ = ens.get_fields()
+    assert all(np.array_equal(a, b) for a, b in zip(ens2.get_fields()[0], f_end))
+
+
+def test_checkpoint_of_another_run_is_rejected(tmp_path):
+    path = str(tmp_path / "run.npz")
+    Simulation(FakeEnsemble(), n_bins=3, sweeps_per_bin=2).run(checkpoint=path)
+    with pytest.raises(ValueError):
+        Simulation(FakeEnsemble(), n_bins=4, sweeps_per_bin=2).run(checkpoint=path)
+    with pytest.raises(ValueError):
+        Simulation(FakeEnsemble(n_chains=2), n_bins=3, sweeps_per_bin=2).run(checkpoint=path)
