@@ -251,7 +251,9 @@ dqmc_status dqmc_energy_backward(dqmc_ctx* ctx, int32_t model_index, const int8_
  * Philox sweep counter (confout / confin of Algorithm 1). */
 dqmc_status dqmc_get_fields(dqmc_ctx* ctx, int8_t* out, uint64_t* rng_counter);
 /* Resume: replaces the fields and the sweep counter and recomputes the left
- * chain and G(0) of every chain. */
+ * chain and G(0) of every chain.  in: the packed fields as dqmc_get_fields
+ * writes them.  Every value is checked first (+-1, or -2,-1,1,2 for
+ * DQMC_FIELD_HS4); an invalid one returns DQMC_EINVAL and changes nothing. */
 dqmc_status dqmc_set_fields(dqmc_ctx* ctx, const int8_t* in, uint64_t rng_counter);
 
 /* Allocation-free computation of G^s(0) for every flavor (no counterpart in

@@ -756,6 +756,7 @@ dqmc_status dqmc_get_fields(dqmc_ctx* ctx, int8_t* out, uint64_t* rng_counter) {
 dqmc_status dqmc_set_fields(dqmc_ctx* ctx, const int8_t* in, uint64_t rng_counter) {
   if (!ctx) return DQMC_EINVAL;
   if (!in) return fail(ctx, DQMC_EINVAL, "null input");
+  // every chain is checked before any is replaced: a rejected call leaves the ensemble as it was
   size_t off = 0;
   for (const ChainDev& C : ctx->chains_h) {
     const size_t nf = (size_t)C.L * C.MV;
@@ -764,6 +765,11 @@ dqmc_status dqmc_set_fields(dqmc_ctx* ctx, const int8_t* in, uint64_t rng_counte
       const bool ok = (C.ft == DQMC_FIELD_ISING) ? (f == 1 || f == -1) : (f == 1 || f == -1 || f == 2 || f == -2);
       if (!ok) return fail(ctx, DQMC_EINVAL, "chain %u: invalid field value %d", C.chain_id, (int)f);
     }
+    off += nf;
+  }
+  off = 0;
+  for (const ChainDev& C : ctx->chains_h) {
+    const size_t nf = (size_t)C.L * C.MV;
     CUDA_TRY(ctx, cudaMemcpyAsync(C.fields, in + off, nf, cudaMemcpyHostToDevice, ctx->stream));
     off += nf;
   }

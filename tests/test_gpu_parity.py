@@ -348,6 +348,16 @@ def test_invalid_arguments_are_rejected(dq):
     ens = dq.Ensemble([m], [0])
     with pytest.raises(dq.DqmcError):
         ens.greens(5, 0)
+    # a resume with one invalid value changes no chain (nor the counter)
+    ens = dq.Ensemble([m], [0, 0], seed=9)
+    f, ctr = ens.get_fields()
+    g = [-f[0], f[1].copy()]
+    g[1][3, 5] = 3
+    with pytest.raises(dq.DqmcError) as e:
+        ens.set_fields(g, ctr + 5)
+    assert e.value.status == dq.DQMC_EINVAL
+    f2, ctr2 = ens.get_fields()
+    assert ctr2 == ctr and all(np.array_equal(a, b) for a, b in zip(f, f2))
 
 
 # ------------------------------------------------------- failure handling
