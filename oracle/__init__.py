@@ -109,6 +109,7 @@ def lib():
         _lib.orc_bond_rank2_update.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         _lib.orc_hubbard_ising_sweep.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, d, d, d, ctypes.c_int, vp, d, d,
                                                  ctypes.c_int, vp, vp, u64, u32, u64, vp, vp, vp]
+        _lib.orc_tau_correlations.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp]
         _lib.orc_su2_green_udv.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
         del i32
     return _lib
@@ -329,6 +330,17 @@ def tau_observables(model: Model, fields: np.ndarray, n_tau: int, phase=None):
     _check(lib().orc_tau_observables(model.cref(), _ptr(f), n_tau, None if ph is None else _ptr(ph), _ptr(out),
                                      _ptr(sg)), "tau_observables")
     return out, sg
+
+
+def tau_correlations(model: Model, fields: np.ndarray, n_tau: int, pair_class: np.ndarray, n_class: int):
+    """Per displacement tau = 0..n_tau and pair class: sums of sum_s <c_xs(tau) c^+_ys(0)>,
+    <S^z_x(tau) S^z_y(0)> and <n_x(tau) n_y(0)> of one configuration; returns [n_tau+1, n_class, 3]."""
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    cls = np.ascontiguousarray(pair_class, dtype=np.int32)
+    out = np.zeros((n_tau + 1, n_class, 3))
+    _check(lib().orc_tau_correlations(model.cref(), _ptr(f), int(n_tau), _ptr(cls), int(n_class), _ptr(out)),
+           "tau_correlations")
+    return out
 
 
 def correlations(G: np.ndarray, pair_class: np.ndarray, n_class: int) -> np.ndarray:

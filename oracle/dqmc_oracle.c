@@ -1264,6 +1264,61 @@ int orc_tau_observables(const orc_model* m, const int8_t* fields, int n_tau, con
   return st;
 }
 
+/* Time-displaced correlation functions per pair class of one configuration
+ * (the ObserT quantities of Sec. 5.2 collected per lattice displacement, as
+ * Obser_Latt does for the equal-time ones), spin-z decoupling with two flavors.
+ * With G^s(tau,0)_xy = <c_xs(tau) c^+_ys(0)>, G^s(0,tau)_yx = -<c^+_xs(tau) c_ys(0)>,
+ * m_x(tau) = sum_s sigma_s (1 - G^s(tau,tau)_xx), sigma = (+1, -1),
+ * rho_x(tau) = sum_s (1 - G^s(tau,tau)_xx) and the Wick-connected
+ * X^s_xy(tau) = -G^s(0,tau)_yx G^s(tau,0)_xy (flavors independent in one
+ * configuration):
+ *   sum_s <c_xs(tau) c^+_ys(0)>  = sum_s G^s(tau,0)_xy
+ *   <S^z_x(tau) S^z_y(0)>        = [m_x(tau) m_y(0) + X^0_xy + X^1_xy] / 4
+ *   <n_x(tau) n_y(0)>            = rho_x(tau) rho_y(0) + X^0_xy + X^1_xy
+ * out[(tau * n_class + c) * 3 + {0, 1, 2}] = sums of these over the pairs
+ * (x, y) with cls[x * N + y] == c, for tau = 0..n_tau; every Green function is
+ * computed from scratch through the UDV chains.  At tau = 0 they reduce to the
+ * equal-time G, S^z S^z and n n of orc_correlations. */
+int orc_tau_correlations(const orc_model* m, const int8_t* fields, int n_tau, const int32_t* cls, int n_class,
+                         double* out) {
+  if (!m || m->n_flavors != 2 || n_class < 1 || n_tau < 0 || n_tau > m->L) return ORC_EINVAL;
+  const int N = m->n_sites;
+  for (int e = 0; e < N * N; ++e)
+    if (cls[e] >= n_class) return ORC_EINVAL;
+  const size_t NN = (size_t)N * N;
+  double *Gt0[2], *G0t[2], *Gtt[2], *G00[2];
+  for (int s = 0; s < 2; ++s) {
+    Gt0[s] = dalloc(NN); G0t[s] = dalloc(NN); Gtt[s] = dalloc(NN); G00[s] = dalloc(NN);
+  }
+  int st = ORC_OK;
+  double ld;
+  int sg;
+  for (int s = 0; s < 2 && !st; ++s) st = orc_green_udv(m, fields, s, 0, G00[s], &ld, &sg);
+  for (int q = 0; q < (n_tau + 1) * n_class * 3; ++q) out[q] = 0.0;
+  for (int tau = 0; tau <= n_tau && !st; ++tau) {
+    for (int s = 0; s < 2 && !st; ++s) {
+      st = orc_green_displaced(m, fields, s, tau, Gt0[s], G0t[s]);
+      if (!st) st = orc_green_udv(m, fields, s, tau, Gtt[s], &ld, &sg);
+    }
+    if (st) break;
+    for (int x = 0; x < N; ++x)
+      for (int y = 0; y < N; ++y) {
+        const int c = cls[x * N + y];
+        if (c < 0) continue;
+        const double nxu = 1.0 - Gtt[0][x * N + x], nxd = 1.0 - Gtt[1][x * N + x];
+        const double nyu = 1.0 - G00[0][y * N + y], nyd = 1.0 - G00[1][y * N + y];
+        const double X0 = -G0t[0][y * N + x] * Gt0[0][x * N + y];
+        const double X1 = -G0t[1][y * N + x] * Gt0[1][x * N + y];
+        double* o = out + ((size_t)tau * n_class + c) * 3;
+        o[0] += Gt0[0][x * N + y] + Gt0[1][x * N + y];
+        o[1] += 0.25 * ((nxu - nxd) * (nyu - nyd) + X0 + X1);
+        o[2] += (nxu + nxd) * (nyu + nyd) + X0 + X1;
+      }
+  }
+  for (int s = 0; s < 2; ++s) { free(Gt0[s]); free(G0t[s]); free(Gtt[s]); free(G00[s]); }
+  return st;
+}
+
 /* Equal-time correlation functions of one configuration (the equal-time
  * observables of Sec. 5.2 and 6, Obser_Latt), for the spin-z decoupling with
  * two flavors (0 = up, 1 = down); G[s] is the equal-time Green function

@@ -109,6 +109,31 @@ def tau_observables(F, K, U, dtau, L, ph, W=None):
     return np.array(gl), np.array(szz)
 
 
+def tau_correlations(F, K, U, dtau, L, cls, n_class):
+    """Per tau = 0..L and pair class: sums of sum_s <c_xs(tau) c^+_ys(0)>,
+    <S^z_x(tau) S^z_y(0)> and <n_x(tau) n_y(0)> of the Trotterised Hubbard model
+    (exact Ising decoupling), <A(tau) B(0)> = Tr[T^{L-tau} A T^tau B] / Tr[T^L]."""
+    N = K.shape[0]
+    T = expm(-dtau * F.hopping(K)) @ expm(-dtau * F.hubbard_ph(U))
+    Z = np.trace(np.linalg.matrix_power(T, L))
+    out = np.zeros((L + 1, n_class, 3))
+    sz = [0.5 * (F.n(0, x) - F.n(1, x)) for x in range(N)]
+    nn = [F.n(0, x) + F.n(1, x) for x in range(N)]
+    for tau in range(L + 1):
+        A = np.linalg.matrix_power(T, L - tau)
+        B = np.linalg.matrix_power(T, tau)
+        for x in range(N):
+            for y in range(N):
+                c = cls[x * N + y]
+                if c < 0:
+                    continue
+                g = sum(np.trace(A @ F.c[F.mode(s, x)] @ B @ F.c[F.mode(s, y)].T) for s in range(2))
+                out[tau, c, 0] += g / Z
+                out[tau, c, 1] += np.trace(A @ sz[x] @ B @ sz[y]) / Z
+                out[tau, c, 2] += np.trace(A @ nn[x] @ B @ nn[y]) / Z
+    return out
+
+
 def equal_time_correlations(F, K, U, dtau, L, cls, n_class):
     """Per pair class: sums of <S^z_x S^z_y>, <n_x n_y>, <S^+_x S^-_y> and
     sum_s <c^+_xs c_ys> in the Trotterised density matrix (trace boundary)."""
