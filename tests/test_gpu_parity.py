@@ -205,6 +205,36 @@ def test_mixed_path_drift_and_batch(dq, orc, precision):
     assert st["prec_green_max"] < 1e-5 and st["prec_green_mean"] < 1e-8, st
 
 
+def test_sign_problem_trajectory_fp64(dq, orc):
+    """Frustrated 3x3 torus away from half filling (U = 6, mu = -0.5): negative
+    weights occur, so the sign carried through accepted negative ratios matters.
+    The GPU chain follows the oracle's trajectory bit for bit, with the same mean
+    sign (below 1), a phase monitor of 0 and the same sign-weighted measurements."""
+    K = W.square_lattice(3, 3, 1.0, 0.0, -0.5)
+    m = W.ModelSpec(K, U=6.0, dtau=0.125, L=32, n_wrap=4)
+    f0 = W.random_fields(1, 32, 9, seed=1).reshape(32, 9)
+    ens = dq.Ensemble([m], [0], fields=[f0], precision="fp64", delay_k=16, seed=5, measure=True)
+    och = orc.Chain(omodel(orc, m), f0, seed=5, chain=0, measure=True)
+    signs = []
+    for rep in range(4):
+        sg = ens.sweep(5)
+        so = och.sweep(5)
+        fg, _ = ens.get_fields()
+        fo, _, sign = och.fields()
+        assert np.array_equal(fg[0], fo), f"fields differ after sweep {5 * (rep + 1)}"
+        assert sg["accepted"] == so.accepted and sg["mean_sign"] == so.mean_sign
+        assert sg["prec_phase_max"] == 0.0 == so.prec_phase_max
+        signs.append(so.mean_sign)
+        for s in (0, 1):
+            assert np.abs(ens.greens(0, s)[0] - och.green(s)).max() < 1e-10
+    assert min(signs) < 1.0
+    mg, ssg, nmg = ens.measure()
+    mo, sso, nmo = och.measure()
+    assert nmg[0] == nmo and ssg[0] == sso
+    assert np.abs(mg[0] - mo).max() < 1e-8 * max(1.0, np.abs(mo).max())
+    ens.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_large_lattice_324_sites(dq, orc, precision):
     """18x18 square lattice with t' = -0.2, mu = -0.5 (N = 324: seven 48-wide tiles with

@@ -12,7 +12,8 @@ transposed operand) fails it:
   against the Fock-space trace of the Trotterised density matrix (ED);
 * particle-hole symmetry at half filling on bipartite lattices;
 * the UDV chain against the plain product, and n_wrap independence;
-* the fast-updated, wrapped G against the freshly stabilised one;
+* the fast-updated, wrapped G against the freshly stabilised one, and the sign
+  carried through negative ratios against the recomputed one;
 * central finite differences of log|det(1 + B(beta,0))|;
 * Monte Carlo estimates of the sampler against ED within 3 sigma.
 """
@@ -354,6 +355,23 @@ def test_precision_monitor_low_temperature(orc):
     assert st.prec_green_mean < 1e-8
     assert st.prec_green_max < 1e-5
     assert st.prec_phase_max == 0.0 and st.mean_sign == 1.0
+
+
+def test_sign_tracked_through_negative_ratios(orc):
+    """Away from half filling on the frustrated 3x3 torus the spin-z decoupling has
+    negative weights: the sign carried through the updates (flipped on every
+    accepted negative ratio) must equal the sign of det(1 + B_up) det(1 + B_dn)
+    recomputed at every stabilisation (the phase monitor of Sec. 2.3 stays 0) and
+    at the end of the sweeps, while the chain visits both signs."""
+    K = W.square_lattice(3, 3, t=1.0, mu=-0.5)
+    m = make_model(orc, K, 6.0, 0.125, 32, 4)
+    ch = orc.Chain(m, W.random_fields(1, 32, 9, seed=1).reshape(32, 9), seed=5, chain=0)
+    st = ch.sweep(20)
+    assert st.mean_sign < 0.99
+    assert st.prec_phase_max == 0.0
+    f, _, sign = ch.fields()
+    want = orc.green_udv(m, f, 0, 0)[2] * orc.green_udv(m, f, 1, 0)[2]
+    assert sign == want
 
 
 # ---------------------------------------------------------------- derivatives
