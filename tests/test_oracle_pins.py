@@ -289,6 +289,34 @@ def test_udv_agrees_with_plain_product(orc):
             assert lu == pytest.approx(lp, rel=1e-12) and su == sp
 
 
+def test_udv_sign_per_flavor_odd_lattice(orc):
+    """Per flavor, the sign and log|det| of the UDV chain equal numpy's slogdet of
+    1 + B(tau,0)B(beta,tau) built from plain numpy products, on an odd lattice
+    (3x3 torus away from half filling) where single-flavor determinants change
+    sign and an odd number of reflections enters each orthogonal factor."""
+    K = W.square_lattice(3, 3, t=1.0, mu=-0.5)
+    N, U, dtau, L = 9, 6.0, 0.25, 16
+    m = make_model(orc, K, U, dtau, L, 4)
+    lam = np.arccosh(np.exp(0.5 * dtau * U))
+    E = expm(-dtau * K)
+    seen = set()
+    for seed in range(6):
+        f = W.random_fields(1, L, N, seed=40 + seed)
+        for s, sig in ((0, 1.0), (1, -1.0)):
+            Bs = [E @ np.diag(np.exp(sig * lam * f[t].astype(float))) for t in range(L)]
+            for tau in (0, 6, L):
+                P = np.eye(N)
+                for t in list(range(tau, L)) + list(range(tau)):   # B(tau,0) B(beta,tau), cyclically
+                    P = Bs[t] @ P
+                sg_np, ld_np = np.linalg.slogdet(np.eye(N) + P)
+                # the plain product's determinant carries eps * cond(1 + B) (Sec. 2.3)
+                tol = 1e-11 * abs(ld_np) + 100 * np.finfo(float).eps * np.linalg.cond(np.eye(N) + P)
+                _, lu, su = orc.green_udv(m, f, s, tau)
+                assert su == int(sg_np) and abs(lu - ld_np) < tol, (seed, s, tau, lu - ld_np, tol)
+                seen.add(su)
+    assert seen == {-1, 1}
+
+
 def test_udv_independent_of_nwrap_at_low_temperature(orc):
     """beta = 10, U = 4: the plain product is hopeless, chunk sizes must agree."""
     K = W.square_lattice(4, 4)
