@@ -110,6 +110,8 @@ def lib():
         _lib.orc_hubbard_ising_sweep.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, d, d, d, ctypes.c_int, vp, d, d,
                                                  ctypes.c_int, vp, vp, u64, u32, u64, vp, vp, vp]
         _lib.orc_tau_correlations.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp]
+        _lib.orc_hubbard_ising_green_udv.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, d, d, d, ctypes.c_int,
+                                                      ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, vp]
         _lib.orc_su2_green_udv.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
         del i32
     return _lib
@@ -435,6 +437,23 @@ def hubbard_ising_green_at(T: np.ndarray, bonds, xi: float, dtau: float, U: floa
                                             float(U), f.size // N, _ptr(f), _ptr(z), int(tau), int(part), _ptr(G)),
            "hubbard_ising_green_at")
     return G[..., 0] + 1j * G[..., 1]
+
+
+def hubbard_ising_green_udv(T: np.ndarray, bonds, xi: float, dtau: float, U: float, n_wrap: int, hs: np.ndarray,
+                            ising: np.ndarray, tau: int = 0):
+    """G(tau) of one color of the bond model through the complex UDV chains:
+    (G complex [N, N], log|det(1 + B(beta,0))|, arg det(1 + B(beta,0)))."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    N = T.shape[0]
+    bi, bj = _bond_arrays(bonds)
+    f = np.ascontiguousarray(hs, dtype=np.int8)
+    z = np.ascontiguousarray(ising, dtype=np.int8)
+    G = np.zeros((N, N, 2))
+    la, ar = ctypes.c_double(), ctypes.c_double()
+    _check(lib().orc_hubbard_ising_green_udv(N, _ptr(T), len(bi), _ptr(bi), _ptr(bj), float(xi), float(dtau),
+                                             float(U), f.size // N, int(n_wrap), _ptr(f), _ptr(z), int(tau), _ptr(G),
+                                             ctypes.byref(la), ctypes.byref(ar)), "hubbard_ising_green_udv")
+    return G[..., 0] + 1j * G[..., 1], la.value, ar.value
 
 
 def bond_rank2_update(G: np.ndarray, i: int, j: int, delta: np.ndarray):

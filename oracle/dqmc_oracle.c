@@ -1728,37 +1728,28 @@ static void cudv_step(int N, const double* E, double g, const int8_t* fields, in
   free(X); free(Y);
 }
 
-/* G(tau) of one color of the SU(2) decoupling through the complex UDV chains
- * (chunks of n_wrap slices; a partial chunk closes each chain), with
- * log|det(1 + B(beta,0))| and its argument.  G_out [N][N] complex (re, im). */
-int orc_su2_green_udv(int N, const double* K, double dtau, double U, int L, int n_wrap, const int8_t* fields,
-                      int tau, double* G_out, double* logabs, double* arg) {
-  if (N < 1 || L < 1 || n_wrap < 1 || tau < 0 || tau > L || !(dtau > 0.0) || !(U >= 0.0)) return ORC_EINVAL;
+/* G = (1 + B(tau,0) B(beta,tau))^-1 from the right chain R = B(tau,0) and the
+ * left chain Lf = B(beta,tau)^H by scale separation (the complex form of the
+ * stable G), with log|det(1 + B)| and its argument.  G_out [N][N] complex
+ * (re, im interleaved). */
+static int cudv_green(int N, const cudv_t* R, const cudv_t* Lf, double* G_out, double* logabs, double* arg) {
   const size_t NN = (size_t)N * N;
-  const double g = sqrt(0.5 * dtau * U);
-  double* E = dalloc(NN);
-  orc_expm_sym(N, K, -dtau, E);
-  cudv_t R, Lf;
-  cudv_alloc(N, &R);
-  cudv_alloc(N, &Lf);
-  for (int t = 0; t < tau; t += n_wrap) cudv_step(N, E, g, fields, t, (t + n_wrap < tau) ? t + n_wrap : tau, 0, &R);
-  for (int t = L; t > tau; t -= n_wrap) cudv_step(N, E, g, fields, (t - n_wrap > tau) ? t - n_wrap : tau, t, 1, &Lf);
   double complex* Mid = (double complex*)calloc(NN, sizeof(double complex));
   double complex* X = (double complex*)calloc(NN, sizeof(double complex));
   double *dbR = dalloc(N), *dsR = dalloc(N), *dbL = dalloc(N), *dsL = dalloc(N);
   for (int i = 0; i < N; ++i) {
-    dbR[i] = R.D[i] > 1.0 ? R.D[i] : 1.0;  dsR[i] = R.D[i] > 1.0 ? 1.0 : R.D[i];
-    dbL[i] = Lf.D[i] > 1.0 ? Lf.D[i] : 1.0; dsL[i] = Lf.D[i] > 1.0 ? 1.0 : Lf.D[i];
+    dbR[i] = R->D[i] > 1.0 ? R->D[i] : 1.0;  dsR[i] = R->D[i] > 1.0 ? 1.0 : R->D[i];
+    dbL[i] = Lf->D[i] > 1.0 ? Lf->D[i] : 1.0; dsL[i] = Lf->D[i] > 1.0 ? 1.0 : Lf->D[i];
   }
   for (int i = 0; i < N; ++i)
     for (int j = 0; j < N; ++j) {
       double complex qq = 0.0, tt = 0.0;
       for (int k = 0; k < N; ++k) {
-        qq += conj(R.Q[(size_t)k * N + i]) * Lf.Q[(size_t)k * N + j];   /* Q_R^H Q_L */
-        tt += R.T[(size_t)i * N + k] * conj(Lf.T[(size_t)j * N + k]);   /* T_R T_L^H */
+        qq += conj(R->Q[(size_t)k * N + i]) * Lf->Q[(size_t)k * N + j];   /* Q_R^H Q_L */
+        tt += R->T[(size_t)i * N + k] * conj(Lf->T[(size_t)j * N + k]);   /* T_R T_L^H */
       }
       Mid[(size_t)i * N + j] = qq / (dbR[i] * dbL[j]) + dsR[i] * tt * dsL[j];
-      X[(size_t)i * N + j] = conj(R.Q[(size_t)j * N + i]) / dbR[i];    /* Db_R^-1 Q_R^H */
+      X[(size_t)i * N + j] = conj(R->Q[(size_t)j * N + i]) / dbR[i];    /* Db_R^-1 Q_R^H */
     }
   /* Gauss-Jordan: X <- Mid^-1 X, with the determinant of Mid */
   double la = 0.0, ar = 0.0;
@@ -1792,16 +1783,36 @@ int orc_su2_green_udv(int N, const double* K, double dtau, double U, int L, int 
     for (int i = 0; i < N; ++i)
       for (int j = 0; j < N; ++j) {
         double complex acc = 0.0;
-        for (int k = 0; k < N; ++k) acc += Lf.Q[(size_t)i * N + k] * X[(size_t)k * N + j];
+        for (int k = 0; k < N; ++k) acc += Lf->Q[(size_t)i * N + k] * X[(size_t)k * N + j];
         G_out[2 * ((size_t)i * N + j)] = creal(acc);
         G_out[2 * ((size_t)i * N + j) + 1] = cimag(acc);
       }
     for (int i = 0; i < N; ++i) la += log(dbR[i]) + log(dbL[i]);
-    if (R.detQ * Lf.detQ < 0) ar += 3.14159265358979323846;
+    if (R->detQ * Lf->detQ < 0) ar += 3.14159265358979323846;
     *logabs = la;
     *arg = remainder(ar, 2.0 * 3.14159265358979323846);
   }
-  free(Mid); free(X); free(dbR); free(dsR); free(dbL); free(dsL); free(E);
+  free(Mid); free(X); free(dbR); free(dsR); free(dbL); free(dsL);
+  return st;
+}
+
+/* G(tau) of one color of the SU(2) decoupling through the complex UDV chains
+ * (chunks of n_wrap slices; a partial chunk closes each chain), with
+ * log|det(1 + B(beta,0))| and its argument.  G_out [N][N] complex (re, im). */
+int orc_su2_green_udv(int N, const double* K, double dtau, double U, int L, int n_wrap, const int8_t* fields,
+                      int tau, double* G_out, double* logabs, double* arg) {
+  if (N < 1 || L < 1 || n_wrap < 1 || tau < 0 || tau > L || !(dtau > 0.0) || !(U >= 0.0)) return ORC_EINVAL;
+  const size_t NN = (size_t)N * N;
+  const double g = sqrt(0.5 * dtau * U);
+  double* E = dalloc(NN);
+  orc_expm_sym(N, K, -dtau, E);
+  cudv_t R, Lf;
+  cudv_alloc(N, &R);
+  cudv_alloc(N, &Lf);
+  for (int t = 0; t < tau; t += n_wrap) cudv_step(N, E, g, fields, t, (t + n_wrap < tau) ? t + n_wrap : tau, 0, &R);
+  for (int t = L; t > tau; t -= n_wrap) cudv_step(N, E, g, fields, (t - n_wrap > tau) ? t - n_wrap : tau, t, 1, &Lf);
+  const int st = cudv_green(N, &R, &Lf, G_out, logabs, arg);
+  free(E);
   cudv_free(&R); cudv_free(&Lf);
   return st;
 }
@@ -2288,5 +2299,54 @@ int orc_hubbard_ising_sweep(int N, const double* T, int nb, const int32_t* bi, c
     *accepted = acc;
   }
   free(Gt); free(Gd); free((void*)m.E);
+  return st;
+}
+
+/* ---- stable G of the bond model through the complex UDV chains ----------- */
+/* Right chain X <- B_t X (factors in the order they act), left chain          */
+/* X <- B_t^H X = F_0^H F_1^H ... F_{nb+1}^H X, where only the HS factor is not */
+/* self-adjoint (its adjoint has e^{-i g eta}); chunks of n_wrap slices, the   */
+/* complex QR steps and the scale-separated G of the SU(2) decoupling.         */
+static void hi_udv_step(const hi_model_t* m, int t1, int t2, int left, cudv_t* u) {
+  const int N = m->N;
+  const size_t NN = (size_t)N * N;
+  double complex* X = (double complex*)malloc(NN * sizeof(double complex));
+  double complex* Y = (double complex*)malloc(NN * sizeof(double complex));
+  memcpy(X, u->Q, NN * sizeof(double complex));
+  for (int step = 0; step < t2 - t1; ++step) {
+    const int t = left ? t2 - step : t1 + 1 + step;
+    for (int q = 0; q <= m->nb + 1; ++q) {
+      const int part = left ? m->nb + 1 - q : q;
+      if (left && part == 0) {
+        for (int x = 0; x < N; ++x) {
+          const double complex ev = cexp(-_Complex_I * m->g * hs_eta(m->hs[(size_t)(t - 1) * N + x]));
+          for (int y = 0; y < N; ++y) X[(size_t)x * N + y] *= ev;
+        }
+      } else {
+        hi_apply_factor(m, t, part, X, Y);
+      }
+    }
+  }
+  cudv_finish(N, X, u);
+  free(X); free(Y);
+}
+
+/* G(tau) = (1 + B(tau,0) B(beta,tau))^-1 of one color of the bond model at any
+ * beta, with log|det(1 + B(beta,0))| and its argument.  G_out [N][N] complex. */
+int orc_hubbard_ising_green_udv(int N, const double* T, int nb, const int32_t* bi, const int32_t* bj, double xi,
+                                double dtau, double U, int L, int n_wrap, const int8_t* hs, const int8_t* sz, int tau,
+                                double* G_out, double* logabs, double* arg) {
+  if (n_wrap < 1 || tau < 0 || tau > L) return ORC_EINVAL;
+  hi_model_t m;
+  int st = hi_model_init(&m, N, T, nb, bi, bj, xi, dtau, U, L, hs, sz);
+  if (st) return st;
+  cudv_t R, Lf;
+  cudv_alloc(N, &R);
+  cudv_alloc(N, &Lf);
+  for (int t = 0; t < tau; t += n_wrap) hi_udv_step(&m, t, (t + n_wrap < tau) ? t + n_wrap : tau, 0, &R);
+  for (int t = L; t > tau; t -= n_wrap) hi_udv_step(&m, (t - n_wrap > tau) ? t - n_wrap : tau, t, 1, &Lf);
+  st = cudv_green(N, &R, &Lf, G_out, logabs, arg);
+  cudv_free(&R); cudv_free(&Lf);
+  free((void*)m.E);
   return st;
 }

@@ -21,6 +21,10 @@ bond spins' own weight).
   the rank-2 (Woodbury) update of it (orc_bond_rank2_update) equals the Green
   function recomputed on the flipped configuration; at the last factor it is the
   plain product's G.
+* The complex UDV chain of the bond model (orc_hubbard_ising_green_udv) equals
+  the plain product at beta = 1.5 (G at every slice boundary, log|det|, arg
+  det), is independent of n_wrap at beta = 10 and gives the same log|det| and
+  arg det at every tau.
 * The Markov chain over HS fields and bond spins (orc_hubbard_ising_sweep),
   reweighted by sign e^{-S} / Re e^{-S}, reproduces <H_T> and <(sum_b Z_b)^2>
   of the Trotter product within 4 sigma over 24 independent chains, at and away
@@ -206,3 +210,42 @@ def test_sampler_matches_trotter_product(orc, mu):
         mean, err = A.jackknife(est / n, ss / n)
         assert abs(mean - ref) < 4.0 * err, (mean, err, ref)
         assert err < 0.05 * abs(ref)
+
+
+def square_bonds(Lx, Ly):
+    idx = lambda x, y: (x % Lx) + Lx * (y % Ly)
+    return [(idx(x, y), idx(x + 1, y)) for y in range(Ly) for x in range(Lx)] + \
+           [(idx(x, y), idx(x, y + 1)) for y in range(Ly) for x in range(Lx)]
+
+
+def test_udv_chain_agrees_with_plain_product(orc):
+    K = W.square_lattice(3, 3, t=1.0, mu=0.2)
+    bonds = square_bonds(3, 3)
+    xi, dtau, U, L = 0.4, 0.1, 4.0, 15
+    rng = np.random.default_rng(21)
+    hs, z = random_config(rng, L, 9, len(bonds))
+    G0, la0, ar0, _, _ = orc.hubbard_ising_plain(K, bonds, xi, dtau, U, hs, z)
+    for nw in (1, 4, 15):
+        for tau in (0, 6, L):
+            Gu, lu, au = orc.hubbard_ising_green_udv(K, bonds, xi, dtau, U, nw, hs, z, tau)
+            Gp = G0 if tau in (0, L) else orc.hubbard_ising_green_at(K, bonds, xi, dtau, U, hs, z, tau, len(bonds) + 1)
+            assert np.abs(Gu - Gp).max() < 1e-10, (nw, tau)
+            assert lu == pytest.approx(la0, rel=1e-11)
+            assert abs(np.angle(np.exp(1j * (au - ar0)))) < 1e-10
+
+
+def test_udv_chain_low_temperature(orc):
+    """beta = 10: chunk sizes agree on G, and log|det| and arg det do not depend on tau."""
+    K = W.square_lattice(3, 3, t=1.0, mu=0.3)
+    bonds = square_bonds(3, 3)
+    xi, dtau, U, L = 0.5, 0.1, 4.0, 100
+    rng = np.random.default_rng(8)
+    hs, z = random_config(rng, L, 9, len(bonds))
+    ref = orc.hubbard_ising_green_udv(K, bonds, xi, dtau, U, 10, hs, z, 40)
+    for nw in (5, 4):
+        G, la, ar = orc.hubbard_ising_green_udv(K, bonds, xi, dtau, U, nw, hs, z, 40)
+        assert np.abs(G - ref[0]).max() < 1e-9 and la == pytest.approx(ref[1], rel=1e-11)
+        assert abs(np.angle(np.exp(1j * (ar - ref[2])))) < 1e-9
+    for tau in (0, 30, 55, 100):
+        _, la, ar = orc.hubbard_ising_green_udv(K, bonds, xi, dtau, U, 10, hs, z, tau)
+        assert la == pytest.approx(ref[1], rel=1e-11) and abs(np.angle(np.exp(1j * (ar - ref[2])))) < 1e-9
