@@ -68,3 +68,21 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(dqmc, "_LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(ImportError):
         dqmc.load()
+
+
+def test_product_and_oracle_share_no_code():
+    """The CUDA path never imports, links or includes the oracle, and the oracle
+    imports and includes nothing of the package."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_1704_00131_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, fn), encoding="utf-8").read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), fn
+                assert "dqmc_oracle" not in text and "liboracle" not in text, fn
+    for fn in os.listdir(os.path.join(root, "oracle")):
+        if fn.endswith((".py", ".c", ".h")):
+            text = open(os.path.join(root, "oracle", fn), encoding="utf-8").read()
+            assert not re.search(r"^\s*(import|from)\s+paper_1704_00131_gb300\b", text, re.M), fn
+            assert not re.search(r"^\s*#\s*include\s*[<\"].*(dqmc|paper_1704)", text, re.M), fn
