@@ -112,6 +112,7 @@ def lib():
         _lib.orc_tau_correlations.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, vp]
         _lib.orc_hubbard_ising_green_udv.argtypes = [ctypes.c_int, vp, ctypes.c_int, vp, vp, d, d, d, ctypes.c_int,
                                                       ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, vp]
+        _lib.orc_su2_correlations.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp]
         _lib.orc_su2_green_udv.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
         del i32
     return _lib
@@ -370,6 +371,18 @@ def su2_plain(K: np.ndarray, dtau: float, U: float, fields: np.ndarray):
     _check(lib().orc_su2_plain(N, _ptr(K), float(dtau), float(U), L, _ptr(f), _ptr(G), ctypes.byref(la),
                                ctypes.byref(ar), ctypes.byref(ph), _ptr(e)), "su2_plain")
     return G[..., 0] + 1j * G[..., 1], la.value, ar.value, ph.value, complex(e[0], e[1]), complex(e[2], e[3])
+
+
+def su2_correlations(G: np.ndarray, pair_class: np.ndarray, n_class: int) -> np.ndarray:
+    """Equal-time (S^z S^z, n n, S^+ S^-, sum_s c^+ c) sums per pair class of one
+    configuration of the SU(2) decoupling from its complex G [N, N] (both colors);
+    returns complex [n_class, 4]."""
+    N = G.shape[0]
+    Gi = np.ascontiguousarray(np.stack([G.real, G.imag], axis=-1), dtype=np.float64)
+    cls = np.ascontiguousarray(pair_class, dtype=np.int32)
+    out = np.zeros((n_class, 4, 2))
+    _check(lib().orc_su2_correlations(N, _ptr(Gi), _ptr(cls), int(n_class), _ptr(out)), "su2_correlations")
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def su2_green_udv(K: np.ndarray, dtau: float, U: float, n_wrap: int, fields: np.ndarray, tau: int = 0):

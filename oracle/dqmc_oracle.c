@@ -2350,3 +2350,37 @@ int orc_hubbard_ising_green_udv(int N, const double* T, int nb, const int32_t* b
   free((void*)m.E);
   return st;
 }
+
+/* Equal-time correlation functions of one configuration of the SU(2)
+ * decoupling (the paper's default observables SpinZ, SpinXY, Den, Green,
+ * collected per pair class).  Both colors see the same Green function G
+ * (complex), so Wick's theorem gives, with X_xy = (delta_xy - G_yx) G_xy and
+ * rho_x = 2 (1 - G_xx):
+ *   <S^z_x S^z_y>        = X_xy / 2       (per configuration m_x = 0)
+ *   <n_x n_y>            = rho_x rho_y + 2 X_xy
+ *   <S^+_x S^-_y>        = X_xy
+ *   sum_s <c^+_xs c_ys>  = 2 (delta_xy - G_yx)
+ * G: [N][N] complex (re, im interleaved); out[(c * 4 + q) * 2 + {0, 1}] = re, im
+ * of the class sums, classes as orc_correlations. */
+int orc_su2_correlations(int N, const double* G, const int32_t* cls, int n_class, double* out) {
+  if (N < 1 || n_class < 1) return ORC_EINVAL;
+  for (int q = 0; q < 8 * n_class; ++q) out[q] = 0.0;
+#define GZ(x, y) (G[2 * ((size_t)(x) * N + (y))] + _Complex_I * G[2 * ((size_t)(x) * N + (y)) + 1])
+  for (int x = 0; x < N; ++x)
+    for (int y = 0; y < N; ++y) {
+      const int c = cls[x * N + y];
+      if (c < 0) continue;
+      if (c >= n_class) return ORC_EINVAL;
+      const double dxy = (x == y) ? 1.0 : 0.0;
+      const double complex hyx = dxy - GZ(y, x);
+      const double complex X = hyx * GZ(x, y);
+      const double complex rx = 2.0 * (1.0 - GZ(x, x)), ry = 2.0 * (1.0 - GZ(y, y));
+      const double complex v[4] = {0.5 * X, rx * ry + 2.0 * X, X, 2.0 * hyx};
+      for (int q = 0; q < 4; ++q) {
+        out[(c * 4 + q) * 2] += creal(v[q]);
+        out[(c * 4 + q) * 2 + 1] += cimag(v[q]);
+      }
+    }
+#undef GZ
+  return ORC_OK;
+}

@@ -212,3 +212,32 @@ def hubbard_ising_trotter(F, K, U, dtau, L, eta, gamma, bonds, xi, h, J, pairs, 
         return Z, kin
     m2 = np.kron(np.ones(F.dim), s.sum(axis=1) ** 2 / nb)
     return Z, kin, np.trace(np.diag(m2) @ rho) / Z
+
+
+def su2_correlations(F, K, U, dtau, L, eta, gamma, cls, n_class):
+    """Per pair class: sums of <S^z_x S^z_y>, <n_x n_y>, <S^+_x S^-_y> and
+    sum_s <c^+_xs c_ys> in the Trotter product of the SU(2) charge decoupling
+    (summed slice factor W as su2_trotter), at the trace boundary."""
+    N = K.shape[0]
+    g = np.sqrt(0.5 * dtau * U)
+    Wd = np.ones(F.dim, dtype=complex)
+    for i in range(N):
+        ni = np.diag(F.n(0, i)) + np.diag(F.n(1, i))
+        Wd *= sum(gamma[l] / 4.0 * np.exp(1j * g * eta[l] * (ni - 1.0)) for l in (-2, -1, 1, 2))
+    rho = np.linalg.matrix_power(expm(-dtau * F.hopping(K)) @ np.diag(Wd), L)
+    Z = np.trace(rho)
+    out = np.zeros((n_class, 4), dtype=complex)
+    cu = [F.c[F.mode(0, x)] for x in range(N)]
+    cd = [F.c[F.mode(1, x)] for x in range(N)]
+    for x in range(N):
+        for y in range(N):
+            c = cls[x * N + y]
+            szx = 0.5 * (F.n(0, x) - F.n(1, x))
+            szy = 0.5 * (F.n(0, y) - F.n(1, y))
+            nx = F.n(0, x) + F.n(1, x)
+            ny = F.n(0, y) + F.n(1, y)
+            spm = cu[x].T @ cd[x] @ cd[y].T @ cu[y]
+            hop = cu[x].T @ cu[y] + cd[x].T @ cd[y]
+            for q, O in enumerate((szx @ szy, nx @ ny, spm, hop)):
+                out[c, q] += np.trace(O @ rho) / Z
+    return out

@@ -12,6 +12,10 @@
 * The complex UDV chain (orc_su2_green_udv) equals the plain product where both
   hold (G, log|det|, arg det; G(tau) against the rotated field sequence) and is
   independent of n_wrap at beta = 10.
+* Equal-time correlations per pair class (orc_su2_correlations, both colors on
+  one complex G): the enumeration of all four-valued fields of a dimer and of a
+  three-site chain, weighted as above, equals the Fock trace of S^z S^z, n n,
+  S^+ S^- and sum_s c^+ c in the Trotter product, at and away from half filling.
 * The oracle's Markov chain, sampled with W = |Re e^{-S}| and reweighted by
   sign e^{-S} / Re e^{-S} (Sec. 2.2), reproduces the energy of the Trotter
   product within 4 sigma, at and away from half filling (the single-
@@ -26,7 +30,7 @@ import pytest
 
 from paper_1704_00131_gb300 import workloads as W
 
-from .fock_ed import Fock, su2_trotter
+from .fock_ed import Fock, su2_correlations, su2_trotter
 
 
 def enumerate_su2(orc, K, U, dtau, L):
@@ -128,3 +132,28 @@ def test_su2_udv_chain_is_independent_of_n_wrap_at_large_beta(orc):
     G10, l10, a10 = orc.su2_green_udv(K, 0.1, 4.0, 10, f, 0)
     assert np.abs(G5 - G10).max() < 1e-10
     assert l5 == pytest.approx(l10, rel=1e-12) and abs(_wrap_angle(a5 - a10)) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["dimer_half", "dimer_mu", "chain3_mu"])
+def test_su2_correlations_enumeration_equals_fock_trace(orc, case):
+    if case.startswith("dimer"):
+        K, L = W.chain_lattice(2, t=1.0, mu=0.0 if case == "dimer_half" else 0.4), 3
+        cls, ncls = np.array([0, 1, 1, 0], dtype=np.int32), 2
+    else:
+        K, L = W.chain_lattice(3, t=1.0, mu=0.3), 2
+        cls, ncls = np.array([0, 1, 2, 1, 0, 1, 2, 1, 0], dtype=np.int32), 3
+    U, dtau = 4.0, 0.25
+    N = K.shape[0]
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    Z, acc = 0.0, 0.0
+    for ls in itertools.product((-2, -1, 1, 2), repeat=N * L):
+        f = np.array(ls, dtype=np.int8)
+        G, la, ar, ph, _, _ = orc.su2_plain(K, dtau, U, f)
+        w = np.prod([gam[l] / 4.0 for l in ls]) * np.exp(1j * ph) * np.exp(2.0 * (la + 1j * ar))
+        Z += w
+        acc = acc + w * orc.su2_correlations(G, cls, ncls)
+    ref = su2_correlations(Fock(N), K, U, dtau, L, eta, gam, cls, ncls)
+    got = acc / Z
+    assert np.abs(got - ref).max() < 1e-10 * max(1.0, np.abs(ref).max())
+    assert np.abs(ref.imag).max() < 1e-12 and np.abs(got.imag).max() < 1e-10
