@@ -228,28 +228,76 @@ def whole_job_value(proposals_per_step: int, world: int, ms_step: float) -> floa
 
 
 # ---------------------------------------------------------------------- ours
-FP64_PEAK_TF = 1.0994   # cuBLAS DGEMM measured on this GB300 (profiles/peaks_gb300_measured.md)
-FP32_PEAK_TF = 69.83    # cuBLAS SGEMM (FP32 SIMT) measured on the same part
-# one double-word (float pair) multiply-add costs 12 FP32-pipe operations
-DW_PEAK_TF = FP32_PEAK_TF / 12.0 * 1.0
+# A float-pair (double-word) multiply-add costs 12 FP32-pipe operations
+# (TwoProd by FMA, TwoSum, two cross-term FMAs, accumulation).
+DW_OPS_PER_FMA = 12.0
+# An exact-split product spends 28 BF16 digit-pair products (seven digits per
+# operand, diagonals t + u <= 6) on every multiply-add.
+SPLIT_PRODUCTS = 28.0
+
+# DRAM bytes (read + write) per launch of the sweep kernel from one ncu capture,
+# valid only for the kernel sources it was taken on: keyed by (precision,
+# workload, delay_k) -> (sha256 prefix of the kernel sources, bytes).  A source
+# change makes the lookup miss and the line report traffic null.
+TRAFFIC_BYTES = {}
+
+KERNEL_SOURCES = ["dqmc_device.cuh", "dqmc_umma.cuh", "dqmc_internal.h", "dqmc_sweep_fp64.cu",
+                  "dqmc_sweep_fp32.cu", "dqmc_sweep_mixed.cu"]
 
 
-# DRAM bytes (read + write) per launch of the sweep kernel, from one ncu capture
-# of the full workload (profiles/dram_sweep_kernel_square256.md), keyed by
-# (precision, workload, delay_k); other cases report null.
-TRAFFIC_BYTES = {
-    ("mixed", "square 8x8/12x12 x256 chains", 16): 10183387136 + 26127431936,
-    ("fp64", "square 8x8/12x12 x256 chains", 16): 10456027392 + 22116251136,
-}
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1704_00131_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
-def time_path(wl, precision, args, stream, seed, world, local_rank, delay_k=None):
+def measured_peaks() -> dict:
+    """Roofline denominators measured in this process (cuBLAS through torch, best
+    of a few launches): FP64 and FP32-SIMT matmul rates; the BF16 tensor rate from
+    the driver's MEASURED_PEAKS.json when present."""
+    import torch
+
+    def rate(dtype, n, iters):
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        best = 0.0
+        for _ in range(iters):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            a @ b
+            s1.record()
+            torch.cuda.synchronize()
+            best = max(best, 2 * n ** 3 / (s0.elapsed_time(s1) * 1e-3) / 1e12)
+        return best
+
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {"fp64_tflops": rate(torch.float64, 4096, 3), "fp32_simt_tflops": rate(torch.float32, 8192, 5),
+           "source": "cuBLAS DGEMM 4096^3 / SGEMM 8192^3 (TF32 off) measured in this run, best of 3 / 5"}
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        out["bf16_tflops_sustained"] = float(mp["bf16_tflops_sustained"])
+        out["bf16_source"] = "MEASURED_PEAKS.json (cuBLAS bf16, sustained)"
+    except Exception:
+        out["bf16_tflops_sustained"] = 1700.0
+        out["bf16_source"] = "fallback (no MEASURED_PEAKS.json)"
+    return out
+
+
+def time_path(wl, precision, args, stream, seed, world, local_rank, delay_k=None, peaks=None, options=None):
     """Warm up, then time args.steps sweeps of every chain with CUDA events."""
     import torch
 
     from paper_1704_00131_gb300 import dqmc
     ens = dqmc.Ensemble(wl.models, wl.chain_model, precision=precision, delay_k=delay_k or wl.delay_k, seed=seed,
-                        stream=stream)
+                        stream=stream, **(options or {}))
     ens.sweep(max(args.warmup - 1, 0), stats=False)
     st = ens.sweep(1)
     acc_per_chain = st["accepted"] / wl.n_chains
@@ -279,28 +327,48 @@ def time_path(wl, precision, args, stream, seed, world, local_rank, delay_k=None
     value = whole_job_value(wl.proposals_per_sweep(), world, ms_step)
     avg_launch_s = statistics.mean(per_launch_ms) / 1000.0
     achieved = flops_per_step / avg_launch_s / 1e12
+    pk = peaks or {}
     if precision == "fp64":
-        peak, src, kern = FP64_PEAK_TF, "measured cuBLAS DGEMM on this GB300 (FP64 pipe)", "sweep_kernel<double>"
+        bound, peak, kern = "alu", pk.get("fp64_tflops"), "sweep_kernel<double>"
+        src = "FP64 pipe: " + pk.get("source", "")
     elif precision == "fp32":
-        peak, src, kern = FP32_PEAK_TF, "measured cuBLAS SGEMM on this GB300 (FP32 SIMT)", "sweep_kernel<float>"
+        bound, peak, kern = "alu", pk.get("fp32_simt_tflops"), "sweep_kernel<float>"
+        src = "FP32 SIMT pipe: " + pk.get("source", "")
     elif precision == "mixed_tc":
-        peak, src, kern = DW_PEAK_TF, ("double-word peak of the FP32 pipes (SGEMM / 12); the N^3 products run as "
-                                       "exact-split BF16 tensor-core products"), "sweep_kernel<dd> (split-BF16 mma)"
+        bound, kern = "tensor", "sweep_kernel<dd> (tcgen05 split-BF16 products)"
+        peak = pk.get("bf16_tflops_sustained", 0.0) / SPLIT_PRODUCTS if pk else None
+        src = ("BF16 tensor peak / 28 digit-pair products per multiply-add (" + pk.get("bf16_source", "") +
+               "); only the N^3 products run on the tensor cores, the QR, LU, solves and updates on the "
+               "FP32 pipes in float pairs")
     else:
-        peak, src, kern = DW_PEAK_TF, ("double-word arithmetic on the FP32 pipes: measured SGEMM rate / 12 "
-                                       "FP32 operations per float-pair multiply-add (the FP64 share of the "
-                                       "stabilisation runs at the 1.10 TFLOP/s FP64 rate)"), "sweep_kernel<dd>"
-    traffic = TRAFFIC_BYTES.get((precision, wl.name, delay_k or wl.delay_k))
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_unit": "bytes per launch (DRAM read + write, ncu)" if traffic else None,
+        bound, kern = "alu", "sweep_kernel<dd>"
+        peak = pk.get("fp32_simt_tflops", 0.0) / DW_OPS_PER_FMA if pk else None
+        src = ("double-word arithmetic on the FP32 pipes: SGEMM rate / 12 FP32 operations per float-pair "
+               "multiply-add (" + pk.get("source", "") + ")")
+    hit = TRAFFIC_BYTES.get((precision, wl.name, delay_k or wl.delay_k))
+    srchash = kernel_source_hash()
+    traffic = hit[1] if hit and hit[0] == srchash else None
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if peak else None, "traffic": traffic,
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+            "traffic_note": ("ncu capture on these kernel sources" if traffic is not None else
+                             f"no ncu capture on these kernel sources (sha {srchash})"),
             "kernel": kern, "peak_source": src}
     return {"ens": ens, "st": st, "ms_step": ms_step, "value": value, "roofline": roof, "clocks": clk.summary(),
             "algorithmic_tflop_per_step": flops_per_step / 1e12}
 
 
-def oracle_dg(wl, ens, n_threads):
-    """max |G_GPU(0) - G_oracle(0)| on the GPU's current fields, one chain per model
-    class of the workload (flavor up), computed by the FP64 oracle on the host."""
+def oracle_checks(wl, ens, n_threads):
+    """Accuracy of a path against the FP64 oracle on the GPU's current fields, one
+    chain per model class of the workload (flavor up):
+    * fresh_G0: max |G_GPU(0) - G_oracle(0)| of the working G after the sweeps
+      (a stable recompute at the end of every sweep);
+    * wrapped_interior: max |G_wrap(tau) - G_oracle(tau)| at tau = L/2 - 1, n_wrap - 1
+      slices after a stabilisation point, with G_wrap the path's own wrapped G on
+      frozen fields (dqmc_greens_tau);
+    * oracle_nwrap_sensitivity: max |G_oracle(tau; n_wrap) - G_oracle(tau; n_wrap / 2)|
+      at the same tau, the FP64 oracle's own round-off amplification at that
+      conditioning."""
     import oracle
     oracle.build()
     fields, _ = ens.get_fields()
@@ -311,13 +379,14 @@ def oracle_dg(wl, ens, n_threads):
     for mi, c in sorted(picks.items()):
         m = wl.models[mi]
         om = oracle.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
-        jobs.append((om, fields[c], c))
+        om2 = oracle.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, max(1, m.n_wrap // 2),
+                           m.field_type)
+        jobs.append((om, om2, fields[c], c, m.L // 2 - 1))
     res = [None] * len(jobs)
 
     def work(i):
-        om, f, c = jobs[i]
-        Go, _, _ = oracle.green_udv(om, f, 0, 0)
-        res[i] = Go
+        om, om2, f, c, ti = jobs[i]
+        res[i] = (oracle.green_udv(om, f, 0, 0)[0], oracle.green_udv(om, f, 0, ti)[0], oracle.green_udv(om2, f, 0, ti)[0])
 
     ths = []
     for i in range(len(jobs)):
@@ -330,11 +399,14 @@ def oracle_dg(wl, ens, n_threads):
             ths = []
     for t in ths:
         t.join()
-    worst = 0.0
-    for i, (_, _, c) in enumerate(jobs):
-        Gg, _, _ = ens.greens(c, 0)
-        worst = max(worst, float(np.abs(Gg - res[i]).max()))
-    return worst, len(jobs)
+    fresh = wrapped = delta = 0.0
+    for i, (_, _, _, c, ti) in enumerate(jobs):
+        G0, Gt, Gt2 = res[i]
+        fresh = max(fresh, float(np.abs(ens.greens(c, 0)[0] - G0).max()))
+        wrapped = max(wrapped, float(np.abs(ens.greens_tau(c, 0, ti) - Gt).max()))
+        delta = max(delta, float(np.abs(Gt - Gt2).max()))
+    return {"fresh_G0_max_abs_dG": fresh, "wrapped_interior_max_abs_dG": wrapped,
+            "oracle_nwrap_sensitivity": delta, "chains_checked": len(jobs)}
 
 
 def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
@@ -346,19 +418,22 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
     seed = rank_seed(rank)
+    peaks = measured_peaks()
     main_prec, k_main, k_fp64 = args.precision, wl.delay_k, wl.delay_k
+    opt_main = {}
     tuned = None
     if not args.no_autotune:
         # untimed: pick the product family and the delayed-update rank on this GPU
         from paper_1704_00131_gb300 import autotune
         ch = autotune.tune(wl.models, wl.chain_model, args.precision, seed=seed, stream=stream, cache=None)
-        main_prec, k_main = ch.precision, ch.delay_k
+        main_prec, k_main, opt_main = ch.precision, ch.delay_k, dict(ch.options)
         tuned = {"main": ch.as_dict()}
         if main_prec != "fp64" and not args.no_fp64_compare:
             cf = autotune.tune(wl.models, wl.chain_model, "fp64", seed=seed, stream=stream, cache=None)
             k_fp64 = cf.delay_k
             tuned["fp64"] = cf.as_dict()
-    r = time_path(wl, main_prec, args, stream, seed, world, local_rank, delay_k=k_main)
+    r = time_path(wl, main_prec, args, stream, seed, world, local_rank, delay_k=k_main, peaks=peaks,
+                  options=opt_main)
     ens, st = r["ens"], r["st"]
     props_step = wl.proposals_per_sweep()
     # end to end through the public API with host buffers: fields in (pinned host),
@@ -384,15 +459,15 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
     dg = None
     cores = os.cpu_count() or 1
     if rank == 0 and not args.no_oracle_check:
-        worst, n = oracle_dg(wl, ens, cores)
-        dg = {"max_abs_dG_vs_oracle": worst, "chains_checked": n,
-              "what": "working G(0) after the timed sweeps vs the FP64 oracle's G(0) on the same fields"}
+        dg = oracle_checks(wl, ens, cores)
     ens.close()
     fp64 = None
     if main_prec != "fp64" and not args.no_fp64_compare:
-        rf = time_path(wl, "fp64", args, stream, seed, world, local_rank, delay_k=k_fp64)
+        rf = time_path(wl, "fp64", args, stream, seed, world, local_rank, delay_k=k_fp64, peaks=peaks)
+        dg64 = oracle_checks(wl, rf["ens"], cores) if (rank == 0 and not args.no_oracle_check) else None
         rf["ens"].close()
         fp64 = {"value": rf["value"], "unit": UNIT, "ms_per_step": rf["ms_step"], "delay_k": k_fp64,
+                "accuracy": dg64,
                 "roofline": rf["roofline"],
                 "critical_chain_ms": {k: round(rf["st"][k], 3) for k in ("ms_update", "ms_wrap", "ms_stab")},
                 "prec_green_max": rf["st"]["prec_green_max"], "prec_green_mean": rf["st"]["prec_green_mean"]}
@@ -408,12 +483,13 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32+f64", "mixed": "f32x2+f64", "mixed_tc": "bf16-split+f32x2+f64"}[main_prec],
             "data": "synthetic (seeded Philox fields, random-init Markov chains)",
             "config": {"workload": wl.name, "chains": wl.n_chains, "precision": main_prec,
-                       "delay_k": k_main, "n_wrap": 10, "autotune": tuned,
+                       "delay_k": k_main, "run_options": opt_main, "n_wrap": 10, "autotune": tuned,
                        "l2": "resident state > L2 (per-chain G, UDV storage and workspace, "
                              f"{ens_bytes(wl, main_prec) / 1e9:.2f} GB); no flush"},
             "sweeps_per_s": 1000.0 / r["ms_step"] * world,
             "accept_rate": st["accepted"] / st["proposals"],
             "accuracy": dg,
+            "peaks": peaks,
             "prec_green_max": st["prec_green_max"], "prec_green_mean": st["prec_green_mean"],
             "critical_chain_ms": {k: round(st[k], 3) for k in ("ms_update", "ms_wrap", "ms_stab", "ms_measure")},
             "critical_chain_detail_ms": dict(zip(("ratio_precompute", "accept_scan", "update_vectors", "flushes",

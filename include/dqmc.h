@@ -52,30 +52,41 @@ typedef enum {
   DQMC_ECUDA = 3,     /* a CUDA call failed (message in dqmc_last_error)       */
   DQMC_EUNSTABLE = 4, /* stabilisation failed, or max|G_wrap - G_fresh|
                          exceeded dqmc_run_opts.unstable_threshold             */
-  DQMC_ETIMEOUT = 5,  /* reserved: a bounded device wait gave up               */
+  DQMC_ETIMEOUT = 5,  /* a bounded device wait gave up (the tensor-core products
+                         of DQMC_PREC_MIXED_TC wait on their copies and MMAs) */
   DQMC_ESTATE = 6     /* the call is not valid in the context's state          */
 } dqmc_status;
 
 typedef enum { DQMC_FIELD_ISING = 1, DQMC_FIELD_HS4 = 2 } dqmc_field_type;
 
-/* Arithmetic of the working Green function, wraps and delayed updates.  The
- * stabilisation (B-chain products, pivoted QR, T update, (1 + UDV)^-1 and
- * log|det|) is FP64 in every mode.
- *   DQMC_PREC_FP64: plain FP64.
- *   DQMC_PREC_FP32: plain FP32 between stabilisations.  Round-off grows by the
- *     condition number of the unstabilised slice product (Sec. 2.3), so the
- *     wrapped G can drift far from the fresh one at strong coupling; the
- *     precision monitor of dqmc_sweep reports it.
- *   DQMC_PREC_MIXED: the working G and the update vectors are float pairs
- *     (hi + lo, about 48 significant bits) computed with error-free
- *     transformations on the FP32 pipes; the dense products of the
- *     stabilisation (B chain, T update, Q^T Q, T T^T, Q Y) are float-pair
- *     products; the pivoted QR, the LU and the solves are FP64.
- *   DQMC_PREC_MIXED_TC: as DQMC_PREC_MIXED, with the N x N x N products (wraps
- *     and the stabilisation products) as exact-split BF16 tensor-core products
- *     (seven 8-bit digits per operand, digit diagonals accumulated exactly in
- *     FP32, recombined in float pairs).  Needs extra device memory for the
- *     digit planes. */
+/* Arithmetic of each precision mode.  The scales D of the UDV chains (which
+ * reach e^100 and more) are FP64 in every mode.
+ *   DQMC_PREC_FP64: everything in FP64: working G, wraps, delayed updates, the
+ *     B-chain products, the pivoted QR, the T update, (1 + UDV)^-1 and log|det|
+ *     (Sec. 2.3).
+ *   DQMC_PREC_FP32: working G, wraps and delayed updates in plain FP32; the
+ *     stabilisation in FP64 as above.  Round-off grows by the condition number of
+ *     the unstabilised slice product (Sec. 2.3), so at strong coupling the wrapped
+ *     G drifts far from the fresh one; the precision monitor reports it.
+ *   DQMC_PREC_MIXED: float pairs (hi + lo, about 48 significant bits, error-free
+ *     transformations on the FP32 pipes) for the working G, the wraps and the
+ *     delayed updates, and also for the stabilisation: the B-chain and T-update
+ *     products, the Householder QR (pivot chosen in FP64 on the FP64-scaled column
+ *     norms), Q^T Q, T T^T, the LU of the middle matrix and the solves, with the
+ *     FP64 scales D kept apart.  This departs from an FP64 stabilisation: the
+ *     float-pair products accumulate about 42 bits, and the stable G then differs
+ *     from an FP64 recompute by up to ~30x the FP64 round-off amplified by the
+ *     conditioning (measured: 1e-9 at U = 4 - 6, beta = 4 - 8, n_wrap = 10 on
+ *     equilibrated fields; up to 2e-6 on i.i.d. fields at U = 6, beta = 8, where
+ *     FP64 itself moves by 3e-8 between n_wrap = 10 and 5).  The wrapped G between
+ *     stabilisations drifts ~25x further than on the FP64 path (monitor).
+ *   DQMC_PREC_MIXED_TC: as DQMC_PREC_MIXED, with every N x N x N product (wraps,
+ *     B chain, T update, Q^T Q, T T^T, Q Y) an exact-split BF16 product on the
+ *     tensor cores (tcgen05: seven 8-bit digits per operand, digit diagonals
+ *     accumulated exactly in FP32 tensor memory, recombined in float pairs, about
+ *     55 bits), so the products are as accurate as FP64 ones; QR, LU and solves
+ *     stay float pairs.  Needs device memory for the digit planes and half of the
+ *     tensor memory of each SM while a sweep runs. */
 typedef enum {
   DQMC_PREC_FP64 = 0,
   DQMC_PREC_FP32 = 1,
@@ -108,7 +119,14 @@ typedef struct {
   int32_t meas_last;          /*   (upward tau = 1..L, downward tau-1 = L-1..0)    */
   uint64_t seed;              /* Philox key (seed_lo, seed_hi ^ chain)             */
   double unstable_threshold;  /* > 0: DQMC_EUNSTABLE when prec_green_max exceeds it*/
-  int64_t spin_limit;         /* reserved, 0                                       */
+  int64_t spin_limit;         /* SM cycles before a bounded device wait gives up
+                                 (DQMC_ETIMEOUT); 0: about one second            */
+  int32_t tc_min_sites;       /* DQMC_PREC_MIXED_TC: chains of fewer sites use the
+                                 float-pair SIMT products (0: 96, where the tensor-
+                                 core product overtakes them on GB300)            */
+  int32_t dd_tile;            /* float-pair SIMT products: output tiles of 48 x 48
+                                 (3) or 64 x 64 (4) per CTA; 0: the one that pads
+                                 the matrix least                                 */
 } dqmc_run_opts;
 
 /* Statistics of one dqmc_sweep call, over all chains (Sec. 4.5 "info" file:
@@ -150,13 +168,28 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
 dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats_or_null);
 
 /* Equal-time Green function G^flavor(0) of one chain between sweeps (Eq.
- * Green_eq).  fresh = 0: the library's working G (FP64 or the mixed path's FP32
- * values widened); fresh = 1: recomputed from the fields through the FP64 UDV
- * chain (Sec. 2.3).  out: N x N doubles, host (out_is_device = 0) or device.
+ * Green_eq).  fresh = 0: the library's working G (FP64, or the FP32 / float-pair
+ * values of the reduced-precision modes widened to FP64); fresh = 1: recomputed
+ * from the fields through the FP64 UDV chain (Sec. 2.3).  out: N x N doubles, host (out_is_device = 0) or device.
  * logdet_out / sign_out (nullable): log|det(1 + B(beta,0))| and its sign from
  * the last stable recompute of that flavor. */
 dqmc_status dqmc_greens(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t fresh, double* out,
                         int32_t out_is_device, double* logdet_out, int32_t* sign_out);
+
+/* Equal-time Green function G^flavor(tau) of one chain on its current fields,
+ * wrapped in the context's working precision the way the upward pass of a sweep
+ * carries it between stabilisations when no proposal is accepted (Sec. 2.3, the
+ * wrapped Green function whose drift the "Precision Green" monitor measures;
+ * Algorithm 1, wrapgrup): the stable G(tau0) at the last stabilisation point
+ * tau0 = n_wrap floor(tau / n_wrap), from the right chain B(tau0,0) and the
+ * stored left chain B(beta,tau0)^T in the working precision's stabilisation
+ * arithmetic, followed by tau - tau0 wraps G <- B_t G B_t^-1.  Call it between
+ * sweeps (the stored chain then holds the left chain).  tau in [0, L]; out: N x N
+ * doubles, host (out_is_device = 0) or device.  The chain's fields, working G
+ * and stored chain are left as they are.  Errors: DQMC_EINVAL, DQMC_ECUDA,
+ * DQMC_EUNSTABLE (singular middle matrix). */
+dqmc_status dqmc_greens_tau(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t tau, double* out,
+                            int32_t out_is_device);
 
 /* Sign-weighted sums of the energy estimator since dqmc_init (Sec. 6.1
  * observables in the U n_up n_dn form):
@@ -198,6 +231,34 @@ dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* 
  * DQMC_EUNSTABLE if a recompute meets a singular matrix. */
 dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_phase, double* out, int32_t* sign,
                              double* prec);
+
+/* Time-displaced correlation functions of every chain's current configuration
+ * per class of site pairs: the lattice-resolved quantities that ObserT collects
+ * (Sec. 5.2; Algorithm 1, the tau measurement at the end of a sweep), for the two
+ * flavors of the spin-z decoupling (flavor 0 up, flavor 1 down; two-flavor
+ * models only).  G^s(tau,0), G^s(0,tau) and G^s(tau,tau) are wrapped and
+ * re-stabilised exactly as in dqmc_measure_tau (FP64), and with
+ * n^s_x(tau) = 1 - G^s(tau,tau)_xx and X^s_xy = -G^s(0,tau)_yx G^s(tau,0)_xy
+ * Wick's theorem per configuration gives
+ *     sum_s <c_xs(tau) c^+_ys(0)> = sum_s G^s(tau,0)_xy
+ *     <S^z_x(tau) S^z_y(0)> = [(n^0_x(tau) - n^1_x(tau)) (n^0_y(0) - n^1_y(0)) + X^0_xy + X^1_xy] / 4
+ *     <n_x(tau) n_y(0)>     = (n^0_x(tau) + n^1_x(tau)) (n^0_y(0) + n^1_y(0)) + X^0_xy + X^1_xy
+ *     n_tau       chain c measures tau = 0 .. min(n_tau, L_c); 0 <= n_tau <= max L
+ *     pair_class  host, per model [n_sites][n_sites] int32 (models concatenated):
+ *                 class of the pair (x, y) in [0, n_class[m]), or -1 to skip it
+ *     n_class     host [n_models], each >= 1
+ * Outputs (host):
+ *     out  [n_chains][n_tau + 1][max over models of n_class][3]: per class the
+ *          sums over its pairs of the three expectation values above
+ *          (unweighted); rows tau > L_c and classes beyond the chain's model's
+ *          n_class are 0
+ *     sign [n_chains]: sign of the configuration's weight (product of the
+ *          flavors' det signs)
+ * The chains are left as they are.  Errors: DQMC_EINVAL (one-flavor model, a
+ * class outside [-1, n_class), n_tau out of range), DQMC_ENOMEM, DQMC_ECUDA,
+ * DQMC_EUNSTABLE. */
+dqmc_status dqmc_measure_tau_corr(dqmc_ctx* ctx, int32_t n_tau, const int32_t* pair_class, const int32_t* n_class,
+                                  double* out, int32_t* sign);
 
 /* Equal-time correlation functions of every chain's current configuration (the
  * equal-time observables of Sec. 5.2 and the correlation functions of Sec. 6,
@@ -264,11 +325,13 @@ dqmc_status dqmc_set_fields(dqmc_ctx* ctx, const int8_t* in, uint64_t rng_counte
  * caller's device buffers, and its scratch is one device array of this library
  * (about 1 MiB, held by every GPU that loads the library until exit).
  *   Inputs (device): E_dev [n_flavors][N][N] = exp(-dtau K^s) row-major;
- *     vertex_site_dev [M_V]; vertex_sign_dev [n_flavors][M_V];
- *     fields_dev [L][M_V] int8 (+-1, or -2,-1,1,2 for DQMC_FIELD_HS4).
+ *     vertex_site_dev [M_V]: distinct sites in [0, N) (the kernel checks this
+ *     before it uses them; a violation gives sign 0, log|det| 0 and a G of
+ *     NaNs); vertex_sign_dev [n_flavors][M_V]; fields_dev [L][M_V] int8 (+-1,
+ *     or -2,-1,1,2 for DQMC_FIELD_HS4).
  *   Outputs (device): G_out_dev [n_flavors][N][N]; logdet_out_dev [n_flavors]
  *     and sign_out_dev [n_flavors] (nullable; sign 0 marks a singular
- *     stabilisation).
+ *     stabilisation or invalid vertex sites).
  * Limits: N <= 64, n_flavors <= 2; larger sizes return DQMC_EINVAL before any
  * device work.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

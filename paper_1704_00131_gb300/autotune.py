@@ -1,12 +1,17 @@
 """Autotuner of the sweep's launch parameters on this GPU.
 
-For a batch of chains (models and the chain -> model map) it picks
-* the product kernel family of the reduced-precision path: float-pair SIMT
-  register tiles ("mixed") or exact-split BF16 tensor-core tiles ("mixed_tc");
-  the FP64 path has one family ("fp64");
-* the rank k of the delayed updates (accepted flips per flush), which sets the
-  shape of the flush product (N x k times k x N) and the shared memory the
-  delayed vectors take, hence how many CTAs share an SM.
+For a batch of chains (models and the chain -> model map) it picks, in two
+rounds:
+1. the product kernel family of the reduced-precision path: float-pair SIMT
+   register tiles ("mixed") or exact-split BF16 products on the tensor cores
+   ("mixed_tc"; the FP64 path has one family, "fp64"), together with the rank k
+   of the delayed updates (accepted flips per flush), which sets the shape of the
+   flush product (N x k times k x N) and the shared memory the delayed vectors
+   take, hence how many CTAs share an SM;
+2. for the winner, the tile options: the output tile of the float-pair SIMT
+   products (48 x 48 or 64 x 64 per CTA: `dd_tile` 3 or 4) and, with the
+   tensor cores, the lattice size from which chains use them (`tc_min_sites`:
+   all chains, or the default crossover).
 
 Each candidate runs one untimed sweep of the whole batch, then one sweep timed
 with CUDA events on the launching stream; the fastest candidate wins.  All
@@ -28,6 +33,8 @@ import numpy as np
 DEFAULT_DELAYS = (8, 16, 24, 32)
 FAMILIES = {"mixed": ("mixed", "mixed_tc"), "mixed_tc": ("mixed", "mixed_tc"), "fp64": ("fp64",),
             "fp32": ("fp32",)}
+DD_TILES = (3, 4)
+TC_MIN_SITES = (1, 0)   # every chain on the tensor cores; the library's default crossover
 
 
 @dataclass
@@ -35,12 +42,23 @@ class Choice:
     precision: str
     delay_k: int
     ms: float
-    timings: list = field(default_factory=list)   # [(precision, delay_k, ms)]
+    timings: list = field(default_factory=list)   # [(precision, delay_k, options, ms)]
     cached: bool = False
+    options: dict = field(default_factory=dict)   # run options: dd_tile, tc_min_sites
 
     def as_dict(self) -> dict:
-        return {"precision": self.precision, "delay_k": self.delay_k, "ms": self.ms,
+        return {"precision": self.precision, "delay_k": self.delay_k, "ms": self.ms, "options": dict(self.options),
                 "timings": [list(t) for t in self.timings], "cached": self.cached}
+
+
+def option_candidates(precision: str) -> list:
+    """Tile options tried for the winner of the first round."""
+    if precision not in ("mixed", "mixed_tc"):
+        return []
+    out = [{"dd_tile": t} for t in DD_TILES]
+    if precision == "mixed_tc":
+        out += [{"tc_min_sites": m} for m in TC_MIN_SITES]
+    return out
 
 
 def candidates(precision: str, delays=DEFAULT_DELAYS) -> list:
@@ -57,13 +75,15 @@ def candidates(precision: str, delays=DEFAULT_DELAYS) -> list:
 
 
 def choose(timings) -> tuple:
-    """The fastest (precision, delay_k, ms); ties go to the earlier candidate."""
+    """The fastest (precision, delay_k, options, ms) of entries (p, k, ms) or
+    (p, k, options, ms); ties go to the earlier candidate."""
     best = None
-    for p, k, ms in timings:
+    for t in timings:
+        p, k, opt, ms = (t[0], t[1], {}, t[2]) if len(t) == 3 else t
         if not np.isfinite(ms) or ms <= 0:
             continue
-        if best is None or ms < best[2]:
-            best = (p, k, ms)
+        if best is None or ms < best[3]:
+            best = (p, k, dict(opt), ms)
     if best is None:
         raise RuntimeError("no candidate ran")
     return best
@@ -97,7 +117,8 @@ class Cache:
         d = self._load().get(device, {}).get(key)
         if d is None:
             return None
-        return Choice(d["precision"], int(d["delay_k"]), float(d["ms"]), [tuple(t) for t in d["timings"]], True)
+        return Choice(d["precision"], int(d["delay_k"]), float(d["ms"]), [tuple(t) for t in d["timings"]], True,
+                      dict(d.get("options", {})))
 
     def put(self, device: str, key: str, choice: Choice):
         data = self._load()
@@ -109,13 +130,13 @@ class Cache:
         os.replace(tmp, self.path)
 
 
-def time_candidate(models, chain_model, precision: str, delay_k: int, seed: int, stream=None) -> float:
+def time_candidate(models, chain_model, precision: str, delay_k: int, seed: int, stream=None, **options) -> float:
     """Milliseconds of one sweep of the batch (after one untimed sweep)."""
     import torch
 
     from . import dqmc
     st = stream if stream is not None else torch.cuda.current_stream()
-    ens = dqmc.Ensemble(models, chain_model, precision=precision, delay_k=delay_k, seed=seed, stream=st)
+    ens = dqmc.Ensemble(models, chain_model, precision=precision, delay_k=delay_k, seed=seed, stream=st, **options)
     try:
         ens.sweep(1, stats=False)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -146,9 +167,12 @@ def tune(models, chain_model, precision: str = "mixed", delays=DEFAULT_DELAYS, s
     run = timer or time_candidate
     timings = []
     for p, k in candidates(precision, delays):
-        timings.append((p, k, float(run(models, chain_model, p, k, seed, stream))))
-    p, k, ms = choose(timings)
-    ch = Choice(p, k, ms, timings)
+        timings.append((p, k, {}, float(run(models, chain_model, p, k, seed, stream))))
+    p, k, opt, ms = choose(timings)
+    for o in option_candidates(p):
+        timings.append((p, k, o, float(run(models, chain_model, p, k, seed, stream, **o))))
+    p, k, opt, ms = choose(timings)
+    ch = Choice(p, k, ms, timings, False, opt)
     if cache is not None:
         cache.put(device, key, ch)
     return ch

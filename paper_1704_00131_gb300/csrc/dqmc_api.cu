@@ -92,6 +92,12 @@ std::vector<double> expm_symmetric(int n, const std::vector<double>& w, const st
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Site count from which chains of a DQMC_PREC_MIXED_TC context run their N^3
+// products on the tensor cores (smaller ones keep the float-pair SIMT tiles).
+constexpr int kDefaultTcMinSites = 96;
+int tc_min_sites(const dqmc_run_opts& o) { return o.tc_min_sites > 0 ? o.tc_min_sites : kDefaultTcMinSites; }
+
+
 struct ModelHost {
   dqmc_model_desc d;
   int ld = 0;
@@ -104,6 +110,9 @@ struct ModelHost {
   float *E32 = nullptr, *Einv32 = nullptr;
   float *Edd = nullptr, *Einvdd = nullptr;  // (hi, lo) pairs
   int* site_d = nullptr;
+  // split-product planes of the constant propagators (tensor-core products only)
+  void* cpl[dqmc::kMaxFlavors][5] = {};
+  int* cex[dqmc::kMaxFlavors][5] = {};
 };
 
 }  // namespace
@@ -252,12 +261,37 @@ dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
   if ((st = upload(ctx, &M.ident, ident.data(), ident.size()))) return st;
   if ((st = upload(ctx, &M.site_d, M.site.data(), M.site.size()))) return st;
   if ((st = upload(ctx, &M.vsign_d, M.vsign.data(), M.vsign.size()))) return st;
+  if (ctx->opts.precision == DQMC_PREC_MIXED_TC && N >= tc_min_sites(ctx->opts)) {
+    // digit planes of e^-dtau K and e^+dtau K as the left and right factors of the
+    // wraps and of the B chain, split once per model (Sec. 3.1: the hopping
+    // propagator is a constant of the model)
+    struct { int which, right, tr; bool inv; } sets[5] = {{dqmc::kCpEA, 0, 0, false},
+                                                           {dqmc::kCpEtA, 0, 1, false},
+                                                           {dqmc::kCpEiA, 0, 0, true},
+                                                           {dqmc::kCpEiB, 1, 0, true},
+                                                           {dqmc::kCpEB, 1, 0, false}};
+    const size_t mat = (size_t)N * ld;
+    for (int f = 0; f < nfl; ++f)
+      for (const auto& q : sets) {
+        void* p = nullptr;
+        int* e = nullptr;
+        CUDA_TRY(ctx, cudaMalloc(&p, dqmc::const_plane_bytes(N, q.right)));
+        ctx->model_allocs.push_back(p);
+        CUDA_TRY(ctx, cudaMalloc((void**)&e, sizeof(int) * dqmc::const_plane_exps(N, q.right)));
+        ctx->model_allocs.push_back(e);
+        const float* X = (q.inv ? M.Einvdd : M.Edd) + 2 * f * mat;
+        CUDA_TRY(ctx, dqmc::launch_const_planes(X, N, ld, q.right, q.tr, p, e, ctx->stream));
+        M.cpl[f][q.which] = p;
+        M.cex[f][q.which] = e;
+      }
+  }
   return DQMC_OK;
 }
 
 // Per-chain device memory, carved from one arena.  Returns the bytes needed
 // (ptrs filled when base != nullptr).
-size_t chain_layout(const ModelHost& M, int precision, int delay_k, unsigned char* base, ChainDev* C) {
+size_t chain_layout(const ModelHost& M, int precision, int delay_k, unsigned char* base, ChainDev* C,
+                    int tc_min = 1) {
   const int N = M.d.n_sites, ld = M.ld, nfl = M.d.n_flavors, nst = M.d.L / M.d.n_wrap;
   const size_t rs = precision == DQMC_PREC_FP32 ? sizeof(float) : sizeof(double);  // FP64 or float pairs
   size_t off = 0;
@@ -286,12 +320,9 @@ size_t chain_layout(const ModelHost& M, int precision, int delay_k, unsigned cha
     if (C) C->work[s] = (double*)p;
     p = take((size_t)2 * ld * sizeof(int));
     if (C) C->iwork[s] = (int*)p;
-    if (precision == DQMC_PREC_MIXED_TC) {
-      // BF16 digit planes: kDig x (roundup(N,64) + roundup(N,32)) x roundup(max(N,k),16)
-      const int kmax = N > delay_k ? N : delay_k;
-      const size_t kp = (size_t)((kmax + 15) / 16 * 16);
-      const size_t elems = (size_t)7 * (size_t)(((N + 63) / 64) * 64 + ((N + 31) / 32) * 32) * kp;
-      p = take(elems * 2);
+    if (precision == DQMC_PREC_MIXED_TC && N >= tc_min) {
+      // BF16 digit planes of the split tensor-core products (N x N x N at most)
+      p = take(dqmc::plane_bytes(N, N));
       if (C) C->planes[s] = p;
     }
   }
@@ -319,6 +350,10 @@ void fill_model_fields(const ModelHost& M, ChainDev& C) {
     C.Einv32[s] = M.Einv32 + s * mat;
     C.Edd[s] = M.Edd + 2 * s * mat;
     C.Einvdd[s] = M.Einvdd + 2 * s * mat;
+    for (int q = 0; q < 5; ++q) {
+      C.cpl[s][q] = M.cpl[s][q];
+      C.cex[s][q] = M.cex[s][q];
+    }
   }
   C.site = M.site_d;
   C.vsign = M.vsign_d;
@@ -337,6 +372,20 @@ dqmc_status download_chains(dqmc_ctx* ctx) {
   return sync_check(ctx);
 }
 
+// DQMC_ETIMEOUT with the first wait that gave up in each flavor of chain C.
+dqmc_status timeout_message(dqmc_ctx* ctx, const ChainDev& C) {
+  std::string m;
+  for (int s = 0; s < C.nfl; ++s) {
+    const int* w = C.wait_where[s];
+    char b[200];
+    snprintf(b, sizeof(b), "; flavor %d: kind %d at chunk %d of %d in product %d (barrier %08x %08x)", s, w[0], w[1],
+             w[2], w[3], (unsigned)w[5], (unsigned)w[4]);
+    m += b;
+  }
+  return fail(ctx, DQMC_ETIMEOUT, "chain %u: a bounded wait of the tensor-core products gave up%s", C.chain_id,
+              m.c_str());
+}
+
 // Fields in place -> left chain, G(0), sign of every chain.
 dqmc_status initial_fill(dqmc_ctx* ctx) {
   const int n = (int)ctx->chains_h.size();
@@ -345,8 +394,10 @@ dqmc_status initial_fill(dqmc_ctx* ctx) {
   CUDA_TRY(ctx, dqmc::launch_finalize_init(ctx->chains_d, n, ctx->stream));
   dqmc_status st = download_chains(ctx);
   if (st) return st;
-  for (const ChainDev& C : ctx->chains_h)
+  for (const ChainDev& C : ctx->chains_h) {
+    if (C.error & 2) return timeout_message(ctx, C);
     if (C.error) return fail(ctx, DQMC_EUNSTABLE, "chain %u: singular matrix in the stabilisation", C.chain_id);
+  }
   return DQMC_OK;
 }
 
@@ -369,6 +420,14 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
   if (opts->precision < DQMC_PREC_FP64 || opts->precision > DQMC_PREC_MIXED_TC) {
     *out = ctx.release();
     return fail(*out, DQMC_EINVAL, "unknown precision %d", opts->precision);
+  }
+  if (opts->spin_limit < 0 || opts->tc_min_sites < 0) {
+    *out = ctx.release();
+    return fail(*out, DQMC_EINVAL, "spin_limit and tc_min_sites must be >= 0");
+  }
+  if (opts->dd_tile != 0 && opts->dd_tile != 3 && opts->dd_tile != 4) {
+    *out = ctx.release();
+    return fail(*out, DQMC_EINVAL, "dd_tile must be 0, 3 or 4");
   }
   if (opts->delay_k < 1 || opts->delay_k > 64) {
     *out = ctx.release();
@@ -409,7 +468,8 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
   size_t total = 0;
   for (int i = 0; i < n_chains; ++i) {
     offs[i] = total;
-    total += chain_layout(c->models[chain_model[i]], opts->precision, opts->delay_k, nullptr, nullptr);
+    total += chain_layout(c->models[chain_model[i]], opts->precision, opts->delay_k, nullptr, nullptr,
+                          tc_min_sites(*opts));
   }
   if (cudaMalloc((void**)&c->arena, total) != cudaSuccess) {
     *out = ctx.release();
@@ -421,10 +481,12 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
   for (int i = 0; i < n_chains; ++i) {
     ChainDev& C = c->chains_h[i];
     const ModelHost& M = c->models[chain_model[i]];
-    chain_layout(M, opts->precision, opts->delay_k, c->arena + offs[i], &C);
+    chain_layout(M, opts->precision, opts->delay_k, c->arena + offs[i], &C, tc_min_sites(*opts));
     fill_model_fields(M, C);
     C.chain_id = (uint32_t)i;
     C.sign = 1;
+    C.wait_cycles = opts->spin_limit;
+    C.dd_tile = opts->dd_tile;
     if (fields_or_null) {
       const size_t nf = (size_t)M.d.L * M.d.n_vertices;
       for (size_t q = 0; q < nf; ++q) {
@@ -458,13 +520,24 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
   CUDA_TRY(c, cudaMalloc((void**)&c->scratch, sizeof(double) * c->nfl * c->maxN * c->maxN));
   CUDA_TRY(c, cudaEventCreate(&c->ev0));
   CUDA_TRY(c, cudaEventCreate(&c->ev1));
-  c->smem = dqmc::sweep_smem_bytes(c->maxN, c->maxld, c->maxMV, opts->delay_k, opts->precision);
   {
-    // delayed vectors A, B in shared memory when they fit beside the rest
+    // the split tensor-core products stage their operands in a region of the
+    // dynamic shared memory; in the sweep it doubles as the delayed vectors A, B,
+    // kept in shared memory when they fit beside the rest
+    const int umma = opts->precision == DQMC_PREC_MIXED_TC;
+    const size_t base = dqmc::sweep_smem_bytes(c->maxN, c->maxld, c->maxMV, opts->delay_k, opts->precision);
     const size_t rs = c->kprec == DQMC_PREC_FP32 ? sizeof(float) : sizeof(double);
     const size_t ab = (size_t)2 * opts->delay_k * c->maxld * rs;
-    c->ab_smem = (c->smem + ab <= 200 * 1024) ? 1 : 0;
-    c->smem_sweep = c->smem + (c->ab_smem ? ab : 0);
+    c->smem = base + (umma ? dqmc::smem_tail(0, umma) : 0);
+    c->ab_smem = (base + dqmc::smem_tail(ab, umma) <= 200 * 1024) ? 1 : 0;
+    c->smem_sweep = base + dqmc::smem_tail(c->ab_smem ? ab : 0, umma);
+    if (umma) {
+      // every CTA of these kernels holds half of the SM's tensor
+      // memory (256 of 512 columns): at least 78 KB of shared memory per CTA keeps
+      // three of them from sharing an SM, so an allocation never waits
+      c->smem = std::max<size_t>(c->smem, 78 * 1024);
+      c->smem_sweep = std::max<size_t>(c->smem_sweep, 78 * 1024);
+    }
   }
   if (!fields_or_null) CUDA_TRY(c, dqmc::launch_init_fields(c->chains_d, n_chains, opts->seed, 0, 0, c->stream));
   return initial_fill(c);
@@ -535,6 +608,10 @@ dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats)
   S.mean_sign = n_sweeps ? sign_sum / ((double)n_sweeps * n) : 0.0;
   S.ms_total = ms;
   *stats = S;
+  if (err & 2) {
+    for (const ChainDev& C : ctx->chains_h)
+      if (C.error & 2) return timeout_message(ctx, C);
+  }
   if (err) return fail(ctx, DQMC_EUNSTABLE, "singular matrix in the stabilisation");
   if (ctx->opts.unstable_threshold > 0.0 && S.prec_green_max > ctx->opts.unstable_threshold)
     return fail(ctx, DQMC_EUNSTABLE, "max|G_wrap - G_fresh| = %.3e exceeds %.3e", S.prec_green_max,
@@ -569,6 +646,24 @@ dqmc_status dqmc_greens(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t fr
   return DQMC_OK;
 }
 
+dqmc_status dqmc_greens_tau(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t tau, double* out,
+                            int32_t out_is_device) {
+  if (!ctx) return DQMC_EINVAL;
+  if (chain < 0 || chain >= (int)ctx->chains_h.size() || flavor < 0 || flavor >= ctx->nfl || !out)
+    return fail(ctx, DQMC_EINVAL, "chain or flavor out of range, or null output");
+  const ChainDev& H = ctx->chains_h[chain];
+  if (tau < 0 || tau > H.L) return fail(ctx, DQMC_EINVAL, "tau must be in [0, %d]", H.L);
+  const int N = H.N;
+  dqmc::set_smem_bytes(ctx->smem);
+  CUDA_TRY(ctx, dqmc::launch_green_tau(ctx->chains_d, chain, ctx->nfl, ctx->kprec, tau, ctx->scratch, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->scratch + (size_t)flavor * N * N, sizeof(double) * N * N,
+                                out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+  dqmc_status st = download_chains(ctx);
+  if (st) return st;
+  if (ctx->chains_h[chain].error) return fail(ctx, DQMC_EUNSTABLE, "singular matrix in the stabilisation");
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas) {
   if (!ctx) return DQMC_EINVAL;
   if (!out || !sign_sum || !n_meas) return fail(ctx, DQMC_EINVAL, "null output");
@@ -583,13 +678,93 @@ dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* 
   return DQMC_OK;
 }
 
-dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_phase, double* out, int32_t* sign,
-                             double* prec) {
-  if (!ctx) return DQMC_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// Pair classes per model as CSR lists (pairs x * N + y sorted by class, then
+// by x, y) and the per-chain offsets into them; rejects classes outside
+// [-1, n_class).
+struct ClassLists {
+  std::vector<int> csr, pairs, ccsr, cpairs, cncls;
+  int max_cls = 0;
+};
+
+dqmc_status build_class_lists(dqmc_ctx* ctx, const int32_t* pair_class, const int32_t* n_class, ClassLists& L) {
+  const int nm = (int)ctx->models.size(), nch = (int)ctx->chains_h.size();
+  std::vector<int> mcsr(nm), mpairs(nm);
+  size_t coff = 0;
+  for (int m = 0; m < nm; ++m) {
+    const int N = ctx->models[m].d.n_sites, nc = n_class[m];
+    if (nc < 1) return fail(ctx, DQMC_EINVAL, "model %d: n_class < 1", m);
+    L.max_cls = nc > L.max_cls ? nc : L.max_cls;
+    const int32_t* cl = pair_class + coff;
+    std::vector<int> cnt(nc + 1, 0);
+    for (int e = 0; e < N * N; ++e) {
+      if (cl[e] < -1 || cl[e] >= nc) return fail(ctx, DQMC_EINVAL, "model %d: pair class %d out of range", m, cl[e]);
+      if (cl[e] >= 0) ++cnt[cl[e] + 1];
+    }
+    for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
+    mcsr[m] = (int)L.csr.size();
+    mpairs[m] = (int)L.pairs.size();
+    L.csr.insert(L.csr.end(), cnt.begin(), cnt.end());
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    L.pairs.resize(L.pairs.size() + cnt[nc]);
+    for (int e = 0; e < N * N; ++e)
+      if (cl[e] >= 0) L.pairs[mpairs[m] + fill[cl[e]]++] = e;
+    coff += (size_t)N * N;
+  }
+  L.ccsr.resize(nch);
+  L.cpairs.resize(nch);
+  L.cncls.resize(nch);
+  for (int c = 0; c < nch; ++c) {
+    const int m = ctx->chain_model[c];
+    L.ccsr[c] = mcsr[m];
+    L.cpairs[c] = mpairs[m];
+    L.cncls[c] = n_class[m];
+  }
+  if (L.pairs.empty()) L.pairs.push_back(0);
+  return DQMC_OK;
+}
+
+// Device copy of the class lists: one int buffer [csr | pairs | ccsr | cpairs | cncls].
+struct ClassListsDev {
+  int* buf = nullptr;
+  const int *csr = nullptr, *pairs = nullptr, *ccsr = nullptr, *cpairs = nullptr, *cncls = nullptr;
+  ~ClassListsDev() { cudaFree(buf); }
+};
+
+dqmc_status upload_class_lists(dqmc_ctx* ctx, const ClassLists& L, ClassListsDev& D) {
+  const size_t nch = L.ccsr.size();
+  const size_t n = L.csr.size() + L.pairs.size() + 3 * nch;
+  if (cudaMalloc((void**)&D.buf, sizeof(int) * n) != cudaSuccess) {
+    D.buf = nullptr;
+    cudaGetLastError();
+    return fail(ctx, DQMC_ENOMEM, "no device memory for the pair classes");
+  }
+  std::vector<int> h;
+  h.reserve(n);
+  h.insert(h.end(), L.csr.begin(), L.csr.end());
+  h.insert(h.end(), L.pairs.begin(), L.pairs.end());
+  h.insert(h.end(), L.ccsr.begin(), L.ccsr.end());
+  h.insert(h.end(), L.cpairs.begin(), L.cpairs.end());
+  h.insert(h.end(), L.cncls.begin(), L.cncls.end());
+  CUDA_TRY(ctx, cudaMemcpyAsync(D.buf, h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  D.csr = D.buf;
+  D.pairs = D.csr + L.csr.size();
+  D.ccsr = D.pairs + L.pairs.size();
+  D.cpairs = D.ccsr + nch;
+  D.cncls = D.cpairs + nch;
+  return DQMC_OK;
+}
+
+// The time-displaced measurement shared by dqmc_measure_tau (sums) and
+// dqmc_measure_tau_corr (class-resolved correlations, tc.part set).
+dqmc_status run_tau_measure(dqmc_ctx* ctx, int32_t n_tau, const double* site_phase, double* out, int32_t* sign,
+                            double* prec, const dqmc::TauCorrArgs& tc) {
   int maxL = 0;
   for (const ChainDev& C : ctx->chains_h) maxL = C.L > maxL ? C.L : maxL;
-  if (n_tau < 0 || n_tau > maxL || !out || !sign)
-    return fail(ctx, DQMC_EINVAL, "n_tau outside 0..%d, or null output", maxL);
+  if (n_tau < 0 || n_tau > maxL) return fail(ctx, DQMC_EINVAL, "n_tau outside 0..%d", maxL);
   const int nch = (int)ctx->chains_h.size(), nfl = ctx->nfl, pld = ctx->maxN;
   std::vector<size_t> moff(ctx->models.size() + 1, 0);
   for (size_t m = 0; m < ctx->models.size(); ++m) moff[m + 1] = moff[m] + ctx->models[m].d.n_sites;
@@ -634,9 +809,9 @@ dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_ph
         cudaSuccess) { st = fail(ctx, DQMC_ECUDA, "phase upload failed"); break; }
     dqmc::set_smem_bytes(ctx->smem);
     cudaError_t e = dqmc::launch_tau_measure(ctx->chains_d, nch, nfl, n_tau, ph_d, pld, ctx->tau_work, tw_stride,
-                                             obs_d, prec_d, sg_d, ctx->stream);
+                                             obs_d, prec_d, sg_d, tc, ctx->stream);
     if (e != cudaSuccess) { st = fail(ctx, DQMC_ECUDA, "tau measurement launch: %s", cudaGetErrorString(e)); break; }
-    if (cudaMemcpyAsync(out, obs_d, sizeof(double) * nobs, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+    if ((out && cudaMemcpyAsync(out, obs_d, sizeof(double) * nobs, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) ||
         cudaMemcpyAsync(sign, sg_d, sizeof(int) * nch * nfl, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
         cudaMemcpyAsync(prec_h.data(), prec_d, sizeof(double) * prec_h.size(), cudaMemcpyDeviceToHost,
                         ctx->stream) != cudaSuccess) { st = fail(ctx, DQMC_ECUDA, "download failed"); break; }
@@ -660,73 +835,85 @@ dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_ph
   return DQMC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+dqmc_status dqmc_measure_tau(dqmc_ctx* ctx, int32_t n_tau, const double* site_phase, double* out, int32_t* sign,
+                             double* prec) {
+  if (!ctx) return DQMC_EINVAL;
+  if (!out || !sign) return fail(ctx, DQMC_EINVAL, "null output");
+  return run_tau_measure(ctx, n_tau, site_phase, out, sign, prec, dqmc::TauCorrArgs{});
+}
+
+dqmc_status dqmc_measure_tau_corr(dqmc_ctx* ctx, int32_t n_tau, const int32_t* pair_class, const int32_t* n_class,
+                                  double* out, int32_t* sign) {
+  if (!ctx) return DQMC_EINVAL;
+  if (!pair_class || !n_class || !out || !sign) return fail(ctx, DQMC_EINVAL, "null argument");
+  if (ctx->nfl != 2) return fail(ctx, DQMC_EINVAL, "correlation functions need the two flavors of the spin-z decoupling");
+  int maxL = 0;
+  for (const ChainDev& C : ctx->chains_h) maxL = C.L > maxL ? C.L : maxL;
+  if (n_tau < 0 || n_tau > maxL) return fail(ctx, DQMC_EINVAL, "n_tau outside 0..%d", maxL);
+  ClassLists L;
+  dqmc_status st = build_class_lists(ctx, pair_class, n_class, L);
+  if (st) return st;
+  ClassListsDev D;
+  if ((st = upload_class_lists(ctx, L, D))) return st;
+  const int nch = (int)ctx->chains_h.size();
+  const size_t npart = (size_t)nch * (n_tau + 1) * 2 * L.max_cls * 2;
+  const size_t ndens = (size_t)nch * (n_tau + 1) * 2 * ctx->maxN;
+  const size_t nout = (size_t)nch * (n_tau + 1) * L.max_cls * 3;
+  double* work = nullptr;
+  if (cudaMalloc((void**)&work, sizeof(double) * (npart + ndens + nout)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DQMC_ENOMEM, "no device memory for the time-displaced correlations");
+  }
+  dqmc::TauCorrArgs tc;
+  tc.csr_all = D.csr;
+  tc.pairs_all = D.pairs;
+  tc.chain_csr = D.ccsr;
+  tc.chain_pairs = D.cpairs;
+  tc.chain_ncls = D.cncls;
+  tc.max_cls = L.max_cls;
+  tc.part = work;
+  tc.dens = work + npart;
+  tc.dens_ld = ctx->maxN;
+  double* out_d = work + npart + ndens;
+  std::vector<int32_t> sg2((size_t)nch * 2);
+  st = run_tau_measure(ctx, n_tau, nullptr, nullptr, sg2.data(), nullptr, tc);
+  if (!st) {
+    cudaError_t e = dqmc::launch_tau_corr_combine(ctx->chains_d, nch, n_tau, tc, out_d, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, out_d, sizeof(double) * nout, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = fail(ctx, DQMC_ECUDA, "time-displaced correlations: %s", cudaGetErrorString(e));
+  }
+  cudaFree(work);
+  if (st) return st;
+  for (int c = 0; c < nch; ++c) sign[c] = sg2[2 * c] * sg2[2 * c + 1];
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_measure_corr(dqmc_ctx* ctx, const int32_t* pair_class, const int32_t* n_class, double* out,
                               int32_t* sign) {
   if (!ctx) return DQMC_EINVAL;
   if (!pair_class || !n_class || !out || !sign) return fail(ctx, DQMC_EINVAL, "null argument");
   if (ctx->nfl != 2) return fail(ctx, DQMC_EINVAL, "correlation functions need the two flavors of the spin-z decoupling");
-  const int nm = (int)ctx->models.size(), nch = (int)ctx->chains_h.size();
-  // per model: class offsets and the pairs sorted by class (then by x, y)
-  std::vector<int> csr, pairs, mcsr(nm), mpairs(nm);
-  int max_cls = 0;
-  size_t coff = 0;
-  for (int m = 0; m < nm; ++m) {
-    const int N = ctx->models[m].d.n_sites, nc = n_class[m];
-    if (nc < 1) return fail(ctx, DQMC_EINVAL, "model %d: n_class < 1", m);
-    max_cls = nc > max_cls ? nc : max_cls;
-    const int32_t* cl = pair_class + coff;
-    std::vector<int> cnt(nc + 1, 0);
-    for (int e = 0; e < N * N; ++e) {
-      if (cl[e] < -1 || cl[e] >= nc) return fail(ctx, DQMC_EINVAL, "model %d: pair class %d out of range", m, cl[e]);
-      if (cl[e] >= 0) ++cnt[cl[e] + 1];
-    }
-    for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
-    mcsr[m] = (int)csr.size();
-    mpairs[m] = (int)pairs.size();
-    csr.insert(csr.end(), cnt.begin(), cnt.end());
-    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-    pairs.resize(pairs.size() + cnt[nc]);
-    for (int e = 0; e < N * N; ++e)
-      if (cl[e] >= 0) pairs[mpairs[m] + fill[cl[e]]++] = e;
-    coff += (size_t)N * N;
-  }
-  std::vector<int> ccsr(nch), cpairs(nch), cncls(nch);
-  for (int c = 0; c < nch; ++c) {
-    const int m = ctx->chain_model[c];
-    ccsr[c] = mcsr[m];
-    cpairs[c] = mpairs[m];
-    cncls[c] = n_class[m];
-  }
-  if (pairs.empty()) pairs.push_back(0);
-  int *csr_d = nullptr, *pairs_d = nullptr, *meta_d = nullptr;
+  const int nch = (int)ctx->chains_h.size();
+  ClassLists L;
+  dqmc_status st = build_class_lists(ctx, pair_class, n_class, L);
+  if (st) return st;
+  ClassListsDev D;
+  if ((st = upload_class_lists(ctx, L, D))) return st;
   double* out_d = nullptr;
-  auto cleanup = [&]() {
-    cudaFree(csr_d);
-    cudaFree(pairs_d);
-    cudaFree(meta_d);
-    cudaFree(out_d);
-  };
-  const size_t nout = (size_t)nch * max_cls * 4;
-  if (cudaMalloc((void**)&csr_d, sizeof(int) * csr.size()) != cudaSuccess ||
-      cudaMalloc((void**)&pairs_d, sizeof(int) * pairs.size()) != cudaSuccess ||
-      cudaMalloc((void**)&meta_d, sizeof(int) * 3 * nch) != cudaSuccess ||
-      cudaMalloc((void**)&out_d, sizeof(double) * nout) != cudaSuccess) {
+  const size_t nout = (size_t)nch * L.max_cls * 4;
+  if (cudaMalloc((void**)&out_d, sizeof(double) * nout) != cudaSuccess) {
     cudaGetLastError();
-    cleanup();
     return fail(ctx, DQMC_ENOMEM, "no device memory for the correlation functions");
   }
-  dqmc_status st = DQMC_OK;
   do {
-    if (cudaMemcpyAsync(csr_d, csr.data(), sizeof(int) * csr.size(), cudaMemcpyHostToDevice, ctx->stream) ||
-        cudaMemcpyAsync(pairs_d, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, ctx->stream) ||
-        cudaMemcpyAsync(meta_d, ccsr.data(), sizeof(int) * nch, cudaMemcpyHostToDevice, ctx->stream) ||
-        cudaMemcpyAsync(meta_d + nch, cpairs.data(), sizeof(int) * nch, cudaMemcpyHostToDevice, ctx->stream) ||
-        cudaMemcpyAsync(meta_d + 2 * nch, cncls.data(), sizeof(int) * nch, cudaMemcpyHostToDevice, ctx->stream)) {
-      st = fail(ctx, DQMC_ECUDA, "upload failed");
-      break;
-    }
-    cudaError_t e = dqmc::launch_corr(ctx->chains_d, nch, ctx->kprec, csr_d, pairs_d, meta_d, meta_d + nch,
-                                      meta_d + 2 * nch, max_cls, out_d, ctx->stream);
+    cudaError_t e = dqmc::launch_corr(ctx->chains_d, nch, ctx->kprec, D.csr, D.pairs, D.ccsr, D.cpairs, D.cncls,
+                                      L.max_cls, out_d, ctx->stream);
     if (e != cudaSuccess) { st = fail(ctx, DQMC_ECUDA, "correlation launch: %s", cudaGetErrorString(e)); break; }
     if (cudaMemcpyAsync(out, out_d, sizeof(double) * nout, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess) {
       st = fail(ctx, DQMC_ECUDA, "download failed");
@@ -734,7 +921,7 @@ dqmc_status dqmc_measure_corr(dqmc_ctx* ctx, const int32_t* pair_class, const in
     }
     st = download_chains(ctx);
   } while (false);
-  cleanup();
+  cudaFree(out_d);
   if (st) return st;
   for (int c = 0; c < nch; ++c) sign[c] = ctx->chains_h[c].sign;
   return DQMC_OK;

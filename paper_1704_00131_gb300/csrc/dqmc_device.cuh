@@ -382,176 +382,19 @@ __device__ void cta_gemm_dd_r(int M, int Nc, int Kd, const dd* __restrict__ A, i
 }
 
 
-// --------------------------------------------------------------------------
-// Exact-split BF16 tensor-core products for float-pair operands (the scheme of
-// Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 2012, on BF16 tensor cores).
-// Each row of op(A) and each column of op(B) is scaled by a power of two and
-// cut into kDig balanced 8-bit digits, x = 2^e sum_t q_t 2^-8(t+1), |q_t| <= 128,
-// each exactly a BF16 number.  Digit products are integers of at most 2^14;
-// the pairs (t,u) with t + u = d share one FP32 accumulator, exact as long as
-// (d + 1) K 2^14 <= 2^24, i.e. for K segments of at most 144.  The kDig
-// partial sums of a segment are recombined in float-float arithmetic and
-// scaled back.  Digits t + u >= kDig (relative weight 2^-64) are dropped.
-// Products run on mma.sync.m16n8k16 (BF16 in, FP32 accumulate); the digit
-// planes live in a per-CTA global scratch (L2-resident).
-// --------------------------------------------------------------------------
-constexpr int kDig = 7;
-constexpr int kKSeg = 144;
+#include "dqmc_umma.cuh"
 
-__host__ __device__ inline int tc_pad(int n, int q) { return (n + q - 1) / q * q; }
-// bf16 elements of the digit planes of one CTA for sizes up to n and K up to kmax
-__host__ __device__ inline size_t tc_plane_elems(int n, int kmax) {
-  const int Kp = tc_pad(kmax, 16);
-  return (size_t)kDig * ((size_t)tc_pad(n, 64) + (size_t)tc_pad(n, 32)) * Kp;
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                               uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// |x| < 2^(e-1) for every element of a row or column whose largest |hi| is amax
-__device__ __forceinline__ int tc_exponent(float amax) { return amax > 0.f ? ilogbf(amax) + 2 : 0; }
-
-__device__ __forceinline__ void tc_digits(dd x, int e, __nv_bfloat16* out, size_t stride) {
-  float h = ldexpf(x.hi, -e), l = ldexpf(x.lo, -e);
-#pragma unroll
-  for (int t = 0; t < kDig; ++t) {
-    h *= 256.f;
-    l *= 256.f;
-    const float q = rintf(h);
-    out[(size_t)t * stride] = __float2bfloat16_rn(q);
-    const dd r = two_sum(h - q, l);
-    h = r.hi;
-    l = r.lo;
-  }
-}
-
-// C (+)= op(A) op(B), M x Nc, inner dimension Kd; float-pair operands.
-template <bool TA, bool TB, bool ACC>
-__device__ void gemm_tc(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B, int ldb,
-                        dd* __restrict__ C, int ldc, __nv_bfloat16* planes, int* expA, int* expB) {
-  const int Mp = tc_pad(M, 64), Np = tc_pad(Nc, 32), Kp = tc_pad(Kd, 16);
-  __nv_bfloat16* PA = planes;
-  __nv_bfloat16* PB = planes + (size_t)kDig * Mp * Kp;
-  const size_t sA = (size_t)Mp * Kp, sB = (size_t)Np * Kp;
-  const int tid = threadIdx.x;
-  // scale exponents: rows of op(A), columns of op(B); a warp per contiguous row,
-  // a thread per strided column, so that every read is coalesced
-  const int warp_id = tid >> 5, lane_id = tid & 31;
-  if (!TA) {
-    for (int m = warp_id; m < Mp; m += kThreads / 32) {
-      float amax = 0.f;
-      if (m < M)
-        for (int k = lane_id; k < Kd; k += 32) amax = fmaxf(amax, fabsf(A[(size_t)m * lda + k].hi));
-#pragma unroll
-      for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-      if (lane_id == 0) expA[m] = tc_exponent(amax);
-    }
-  } else {
-    for (int m = tid; m < Mp; m += kThreads) {
-      float amax = 0.f;
-      if (m < M)
-        for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(A[(size_t)k * lda + m].hi));
-      expA[m] = tc_exponent(amax);
-    }
-  }
-  if (TB) {
-    for (int n = warp_id; n < Np; n += kThreads / 32) {
-      float amax = 0.f;
-      if (n < Nc)
-        for (int k = lane_id; k < Kd; k += 32) amax = fmaxf(amax, fabsf(B[(size_t)n * ldb + k].hi));
-#pragma unroll
-      for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-      if (lane_id == 0) expB[n] = tc_exponent(amax);
-    }
-  } else {
-    for (int n = tid; n < Np; n += kThreads) {
-      float amax = 0.f;
-      if (n < Nc)
-        for (int k = 0; k < Kd; ++k) amax = fmaxf(amax, fabsf(B[(size_t)k * ldb + n].hi));
-      expB[n] = tc_exponent(amax);
-    }
-  }
-  __syncthreads();
-  // digit planes: PA[t][m][k], PB[t][n][k] (k contiguous), zero padded
-  for (size_t e = tid; e < sA; e += kThreads) {
-    const int m = (int)(e / Kp), k = (int)(e - (size_t)m * Kp);
-    dd x = {0.f, 0.f};
-    if (m < M && k < Kd) x = TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
-    tc_digits(x, expA[m], PA + e, sA);
-  }
-  for (size_t e = tid; e < sB; e += kThreads) {
-    const int n = (int)(e / Kp), k = (int)(e - (size_t)n * Kp);
-    dd x = {0.f, 0.f};
-    if (n < Nc && k < Kd) x = TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
-    tc_digits(x, expB[n], PB + e, sB);
-  }
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, cq = lane & 3;
-  const int wm = warp & 3, wn = warp >> 2;
-  for (int m0 = 0; m0 < Mp; m0 += 64)
-    for (int n0 = 0; n0 < Np; n0 += 32)
-      for (int nt = 0; nt < 2; ++nt) {
-        const int r0 = m0 + wm * 16, c0 = n0 + wn * 16 + nt * 8;
-        for (int ks = 0; ks < Kp; ks += kKSeg) {
-          float acc[kDig][4];
-#pragma unroll
-          for (int d = 0; d < kDig; ++d)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[d][q] = 0.f;
-          const int ke = min(Kp, ks + kKSeg);
-          for (int k0 = ks; k0 < ke; k0 += 16) {
-            // all fragments of this k-step first, then the 28 digit-pair products
-            uint32_t af[kDig][4], bf[kDig][2];
-#pragma unroll
-            for (int t = 0; t < kDig; ++t) {
-              const __nv_bfloat16* pa = PA + (size_t)t * sA + (size_t)(r0 + g) * Kp + k0 + 2 * cq;
-              af[t][0] = *reinterpret_cast<const uint32_t*>(pa);
-              af[t][1] = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp);
-              af[t][2] = *reinterpret_cast<const uint32_t*>(pa + 8);
-              af[t][3] = *reinterpret_cast<const uint32_t*>(pa + 8 * (size_t)Kp + 8);
-              const __nv_bfloat16* pb = PB + (size_t)t * sB + (size_t)(c0 + g) * Kp + k0 + 2 * cq;
-              bf[t][0] = *reinterpret_cast<const uint32_t*>(pb);
-              bf[t][1] = *reinterpret_cast<const uint32_t*>(pb + 8);
-            }
-#pragma unroll
-            for (int t = 0; t < kDig; ++t)
-#pragma unroll
-              for (int u = 0; t + u < kDig; ++u)
-                mma_bf16_16816(acc[t + u], af[t][0], af[t][1], af[t][2], af[t][3], bf[u][0], bf[u][1]);
-          }
-          // recombine the digit diagonals of this segment and add into C
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int i = r0 + g + (q >= 2 ? 8 : 0);
-            const int j = c0 + 2 * cq + (q & 1);
-            if (i < M && j < Nc) {
-              dd sum = {0.f, 0.f};
-#pragma unroll
-              for (int d = kDig - 1; d >= 0; --d) sum = dd_add(sum, {ldexpf(acc[d][q], -8 * (d + 2)), 0.f});
-              const int e = expA[i] + expB[j];
-              sum.hi = ldexpf(sum.hi, e);
-              sum.lo = ldexpf(sum.lo, e);
-              dd* cp = C + (size_t)i * ldc + j;
-              *cp = (ACC || ks > 0) ? dd_add(*cp, sum) : sum;
-            }
-          }
-        }
-      }
-  __syncthreads();
-}
-
+// tile: 3 (48 x 48 output tiles) or 4 (64 x 64); 0 picks the one with less
+// padding of max(M, Nc) (the autotuner may override it per context)
 template <bool TA, bool TB, bool ACC>
 __device__ void gemm_dd_tiles(int M, int Nc, int Kd, const dd* A, int lda, const dd* B, int ldb, dd* C, int ldc,
-                              dd* sm) {
-  const int n = M > Nc ? M : Nc;
-  const int p3 = (n + 47) / 48 * 48, p4 = (n + 63) / 64 * 64;
-  if (p3 < p4) cta_gemm_dd_r<TA, TB, 3, ACC>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
+                              dd* sm, int tile = 0) {
+  if (tile != 3 && tile != 4) {
+    const int n = M > Nc ? M : Nc;
+    const int p3 = (n + 47) / 48 * 48, p4 = (n + 63) / 64 * 64;
+    tile = (p3 < p4) ? 3 : 4;
+  }
+  if (tile == 3) cta_gemm_dd_r<TA, TB, 3, ACC>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
   else cta_gemm_dd_r<TA, TB, 4, ACC>(M, Nc, Kd, A, lda, B, ldb, C, ldc, sm);
 }
 
@@ -568,7 +411,8 @@ __device__ __forceinline__ void cta_copy(int N, int ld, const T* src, T* dst) {
 // Shared-memory layout of the sweep kernel.
 // --------------------------------------------------------------------------
 struct Smem {
-  double* gemm;     // 2*16*kGemmMaxTile doubles (also used by float / float-pair GEMMs)
+  double* gemm;     // kGemmRegionBytes: 2*16*kGemmMaxTile doubles of the SIMT GEMM panels (also
+                    // float / float-pair), or a staging buffer of the tensor-core products
   double* v;        // [ld] slice potential / exp factors
   double* ev;       // [ld]
   double* d;        // [ld] current diagonal of the effective G
@@ -586,20 +430,35 @@ struct Smem {
   int* qinv;        // [ld] position in the slice's visiting order of the vertex on site x (-1: none)
   int8_t* fnew;     // [MV]
   int8_t* fslice;   // [MV] fields of the current slice
-  int* expA;        // [roundup(ld,64)] row exponents of the split tensor-core products
-  int* expB;        // [roundup(ld,64)] column exponents
+  int* expA;        // [kExpLen(ld)] row exponents of the split tensor-core products
+  int* expB;        // [kExpLen(ld)] column exponents
   double* ab;       // delayed vectors A, B [2][k][ld] when they fit in shared memory
   int flavor;       // the CTA's flavor
   double* qred;     // [8][128] partial sums of the QR trailing update
+  Umma um;          // tensor-core products: barriers and TMEM slot, staging aliased with ab
+  int dd_tile;      // register tile of the float-pair SIMT products (0: by padding, 3, 4)
 };
 
 // The first kSmemCounterBytes of the dynamic shared memory hold thread 0's
 // cycle counters of the sweep kernel (fixed addresses, no registers).
 constexpr int kSmemCounterBytes = 16 * 8;
 
+// exponent entries per operand of the split products: rows padded to the tile height
+__host__ __device__ inline int exp_len(int ld) {
+  const int a = umma_pad(ld, kUmmaM), b = umma_pad(ld, kUmmaNT);
+  return a > b ? a : b;
+}
+
+// Shared memory of the fresh-G, measurement and adjoint kernels.  The sweep
+// kernel adds the delayed vectors at the end; with the tensor-core products
+// the same region (s.ab) holds their two staging buffers, which are only live
+// inside a product, never while delayed vectors are pending.
+constexpr int kGemmRegionBytes =
+    (2 * 16 * kGemmMaxTile * 8 > kUmmaStageBytes) ? 2 * 16 * kGemmMaxTile * 8 : kUmmaStageBytes;
+
 __host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
   size_t b = kSmemCounterBytes;
-  b += 2 * 16 * kGemmMaxTile * 8;
+  b += kGemmRegionBytes;
   b += 6 * (size_t)ld * 8;        // v, ev, d, hv, xdiag, spare
   b += 6 * (size_t)MV * 8;        // u2, delta, gam, Rs[2], Rp
   b += 8 * 8 + 32 * 8 + 32 * 4;   // xs, red, ired
@@ -608,15 +467,24 @@ __host__ __device__ inline size_t smem_bytes_for(int ld, int MV) {
   b += 2 * (size_t)MV + 16;       // fnew, fslice
   b = (b + 15) / 16 * 16;
   b += 8 * 128 * 8;               // qred
-  b += 2 * (size_t)((ld + 63) / 64 * 64) * 4;  // expA, expB
+  b += 2 * (size_t)exp_len(ld) * 4;  // expA, expB
+  b = (b + 15) / 16 * 16;
+  b += 128;                       // mbarriers and the TMEM slot of the tensor-core products
   return b;
+}
+// Bytes of the region at s.ab (start 128-byte aligned by carve_smem): the
+// delayed vectors, or the second and third staging buffers of the tensor-core
+// products (the first is the GEMM region).
+__host__ __device__ inline size_t smem_tail_bytes(size_t ab_bytes, bool umma) {
+  const size_t st = umma ? (size_t)(kUmmaStages - 1) * kUmmaStageBytes : 0;
+  return 128 + (ab_bytes > st ? ab_bytes : st);
 }
 
 __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   Smem s;
   base += kSmemCounterBytes;
   double* p = reinterpret_cast<double*>(base);
-  s.gemm = p; p += 2 * 16 * kGemmMaxTile;
+  s.gemm = p; p += kGemmRegionBytes / 8;
   s.v = p; p += ld;
   s.ev = p; p += ld;
   s.d = p; p += ld;
@@ -639,10 +507,25 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   s.fslice = bp; bp += MV + 16;
   const size_t off = ((size_t)(bp - reinterpret_cast<int8_t*>(base)) + 15) / 16 * 16;
   s.qred = reinterpret_cast<double*>(base + off);
-  const int le = (ld + 63) / 64 * 64;
+  const int le = exp_len(ld);
   s.expA = reinterpret_cast<int*>(s.qred + 8 * 128);
   s.expB = s.expA + le;
-  s.ab = reinterpret_cast<double*>(s.expB + le);
+  unsigned char* q = reinterpret_cast<unsigned char*>(s.expB + le);
+  q = base + (((size_t)(q - base) + 15) / 16 * 16);
+  s.um.bar = reinterpret_cast<uint64_t*>(q);                 // 2 kUmmaStages mbarriers
+  s.um.tmem_slot = reinterpret_cast<uint32_t*>(q + 16 * kUmmaStages);
+  s.um.err = nullptr;
+  s.um.where = nullptr;
+  s.um.calls = 0;
+  s.dd_tile = 0;
+  s.um.limit = kUmmaWaitCycles;
+  q += 128;
+  // base is 16-byte aligned (kSmemCounterBytes past the start); align s.ab to 128
+  const uintptr_t qa = (reinterpret_cast<uintptr_t>(q) + 127) & ~(uintptr_t)127;
+  s.ab = reinterpret_cast<double*>(qa);
+  s.um.stage[0] = reinterpret_cast<unsigned char*>(s.gemm);
+  for (int st = 1; st < kUmmaStages; ++st)
+    s.um.stage[st] = reinterpret_cast<unsigned char*>(qa) + (size_t)(st - 1) * kUmmaStageBytes;
   return s;
 }
 
@@ -650,11 +533,17 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
 // the chain has digit-plane scratch, the float-pair SIMT tiles otherwise.
 template <bool TA, bool TB, bool ACC>
 __device__ void gemm_dd(const ChainDev& C, int s, Smem& S, int M, int Nc, int Kd, const dd* A, int lda, const dd* B,
-                        int ldb, dd* Cm, int ldc) {
-  if (C.planes[s])
-    gemm_tc<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, (__nv_bfloat16*)C.planes[s], S.expA, S.expB);
-  else
-    gemm_dd_tiles<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, reinterpret_cast<dd*>(S.gemm));
+                        int ldb, dd* Cm, int ldc, int constA = -1, int constB = -1) {
+  if (C.planes[s]) {
+    // constA / constB: index of a prepared constant operand (kCpEA ...), -1: split here
+    const UmmaOperand cA = constA >= 0 ? UmmaOperand{(const __nv_bfloat16*)C.cpl[s][constA], C.cex[s][constA]}
+                                       : UmmaOperand{nullptr, nullptr};
+    const UmmaOperand cB = constB >= 0 ? UmmaOperand{(const __nv_bfloat16*)C.cpl[s][constB], C.cex[s][constB]}
+                                       : UmmaOperand{nullptr, nullptr};
+    gemm_umma<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, (__nv_bfloat16*)C.planes[s], S.expA, S.expB, S.um,
+                           cA, cB);
+  } else
+    gemm_dd_tiles<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, reinterpret_cast<dd*>(S.gemm), S.dd_tile);
 }
 
 // Slice potential v^s_i of slice tau (1-based) from global fields.
@@ -1002,7 +891,7 @@ __device__ inline void gemm_acc(int M, int Nc, int Kd, const double* A, int lda,
 }
 __device__ inline void gemm_acc(int M, int Nc, int Kd, const dd* A, int lda, const dd* B, int ldb, dd* C, int ldc,
                                 Smem& S) {
-  gemm_dd_tiles<false, false, true>(M, Nc, Kd, A, lda, B, ldb, C, ldc, reinterpret_cast<dd*>(S.gemm));
+  gemm_dd_tiles<false, false, true>(M, Nc, Kd, A, lda, B, ldb, C, ldc, reinterpret_cast<dd*>(S.gemm), S.dd_tile);
 }
 
 // P A = L U in place (unit L below the diagonal, rows interchanged whole);
@@ -1294,10 +1183,18 @@ __global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains,
   if (mode == 1 && c != out_chain) return;
   ChainDev& C = chains[c];
   Smem S = carve_smem(smem_raw, C.ld, C.MV);
+  // the working precision's tensor-core products need the CTA's tensor memory
+  const bool umma = std::is_same<Real, dd>::value && mode == 0 && C.planes[s] != nullptr;
+  S.um.err = &C.error;
+  S.dd_tile = C.dd_tile;
+  S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
+  S.um.where = C.wait_where[s];
+  if (umma) umma_alloc(S.um);
   double logdet;
   int sign;
   const int bad = (mode == 0) ? fill_left_chain_working<Real>(C, s, S, logdet, sign)
                               : fill_left_chain(C, s, S, logdet, sign);
+  if (umma) umma_free(S.um);
   if (bad) {
     if (threadIdx.x == 0) C.error = 1;
     return;
@@ -1318,6 +1215,75 @@ __global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains,
   if (threadIdx.x == 0) {
     C.logdet[s] = logdet;
     C.fresh_sign[s] = sign;
+  }
+}
+
+// Hopping and potential wraps of one slice (defined with the sweep pieces below).
+template <typename Real>
+__device__ void v_wrap(const ChainDev& C, Real* G, const double* v, double a, Smem& S);
+template <typename Real>
+__device__ void t_wrap(const ChainDev& C, int s, Real* G, Real* Gt, bool up, Smem& S);
+
+// G^s(tau) of one chain on its current fields as the upward pass of a sweep
+// holds it when every proposal of the slices tau0+1..tau is rejected (Sec. 2.3,
+// the wrapped Green function between stabilisations; Algorithm 1 wrapgrup):
+// the stable G(tau0) at the last stabilisation point tau0 = n_wrap floor(tau /
+// n_wrap), from the right chain B(tau0,0) built here and the stored left chain
+// B(beta,tau0)^T, in the working precision's stabilisation arithmetic, then
+// tau - tau0 wraps G <- E e^V G e^-V E^-1 in the working precision.  One CTA per
+// flavor; the stored chain, the working G and the fields are only read.  Uses
+// the work matrices W0..W8; out: [nfl][N][N] FP64.
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) green_tau_kernel(ChainDev* chains, int chain, int tau, double* out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ChainDev& C = chains[chain];
+  const int s = blockIdx.x;
+  if (s >= C.nfl) return;
+  Smem S = carve_smem(smem_raw, C.ld, C.MV);
+  S.flavor = s;
+  const int N = C.N, ld = C.ld, nw = C.nw, nst = C.L / nw;
+  const int j0 = tau / nw;
+  constexpr bool mixed = std::is_same<Real, dd>::value;
+  const bool umma = mixed && C.planes[s] != nullptr;
+  S.um.err = &C.error;
+  S.dd_tile = C.dd_tile;
+  S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
+  S.um.where = C.wait_where[s];
+  if (umma) umma_alloc(S.um);
+  int dq = 1;
+  for (int j = 1; j <= j0; ++j) {
+    const UDV src = (j == 1) ? ident_udv(C) : work_udv(C, s, dq);
+    dq = mixed ? chain_step_mixed(C, s, (j - 1) * nw, j * nw, false, src, S, nullptr)
+               : chain_step(C, s, (j - 1) * nw, j * nw, false, src, S);
+  }
+  const UDV R = (j0 == 0) ? ident_udv(C) : work_udv(C, s, dq);
+  const UDV Lf = (j0 >= nst) ? ident_udv(C) : slot_udv(C, s, j0);
+  double* Gf = wmat(C, s, 6);
+  double logdet;
+  int sg;
+  const int bad = mixed ? green_from_udv_mixed(C, s, R, Lf, Gf, logdet, sg, S)
+                        : green_from_udv(C, s, R, Lf, Gf, logdet, sg, S);
+  if (bad) {
+    if (umma) umma_free(S.um);
+    if (threadIdx.x == 0) C.error = 1;
+    return;
+  }
+  Real* G = reinterpret_cast<Real*>(wmat(C, s, 7));
+  Real* Gt = reinterpret_cast<Real*>(wmat(C, s, 8));
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    G[(size_t)x * ld + y] = from_d<Real>(Gf[(size_t)x * ld + y]);
+  }
+  __syncthreads();
+  for (int t = j0 * nw + 1; t <= tau; ++t) {
+    slice_potential_global(C, s, t, S.v);
+    v_wrap<Real>(C, G, S.v, +1.0, S);
+    t_wrap<Real>(C, s, G, Gt, true, S);
+  }
+  if (umma) umma_free(S.um);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    out[(size_t)s * N * N + e] = to_d(G[(size_t)x * ld + y]);
   }
 }
 
@@ -1378,8 +1344,8 @@ __device__ void t_wrap<dd>(const ChainDev& C, int s, dd* G, dd* Gt, bool up, Sme
   const int N = C.N, ld = C.ld;
   const dd* X = (const dd*)(up ? C.Edd[s] : C.Einvdd[s]);
   const dd* Y = (const dd*)(up ? C.Einvdd[s] : C.Edd[s]);
-  gemm_dd<false, false, false>(C, s, S, N, N, N, X, ld, G, ld, Gt, ld);
-  gemm_dd<false, false, false>(C, s, S, N, N, N, Gt, ld, Y, ld, G, ld);
+  gemm_dd<false, false, false>(C, s, S, N, N, N, X, ld, G, ld, Gt, ld, up ? kCpEA : kCpEiA, -1);
+  gemm_dd<false, false, false>(C, s, S, N, N, N, Gt, ld, Y, ld, G, ld, -1, up ? kCpEiB : kCpEB);
 }
 
 // G <- G + sum_m a_m b_m^T  (flush of the delayed rank-k update), a register-
@@ -1410,7 +1376,8 @@ template <>
 __device__ void flush_delayed<dd>(const ChainDev& C, dd* G, const dd* A, const dd* B, int nacc, Smem& S) {
   // a rank-k update (k <= 64): the float-pair SIMT tiles beat the split
   // tensor-core product, whose digit split and recombination cost O(N^2 k_dig)
-  gemm_dd_tiles<true, false, true>(C.N, C.N, nacc, A, C.ld, B, C.ld, G, C.ld, reinterpret_cast<dd*>(S.gemm));
+  gemm_dd_tiles<true, false, true>(C.N, C.N, nacc, A, C.ld, B, C.ld, G, C.ld, reinterpret_cast<dd*>(S.gemm),
+                                   S.dd_tile);
 }
 
 // Sequential single-field updates of one slice (Sec. 2.2.1) for this CTA's
@@ -1792,12 +1759,12 @@ __device__ int chain_step_mixed(const ChainDev& C, int s, int t1, int t2, bool l
         X[(size_t)x * ld + y] = dd_mul(X[(size_t)x * ld + y], evr[x]);
       }
       __syncthreads();
-      gemm_dd<false, false, false>(C, s, S, N, N, N, E, ld, X, ld, Y, ld);
+      gemm_dd<false, false, false>(C, s, S, N, N, N, E, ld, X, ld, Y, ld, kCpEA, -1);
       dd* t_ = X; X = Y; Y = t_;
     }
   } else {
     for (int t = t2; t >= t1 + 1; --t) {
-      gemm_dd<true, false, false>(C, s, S, N, N, N, E, ld, X, ld, Y, ld);
+      gemm_dd<true, false, false>(C, s, S, N, N, N, E, ld, X, ld, Y, ld, kCpEtA, -1);
       slice_potential_global(C, s, t, S.v);
       for (int x = threadIdx.x; x < N; x += kThreads) evr[x] = from_d<dd>(exp(S.v[x]));
       __syncthreads();
@@ -2044,6 +2011,14 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
   ChainDev& C = chains[c];
   Smem S = carve_smem(smem_raw, C.ld, C.MV);
   S.flavor = s;
+  // the split tensor-core products (float-pair path with digit planes) need the
+  // CTA's tensor memory for the whole sweep
+  const bool umma = std::is_same<Real, dd>::value && C.planes[s] != nullptr;
+  S.um.err = &C.error;
+  S.dd_tile = C.dd_tile;
+  S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
+  S.um.where = C.wait_where[s];
+  if (umma) umma_alloc(S.um);
   Real* G = (Real*)C.G[s];
   Real* Gt = (Real*)C.Gtmp[s];
   Real* A = P.ab_smem ? reinterpret_cast<Real*>(S.ab) : (Real*)C.dA[s];
@@ -2114,6 +2089,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
     }
   }
   cl.sync();
+  if (umma) umma_free(S.um);
   if (threadIdx.x == 0) {
     for (int q = 0; q < 4; ++q) C.cyc[s][q] += cyc[q];
     for (int q = 0; q < 8; ++q) C.cycd[s][q] += det[q];
@@ -2137,6 +2113,15 @@ static cudaError_t launch_fresh_green_t(ChainDev* chains, int n_chains, int nfl,
   cudaError_t e = set_smem((const void*)fresh_green_kernel<Real>, smem);
   if (e != cudaSuccess) return e;
   fresh_green_kernel<Real><<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, mode, out, out_chain);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+static cudaError_t launch_green_tau_t(ChainDev* chains, int chain, int nfl, size_t smem, int tau, double* out,
+                                      cudaStream_t st) {
+  cudaError_t e = set_smem((const void*)green_tau_kernel<Real>, smem);
+  if (e != cudaSuccess) return e;
+  green_tau_kernel<Real><<<nfl, kThreads, smem, st>>>(chains, chain, tau, out);
   return cudaGetLastError();
 }
 
@@ -2228,5 +2213,11 @@ cudaError_t launch_fresh_green_fp32(ChainDev* chains, int n_chains, int nfl, siz
                                     int out_chain, cudaStream_t st);
 cudaError_t launch_fresh_green_mixed(ChainDev* chains, int n_chains, int nfl, size_t smem, int mode, double* out,
                                      int out_chain, cudaStream_t st);
+cudaError_t launch_green_tau_fp64(ChainDev* chains, int chain, int nfl, size_t smem, int tau, double* out,
+                                  cudaStream_t st);
+cudaError_t launch_green_tau_fp32(ChainDev* chains, int chain, int nfl, size_t smem, int tau, double* out,
+                                  cudaStream_t st);
+cudaError_t launch_green_tau_mixed(ChainDev* chains, int chain, int nfl, size_t smem, int tau, double* out,
+                                   cudaStream_t st);
 
 }  // namespace dqmc

@@ -36,6 +36,11 @@ struct ChainDev {
   int* slot_detq[kMaxFlavors];    // [nst+1]
   double* work[kMaxFlavors];      // FP64 stabilisation workspace, kWorkMats matrices + vectors
   void* planes[kMaxFlavors];      // BF16 digit planes of the split tensor-core products (mixed path)
+  // digit planes and row exponents of the constant split operands, prepared once
+  // per model: kCpEA = E as left factor, kCpEtA = E^T left, kCpEiA = E^-1 left,
+  // kCpEiB = E^-1 right, kCpEB = E right (null without tensor-core products)
+  const void* cpl[kMaxFlavors][5];
+  const int* cex[kMaxFlavors][5];
   int* iwork[kMaxFlavors];        // [2*ld]
   uint32_t chain_id;
   int sign;                       // sign of the current weight (written by rank 0)
@@ -52,7 +57,13 @@ struct ChainDev {
   // last fresh log|det| and sign per flavor (written by greens/init kernels)
   double logdet[kMaxFlavors];
   int fresh_sign[kMaxFlavors];
-  int error;                      // nonzero: a numerical failure was detected
+  int error;                      // bit 0: a numerical failure; bit 1: a bounded device wait gave up
+  long long wait_cycles;          // SM cycles before a bounded device wait gives up
+  int dd_tile;                    // register tile of the float-pair SIMT products (0 by padding, 3, 4)
+  int wait_where[kMaxFlavors][6]; // first wait that gave up per flavor: kind (1 copy, 2 MMAs
+                                  // before a refill, 3 MMAs before the epilogue, 4 / 5 copy / MMAs
+                                  // at the end of a product), chunk (stage for 4, 5), chunks,
+                                  // product ordinal in the kernel, barrier word (low, high)
   // SM cycles spent per phase during the current dqmc_sweep call, per flavor:
   // 0 updates, 1 wraps (V and T), 2 stabilisation, 3 measurement
   int64_t cyc[kMaxFlavors][4];
@@ -63,6 +74,7 @@ struct ChainDev {
 };
 
 constexpr int kWorkMats = 10;     // N x ld FP64 matrices per flavor in `work`
+enum { kCpEA = 0, kCpEtA = 1, kCpEiA = 2, kCpEiB = 3, kCpEB = 4 };
 
 __host__ __device__ inline size_t slot_stride(int N, int ld) { return (size_t)2 * N * ld + ld; }
 __host__ __device__ inline size_t work_elems(int N, int ld) { return (size_t)kWorkMats * N * ld + 8 * (size_t)ld; }
@@ -85,8 +97,22 @@ cudaError_t launch_fresh_green(ChainDev* chains, int n_chains, int nfl, int prec
 cudaError_t launch_sweep(ChainDev* chains, const SweepParams& p, int nfl, int precision, size_t smem,
                          cudaStream_t st);
 size_t sweep_smem_bytes(int maxN, int maxld, int maxMV, int delay_k, int precision);
+// bytes of the shared-memory region behind the base (delayed vectors and/or the
+// staging buffers of the split tensor-core products)
+size_t smem_tail(size_t ab_bytes, int umma);
+// bytes of the BF16 digit planes of one CTA's split products up to N x N x kmax
+size_t plane_bytes(int N, int kmax);
+// digit planes of a constant N x N float-pair operand: as the left factor
+// (right = 0; tr = 1 for its transpose) or as the right factor (right = 1);
+// bytes of the planes and entries of the exponent vector
+size_t const_plane_bytes(int N, int right);
+int const_plane_exps(int N, int right);
+cudaError_t launch_const_planes(const void* X, int N, int ld, int right, int tr, void* planes, int* ex,
+                                cudaStream_t st);
 cudaError_t launch_copy_green(ChainDev* chains, int chain, int flavor, int precision, double* out,
                               cudaStream_t st);
+cudaError_t launch_green_tau(ChainDev* chains, int chain, int nfl, int precision, int tau, double* out,
+                             cudaStream_t st);
 void set_smem_bytes(size_t bytes);
 cudaError_t launch_energy_grad(ChainDev* chains, int n_cfg, int nfl, const double* eigvec, const double* eigval,
                                double* G0all, double* ework, double* gK, double* gU, double* eparts,
@@ -95,9 +121,25 @@ cudaError_t launch_finalize_init(ChainDev* chains, int n_chains, cudaStream_t st
 cudaError_t launch_corr(ChainDev* chains, int n_chains, int precision, const int* csr_all, const int* pairs_all,
                         const int* chain_csr, const int* chain_pairs, const int* chain_ncls, int max_cls,
                         double* out, cudaStream_t st);
+// Class lists and outputs of the time-displaced correlation functions (all
+// null / 0 when only the sums of dqmc_measure_tau are wanted).
+struct TauCorrArgs {
+  const int* csr_all = nullptr;      // per model: class offsets [n_class + 1] into its pair list
+  const int* pairs_all = nullptr;    // per model: pairs x * N + y sorted by class, then x, y
+  const int* chain_csr = nullptr;    // [n_chains] offset of the chain's model in csr_all
+  const int* chain_pairs = nullptr;  // [n_chains] offset of the chain's model in pairs_all
+  const int* chain_ncls = nullptr;   // [n_chains] number of classes of the chain's model
+  int max_cls = 0;
+  double* part = nullptr;            // [n_chains][n_tau+1][nfl][max_cls][2]
+  double* dens = nullptr;            // [n_chains][n_tau+1][nfl][dens_ld]
+  int dens_ld = 0;
+};
+
 cudaError_t launch_tau_measure(ChainDev* chains, int n_chains, int nfl, int n_tau, const double* phase,
                                int phase_ld, double* tw, size_t tw_stride, double* obs, double* prec, int* sign,
-                               cudaStream_t st);
+                               const TauCorrArgs& tc, cudaStream_t st);
+cudaError_t launch_tau_corr_combine(const ChainDev* chains, int n_chains, int n_tau, const TauCorrArgs& tc,
+                                    double* out, cudaStream_t st);
 cudaError_t launch_reset_stats(ChainDev* chains, int n_chains, cudaStream_t st);
 cudaError_t launch_logdet_grad(ChainDev* chains, int n_cfg, int nfl, const double* eigvec,
                                const double* eigval, double* gK, double* gU, double* Sacc,

@@ -116,6 +116,37 @@ size_t sweep_smem_bytes(int maxN, int maxld, int maxMV, int delay_k, int precisi
   return smem_bytes_for(maxld, maxMV);
 }
 
+size_t smem_tail(size_t ab_bytes, int umma) { return smem_tail_bytes(ab_bytes, umma != 0); }
+
+size_t plane_bytes(int N, int kmax) { return umma_plane_elems(N, kmax) * sizeof(__nv_bfloat16); }
+
+// Digit planes and row exponents of a constant operand of the split products
+// (one CTA): the left factor's rows (tiles of kUmmaM) or the right factor's
+// columns (tiles of kUmmaNT), laid out as gemm_umma stages them.
+__global__ void __launch_bounds__(kThreads) const_planes_kernel(const dd* X, int N, int ld, int right, int tr,
+                                                                __nv_bfloat16* P, int* ex) {
+  const int rows = right ? kUmmaNT : kUmmaM;
+  const int Rp = umma_pad(N, rows), Kp = umma_pad(N, kUmmaK);
+  // logical row r of the operand: row r of X, or column r (transpose / right factor)
+  const bool colwise = right ? !tr : tr;
+  if (colwise) umma_row_exponents<true>(N, N, X, ld, Rp, ex);
+  else umma_row_exponents<false>(N, N, X, ld, Rp, ex);
+  __syncthreads();
+  if (colwise) umma_planes<true>(N, N, X, ld, Rp, Kp, rows, ex, P);
+  else umma_planes<false>(N, N, X, ld, Rp, Kp, rows, ex, P);
+}
+
+size_t const_plane_bytes(int N, int right) {
+  return (size_t)kUmmaDig * umma_pad(N, right ? kUmmaNT : kUmmaM) * umma_pad(N, kUmmaK) * sizeof(__nv_bfloat16);
+}
+int const_plane_exps(int N, int right) { return umma_pad(N, right ? kUmmaNT : kUmmaM); }
+
+cudaError_t launch_const_planes(const void* X, int N, int ld, int right, int tr, void* planes, int* ex,
+                                cudaStream_t st) {
+  const_planes_kernel<<<1, kThreads, 0, st>>>((const dd*)X, N, ld, right, tr, (__nv_bfloat16*)planes, ex);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_fields(ChainDev* chains, int n_chains, uint64_t seed, int, int, cudaStream_t st) {
   init_fields_kernel<<<n_chains, kThreads, 0, st>>>(chains, n_chains, seed);
   return cudaGetLastError();
@@ -129,6 +160,13 @@ cudaError_t launch_fresh_green(ChainDev* chains, int n_chains, int nfl, int prec
   if (precision == 0) return launch_fresh_green_fp64(chains, n_chains, nfl, g_smem_bytes, mode, out, out_chain, st);
   if (precision == 1) return launch_fresh_green_fp32(chains, n_chains, nfl, g_smem_bytes, mode, out, out_chain, st);
   return launch_fresh_green_mixed(chains, n_chains, nfl, g_smem_bytes, mode, out, out_chain, st);
+}
+
+cudaError_t launch_green_tau(ChainDev* chains, int chain, int nfl, int precision, int tau, double* out,
+                             cudaStream_t st) {
+  if (precision == 0) return launch_green_tau_fp64(chains, chain, nfl, g_smem_bytes, tau, out, st);
+  if (precision == 1) return launch_green_tau_fp32(chains, chain, nfl, g_smem_bytes, tau, out, st);
+  return launch_green_tau_mixed(chains, chain, nfl, g_smem_bytes, tau, out, st);
 }
 
 cudaError_t launch_copy_green(ChainDev* chains, int chain, int flavor, int precision, double* out,

@@ -70,8 +70,26 @@ __global__ void __launch_bounds__(kThreads) fresh_green_noalloc_kernel(ChainDev 
     ident[(size_t)N * ld + (size_t)x * ld + y] = (x == y) ? 1.0 : 0.0;
   }
   for (int x = threadIdx.x; x < N; x += kThreads) ident[(size_t)2 * N * ld + x] = 1.0;
-  __syncthreads();
   Smem S = carve_smem(smem_raw, ld, C.MV);
+  // the vertex sites are caller device data the host cannot inspect: they must
+  // be distinct and in [0, N) (they index the slice potential in shared memory);
+  // otherwise the call returns sign 0, log|det| 0 and a G of NaNs
+  for (int x = threadIdx.x; x < N; x += kThreads) S.qinv[x] = 0;
+  __syncthreads();
+  int bad_site = 0;
+  for (int k = threadIdx.x; k < C.MV; k += kThreads) {
+    const int site = C.site[k];
+    if (site < 0 || site >= N) bad_site = 1;
+    else if (atomicAdd(&S.qinv[site], 1) != 0) bad_site = 1;
+  }
+  if (__syncthreads_or(bad_site)) {
+    for (int e = threadIdx.x; e < N * N; e += kThreads) out[(size_t)s * N * N + e] = __longlong_as_double(0x7ff8000000000000LL);
+    if (threadIdx.x == 0) {
+      if (logdet_out) logdet_out[s] = 0.0;
+      if (sign_out) sign_out[s] = 0;
+    }
+    return;
+  }
   double logdet = 0.0;
   int sign = 0;
   const int bad = left_chain_running(Cl, s, S, logdet, sign);

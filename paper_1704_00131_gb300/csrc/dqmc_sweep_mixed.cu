@@ -12,4 +12,9 @@ cudaError_t launch_fresh_green_mixed(ChainDev* chains, int n_chains, int nfl, si
   return launch_fresh_green_t<dd>(chains, n_chains, nfl, smem, mode, out, out_chain, st);
 }
 
+cudaError_t launch_green_tau_mixed(ChainDev* chains, int chain, int nfl, size_t smem, int tau, double* out,
+                                  cudaStream_t st) {
+  return launch_green_tau_t<dd>(chains, chain, nfl, smem, tau, out, st);
+}
+
 }  // namespace dqmc

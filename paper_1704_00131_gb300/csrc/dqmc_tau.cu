@@ -20,10 +20,19 @@ namespace dqmc {
 // Buffers: tw [n_chains][nfl][4][N][ld] (G(tau,0), G(0,tau), G(tau,tau), temp);
 // obs [n_chains][n_tau+1][nfl][3]; prec [n_chains][nfl][3] = (sum of element
 // means, max, events); sign [n_chains][nfl].
+//
+// With class lists (tc.part != nullptr) the flavor's CTA also writes, per tau and
+// per class k of the chain's model, the flavor's share of the time-displaced
+// correlation functions (the lattice-resolved ObserT quantities, Sec. 5.2):
+//   part[c][tau][s][k] = (sum_(x,y) in k G^s(tau,0)_xy,
+//                         sum_(x,y) in k X^s_xy),  X^s_xy = -G^s(0,tau)_yx G^s(tau,0)_xy,
+//   dens[c][tau][s][x] = 1 - G^s(tau,tau)_xx,
+// one thread per class walking the class's pairs in a fixed order; the flavors
+// are combined by tau_corr_combine_kernel.
 __global__ void __launch_bounds__(kThreads) tau_measure_kernel(ChainDev* chains, int n_chains, int n_tau,
                                                                const double* phase, int phase_ld, double* tw_all,
                                                                size_t tw_stride, double* obs, double* prec,
-                                                               int* sign_out) {
+                                                               int* sign_out, TauCorrArgs tc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nfl = chains[0].nfl;
   const int c = blockIdx.x / nfl, s = blockIdx.x % nfl;
@@ -122,6 +131,26 @@ __global__ void __launch_bounds__(kThreads) tau_measure_kernel(ChainDev* chains,
       const int x = e / N, y = e - x * N;
       cc -= ph[x] * ph[y] * G0t[(size_t)y * ld + x] * Gt0[(size_t)x * ld + y];
     }
+    if (tc.part) {
+      const int ncls = tc.chain_ncls[c];
+      const int* off = tc.csr_all + tc.chain_csr[c];
+      const int* pairs = tc.pairs_all + tc.chain_pairs[c];
+      double* pt = tc.part + (((size_t)c * (n_tau + 1) + tau) * nfl + s) * tc.max_cls * 2;
+      for (int k = threadIdx.x; k < tc.max_cls; k += kThreads) {
+        double gs = 0.0, xs = 0.0;
+        if (k < ncls)
+          for (int q = off[k]; q < off[k + 1]; ++q) {
+            const int x = pairs[q] / N, y = pairs[q] - (pairs[q] / N) * N;
+            const double gt0 = Gt0[(size_t)x * ld + y];
+            gs += gt0;
+            xs -= G0t[(size_t)y * ld + x] * gt0;
+          }
+        pt[2 * k] = gs;
+        pt[2 * k + 1] = xs;
+      }
+      double* dn = tc.dens + (((size_t)c * (n_tau + 1) + tau) * nfl + s) * tc.dens_ld;
+      for (int x = threadIdx.x; x < N; x += kThreads) dn[x] = 1.0 - Gtt[(size_t)x * ld + x];
+    }
     a = block_sum(a, S.red);
     cc = block_sum(cc, S.red);
     p = block_sum(p, S.red);
@@ -140,14 +169,62 @@ __global__ void __launch_bounds__(kThreads) tau_measure_kernel(ChainDev* chains,
   }
 }
 
+// Time-displaced correlation functions per class from the flavors' shares (two
+// flavors, spin-z decoupling, flavor 0 up and 1 down; Wick's theorem per
+// configuration with independent flavors), n^s_x(tau) = 1 - G^s(tau,tau)_xx:
+//   out[c][tau][k][0] = sum_s sum_(x,y) in k G^s(tau,0)_xy          (sum_s <c_xs(tau) c^+_ys(0)>)
+//   out[c][tau][k][1] = sum_(x,y) in k [(n^0_x(tau) - n^1_x(tau)) (n^0_y(0) - n^1_y(0)) + X^0_xy + X^1_xy] / 4
+//                                                                    (<S^z_x(tau) S^z_y(0)>)
+//   out[c][tau][k][2] = sum_(x,y) in k [(n^0_x(tau) + n^1_x(tau)) (n^0_y(0) + n^1_y(0)) + X^0_xy + X^1_xy]
+//                                                                    (<n_x(tau) n_y(0)>)
+// Rows tau > L_c and classes beyond the chain's model's count are 0.
+__global__ void tau_corr_combine_kernel(const ChainDev* chains, int n_chains, int n_tau, TauCorrArgs tc,
+                                        double* out) {
+  const int c = blockIdx.x / (n_tau + 1), tau = blockIdx.x % (n_tau + 1);
+  if (c >= n_chains) return;
+  const ChainDev& C = chains[c];
+  const int N = C.N, ncls = tc.chain_ncls[c];
+  const int* off = tc.csr_all + tc.chain_csr[c];
+  const int* pairs = tc.pairs_all + tc.chain_pairs[c];
+  const double* pt = tc.part + ((size_t)c * (n_tau + 1) + tau) * 2 * tc.max_cls * 2;
+  const double* dt = tc.dens + ((size_t)c * (n_tau + 1) + tau) * 2 * tc.dens_ld;
+  const double* d0 = tc.dens + ((size_t)c * (n_tau + 1)) * 2 * tc.dens_ld;
+  double* o = out + ((size_t)c * (n_tau + 1) + tau) * tc.max_cls * 3;
+  const bool live = tau <= C.L;
+  for (int k = threadIdx.x; k < tc.max_cls; k += blockDim.x) {
+    double g = 0.0, zz = 0.0, nn = 0.0;
+    if (live && k < ncls) {
+      const double X = pt[2 * k + 1] + pt[2 * tc.max_cls + 2 * k + 1];
+      g = pt[2 * k] + pt[2 * tc.max_cls + 2 * k];
+      for (int q = off[k]; q < off[k + 1]; ++q) {
+        const int x = pairs[q] / N, y = pairs[q] - (pairs[q] / N) * N;
+        const double nxu = dt[x], nxd = dt[tc.dens_ld + x], nyu = d0[y], nyd = d0[tc.dens_ld + y];
+        zz += (nxu - nxd) * (nyu - nyd);
+        nn += (nxu + nxd) * (nyu + nyd);
+      }
+      zz = 0.25 * (zz + X);
+      nn += X;
+    }
+    o[3 * k] = g;
+    o[3 * k + 1] = zz;
+    o[3 * k + 2] = nn;
+  }
+}
+
 cudaError_t launch_tau_measure(ChainDev* chains, int n_chains, int nfl, int n_tau, const double* phase,
                                int phase_ld, double* tw, size_t tw_stride, double* obs, double* prec, int* sign,
-                               cudaStream_t st) {
+                               const TauCorrArgs& tc, cudaStream_t st) {
   const size_t smem = get_smem_bytes();
   cudaError_t e = set_smem((const void*)tau_measure_kernel, smem);
   if (e != cudaSuccess) return e;
   tau_measure_kernel<<<n_chains * nfl, kThreads, smem, st>>>(chains, n_chains, n_tau, phase, phase_ld, tw,
-                                                             tw_stride, obs, prec, sign);
+                                                             tw_stride, obs, prec, sign, tc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tau_corr_combine(const ChainDev* chains, int n_chains, int n_tau, const TauCorrArgs& tc,
+                                    double* out, cudaStream_t st) {
+  tau_corr_combine_kernel<<<n_chains * (n_tau + 1), 128, 0, st>>>(chains, n_chains, n_tau, tc, out);
   return cudaGetLastError();
 }
 

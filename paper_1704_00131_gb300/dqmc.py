@@ -20,8 +20,9 @@ _LIB_PATH = os.path.join(_PKG, "libdqmc.so")
 DQMC_OK, DQMC_EINVAL, DQMC_ENOMEM, DQMC_ECUDA, DQMC_EUNSTABLE, DQMC_ETIMEOUT, DQMC_ESTATE = range(7)
 PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tc": 3}
 
-EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_measure", "dqmc_measure_tau", "dqmc_measure_corr", "dqmc_logdet_backward",
-            "dqmc_get_fields", "dqmc_set_fields", "dqmc_last_error", "dqmc_destroy"]
+EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_greens_tau", "dqmc_measure", "dqmc_measure_tau",
+            "dqmc_measure_tau_corr", "dqmc_measure_corr", "dqmc_logdet_backward", "dqmc_energy_backward", "dqmc_get_fields",
+            "dqmc_set_fields", "dqmc_green_fresh_noalloc", "dqmc_last_error", "dqmc_destroy"]
 
 
 class DqmcError(RuntimeError):
@@ -56,6 +57,8 @@ class RunOpts(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("unstable_threshold", ctypes.c_double),
         ("spin_limit", ctypes.c_int64),
+        ("tc_min_sites", ctypes.c_int32),
+        ("dd_tile", ctypes.c_int32),
     ]
 
 
@@ -103,10 +106,14 @@ def load() -> ctypes.CDLL:
     L.dqmc_sweep.restype = ctypes.c_int
     L.dqmc_greens.argtypes = [vp, i32, i32, i32, vp, i32, vp, vp]
     L.dqmc_greens.restype = ctypes.c_int
+    L.dqmc_greens_tau.argtypes = [vp, i32, i32, i32, vp, i32]
+    L.dqmc_greens_tau.restype = ctypes.c_int
     L.dqmc_measure.argtypes = [vp, vp, vp, vp]
     L.dqmc_measure.restype = ctypes.c_int
     L.dqmc_measure_tau.argtypes = [vp, i32, vp, vp, vp, vp]
     L.dqmc_measure_tau.restype = ctypes.c_int
+    L.dqmc_measure_tau_corr.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.dqmc_measure_tau_corr.restype = ctypes.c_int
     L.dqmc_measure_corr.argtypes = [vp, vp, vp, vp, vp]
     L.dqmc_measure_corr.restype = ctypes.c_int
     L.dqmc_logdet_backward.argtypes = [vp, i32, vp, i32, vp, vp, vp]
@@ -142,7 +149,8 @@ class Ensemble:
 
     def __init__(self, models: list[ModelSpec], chain_model, fields=None, precision: str = "fp64",
                  delay_k: int = 16, seed: int = 0, measure: bool = False, meas_first: int = 0,
-                 meas_last: int | None = None, unstable_threshold: float = 0.0, stream=None):
+                 meas_last: int | None = None, unstable_threshold: float = 0.0, stream=None, spin_limit: int = 0,
+                 tc_min_sites: int = 0, dd_tile: int = 0):
         self._lib = load()
         self._h = ctypes.c_void_p()
         self.models = list(models)
@@ -162,7 +170,7 @@ class Ensemble:
         self._descs = descs
         ml = max(m.L for m in self.models) if meas_last is None else meas_last
         self.opts = RunOpts(PREC[precision], int(delay_k), int(measure), int(meas_first), int(ml), int(seed),
-                            float(unstable_threshold), 0)
+                            float(unstable_threshold), int(spin_limit), int(tc_min_sites), int(dd_tile))
         fptr = None
         if fields is not None:
             packed = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int8).ravel() for f in fields]))
@@ -226,6 +234,21 @@ class Ensemble:
                                           ctypes.byref(ld), ctypes.byref(sg)))
         return out, ld.value, sg.value
 
+    def greens_tau(self, chain: int, flavor: int, tau: int, out=None):
+        """G^flavor(tau) of a chain, wrapped in the working precision from the last
+        stabilisation point tau0 <= tau with no accepted proposals (the drift probe
+        of the precision monitor), as a numpy array (or into a CUDA torch tensor)."""
+        if not 0 <= int(chain) < self.n_chains:
+            raise DqmcError(DQMC_EINVAL, f"chain {chain} out of range")
+        N = self.model_of(chain).N
+        if out is None:
+            G = np.zeros((N, N))
+            self._check(self._lib.dqmc_greens_tau(self._h, int(chain), int(flavor), int(tau), _p(G), 0))
+            return G
+        self._check(self._lib.dqmc_greens_tau(self._h, int(chain), int(flavor), int(tau),
+                                              ctypes.c_void_p(out.data_ptr()), 1))
+        return out
+
     def measure(self):
         n = self.n_chains
         out = np.zeros((n, 4))
@@ -267,6 +290,20 @@ class Ensemble:
         out = np.zeros((self.n_chains, int(nc.max()), 4))
         sg = np.zeros(self.n_chains, dtype=np.int32)
         self._check(self._lib.dqmc_measure_corr(self._h, _p(cls), _p(nc), _p(out), _p(sg)))
+        return out, sg
+
+    def measure_tau_corr(self, n_tau: int, pair_class, n_class):
+        """Time-displaced correlation sums per pair class of every chain's current
+        configuration: out[c, tau, k] = (sum_s <c_xs(tau) c^+_ys(0)>, <S^z_x(tau) S^z_y(0)>,
+        <n_x(tau) n_y(0)>) summed over the pairs (x, y) of class k; sign[c] = the
+        configuration's sign.  pair_class and n_class: one entry per model."""
+        cls = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.int32).ravel() for a in pair_class]))
+        nc = np.ascontiguousarray(n_class, dtype=np.int32)
+        if cls.size != sum(m.N * m.N for m in self.models) or nc.size != len(self.models):
+            raise DqmcError(DQMC_EINVAL, "one class map [N*N] and one class count per model")
+        out = np.zeros((self.n_chains, int(n_tau) + 1, int(nc.max()), 3))
+        sg = np.zeros(self.n_chains, dtype=np.int32)
+        self._check(self._lib.dqmc_measure_tau_corr(self._h, int(n_tau), _p(cls), _p(nc), _p(out), _p(sg)))
         return out, sg
 
     def get_fields(self):

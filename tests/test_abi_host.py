@@ -63,6 +63,18 @@ def test_invalid_model_rejected_before_any_device_work(lib):
     assert e.value.status == dqmc.DQMC_EINVAL
 
 
+def test_invalid_options_rejected_before_any_device_work(lib):
+    m = W.ModelSpec(W.square_lattice(2, 2), U=2.0, dtau=0.1, L=4, n_wrap=2)
+    for kw in ({"spin_limit": -1}, {"delay_k": 0}, {"delay_k": 65}):
+        with pytest.raises(dqmc.DqmcError) as e:
+            dqmc.Ensemble([m], [0], **kw)
+        assert e.value.status == dqmc.DQMC_EINVAL, kw
+
+
+def test_binding_lists_every_exported_entry_point(lib):
+    assert set(dqmc.EXPORTED) == declared_symbols()
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(dqmc, "_lib", None)
     monkeypatch.setattr(dqmc, "_LIB_PATH", str(tmp_path / "absent.so"))

@@ -6,10 +6,17 @@
   and seed.  Fields must agree bit for bit and G(0) to the path's tolerance (1e-10
   FP64, 1e-7 float pairs: the reduced-precision bar is 1e-6).
 * 32 chains of the 20x20, beta = 10, L = 200 workload with the split-BF16
-  tensor-core products and rank 32 (the autotuner's choice at N = 400): the oracle
-  needs minutes per G there, so the checks are properties that hold at any size:
-  the working G(0) after the sweep equals the FP64 recompute from the chain's
-  fields to 1e-6, the precision monitor stays below 1e-4, fields stay +-1.
+  tensor-core products and rank 32 (the autotuner's choice at N = 400): after one
+  sweep, the working G(0) and log|det| of two chains equal the FP64 oracle's
+  stable G(0) on the GPU's final fields (1e-7 float pairs); the FP64 path on one
+  chain of the same model to 1e-8 (at N = 400, beta = 10 two FP64 UDV chains with
+  different rounding orders agree to ~1e-9: the oracle's own G moves by that
+  much between n_wrap = 10 and 5); properties that hold at any size: the working
+  G(0) equals the library's FP64 recompute, the precision monitor stays below
+  1e-4, fields stay +-1.  (The oracle's own Markov chain would need minutes per
+  sweep at N = 400, so the trajectory is not replayed there.)
+* The honeycomb 6x6 workload (N = 72, beta = 10, L = 100, one FP64 chain): one
+  sweep replayed by the oracle, fields bit for bit and G(0) to 1e-10.
 """
 import threading
 
@@ -66,7 +73,23 @@ def test_256_chain_workload_sampled_chains_follow_the_oracle(dq, orc, precision)
     ens.close()
 
 
-def test_20x20_workload_properties(dq):
+def _oracle_greens(orc, m, fields_by_chain):
+    """The oracle's stable G(0), log|det| of both flavors per chain, on host threads."""
+    om = orc.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+    res = {}
+
+    def work(c, s):
+        res[(c, s)] = orc.green_udv(om, fields_by_chain[c], s, 0)
+
+    th = [threading.Thread(target=work, args=(c, s)) for c in fields_by_chain for s in (0, 1)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    return res
+
+
+def test_20x20_workload_against_the_oracle(dq, orc):
     wl = W.config_c5()
     ens = dq.Ensemble(wl.models, wl.chain_model, precision="mixed_tc", delay_k=32, seed=W.BASE_SEED)
     st = ens.sweep(1)
@@ -75,9 +98,47 @@ def test_20x20_workload_properties(dq):
     assert st["prec_green_max"] < 1e-4 and st["prec_green_mean"] < 1e-8
     f, _ = ens.get_fields()
     assert all(set(np.unique(x)) <= {-1, 1} for x in f)
+    ref = _oracle_greens(orc, wl.models[0], {0: f[0], 31: f[31]})
     for c in (0, 31):
         for s in (0, 1):
+            Go, ldo, sgo = ref[(c, s)]
             Gw, _, _ = ens.greens(c, s)
-            Gf, _, _ = ens.greens(c, s, fresh=True)
+            assert np.abs(Gw - Go).max() < 1e-7, (c, s)
+            Gf, ldf, sgf = ens.greens(c, s, fresh=True)
             assert np.abs(Gw - Gf).max() < 1e-6, (c, s)
+            assert np.abs(Gf - Go).max() < 1e-8, (c, s)
+            assert ldf == pytest.approx(ldo, rel=1e-10) and sgf == sgo
+    ens.close()
+
+
+def test_20x20_model_fp64_against_the_oracle(dq, orc):
+    wl = W.config_c5()
+    m = wl.models[0]
+    ens = dq.Ensemble([m], [0], precision="fp64", delay_k=32, seed=W.BASE_SEED)
+    st = ens.sweep(1)
+    assert 0 < st["accepted"] < st["proposals"] == 2 * m.L * m.N
+    f, _ = ens.get_fields()
+    ref = _oracle_greens(orc, m, {0: f[0]})
+    for s in (0, 1):
+        Go, ldo, sgo = ref[(0, s)]
+        Gw, ldw, sgw = ens.greens(0, s)
+        assert np.abs(Gw - Go).max() < 1e-8, s
+        assert ldw == pytest.approx(ldo, rel=1e-10) and sgw == sgo
+    ens.close()
+
+
+def test_honeycomb_6x6_beta10_trajectory(dq, orc):
+    wl = W.config_c2()
+    m = wl.models[0]
+    assert (m.N, m.L) == (72, 100)
+    ens = dq.Ensemble(wl.models, wl.chain_model, precision="fp64", delay_k=16, seed=W.BASE_SEED)
+    f0, _ = ens.get_fields()
+    om = orc.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+    och = orc.Chain(om, f0[0], seed=W.BASE_SEED, chain=0)
+    st = ens.sweep(1)
+    so = och.sweep(1)
+    assert st["accepted"] == so.accepted and st["proposals"] == so.proposals == 2 * 100 * 72
+    assert np.array_equal(ens.get_fields()[0][0], och.fields()[0])
+    for s in (0, 1):
+        assert np.abs(ens.greens(0, s)[0] - och.green(s)).max() < 1e-10, s
     ens.close()

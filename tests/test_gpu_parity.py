@@ -160,10 +160,18 @@ def test_fp32_path_green_after_sweeps(dq, orc):
 @pytest.mark.parametrize("precision", ["mixed", "mixed_tc"])
 @pytest.mark.parametrize("ft", [1, 2])
 def test_sweep_trajectory_mixed(dq, orc, ft, precision):
-    """Mixed paths (float-pair G and stabilisation products, FP64 scales and LU): the
-    ratios agree with FP64 to ~1e-12 relative, so every accept/reject decision and
-    every field matches the oracle's trajectory; G after each sweep matches to the
-    float-pair round-off times the conditioning (bar 1e-7, reduced-precision target 1e-6)."""
+    """Reduced-precision paths (float-pair working G, float-pair or exact-split
+    tensor-core products, FP64 scales): the ratios agree with FP64 to ~1e-12
+    relative, so every accept/reject decision and every field matches the
+    oracle's trajectory, and G after each sweep (a stable recompute) matches the
+    oracle's to 1e-10.  The precision monitor (wrapped against fresh G, Sec. 2.3)
+    measures round-off amplified by the condition number of the slices since the
+    last stabilisation; the oracle's FP64 chain reports the same monitor on the
+    same trajectory.  Float pairs store 2^-48 against FP64's 2^-53 (a factor
+    2^5), and their additions (TwoSum of the high words, the low words summed in
+    FP32) and the FP32 cross terms of their products lose up to three more bits,
+    so the path's monitor must stay within 2^8 = 256 times the oracle's, with the
+    mean below the paper's recommended 1e-8."""
     m = square(4, U=4.0, L=20, nw=10, ft=ft)
     seed = 20170401
     ens = dq.Ensemble([m], [0], precision=precision, delay_k=16, seed=seed)
@@ -174,15 +182,18 @@ def test_sweep_trajectory_mixed(dq, orc, ft, precision):
         so = och.sweep(2)
         assert np.array_equal(ens.get_fields()[0][0], och.fields()[0])
         assert sg["accepted"] == so.accepted
-        assert sg["prec_green_max"] < 1e-6
+        assert sg["prec_green_max"] <= 256 * so.prec_green_max + 1e-12, (sg["prec_green_max"], so.prec_green_max)
+        assert sg["prec_green_mean"] <= 256 * so.prec_green_mean + 1e-14 and sg["prec_green_mean"] < 1e-8
         for s in (0, 1):
             assert np.abs(ens.greens(0, s)[0] - och.green(s)).max() < 1e-10
 
 
 @pytest.mark.parametrize("precision", ["mixed", "mixed_tc"])
 def test_mixed_path_drift_and_batch(dq, orc, precision):
-    """Batched uneven chains on the mixed path: each chain follows its FP64 oracle
-    chain, and the wrapped G stays within 1e-6 of the fresh G (precision monitor)."""
+    """Batched uneven chains on the reduced-precision paths: each chain follows its
+    FP64 oracle chain, and the precision monitor stays within 256 times the
+    oracle's own monitor on the same trajectories (float-pair against FP64
+    round-off, as above)."""
     models = [square(8, U=4.0, L=40, nw=10), square(4, U=6.0, L=20, nw=10),
               W.ModelSpec(W.honeycomb_lattice(3, 3), U=4.0, dtau=0.1, L=20, n_wrap=10)]
     cm = [0, 1, 2, 0]
@@ -191,8 +202,7 @@ def test_mixed_path_drift_and_batch(dq, orc, precision):
     f0, _ = ens.get_fields()
     ochs = [orc.Chain(omodel(orc, models[cm[c]]), f0[c], seed=seed, chain=c) for c in range(len(cm))]
     st = ens.sweep(2)
-    for och in ochs:
-        och.sweep(2)
+    so = [och.sweep(2) for och in ochs]
     fg, _ = ens.get_fields()
     for c, och in enumerate(ochs):
         assert np.array_equal(fg[c], och.fields()[0]), c
@@ -200,9 +210,11 @@ def test_mixed_path_drift_and_batch(dq, orc, precision):
             # float-pair stabilisation products and QR (unit round-off ~2^-44) times the
             # conditioning of the middle matrix: ~1e-9 here; the reduced-precision bar is 1e-6
             assert np.abs(ens.greens(c, s)[0] - och.green(s)).max() < 1e-7
-    # the monitor measures the drift of the wrapped G between stabilisations (the
-    # paper's FP64 example prints maxima up to 6e-6); the mean is the recommended figure
-    assert st["prec_green_max"] < 1e-5 and st["prec_green_mean"] < 1e-8, st
+    # the monitor measures the drift of the wrapped G between stabilisations; the
+    # mean is the paper's recommended figure (<= 1e-8)
+    omax = max(x.prec_green_max for x in so)
+    assert st["prec_green_max"] <= 256 * omax + 1e-12, (st["prec_green_max"], omax)
+    assert st["prec_green_mean"] < 1e-8, st
 
 
 def test_sign_problem_trajectory_fp64(dq, orc):
@@ -401,6 +413,22 @@ def test_unstable_threshold_reports_eunstable(dq):
     # the context stays usable: a second sweep runs and reports the same way
     with pytest.raises(dq.DqmcError):
         ens.sweep(1)
+
+
+def test_tensor_core_wait_limit_reports_etimeout(dq):
+    """The tensor-core products wait on their bulk copies and MMAs with a bounded
+    spin (dqmc_run_opts.spin_limit SM cycles).  With a limit of one cycle the first
+    wait gives up: the kernel stops issuing, drains what is in flight, frees its
+    tensor memory and returns, and the call reports DQMC_ETIMEOUT.  The device
+    stays usable: the same workload with the default limit then runs."""
+    m = square(8, U=4.0, L=20)
+    with pytest.raises(dq.DqmcError) as e:
+        dq.Ensemble([m], [0, 0], precision="mixed_tc", seed=3, spin_limit=1)
+    assert e.value.status == dq.DQMC_ETIMEOUT
+    ens = dq.Ensemble([m], [0, 0], precision="mixed_tc", seed=3)
+    st = ens.sweep(1)
+    assert 0 < st["accepted"] < st["proposals"]
+    ens.close()
 
 
 def test_non_finite_propagator_rejected(dq):

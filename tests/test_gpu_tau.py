@@ -122,3 +122,72 @@ def test_tau_measure_invalid_arguments(dq):
         ens.measure_tau(4, [np.full(16, np.nan)])
     assert e.value.status == dq.DQMC_EINVAL
     ens.close()
+
+
+# ------------------------------------------- class-resolved correlation functions
+def test_tau_correlations_per_pair_against_the_oracle(dq, orc):
+    """One class per ordered pair (x, y) on a lattice without inversion symmetry
+    (3x3 torus with t', a site potential and one modified bond): the pair's
+    sum_s G^s(tau,0)_xy, <S^z_x(tau) S^z_y(0)> and <n_x(tau) n_y(0)> against the
+    oracle's, which recomputes every Green function from scratch, for every tau
+    (wrapped slices and stabilisation points, n_wrap = 5).  A transposed or
+    mis-signed entry of G(tau,0) or G(0,tau) fails here: no symmetry hides it."""
+    K = W.square_lattice(3, 3, 1.0, -0.2, 0.1)
+    K[0, 0] -= 0.3
+    K[1, 5] = K[5, 1] = -0.35
+    m = W.ModelSpec(K, U=4.0, dtau=0.1, L=20, n_wrap=5)
+    N = m.N
+    f = W.random_fields(1, m.L, N, seed=31)
+    ens = dq.Ensemble([m], [0], fields=[f], precision="fp64")
+    cls = np.arange(N * N, dtype=np.int32)
+    out, sg = ens.measure_tau_corr(m.L, [cls], [N * N])
+    ref = orc.tau_correlations(omodel(orc, m), f, m.L, cls, N * N)
+    assert out.shape == (1, m.L + 1, N * N, 3)
+    assert np.abs(out[0] - ref).max() < 1e-10
+    _, sgo = orc.tau_observables(omodel(orc, m), f, 0)
+    assert sg[0] == sgo[0] * sgo[1]
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tau_correlations_batch_translation_classes(dq, orc, precision):
+    """Uneven chains after a sweep, translation (displacement) classes of their
+    own lattices: each chain's class sums against the oracle on its current fields;
+    rows beyond the chain's L and classes beyond its model's count are 0."""
+    models = [W.ModelSpec(W.square_lattice(4, 4, tp=-0.1), U=4.0, dtau=0.1, L=20, n_wrap=10),
+              W.ModelSpec(W.honeycomb_lattice(3, 3), U=3.0, dtau=0.1, L=10, n_wrap=5),
+              W.ModelSpec(W.chain_lattice(7, mu=0.2, periodic=True), U=2.0, dtau=0.125, L=16, n_wrap=4,
+                          field_type=2)]
+    chain_cls = np.array([[(j - i) % 7 for j in range(7)] for i in range(7)], dtype=np.int32).ravel()
+    classes = [W.translation_classes_square(4, 4)[:2], W.translation_classes_honeycomb(3, 3)[:2], (chain_cls, 7)]
+    cm = [0, 1, 2, 0]
+    ens = dq.Ensemble(models, cm, precision=precision, delay_k=8, seed=9)
+    ens.sweep(1)
+    fa, _ = ens.get_fields()
+    n_tau = 20
+    out, sg = ens.measure_tau_corr(n_tau, [c for c, _ in classes], [n for _, n in classes])
+    max_cls = max(n for _, n in classes)
+    assert out.shape == (len(cm), n_tau + 1, max_cls, 3)
+    for c, mi in enumerate(cm):
+        m = models[mi]
+        cl, nc = classes[mi]
+        ntc = min(n_tau, m.L)
+        ref = orc.tau_correlations(omodel(orc, m), fa[c], ntc, cl, nc)
+        # each class sums N pairs of products of O(1) entries
+        assert np.abs(out[c, :ntc + 1, :nc] - ref).max() < 2 * m.N * 1e-10, c
+        assert np.all(out[c, ntc + 1:] == 0.0) and np.all(out[c, :, nc:] == 0.0)
+    ens.close()
+
+
+def test_tau_correlations_invalid_arguments(dq):
+    m = W.ModelSpec(W.square_lattice(2, 2), U=4.0, dtau=0.1, L=10, n_wrap=5)
+    ens = dq.Ensemble([m], [0], precision="fp64")
+    cls = np.zeros(16, dtype=np.int32)
+    with pytest.raises(dq.DqmcError) as e:
+        ens.measure_tau_corr(11, [cls], [1])
+    assert e.value.status == dq.DQMC_EINVAL
+    cls[3] = 2
+    with pytest.raises(dq.DqmcError) as e:
+        ens.measure_tau_corr(4, [cls], [2])
+    assert e.value.status == dq.DQMC_EINVAL
+    ens.close()
