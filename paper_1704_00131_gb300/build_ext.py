@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdqmc.so")
 SOURCES = ["dqmc_api.cu", "dqmc_kernels.cu", "dqmc_grad_logdet.cu", "dqmc_grad_energy.cu", "dqmc_tau.cu", "dqmc_noalloc.cu",
-           "dqmc_sweep_fp64.cu", "dqmc_sweep_fp32.cu", "dqmc_sweep_mixed.cu"]
+           "dqmc_sweep_fp64.cu", "dqmc_sweep_fp32.cu", "dqmc_sweep_mixed.cu", "dqmc_sweep_mixed_tc.cu"]
 HEADERS = ["dqmc_internal.h", "dqmc_device.cuh", "dqmc_umma.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

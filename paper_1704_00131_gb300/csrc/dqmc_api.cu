@@ -129,7 +129,8 @@ struct dqmc_ctx {
   int* order_d = nullptr;
   unsigned char* arena = nullptr;
   std::vector<void*> model_allocs;
-  int kprec = 0;          // kernel instantiation: 0 double, 1 float, 2 float pairs
+  int kprec = 0;          // working-G storage: 0 double, 1 float, 2 float pairs (the sweep, fresh-G and
+                          // wrapped-G kernels are chosen by opts.precision: 3 adds the tensor cores)
   size_t smem = 0;        // dynamic shared memory of the fresh-G / gradient kernels
   size_t smem_sweep = 0;  // ... of the sweep kernel (plus the delayed vectors when they fit)
   int ab_smem = 0;
@@ -390,7 +391,8 @@ dqmc_status timeout_message(dqmc_ctx* ctx, const ChainDev& C) {
 dqmc_status initial_fill(dqmc_ctx* ctx) {
   const int n = (int)ctx->chains_h.size();
   dqmc::set_smem_bytes(ctx->smem);
-  CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, n, ctx->nfl, ctx->kprec, 1, nullptr, -1, ctx->stream));
+  CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, n, ctx->nfl, ctx->opts.precision, 1, nullptr, -1,
+                                         ctx->stream));
   CUDA_TRY(ctx, dqmc::launch_finalize_init(ctx->chains_d, n, ctx->stream));
   dqmc_status st = download_chains(ctx);
   if (st) return st;
@@ -560,7 +562,7 @@ dqmc_status dqmc_sweep(dqmc_ctx* ctx, int32_t n_sweeps, dqmc_sweep_stats* stats)
   P.order = ctx->order_d;
   for (int i = 0; i < n_sweeps; ++i) {
     P.sweep = ctx->sweep_counter++;
-    CUDA_TRY(ctx, dqmc::launch_sweep(ctx->chains_d, P, ctx->nfl, ctx->kprec, ctx->smem_sweep, ctx->stream));
+    CUDA_TRY(ctx, dqmc::launch_sweep(ctx->chains_d, P, ctx->nfl, ctx->opts.precision, ctx->smem_sweep, ctx->stream));
   }
   if (!stats) return DQMC_OK;
   CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
@@ -628,7 +630,7 @@ dqmc_status dqmc_greens(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_t fr
   double* src;
   if (fresh) {
     dqmc::set_smem_bytes(ctx->smem);
-    CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, (int)ctx->chains_h.size(), ctx->nfl, ctx->kprec, 0,
+    CUDA_TRY(ctx, dqmc::launch_fresh_green(ctx->chains_d, (int)ctx->chains_h.size(), ctx->nfl, ctx->opts.precision, 0,
                                            ctx->scratch, chain, ctx->stream));
     src = ctx->scratch + (size_t)flavor * N * N;
   } else {
@@ -655,7 +657,8 @@ dqmc_status dqmc_greens_tau(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_
   if (tau < 0 || tau > H.L) return fail(ctx, DQMC_EINVAL, "tau must be in [0, %d]", H.L);
   const int N = H.N;
   dqmc::set_smem_bytes(ctx->smem);
-  CUDA_TRY(ctx, dqmc::launch_green_tau(ctx->chains_d, chain, ctx->nfl, ctx->kprec, tau, ctx->scratch, ctx->stream));
+  CUDA_TRY(ctx, dqmc::launch_green_tau(ctx->chains_d, chain, ctx->nfl, ctx->opts.precision, tau, ctx->scratch,
+                                       ctx->stream));
   CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->scratch + (size_t)flavor * N * N, sizeof(double) * N * N,
                                 out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
   dqmc_status st = download_chains(ctx);

@@ -35,6 +35,13 @@
 #include "../../include/dqmc.h"
 #include "dqmc_internal.h"
 
+// DQMC_WITH_UMMA: 1 compiles the tensor-core product path into the float-pair
+// kernels (the unit of DQMC_PREC_MIXED_TC), 0 leaves it out (the unit of
+// DQMC_PREC_MIXED, whose kernels then keep their registers for the SIMT tiles).
+#ifndef DQMC_WITH_UMMA
+#define DQMC_WITH_UMMA 1
+#endif
+
 namespace cg = cooperative_groups;
 
 namespace dqmc {
@@ -512,20 +519,18 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   s.expB = s.expA + le;
   unsigned char* q = reinterpret_cast<unsigned char*>(s.expB + le);
   q = base + (((size_t)(q - base) + 15) / 16 * 16);
-  s.um.bar = reinterpret_cast<uint64_t*>(q);                 // 2 kUmmaStages mbarriers
-  s.um.tmem_slot = reinterpret_cast<uint32_t*>(q + 16 * kUmmaStages);
+  s.um.bar = reinterpret_cast<uint64_t*>(q);                 // 2 kUmmaStages mbarriers, counters
+  s.um.tmem_slot = reinterpret_cast<uint32_t*>(q + 96);
   s.um.err = nullptr;
   s.um.where = nullptr;
-  s.um.calls = 0;
   s.dd_tile = 0;
   s.um.limit = kUmmaWaitCycles;
   q += 128;
   // base is 16-byte aligned (kSmemCounterBytes past the start); align s.ab to 128
   const uintptr_t qa = (reinterpret_cast<uintptr_t>(q) + 127) & ~(uintptr_t)127;
   s.ab = reinterpret_cast<double*>(qa);
-  s.um.stage[0] = reinterpret_cast<unsigned char*>(s.gemm);
-  for (int st = 1; st < kUmmaStages; ++st)
-    s.um.stage[st] = reinterpret_cast<unsigned char*>(qa) + (size_t)(st - 1) * kUmmaStageBytes;
+  s.um.stage0 = reinterpret_cast<unsigned char*>(s.gemm);
+  s.um.stage1 = reinterpret_cast<unsigned char*>(qa);
   return s;
 }
 
@@ -534,6 +539,7 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
 template <bool TA, bool TB, bool ACC>
 __device__ void gemm_dd(const ChainDev& C, int s, Smem& S, int M, int Nc, int Kd, const dd* A, int lda, const dd* B,
                         int ldb, dd* Cm, int ldc, int constA = -1, int constB = -1) {
+#if DQMC_WITH_UMMA
   if (C.planes[s]) {
     // constA / constB: index of a prepared constant operand (kCpEA ...), -1: split here
     const UmmaOperand cA = constA >= 0 ? UmmaOperand{(const __nv_bfloat16*)C.cpl[s][constA], C.cex[s][constA]}
@@ -542,8 +548,13 @@ __device__ void gemm_dd(const ChainDev& C, int s, Smem& S, int M, int Nc, int Kd
                                        : UmmaOperand{nullptr, nullptr};
     gemm_umma<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, (__nv_bfloat16*)C.planes[s], S.expA, S.expB, S.um,
                            cA, cB);
-  } else
-    gemm_dd_tiles<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, reinterpret_cast<dd*>(S.gemm), S.dd_tile);
+    return;
+  }
+#else
+  (void)constA;
+  (void)constB;
+#endif
+  gemm_dd_tiles<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, reinterpret_cast<dd*>(S.gemm), S.dd_tile);
 }
 
 // Slice potential v^s_i of slice tau (1-based) from global fields.
@@ -1184,7 +1195,7 @@ __global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains,
   ChainDev& C = chains[c];
   Smem S = carve_smem(smem_raw, C.ld, C.MV);
   // the working precision's tensor-core products need the CTA's tensor memory
-  const bool umma = std::is_same<Real, dd>::value && mode == 0 && C.planes[s] != nullptr;
+  const bool umma = DQMC_WITH_UMMA && std::is_same<Real, dd>::value && mode == 0 && C.planes[s] != nullptr;
   S.um.err = &C.error;
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
@@ -1244,7 +1255,7 @@ __global__ void __launch_bounds__(kThreads) green_tau_kernel(ChainDev* chains, i
   const int N = C.N, ld = C.ld, nw = C.nw, nst = C.L / nw;
   const int j0 = tau / nw;
   constexpr bool mixed = std::is_same<Real, dd>::value;
-  const bool umma = mixed && C.planes[s] != nullptr;
+  const bool umma = DQMC_WITH_UMMA && mixed && C.planes[s] != nullptr;
   S.um.err = &C.error;
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
@@ -2013,7 +2024,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
   S.flavor = s;
   // the split tensor-core products (float-pair path with digit planes) need the
   // CTA's tensor memory for the whole sweep
-  const bool umma = std::is_same<Real, dd>::value && C.planes[s] != nullptr;
+  const bool umma = DQMC_WITH_UMMA && std::is_same<Real, dd>::value && C.planes[s] != nullptr;
   S.um.err = &C.error;
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
@@ -2219,5 +2230,10 @@ cudaError_t launch_green_tau_fp32(ChainDev* chains, int chain, int nfl, size_t s
                                   cudaStream_t st);
 cudaError_t launch_green_tau_mixed(ChainDev* chains, int chain, int nfl, size_t smem, int tau, double* out,
                                    cudaStream_t st);
+cudaError_t launch_sweep_mixed_tc(ChainDev* chains, const SweepParams& p, int nfl, size_t smem, cudaStream_t st);
+cudaError_t launch_fresh_green_mixed_tc(ChainDev* chains, int n_chains, int nfl, size_t smem, int mode, double* out,
+                                        int out_chain, cudaStream_t st);
+cudaError_t launch_green_tau_mixed_tc(ChainDev* chains, int chain, int nfl, size_t smem, int tau, double* out,
+                                      cudaStream_t st);
 
 }  // namespace dqmc

@@ -159,6 +159,7 @@ cudaError_t launch_fresh_green(ChainDev* chains, int n_chains, int nfl, int prec
   const int mode = write_working ? 0 : 1;
   if (precision == 0) return launch_fresh_green_fp64(chains, n_chains, nfl, g_smem_bytes, mode, out, out_chain, st);
   if (precision == 1) return launch_fresh_green_fp32(chains, n_chains, nfl, g_smem_bytes, mode, out, out_chain, st);
+  if (precision == 3) return launch_fresh_green_mixed_tc(chains, n_chains, nfl, g_smem_bytes, mode, out, out_chain, st);
   return launch_fresh_green_mixed(chains, n_chains, nfl, g_smem_bytes, mode, out, out_chain, st);
 }
 
@@ -166,6 +167,7 @@ cudaError_t launch_green_tau(ChainDev* chains, int chain, int nfl, int precision
                              cudaStream_t st) {
   if (precision == 0) return launch_green_tau_fp64(chains, chain, nfl, g_smem_bytes, tau, out, st);
   if (precision == 1) return launch_green_tau_fp32(chains, chain, nfl, g_smem_bytes, tau, out, st);
+  if (precision == 3) return launch_green_tau_mixed_tc(chains, chain, nfl, g_smem_bytes, tau, out, st);
   return launch_green_tau_mixed(chains, chain, nfl, g_smem_bytes, tau, out, st);
 }
 
@@ -197,6 +199,7 @@ cudaError_t launch_sweep(ChainDev* chains, const SweepParams& p, int nfl, int pr
                          cudaStream_t st) {
   if (precision == 0) return launch_sweep_fp64(chains, p, nfl, smem, st);
   if (precision == 1) return launch_sweep_fp32(chains, p, nfl, smem, st);
+  if (precision == 3) return launch_sweep_mixed_tc(chains, p, nfl, smem, st);
   return launch_sweep_mixed(chains, p, nfl, smem, st);
 }
 

@@ -1,4 +1,6 @@
-// Sweep and fresh-G kernels instantiated for the float-pair working Green function (mixed and split tensor-core modes).
+// Sweep and fresh-G kernels instantiated for the float-pair working Green function
+// with the float-pair SIMT products only (DQMC_PREC_MIXED).
+#define DQMC_WITH_UMMA 0
 #include "dqmc_device.cuh"
 
 namespace dqmc {

@@ -53,20 +53,30 @@ __host__ __device__ inline size_t umma_plane_elems(int n, int kmax) {
   return (size_t)kUmmaDig * ((size_t)umma_pad(n, kUmmaM) + (size_t)umma_pad(n, kUmmaNT)) * kp;
 }
 
-// State of the tensor-core products of one CTA (in shared memory).
+// State of the tensor-core products of one CTA.  Nothing in it is indexed at
+// run time (that would push the kernel's whole shared-memory descriptor into
+// local memory): the stages are found by umma_stage, and thread 0's
+// bookkeeping lives in the 128-byte shared barrier area.
 struct Umma {
-  unsigned char* stage[kUmmaStages];  // kUmmaStageBytes each, 16-byte aligned
-  uint64_t* bar;          // [2 kUmmaStages]: copies landed per stage, then MMAs done per stage
+  unsigned char* stage0;  // first staging buffer (kUmmaStageBytes, the GEMM region)
+  unsigned char* stage1;  // second; the third follows it
+  uint64_t* bar;          // shared, 128 bytes: [0, 48) the 2 kUmmaStages mbarriers (copies landed
+                          // per stage, then MMAs done per stage); [48, 96) thread 0's counters
+                          // of copies and MMA commits issued and waited per stage; [96, 100)
+                          // the TMEM slot; [100, 104) thread 0's count of products
   uint32_t* tmem_slot;    // tcgen05.alloc writes the accumulator base here
   int* err;               // chain error word (nonzero: a wait gave up)
   long long limit;        // SM cycles after which a wait gives up
   int* where;             // [6] or null: the first wait that gave up (kind, chunk, chunks,
                           // product ordinal, barrier word)
-  int calls;              // products so far in this kernel
-  // thread 0's bookkeeping, kept across the products of a kernel (the barriers
-  // are initialised once): copies and MMA commits issued and waited per stage
-  uint32_t cpy_n[kUmmaStages], cpy_w[kUmmaStages], mma_n[kUmmaStages], mma_w[kUmmaStages];
 };
+
+__device__ __forceinline__ unsigned char* umma_stage(const Umma& U, int st) {
+  return st == 0 ? U.stage0 : U.stage1 + (size_t)(st - 1) * kUmmaStageBytes;
+}
+// thread 0's counters (shared): copies issued / waited, commits issued / waited, per stage
+__device__ __forceinline__ uint32_t* umma_book(const Umma& U) { return reinterpret_cast<uint32_t*>(U.bar + 2 * kUmmaStages); }
+__device__ __forceinline__ uint32_t* umma_calls(const Umma& U) { return U.tmem_slot + 1; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -137,7 +147,7 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // Tensor memory of the CTA: warp 0 allocates kUmmaCols columns (at most two
 // CTAs of a product kernel share an SM, so the 512 columns of an SM never run
 // out) and gives up the right to allocate more; the base goes to *slot.
-__device__ inline void umma_alloc(Umma& U) {
+__device__ inline void umma_alloc(const Umma& U) {
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(U.tmem_slot)),
                  "r"(kUmmaCols)
@@ -146,16 +156,19 @@ __device__ inline void umma_alloc(Umma& U) {
   }
   // the copy and MMA barriers live for the whole kernel: initialised once here,
   // never re-initialised while an arrival could still be on its way
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
     for (int q = 0; q < 2 * kUmmaStages; ++q) mbar_init(U.bar + q);
-  for (int q = 0; q < kUmmaStages; ++q) U.cpy_n[q] = U.cpy_w[q] = U.mma_n[q] = U.mma_w[q] = 0u;
+    uint32_t* book = umma_book(U);
+    for (int q = 0; q < 4 * kUmmaStages; ++q) book[q] = 0u;
+    *umma_calls(U) = 0u;
+  }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
 }
 // Every path out of a kernel that allocated calls this (all threads).
-__device__ inline void umma_free(Umma& U) {
+__device__ inline void umma_free(const Umma& U) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -272,7 +285,7 @@ __device__ __forceinline__ int umma_lane_of_row64(int r) { return ((r >> 4) << 5
 // accumulator base.  C must not alias A or B.
 template <bool TA, bool TB, bool ACC>
 __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B, int ldb,
-                          dd* __restrict__ C, int ldc, __nv_bfloat16* planes, int* expA_s, int* expB_s, Umma& U,
+                          dd* __restrict__ C, int ldc, __nv_bfloat16* planes, int* expA_s, int* expB_s, const Umma U,
                           UmmaOperand cA = {nullptr, nullptr}, UmmaOperand cB = {nullptr, nullptr}) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Mp = umma_pad(M, kUmmaM), Np = umma_pad(Nc, kUmmaNT), Kp = umma_pad(Kd, kUmmaK);
@@ -281,7 +294,7 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
   // products are skipped: the results are void and the host reports it
   // (the chain's error word is shared with the peer flavor's CTA: thread 0
   // reads it once for the whole CTA)
-  ++U.calls;
+  if (tid == 0) *umma_calls(U) += 1u;
   if (__syncthreads_or(tid == 0 && U.err && (*(volatile int*)U.err & 2))) return;
   // earlier generic writes of the staging area (other products) before the
   // copies of this one
@@ -319,10 +332,10 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
   // sound.  live: no wait has given up; once one has, nothing more is issued and
   // the end of the product drains what is in flight before the tensor memory and
   // the staging buffers are used again.
-  uint32_t* cpy_n = U.cpy_n;
-  uint32_t* cpy_w = U.cpy_w;
-  uint32_t* mma_n = U.mma_n;
-  uint32_t* mma_w = U.mma_w;
+  uint32_t* cpy_n = umma_book(U);
+  uint32_t* cpy_w = cpy_n + kUmmaStages;
+  uint32_t* mma_n = cpy_n + 2 * kUmmaStages;
+  uint32_t* mma_w = cpy_n + 3 * kUmmaStages;
   bool live = true;
   auto gave_up = [&](int kind, int g) {
     if (live && U.where && U.where[0] == 0) {
@@ -332,7 +345,7 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
       U.where[0] = kind;
       U.where[1] = g;
       U.where[2] = nch;
-      U.where[3] = U.calls;
+      U.where[3] = (int)*umma_calls(U);
       U.where[4] = (int)(w & 0xffffffffu);
       U.where[5] = (int)(w >> 32);
     }
@@ -358,9 +371,10 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
     if (!wait_mma(st, U.limit)) { gave_up(2, g); return; }
     const int tile = g / nkc, kc = g - tile * nkc, mt = tile / nnt, nt = tile - mt * nnt;
     mbar_expect_tx(bar_full + st, kUmmaStageBytes);
-    bulk_copy_g2s(U.stage[st], PA + ((size_t)mt * nkc + kc) * kUmmaDig * kUmmaM * kUmmaK, kUmmaDig * kUmmaBlockA,
+    unsigned char* dst = umma_stage(U, st);
+    bulk_copy_g2s(dst, PA + ((size_t)mt * nkc + kc) * kUmmaDig * kUmmaM * kUmmaK, kUmmaDig * kUmmaBlockA,
                   bar_full + st);
-    bulk_copy_g2s(U.stage[st] + kUmmaDig * kUmmaBlockA, PB + ((size_t)nt * nkc + kc) * kUmmaDig * kUmmaNT * kUmmaK,
+    bulk_copy_g2s(dst + kUmmaDig * kUmmaBlockA, PB + ((size_t)nt * nkc + kc) * kUmmaDig * kUmmaNT * kUmmaK,
                   kUmmaDig * kUmmaBlockB, bar_full + st);
     ++cpy_n[st];
   };
@@ -376,7 +390,7 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
         gave_up(1, g);
       } else {
         tc_fence_after();
-        const uint32_t sa = smem_u32(U.stage[st]);
+        const uint32_t sa = smem_u32(umma_stage(U, st));
         const uint32_t sb = sa + kUmmaDig * kUmmaBlockA;
 #pragma unroll
         for (int t = 0; t < kUmmaDig; ++t)
