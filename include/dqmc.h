@@ -127,6 +127,11 @@ typedef struct {
   int32_t dd_tile;            /* float-pair SIMT products: output tiles of 48 x 48
                                  (3) or 64 x 64 (4) per CTA; 0: the one that pads
                                  the matrix least                                 */
+  int32_t test_stall;         /* test hook, 0 in production: nonzero makes the
+                                 first bounded wait of every tensor-core product
+                                 wait on a barrier that nothing arrives on, so it
+                                 gives up after spin_limit cycles; the call then
+                                 reports DQMC_ETIMEOUT with the context usable    */
 } dqmc_run_opts;
 
 /* Statistics of one dqmc_sweep call, over all chains (Sec. 4.5 "info" file:

@@ -1,0 +1,117 @@
+/* C ABI of the GB300 DQMC library: Markov chains of the SU(2)-symmetric
+ * Hubbard model in the charge decoupling with complex coupling (the paper's
+ * default Hubbard example, Sec. 6.1; discrete HS transform of Sec. 2.1;
+ * complex weights and the phase of Sec. 2.2).
+ *
+ * Model.  H = sum_xy K_xy sum_s c+_xs c_ys + U/2 sum_i (n_i - 1)^2 with
+ * n_i = n_i,up + n_i,dn.  The four-valued transform of Sec. 2.1 applied to
+ * exp(-dtau U/2 (n_i - 1)^2) has an imaginary coupling:
+ *   exp(-dtau U/2 (n_i - 1)^2) = sum_l gamma(l)/4 exp(i g eta(l) (n_i - 1)) + O(dtau^4),
+ *   g = sqrt(dtau U / 2),  l in {-2, -1, 1, 2}.
+ * Both colors see the same propagator B_tau = exp(-dtau K) exp(V_tau),
+ * V_tau = diag(i g eta(l_tau,x)), so one complex N x N Green function
+ * G(tau) = (1 + B(tau,0) B(beta,tau))^-1 serves both, and the weight is
+ *   prod gamma(l)/4 * exp(-i g sum eta(l)) * det(1 + B(beta,0))^2.
+ * Sampling uses W = |Re e^{-S}| (Sec. 2.2) with the phase
+ * P = e^{-S}/|e^{-S}| = exp(i (-g sum eta + 2 arg det(1 + B(beta,0)))) carried
+ * through the updates; observables are reweighted by sign * P / Re P.
+ *
+ * Arithmetic: complex FP64 throughout (G, wraps, rank-1 updates, the complex
+ * pivoted-QR UDV chain and the stable G of Sec. 2.3).  One CTA per chain.
+ *
+ * Sweep order and random numbers as dqmc.h: up tau = 1..L with sites 0..N-1,
+ * down tau = L..1 with sites N-1..0; Philox4x32-10 with key
+ * (seed_lo, seed_hi ^ chain) and counter (sweep_lo, 2 tau + dir, site,
+ * sweep_hi); u1 from words 0, 1 picks one of the three other field values
+ * (ascending, index floor(3 u1)), u2 from words 2, 3 is the acceptance
+ * uniform.  The sweep counter of a context starts at 0.
+ *
+ * Errors: dqmc_status codes of dqmc.h, no exceptions, no device traps.  A
+ * context is used from one host thread at a time.
+ */
+#ifndef DQMC_SU2_H
+#define DQMC_SU2_H
+
+#include <stdint.h>
+
+#include "dqmc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dqmc_su2_ctx dqmc_su2_ctx; /* opaque, library-owned */
+
+typedef struct {
+  int32_t n_sites;        /* N, 1..1024                                           */
+  const double* hopping;  /* K [N][N] row-major, symmetric, -mu on the diagonal  */
+  double U;               /* Hubbard U >= 0 (g = sqrt(dtau U / 2))               */
+  double dtau;            /* > 0                                                  */
+  int32_t L;              /* Trotter slices >= 1                                  */
+  int32_t n_wrap;         /* stabilisation interval; L % n_wrap == 0 (Sec. 2.3)   */
+} dqmc_su2_model_desc;
+
+typedef struct {
+  int32_t measure;            /* nonzero: accumulate the energy estimator        */
+  int32_t meas_first;         /* measure G(tau) for meas_first <= tau <= meas_last*/
+  int32_t meas_last;          /*   (upward tau = 1..L, downward tau-1 = L-1..0)   */
+  uint64_t seed;              /* Philox key (seed_lo, seed_hi ^ chain)            */
+  double unstable_threshold;  /* > 0: DQMC_EUNSTABLE when prec_green_max or
+                                 prec_phase_max exceeds it                       */
+} dqmc_su2_opts;
+
+typedef struct {
+  int64_t proposals, accepted;
+  double prec_green_mean;     /* "Precision Green" over the stabilisation events: */
+  double prec_green_max;      /*   mean of mean |G_wrap - G_fresh|, max of max    */
+  double prec_phase_max;      /* "Precision Phase": max |P_carried - P_fresh|     */
+  double mean_sign;           /* mean over chains and sweeps of sign(Re P)        */
+  float ms_total;             /* device time of the call (CUDA events)            */
+} dqmc_su2_sweep_stats;
+
+/* Create a context with n_chains chains; chain c uses models[chain_model[c]].
+ * fields_or_null: packed per chain [L_c][N_c] (int8 in {-2,-1,1,2}, host); NULL
+ * draws them i.i.d. uniform from Philox (counter (0xFFFFFFFF, tau, x,
+ * 0xFFFFFFFF)).  The left chain, G(0), log|det|, arg det and the phase P are
+ * computed before return.  Inputs are copied.
+ * Errors: DQMC_EINVAL (bad model, options or field values), DQMC_ENOMEM,
+ * DQMC_ECUDA, DQMC_EUNSTABLE (a singular matrix in the stabilisation).  On an
+ * error *out may still receive a context that only carries the message. */
+dqmc_status dqmc_su2_init(const dqmc_su2_model_desc* models, int32_t n_models, const int32_t* chain_model,
+                          int32_t n_chains, const int8_t* fields_or_null, const dqmc_su2_opts* opts,
+                          void* cuda_stream, dqmc_su2_ctx** out);
+
+/* n_sweeps >= 1 sweeps of every chain (Algorithm 1); stats_or_null receives
+ * the statistics of the call.  Blocks until the sweeps are done.
+ * DQMC_EUNSTABLE: a singular matrix, or a precision figure above the
+ * threshold (the sweeps still ran). */
+dqmc_status dqmc_su2_sweep(dqmc_su2_ctx* ctx, int32_t n_sweeps, dqmc_su2_sweep_stats* stats_or_null);
+
+/* G(0) of one chain ([N][N] complex, re/im interleaved, row-major) into out
+ * (host, or device when out_is_device): fresh = 0 the working G the sweeps
+ * left, fresh = 1 recomputed from the fields through the UDV chain.
+ * logabs_out / arg_out (nullable): log|det(1 + B(beta,0))| and its argument
+ * at the last fresh G; phase_out (nullable, [2]): the chain's phase P. */
+dqmc_status dqmc_su2_greens(dqmc_su2_ctx* ctx, int32_t chain, int32_t fresh, double* out, int32_t out_is_device,
+                            double* logabs_out, double* arg_out, double* phase_out);
+
+/* Reweighted sums since the context was created or last measured-and-reset
+ * (reset = 1): out [n_chains][4][2] = (re, im) of sum sign * P / Re P * O for
+ * O = Kin, Pot, Part, Ener (Sec. 6.1 estimator, both colors); sign_sum
+ * [n_chains] = sum of sign(Re P); n_meas [n_chains].  Host buffers. */
+dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas, int32_t reset);
+
+/* Fields of every chain (packed [L_c][N_c] int8) and the sweep counter. */
+dqmc_status dqmc_su2_get_fields(dqmc_su2_ctx* ctx, int8_t* out, uint64_t* sweep_counter);
+/* Replace the fields and the sweep counter; the left chains, G(0) and the
+ * phases are recomputed. */
+dqmc_status dqmc_su2_set_fields(dqmc_su2_ctx* ctx, const int8_t* in, uint64_t sweep_counter);
+
+const char* dqmc_su2_last_error(const dqmc_su2_ctx* ctx);
+void dqmc_su2_destroy(dqmc_su2_ctx* ctx); /* NULL-safe */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQMC_SU2_H */

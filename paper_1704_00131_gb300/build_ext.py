@@ -15,8 +15,9 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdqmc.so")
 SOURCES = ["dqmc_api.cu", "dqmc_kernels.cu", "dqmc_grad_logdet.cu", "dqmc_grad_energy.cu", "dqmc_tau.cu", "dqmc_noalloc.cu",
-           "dqmc_sweep_fp64.cu", "dqmc_sweep_fp32.cu", "dqmc_sweep_mixed.cu", "dqmc_sweep_mixed_tc.cu"]
-HEADERS = ["dqmc_internal.h", "dqmc_device.cuh", "dqmc_umma.cuh"]
+           "dqmc_sweep_fp64.cu", "dqmc_sweep_fp32.cu", "dqmc_sweep_mixed.cu", "dqmc_sweep_mixed_tc.cu",
+           "dqmc_su2.cu", "dqmc_su2_api.cu"]
+HEADERS = ["dqmc_internal.h", "dqmc_device.cuh", "dqmc_umma.cuh", "dqmc_su2_internal.h", "dqmc_linalg_host.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
@@ -31,7 +32,7 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "dqmc.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", h) for h in ("dqmc.h", "dqmc_su2.h")]
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

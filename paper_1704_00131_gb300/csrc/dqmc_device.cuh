@@ -525,6 +525,7 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   s.um.where = nullptr;
   s.dd_tile = 0;
   s.um.limit = kUmmaWaitCycles;
+  s.um.stall = 0;
   q += 128;
   // base is 16-byte aligned (kSmemCounterBytes past the start); align s.ab to 128
   const uintptr_t qa = (reinterpret_cast<uintptr_t>(q) + 127) & ~(uintptr_t)127;
@@ -1199,6 +1200,7 @@ __global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains,
   S.um.err = &C.error;
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
+  S.um.stall = C.test_stall;
   S.um.where = C.wait_where[s];
   if (umma) umma_alloc(S.um);
   double logdet;
@@ -1259,6 +1261,7 @@ __global__ void __launch_bounds__(kThreads) green_tau_kernel(ChainDev* chains, i
   S.um.err = &C.error;
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
+  S.um.stall = C.test_stall;
   S.um.where = C.wait_where[s];
   if (umma) umma_alloc(S.um);
   int dq = 1;
@@ -2028,6 +2031,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
   S.um.err = &C.error;
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
+  S.um.stall = C.test_stall;
   S.um.where = C.wait_where[s];
   if (umma) umma_alloc(S.um);
   Real* G = (Real*)C.G[s];

@@ -1,0 +1,880 @@
+// GB300 kernels of the SU(2) charge decoupling of the Hubbard model, the
+// paper's default Hubbard example (Sec. 6.1), in complex FP64.
+//
+// The discrete HS transform of Sec. 2.1 applied to exp(-dtau U/2 (n_i - 1)^2)
+// has an imaginary coupling: on fixed four-valued fields l[tau][x] both colors
+// see the same one-body propagator
+//   B_tau = E exp(V_tau),  V_tau = diag(i g eta(l_tau,x)),  g = sqrt(dtau U / 2),
+// and the weight is prod gamma(l)/4 * exp(-i g sum eta(l)) * det(1 + B(beta,0))^2.
+// The Markov chain samples W = |Re e^{-S}| and carries the phase
+// P = e^{-S} / |e^{-S}| (Sec. 2.2); observables are reweighted by
+// sign * P / Re P (Sec. 5.1, ZS and ZP).
+//
+// Work decomposition: one CTA of 256 threads per chain; the chain's Green
+// function, UDV storage and workspace live in its own arena in HBM.
+// Per slice (Algorithm 1, wrapgrup): the V wrap G~ = e^V G e^-V, the
+// sequential single-site updates with the complex ratio and a rank-1
+// Sherman-Morrison update, the T wrap E G~ E^-1; every n_wrap slices the
+// complex pivoted-QR UDV chain (Sec. 2.3) recomputes G, log|det|, the
+// argument of det(1 + B) and with it the phase ("Precision Phase").
+#include "dqmc_device.cuh"
+#include "dqmc_su2_internal.h"
+
+namespace dqmc {
+namespace {
+
+// ---- complex arithmetic on double2 (re, im) -------------------------------
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zscal(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ double zabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double zabs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  // a conj(b) / |b|^2 with b rescaled by its larger component (Smith's idea)
+  const double s = fmax(fabs(b.x), fabs(b.y));
+  const double2 bs = make_double2(b.x / s, b.y / s);
+  const double d = zabs2(bs);
+  const double2 n = zmul(a, zconj(bs));
+  return make_double2(n.x / (d * s), n.y / (d * s));
+}
+__device__ __forceinline__ double2 zexpi(double th) {
+  double s, c;
+  sincos(th, &s, &c);
+  return make_double2(c, s);
+}
+// acc + a b for complex and mixed real/complex operands
+__device__ __forceinline__ double2 zmac(double2 acc, double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 zmac(double2 acc, double a, double2 b) {
+  return make_double2(fma(a, b.x, acc.x), fma(a, b.y, acc.y));
+}
+__device__ __forceinline__ double2 zmac(double2 acc, double2 a, double b) {
+  return make_double2(fma(a.x, b, acc.x), fma(a.y, b, acc.y));
+}
+template <typename T>
+__device__ __forceinline__ T zzero();
+template <>
+__device__ __forceinline__ double zzero<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ double2 zzero<double2>() { return make_double2(0.0, 0.0); }
+// operand transform: 0 as is, 1 transpose, 2 conjugate transpose
+template <int OP>
+__device__ __forceinline__ double zop(double x) { return x; }
+template <int OP>
+__device__ __forceinline__ double2 zop(double2 x) { return OP == 2 ? zconj(x) : x; }
+
+__device__ __forceinline__ double2 block_zsum(double2 v, double* red) {
+  const double re = block_sum(v.x, red);
+  const double im = block_sum(v.y, red);
+  return make_double2(re, im);
+}
+
+// ---- shared memory of a chain's CTA ----------------------------------------
+constexpr int kZgTile = 32;  // C tile of the complex products
+constexpr int kZgK = 16;     // K step
+constexpr int kZgBytes = 2 * kZgK * (kZgTile + 1) * (int)sizeof(double2);
+
+struct Sm {
+  unsigned char* gemm;  // the two staging tiles of zgemm
+  double2* ph;          // [N] exp(i g eta) of the current slice
+  double2* delta;       // [N] e^{i dtheta} - 1 per proposal
+  double2* gr;          // [N] gamma(l') / gamma(l) e^{-i dtheta} per proposal
+  double2* d;           // [N] diagonal of G~
+  double2* col;         // [N] column of G~ at the accepted site
+  double2* row;         // [N] e_k - G~[k, :]
+  double2* hv;          // [N] Householder vector; pivot column of Gauss-Jordan
+  double2* qred;        // [8][32] partial sums of the reflector application
+  double* u2;           // [N] acceptance uniforms
+  double* red;          // [32]
+  int* ired;            // [32]
+  double2* P;           // [1] the phase of the chain
+  int* first;           // [1] first accepted position of a scan
+  int8_t* fsl;          // [N] fields of the current slice
+  int8_t* fn;           // [N] proposed fields
+};
+
+__host__ __device__ inline size_t su2_smem_layout(int N) {
+  return (size_t)kZgBytes + (size_t)8 * N * sizeof(double2) + 256 * sizeof(double2) + (size_t)N * sizeof(double) +
+         32 * sizeof(double) + 32 * sizeof(int) + 16 /* alignment */ + sizeof(double2) + 16 +
+         2 * (size_t)((N + 15) / 16 * 16);
+}
+
+__device__ inline Sm su2_carve(unsigned char* base, int N) {
+  Sm s;
+  unsigned char* q = base;
+  s.gemm = q; q += kZgBytes;
+  s.ph = reinterpret_cast<double2*>(q); q += (size_t)N * sizeof(double2);
+  s.delta = reinterpret_cast<double2*>(q); q += (size_t)N * sizeof(double2);
+  s.gr = reinterpret_cast<double2*>(q); q += (size_t)N * sizeof(double2);
+  s.d = reinterpret_cast<double2*>(q); q += (size_t)N * sizeof(double2);
+  s.col = reinterpret_cast<double2*>(q); q += (size_t)N * sizeof(double2);
+  s.row = reinterpret_cast<double2*>(q); q += (size_t)N * sizeof(double2);
+  s.hv = reinterpret_cast<double2*>(q); q += (size_t)N * sizeof(double2);
+  q += (size_t)N * sizeof(double2);  // spare vector (keeps the layout 16-byte aligned)
+  s.qred = reinterpret_cast<double2*>(q); q += 256 * sizeof(double2);
+  s.u2 = reinterpret_cast<double*>(q); q += (size_t)N * sizeof(double);
+  s.red = reinterpret_cast<double*>(q); q += 32 * sizeof(double);
+  s.ired = reinterpret_cast<int*>(q); q += 32 * sizeof(int);
+  q = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(q) + 15) & ~(uintptr_t)15);
+  s.P = reinterpret_cast<double2*>(q); q += sizeof(double2);
+  s.first = reinterpret_cast<int*>(q); q += 16;
+  s.fsl = reinterpret_cast<int8_t*>(q); q += (size_t)((N + 15) / 16 * 16);
+  s.fn = reinterpret_cast<int8_t*>(q);
+  return s;
+}
+
+// ---- dense complex products -------------------------------------------------
+// C = op(A) op(B) (ACC: C += op(A) op(B)), M x Nc, inner dimension Kd; op 0 as
+// is, 1 transpose, 2 conjugate transpose; A and B real (double) or complex
+// (double2).  Tiles of 32 x 32 outputs, 2 x 2 per thread, K in steps of 16
+// staged in shared memory.  C must not alias A or B.
+template <int OPA, int OPB, bool ACC, typename TA, typename TB>
+__device__ void zgemm(int M, int Nc, int Kd, const TA* A, int lda, const TB* B, int ldb, double2* C, int ldc,
+                      unsigned char* smem) {
+  TA* As = reinterpret_cast<TA*>(smem);                                     // [kZgK][33] (k, m)
+  TB* Bs = reinterpret_cast<TB*>(smem + kZgK * (kZgTile + 1) * sizeof(double2));  // [kZgK][33] (k, n)
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int mt = (M + kZgTile - 1) / kZgTile, nt = (Nc + kZgTile - 1) / kZgTile;
+  for (int t = 0; t < mt * nt; ++t) {
+    const int m0 = (t / nt) * kZgTile, n0 = (t % nt) * kZgTile;
+    double2 acc[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) acc[r][c] = make_double2(0.0, 0.0);
+    for (int k0 = 0; k0 < Kd; k0 += kZgK) {
+      for (int e = tid; e < kZgTile * kZgK; e += kThreads) {
+        int mm, kk;
+        if (OPA == 0) { mm = e >> 4; kk = e & 15; } else { kk = e >> 5; mm = e & 31; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        TA v = zzero<TA>();
+        if (gm < M && gk < Kd) v = (OPA == 0) ? A[(size_t)gm * lda + gk] : zop<OPA>(A[(size_t)gk * lda + gm]);
+        As[kk * (kZgTile + 1) + mm] = v;
+      }
+      for (int e = tid; e < kZgTile * kZgK; e += kThreads) {
+        int nn, kk;
+        if (OPB == 0) { kk = e >> 5; nn = e & 31; } else { nn = e >> 4; kk = e & 15; }
+        const int gn = n0 + nn, gk = k0 + kk;
+        TB v = zzero<TB>();
+        if (gn < Nc && gk < Kd) v = (OPB == 0) ? B[(size_t)gk * ldb + gn] : zop<OPB>(B[(size_t)gn * ldb + gk]);
+        Bs[kk * (kZgTile + 1) + nn] = v;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < kZgK; ++kk) {
+        const TA a0 = As[kk * (kZgTile + 1) + 2 * ty], a1 = As[kk * (kZgTile + 1) + 2 * ty + 1];
+        const TB b0 = Bs[kk * (kZgTile + 1) + 2 * tx], b1 = Bs[kk * (kZgTile + 1) + 2 * tx + 1];
+        acc[0][0] = zmac(acc[0][0], a0, b0);
+        acc[0][1] = zmac(acc[0][1], a0, b1);
+        acc[1][0] = zmac(acc[1][0], a1, b0);
+        acc[1][1] = zmac(acc[1][1], a1, b1);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int gm = m0 + 2 * ty + r, gn = n0 + 2 * tx + c;
+        if (gm < M && gn < Nc) {
+          double2* cp = C + (size_t)gm * ldc + gn;
+          *cp = ACC ? zadd(*cp, acc[r][c]) : acc[r][c];
+        }
+      }
+  }
+  __syncthreads();
+}
+
+__device__ inline void zcopy(int N, int ld, const double2* src, double2* dst) {
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    dst[(size_t)x * ld + y] = src[(size_t)x * ld + y];
+  }
+  __syncthreads();
+}
+
+// ---- per-chain workspace --------------------------------------------------
+__device__ inline double2* zmat(const Su2Dev& C, int m) { return C.work + (size_t)m * C.N * C.ld; }
+__device__ inline double2* zvec(const Su2Dev& C, int v) {
+  return C.work + (size_t)kSu2Mats * C.N * C.ld + (size_t)v * C.ld;
+}
+__device__ inline double* dvec(const Su2Dev& C, int v) { return C.dwork + (size_t)v * C.ld; }
+
+struct ZUdv {
+  const double2* Q;
+  const double* D;
+  const double2* T;
+  int detq;
+};
+__device__ inline ZUdv z_ident(const Su2Dev& C) { return ZUdv{C.ident, C.ones, C.ident, 1}; }
+__device__ inline ZUdv z_slot(const Su2Dev& C, int j) {
+  const double2* b = C.slots + (size_t)j * su2_slot_elems(C.N, C.ld);
+  return ZUdv{b, C.slotD + (size_t)j * C.ld, b + (size_t)C.N * C.ld, C.slot_detq[j]};
+}
+// the decomposition a chain step leaves in the workspace: Q in W2, T in W3, D in dvec 0
+__device__ inline ZUdv z_work(const Su2Dev& C, int detq) { return ZUdv{zmat(C, 2), dvec(C, 0), zmat(C, 3), detq}; }
+__device__ void z_store_slot(const Su2Dev& C, int j, int detq) {
+  const int N = C.N, ld = C.ld;
+  double2* b = C.slots + (size_t)j * su2_slot_elems(N, ld);
+  zcopy(N, ld, zmat(C, 2), b);
+  zcopy(N, ld, zmat(C, 3), b + (size_t)N * ld);
+  for (int x = threadIdx.x; x < N; x += kThreads) C.slotD[(size_t)j * ld + x] = dvec(C, 0)[x];
+  if (threadIdx.x == 0) C.slot_detq[j] = detq;
+  __syncthreads();
+}
+
+// exp(s i g eta(l)) of slice tau for every site, into ph (s = +1 or -1)
+__device__ inline void slice_phases(const Su2Dev& C, const int8_t* f, double s, double2* ph) {
+  for (int x = threadIdx.x; x < C.N; x += kThreads) ph[x] = zexpi(s * C.g * hs_eta(f[x]));
+  __syncthreads();
+}
+
+// ---- complex Householder QR with column pivoting ---------------------------
+// X[k:, j] -= b v (v^H X[k:, j]) for j0 <= j < N, v = hv[k:], b real.  8 row
+// groups x 32 columns; the row groups' partial products are summed in shared
+// memory in a fixed order.
+__device__ void zhouse_apply(int N, int ld, double2* X, int k, int j0, double b, const double2* hv,
+                             double2* qred) {
+  const int tid = threadIdx.x, lane = tid & 31, rg = tid >> 5;
+  for (int c0 = j0; c0 < N; c0 += 32) {
+    const int j = c0 + lane;
+    double2 w = make_double2(0.0, 0.0);
+    if (j < N)
+      for (int i = k + rg; i < N; i += 8) w = zmac(w, zconj(hv[i]), X[(size_t)i * ld + j]);
+    qred[rg * 32 + lane] = w;
+    __syncthreads();
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s = zadd(s, qred[r * 32 + lane]);
+    s = zscal(b, s);
+    if (j < N)
+      for (int i = k + rg; i < N; i += 8) {
+        double2* xp = X + (size_t)i * ld + j;
+        *xp = zsub(*xp, zmul(s, hv[i]));
+      }
+    __syncthreads();
+  }
+}
+
+// Pivoted QR of X (in place): the upper triangle becomes R, the strict lower
+// part keeps the reflector vectors below their first entries (vk0[k]);
+// H_k = 1 - beta_k v v^H maps column k of the remaining block to alpha e_k with
+// alpha = -(x_0/|x_0|) |x| (Hermitian, unitary, det -1).  The pivot is the
+// column of largest remaining norm (ties: lowest index), the norms downdated
+// as in LAPACK's xGEQPF and recomputed when cancellation would spoil them.
+// perm[k] = the original column now at position k.  Returns det Q.
+__device__ int zqr_pivoted(int N, int ld, double2* X, double* beta, double2* vk0, double* cn, double* cn0, int* perm,
+                           Sm& S) {
+  const int tid = threadIdx.x;
+  for (int j = tid; j < N; j += kThreads) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc += zabs2(X[(size_t)i * ld + j]);
+    cn[j] = sqrt(acc);
+    cn0[j] = cn[j];
+    perm[j] = j;
+  }
+  __syncthreads();
+  const double tol3z = sqrt(2.220446049250313e-16);
+  int detq = 1;
+  for (int k = 0; k < N; ++k) {
+    double bv = -1.0;
+    int bi = N;
+    for (int j = k + tid; j < N; j += kThreads)
+      if (cn[j] > bv) { bv = cn[j]; bi = j; }
+    int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N) p = k;
+    if (p != k) {
+      for (int i = tid; i < N; i += kThreads) {
+        const double2 t = X[(size_t)i * ld + k];
+        X[(size_t)i * ld + k] = X[(size_t)i * ld + p];
+        X[(size_t)i * ld + p] = t;
+      }
+      if (tid == 0) {
+        const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
+        double t = cn[k]; cn[k] = cn[p]; cn[p] = t;
+        t = cn0[k]; cn0[k] = cn0[p]; cn0[p] = t;
+      }
+      __syncthreads();
+    }
+    double part = 0.0;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const double2 x = X[(size_t)i * ld + k];
+      part += zabs2(x);
+      S.hv[i] = x;
+    }
+    const double xn2 = block_sum(part, S.red);
+    const double xnorm = sqrt(xn2);
+    const double2 x0 = S.hv[k];
+    double bk = 0.0;
+    double2 alpha = make_double2(0.0, 0.0);
+    if (xnorm > 0.0) {
+      const double a0 = zabs(x0);
+      alpha = (a0 > 0.0) ? zscal(-xnorm / a0, x0) : make_double2(-xnorm, 0.0);
+      const double2 v0 = zsub(x0, alpha);
+      const double vhv = xn2 - zabs2(x0) + zabs2(v0);
+      bk = (vhv > 0.0) ? 2.0 / vhv : 0.0;
+      __syncthreads();
+      if (tid == 0) S.hv[k] = v0;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      beta[k] = bk;
+      vk0[k] = S.hv[k];
+    }
+    if (bk != 0.0) {
+      detq = -detq;
+      zhouse_apply(N, ld, X, k, k + 1, bk, S.hv, S.qred);
+    }
+    __syncthreads();
+    if (tid == 0) X[(size_t)k * ld + k] = (xnorm > 0.0) ? alpha : x0;
+    for (int j = k + 1 + tid; j < N; j += kThreads) {
+      if (cn[j] != 0.0) {
+        double t = zabs(X[(size_t)k * ld + j]) / cn[j];
+        t = fmax(0.0, (1.0 + t) * (1.0 - t));
+        const double r = cn[j] / cn0[j];
+        if (t * r * r <= tol3z) {
+          double acc = 0.0;
+          for (int i = k + 1; i < N; ++i) acc += zabs2(X[(size_t)i * ld + j]);
+          cn[j] = sqrt(acc);
+          cn0[j] = cn[j];
+        } else {
+          cn[j] *= sqrt(t);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  return detq;
+}
+
+// Q = H_0 H_1 ... H_{N-1}, applied to the identity from the last reflector.
+__device__ void zform_q(int N, int ld, const double2* X, const double* beta, const double2* vk0, double2* Q, Sm& S) {
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    Q[(size_t)x * ld + y] = make_double2(x == y ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = N - 1; k >= 0; --k) {
+    const double bk = beta[k];
+    if (bk == 0.0) continue;
+    for (int i = k + threadIdx.x; i < N; i += kThreads) S.hv[i] = (i == k) ? vk0[k] : X[(size_t)i * ld + k];
+    __syncthreads();
+    zhouse_apply(N, ld, Q, k, k, bk, S.hv, S.qred);
+  }
+}
+
+// ---- the UDV chain (Sec. 2.3) -----------------------------------------------
+// Extend a decomposition by the slices t1+1..t2.  Right chain (B(tau,0)):
+// X <- B_t X = E e^{V_t} X for t = t1+1..t2.  Left chain (B(beta,tau)^H):
+// X <- B_t^H X = e^{-V_t} E X for t = t2..t1+1.  Starting from X = src.Q, then
+// M = X diag(src.D) = Q R P^T; the new decomposition is Q (W2), D = |diag R|
+// (dvec 0), T = D^-1 R P^T src.T (W3).  Returns det Q.
+__device__ int z_chain_step(const Su2Dev& C, int t1, int t2, bool left, ZUdv src, Sm& S) {
+  const int N = C.N, ld = C.ld;
+  double2* X = zmat(C, 0);
+  double2* Y = zmat(C, 1);
+  zcopy(N, ld, src.Q, X);
+  for (int q = 0; q < t2 - t1; ++q) {
+    const int t = left ? t2 - q : t1 + 1 + q;
+    const int8_t* f = C.fields + (size_t)(t - 1) * N;
+    if (!left) {
+      slice_phases(C, f, +1.0, S.ph);
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        X[(size_t)x * ld + y] = zmul(S.ph[x], X[(size_t)x * ld + y]);
+      }
+      __syncthreads();
+      zgemm<0, 0, false>(N, N, N, C.E, ld, X, ld, Y, ld, S.gemm);
+    } else {
+      zgemm<0, 0, false>(N, N, N, C.E, ld, X, ld, Y, ld, S.gemm);
+      slice_phases(C, f, -1.0, S.ph);
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        Y[(size_t)x * ld + y] = zmul(S.ph[x], Y[(size_t)x * ld + y]);
+      }
+      __syncthreads();
+    }
+    double2* t_ = X; X = Y; Y = t_;
+  }
+  // M = X diag(D)
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    X[(size_t)x * ld + y] = zscal(src.D[y], X[(size_t)x * ld + y]);
+  }
+  __syncthreads();
+  double* Dn = dvec(C, 0);
+  double* beta = dvec(C, 1);
+  double2* vk0 = zvec(C, 0);
+  int* perm = C.iwork;
+  const int detq = zqr_pivoted(N, ld, X, beta, vk0, dvec(C, 2), dvec(C, 3), perm, S);
+  zform_q(N, ld, X, beta, vk0, zmat(C, 2), S);
+  for (int k = threadIdx.x; k < N; k += kThreads) Dn[k] = zabs(X[(size_t)k * ld + k]);
+  __syncthreads();
+  // Y = D^-1 R (upper triangle), Rt = P^T src.T (row k = row perm[k] of src.T)
+  double2* Rt = zmat(C, 7);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double dinv = Dn[x] > 0.0 ? 1.0 / Dn[x] : 0.0;
+    Y[(size_t)x * ld + y] = (y >= x) ? zscal(dinv, X[(size_t)x * ld + y]) : make_double2(0.0, 0.0);
+    Rt[(size_t)x * ld + y] = src.T[(size_t)perm[x] * ld + y];
+  }
+  __syncthreads();
+  zgemm<0, 0, false>(N, N, N, (const double2*)Y, ld, (const double2*)Rt, ld, zmat(C, 3), ld, S.gemm);
+  return detq;
+}
+
+// G = (1 + B(tau,0) B(beta,tau))^-1 from the right chain R = B(tau,0) and the
+// left chain Lf = B(beta,tau)^H by scale separation (D = Db Ds with
+// Db = max(D, 1), Ds = min(D, 1)):
+//   1 + B(tau,0) B(beta,tau) = Q_R Db_R Mid Db_L Q_L^H,
+//   Mid = Db_R^-1 Q_R^H Q_L Db_L^-1 + Ds_R T_R T_L^H Ds_L,
+//   G = Q_L Db_L^-1 Mid^-1 Db_R^-1 Q_R^H,
+//   det(1 + B) = det Q_R det Q_L prod Db_R prod Db_L det Mid (det Q = +-1).
+// Mid^-1 by Gauss-Jordan with partial pivoting.  Returns 1 on a singular Mid.
+__device__ int z_green(const Su2Dev& C, ZUdv R, ZUdv Lf, double2* Gout, double& logabs, double& arg, Sm& S) {
+  const int N = C.N, ld = C.ld, tid = threadIdx.x;
+  double *dbR = dvec(C, 4), *dsR = dvec(C, 5), *dbL = dvec(C, 6), *dsL = dvec(C, 7);
+  double lsum = 0.0;
+  for (int i = tid; i < N; i += kThreads) {
+    dbR[i] = fmax(R.D[i], 1.0);
+    dsR[i] = fmin(R.D[i], 1.0);
+    dbL[i] = fmax(Lf.D[i], 1.0);
+    dsL[i] = fmin(Lf.D[i], 1.0);
+    lsum += log(dbR[i]) + log(dbL[i]);
+  }
+  lsum = block_sum(lsum, S.red);
+  double2* Mid = zmat(C, 4);
+  double2* X = zmat(C, 5);
+  zgemm<2, 0, false>(N, N, N, R.Q, ld, Lf.Q, ld, Mid, ld, S.gemm);  // Q_R^H Q_L
+  zgemm<0, 2, false>(N, N, N, R.T, ld, Lf.T, ld, X, ld, S.gemm);    // T_R T_L^H
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    const double2 qq = Mid[(size_t)i * ld + j], tt = X[(size_t)i * ld + j];
+    Mid[(size_t)i * ld + j] = zadd(zscal(1.0 / (dbR[i] * dbL[j]), qq), zscal(dsR[i] * dsL[j], tt));
+  }
+  __syncthreads();
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    X[(size_t)i * ld + j] = zscal(1.0 / dbR[i], zconj(R.Q[(size_t)j * ld + i]));  // Db_R^-1 Q_R^H
+  }
+  __syncthreads();
+  double la = 0.0, ar = 0.0;
+  for (int k = 0; k < N; ++k) {
+    double bv = -1.0;
+    int bi = N;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const double a = zabs(Mid[(size_t)i * ld + k]);
+      if (a > bv) { bv = a; bi = i; }
+    }
+    const int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N || zabs(Mid[(size_t)p * ld + k]) == 0.0) return 1;
+    if (p != k) {
+      for (int j = tid; j < N; j += kThreads) {
+        double2 t = Mid[(size_t)k * ld + j]; Mid[(size_t)k * ld + j] = Mid[(size_t)p * ld + j]; Mid[(size_t)p * ld + j] = t;
+        t = X[(size_t)k * ld + j]; X[(size_t)k * ld + j] = X[(size_t)p * ld + j]; X[(size_t)p * ld + j] = t;
+      }
+      ar += 3.14159265358979323846;
+      __syncthreads();
+    }
+    const double2 d = Mid[(size_t)k * ld + k];
+    la += log(zabs(d));
+    ar += atan2(d.y, d.x);
+    const double2 dinv = zdiv(make_double2(1.0, 0.0), d);
+    __syncthreads();
+    for (int j = tid; j < N; j += kThreads) {
+      Mid[(size_t)k * ld + j] = zmul(Mid[(size_t)k * ld + j], dinv);
+      X[(size_t)k * ld + j] = zmul(X[(size_t)k * ld + j], dinv);
+    }
+    for (int i = tid; i < N; i += kThreads) S.hv[i] = (i == k) ? make_double2(0.0, 0.0) : Mid[(size_t)i * ld + k];
+    __syncthreads();
+    for (int e = tid; e < N * N; e += kThreads) {
+      const int i = e / N, j = e - i * N;
+      if (i == k) continue;
+      const double2 f = S.hv[i];
+      Mid[(size_t)i * ld + j] = zsub(Mid[(size_t)i * ld + j], zmul(f, Mid[(size_t)k * ld + j]));
+      X[(size_t)i * ld + j] = zsub(X[(size_t)i * ld + j], zmul(f, X[(size_t)k * ld + j]));
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    X[(size_t)i * ld + j] = zscal(1.0 / dbL[i], X[(size_t)i * ld + j]);
+  }
+  __syncthreads();
+  zgemm<0, 0, false>(N, N, N, Lf.Q, ld, (const double2*)X, ld, Gout, ld, S.gemm);
+  if (R.detq * Lf.detq < 0) ar += 3.14159265358979323846;
+  logabs = la + lsum;
+  arg = remainder(ar, 2.0 * 3.14159265358979323846);
+  return 0;
+}
+
+// -g sum over every slice and site of eta(l): the phase of the bosonic factor
+// exp(-i g sum eta) of the weight
+__device__ double bosonic_phase(const Su2Dev& C, Sm& S) {
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < C.L * C.N; e += kThreads) acc += hs_eta(C.fields[e]);
+  return -C.g * block_sum(acc, S.red);
+}
+
+// the phase of e^{-S}: exp(i (ph + 2 arg det(1 + B))) (two colors)
+__device__ inline double2 fresh_phase(double ph, double arg) { return zexpi(ph + 2.0 * arg); }
+
+// Left chain into the storage slots, then G(0) into W6 (Algorithm 1, before the sweeps).
+__device__ int z_fill_left(const Su2Dev& C, Sm& S, double& logabs, double& arg) {
+  const int nst = C.L / C.nw;
+  for (int j = nst - 1; j >= 0; --j) {
+    const ZUdv src = (j + 1 == nst) ? z_ident(C) : z_slot(C, j + 1);
+    const int dq = z_chain_step(C, j * C.nw, (j + 1) * C.nw, true, src, S);
+    z_store_slot(C, j, dq);
+  }
+  return z_green(C, z_ident(C), z_slot(C, 0), zmat(C, 6), logabs, arg, S);
+}
+
+// ---- the sweep --------------------------------------------------------------
+// V wrap: G_xy <- ph_x G_xy conj(ph_y) (ph = e^{+-V} of the slice)
+__device__ void z_v_wrap(const Su2Dev& C, double2* G, const double2* ph) {
+  const int N = C.N, ld = C.ld;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    G[(size_t)x * ld + y] = zmul(zmul(ph[x], G[(size_t)x * ld + y]), zconj(ph[y]));
+  }
+  __syncthreads();
+}
+
+// T wrap: up G <- E G E^-1, down G <- E^-1 G E
+__device__ void z_t_wrap(const Su2Dev& C, bool up, Sm& S) {
+  const int N = C.N, ld = C.ld;
+  zgemm<0, 0, false>(N, N, N, up ? C.E : C.Einv, ld, (const double2*)C.G, ld, C.Gt, ld, S.gemm);
+  zgemm<0, 0, false>(N, N, N, (const double2*)C.Gt, ld, up ? C.Einv : C.E, ld, C.G, ld, S.gemm);
+}
+
+// The sites of slice tau in order (up: 0..N-1, down: N-1..0).  Per proposal:
+// l' one of the other three values (index floor(3 u1)), dtheta = g (eta(l') -
+// eta(l)), Delta = e^{i dtheta} - 1, r1 = 1 + Delta (1 - G~_kk),
+//   R = gamma(l')/gamma(l) e^{-i dtheta} r1^2     (two colors share G~),
+// accepted when u2 < min(1, |Re(P R)| / |Re P|); then P <- P R / |P R| and
+// G~ <- G~ - (Delta / r1) G~[:, k] (e_k - G~[k, :]).  Rejections leave G~ and
+// P unchanged, so every remaining proposal's test is evaluated in parallel and
+// the first accepted one is applied.
+__device__ void z_update_slice(Su2Dev& C, int tau, int dir, const Su2SweepParams& P, Sm& S) {
+  const int N = C.N, ld = C.ld, tid = threadIdx.x;
+  double2* G = C.G;
+  const uint32_t key0 = (uint32_t)P.seed, key1 = (uint32_t)(P.seed >> 32) ^ C.chain_id;
+  for (int q = tid; q < N; q += kThreads) {
+    const int k = dir ? N - 1 - q : q;
+    uint32_t ctr[4] = {(uint32_t)P.sweep, (uint32_t)(2 * tau + dir), (uint32_t)k, (uint32_t)(P.sweep >> 32)};
+    philox4x32_10(ctr, key0, key1);
+    const double u1 = uniform53(ctr[0], ctr[1]);
+    S.u2[q] = uniform53(ctr[2], ctr[3]);
+    const int f = S.fsl[k];
+    const int fn = propose_field(2, f, u1);
+    const double dth = C.g * (hs_eta(fn) - hs_eta(f));
+    const double2 e = zexpi(dth);
+    S.delta[q] = make_double2(e.x - 1.0, e.y);
+    S.gr[q] = zscal(hs_gamma(fn) / hs_gamma(f), zconj(e));
+    S.fn[q] = (int8_t)fn;
+  }
+  for (int x = tid; x < N; x += kThreads) S.d[x] = G[(size_t)x * ld + x];
+  __syncthreads();
+  int pos = 0;
+  int64_t nacc = 0;
+  while (pos < N) {
+    if (tid == 0) *S.first = N;
+    __syncthreads();
+    const double2 Pc = *S.P;
+    for (int q = pos + tid; q < N; q += kThreads) {
+      const int k = dir ? N - 1 - q : q;
+      const double2 r1 = zadd(make_double2(1.0, 0.0), zmul(S.delta[q], zsub(make_double2(1.0, 0.0), S.d[k])));
+      const double2 R = zmul(S.gr[q], zmul(r1, r1));
+      const double ratio = fabs(zmul(Pc, R).x) / fabs(Pc.x);
+      if (S.u2[q] < (ratio < 1.0 ? ratio : 1.0)) {
+        atomicMin(S.first, q);
+        break;
+      }
+    }
+    __syncthreads();
+    const int first = *S.first;
+    if (first >= N) break;
+    const int k = dir ? N - 1 - first : first;
+    const double2 r1 = zadd(make_double2(1.0, 0.0), zmul(S.delta[first], zsub(make_double2(1.0, 0.0), S.d[k])));
+    const double2 coef = zdiv(S.delta[first], r1);
+    for (int x = tid; x < N; x += kThreads) {
+      S.col[x] = G[(size_t)x * ld + k];
+      const double2 gkx = G[(size_t)k * ld + x];
+      S.row[x] = make_double2((x == k ? 1.0 : 0.0) - gkx.x, -gkx.y);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double2 R = zmul(S.gr[first], zmul(r1, r1));
+      const double2 PR = zmul(Pc, R);
+      *S.P = zscal(1.0 / zabs(PR), PR);
+      S.fsl[k] = S.fn[first];
+    }
+    for (int e = tid; e < N * N; e += kThreads) {
+      const int x = e / N, y = e - x * N;
+      double2* gp = G + (size_t)x * ld + y;
+      *gp = zsub(*gp, zmul(zmul(coef, S.col[x]), S.row[y]));
+    }
+    for (int x = tid; x < N; x += kThreads) S.d[x] = zsub(S.d[x], zmul(zmul(coef, S.col[x]), S.row[x]));
+    ++nacc;
+    pos = first + 1;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    C.proposals += N;
+    C.accepted += nacc;
+  }
+}
+
+// Stabilisation event j (Sec. 2.3): the chain extended by n_wrap slices, the
+// stable G replaces the wrapped one (max and mean |dG| booked: "Precision
+// Green"), and the fresh phase replaces the carried one (|dP| booked:
+// "Precision Phase").  The new decomposition goes to slot j.
+__device__ void z_stabilise(Su2Dev& C, int j, bool up, Sm& S) {
+  const int N = C.N, ld = C.ld, nst = C.L / C.nw, nw = C.nw;
+  int dq;
+  ZUdv R, Lf;
+  if (up) {
+    const ZUdv src = (j == 1) ? z_ident(C) : z_slot(C, j - 1);
+    dq = z_chain_step(C, (j - 1) * nw, j * nw, false, src, S);
+    R = z_work(C, dq);
+    Lf = (j == nst) ? z_ident(C) : z_slot(C, j);
+  } else {
+    const ZUdv src = (j + 1 == nst) ? z_ident(C) : z_slot(C, j + 1);
+    dq = z_chain_step(C, j * nw, (j + 1) * nw, true, src, S);
+    Lf = z_work(C, dq);
+    R = (j == 0) ? z_ident(C) : z_slot(C, j);
+  }
+  double2* Gf = zmat(C, 6);
+  double la = 0.0, ar = 0.0;
+  const int bad = z_green(C, R, Lf, Gf, la, ar, S);
+  if (bad) {
+    if (threadIdx.x == 0) C.error |= 1;
+    z_store_slot(C, j, dq);
+    return;
+  }
+  double mx = 0.0, sm = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double2 gf = Gf[(size_t)x * ld + y];
+    const double dg = zabs(zsub(gf, C.G[(size_t)x * ld + y]));
+    mx = fmax(mx, dg);
+    sm += dg;
+    C.G[(size_t)x * ld + y] = gf;
+  }
+  mx = block_max(mx, S.red);
+  sm = block_sum(sm, S.red);
+  const double ph = bosonic_phase(C, S);
+  if (threadIdx.x == 0) {
+    const double2 Pf = fresh_phase(ph, ar);
+    C.phase_max = fmax(C.phase_max, zabs(zsub(*S.P, Pf)));
+    *S.P = Pf;
+    C.prec_sum += sm / ((double)N * N);
+    C.prec_max = fmax(C.prec_max, mx);
+    C.prec_events += 1;
+    C.logabs = la;
+    C.arg = ar;
+  }
+  z_store_slot(C, j, dq);
+}
+
+// Energy estimator at the current G (Sec. 6.1, both colors):
+//   Kin = 2 sum_xy K_xy (delta_xy - G_yx),
+//   Pot = U/2 sum_i <(n_i - 1)^2> = U/2 sum_i [2 (1 - G_ii)^2 - 2 (1 - G_ii) + 1],
+//   Part = 2 sum_i (1 - G_ii),
+// reweighted by sign * P / Re P (Sec. 5.1: ZS, ZP).
+__device__ void z_measure(Su2Dev& C, Sm& S) {
+  const int N = C.N, ld = C.ld;
+  double2 kin = make_double2(0.0, 0.0), pot = kin, part = kin;
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double2 g = C.G[(size_t)y * ld + x];
+    const double kxy = 2.0 * C.K[(size_t)x * ld + y];
+    kin = zadd(kin, make_double2(kxy * ((x == y ? 1.0 : 0.0) - g.x), -kxy * g.y));
+  }
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    const double2 gi = C.G[(size_t)i * ld + i];
+    const double2 h = make_double2(1.0 - gi.x, -gi.y);
+    const double2 q = zadd(zsub(zscal(2.0, zmul(h, h)), zscal(2.0, h)), make_double2(1.0, 0.0));
+    pot = zadd(pot, zscal(0.5 * C.U, q));
+    part = zadd(part, zscal(2.0, h));
+  }
+  kin = block_zsum(kin, S.red);
+  pot = block_zsum(pot, S.red);
+  part = block_zsum(part, S.red);
+  if (threadIdx.x == 0) {
+    const double2 Pc = *S.P;
+    const double sg = Pc.x >= 0.0 ? 1.0 : -1.0;
+    const double2 w = zscal(sg / Pc.x, Pc);
+    const double2 v[4] = {zmul(w, kin), zmul(w, pot), zmul(w, part), zmul(w, zadd(kin, pot))};
+    for (int q = 0; q < 4; ++q) {
+      C.meas[2 * q] += v[q].x;
+      C.meas[2 * q + 1] += v[q].y;
+    }
+    C.meas_sign += sg;
+    C.n_meas += 1;
+  }
+  __syncthreads();
+}
+
+__device__ inline void load_slice(const Su2Dev& C, int tau, Sm& S) {
+  for (int x = threadIdx.x; x < C.N; x += kThreads) S.fsl[x] = C.fields[(size_t)(tau - 1) * C.N + x];
+  __syncthreads();
+}
+__device__ inline void store_slice(const Su2Dev& C, int tau, Sm& S) {
+  for (int x = threadIdx.x; x < C.N; x += kThreads) C.fields[(size_t)(tau - 1) * C.N + x] = S.fsl[x];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) su2_sweep_kernel(Su2Dev* chains, Su2SweepParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Su2Dev& C = chains[blockIdx.x];
+  if (blockIdx.x >= P.n_chains) return;
+  Sm S = su2_carve(smem_raw, C.N);
+  const int L = C.L, nw = C.nw;
+  if (threadIdx.x == 0) *S.P = C.P;
+  __syncthreads();
+  for (int tau = 1; tau <= L; ++tau) {
+    load_slice(C, tau, S);
+    slice_phases(C, S.fsl, +1.0, S.ph);
+    z_v_wrap(C, C.G, S.ph);
+    z_update_slice(C, tau, 0, P, S);
+    store_slice(C, tau, S);
+    z_t_wrap(C, true, S);
+    if (tau % nw == 0) z_stabilise(C, tau / nw, true, S);
+    if (P.measure && tau >= P.meas_first && tau <= P.meas_last) z_measure(C, S);
+  }
+  for (int tau = L; tau >= 1; --tau) {
+    load_slice(C, tau, S);
+    z_t_wrap(C, false, S);
+    z_update_slice(C, tau, 1, P, S);
+    store_slice(C, tau, S);
+    slice_phases(C, S.fsl, -1.0, S.ph);
+    z_v_wrap(C, C.G, S.ph);
+    if ((tau - 1) % nw == 0) z_stabilise(C, (tau - 1) / nw, false, S);
+    if (P.measure && tau - 1 >= P.meas_first && tau - 1 <= P.meas_last) z_measure(C, S);
+  }
+  if (threadIdx.x == 0) {
+    C.P = *S.P;
+    C.sweep_sign_sum += (S.P->x >= 0.0) ? 1.0 : -1.0;
+  }
+}
+
+// mode 0: left chain, G(0) into the working G, log|det|, arg and the phase;
+// mode 1: the same chain recomputation for chain `only`, G(0) into out
+// ([N][N] complex), log|det| and arg booked, the working G and P untouched.
+__global__ void __launch_bounds__(kThreads) su2_fresh_kernel(Su2Dev* chains, int n_chains, int mode, int only,
+                                                            double2* out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = blockIdx.x;
+  if (c >= n_chains || (mode == 1 && c != only)) return;
+  Su2Dev& C = chains[c];
+  Sm S = su2_carve(smem_raw, C.N);
+  double la = 0.0, ar = 0.0;
+  if (z_fill_left(C, S, la, ar)) {
+    if (threadIdx.x == 0) C.error |= 1;
+    return;
+  }
+  const int N = C.N, ld = C.ld;
+  const double2* Gf = zmat(C, 6);
+  const double ph = bosonic_phase(C, S);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    if (mode == 0)
+      C.G[(size_t)x * ld + y] = Gf[(size_t)x * ld + y];
+    else
+      out[e] = Gf[(size_t)x * ld + y];
+  }
+  if (threadIdx.x == 0) {
+    C.logabs = la;
+    C.arg = ar;
+    if (mode == 0) C.P = fresh_phase(ph, ar);
+  }
+}
+
+__global__ void su2_copy_green_kernel(Su2Dev* chains, int chain, double2* out) {
+  const Su2Dev& C = chains[chain];
+  const int N = C.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * N; e += gridDim.x * blockDim.x) {
+    const int x = e / N, y = e - x * N;
+    out[e] = C.G[(size_t)x * C.ld + y];
+  }
+}
+
+// Four-valued fields i.i.d. uniform over (-2, -1, 1, 2) from Philox (counter
+// (0xFFFFFFFF, tau, x, 0xFFFFFFFF), key (seed_lo, seed_hi ^ chain)).
+__global__ void su2_init_fields_kernel(Su2Dev* chains, int n_chains, uint64_t seed) {
+  const int c = blockIdx.x;
+  if (c >= n_chains) return;
+  const Su2Dev& C = chains[c];
+  for (int e = threadIdx.x; e < C.L * C.N; e += blockDim.x) {
+    const int t = e / C.N, k = e - t * C.N;
+    uint32_t ctr[4] = {0xFFFFFFFFu, (uint32_t)(t + 1), (uint32_t)k, 0xFFFFFFFFu};
+    philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32) ^ C.chain_id);
+    const double u = uniform53(ctr[0], ctr[1]);
+    int idx = (int)floor(4.0 * u);
+    idx = idx > 3 ? 3 : idx;
+    const int8_t vals[4] = {-2, -1, 1, 2};
+    C.fields[e] = vals[idx];
+  }
+}
+
+__global__ void su2_reset_stats_kernel(Su2Dev* chains, int n_chains, int clear_meas) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chains) return;
+  Su2Dev& C = chains[c];
+  C.prec_sum = C.prec_max = C.phase_max = 0.0;
+  C.prec_events = C.proposals = C.accepted = 0;
+  C.sweep_sign_sum = 0.0;
+  C.error = 0;
+  if (clear_meas) {
+    for (int q = 0; q < 8; ++q) C.meas[q] = 0.0;
+    C.meas_sign = 0.0;
+    C.n_meas = 0;
+  }
+}
+
+}  // namespace
+
+size_t su2_smem_bytes(int maxN) { return su2_smem_layout(maxN); }
+
+static cudaError_t su2_set_smem(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t su2_launch_init_fields(Su2Dev* chains, int n_chains, uint64_t seed, cudaStream_t st) {
+  su2_init_fields_kernel<<<n_chains, kThreads, 0, st>>>(chains, n_chains, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t su2_launch_fresh(Su2Dev* chains, int n_chains, int mode, int only, double2* out, size_t smem,
+                             cudaStream_t st) {
+  cudaError_t e = su2_set_smem((const void*)su2_fresh_kernel, smem);
+  if (e != cudaSuccess) return e;
+  su2_fresh_kernel<<<n_chains, kThreads, smem, st>>>(chains, n_chains, mode, only, out);
+  return cudaGetLastError();
+}
+
+cudaError_t su2_launch_sweep(Su2Dev* chains, const Su2SweepParams& p, size_t smem, cudaStream_t st) {
+  cudaError_t e = su2_set_smem((const void*)su2_sweep_kernel, smem);
+  if (e != cudaSuccess) return e;
+  su2_sweep_kernel<<<p.n_chains, kThreads, smem, st>>>(chains, p);
+  return cudaGetLastError();
+}
+
+cudaError_t su2_launch_copy_green(Su2Dev* chains, int chain, double2* out, cudaStream_t st) {
+  su2_copy_green_kernel<<<16, kThreads, 0, st>>>(chains, chain, out);
+  return cudaGetLastError();
+}
+
+cudaError_t su2_launch_reset_stats(Su2Dev* chains, int n_chains, int clear_meas, cudaStream_t st) {
+  su2_reset_stats_kernel<<<(n_chains + 127) / 128, 128, 0, st>>>(chains, n_chains, clear_meas);
+  return cudaGetLastError();
+}
+
+}  // namespace dqmc

@@ -1,0 +1,340 @@
+// Host side of the C ABI declared in include/dqmc_su2.h: validation, the
+// exponentials exp(-+dtau K) of each model (Sec. 3.1, Op_set), the device arena
+// of every chain of the SU(2) decoupling, and the launches of dqmc_su2.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dqmc_su2.h"
+#include "dqmc_linalg_host.h"
+#include "dqmc_su2_internal.h"
+
+using dqmc::Su2Dev;
+
+struct dqmc_su2_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  dqmc_su2_opts opts{};
+  std::vector<dqmc_su2_model_desc> models;
+  std::vector<int> chain_model;
+  std::vector<Su2Dev> chains_h;
+  Su2Dev* chains_d = nullptr;
+  std::vector<void*> allocs;
+  size_t smem = 0;
+  uint64_t sweep_counter = 0;
+  int maxN = 0;
+  double2* out_scratch = nullptr;  // [maxN][maxN] complex for dqmc_su2_greens
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+dqmc_status fail(dqmc_su2_ctx* ctx, dqmc_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+#define SU2_CUDA_TRY(ctx, expr)                                                                  \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess) return fail((ctx), DQMC_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kMaxSites = 1024;
+
+dqmc_status validate(dqmc_su2_ctx* ctx, const dqmc_su2_model_desc& m, int idx) {
+  if (m.n_sites < 1 || m.n_sites > kMaxSites)
+    return fail(ctx, DQMC_EINVAL, "model %d: n_sites must be in 1..%d", idx, kMaxSites);
+  if (!m.hopping) return fail(ctx, DQMC_EINVAL, "model %d: null hopping", idx);
+  if (!(m.dtau > 0.0) || !std::isfinite(m.dtau)) return fail(ctx, DQMC_EINVAL, "model %d: dtau must be > 0", idx);
+  if (!(m.U >= 0.0) || !std::isfinite(m.U)) return fail(ctx, DQMC_EINVAL, "model %d: U must be >= 0", idx);
+  if (m.L < 1 || m.n_wrap < 1 || m.L % m.n_wrap != 0)
+    return fail(ctx, DQMC_EINVAL, "model %d: need L >= 1, n_wrap >= 1 and L %% n_wrap == 0", idx);
+  const int N = m.n_sites;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      const double a = m.hopping[(size_t)i * N + j], b = m.hopping[(size_t)j * N + i];
+      if (!std::isfinite(a)) return fail(ctx, DQMC_EINVAL, "model %d: non-finite hopping", idx);
+      if (std::fabs(a - b) > 1e-12 * (1.0 + std::fabs(a))) return fail(ctx, DQMC_EINVAL, "model %d: hopping not symmetric", idx);
+    }
+  return DQMC_OK;
+}
+
+template <typename T>
+dqmc_status dev_alloc(dqmc_su2_ctx* ctx, T** p, size_t n) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, n * sizeof(T) + 16) != cudaSuccess) return fail(ctx, DQMC_ENOMEM, "cudaMalloc of %zu bytes", n * sizeof(T));
+  ctx->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return DQMC_OK;
+}
+
+dqmc_status check_fields(dqmc_su2_ctx* ctx, const int8_t* f, size_t n) {
+  for (size_t e = 0; e < n; ++e)
+    if (f[e] != 1 && f[e] != -1 && f[e] != 2 && f[e] != -2)
+      return fail(ctx, DQMC_EINVAL, "field value %d at %zu is not in {-2, -1, 1, 2}", (int)f[e], e);
+  return DQMC_OK;
+}
+
+size_t total_fields(const dqmc_su2_ctx* ctx) {
+  size_t n = 0;
+  for (const Su2Dev& C : ctx->chains_h) n += (size_t)C.L * C.N;
+  return n;
+}
+
+dqmc_status download(dqmc_su2_ctx* ctx) {
+  SU2_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->chains_h.data(), ctx->chains_d, sizeof(Su2Dev) * ctx->chains_h.size(),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  SU2_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return DQMC_OK;
+}
+
+// left chains, G(0), log|det|, arg and phase of every chain from its fields
+dqmc_status refill(dqmc_su2_ctx* ctx) {
+  const int n = (int)ctx->chains_h.size();
+  SU2_CUDA_TRY(ctx, dqmc::su2_launch_reset_stats(ctx->chains_d, n, 0, ctx->stream));
+  SU2_CUDA_TRY(ctx, dqmc::su2_launch_fresh(ctx->chains_d, n, 0, -1, nullptr, ctx->smem, ctx->stream));
+  dqmc_status st = download(ctx);
+  if (st) return st;
+  for (const Su2Dev& C : ctx->chains_h)
+    if (C.error) return fail(ctx, DQMC_EUNSTABLE, "chain %u: singular matrix in the stabilisation", C.chain_id);
+  return DQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dqmc_status dqmc_su2_init(const dqmc_su2_model_desc* models, int32_t n_models, const int32_t* chain_model,
+                          int32_t n_chains, const int8_t* fields, const dqmc_su2_opts* opts, void* cuda_stream,
+                          dqmc_su2_ctx** out) {
+  if (!out) return DQMC_EINVAL;
+  *out = nullptr;
+  dqmc_su2_ctx* ctx = new dqmc_su2_ctx();
+  *out = ctx;
+  if (!models || n_models < 1 || !chain_model || n_chains < 1 || !opts)
+    return fail(ctx, DQMC_EINVAL, "null argument or empty model / chain list");
+  ctx->opts = *opts;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  for (int i = 0; i < n_models; ++i) {
+    dqmc_status st = validate(ctx, models[i], i);
+    if (st) return st;
+    ctx->models.push_back(models[i]);
+  }
+  for (int c = 0; c < n_chains; ++c) {
+    if (chain_model[c] < 0 || chain_model[c] >= n_models)
+      return fail(ctx, DQMC_EINVAL, "chain %d: model index %d out of range", c, chain_model[c]);
+    ctx->chain_model.push_back(chain_model[c]);
+  }
+  if (opts->measure && opts->meas_first > opts->meas_last)
+    return fail(ctx, DQMC_EINVAL, "meas_first > meas_last");
+  SU2_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev0));
+  SU2_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev1));
+  // per model: K, E = exp(-dtau K), E^-1, the identity and a vector of ones
+  struct Dm { double *K, *E, *Einv, *ones; double2* ident; int ld; };
+  std::vector<Dm> dm(n_models);
+  for (int i = 0; i < n_models; ++i) {
+    const dqmc_su2_model_desc& m = models[i];
+    const int N = m.n_sites, ld = N;
+    std::vector<double> K(m.hopping, m.hopping + (size_t)N * N), w, V;
+    dqmc::host::symmetric_eigen(N, K, w, V);
+    const std::vector<double> E = dqmc::host::expm_symmetric(N, w, V, -m.dtau);
+    const std::vector<double> Ei = dqmc::host::expm_symmetric(N, w, V, +m.dtau);
+    for (double x : E)
+      if (!std::isfinite(x)) return fail(ctx, DQMC_EINVAL, "model %d: exp(-dtau K) is not finite", i);
+    for (double x : Ei)
+      if (!std::isfinite(x)) return fail(ctx, DQMC_EINVAL, "model %d: exp(dtau K) is not finite", i);
+    std::vector<double2> I((size_t)N * ld, make_double2(0.0, 0.0));
+    for (int x = 0; x < N; ++x) I[(size_t)x * ld + x] = make_double2(1.0, 0.0);
+    std::vector<double> ones(ld, 1.0);
+    Dm& d = dm[i];
+    d.ld = ld;
+    dqmc_status st;
+    if ((st = dev_alloc(ctx, &d.K, K.size())) || (st = dev_alloc(ctx, &d.E, E.size())) ||
+        (st = dev_alloc(ctx, &d.Einv, Ei.size())) || (st = dev_alloc(ctx, &d.ident, I.size())) ||
+        (st = dev_alloc(ctx, &d.ones, ones.size())))
+      return st;
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.K, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice));
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.E, E.data(), E.size() * sizeof(double), cudaMemcpyHostToDevice));
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.Einv, Ei.data(), Ei.size() * sizeof(double), cudaMemcpyHostToDevice));
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.ident, I.data(), I.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.ones, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice));
+    ctx->maxN = std::max(ctx->maxN, N);
+  }
+  // per chain: one arena
+  size_t foff = 0;
+  for (int c = 0; c < n_chains; ++c) {
+    const dqmc_su2_model_desc& m = models[chain_model[c]];
+    const Dm& d = dm[chain_model[c]];
+    const int N = m.n_sites, ld = d.ld, nst = m.L / m.n_wrap;
+    Su2Dev C{};
+    C.N = N; C.ld = ld; C.L = m.L; C.nw = m.n_wrap;
+    C.dtau = m.dtau; C.U = m.U; C.g = std::sqrt(0.5 * m.dtau * m.U);
+    C.K = d.K; C.E = d.E; C.Einv = d.Einv; C.ident = d.ident; C.ones = d.ones;
+    C.chain_id = (uint32_t)c;
+    dqmc_status st;
+    if ((st = dev_alloc(ctx, &C.fields, (size_t)m.L * N)) || (st = dev_alloc(ctx, &C.G, (size_t)N * ld)) ||
+        (st = dev_alloc(ctx, &C.Gt, (size_t)N * ld)) ||
+        (st = dev_alloc(ctx, &C.slots, (size_t)(nst + 1) * dqmc::su2_slot_elems(N, ld))) ||
+        (st = dev_alloc(ctx, &C.slotD, (size_t)(nst + 1) * ld)) || (st = dev_alloc(ctx, &C.slot_detq, nst + 1)) ||
+        (st = dev_alloc(ctx, &C.work, dqmc::su2_work_elems(N, ld))) ||
+        (st = dev_alloc(ctx, &C.dwork, (size_t)dqmc::kSu2DVecs * ld)) || (st = dev_alloc(ctx, &C.iwork, ld)))
+      return st;
+    if (fields) {
+      dqmc_status fs = check_fields(ctx, fields + foff, (size_t)m.L * N);
+      if (fs) return fs;
+      SU2_CUDA_TRY(ctx, cudaMemcpy(C.fields, fields + foff, (size_t)m.L * N, cudaMemcpyHostToDevice));
+    }
+    foff += (size_t)m.L * N;
+    ctx->chains_h.push_back(C);
+  }
+  SU2_CUDA_TRY(ctx, cudaMalloc(&ctx->chains_d, sizeof(Su2Dev) * n_chains));
+  SU2_CUDA_TRY(ctx, cudaMalloc(&ctx->out_scratch, sizeof(double2) * (size_t)ctx->maxN * ctx->maxN));
+  SU2_CUDA_TRY(ctx, cudaMemcpy(ctx->chains_d, ctx->chains_h.data(), sizeof(Su2Dev) * n_chains,
+                               cudaMemcpyHostToDevice));
+  ctx->smem = dqmc::su2_smem_bytes(ctx->maxN);
+  if (!fields) SU2_CUDA_TRY(ctx, dqmc::su2_launch_init_fields(ctx->chains_d, n_chains, opts->seed, ctx->stream));
+  SU2_CUDA_TRY(ctx, dqmc::su2_launch_reset_stats(ctx->chains_d, n_chains, 1, ctx->stream));
+  return refill(ctx);
+}
+
+dqmc_status dqmc_su2_sweep(dqmc_su2_ctx* ctx, int32_t n_sweeps, dqmc_su2_sweep_stats* stats) {
+  if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
+  if (n_sweeps < 1) return fail(ctx, DQMC_EINVAL, "n_sweeps must be >= 1");
+  const int n = (int)ctx->chains_h.size();
+  SU2_CUDA_TRY(ctx, dqmc::su2_launch_reset_stats(ctx->chains_d, n, 0, ctx->stream));
+  SU2_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+  for (int s = 0; s < n_sweeps; ++s) {
+    dqmc::Su2SweepParams p{};
+    p.seed = ctx->opts.seed;
+    p.sweep = ctx->sweep_counter++;
+    p.measure = ctx->opts.measure;
+    p.meas_first = ctx->opts.meas_first;
+    p.meas_last = ctx->opts.meas_last;
+    p.n_chains = n;
+    SU2_CUDA_TRY(ctx, dqmc::su2_launch_sweep(ctx->chains_d, p, ctx->smem, ctx->stream));
+  }
+  SU2_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+  dqmc_status st = download(ctx);
+  if (st) return st;
+  float ms = 0.f;
+  SU2_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  dqmc_su2_sweep_stats S{};
+  double prec_sum = 0.0, sign_sum = 0.0;
+  int64_t events = 0;
+  int err = 0;
+  for (const Su2Dev& C : ctx->chains_h) {
+    S.proposals += C.proposals;
+    S.accepted += C.accepted;
+    prec_sum += C.prec_sum;
+    events += C.prec_events;
+    S.prec_green_max = std::max(S.prec_green_max, C.prec_max);
+    S.prec_phase_max = std::max(S.prec_phase_max, C.phase_max);
+    sign_sum += C.sweep_sign_sum;
+    err |= C.error;
+  }
+  S.prec_green_mean = events ? prec_sum / (double)events : 0.0;
+  S.mean_sign = sign_sum / ((double)n_sweeps * n);
+  S.ms_total = ms;
+  if (stats) *stats = S;
+  if (err) return fail(ctx, DQMC_EUNSTABLE, "singular matrix in the stabilisation");
+  const double thr = ctx->opts.unstable_threshold;
+  if (thr > 0.0 && (S.prec_green_max > thr || S.prec_phase_max > thr))
+    return fail(ctx, DQMC_EUNSTABLE, "precision %.3e / phase %.3e above the threshold %.3e", S.prec_green_max,
+                S.prec_phase_max, thr);
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_su2_greens(dqmc_su2_ctx* ctx, int32_t chain, int32_t fresh, double* out, int32_t out_is_device,
+                            double* logabs_out, double* arg_out, double* phase_out) {
+  if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
+  if (chain < 0 || chain >= (int)ctx->chains_h.size() || !out) return fail(ctx, DQMC_EINVAL, "bad chain or output");
+  const int N = ctx->chains_h[chain].N;
+  const size_t bytes = sizeof(double2) * (size_t)N * N;
+  double2* dst = out_is_device ? reinterpret_cast<double2*>(out) : ctx->out_scratch;
+  if (fresh)
+    SU2_CUDA_TRY(ctx, dqmc::su2_launch_fresh(ctx->chains_d, (int)ctx->chains_h.size(), 1, chain, dst, ctx->smem,
+                                             ctx->stream));
+  else
+    SU2_CUDA_TRY(ctx, dqmc::su2_launch_copy_green(ctx->chains_d, chain, dst, ctx->stream));
+  if (!out_is_device)
+    SU2_CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->out_scratch, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  dqmc_status st = download(ctx);
+  if (st) return st;
+  const Su2Dev& C = ctx->chains_h[chain];
+  if (C.error) return fail(ctx, DQMC_EUNSTABLE, "chain %d: singular matrix in the stabilisation", chain);
+  if (logabs_out) *logabs_out = C.logabs;
+  if (arg_out) *arg_out = C.arg;
+  if (phase_out) { phase_out[0] = C.P.x; phase_out[1] = C.P.y; }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas, int32_t reset) {
+  if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
+  dqmc_status st = download(ctx);
+  if (st) return st;
+  for (size_t c = 0; c < ctx->chains_h.size(); ++c) {
+    const Su2Dev& C = ctx->chains_h[c];
+    if (out)
+      for (int q = 0; q < 8; ++q) out[c * 8 + q] = C.meas[q];
+    if (sign_sum) sign_sum[c] = C.meas_sign;
+    if (n_meas) n_meas[c] = C.n_meas;
+  }
+  if (reset) SU2_CUDA_TRY(ctx, dqmc::su2_launch_reset_stats(ctx->chains_d, (int)ctx->chains_h.size(), 1, ctx->stream));
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_su2_get_fields(dqmc_su2_ctx* ctx, int8_t* out, uint64_t* sweep_counter) {
+  if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
+  if (out) {
+    size_t off = 0;
+    for (const Su2Dev& C : ctx->chains_h) {
+      SU2_CUDA_TRY(ctx, cudaMemcpyAsync(out + off, C.fields, (size_t)C.L * C.N, cudaMemcpyDeviceToHost, ctx->stream));
+      off += (size_t)C.L * C.N;
+    }
+    SU2_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  if (sweep_counter) *sweep_counter = ctx->sweep_counter;
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_su2_set_fields(dqmc_su2_ctx* ctx, const int8_t* in, uint64_t sweep_counter) {
+  if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
+  if (!in) return fail(ctx, DQMC_EINVAL, "null fields");
+  dqmc_status st = check_fields(ctx, in, total_fields(ctx));
+  if (st) return st;
+  size_t off = 0;
+  for (const Su2Dev& C : ctx->chains_h) {
+    SU2_CUDA_TRY(ctx, cudaMemcpyAsync(C.fields, in + off, (size_t)C.L * C.N, cudaMemcpyHostToDevice, ctx->stream));
+    off += (size_t)C.L * C.N;
+  }
+  ctx->sweep_counter = sweep_counter;
+  return refill(ctx);
+}
+
+const char* dqmc_su2_last_error(const dqmc_su2_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void dqmc_su2_destroy(dqmc_su2_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->chains_d) cudaFree(ctx->chains_d);
+  if (ctx->out_scratch) cudaFree(ctx->out_scratch);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+}
+
+}  // extern "C"

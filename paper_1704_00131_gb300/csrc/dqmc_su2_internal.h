@@ -1,0 +1,74 @@
+// Internal declarations of the SU(2) charge-decoupling path, shared by the
+// host side (dqmc_su2_api.cu) and the kernels (dqmc_su2.cu).  Not part of the
+// public C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dqmc {
+
+// Device-resident description and state of one Markov chain of the SU(2)
+// decoupling (Sec. 6.1).  One CTA works on it.  Complex matrices are double2
+// (re, im), row-major with leading dimension `ld` (in complex elements).
+struct Su2Dev {
+  // model: B_tau = E exp(V_tau), V_tau = diag(i g eta(l_tau,x)), g = sqrt(dtau U / 2)
+  int N, ld, L, nw;
+  double dtau, U, g;
+  const double* K;        // hopping [N][ld] (real symmetric, -mu on the diagonal)
+  const double* E;        // exp(-dtau K) [N][ld]
+  const double* Einv;     // exp(+dtau K) [N][ld]
+  const double2* ident;   // identity [N][ld] (Q and T of the empty chain)
+  const double* ones;     // [ld] of 1 (its D)
+  // state
+  int8_t* fields;         // [L][N], four-valued l in {-2, -1, 1, 2}
+  double2* G;             // working G [N][ld]
+  double2* Gt;            // scratch of the wraps [N][ld]
+  double2* slots;         // (L/nw + 1) x {Q [N][ld], T [N][ld]}
+  double* slotD;          // (L/nw + 1) x D [ld]
+  int* slot_detq;         // [L/nw + 1]: det Q = +-1 (product of Householder reflectors)
+  double2* work;          // kSu2Mats complex matrices [N][ld], then kSu2ZVecs complex vectors [ld]
+  double* dwork;          // kSu2DVecs real vectors [ld]
+  int* iwork;             // [ld] pivot order
+  uint32_t chain_id;
+  double2 P;              // phase of e^{-S(C)}: exp(i (ph + 2 arg det(1 + B(beta,0)))), ph = -g sum eta
+  double logabs, arg;     // log|det(1 + B(beta,0))| and its argument at the last fresh G
+  // statistics of the current dqmc_su2_sweep call
+  double prec_sum, prec_max, phase_max;
+  int64_t prec_events, proposals, accepted;
+  double sweep_sign_sum;
+  // reweighted measurement sums: (re, im) of kin, pot, part, ener; sum of signs; count
+  double meas[8];
+  double meas_sign;
+  int64_t n_meas;
+  int error;              // bit 0: a singular matrix in the stabilisation
+};
+
+constexpr int kSu2Mats = 8;   // complex N x ld work matrices per chain
+constexpr int kSu2ZVecs = 4;  // complex work vectors per chain
+constexpr int kSu2DVecs = 10; // real work vectors per chain
+
+__host__ __device__ inline size_t su2_slot_elems(int N, int ld) { return (size_t)2 * N * ld; }
+__host__ __device__ inline size_t su2_work_elems(int N, int ld) {
+  return (size_t)kSu2Mats * N * ld + (size_t)kSu2ZVecs * ld;
+}
+
+struct Su2SweepParams {
+  uint64_t seed;
+  uint64_t sweep;       // Philox sweep counter of this sweep
+  int measure, meas_first, meas_last;
+  int n_chains;
+};
+
+// launchers (dqmc_su2.cu)
+size_t su2_smem_bytes(int maxN);
+cudaError_t su2_launch_init_fields(Su2Dev* chains, int n_chains, uint64_t seed, cudaStream_t st);
+// mode 0: recompute the left chain and G(0) of every chain, write the working
+// G, log|det|, arg and the phase P; mode 1: the same for chain `only` into
+// `out` ([N][N] complex) without touching the working G or P
+cudaError_t su2_launch_fresh(Su2Dev* chains, int n_chains, int mode, int only, double2* out, size_t smem,
+                             cudaStream_t st);
+cudaError_t su2_launch_sweep(Su2Dev* chains, const Su2SweepParams& p, size_t smem, cudaStream_t st);
+cudaError_t su2_launch_copy_green(Su2Dev* chains, int chain, double2* out, cudaStream_t st);
+cudaError_t su2_launch_reset_stats(Su2Dev* chains, int n_chains, int clear_meas, cudaStream_t st);
+
+}  // namespace dqmc

@@ -63,10 +63,13 @@ struct Umma {
   uint64_t* bar;          // shared, 128 bytes: [0, 48) the 2 kUmmaStages mbarriers (copies landed
                           // per stage, then MMAs done per stage); [48, 96) thread 0's counters
                           // of copies and MMA commits issued and waited per stage; [96, 100)
-                          // the TMEM slot; [100, 104) thread 0's count of products
+                          // the TMEM slot; [100, 104) thread 0's count of products; [104, 112)
+                          // a barrier that nothing arrives on (the test_stall hook)
   uint32_t* tmem_slot;    // tcgen05.alloc writes the accumulator base here
   int* err;               // chain error word (nonzero: a wait gave up)
   long long limit;        // SM cycles after which a wait gives up
+  int stall;              // test hook: the first wait of a product waits on the barrier at
+                          // [104, 112), which gives up after `limit`
   int* where;             // [6] or null: the first wait that gave up (kind, chunk, chunks,
                           // product ordinal, barrier word)
 };
@@ -77,6 +80,7 @@ __device__ __forceinline__ unsigned char* umma_stage(const Umma& U, int st) {
 // thread 0's counters (shared): copies issued / waited, commits issued / waited, per stage
 __device__ __forceinline__ uint32_t* umma_book(const Umma& U) { return reinterpret_cast<uint32_t*>(U.bar + 2 * kUmmaStages); }
 __device__ __forceinline__ uint32_t* umma_calls(const Umma& U) { return U.tmem_slot + 1; }
+__device__ __forceinline__ uint64_t* umma_never(const Umma& U) { return U.bar + 2 * kUmmaStages + 7; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -158,6 +162,7 @@ __device__ inline void umma_alloc(const Umma& U) {
   // never re-initialised while an arrival could still be on its way
   if (threadIdx.x == 0) {
     for (int q = 0; q < 2 * kUmmaStages; ++q) mbar_init(U.bar + q);
+    mbar_init(umma_never(U));
     uint32_t* book = umma_book(U);
     for (int q = 0; q < 4 * kUmmaStages; ++q) book[q] = 0u;
     *umma_calls(U) = 0u;
@@ -386,7 +391,10 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
     const int tile = g / nkc, kc = g - tile * nkc, mt = tile / nnt, nt = tile - mt * nnt;
     if (kc % segc == 0) written = 0u;
     if (tid == 0 && live) {
-      if (!wait_copy(st, U.limit)) {
+      bool landed = wait_copy(st, U.limit);
+      // test hook: a wait that cannot end (its barrier's phase 0 never completes)
+      if (landed && U.stall && g == 0) landed = mbar_wait(umma_never(U), 0u, U.limit);
+      if (!landed) {
         gave_up(1, g);
       } else {
         tc_fence_after();

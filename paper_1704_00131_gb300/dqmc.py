@@ -1,4 +1,5 @@
-"""ctypes binding of the C ABI in include/dqmc.h (argument marshalling only).
+"""ctypes binding of the C ABI in include/dqmc.h and include/dqmc_su2.h
+(argument marshalling only).
 
 Every step of the sweep runs in the CUDA kernels of libdqmc.so; this module
 only packs numpy/torch arguments into the C structs and unpacks results.  It
@@ -22,7 +23,9 @@ PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tc": 3}
 
 EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_greens_tau", "dqmc_measure", "dqmc_measure_tau",
             "dqmc_measure_tau_corr", "dqmc_measure_corr", "dqmc_logdet_backward", "dqmc_energy_backward", "dqmc_get_fields",
-            "dqmc_set_fields", "dqmc_green_fresh_noalloc", "dqmc_last_error", "dqmc_destroy"]
+            "dqmc_set_fields", "dqmc_green_fresh_noalloc", "dqmc_last_error", "dqmc_destroy",
+            "dqmc_su2_init", "dqmc_su2_sweep", "dqmc_su2_greens", "dqmc_su2_measure", "dqmc_su2_get_fields",
+            "dqmc_su2_set_fields", "dqmc_su2_last_error", "dqmc_su2_destroy"]
 
 
 class DqmcError(RuntimeError):
@@ -59,6 +62,7 @@ class RunOpts(ctypes.Structure):
         ("spin_limit", ctypes.c_int64),
         ("tc_min_sites", ctypes.c_int32),
         ("dd_tile", ctypes.c_int32),
+        ("test_stall", ctypes.c_int32),
     ]
 
 
@@ -128,6 +132,22 @@ def load() -> ctypes.CDLL:
     L.dqmc_last_error.restype = ctypes.c_char_p
     L.dqmc_destroy.argtypes = [vp]
     L.dqmc_destroy.restype = None
+    L.dqmc_su2_init.argtypes = [vp, i32, vp, i32, vp, vp, vp, ctypes.POINTER(vp)]
+    L.dqmc_su2_init.restype = ctypes.c_int
+    L.dqmc_su2_sweep.argtypes = [vp, i32, vp]
+    L.dqmc_su2_sweep.restype = ctypes.c_int
+    L.dqmc_su2_greens.argtypes = [vp, i32, i32, vp, i32, vp, vp, vp]
+    L.dqmc_su2_greens.restype = ctypes.c_int
+    L.dqmc_su2_measure.argtypes = [vp, vp, vp, vp, i32]
+    L.dqmc_su2_measure.restype = ctypes.c_int
+    L.dqmc_su2_get_fields.argtypes = [vp, vp, vp]
+    L.dqmc_su2_get_fields.restype = ctypes.c_int
+    L.dqmc_su2_set_fields.argtypes = [vp, vp, u64]
+    L.dqmc_su2_set_fields.restype = ctypes.c_int
+    L.dqmc_su2_last_error.argtypes = [vp]
+    L.dqmc_su2_last_error.restype = ctypes.c_char_p
+    L.dqmc_su2_destroy.argtypes = [vp]
+    L.dqmc_su2_destroy.restype = None
     del i64, d
     _lib = L
     return L
@@ -150,7 +170,7 @@ class Ensemble:
     def __init__(self, models: list[ModelSpec], chain_model, fields=None, precision: str = "fp64",
                  delay_k: int = 16, seed: int = 0, measure: bool = False, meas_first: int = 0,
                  meas_last: int | None = None, unstable_threshold: float = 0.0, stream=None, spin_limit: int = 0,
-                 tc_min_sites: int = 0, dd_tile: int = 0):
+                 tc_min_sites: int = 0, dd_tile: int = 0, test_stall: int = 0):
         self._lib = load()
         self._h = ctypes.c_void_p()
         self.models = list(models)
@@ -170,7 +190,8 @@ class Ensemble:
         self._descs = descs
         ml = max(m.L for m in self.models) if meas_last is None else meas_last
         self.opts = RunOpts(PREC[precision], int(delay_k), int(measure), int(meas_first), int(ml), int(seed),
-                            float(unstable_threshold), int(spin_limit), int(tc_min_sites), int(dd_tile))
+                            float(unstable_threshold), int(spin_limit), int(tc_min_sites), int(dd_tile),
+                            int(test_stall))
         fptr = None
         if fields is not None:
             packed = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int8).ravel() for f in fields]))
@@ -349,3 +370,154 @@ class Ensemble:
         gU = np.zeros(n_cfg)
         self._check(self._lib.dqmc_energy_backward(self._h, int(model_index), _p(f), n_cfg, _p(e), _p(gK), _p(gU)))
         return e, gK, gU
+
+
+# ---------------------------------------------------------------------------
+# SU(2) charge decoupling with complex coupling (include/dqmc_su2.h)
+# ---------------------------------------------------------------------------
+class Su2ModelDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_sites", ctypes.c_int32),
+        ("hopping", ctypes.POINTER(ctypes.c_double)),
+        ("U", ctypes.c_double),
+        ("dtau", ctypes.c_double),
+        ("L", ctypes.c_int32),
+        ("n_wrap", ctypes.c_int32),
+    ]
+
+
+class Su2Opts(ctypes.Structure):
+    _fields_ = [
+        ("measure", ctypes.c_int32),
+        ("meas_first", ctypes.c_int32),
+        ("meas_last", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("unstable_threshold", ctypes.c_double),
+    ]
+
+
+class Su2SweepStats(ctypes.Structure):
+    _fields_ = [
+        ("proposals", ctypes.c_int64),
+        ("accepted", ctypes.c_int64),
+        ("prec_green_mean", ctypes.c_double),
+        ("prec_green_max", ctypes.c_double),
+        ("prec_phase_max", ctypes.c_double),
+        ("mean_sign", ctypes.c_double),
+        ("ms_total", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+@dataclass
+class Su2Model:
+    """One lattice of the SU(2) Hubbard model: hopping K [N, N] (-mu on the
+    diagonal), U, dtau, L slices, stabilisation interval n_wrap."""
+    hopping: np.ndarray
+    U: float
+    dtau: float
+    L: int
+    n_wrap: int
+
+    @property
+    def N(self) -> int:
+        return int(self.hopping.shape[0])
+
+
+class Su2Ensemble:
+    """Markov chains of the SU(2) decoupling on one GPU (one dqmc_su2_ctx)."""
+
+    def __init__(self, models: list[Su2Model], chain_model, fields=None, seed: int = 0, measure: bool = False,
+                 meas_first: int = 0, meas_last: int | None = None, unstable_threshold: float = 0.0, stream=None):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        self.models = list(models)
+        self.chain_model = np.ascontiguousarray(chain_model, dtype=np.int32)
+        self._keep = []
+        descs = (Su2ModelDesc * len(self.models))()
+        for i, m in enumerate(self.models):
+            H = np.ascontiguousarray(m.hopping, dtype=np.float64)
+            self._keep.append(H)
+            descs[i] = Su2ModelDesc(m.N, H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(m.U),
+                                    float(m.dtau), int(m.L), int(m.n_wrap))
+        self._descs = descs
+        ml = max(m.L for m in self.models) if meas_last is None else meas_last
+        self.opts = Su2Opts(int(measure), int(meas_first), int(ml), int(seed), float(unstable_threshold))
+        fptr = None
+        if fields is not None:
+            packed = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int8).ravel() for f in fields]))
+            self._keep.append(packed)
+            fptr = _p(packed)
+        st_ptr = None
+        if stream is not None:
+            st_ptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        st = self._lib.dqmc_su2_init(ctypes.cast(descs, ctypes.c_void_p), len(self.models), _p(self.chain_model),
+                                     len(self.chain_model), fptr, ctypes.byref(self.opts), st_ptr,
+                                     ctypes.byref(self._h))
+        if st != DQMC_OK:
+            msg = self._lib.dqmc_su2_last_error(self._h).decode() if self._h.value else "init failed"
+            self.close()
+            raise DqmcError(st, msg)
+
+    def _check(self, st: int):
+        if st != DQMC_OK:
+            raise DqmcError(st, self._lib.dqmc_su2_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.dqmc_su2_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_chains(self) -> int:
+        return int(len(self.chain_model))
+
+    def model_of(self, c: int) -> Su2Model:
+        return self.models[int(self.chain_model[c])]
+
+    def sweep(self, n: int = 1) -> dict:
+        s = Su2SweepStats()
+        self._check(self._lib.dqmc_su2_sweep(self._h, int(n), ctypes.byref(s)))
+        return s.as_dict()
+
+    def greens(self, chain: int, fresh: bool = False):
+        """(G(0) complex [N, N], log|det(1+B)|, arg det(1+B), phase P complex) of a chain."""
+        N = self.model_of(chain).N
+        G = np.zeros((N, N, 2))
+        la, ar = ctypes.c_double(), ctypes.c_double()
+        ph = np.zeros(2)
+        self._check(self._lib.dqmc_su2_greens(self._h, int(chain), int(fresh), _p(G), 0, ctypes.byref(la),
+                                              ctypes.byref(ar), _p(ph)))
+        return G[..., 0] + 1j * G[..., 1], la.value, ar.value, complex(ph[0], ph[1])
+
+    def measure(self, reset: bool = False):
+        """(complex [n_chains, 4] reweighted sums of Kin, Pot, Part, Ener; sign sums; counts)."""
+        out = np.zeros((self.n_chains, 4, 2))
+        sg = np.zeros(self.n_chains)
+        nm = np.zeros(self.n_chains, dtype=np.int64)
+        self._check(self._lib.dqmc_su2_measure(self._h, _p(out), _p(sg), _p(nm), int(reset)))
+        return out[..., 0] + 1j * out[..., 1], sg, nm
+
+    def get_fields(self):
+        total = sum(self.model_of(c).L * self.model_of(c).N for c in range(self.n_chains))
+        buf = np.zeros(total, dtype=np.int8)
+        ctr = ctypes.c_uint64()
+        self._check(self._lib.dqmc_su2_get_fields(self._h, _p(buf), ctypes.byref(ctr)))
+        out, off = [], 0
+        for c in range(self.n_chains):
+            m = self.model_of(c)
+            out.append(buf[off:off + m.L * m.N].reshape(m.L, m.N).copy())
+            off += m.L * m.N
+        return out, ctr.value
+
+    def set_fields(self, fields, sweep_counter: int = 0):
+        packed = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int8).ravel() for f in fields]))
+        self._check(self._lib.dqmc_su2_set_fields(self._h, _p(packed), int(sweep_counter)))

@@ -417,15 +417,19 @@ def test_unstable_threshold_reports_eunstable(dq):
 
 def test_tensor_core_wait_limit_reports_etimeout(dq):
     """The tensor-core products wait on their bulk copies and MMAs with a bounded
-    spin (dqmc_run_opts.spin_limit SM cycles).  With a limit of one cycle the first
-    wait gives up: the kernel stops issuing, drains what is in flight, frees its
-    tensor memory and returns, and the call reports DQMC_ETIMEOUT.  The device
-    stays usable: the same workload with the default limit then runs."""
+    spin (dqmc_run_opts.spin_limit SM cycles).  The test_stall hook makes the first
+    wait of each product wait on a barrier that nothing arrives on: it gives up
+    after the limit, the kernel stops issuing, drains the copies in flight, frees
+    its tensor memory and returns, and the call reports DQMC_ETIMEOUT with the
+    diagnostics of the wait.  The device stays usable: the same workload without
+    the hook then runs.  The 8x8 lattice is below the default tensor-core
+    threshold, so tc_min_sites=1 puts its products on the tensor cores."""
     m = square(8, U=4.0, L=20)
     with pytest.raises(dq.DqmcError) as e:
-        dq.Ensemble([m], [0, 0], precision="mixed_tc", seed=3, spin_limit=1)
+        dq.Ensemble([m], [0, 0], precision="mixed_tc", seed=3, spin_limit=20000, tc_min_sites=1, test_stall=1)
     assert e.value.status == dq.DQMC_ETIMEOUT
-    ens = dq.Ensemble([m], [0, 0], precision="mixed_tc", seed=3)
+    assert "gave up" in str(e.value)
+    ens = dq.Ensemble([m], [0, 0], precision="mixed_tc", seed=3, tc_min_sites=1)
     st = ens.sweep(1)
     assert 0 < st["accepted"] < st["proposals"]
     ens.close()

@@ -1,0 +1,137 @@
+"""The SU(2) charge decoupling on the GPU (dqmc_su2_*: complex FP64, one CTA per
+chain) against the oracle (Sec. 6.1 model; Sec. 2.1 transform with imaginary
+coupling; Sec. 2.2 phase; Sec. 2.3 stabilisation).
+
+* Fields drawn by the library equal the oracle's Philox draws bit for bit.
+* Fixed fields: G(0), log|det(1 + B)| and arg det(1 + B) of the complex UDV
+  chain against orc_su2_green_udv (FP64: 1e-10) at beta = 2 and at the paper's
+  example beta = 10 (4 x 4, U = 4, n_wrap = 10), at and away from half filling;
+  the phase P = exp(i (-g sum eta + 2 arg det)).
+* Markov chain: the field trajectory, acceptance count and phase after each
+  sweep equal orc_su2_sweep (plain recompute of G~ for every proposal) on the
+  same Philox streams, and the reweighted energy at tau = 0 agrees.
+* Precision Green / Precision Phase at beta = 10 stay at the level of the
+  paper's example; at half filling every weight is positive (sign 1, P = 1).
+"""
+import numpy as np
+import pytest
+
+from paper_1704_00131_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_00131_gb300 import build_ext, dqmc
+    build_ext.build()
+    return dqmc
+
+
+def _wrap(a):
+    return (a + np.pi) % (2 * np.pi) - np.pi
+
+
+def _phase(orc, f, dtau, U, ar):
+    g = np.sqrt(0.5 * dtau * U)
+    ph = -g * sum(orc.field_coupling(2, 1.0, 2.0, int(l)) for l in np.asarray(f).ravel())
+    return np.exp(1j * (ph + 2.0 * ar))
+
+
+def test_su2_fields_drawn_like_the_oracle(dq, orc):
+    m = dq.Su2Model(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=20, n_wrap=5)
+    ens = dq.Su2Ensemble([m], [0, 0, 0], seed=777)
+    fields, ctr = ens.get_fields()
+    assert ctr == 0
+    for c in range(3):
+        ref = np.asarray(orc.init_fields(2, m.L, m.N, 777, c)).reshape(m.L, m.N)
+        assert np.array_equal(fields[c], ref), c
+    ens.close()
+
+
+@pytest.mark.parametrize("mu,L,nw", [(0.0, 20, 5), (0.3, 20, 5), (0.0, 100, 10), (-0.5, 100, 10)])
+def test_su2_fresh_green_matches_oracle(dq, orc, mu, L, nw):
+    K = W.square_lattice(4, 4, t=1.0, mu=mu)
+    dtau, U = 0.1, 4.0
+    rng = np.random.default_rng(int(L + 100 * mu))
+    fields = [rng.choice([-2, -1, 1, 2], size=(L, 16)).astype(np.int8) for _ in range(3)]
+    m = dq.Su2Model(K, U=U, dtau=dtau, L=L, n_wrap=nw)
+    ens = dq.Su2Ensemble([m], [0, 0, 0], fields=fields, seed=5)
+    for c in range(3):
+        Go, lo, ao = orc.su2_green_udv(K, dtau, U, nw, fields[c], 0)
+        for fresh in (False, True):
+            G, la, ar, P = ens.greens(c, fresh=fresh)
+            assert np.abs(G - Go).max() < 1e-10, (c, fresh)
+            assert la == pytest.approx(lo, rel=1e-10, abs=1e-10)
+            assert abs(_wrap(ar - ao)) < 1e-10
+            assert abs(P - _phase(orc, fields[c], dtau, U, ao)) < 1e-9
+        if L == 20:   # small beta: also the plain product
+            Gp, lp, ap, _, _, _ = orc.su2_plain(K, dtau, U, fields[c])
+            assert np.abs(G - Gp).max() < 1e-10 and abs(_wrap(ar - ap)) < 1e-10
+    ens.close()
+
+
+@pytest.mark.parametrize("lattice,mu", [("plaquette", 0.0), ("plaquette", 0.4), ("square4", 0.0), ("square4", -0.3)])
+def test_su2_trajectory_matches_oracle(dq, orc, lattice, mu):
+    """Three sweeps of four chains: fields, acceptances, phase and the reweighted
+    energy at tau = 0 against the oracle's chain (plain recompute per proposal)."""
+    if lattice == "plaquette":
+        K, dtau, U, L, nw, n_sweeps = W.square_lattice(2, 2, t=1.0, mu=mu), 0.125, 4.0, 8, 4, 3
+    else:
+        K, dtau, U, L, nw, n_sweeps = W.square_lattice(4, 4, t=1.0, mu=mu), 0.1, 4.0, 20, 5, 2
+    N, seed, n_ch = K.shape[0], 2024, 4
+    f0 = [np.asarray(orc.init_fields(2, L, N, 99, c), dtype=np.int8).reshape(L, N) for c in range(n_ch)]
+    m = dq.Su2Model(K, U=U, dtau=dtau, L=L, n_wrap=nw)
+    ens = dq.Su2Ensemble([m], [0] * n_ch, fields=f0, seed=seed, measure=True, meas_first=0, meas_last=0)
+    chains = [orc.Su2Chain(K, dtau, U, f0[c], seed=seed, chain=c) for c in range(n_ch)]
+    for sweep in range(n_sweeps):
+        st = ens.sweep(1)
+        obs, sg, nm = ens.measure(reset=True)
+        fields, _ = ens.get_fields()
+        acc = 0
+        for c in range(n_ch):
+            o, s_o, a = chains[c].sweep()
+            acc += a
+            assert np.array_equal(fields[c], chains[c].fields.reshape(L, N)), (sweep, c)
+            _, _, _, P = ens.greens(c)
+            Po = complex(chains[c].phase[0], chains[c].phase[1])
+            assert abs(P - Po) < 1e-9, (sweep, c)
+            assert nm[c] == 1 and sg[c] == s_o
+            assert abs(obs[c, 3] - o) < 1e-8 * max(1.0, abs(o)), (sweep, c)
+        assert st["accepted"] == acc and st["proposals"] == n_ch * 2 * L * N
+        assert 0 < acc < st["proposals"]
+    ens.close()
+
+
+def test_su2_paper_example_precision(dq):
+    """4 x 4, U = 4, beta = 10 (the paper's SU(2) example), n_wrap = 10, half
+    filling: Precision Green / Phase at the level the paper reports for its
+    example, sign 1 and a real phase throughout."""
+    m = dq.Su2Model(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=100, n_wrap=10)
+    ens = dq.Su2Ensemble([m], [0] * 8, seed=11)
+    ens.sweep(2)
+    st = ens.sweep(3)
+    assert st["prec_green_max"] < 1e-8 and st["prec_green_mean"] < 1e-10
+    assert st["prec_phase_max"] < 1e-8
+    assert st["mean_sign"] == 1.0
+    assert 0.1 < st["accepted"] / st["proposals"] < 0.9
+    for c in range(8):
+        _, _, _, P = ens.greens(c)
+        assert abs(P.imag) < 1e-8 and P.real > 0
+    ens.close()
+
+
+def test_su2_rejects_bad_input(dq):
+    m = dq.Su2Model(W.square_lattice(2, 2), U=4.0, dtau=0.1, L=10, n_wrap=3)
+    with pytest.raises(dq.DqmcError) as e:
+        dq.Su2Ensemble([m], [0])
+    assert e.value.status == dq.DQMC_EINVAL
+    m = dq.Su2Model(W.square_lattice(2, 2), U=4.0, dtau=0.1, L=10, n_wrap=5)
+    bad = np.ones((10, 4), dtype=np.int8)
+    bad[3, 2] = 0
+    with pytest.raises(dq.DqmcError) as e:
+        dq.Su2Ensemble([m], [0], fields=[bad])
+    assert e.value.status == dq.DQMC_EINVAL
