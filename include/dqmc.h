@@ -132,6 +132,11 @@ typedef struct {
                                  wait on a barrier that nothing arrives on, so it
                                  gives up after spin_limit cycles; the call then
                                  reports DQMC_ETIMEOUT with the context usable    */
+  int32_t stab_svd;           /* decomposition of the stabilisation chain: 0 the
+                                 pivoted QR (default), 1 one-sided Jacobi SVD,
+                                 Q = U, D = S, T = V^T T (the SVD alternative of
+                                 Sec. 2.3 / the -DSTAB1 build option of Sec. 5);
+                                 DQMC_PREC_FP64 only, DQMC_EINVAL otherwise     */
 } dqmc_run_opts;
 
 /* Statistics of one dqmc_sweep call, over all chains (Sec. 4.5 "info" file:

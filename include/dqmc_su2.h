@@ -16,6 +16,19 @@
  * P = e^{-S}/|e^{-S}| = exp(i (-g sum eta + 2 arg det(1 + B(beta,0)))) carried
  * through the updates; observables are reweighted by sign * P / Re P.
  *
+ * Bond model (optional, n_bonds > 0): the Hubbard-Ising model of Sec. 6, the
+ * hopping on bond b = (i, j) coupled to an Ising spin s_b = +-1 with a
+ * transverse field h and a coupling J between paired bonds.  Per slice the
+ * two-site type-1 factors X_b = exp(-dtau xi s_b (|i><j| + |j><i|)) enter
+ * B_tau = exp(-dtau K) X_0 X_1 ... X_{nb-1} exp(V_tau), and the weight gains
+ * the spins' own factor prod_{tau,b} [cosh(dtau h) if s_b(tau) = s_b(tau+1)
+ * else sinh(dtau h)] * exp(dtau J sum_{tau, pairs} s_b s_b') (periodic in tau).
+ * Within a slice the vertices are visited in the order their factors act:
+ * up the sites 0..N-1, then the bonds nb-1..0; down the reverse.  A bond
+ * proposal is the flip s -> -s with the ratio det(1 + delta (1 - G~)_PP)^2
+ * times the spins' weight ratio, and a rank-2 (Woodbury) update of G~; its
+ * acceptance uniform comes from the Philox counter of vertex N + b.
+ *
  * Arithmetic: complex FP64 throughout (G, wraps, rank-1 updates, the complex
  * pivoted-QR UDV chain and the stable G of Sec. 2.3).  One CTA per chain.
  *
@@ -49,6 +62,13 @@ typedef struct {
   double dtau;            /* > 0                                                  */
   int32_t L;              /* Trotter slices >= 1                                  */
   int32_t n_wrap;         /* stabilisation interval; L % n_wrap == 0 (Sec. 2.3)   */
+  int32_t n_bonds;        /* Ising spins on bonds; 0: the plain SU(2) model       */
+  const int32_t* bond_sites; /* [n_bonds][2] sites (i, j), i != j, in [0, N)       */
+  double xi;              /* coupling of s_b to the hopping of its bond           */
+  double h;               /* transverse field of the bond spins, > 0 with bonds   */
+  double J;               /* coupling of paired bond spins                        */
+  int32_t n_pairs;        /* J pairs                                              */
+  const int32_t* pairs;   /* [n_pairs][2] bonds (b, b'), b != b', in [0, n_bonds) */
 } dqmc_su2_model_desc;
 
 typedef struct {
@@ -70,10 +90,12 @@ typedef struct {
 } dqmc_su2_sweep_stats;
 
 /* Create a context with n_chains chains; chain c uses models[chain_model[c]].
- * fields_or_null: packed per chain [L_c][N_c] (int8 in {-2,-1,1,2}, host); NULL
- * draws them i.i.d. uniform from Philox (counter (0xFFFFFFFF, tau, x,
- * 0xFFFFFFFF)).  The left chain, G(0), log|det|, arg det and the phase P are
- * computed before return.  Inputs are copied.
+ * fields_or_null: packed per chain [L_c][N_c + n_bonds_c] (int8, host): per
+ * slice the site fields in {-2,-1,1,2}, then the bond spins in {-1,1}; NULL
+ * draws them i.i.d. uniform from Philox (counter (0xFFFFFFFF, tau, vertex,
+ * 0xFFFFFFFF), vertex x for site x and N + b for bond b).  The left chain,
+ * G(0), log|det|, arg det and the phase P are computed before return.  Inputs
+ * are copied.
  * Errors: DQMC_EINVAL (bad model, options or field values), DQMC_ENOMEM,
  * DQMC_ECUDA, DQMC_EUNSTABLE (a singular matrix in the stabilisation).  On an
  * error *out may still receive a context that only carries the message. */
@@ -96,12 +118,14 @@ dqmc_status dqmc_su2_greens(dqmc_su2_ctx* ctx, int32_t chain, int32_t fresh, dou
                             double* logabs_out, double* arg_out, double* phase_out);
 
 /* Reweighted sums since the context was created or last measured-and-reset
- * (reset = 1): out [n_chains][4][2] = (re, im) of sum sign * P / Re P * O for
- * O = Kin, Pot, Part, Ener (Sec. 6.1 estimator, both colors); sign_sum
- * [n_chains] = sum of sign(Re P); n_meas [n_chains].  Host buffers. */
+ * (reset = 1): out [n_chains][5][2] = (re, im) of sum sign * P / Re P * O for
+ * O = Kin, Pot, Part, Ener (Sec. 6.1 estimator, both colors; Kin of the hopping
+ * K alone) and the bond spins' (sum_b s_b)^2 / n_bonds averaged over the slices
+ * (0 without bonds); sign_sum [n_chains] = sum of sign(Re P); n_meas
+ * [n_chains].  Host buffers. */
 dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas, int32_t reset);
 
-/* Fields of every chain (packed [L_c][N_c] int8) and the sweep counter. */
+/* Fields of every chain (packed [L_c][N_c + n_bonds_c] int8) and the sweep counter. */
 dqmc_status dqmc_su2_get_fields(dqmc_su2_ctx* ctx, int8_t* out, uint64_t* sweep_counter);
 /* Replace the fields and the sweep counter; the left chains, G(0) and the
  * phases are recomputed. */

@@ -358,6 +358,10 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
     *out = ctx.release();
     return fail(*out, DQMC_EINVAL, "spin_limit and tc_min_sites must be >= 0");
   }
+  if (opts->stab_svd != 0 && (opts->stab_svd != 1 || opts->precision != DQMC_PREC_FP64)) {
+    *out = ctx.release();
+    return fail(*out, DQMC_EINVAL, "stab_svd must be 0, or 1 with DQMC_PREC_FP64");
+  }
   if (opts->dd_tile != 0 && opts->dd_tile != 3 && opts->dd_tile != 4) {
     *out = ctx.release();
     return fail(*out, DQMC_EINVAL, "dd_tile must be 0, 3 or 4");
@@ -421,6 +425,7 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
     C.wait_cycles = opts->spin_limit;
     C.dd_tile = opts->dd_tile;
     C.test_stall = opts->test_stall;
+    C.stab_svd = opts->stab_svd;
     if (fields_or_null) {
       const size_t nf = (size_t)M.d.L * M.d.n_vertices;
       for (size_t q = 0; q < nf; ++q) {

@@ -805,6 +805,86 @@ __device__ void form_q(int N, int ld, const double* M, const double* beta, const
 // D = |diag R|, T = D^-1 R P^T T_src.  Right chain (left == false): Bcal =
 // B_t2 ... B_t1+1.  Left chain: Bcal = B_t1+1^T ... B_t2^T.  Result in
 // (W2, wvec 0, W5); returns det(Q).
+// One-sided Jacobi SVD (Hestenes) of M = U S V^T, N x N in place: column
+// pairs of M are rotated until mutually orthogonal (|m_p . m_q| <= 1e-15
+// |m_p| |m_q| for every pair, at most 60 sweeps); then S_j = |m_j|, the
+// columns of M are normalised to U (e_j for a zero column) and V holds the
+// product of the rotations.  One-sided Jacobi keeps the relative accuracy of
+// the small singular values of a column-scaled matrix, which is what the scale
+// separation of the stable G needs.  The pairs of a sweep follow the
+// round-robin (circle) schedule, N/2 disjoint pairs per round, one warp per
+// pair; every warp sums its dot products in the same butterfly order, so the
+// result does not depend on timing.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ void svd_jacobi(int N, int ld, double* M, double* V, double* Sv) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    V[(size_t)x * ld + y] = (x == y) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int n = N + (N & 1);  // players of the schedule (a dummy when N is odd)
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < n - 1; ++r) {
+      for (int k = warp; k < n / 2; k += kThreads / 32) {
+        int p = (k == 0) ? n - 1 : (r + k) % (n - 1);
+        int q = (k == 0) ? r : (r - k + n - 1) % (n - 1);
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= N) continue;
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int i = lane; i < N; i += 32) {
+          const double xp = M[(size_t)i * ld + p], xq = M[(size_t)i * ld + q];
+          a = fma(xp, xp, a);
+          b = fma(xq, xq, b);
+          c = fma(xp, xq, c);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        if (c == 0.0 || fabs(c) <= 1e-15 * sqrt(a * b)) continue;
+        rotated = 1;
+        const double zeta = (b - a) / (2.0 * c);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int i = lane; i < N; i += 32) {
+          double* mp = M + (size_t)i * ld + p;
+          double* mq = M + (size_t)i * ld + q;
+          const double xp = *mp, xq = *mq;
+          *mp = cs * xp - sn * xq;
+          *mq = sn * xp + cs * xq;
+          double* vp = V + (size_t)i * ld + p;
+          double* vq = V + (size_t)i * ld + q;
+          const double yp = *vp, yq = *vq;
+          *vp = cs * yp - sn * yq;
+          *vq = sn * yp + cs * yq;
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) break;
+  }
+  for (int j = tid; j < N; j += kThreads) {
+    double s2 = 0.0;
+    for (int i = 0; i < N; ++i) s2 = fma(M[(size_t)i * ld + j], M[(size_t)i * ld + j], s2);
+    Sv[j] = sqrt(s2);
+  }
+  __syncthreads();
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double sj = Sv[y];
+    M[(size_t)x * ld + y] = (sj > 0.0) ? M[(size_t)x * ld + y] / sj : (x == y ? 1.0 : 0.0);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ int lu_factor_blk(int N, int ld, T* A, int* piv, T* tmp, double& logdet, int& sign, Smem& S);
+
 __device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, UDV src, Smem& S,
                       long long* det = nullptr) {
   long long t0 = clock64();
@@ -848,6 +928,26 @@ __device__ int chain_step(const ChainDev& C, int s, int t1, int t2, bool left, U
   }
   __syncthreads();
   double* Dn = wvec(C, s, 0);
+  if (C.stab_svd) {
+    // M = U S V^T: Q = U, D = S, T = V^T T_src, det Q from an LU of U
+    double* V = Y;
+    svd_jacobi(N, ld, X, V, Dn);
+    double* Qn = wmat(C, s, 2);
+    double* Ucp = wmat(C, s, 3);
+    for (int e = threadIdx.x; e < N * N; e += kThreads) {
+      const int x = e / N, y = e - x * N;
+      Qn[(size_t)x * ld + y] = X[(size_t)x * ld + y];
+      Ucp[(size_t)x * ld + y] = X[(size_t)x * ld + y];
+    }
+    __syncthreads();
+    double ldu;
+    int detq = 1;
+    if (lu_factor_blk(N, ld, Ucp, C.iwork[s] + ld, wmat(C, s, 9), ldu, detq, S)) detq = 1;
+    tick(det, 5, t0);
+    cta_gemm<double, true, false>(N, N, N, V, ld, src.T, ld, wmat(C, s, 5), ld, S.gemm);
+    tick(det, 6, t0);
+    return detq;
+  }
   double* beta = wvec(C, s, 1);
   double* vk0 = wvec(C, s, 2);
   int* perm = C.iwork[s];

@@ -59,6 +59,7 @@ struct ChainDev {
   int fresh_sign[kMaxFlavors];
   int error;                      // bit 0: a numerical failure; bit 1: a bounded device wait gave up
   long long wait_cycles;          // SM cycles before a bounded device wait gives up
+  int stab_svd;                   // stabilisation by one-sided Jacobi SVD instead of the pivoted QR (FP64)
   int test_stall;                 // test hook: tensor-core products wait on a barrier nothing arrives on
   int dd_tile;                    // register tile of the float-pair SIMT products (0 by padding, 3, 4)
   int wait_where[kMaxFlavors][6]; // first wait that gave up per flavor: kind (1 copy, 2 MMAs

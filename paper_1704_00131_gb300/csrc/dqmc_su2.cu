@@ -17,6 +17,17 @@
 // Sherman-Morrison update, the T wrap E G~ E^-1; every n_wrap slices the
 // complex pivoted-QR UDV chain (Sec. 2.3) recomputes G, log|det|, the
 // argument of det(1 + B) and with it the phase ("Precision Phase").
+//
+// Bond model (the Hubbard-Ising example of Sec. 6): Ising spins s_b on bonds
+// couple to the hopping through two-site type-1 factors
+// X_b = exp(-dtau xi s_b O_b), O_b = |i><j| + |j><i|, so that
+// B_tau = E X_0 X_1 ... X_{nb-1} exp(V_tau).  The factors act in the order
+// exp(V), X_{nb-1}, ..., X_0, E; each vertex sees the Green function just after
+// its own factor acted.  A bond flip s -> -s changes its factor by
+// (1 + Delta) with Delta = X(-2a) - 1 on the bond's 2 x 2 block: the ratio per
+// color is det(1 + delta (1 - G~)_PP) and G~ takes a rank-2 (Woodbury) update;
+// the spins' own weight (transverse field h between slices, coupling J between
+// paired bonds; the S0 ratio of Sec. 6) multiplies the ratio.
 #include "dqmc_device.cuh"
 #include "dqmc_su2_internal.h"
 
@@ -94,17 +105,17 @@ struct Sm {
   int* ired;            // [32]
   double2* P;           // [1] the phase of the chain
   int* first;           // [1] first accepted position of a scan
-  int8_t* fsl;          // [N] fields of the current slice
+  int8_t* fsl;          // [MV] fields of the current slice (sites, then bonds)
   int8_t* fn;           // [N] proposed fields
 };
 
-__host__ __device__ inline size_t su2_smem_layout(int N) {
+__host__ __device__ inline size_t su2_smem_layout(int N, int MV) {
   return (size_t)kZgBytes + (size_t)8 * N * sizeof(double2) + 256 * sizeof(double2) + (size_t)N * sizeof(double) +
          32 * sizeof(double) + 32 * sizeof(int) + 16 /* alignment */ + sizeof(double2) + 16 +
-         2 * (size_t)((N + 15) / 16 * 16);
+         (size_t)((MV + 15) / 16 * 16) + (size_t)((N + 15) / 16 * 16);
 }
 
-__device__ inline Sm su2_carve(unsigned char* base, int N) {
+__device__ inline Sm su2_carve(unsigned char* base, int N, int MV) {
   Sm s;
   unsigned char* q = base;
   s.gemm = q; q += kZgBytes;
@@ -123,7 +134,7 @@ __device__ inline Sm su2_carve(unsigned char* base, int N) {
   q = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(q) + 15) & ~(uintptr_t)15);
   s.P = reinterpret_cast<double2*>(q); q += sizeof(double2);
   s.first = reinterpret_cast<int*>(q); q += 16;
-  s.fsl = reinterpret_cast<int8_t*>(q); q += (size_t)((N + 15) / 16 * 16);
+  s.fsl = reinterpret_cast<int8_t*>(q); q += (size_t)((MV + 15) / 16 * 16);
   s.fn = reinterpret_cast<int8_t*>(q);
   return s;
 }
@@ -231,6 +242,27 @@ __device__ void z_store_slot(const Su2Dev& C, int j, int detq) {
 // exp(s i g eta(l)) of slice tau for every site, into ph (s = +1 or -1)
 __device__ inline void slice_phases(const Su2Dev& C, const int8_t* f, double s, double2* ph) {
   for (int x = threadIdx.x; x < C.N; x += kThreads) ph[x] = zexpi(s * C.g * hs_eta(f[x]));
+  __syncthreads();
+}
+
+// A <- X_b(a) A: rows i, j of A mixed by [[cosh a, sinh a], [sinh a, cosh a]]
+__device__ void bond_rows(int N, int ld, double2* A, int i, int j, double a) {
+  const double ch = cosh(a), sh = sinh(a);
+  for (int y = threadIdx.x; y < N; y += kThreads) {
+    const double2 ri = A[(size_t)i * ld + y], rj = A[(size_t)j * ld + y];
+    A[(size_t)i * ld + y] = zadd(zscal(ch, ri), zscal(sh, rj));
+    A[(size_t)j * ld + y] = zadd(zscal(sh, ri), zscal(ch, rj));
+  }
+  __syncthreads();
+}
+// A <- A X_b(a): columns i, j of A mixed the same way (X_b is symmetric)
+__device__ void bond_cols(int N, int ld, double2* A, int i, int j, double a) {
+  const double ch = cosh(a), sh = sinh(a);
+  for (int x = threadIdx.x; x < N; x += kThreads) {
+    const double2 ci = A[(size_t)x * ld + i], cj = A[(size_t)x * ld + j];
+    A[(size_t)x * ld + i] = zadd(zscal(ch, ci), zscal(sh, cj));
+    A[(size_t)x * ld + j] = zadd(zscal(sh, ci), zscal(ch, cj));
+  }
   __syncthreads();
 }
 
@@ -381,7 +413,7 @@ __device__ int z_chain_step(const Su2Dev& C, int t1, int t2, bool left, ZUdv src
   zcopy(N, ld, src.Q, X);
   for (int q = 0; q < t2 - t1; ++q) {
     const int t = left ? t2 - q : t1 + 1 + q;
-    const int8_t* f = C.fields + (size_t)(t - 1) * N;
+    const int8_t* f = C.fields + (size_t)(t - 1) * C.MV;
     if (!left) {
       slice_phases(C, f, +1.0, S.ph);
       for (int e = threadIdx.x; e < N * N; e += kThreads) {
@@ -389,9 +421,11 @@ __device__ int z_chain_step(const Su2Dev& C, int t1, int t2, bool left, ZUdv src
         X[(size_t)x * ld + y] = zmul(S.ph[x], X[(size_t)x * ld + y]);
       }
       __syncthreads();
+      for (int b = C.nb - 1; b >= 0; --b) bond_rows(N, ld, X, C.bi[b], C.bj[b], C.a0 * f[N + b]);
       zgemm<0, 0, false>(N, N, N, C.E, ld, X, ld, Y, ld, S.gemm);
     } else {
       zgemm<0, 0, false>(N, N, N, C.E, ld, X, ld, Y, ld, S.gemm);
+      for (int b = 0; b < C.nb; ++b) bond_rows(N, ld, Y, C.bi[b], C.bj[b], C.a0 * f[N + b]);
       slice_phases(C, f, -1.0, S.ph);
       for (int e = threadIdx.x; e < N * N; e += kThreads) {
         const int x = e / N, y = e - x * N;
@@ -517,7 +551,10 @@ __device__ int z_green(const Su2Dev& C, ZUdv R, ZUdv Lf, double2* Gout, double& 
 // exp(-i g sum eta) of the weight
 __device__ double bosonic_phase(const Su2Dev& C, Sm& S) {
   double acc = 0.0;
-  for (int e = threadIdx.x; e < C.L * C.N; e += kThreads) acc += hs_eta(C.fields[e]);
+  for (int e = threadIdx.x; e < C.L * C.N; e += kThreads) {
+    const int t = e / C.N, x = e - t * C.N;
+    acc += hs_eta(C.fields[(size_t)t * C.MV + x]);
+  }
   return -C.g * block_sum(acc, S.red);
 }
 
@@ -631,6 +668,107 @@ __device__ void z_update_slice(Su2Dev& C, int tau, int dir, const Su2SweepParams
   }
 }
 
+// Bond wraps: up G~ <- X_b G~ X_b^-1 (the bond's factor acts), down the inverse.
+__device__ void z_bond_wrap(const Su2Dev& C, int b, int s, bool up) {
+  const double a = C.a0 * (double)s;
+  if (up) {
+    bond_rows(C.N, C.ld, C.G, C.bi[b], C.bj[b], a);
+    bond_cols(C.N, C.ld, C.G, C.bi[b], C.bj[b], -a);
+  } else {
+    bond_rows(C.N, C.ld, C.G, C.bi[b], C.bj[b], -a);
+    bond_cols(C.N, C.ld, C.G, C.bi[b], C.bj[b], a);
+  }
+}
+
+// Change of the bond spins' log weight when s_b of slice tau flips: the
+// transverse field between neighbouring slices (periodic in tau) contributes
+// log cosh(dtau h) for equal and log sinh(dtau h) for opposite spins, and each
+// J pair (b, b') of the slice dtau J s_b s_b'.
+__device__ double bond_dlogw(const Su2Dev& C, int tau, int b, const int8_t* fsl) {
+  const int s = fsl[C.N + b];
+  double dl = 0.0;
+  if (C.L > 1) {
+    const int tp = (tau - 2 + C.L) % C.L, tn = tau % C.L;   // 0-based neighbours of slice tau - 1
+    const int nbs[2] = {C.fields[(size_t)tp * C.MV + C.N + b], C.fields[(size_t)tn * C.MV + C.N + b]};
+    for (int q = 0; q < 2; ++q) {
+      const double before = (s == nbs[q]) ? C.lch : C.lsh;
+      const double after = (-s == nbs[q]) ? C.lch : C.lsh;
+      dl += after - before;
+    }
+  }
+  double js = 0.0;
+  for (int e = C.nbr_off[b]; e < C.nbr_off[b + 1]; ++e) js += (double)fsl[C.N + C.nbr[e]];
+  dl += -2.0 * C.dJ * (double)s * js;
+  return dl;
+}
+
+// One bond proposal (the flip s_b -> -s_b) at the G~ its factor sees.  With
+// delta = X(-2a) - 1 on the block P = (i, j), a = -dtau xi s_b, and
+// S = 1 + delta (1 - G~)_PP (2 x 2):
+//   R = det(S)^2 exp(dlogw)   (two colors, the spins' own weight),
+// accepted when u2 < min(1, |Re(P R)| / |Re P|) (u2 from the Philox counter of
+// vertex N + b); then G~ <- G~ - G~_:P S^-1 delta (1 - G~)_P: (Woodbury).
+__device__ void z_bond_update(Su2Dev& C, int tau, int dir, int b, const Su2SweepParams& P, Sm& S) {
+  const int N = C.N, ld = C.ld, tid = threadIdx.x;
+  double2* G = C.G;
+  const uint32_t key0 = (uint32_t)P.seed, key1 = (uint32_t)(P.seed >> 32) ^ C.chain_id;
+  uint32_t ctr[4] = {(uint32_t)P.sweep, (uint32_t)(2 * tau + dir), (uint32_t)(N + b), (uint32_t)(P.sweep >> 32)};
+  philox4x32_10(ctr, key0, key1);
+  const double u2 = uniform53(ctr[2], ctr[3]);
+  const int s = S.fsl[N + b];
+  const double a = C.a0 * (double)s;
+  const double d0 = cosh(2.0 * a) - 1.0, d1 = -sinh(2.0 * a);
+  const int i = C.bi[b], j = C.bj[b];
+  const double2 gii = G[(size_t)i * ld + i], gij = G[(size_t)i * ld + j];
+  const double2 gji = G[(size_t)j * ld + i], gjj = G[(size_t)j * ld + j];
+  const double2 h00 = make_double2(1.0 - gii.x, -gii.y), h01 = make_double2(-gij.x, -gij.y);
+  const double2 h10 = make_double2(-gji.x, -gji.y), h11 = make_double2(1.0 - gjj.x, -gjj.y);
+  const double2 S00 = zadd(make_double2(1.0, 0.0), zadd(zscal(d0, h00), zscal(d1, h10)));
+  const double2 S01 = zadd(zscal(d0, h01), zscal(d1, h11));
+  const double2 S10 = zadd(zscal(d1, h00), zscal(d0, h10));
+  const double2 S11 = zadd(make_double2(1.0, 0.0), zadd(zscal(d1, h01), zscal(d0, h11)));
+  const double2 det = zsub(zmul(S00, S11), zmul(S01, S10));
+  const double2 R = zscal(exp(bond_dlogw(C, tau, b, S.fsl)), zmul(det, det));
+  const double2 Pc = *S.P;
+  const double ratio = fabs(zmul(Pc, R).x) / fabs(Pc.x);
+  const bool accept = zabs(det) > 0.0 && u2 < (ratio < 1.0 ? ratio : 1.0);
+  __syncthreads();
+  if (tid == 0) C.proposals += 1;
+  if (!accept) return;
+  // W = S^-1 delta (2 x 2)
+  const double2 idet = zdiv(make_double2(1.0, 0.0), det);
+  const double2 I00 = zmul(S11, idet), I01 = zscal(-1.0, zmul(S01, idet));
+  const double2 I10 = zscal(-1.0, zmul(S10, idet)), I11 = zmul(S00, idet);
+  const double2 W00 = zadd(zscal(d0, I00), zscal(d1, I01)), W01 = zadd(zscal(d1, I00), zscal(d0, I01));
+  const double2 W10 = zadd(zscal(d0, I10), zscal(d1, I11)), W11 = zadd(zscal(d1, I10), zscal(d0, I11));
+  double2* c0 = S.col;    // G~[:, i]
+  double2* c1 = S.hv;     // G~[:, j]
+  double2* r0 = S.row;    // e_i - G~[i, :]
+  double2* r1 = S.delta;  // e_j - G~[j, :]
+  for (int x = tid; x < N; x += kThreads) {
+    c0[x] = G[(size_t)x * ld + i];
+    c1[x] = G[(size_t)x * ld + j];
+    const double2 gi = G[(size_t)i * ld + x], gj = G[(size_t)j * ld + x];
+    r0[x] = make_double2((x == i ? 1.0 : 0.0) - gi.x, -gi.y);
+    r1[x] = make_double2((x == j ? 1.0 : 0.0) - gj.x, -gj.y);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double2 PR = zmul(Pc, R);
+    *S.P = zscal(1.0 / zabs(PR), PR);
+    S.fsl[N + b] = (int8_t)(-s);
+    C.accepted += 1;
+  }
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double2 t0 = zadd(zmul(W00, r0[y]), zmul(W01, r1[y]));
+    const double2 t1 = zadd(zmul(W10, r0[y]), zmul(W11, r1[y]));
+    double2* gp = G + (size_t)x * ld + y;
+    *gp = zsub(*gp, zadd(zmul(c0[x], t0), zmul(c1[x], t1)));
+  }
+  __syncthreads();
+}
+
 // Stabilisation event j (Sec. 2.3): the chain extended by n_wrap slices, the
 // stable G replaces the wrapped one (max and mean |dG| booked: "Precision
 // Green"), and the fresh phase replaces the carried one (|dP| booked:
@@ -707,12 +845,22 @@ __device__ void z_measure(Su2Dev& C, Sm& S) {
   kin = block_zsum(kin, S.red);
   pot = block_zsum(pot, S.red);
   part = block_zsum(part, S.red);
+  // bond spins: (sum_b s_b)^2 / nb averaged over the slices
+  double m2 = 0.0;
+  if (C.nb > 0) {
+    for (int t = threadIdx.x; t < C.L; t += kThreads) {
+      double mt = 0.0;
+      for (int b = 0; b < C.nb; ++b) mt += (double)C.fields[(size_t)t * C.MV + N + b];
+      m2 += mt * mt / (double)C.nb;
+    }
+    m2 = block_sum(m2, S.red) / (double)C.L;
+  }
   if (threadIdx.x == 0) {
     const double2 Pc = *S.P;
     const double sg = Pc.x >= 0.0 ? 1.0 : -1.0;
     const double2 w = zscal(sg / Pc.x, Pc);
-    const double2 v[4] = {zmul(w, kin), zmul(w, pot), zmul(w, part), zmul(w, zadd(kin, pot))};
-    for (int q = 0; q < 4; ++q) {
+    const double2 v[5] = {zmul(w, kin), zmul(w, pot), zmul(w, part), zmul(w, zadd(kin, pot)), zscal(m2, w)};
+    for (int q = 0; q < 5; ++q) {
       C.meas[2 * q] += v[q].x;
       C.meas[2 * q + 1] += v[q].y;
     }
@@ -723,11 +871,11 @@ __device__ void z_measure(Su2Dev& C, Sm& S) {
 }
 
 __device__ inline void load_slice(const Su2Dev& C, int tau, Sm& S) {
-  for (int x = threadIdx.x; x < C.N; x += kThreads) S.fsl[x] = C.fields[(size_t)(tau - 1) * C.N + x];
+  for (int x = threadIdx.x; x < C.MV; x += kThreads) S.fsl[x] = C.fields[(size_t)(tau - 1) * C.MV + x];
   __syncthreads();
 }
 __device__ inline void store_slice(const Su2Dev& C, int tau, Sm& S) {
-  for (int x = threadIdx.x; x < C.N; x += kThreads) C.fields[(size_t)(tau - 1) * C.N + x] = S.fsl[x];
+  for (int x = threadIdx.x; x < C.MV; x += kThreads) C.fields[(size_t)(tau - 1) * C.MV + x] = S.fsl[x];
   __syncthreads();
 }
 
@@ -735,7 +883,7 @@ __global__ void __launch_bounds__(kThreads) su2_sweep_kernel(Su2Dev* chains, Su2
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Su2Dev& C = chains[blockIdx.x];
   if (blockIdx.x >= P.n_chains) return;
-  Sm S = su2_carve(smem_raw, C.N);
+  Sm S = su2_carve(smem_raw, C.N, C.MV);
   const int L = C.L, nw = C.nw;
   if (threadIdx.x == 0) *S.P = C.P;
   __syncthreads();
@@ -744,6 +892,10 @@ __global__ void __launch_bounds__(kThreads) su2_sweep_kernel(Su2Dev* chains, Su2
     slice_phases(C, S.fsl, +1.0, S.ph);
     z_v_wrap(C, C.G, S.ph);
     z_update_slice(C, tau, 0, P, S);
+    for (int b = C.nb - 1; b >= 0; --b) {
+      z_bond_wrap(C, b, S.fsl[C.N + b], true);
+      z_bond_update(C, tau, 0, b, P, S);
+    }
     store_slice(C, tau, S);
     z_t_wrap(C, true, S);
     if (tau % nw == 0) z_stabilise(C, tau / nw, true, S);
@@ -752,6 +904,10 @@ __global__ void __launch_bounds__(kThreads) su2_sweep_kernel(Su2Dev* chains, Su2
   for (int tau = L; tau >= 1; --tau) {
     load_slice(C, tau, S);
     z_t_wrap(C, false, S);
+    for (int b = 0; b < C.nb; ++b) {
+      z_bond_update(C, tau, 1, b, P, S);
+      z_bond_wrap(C, b, S.fsl[C.N + b], false);
+    }
     z_update_slice(C, tau, 1, P, S);
     store_slice(C, tau, S);
     slice_phases(C, S.fsl, -1.0, S.ph);
@@ -774,7 +930,7 @@ __global__ void __launch_bounds__(kThreads) su2_fresh_kernel(Su2Dev* chains, int
   const int c = blockIdx.x;
   if (c >= n_chains || (mode == 1 && c != only)) return;
   Su2Dev& C = chains[c];
-  Sm S = su2_carve(smem_raw, C.N);
+  Sm S = su2_carve(smem_raw, C.N, C.MV);
   double la = 0.0, ar = 0.0;
   if (z_fill_left(C, S, la, ar)) {
     if (threadIdx.x == 0) C.error |= 1;
@@ -806,21 +962,26 @@ __global__ void su2_copy_green_kernel(Su2Dev* chains, int chain, double2* out) {
   }
 }
 
-// Four-valued fields i.i.d. uniform over (-2, -1, 1, 2) from Philox (counter
-// (0xFFFFFFFF, tau, x, 0xFFFFFFFF), key (seed_lo, seed_hi ^ chain)).
+// Four-valued fields i.i.d. uniform over (-2, -1, 1, 2) and bond spins i.i.d.
+// +-1 from Philox (counter (0xFFFFFFFF, tau, vertex, 0xFFFFFFFF), key
+// (seed_lo, seed_hi ^ chain); vertex x for site x, N + b for bond b).
 __global__ void su2_init_fields_kernel(Su2Dev* chains, int n_chains, uint64_t seed) {
   const int c = blockIdx.x;
   if (c >= n_chains) return;
   const Su2Dev& C = chains[c];
-  for (int e = threadIdx.x; e < C.L * C.N; e += blockDim.x) {
-    const int t = e / C.N, k = e - t * C.N;
+  for (int e = threadIdx.x; e < C.L * C.MV; e += blockDim.x) {
+    const int t = e / C.MV, k = e - t * C.MV;
     uint32_t ctr[4] = {0xFFFFFFFFu, (uint32_t)(t + 1), (uint32_t)k, 0xFFFFFFFFu};
     philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32) ^ C.chain_id);
     const double u = uniform53(ctr[0], ctr[1]);
-    int idx = (int)floor(4.0 * u);
-    idx = idx > 3 ? 3 : idx;
-    const int8_t vals[4] = {-2, -1, 1, 2};
-    C.fields[e] = vals[idx];
+    if (k >= C.N) {
+      C.fields[e] = u < 0.5 ? -1 : 1;
+    } else {
+      int idx = (int)floor(4.0 * u);
+      idx = idx > 3 ? 3 : idx;
+      const int8_t vals[4] = {-2, -1, 1, 2};
+      C.fields[e] = vals[idx];
+    }
   }
 }
 
@@ -833,7 +994,7 @@ __global__ void su2_reset_stats_kernel(Su2Dev* chains, int n_chains, int clear_m
   C.sweep_sign_sum = 0.0;
   C.error = 0;
   if (clear_meas) {
-    for (int q = 0; q < 8; ++q) C.meas[q] = 0.0;
+    for (int q = 0; q < 10; ++q) C.meas[q] = 0.0;
     C.meas_sign = 0.0;
     C.n_meas = 0;
   }
@@ -841,7 +1002,7 @@ __global__ void su2_reset_stats_kernel(Su2Dev* chains, int n_chains, int clear_m
 
 }  // namespace
 
-size_t su2_smem_bytes(int maxN) { return su2_smem_layout(maxN); }
+size_t su2_smem_bytes(int maxN, int maxMV) { return su2_smem_layout(maxN, maxMV); }
 
 static cudaError_t su2_set_smem(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

@@ -26,7 +26,7 @@ struct dqmc_su2_ctx {
   std::vector<void*> allocs;
   size_t smem = 0;
   uint64_t sweep_counter = 0;
-  int maxN = 0;
+  int maxN = 0, maxMV = 0;
   double2* out_scratch = nullptr;  // [maxN][maxN] complex for dqmc_su2_greens
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -68,6 +68,25 @@ dqmc_status validate(dqmc_su2_ctx* ctx, const dqmc_su2_model_desc& m, int idx) {
       if (!std::isfinite(a)) return fail(ctx, DQMC_EINVAL, "model %d: non-finite hopping", idx);
       if (std::fabs(a - b) > 1e-12 * (1.0 + std::fabs(a))) return fail(ctx, DQMC_EINVAL, "model %d: hopping not symmetric", idx);
     }
+  if (m.n_bonds < 0 || m.n_pairs < 0) return fail(ctx, DQMC_EINVAL, "model %d: negative bond or pair count", idx);
+  if (m.n_bonds > 0) {
+    if (!m.bond_sites) return fail(ctx, DQMC_EINVAL, "model %d: null bond_sites", idx);
+    if (!(m.h > 0.0) || !std::isfinite(m.h) || !std::isfinite(m.xi) || !std::isfinite(m.J))
+      return fail(ctx, DQMC_EINVAL, "model %d: need a finite xi, J and h > 0 with bonds", idx);
+    for (int b = 0; b < m.n_bonds; ++b) {
+      const int i = m.bond_sites[2 * b], j = m.bond_sites[2 * b + 1];
+      if (i < 0 || i >= N || j < 0 || j >= N || i == j)
+        return fail(ctx, DQMC_EINVAL, "model %d: bond %d = (%d, %d) invalid", idx, b, i, j);
+    }
+  } else if (m.n_pairs > 0) {
+    return fail(ctx, DQMC_EINVAL, "model %d: J pairs without bonds", idx);
+  }
+  if (m.n_pairs > 0 && !m.pairs) return fail(ctx, DQMC_EINVAL, "model %d: null pairs", idx);
+  for (int q = 0; q < m.n_pairs; ++q) {
+    const int a = m.pairs[2 * q], b = m.pairs[2 * q + 1];
+    if (a < 0 || a >= m.n_bonds || b < 0 || b >= m.n_bonds || a == b)
+      return fail(ctx, DQMC_EINVAL, "model %d: pair %d = (%d, %d) invalid", idx, q, a, b);
+  }
   return DQMC_OK;
 }
 
@@ -80,17 +99,15 @@ dqmc_status dev_alloc(dqmc_su2_ctx* ctx, T** p, size_t n) {
   return DQMC_OK;
 }
 
-dqmc_status check_fields(dqmc_su2_ctx* ctx, const int8_t* f, size_t n) {
-  for (size_t e = 0; e < n; ++e)
-    if (f[e] != 1 && f[e] != -1 && f[e] != 2 && f[e] != -2)
-      return fail(ctx, DQMC_EINVAL, "field value %d at %zu is not in {-2, -1, 1, 2}", (int)f[e], e);
+// fields of one chain, [L][N + nb]: sites in {-2, -1, 1, 2}, bond spins in {-1, 1}
+dqmc_status check_fields(dqmc_su2_ctx* ctx, const int8_t* f, int L, int N, int MV) {
+  for (int t = 0; t < L; ++t)
+    for (int v = 0; v < MV; ++v) {
+      const int x = f[(size_t)t * MV + v];
+      const bool ok = (v < N) ? (x == 1 || x == -1 || x == 2 || x == -2) : (x == 1 || x == -1);
+      if (!ok) return fail(ctx, DQMC_EINVAL, "field value %d at slice %d, vertex %d is invalid", x, t, v);
+    }
   return DQMC_OK;
-}
-
-size_t total_fields(const dqmc_su2_ctx* ctx) {
-  size_t n = 0;
-  for (const Su2Dev& C : ctx->chains_h) n += (size_t)C.L * C.N;
-  return n;
 }
 
 dqmc_status download(dqmc_su2_ctx* ctx) {
@@ -141,8 +158,9 @@ dqmc_status dqmc_su2_init(const dqmc_su2_model_desc* models, int32_t n_models, c
     return fail(ctx, DQMC_EINVAL, "meas_first > meas_last");
   SU2_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev0));
   SU2_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev1));
-  // per model: K, E = exp(-dtau K), E^-1, the identity and a vector of ones
-  struct Dm { double *K, *E, *Einv, *ones; double2* ident; int ld; };
+  // per model: K, E = exp(-dtau K), E^-1, the identity and a vector of ones, the
+  // bonds and the CSR lists of the J pairs
+  struct Dm { double *K, *E, *Einv, *ones; double2* ident; int ld; int *bi, *bj, *nbr_off, *nbr; };
   std::vector<Dm> dm(n_models);
   for (int i = 0; i < n_models; ++i) {
     const dqmc_su2_model_desc& m = models[i];
@@ -170,21 +188,50 @@ dqmc_status dqmc_su2_init(const dqmc_su2_model_desc* models, int32_t n_models, c
     SU2_CUDA_TRY(ctx, cudaMemcpy(d.Einv, Ei.data(), Ei.size() * sizeof(double), cudaMemcpyHostToDevice));
     SU2_CUDA_TRY(ctx, cudaMemcpy(d.ident, I.data(), I.size() * sizeof(double2), cudaMemcpyHostToDevice));
     SU2_CUDA_TRY(ctx, cudaMemcpy(d.ones, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice));
+    const int nb = m.n_bonds;
+    std::vector<int> bi(nb + 1, 0), bj(nb + 1, 0), off(nb + 2, 0), nbr;
+    for (int b = 0; b < nb; ++b) { bi[b] = m.bond_sites[2 * b]; bj[b] = m.bond_sites[2 * b + 1]; }
+    std::vector<std::vector<int>> adj(nb);
+    for (int q = 0; q < m.n_pairs; ++q) {
+      adj[m.pairs[2 * q]].push_back(m.pairs[2 * q + 1]);
+      adj[m.pairs[2 * q + 1]].push_back(m.pairs[2 * q]);
+    }
+    for (int b = 0; b < nb; ++b) {
+      off[b + 1] = off[b] + (int)adj[b].size();
+      nbr.insert(nbr.end(), adj[b].begin(), adj[b].end());
+    }
+    nbr.push_back(0);
+    if ((st = dev_alloc(ctx, &d.bi, bi.size())) || (st = dev_alloc(ctx, &d.bj, bj.size())) ||
+        (st = dev_alloc(ctx, &d.nbr_off, off.size())) || (st = dev_alloc(ctx, &d.nbr, nbr.size())))
+      return st;
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.bi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.bj, bj.data(), bj.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.nbr_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SU2_CUDA_TRY(ctx, cudaMemcpy(d.nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
     ctx->maxN = std::max(ctx->maxN, N);
+    ctx->maxMV = std::max(ctx->maxMV, N + nb);
   }
   // per chain: one arena
   size_t foff = 0;
   for (int c = 0; c < n_chains; ++c) {
     const dqmc_su2_model_desc& m = models[chain_model[c]];
     const Dm& d = dm[chain_model[c]];
-    const int N = m.n_sites, ld = d.ld, nst = m.L / m.n_wrap;
+    const int N = m.n_sites, ld = d.ld, nst = m.L / m.n_wrap, MV = N + m.n_bonds;
     Su2Dev C{};
     C.N = N; C.ld = ld; C.L = m.L; C.nw = m.n_wrap;
+    C.nb = m.n_bonds; C.MV = MV;
     C.dtau = m.dtau; C.U = m.U; C.g = std::sqrt(0.5 * m.dtau * m.U);
+    C.a0 = -m.dtau * m.xi;
+    if (m.n_bonds > 0) {
+      C.lch = std::log(std::cosh(m.dtau * m.h));
+      C.lsh = std::log(std::sinh(m.dtau * m.h));
+      C.dJ = m.dtau * m.J;
+    }
+    C.bi = d.bi; C.bj = d.bj; C.nbr_off = d.nbr_off; C.nbr = d.nbr;
     C.K = d.K; C.E = d.E; C.Einv = d.Einv; C.ident = d.ident; C.ones = d.ones;
     C.chain_id = (uint32_t)c;
     dqmc_status st;
-    if ((st = dev_alloc(ctx, &C.fields, (size_t)m.L * N)) || (st = dev_alloc(ctx, &C.G, (size_t)N * ld)) ||
+    if ((st = dev_alloc(ctx, &C.fields, (size_t)m.L * MV)) || (st = dev_alloc(ctx, &C.G, (size_t)N * ld)) ||
         (st = dev_alloc(ctx, &C.Gt, (size_t)N * ld)) ||
         (st = dev_alloc(ctx, &C.slots, (size_t)(nst + 1) * dqmc::su2_slot_elems(N, ld))) ||
         (st = dev_alloc(ctx, &C.slotD, (size_t)(nst + 1) * ld)) || (st = dev_alloc(ctx, &C.slot_detq, nst + 1)) ||
@@ -192,18 +239,18 @@ dqmc_status dqmc_su2_init(const dqmc_su2_model_desc* models, int32_t n_models, c
         (st = dev_alloc(ctx, &C.dwork, (size_t)dqmc::kSu2DVecs * ld)) || (st = dev_alloc(ctx, &C.iwork, ld)))
       return st;
     if (fields) {
-      dqmc_status fs = check_fields(ctx, fields + foff, (size_t)m.L * N);
+      dqmc_status fs = check_fields(ctx, fields + foff, m.L, N, MV);
       if (fs) return fs;
-      SU2_CUDA_TRY(ctx, cudaMemcpy(C.fields, fields + foff, (size_t)m.L * N, cudaMemcpyHostToDevice));
+      SU2_CUDA_TRY(ctx, cudaMemcpy(C.fields, fields + foff, (size_t)m.L * MV, cudaMemcpyHostToDevice));
     }
-    foff += (size_t)m.L * N;
+    foff += (size_t)m.L * MV;
     ctx->chains_h.push_back(C);
   }
   SU2_CUDA_TRY(ctx, cudaMalloc(&ctx->chains_d, sizeof(Su2Dev) * n_chains));
   SU2_CUDA_TRY(ctx, cudaMalloc(&ctx->out_scratch, sizeof(double2) * (size_t)ctx->maxN * ctx->maxN));
   SU2_CUDA_TRY(ctx, cudaMemcpy(ctx->chains_d, ctx->chains_h.data(), sizeof(Su2Dev) * n_chains,
                                cudaMemcpyHostToDevice));
-  ctx->smem = dqmc::su2_smem_bytes(ctx->maxN);
+  ctx->smem = dqmc::su2_smem_bytes(ctx->maxN, ctx->maxMV);
   if (!fields) SU2_CUDA_TRY(ctx, dqmc::su2_launch_init_fields(ctx->chains_d, n_chains, opts->seed, ctx->stream));
   SU2_CUDA_TRY(ctx, dqmc::su2_launch_reset_stats(ctx->chains_d, n_chains, 1, ctx->stream));
   return refill(ctx);
@@ -287,7 +334,7 @@ dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, i
   for (size_t c = 0; c < ctx->chains_h.size(); ++c) {
     const Su2Dev& C = ctx->chains_h[c];
     if (out)
-      for (int q = 0; q < 8; ++q) out[c * 8 + q] = C.meas[q];
+      for (int q = 0; q < 10; ++q) out[c * 10 + q] = C.meas[q];
     if (sign_sum) sign_sum[c] = C.meas_sign;
     if (n_meas) n_meas[c] = C.n_meas;
   }
@@ -300,8 +347,8 @@ dqmc_status dqmc_su2_get_fields(dqmc_su2_ctx* ctx, int8_t* out, uint64_t* sweep_
   if (out) {
     size_t off = 0;
     for (const Su2Dev& C : ctx->chains_h) {
-      SU2_CUDA_TRY(ctx, cudaMemcpyAsync(out + off, C.fields, (size_t)C.L * C.N, cudaMemcpyDeviceToHost, ctx->stream));
-      off += (size_t)C.L * C.N;
+      SU2_CUDA_TRY(ctx, cudaMemcpyAsync(out + off, C.fields, (size_t)C.L * C.MV, cudaMemcpyDeviceToHost, ctx->stream));
+      off += (size_t)C.L * C.MV;
     }
     SU2_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   }
@@ -312,12 +359,16 @@ dqmc_status dqmc_su2_get_fields(dqmc_su2_ctx* ctx, int8_t* out, uint64_t* sweep_
 dqmc_status dqmc_su2_set_fields(dqmc_su2_ctx* ctx, const int8_t* in, uint64_t sweep_counter) {
   if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
   if (!in) return fail(ctx, DQMC_EINVAL, "null fields");
-  dqmc_status st = check_fields(ctx, in, total_fields(ctx));
-  if (st) return st;
   size_t off = 0;
   for (const Su2Dev& C : ctx->chains_h) {
-    SU2_CUDA_TRY(ctx, cudaMemcpyAsync(C.fields, in + off, (size_t)C.L * C.N, cudaMemcpyHostToDevice, ctx->stream));
-    off += (size_t)C.L * C.N;
+    dqmc_status st = check_fields(ctx, in + off, C.L, C.N, C.MV);
+    if (st) return st;
+    off += (size_t)C.L * C.MV;
+  }
+  off = 0;
+  for (const Su2Dev& C : ctx->chains_h) {
+    SU2_CUDA_TRY(ctx, cudaMemcpyAsync(C.fields, in + off, (size_t)C.L * C.MV, cudaMemcpyHostToDevice, ctx->stream));
+    off += (size_t)C.L * C.MV;
   }
   ctx->sweep_counter = sweep_counter;
   return refill(ctx);

@@ -8,19 +8,31 @@
 namespace dqmc {
 
 // Device-resident description and state of one Markov chain of the SU(2)
-// decoupling (Sec. 6.1).  One CTA works on it.  Complex matrices are double2
-// (re, im), row-major with leading dimension `ld` (in complex elements).
+// decoupling (Sec. 6.1), optionally with Ising spins on bonds coupling to the
+// hopping (the Hubbard-Ising model of Sec. 6).  One CTA works on it.  Complex
+// matrices are double2 (re, im), row-major with leading dimension `ld` (in
+// complex elements).
 struct Su2Dev {
-  // model: B_tau = E exp(V_tau), V_tau = diag(i g eta(l_tau,x)), g = sqrt(dtau U / 2)
+  // model: B_tau = E X_0 X_1 ... X_{nb-1} exp(V_tau), V_tau = diag(i g eta(l_tau,x)),
+  // g = sqrt(dtau U / 2), X_b = exp(a0 s_b O_b) on the bond (bi[b], bj[b]),
+  // O_b = |i><j| + |j><i|, a0 = -dtau xi
   int N, ld, L, nw;
+  int nb, MV;             // bonds; vertices per slice MV = N + nb (fields [L][MV])
   double dtau, U, g;
+  double a0;              // -dtau xi
+  double lch, lsh, dJ;    // log cosh(dtau h), log sinh(dtau h), dtau J (bond spins' weight)
+  const int* bi;          // [nb]
+  const int* bj;          // [nb]
+  const int* nbr_off;     // [nb + 1] CSR of the J pairs: bonds paired with b are
+  const int* nbr;         //   nbr[nbr_off[b] .. nbr_off[b + 1])
   const double* K;        // hopping [N][ld] (real symmetric, -mu on the diagonal)
   const double* E;        // exp(-dtau K) [N][ld]
   const double* Einv;     // exp(+dtau K) [N][ld]
   const double2* ident;   // identity [N][ld] (Q and T of the empty chain)
   const double* ones;     // [ld] of 1 (its D)
   // state
-  int8_t* fields;         // [L][N], four-valued l in {-2, -1, 1, 2}
+  int8_t* fields;         // [L][MV]: per slice the four-valued l in {-2, -1, 1, 2} of the
+                          // N sites, then the Ising spins +-1 of the nb bonds
   double2* G;             // working G [N][ld]
   double2* Gt;            // scratch of the wraps [N][ld]
   double2* slots;         // (L/nw + 1) x {Q [N][ld], T [N][ld]}
@@ -36,8 +48,9 @@ struct Su2Dev {
   double prec_sum, prec_max, phase_max;
   int64_t prec_events, proposals, accepted;
   double sweep_sign_sum;
-  // reweighted measurement sums: (re, im) of kin, pot, part, ener; sum of signs; count
-  double meas[8];
+  // reweighted measurement sums: (re, im) of kin, pot, part, ener and of the bond
+  // spins' (sum_b s_b)^2 / nb averaged over the slices; sum of signs; count
+  double meas[10];
   double meas_sign;
   int64_t n_meas;
   int error;              // bit 0: a singular matrix in the stabilisation
@@ -60,7 +73,7 @@ struct Su2SweepParams {
 };
 
 // launchers (dqmc_su2.cu)
-size_t su2_smem_bytes(int maxN);
+size_t su2_smem_bytes(int maxN, int maxMV);
 cudaError_t su2_launch_init_fields(Su2Dev* chains, int n_chains, uint64_t seed, cudaStream_t st);
 // mode 0: recompute the left chain and G(0) of every chain, write the working
 // G, log|det|, arg and the phase P; mode 1: the same for chain `only` into

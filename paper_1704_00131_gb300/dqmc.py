@@ -63,6 +63,7 @@ class RunOpts(ctypes.Structure):
         ("tc_min_sites", ctypes.c_int32),
         ("dd_tile", ctypes.c_int32),
         ("test_stall", ctypes.c_int32),
+        ("stab_svd", ctypes.c_int32),
     ]
 
 
@@ -170,7 +171,7 @@ class Ensemble:
     def __init__(self, models: list[ModelSpec], chain_model, fields=None, precision: str = "fp64",
                  delay_k: int = 16, seed: int = 0, measure: bool = False, meas_first: int = 0,
                  meas_last: int | None = None, unstable_threshold: float = 0.0, stream=None, spin_limit: int = 0,
-                 tc_min_sites: int = 0, dd_tile: int = 0, test_stall: int = 0):
+                 tc_min_sites: int = 0, dd_tile: int = 0, test_stall: int = 0, stab_svd: bool = False):
         self._lib = load()
         self._h = ctypes.c_void_p()
         self.models = list(models)
@@ -191,7 +192,7 @@ class Ensemble:
         ml = max(m.L for m in self.models) if meas_last is None else meas_last
         self.opts = RunOpts(PREC[precision], int(delay_k), int(measure), int(meas_first), int(ml), int(seed),
                             float(unstable_threshold), int(spin_limit), int(tc_min_sites), int(dd_tile),
-                            int(test_stall))
+                            int(test_stall), int(bool(stab_svd)))
         fptr = None
         if fields is not None:
             packed = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int8).ravel() for f in fields]))
@@ -383,6 +384,13 @@ class Su2ModelDesc(ctypes.Structure):
         ("dtau", ctypes.c_double),
         ("L", ctypes.c_int32),
         ("n_wrap", ctypes.c_int32),
+        ("n_bonds", ctypes.c_int32),
+        ("bond_sites", ctypes.POINTER(ctypes.c_int32)),
+        ("xi", ctypes.c_double),
+        ("h", ctypes.c_double),
+        ("J", ctypes.c_double),
+        ("n_pairs", ctypes.c_int32),
+        ("pairs", ctypes.POINTER(ctypes.c_int32)),
     ]
 
 
@@ -414,16 +422,32 @@ class Su2SweepStats(ctypes.Structure):
 @dataclass
 class Su2Model:
     """One lattice of the SU(2) Hubbard model: hopping K [N, N] (-mu on the
-    diagonal), U, dtau, L slices, stabilisation interval n_wrap."""
+    diagonal), U, dtau, L slices, stabilisation interval n_wrap; optionally
+    Ising spins on `bonds` [(i, j), ...] coupled to their hopping by xi, with a
+    transverse field h and a coupling J between the bond `pairs` [(b, b'), ...]
+    (the Hubbard-Ising model)."""
     hopping: np.ndarray
     U: float
     dtau: float
     L: int
     n_wrap: int
+    bonds: tuple = ()
+    xi: float = 0.0
+    h: float = 0.0
+    J: float = 0.0
+    pairs: tuple = ()
 
     @property
     def N(self) -> int:
         return int(self.hopping.shape[0])
+
+    @property
+    def n_bonds(self) -> int:
+        return len(self.bonds)
+
+    @property
+    def MV(self) -> int:
+        return self.N + self.n_bonds
 
 
 class Su2Ensemble:
@@ -437,11 +461,15 @@ class Su2Ensemble:
         self.chain_model = np.ascontiguousarray(chain_model, dtype=np.int32)
         self._keep = []
         descs = (Su2ModelDesc * len(self.models))()
+        i32p = ctypes.POINTER(ctypes.c_int32)
         for i, m in enumerate(self.models):
             H = np.ascontiguousarray(m.hopping, dtype=np.float64)
-            self._keep.append(H)
+            bs = np.ascontiguousarray(np.asarray(m.bonds, dtype=np.int32).reshape(-1, 2))
+            ps = np.ascontiguousarray(np.asarray(m.pairs, dtype=np.int32).reshape(-1, 2))
+            self._keep += [H, bs, ps]
             descs[i] = Su2ModelDesc(m.N, H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(m.U),
-                                    float(m.dtau), int(m.L), int(m.n_wrap))
+                                    float(m.dtau), int(m.L), int(m.n_wrap), len(bs), bs.ctypes.data_as(i32p),
+                                    float(m.xi), float(m.h), float(m.J), len(ps), ps.ctypes.data_as(i32p))
         self._descs = descs
         ml = max(m.L for m in self.models) if meas_last is None else meas_last
         self.opts = Su2Opts(int(measure), int(meas_first), int(ml), int(seed), float(unstable_threshold))
@@ -499,23 +527,24 @@ class Su2Ensemble:
         return G[..., 0] + 1j * G[..., 1], la.value, ar.value, complex(ph[0], ph[1])
 
     def measure(self, reset: bool = False):
-        """(complex [n_chains, 4] reweighted sums of Kin, Pot, Part, Ener; sign sums; counts)."""
-        out = np.zeros((self.n_chains, 4, 2))
+        """(complex [n_chains, 5] reweighted sums of Kin, Pot, Part, Ener and the bond
+        spins' (sum_b s_b)^2 / n_bonds; sign sums; counts)."""
+        out = np.zeros((self.n_chains, 5, 2))
         sg = np.zeros(self.n_chains)
         nm = np.zeros(self.n_chains, dtype=np.int64)
         self._check(self._lib.dqmc_su2_measure(self._h, _p(out), _p(sg), _p(nm), int(reset)))
         return out[..., 0] + 1j * out[..., 1], sg, nm
 
     def get_fields(self):
-        total = sum(self.model_of(c).L * self.model_of(c).N for c in range(self.n_chains))
+        total = sum(self.model_of(c).L * self.model_of(c).MV for c in range(self.n_chains))
         buf = np.zeros(total, dtype=np.int8)
         ctr = ctypes.c_uint64()
         self._check(self._lib.dqmc_su2_get_fields(self._h, _p(buf), ctypes.byref(ctr)))
         out, off = [], 0
         for c in range(self.n_chains):
             m = self.model_of(c)
-            out.append(buf[off:off + m.L * m.N].reshape(m.L, m.N).copy())
-            off += m.L * m.N
+            out.append(buf[off:off + m.L * m.MV].reshape(m.L, m.MV).copy())
+            off += m.L * m.MV
         return out, ctr.value
 
     def set_fields(self, fields, sweep_counter: int = 0):

@@ -468,3 +468,58 @@ def test_gpu_sampler_matches_exact_diagonalisation(dq, precision):
         x = per_chain[:, q]
         mean, err = x.mean(), x.std(ddof=1) / np.sqrt(n)
         assert abs(mean - ref) < 3 * err + 1e-12, (q, mean, err, ref)
+
+
+# ------------------------------------------ SVD stabilisation (FP64 option)
+@pytest.mark.parametrize("ft", [1, 2])
+def test_svd_stabilisation_green_matches_oracle(dq, orc, ft):
+    """stab_svd=1: every chain step decomposed by one-sided Jacobi SVD.  The fresh
+    G(0) and an interior G(tau) against the oracle's SVD chain and its QR chain at
+    beta = 10, U = 6 (relative to max(1, max|G|), as the oracle's own SVD-vs-QR
+    pin: two backward-stable routes agree to rounding times the conditioning)."""
+    m = W.ModelSpec(W.square_lattice(4, 4, tp=-0.1, mu=-0.2), U=6.0, dtau=0.1, L=100, n_wrap=10, field_type=ft)
+    f = W.random_fields(ft, m.L, 16, seed=3)
+    ens = dq.Ensemble([m], [0], fields=[f], precision="fp64", stab_svd=True)
+    om = omodel(orc, m)
+    for s in (0, 1):
+        Gs, ls, ss = orc.green_udv_svd(om, f, s, 0)
+        Gq, lq, sq = orc.green_udv(om, f, s, 0)
+        scale = max(1.0, np.abs(Gq).max())
+        for fresh in (True, False):
+            Gg, ldg, sgg = ens.greens(0, s, fresh=fresh)
+            assert np.abs(Gg - Gs).max() < 1e-10 * scale and np.abs(Gg - Gq).max() < 1e-10 * scale, (s, fresh)
+            assert ldg == pytest.approx(ls, rel=1e-11) and sgg == ss == sq
+        # G(30): the stored SVD chain at an interior stabilisation point (no wraps)
+        Gt = ens.greens_tau(0, s, 30)
+        Go, _, _ = orc.green_udv_svd(om, f, s, 30)
+        assert np.abs(Gt - Go).max() < 1e-10 * max(1.0, np.abs(Go).max())
+        # G(37): seven FP64 wraps from there; rounding grows with the wraps as the
+        # precision monitor of Sec. 2.3 measures it, so the bar is the monitor's
+        Gt = ens.greens_tau(0, s, 37)
+        Go, _, _ = orc.green_udv_svd(om, f, s, 37)
+        assert np.abs(Gt - Go).max() < 1e-6
+    ens.close()
+
+
+def test_svd_stabilisation_trajectory_and_monitor(dq, orc):
+    """The SVD option changes G only by rounding: the field trajectory equals the
+    oracle's (QR) chain, and the monitor stays at the QR path's level."""
+    m = square(4, U=4.0, L=20, nw=10, ft=1)
+    seed = 20170401
+    ens = dq.Ensemble([m], [0], precision="fp64", delay_k=8, seed=seed, stab_svd=True)
+    f0, _ = ens.get_fields()
+    och = orc.Chain(omodel(orc, m), f0[0], seed=seed, chain=0)
+    sg = ens.sweep(3)
+    so = och.sweep(3)
+    fg, _ = ens.get_fields()
+    fo, _, _ = och.fields()
+    assert np.array_equal(fg[0], fo)
+    assert sg["accepted"] == so.accepted
+    assert sg["prec_green_mean"] < 1e-8 and sg["prec_green_max"] < 1e-6
+    for s in (0, 1):
+        Gg, _, _ = ens.greens(0, s)
+        assert np.abs(Gg - och.green(s)).max() < 1e-10
+    ens.close()
+    with pytest.raises(dq.DqmcError) as e:
+        dq.Ensemble([m], [0], precision="mixed", stab_svd=True)
+    assert e.value.status == dq.DQMC_EINVAL

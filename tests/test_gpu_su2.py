@@ -12,6 +12,10 @@ coupling; Sec. 2.2 phase; Sec. 2.3 stabilisation).
   same Philox streams, and the reweighted energy at tau = 0 agrees.
 * Precision Green / Precision Phase at beta = 10 stay at the level of the
   paper's example; at half filling every weight is positive (sign 1, P = 1).
+* Hubbard-Ising bond model (Sec. 6): Ising spins on bonds entering the
+  propagator as two-site factors; G(0), log|det| and arg det against the
+  oracle's bond-model UDV chain, and the joint trajectory of HS fields and bond
+  spins (rank-2 updates, the spins' own weight) against its Markov chain.
 """
 import numpy as np
 import pytest
@@ -132,6 +136,102 @@ def test_su2_rejects_bad_input(dq):
     m = dq.Su2Model(W.square_lattice(2, 2), U=4.0, dtau=0.1, L=10, n_wrap=5)
     bad = np.ones((10, 4), dtype=np.int8)
     bad[3, 2] = 0
+    with pytest.raises(dq.DqmcError) as e:
+        dq.Su2Ensemble([m], [0], fields=[bad])
+    assert e.value.status == dq.DQMC_EINVAL
+
+
+# ------------------------------------------------ Hubbard-Ising bond model
+def _square_bonds(Lx, Ly):
+    idx = lambda x, y: (x % Lx) + Lx * (y % Ly)
+    return [(idx(x, y), idx(x + 1, y)) for y in range(Ly) for x in range(Lx)] + \
+           [(idx(x, y), idx(x, y + 1)) for y in range(Ly) for x in range(Lx)]
+
+
+def _bond_config(rng, L, N, nb):
+    hs = rng.choice(np.array([-2, -1, 1, 2], dtype=np.int8), size=(L, N))
+    z = rng.choice(np.array([-1, 1], dtype=np.int8), size=(L, nb))
+    return hs, z
+
+
+@pytest.mark.parametrize("L,nw,mu", [(15, 5, 0.2), (100, 10, 0.3)])
+def test_bond_model_fresh_green_matches_oracle(dq, orc, L, nw, mu):
+    """3 x 3 square with an Ising spin on every bond: G(0), log|det| and arg det of
+    the complex UDV chain with the bond factors against the oracle's chain."""
+    K = W.square_lattice(3, 3, t=1.0, mu=mu)
+    bonds = _square_bonds(3, 3)
+    xi, h, J, dtau, U = 0.4, 0.6, 0.3, 0.1, 4.0
+    pairs = [(b, (b + 1) % len(bonds)) for b in range(len(bonds))]
+    rng = np.random.default_rng(L)
+    cfg = [_bond_config(rng, L, 9, len(bonds)) for _ in range(2)]
+    m = dq.Su2Model(K, U=U, dtau=dtau, L=L, n_wrap=nw, bonds=bonds, xi=xi, h=h, J=J, pairs=pairs)
+    ens = dq.Su2Ensemble([m], [0, 0], fields=[np.concatenate([hs, z], axis=1) for hs, z in cfg], seed=1)
+    for c, (hs, z) in enumerate(cfg):
+        Go, lo, ao = orc.hubbard_ising_green_udv(K, bonds, xi, dtau, U, nw, hs, z, 0)
+        for fresh in (False, True):
+            G, la, ar, _ = ens.greens(c, fresh=fresh)
+            assert np.abs(G - Go).max() < 1e-10, (c, fresh)
+            assert la == pytest.approx(lo, rel=1e-10, abs=1e-10) and abs(_wrap(ar - ao)) < 1e-10
+    f, _ = ens.get_fields()
+    assert all(np.array_equal(f[c], np.concatenate(cfg[c], axis=1)) for c in range(2))
+    ens.close()
+
+
+@pytest.mark.parametrize("case", ["chain3_half", "chain3_mu", "square3x3"])
+def test_bond_model_trajectory_matches_oracle(dq, orc, case):
+    """HS fields and bond spins sampled together: after every sweep the fields,
+    the spins, the acceptance count, the phase and the reweighted Kin and
+    (sum_b s_b)^2 / n_bonds at tau = 0 equal the oracle's chain (plain recompute
+    of the Green function at every vertex)."""
+    if case.startswith("chain3"):
+        K = W.chain_lattice(3, t=1.0, mu=0.0 if case == "chain3_half" else 0.4)
+        bonds, pairs, L, nw, dtau, n_sweeps = [(0, 1), (1, 2)], [(0, 1)], 4, 2, 0.25, 3
+        xi, h, J, U = 0.7, 0.8, 0.4, 2.0
+    else:
+        K = W.square_lattice(3, 3, t=1.0, mu=0.2)
+        bonds = _square_bonds(3, 3)
+        pairs = [(b, (b + 9) % 18) for b in range(9)]
+        L, nw, dtau, n_sweeps = 8, 4, 0.125, 2
+        xi, h, J, U = 0.4, 0.6, 0.3, 4.0
+    N, nb, n_ch, seed = K.shape[0], len(bonds), 3, 4321
+    rng = np.random.default_rng(7)
+    cfg = [_bond_config(rng, L, N, nb) for _ in range(n_ch)]
+    m = dq.Su2Model(K, U=U, dtau=dtau, L=L, n_wrap=nw, bonds=bonds, xi=xi, h=h, J=J, pairs=pairs)
+    ens = dq.Su2Ensemble([m], [0] * n_ch, fields=[np.concatenate([hs, z], axis=1) for hs, z in cfg], seed=seed,
+                         measure=True, meas_first=0, meas_last=0)
+    chains = [orc.HubbardIsingChain(K, bonds, xi, h, J, pairs, dtau, U, hs, z, seed=seed, chain=c)
+              for c, (hs, z) in enumerate(cfg)]
+    for sweep in range(n_sweeps):
+        st = ens.sweep(1)
+        obs, sg, nm = ens.measure(reset=True)
+        fields, _ = ens.get_fields()
+        acc = 0
+        for c in range(n_ch):
+            kin_o, s_o, m2_o, a = chains[c].sweep()
+            acc += a
+            assert np.array_equal(fields[c][:, :N], chains[c].hs.reshape(L, N)), (sweep, c)
+            assert np.array_equal(fields[c][:, N:], chains[c].ising.reshape(L, nb)), (sweep, c)
+            _, _, _, P = ens.greens(c)
+            assert abs(P - complex(chains[c].phase[0], chains[c].phase[1])) < 1e-9
+            assert nm[c] == 1 and sg[c] == s_o
+            assert abs(obs[c, 0] - kin_o) < 1e-8 * max(1.0, abs(kin_o))
+            assert abs(obs[c, 4] - m2_o) < 1e-8 * max(1.0, abs(m2_o))
+        assert st["accepted"] == acc and st["proposals"] == n_ch * 2 * L * (N + nb)
+        assert 0 < acc < st["proposals"]
+    ens.close()
+
+
+def test_bond_model_rejects_bad_bonds(dq):
+    K = W.chain_lattice(3)
+    for kw in (dict(bonds=[(0, 0)], h=1.0), dict(bonds=[(0, 3)], h=1.0), dict(bonds=[(0, 1)], h=0.0),
+               dict(bonds=[(0, 1)], h=1.0, pairs=[(0, 0)]), dict(bonds=[], pairs=[(0, 1)])):
+        m = dq.Su2Model(K, U=2.0, dtau=0.1, L=4, n_wrap=2, xi=0.5, **kw)
+        with pytest.raises(dq.DqmcError) as e:
+            dq.Su2Ensemble([m], [0])
+        assert e.value.status == dq.DQMC_EINVAL, kw
+    m = dq.Su2Model(K, U=2.0, dtau=0.1, L=4, n_wrap=2, bonds=[(0, 1)], xi=0.5, h=1.0)
+    bad = np.ones((4, 4), dtype=np.int8)
+    bad[2, 3] = 2                      # a bond spin must be +-1
     with pytest.raises(dq.DqmcError) as e:
         dq.Su2Ensemble([m], [0], fields=[bad])
     assert e.value.status == dq.DQMC_EINVAL
