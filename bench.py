@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-oracle-check", action="store_true", help="skip the max|dG| check against the oracle")
     ap.add_argument("--paper-example", action="store_true",
                     help="precision monitors of the paper's 4x4, U=4, beta=10 spin-z example instead of the bench")
+    ap.add_argument("--run-option", action="append", default=[], metavar="KEY=VALUE",
+                    help="a dqmc_run_opts field for the main path without the autotuner (e.g. tc_min_sites=1)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --precision and the workload's delay_k as given instead of tuning them")
     return ap.parse_args()
@@ -420,7 +422,7 @@ def run_ours(args, wl: W.Workload, rank: int, world: int, local_rank: int):
     seed = rank_seed(rank)
     peaks = measured_peaks()
     main_prec, k_main, k_fp64 = args.precision, wl.delay_k, wl.delay_k
-    opt_main = {}
+    opt_main = {k: int(v) for k, v in (o.split("=", 1) for o in args.run_option)}
     tuned = None
     if not args.no_autotune:
         # untimed: pick the product family and the delayed-update rank on this GPU
