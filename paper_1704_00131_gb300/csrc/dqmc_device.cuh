@@ -430,6 +430,7 @@ struct Smem {
   double* Rs;       // [2][MV] own-flavor ratios, double buffered (read by the peer CTA)
   double* Rp;       // [MV] full ratio of the position a thread found accepted
   double* xdiag;    // [ld] exchange: diagonal of G for the potential energy
+  double* spare;    // [ld] scratch (the float-pair QR's list of norms to recompute)
   double* xs;       // [8]  exchange: scalars
   double* red;      // [32]
   int* ired;        // [32]
@@ -497,7 +498,7 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   s.d = p; p += ld;
   s.hv = p; p += ld;
   s.xdiag = p; p += ld;
-  p += ld;
+  s.spare = p; p += ld;
   s.u2 = p; p += MV;
   s.delta = p; p += MV;
   s.gam = p; p += MV;
@@ -1717,11 +1718,25 @@ __device__ void householder_apply_dd(int N, int ld, dd* M, int k, int j0, dd bk,
   }
 }
 
-__device__ int qr_pivoted_dd(int N, int ld, dd* X, double* dsc, double* beta, dd* vk0, double* cn, double* cn0,
-                             int* perm, Smem& S) {
-  const int tid = threadIdx.x;
+__device__ int qr_pivoted_dd(int N, int ld, dd* X, double* dsc, double* beta, dd* vk0, double* cn_g, double* cn0_g,
+                             int* perm_g, Smem& S) {
+  // Per-column state in shared memory (the sweep's slice buffers, idle during
+  // the stabilisation): norms cn / cn0, scales, pivot order, recompute list.
+  // The reflector's scalars are formed by thread 0 and broadcast; the norms are
+  // downdated with LAPACK's xGEQPF rule and those that cancel below its
+  // threshold are recomputed in FP64 by one warp each.
+  (void)cn_g;
+  (void)cn0_g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   dd* hv = reinterpret_cast<dd*>(S.hv);
   dd* qred = reinterpret_cast<dd*>(S.qred);
+  double* cn = S.d;
+  double* cn0 = S.xdiag;
+  double* sd = S.ev;
+  int* perm = S.qinv;
+  int* flag = reinterpret_cast<int*>(S.spare);
+  int* nflag = S.ired + 24;
+  double* sc = S.xs + 4;
   for (int j = tid; j < N; j += kThreads) {
     double acc = 0.0;
     for (int i = 0; i < N; ++i) {
@@ -1731,6 +1746,7 @@ __device__ int qr_pivoted_dd(int N, int ld, dd* X, double* dsc, double* beta, dd
     cn[j] = sqrt(acc);
     cn0[j] = cn[j];
     perm[j] = j;
+    sd[j] = dsc[j];
   }
   __syncthreads();
   const double tol3z = sqrt(2.220446049250313e-16);
@@ -1739,7 +1755,7 @@ __device__ int qr_pivoted_dd(int N, int ld, dd* X, double* dsc, double* beta, dd
     double bv = -1.0;
     int bi = N;
     for (int j = k + tid; j < N; j += kThreads) {
-      const double sn = dsc[j] * cn[j];
+      const double sn = sd[j] * cn[j];
       if (sn > bv) { bv = sn; bi = j; }
     }
     int p = block_argmax(bv, bi, S.red, S.ired);
@@ -1754,7 +1770,7 @@ __device__ int qr_pivoted_dd(int N, int ld, dd* X, double* dsc, double* beta, dd
         const int tp = perm[k]; perm[k] = perm[p]; perm[p] = tp;
         double t = cn[k]; cn[k] = cn[p]; cn[p] = t;
         t = cn0[k]; cn0[k] = cn0[p]; cn0[p] = t;
-        t = dsc[k]; dsc[k] = dsc[p]; dsc[p] = t;
+        t = sd[k]; sd[k] = sd[p]; sd[p] = t;
       }
       __syncthreads();
     }
@@ -1766,48 +1782,65 @@ __device__ int qr_pivoted_dd(int N, int ld, dd* X, double* dsc, double* beta, dd
       hv[i] = x;
     }
     const double xn2 = block_sum(part, S.red);
-    const double xnorm = sqrt(xn2);
-    const dd x0 = hv[k];
-    double bk = 0.0, alpha = 0.0;
-    if (xnorm > 0.0) {
-      const double x0d = to_d(x0);
-      alpha = (x0d >= 0.0) ? -xnorm : xnorm;
-      const dd v0 = dd_add(x0, from_d<dd>(-alpha));
-      const double v0d = to_d(v0);
-      const double vtv = xn2 - x0d * x0d + v0d * v0d;
-      bk = (vtv > 0.0) ? 2.0 / vtv : 0.0;
-      __syncthreads();
-      if (tid == 0) hv[k] = v0;
-      __syncthreads();
-    }
     if (tid == 0) {
+      const double xnorm = sqrt(xn2);
+      const dd x0 = hv[k];
+      double bk = 0.0;
+      if (xnorm > 0.0) {
+        const double x0d = to_d(x0);
+        const double alpha = (x0d >= 0.0) ? -xnorm : xnorm;
+        const dd v0 = dd_add(x0, from_d<dd>(-alpha));
+        const double v0d = to_d(v0);
+        const double vtv = xn2 - x0d * x0d + v0d * v0d;
+        bk = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+        hv[k] = v0;
+        X[(size_t)k * ld + k] = from_d<dd>(alpha);
+      }
       beta[k] = bk;
       vk0[k] = hv[k];
+      sc[0] = bk;
+      *nflag = 0;
     }
-    if (bk != 0.0) detq = -detq;
-    if (bk != 0.0) householder_apply_dd(N, ld, X, k, k + 1, from_d<dd>(bk), hv, qred);
     __syncthreads();
-    if (tid == 0) X[(size_t)k * ld + k] = (xnorm > 0.0) ? from_d<dd>(alpha) : x0;
+    const double bk = sc[0];
+    if (bk != 0.0) {
+      detq = -detq;
+      householder_apply_dd(N, ld, X, k, k + 1, from_d<dd>(bk), hv, qred);
+    }
     for (int j = k + 1 + tid; j < N; j += kThreads) {
       if (cn[j] != 0.0) {
         double t = fabs(to_d(X[(size_t)k * ld + j])) / cn[j];
         t = fmax(0.0, (1.0 + t) * (1.0 - t));
         const double r = cn[j] / cn0[j];
-        if (t * r * r <= tol3z) {
-          double acc = 0.0;
-          for (int i = k + 1; i < N; ++i) {
-            const double x = to_d(X[(size_t)i * ld + j]);
-            acc = fma(x, x, acc);
-          }
-          cn[j] = sqrt(acc);
-          cn0[j] = cn[j];
-        } else {
-          cn[j] *= sqrt(t);
-        }
+        if (t * r * r <= tol3z) flag[atomicAdd(nflag, 1)] = j;
+        else cn[j] *= sqrt(t);
       }
     }
     __syncthreads();
+    const int nf = *nflag;
+    if (nf) {
+      for (int q = warp; q < nf; q += kThreads / 32) {
+        const int j = flag[q];
+        double acc = 0.0;
+        for (int i = k + 1 + lane; i < N; i += 32) {
+          const double x = to_d(X[(size_t)i * ld + j]);
+          acc = fma(x, x, acc);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+          cn[j] = sqrt(acc);
+          cn0[j] = cn[j];
+        }
+      }
+      __syncthreads();
+    }
   }
+  for (int j = tid; j < N; j += kThreads) {
+    perm_g[j] = perm[j];
+    dsc[j] = sd[j];
+  }
+  __syncthreads();
   return detq;
 }
 

@@ -235,3 +235,64 @@ def test_bond_model_rejects_bad_bonds(dq):
     with pytest.raises(dq.DqmcError) as e:
         dq.Su2Ensemble([m], [0], fields=[bad])
     assert e.value.status == dq.DQMC_EINVAL
+
+
+# ------------------------------------------------- the samplers against ED
+@pytest.mark.parametrize("mu", [0.0, 0.4])
+def test_su2_sampler_matches_trotter_energy(dq, orc, mu):
+    """256 GPU chains of the SU(2) decoupling on a dimer, reweighted by
+    sign P / Re P (Sec. 2.2): the energy at tau = 0 agrees with the Fock-space
+    trace of the Trotter product within 4 sigma (spread over the chains), at and
+    away from half filling."""
+    from paper_1704_00131_gb300 import analysis as A
+
+    from .fock_ed import Fock, su2_trotter
+    K, U, dtau, L = W.chain_lattice(2, t=1.0, mu=mu), 4.0, 0.25, 4
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+    _, Ef = su2_trotter(Fock(2), K, U, dtau, L, eta, gam)
+    n_ch, burn, n = 256, 40, 300
+    m = dq.Su2Model(K, U=U, dtau=dtau, L=L, n_wrap=2)
+    ens = dq.Su2Ensemble([m], [0] * n_ch, seed=31 + int(10 * mu), measure=True, meas_first=0, meas_last=0)
+    ens.sweep(burn)
+    ens.measure(reset=True)
+    st = ens.sweep(n)
+    obs, sg, nm = ens.measure()
+    ens.close()
+    assert (nm == n).all() and 0 < st["accepted"] < st["proposals"]
+    mean_re, err_re = A.jackknife(obs[:, 3].real / n, sg / n)
+    mean_im, err_im = A.jackknife(obs[:, 3].imag / n, sg / n)
+    assert abs(mean_re - Ef.real) < 4 * err_re, (mean_re, err_re, Ef)
+    assert abs(mean_im) < 4 * err_im + 1e-12
+    assert err_re < 0.05 * abs(Ef.real)
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.4])
+def test_bond_model_sampler_matches_trotter_product(dq, orc, mu):
+    """256 GPU chains of the Hubbard-Ising model on a three-site chain with two
+    bonds: the reweighted Kin and the bond spins' (sum_b s_b)^2 / n_bonds at
+    tau = 0 agree with the trace of the Trotter product on Fock (x) Ising space
+    within 4 sigma."""
+    from paper_1704_00131_gb300 import analysis as A
+
+    from .fock_ed import Fock, hubbard_ising_trotter
+    K, U, dtau, L = W.chain_lattice(3, t=1.0, mu=mu), 2.0, 0.25, 4
+    bonds, pairs = [(0, 1), (1, 2)], [(0, 1)]
+    xi, h, J = 0.7, 0.8, 0.4
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+    _, kin_ref, m2_ref = hubbard_ising_trotter(Fock(3), K, U, dtau, L, eta, gam, bonds, xi, h, J, pairs,
+                                               with_m2=True)
+    n_ch, burn, n = 256, 40, 300
+    m = dq.Su2Model(K, U=U, dtau=dtau, L=L, n_wrap=2, bonds=bonds, xi=xi, h=h, J=J, pairs=pairs)
+    ens = dq.Su2Ensemble([m], [0] * n_ch, seed=57 + int(10 * mu), measure=True, meas_first=0, meas_last=0)
+    ens.sweep(burn)
+    ens.measure(reset=True)
+    st = ens.sweep(n)
+    obs, sg, nm = ens.measure()
+    ens.close()
+    assert (nm == n).all() and 0.05 < st["accepted"] / st["proposals"] < 0.95
+    for q, ref in ((0, kin_ref.real), (4, m2_ref.real)):
+        mean, err = A.jackknife(obs[:, q].real / n, sg / n)
+        assert abs(mean - ref) < 4 * err, (q, mean, err, ref)
+        assert err < 0.05 * abs(ref)
