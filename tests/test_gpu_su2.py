@@ -264,7 +264,9 @@ def test_su2_sampler_matches_trotter_energy(dq, orc, mu):
     mean_im, err_im = A.jackknife(obs[:, 3].imag / n, sg / n)
     assert abs(mean_re - Ef.real) < 4 * err_re, (mean_re, err_re, Ef)
     assert abs(mean_im) < 4 * err_im + 1e-12
-    assert err_re < 0.05 * abs(Ef.real)
+    # power of the test: the energy scale of the dimer is ~1 (the energy itself is
+    # ~0 at half filling, so the bar on the error is absolute)
+    assert err_re < 0.1
 
 
 @pytest.mark.parametrize("mu", [0.0, 0.4])
