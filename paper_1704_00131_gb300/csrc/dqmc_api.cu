@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/dqmc.h"
 #include "dqmc_internal.h"
 #include "dqmc_linalg_host.h"
@@ -44,6 +46,7 @@ struct ModelHost {
   // split-product planes of the constant propagators (tensor-core products only)
   void* cpl[dqmc::kMaxFlavors][5] = {};
   int* cex[dqmc::kMaxFlavors][5] = {};
+  CUtensorMap tmc[dqmc::kMaxFlavors][5] = {};
 };
 
 }  // namespace
@@ -139,6 +142,43 @@ dqmc_status upload(dqmc_ctx* ctx, T** dst, const T* src, size_t n) {
   return DQMC_OK;
 }
 
+// The driver's tensor-map encoder, through the runtime's entry-point query (the
+// library does not link against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a digit-plane buffer of `bytes` bytes for the split products:
+// the 4D view [blocks][kPlaneDigits][rows][kPlaneK] of bf16 (k innermost,
+// contiguous) with a box of one whole block, so that a tiled copy at block
+// coordinate b moves the b-th block's bytes unchanged.  0 on success.
+int encode_plane_map(CUtensorMap* tm, void* base, int rows, size_t bytes) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn) return 1;
+  const uint64_t row_bytes = (uint64_t)dqmc::kPlaneK * 2;
+  const uint64_t blk = (uint64_t)dqmc::kPlaneDigits * rows * row_bytes;
+  if (bytes < blk || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return 2;
+  const cuuint64_t dims[4] = {(cuuint64_t)dqmc::kPlaneK, (cuuint64_t)rows, (cuuint64_t)dqmc::kPlaneDigits,
+                              (cuuint64_t)(bytes / blk)};
+  const cuuint64_t strides[3] = {row_bytes, (cuuint64_t)rows * row_bytes, blk};
+  const cuuint32_t box[4] = {(cuuint32_t)dqmc::kPlaneK, (cuuint32_t)rows, (cuuint32_t)dqmc::kPlaneDigits, 1u};
+  const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+  const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : 3;
+}
+
+size_t pad_to(size_t n, size_t q) { return (n + q - 1) / q * q; }
+
 dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
   const dqmc_model_desc& d = M.d;
   const int N = d.n_sites, nfl = d.n_flavors;
@@ -215,6 +255,9 @@ dqmc_status setup_model(dqmc_ctx* ctx, ModelHost& M) {
         CUDA_TRY(ctx, dqmc::launch_const_planes(X, N, ld, q.right, q.tr, p, e, ctx->stream));
         M.cpl[f][q.which] = p;
         M.cex[f][q.which] = e;
+        const int em = encode_plane_map(&M.tmc[f][q.which], p, q.right ? dqmc::kPlaneRowsB : dqmc::kPlaneRowsA,
+                                        dqmc::const_plane_bytes(N, q.right));
+        if (em) return fail(ctx, DQMC_ECUDA, "tensor map of the constant digit planes (code %d)", em);
       }
   }
   return DQMC_OK;
@@ -285,6 +328,7 @@ void fill_model_fields(const ModelHost& M, ChainDev& C) {
     for (int q = 0; q < 5; ++q) {
       C.cpl[s][q] = M.cpl[s][q];
       C.cex[s][q] = M.cex[s][q];
+      C.tm_cp[s][q] = M.tmc[s][q];
     }
   }
   C.site = M.site_d;
@@ -307,13 +351,18 @@ dqmc_status download_chains(dqmc_ctx* ctx) {
 // DQMC_ETIMEOUT with the first wait that gave up in each flavor of chain C.
 dqmc_status timeout_message(dqmc_ctx* ctx, const ChainDev& C) {
   std::string m;
+  bool misaligned = false;
   for (int s = 0; s < C.nfl; ++s) {
     const int* w = C.wait_where[s];
+    misaligned = misaligned || w[0] == 9;
     char b[200];
     snprintf(b, sizeof(b), "; flavor %d: kind %d at chunk %d of %d in product %d (barrier %08x %08x)", s, w[0], w[1],
              w[2], w[3], (unsigned)w[5], (unsigned)w[4]);
     m += b;
   }
+  if (misaligned)
+    return fail(ctx, DQMC_ECUDA, "chain %u: staging buffers of the tensor-core products not 128-byte aligned%s",
+                C.chain_id, m.c_str());
   return fail(ctx, DQMC_ETIMEOUT, "chain %u: a bounded wait of the tensor-core products gave up%s", C.chain_id,
               m.c_str());
 }
@@ -420,6 +469,22 @@ dqmc_status dqmc_init(const dqmc_model_desc* models, int32_t n_models, const int
     const ModelHost& M = c->models[chain_model[i]];
     chain_layout(M, opts->precision, opts->delay_k, c->arena + offs[i], &C, tc_min_sites(*opts));
     fill_model_fields(M, C);
+    for (int s = 0; s < M.d.n_flavors; ++s) {
+      if (!C.planes[s]) continue;
+      // the scratch planes: the left operand's blocks first, the right operand's
+      // after them (the offset the kernels use)
+      const size_t N = (size_t)M.d.n_sites, kp = pad_to(N, dqmc::kPlaneK);
+      const size_t bytesA = (size_t)dqmc::kPlaneDigits * pad_to(N, dqmc::kPlaneRowsA) * kp * 2;
+      const size_t bytesB = (size_t)dqmc::kPlaneDigits * pad_to(N, dqmc::kPlaneRowsB) * kp * 2;
+      int em = encode_plane_map(&C.tm_pl[s][0], C.planes[s], dqmc::kPlaneRowsA, bytesA);
+      if (!em)
+        em = encode_plane_map(&C.tm_pl[s][1], static_cast<unsigned char*>(C.planes[s]) + bytesA, dqmc::kPlaneRowsB,
+                              bytesB);
+      if (em) {
+        *out = ctx.release();
+        return fail(*out, DQMC_ECUDA, "tensor map of the digit-plane scratch (code %d)", em);
+      }
+    }
     C.chain_id = (uint32_t)i;
     C.sign = 1;
     C.wait_cycles = opts->spin_limit;

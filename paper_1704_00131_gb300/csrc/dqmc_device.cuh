@@ -527,6 +527,9 @@ __device__ inline Smem carve_smem(unsigned char* base, int ld, int MV) {
   s.dd_tile = 0;
   s.um.limit = kUmmaWaitCycles;
   s.um.stall = 0;
+  s.um.tmA = nullptr;
+  s.um.tmB = nullptr;
+  s.um.boff = 0;
   q += 128;
   // base is 16-byte aligned (kSmemCounterBytes past the start); align s.ab to 128
   const uintptr_t qa = (reinterpret_cast<uintptr_t>(q) + 127) & ~(uintptr_t)127;
@@ -544,10 +547,12 @@ __device__ void gemm_dd(const ChainDev& C, int s, Smem& S, int M, int Nc, int Kd
 #if DQMC_WITH_UMMA
   if (C.planes[s]) {
     // constA / constB: index of a prepared constant operand (kCpEA ...), -1: split here
-    const UmmaOperand cA = constA >= 0 ? UmmaOperand{(const __nv_bfloat16*)C.cpl[s][constA], C.cex[s][constA]}
-                                       : UmmaOperand{nullptr, nullptr};
-    const UmmaOperand cB = constB >= 0 ? UmmaOperand{(const __nv_bfloat16*)C.cpl[s][constB], C.cex[s][constB]}
-                                       : UmmaOperand{nullptr, nullptr};
+    const UmmaOperand cA = constA >= 0 ? UmmaOperand{(const __nv_bfloat16*)C.cpl[s][constA], C.cex[s][constA],
+                                                     &C.tm_cp[s][constA]}
+                                       : UmmaOperand{nullptr, nullptr, nullptr};
+    const UmmaOperand cB = constB >= 0 ? UmmaOperand{(const __nv_bfloat16*)C.cpl[s][constB], C.cex[s][constB],
+                                                     &C.tm_cp[s][constB]}
+                                       : UmmaOperand{nullptr, nullptr, nullptr};
     gemm_umma<TA, TB, ACC>(M, Nc, Kd, A, lda, B, ldb, Cm, ldc, (__nv_bfloat16*)C.planes[s], S.expA, S.expB, S.um,
                            cA, cB);
     return;
@@ -1302,6 +1307,9 @@ __global__ void __launch_bounds__(kThreads) fresh_green_kernel(ChainDev* chains,
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
   S.um.stall = C.test_stall;
+  S.um.tmA = &C.tm_pl[s][0];
+  S.um.tmB = &C.tm_pl[s][1];
+  S.um.boff = (size_t)kUmmaDig * umma_pad(C.N, kUmmaM) * umma_pad(C.N, kUmmaK);
   S.um.where = C.wait_where[s];
   if (umma) umma_alloc(S.um);
   double logdet;
@@ -1363,6 +1371,9 @@ __global__ void __launch_bounds__(kThreads) green_tau_kernel(ChainDev* chains, i
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
   S.um.stall = C.test_stall;
+  S.um.tmA = &C.tm_pl[s][0];
+  S.um.tmB = &C.tm_pl[s][1];
+  S.um.boff = (size_t)kUmmaDig * umma_pad(C.N, kUmmaM) * umma_pad(C.N, kUmmaK);
   S.um.where = C.wait_where[s];
   if (umma) umma_alloc(S.um);
   int dq = 1;
@@ -2165,6 +2176,9 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(ChainDev* chains, Sw
   S.dd_tile = C.dd_tile;
   S.um.limit = C.wait_cycles > 0 ? C.wait_cycles : kUmmaWaitCycles;
   S.um.stall = C.test_stall;
+  S.um.tmA = &C.tm_pl[s][0];
+  S.um.tmB = &C.tm_pl[s][1];
+  S.um.boff = (size_t)kUmmaDig * umma_pad(C.N, kUmmaM) * umma_pad(C.N, kUmmaK);
   S.um.where = C.wait_where[s];
   if (umma) umma_alloc(S.um);
   Real* G = (Real*)C.G[s];

@@ -2,12 +2,18 @@
 // (dqmc_kernels.cu) of the GB300 DQMC library.  Not part of the public C ABI.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace dqmc {
 
 constexpr int kThreads = 256;      // threads per CTA of every kernel
 constexpr int kMaxFlavors = 2;
+// Digit planes of the split tensor-core products: blocks of kPlaneDigits digits
+// x rows x kPlaneK bf16 (rows: kPlaneRowsA for a left operand, kPlaneRowsB for
+// a right one), one block per (tile, 16-wide K chunk), copied to shared memory
+// by one tiled tensor copy each.
+constexpr int kPlaneDigits = 7, kPlaneRowsA = 64, kPlaneRowsB = 48, kPlaneK = 16;
 
 // Device-resident description and state of one Markov chain.  One CTA per
 // (chain, flavor) works on it; the CTAs of a chain form one thread-block
@@ -41,6 +47,11 @@ struct ChainDev {
   // kCpEiB = E^-1 right, kCpEB = E right (null without tensor-core products)
   const void* cpl[kMaxFlavors][5];
   const int* cex[kMaxFlavors][5];
+  // tensor maps (4D views [blocks][digits][rows][k] with a box of one block) of
+  // the scratch planes as left [0] and right [1] operand, and of the constant
+  // operands' planes
+  CUtensorMap tm_pl[kMaxFlavors][2];
+  CUtensorMap tm_cp[kMaxFlavors][5];
   int* iwork[kMaxFlavors];        // [2*ld]
   uint32_t chain_id;
   int sign;                       // sign of the current weight (written by rank 0)
@@ -64,7 +75,8 @@ struct ChainDev {
   int dd_tile;                    // register tile of the float-pair SIMT products (0 by padding, 3, 4)
   int wait_where[kMaxFlavors][6]; // first wait that gave up per flavor: kind (1 copy, 2 MMAs
                                   // before a refill, 3 MMAs before the epilogue, 4 / 5 copy / MMAs
-                                  // at the end of a product), chunk (stage for 4, 5), chunks,
+                                  // at the end of a product; 9 a staging buffer not 128-byte
+                                  // aligned for the tensor copies), chunk (stage for 4, 5), chunks,
                                   // product ordinal in the kernel, barrier word (low, high)
   // SM cycles spent per phase during the current dqmc_sweep call, per flavor:
   // 0 updates, 1 wraps (V and T), 2 stabilisation, 3 measurement

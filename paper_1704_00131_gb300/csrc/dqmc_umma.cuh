@@ -1,6 +1,6 @@
 // Exact-split BF16 products of float-pair matrices on the fifth-generation
 // tensor cores (tcgen05.mma, accumulators in tensor memory, operands staged in
-// shared memory by bulk copies).  Included by dqmc_device.cuh inside its
+// shared memory by tiled tensor copies).  Included by dqmc_device.cuh inside its
 // namespace, after the float-pair arithmetic.
 //
 // Scheme (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012, on BF16
@@ -25,7 +25,10 @@
 // planes are laid out in global memory (per-chain scratch, L2-resident; the
 // constant propagators' planes are prepared once per model) in the order
 // (tile, k chunk, digit) with each 16-wide block in the canonical K-major layout
-// without swizzle, so one chunk is two contiguous bulk copies.  The chunks of
+// without swizzle.  The host describes each plane buffer by a tensor map, a 4D
+// view [blocks][7 digits][rows][16 k] whose box is one whole block, so one chunk
+// is two tiled tensor copies (cp.async.bulk.tensor) of 14 KB and 10.5 KB that
+// reproduce the blocks byte for byte in shared memory.  The chunks of
 // all tiles form one sequence streamed through three stages: while the 28 MMAs
 // of chunk g run, the copies of chunks g+1 and g+2 are in flight, across tile
 // boundaries too.  One thread issues the copies and the MMAs; completion is
@@ -38,6 +41,8 @@ constexpr int kUmmaSlots = 5;               // accumulators: diagonals 0, 1, 2, 
 constexpr int kUmmaM = 64;                  // tile rows (MMA M)
 constexpr int kUmmaNT = 48;                 // tile columns (MMA N)
 constexpr int kUmmaK = 16;                  // MMA K and staged chunk
+static_assert(kUmmaDig == kPlaneDigits && kUmmaM == kPlaneRowsA && kUmmaNT == kPlaneRowsB && kUmmaK == kPlaneK,
+              "the host's tensor maps describe these plane blocks");
 constexpr int kUmmaKSeg = 256;              // k per exactly accumulated segment
 constexpr int kUmmaCols = 256;              // tensor-memory columns allocated per CTA
 constexpr int kUmmaBlockA = kUmmaM * kUmmaK * 2;    // bytes of one digit block of A
@@ -58,6 +63,9 @@ __host__ __device__ inline size_t umma_plane_elems(int n, int kmax) {
 // local memory): the stages are found by umma_stage, and thread 0's
 // bookkeeping lives in the 128-byte shared barrier area.
 struct Umma {
+  const CUtensorMap* tmA; // tensor maps of the scratch planes as left / right operand
+  const CUtensorMap* tmB;
+  size_t boff;            // elements from the scratch planes to the right operand's planes
   unsigned char* stage0;  // first staging buffer (kUmmaStageBytes, the GEMM region)
   unsigned char* stage1;  // second; the third follows it
   uint64_t* bar;          // shared, 128 bytes: [0, 48) the 2 kUmmaStages mbarriers (copies landed
@@ -121,11 +129,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     if (clock64() - t0 > limit) return false;
   }
 }
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
+// One block of digit planes (all seven digits of a tile x 16-wide K chunk)
+// into shared memory: a tiled tensor copy of box (16, rows, 7, 1) at block
+// coordinate `block` of the 4D view [blocks][7][rows][16] the map describes.
+__device__ __forceinline__ void tma_load_block(void* dst, const CUtensorMap* tm, int block, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(0), "r"(0), "r"(block), "r"(smem_u32(bar))
+      : "memory");
 }
 __device__ __forceinline__ void umma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
   asm volatile(
@@ -166,6 +178,13 @@ __device__ inline void umma_alloc(const Umma& U) {
     uint32_t* book = umma_book(U);
     for (int q = 0; q < 4 * kUmmaStages; ++q) book[q] = 0u;
     *umma_calls(U) = 0u;
+  }
+  // tiled tensor copies need 128-byte aligned shared destinations: a staging
+  // buffer that is not marks the products void (they are then skipped and the
+  // call reports it) instead of issuing a copy the hardware would reject
+  if (threadIdx.x == 0 && (((smem_u32(U.stage0) | smem_u32(U.stage1)) & 127u) != 0u)) {
+    if (U.where && U.where[0] == 0) U.where[0] = 9;
+    if (U.err) atomicOr(U.err, 2);
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   tc_fence_before();
@@ -251,6 +270,7 @@ __device__ void umma_row_exponents(int R, int Kd, const dd* X, int ldx, int Rp, 
 struct UmmaOperand {
   const __nv_bfloat16* planes;
   const int* ex;
+  const CUtensorMap* tm;  // its tensor map (the 4D block view of `planes`)
 };
 
 // Digit planes of op(A) (rows of tile height UM) or of op(B)^T (rows = columns
@@ -285,13 +305,13 @@ __device__ __forceinline__ int umma_lane_of_row64(int r) { return ((r >> 4) << 5
 
 // C (+)= op(A) op(B), M x Nc, inner dimension Kd, float-pair operands (global
 // or L2-resident), on the tensor cores.  All threads of the CTA call it.
-// planes: umma_plane_elems(max(M, Nc), Kd) bf16 of global scratch; expA,
-// expB: shared [roundup(M,64)], [roundup(Nc,48)] ints; tmem: the CTA's
-// accumulator base.  C must not alias A or B.
+// planes: the chain's scratch (left operand's planes at the start, the right
+// operand's at U.boff; U.tmA / U.tmB their tensor maps); expA, expB: shared
+// [roundup(M,64)], [roundup(Nc,48)] ints.  C must not alias A or B.
 template <bool TA, bool TB, bool ACC>
 __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int lda, const dd* __restrict__ B, int ldb,
                           dd* __restrict__ C, int ldc, __nv_bfloat16* planes, int* expA_s, int* expB_s, const Umma U,
-                          UmmaOperand cA = {nullptr, nullptr}, UmmaOperand cB = {nullptr, nullptr}) {
+                          UmmaOperand cA = {nullptr, nullptr, nullptr}, UmmaOperand cB = {nullptr, nullptr, nullptr}) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Mp = umma_pad(M, kUmmaM), Np = umma_pad(Nc, kUmmaNT), Kp = umma_pad(Kd, kUmmaK);
   const int nmt = Mp / kUmmaM, nnt = Np / kUmmaNT, nkc = Kp / kUmmaK;
@@ -304,8 +324,8 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
   // earlier generic writes of the staging area (other products) before the
   // copies of this one
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  const __nv_bfloat16* PA = cA.planes;
-  const __nv_bfloat16* PB = cB.planes;
+  const CUtensorMap* tmA = cA.planes ? cA.tm : U.tmA;
+  const CUtensorMap* tmB = cB.planes ? cB.tm : U.tmB;
   const int* expA = cA.planes ? cA.ex : expA_s;
   const int* expB = cB.planes ? cB.ex : expB_s;
   if (!cA.planes) umma_row_exponents<TA>(M, Kd, A, lda, Mp, expA_s);
@@ -313,12 +333,10 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
   __syncthreads();
   if (!cA.planes) {
     umma_planes<TA>(M, Kd, A, lda, Mp, Kp, kUmmaM, expA_s, planes);
-    PA = planes;
   }
   if (!cB.planes) {
-    __nv_bfloat16* pb = planes + (size_t)kUmmaDig * Mp * Kp;
+    __nv_bfloat16* pb = planes + U.boff;
     umma_planes<!TB>(Nc, Kd, B, ldb, Np, Kp, kUmmaNT, expB_s, pb);
-    PB = pb;
   }
   // the planes are read by the bulk copies (async proxy)
   asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -377,10 +395,8 @@ __device__ void gemm_umma(int M, int Nc, int Kd, const dd* __restrict__ A, int l
     const int tile = g / nkc, kc = g - tile * nkc, mt = tile / nnt, nt = tile - mt * nnt;
     mbar_expect_tx(bar_full + st, kUmmaStageBytes);
     unsigned char* dst = umma_stage(U, st);
-    bulk_copy_g2s(dst, PA + ((size_t)mt * nkc + kc) * kUmmaDig * kUmmaM * kUmmaK, kUmmaDig * kUmmaBlockA,
-                  bar_full + st);
-    bulk_copy_g2s(dst + kUmmaDig * kUmmaBlockA, PB + ((size_t)nt * nkc + kc) * kUmmaDig * kUmmaNT * kUmmaK,
-                  kUmmaDig * kUmmaBlockB, bar_full + st);
+    tma_load_block(dst, tmA, mt * nkc + kc, bar_full + st);
+    tma_load_block(dst + kUmmaDig * kUmmaBlockA, tmB, nt * nkc + kc, bar_full + st);
     ++cpy_n[st];
   };
   if (tid == 0)
