@@ -1,7 +1,8 @@
 """Parity at the benchmark's full sizes, in the launch configurations bench.py times.
 
 * 256 chains of the square 8x8 / 12x12 workload (one launch per sweep, delayed
-  rank 16, mixed and FP64 paths): after one sweep of the whole batch, one chain of
+  rank 16; the tensor-core path as the bench times it, the float-pair SIMT path
+  and FP64): after one sweep of the whole batch, one chain of
   each (N, beta) class is replayed by the FP64 oracle from the same initial fields
   and seed.  Fields must agree bit for bit and G(0) to the path's tolerance (1e-10
   FP64, 1e-7 float pairs: the reduced-precision bar is 1e-6).
@@ -27,7 +28,7 @@ from paper_1704_00131_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "mixed": 1e-7}
+TOL = {"fp64": 1e-10, "mixed": 1e-7, "mixed_tc": 1e-7}
 
 
 @pytest.fixture(scope="module")
@@ -40,10 +41,13 @@ def dq():
     return dqmc
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed_tc", "mixed", "fp64"])
 def test_256_chain_workload_sampled_chains_follow_the_oracle(dq, orc, precision):
     wl = W.config_c3()
-    ens = dq.Ensemble(wl.models, wl.chain_model, precision=precision, delay_k=16, seed=W.BASE_SEED)
+    # mixed_tc as the bench runs it: the split products on the tensor cores at
+    # N = 64 and N = 144 (tc_min_sites = 1, the autotuner's choice)
+    opts = {"tc_min_sites": 1} if precision == "mixed_tc" else {}
+    ens = dq.Ensemble(wl.models, wl.chain_model, precision=precision, delay_k=16, seed=W.BASE_SEED, **opts)
     f0, _ = ens.get_fields()
     st = ens.sweep(1)
     assert st["proposals"] == wl.proposals_per_sweep()
