@@ -125,6 +125,23 @@ dqmc_status dqmc_su2_greens(dqmc_su2_ctx* ctx, int32_t chain, int32_t fresh, dou
  * [n_chains].  Host buffers. */
 dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas, int32_t reset);
 
+/* Equal-time correlation functions of every chain's current configuration from
+ * its working G(0) (the paper's SpinZ, Den, SpinXY and Green observables of
+ * Sec. 6, collected per class of site pairs as Obser_Latt collects them per
+ * displacement).  Both colors share G; with X_xy = (delta_xy - G_yx) G_xy and
+ * rho_x = 2 (1 - G_xx), per configuration
+ *     <S^z_x S^z_y> = X_xy / 2,  <n_x n_y> = rho_x rho_y + 2 X_xy,
+ *     <S^+_x S^-_y> = X_xy,      sum_s <c^+_xs c_ys> = 2 (delta_xy - G_yx).
+ *     pair_class  host, per model [n_sites][n_sites] int32 (models concatenated):
+ *                 class of (x, y) in [0, n_class[m]), or -1 to skip it
+ *     n_class     host [n_models], each >= 1
+ * Outputs (host): out [n_chains][max n_class][4][2]: (re, im) of the sums over
+ * each class's pairs (unweighted; rows beyond the chain's model's n_class are
+ * 0); phase [n_chains][2]: the chain's phase P (reweight by sign(Re P) P / Re P).
+ * The chains are left as they are.  DQMC_EINVAL for a class out of range. */
+dqmc_status dqmc_su2_measure_corr(dqmc_su2_ctx* ctx, const int32_t* pair_class, const int32_t* n_class, double* out,
+                                  double* phase);
+
 /* Fields of every chain (packed [L_c][N_c + n_bonds_c] int8) and the sweep counter. */
 dqmc_status dqmc_su2_get_fields(dqmc_su2_ctx* ctx, int8_t* out, uint64_t* sweep_counter);
 /* Replace the fields and the sweep counter; the left chains, G(0) and the

@@ -953,6 +953,45 @@ __global__ void __launch_bounds__(kThreads) su2_fresh_kernel(Su2Dev* chains, int
   }
 }
 
+// Equal-time correlation functions of each chain's current configuration from
+// its working G(0) (the paper's SpinZ, Den, SpinXY and Green observables,
+// collected per pair class as Obser_Latt collects them per displacement).  Both
+// colors see the same G, so with X_xy = (delta_xy - G_yx) G_xy and
+// rho_x = 2 (1 - G_xx), Wick's theorem gives per configuration
+//   <S^z_x S^z_y> = X_xy / 2, <n_x n_y> = rho_x rho_y + 2 X_xy,
+//   <S^+_x S^-_y> = X_xy,     sum_s <c^+_xs c_ys> = 2 (delta_xy - G_yx).
+// One CTA per chain; thread c sums class c's pairs (CSR: pairs[off[c] ..
+// off[c+1]), each x N + y) in their listed order.  out: [n_chains][max_cls][4]
+// complex.
+__global__ void su2_corr_kernel(const Su2Dev* chains, int n_chains, const int* const* off, const int* const* pairs,
+                                const int* ncls, int max_cls, double2* out) {
+  const int c = blockIdx.x;
+  if (c >= n_chains) return;
+  const Su2Dev& C = chains[c];
+  const int N = C.N, ld = C.ld, nc = ncls[c];
+  const int* o = off[c];
+  const int* pr = pairs[c];
+  for (int k = threadIdx.x; k < max_cls; k += blockDim.x) {
+    double2 v[4];
+    for (int q = 0; q < 4; ++q) v[q] = make_double2(0.0, 0.0);
+    if (k < nc)
+      for (int e = o[k]; e < o[k + 1]; ++e) {
+        const int x = pr[e] / N, y = pr[e] - x * N;
+        const double2 gyx = C.G[(size_t)y * ld + x], gxy = C.G[(size_t)x * ld + y];
+        const double2 gxx = C.G[(size_t)x * ld + x], gyy = C.G[(size_t)y * ld + y];
+        const double2 h = make_double2((x == y ? 1.0 : 0.0) - gyx.x, -gyx.y);
+        const double2 X = zmul(h, gxy);
+        const double2 rx = make_double2(2.0 * (1.0 - gxx.x), -2.0 * gxx.y);
+        const double2 ry = make_double2(2.0 * (1.0 - gyy.x), -2.0 * gyy.y);
+        v[0] = zadd(v[0], zscal(0.5, X));
+        v[1] = zadd(v[1], zadd(zmul(rx, ry), zscal(2.0, X)));
+        v[2] = zadd(v[2], X);
+        v[3] = zadd(v[3], zscal(2.0, h));
+      }
+    for (int q = 0; q < 4; ++q) out[((size_t)c * max_cls + k) * 4 + q] = v[q];
+  }
+}
+
 __global__ void su2_copy_green_kernel(Su2Dev* chains, int chain, double2* out) {
   const Su2Dev& C = chains[chain];
   const int N = C.N;
@@ -1030,6 +1069,12 @@ cudaError_t su2_launch_sweep(Su2Dev* chains, const Su2SweepParams& p, size_t sme
 
 cudaError_t su2_launch_copy_green(Su2Dev* chains, int chain, double2* out, cudaStream_t st) {
   su2_copy_green_kernel<<<16, kThreads, 0, st>>>(chains, chain, out);
+  return cudaGetLastError();
+}
+
+cudaError_t su2_launch_corr(const Su2Dev* chains, int n_chains, const int* const* off, const int* const* pairs,
+                            const int* ncls, int max_cls, double2* out, cudaStream_t st) {
+  su2_corr_kernel<<<n_chains, 128, 0, st>>>(chains, n_chains, off, pairs, ncls, max_cls, out);
   return cudaGetLastError();
 }
 

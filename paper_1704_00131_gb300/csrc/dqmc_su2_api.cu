@@ -342,6 +342,80 @@ dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, i
   return DQMC_OK;
 }
 
+dqmc_status dqmc_su2_measure_corr(dqmc_su2_ctx* ctx, const int32_t* pair_class, const int32_t* n_class, double* out,
+                                  double* phase) {
+  if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
+  if (!pair_class || !n_class || !out || !phase) return fail(ctx, DQMC_EINVAL, "null argument");
+  const int nm = (int)ctx->models.size(), nch = (int)ctx->chains_h.size();
+  // CSR lists of every model's pair classes (pairs in row-major order of (x, y))
+  std::vector<std::vector<int>> off(nm), prs(nm);
+  size_t cls_off = 0;
+  int max_cls = 1;
+  for (int m = 0; m < nm; ++m) {
+    const int N = ctx->models[m].n_sites, nc = n_class[m];
+    if (nc < 1) return fail(ctx, DQMC_EINVAL, "model %d: n_class must be >= 1", m);
+    max_cls = std::max(max_cls, nc);
+    const int32_t* cls = pair_class + cls_off;
+    cls_off += (size_t)N * N;
+    std::vector<int> cnt(nc + 1, 0);
+    for (int e = 0; e < N * N; ++e) {
+      if (cls[e] < -1 || cls[e] >= nc) return fail(ctx, DQMC_EINVAL, "model %d: pair class %d out of range", m, cls[e]);
+      if (cls[e] >= 0) ++cnt[cls[e] + 1];
+    }
+    for (int k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
+    off[m] = cnt;
+    prs[m].assign((size_t)cnt[nc] + 1, 0);
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int e = 0; e < N * N; ++e)
+      if (cls[e] >= 0) prs[m][fill[cls[e]]++] = e;
+  }
+  std::vector<void*> tmp;
+  auto release = [&]() { for (void* q : tmp) cudaFree(q); };
+  auto up = [&](const void* src, size_t bytes) -> void* {
+    void* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return nullptr;
+    tmp.push_back(d);
+    if (cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    return d;
+  };
+  std::vector<const int*> offd(nm), prd(nm), coff(nch), cpr(nch);
+  std::vector<int> cnc(nch);
+  for (int m = 0; m < nm; ++m) {
+    offd[m] = static_cast<const int*>(up(off[m].data(), off[m].size() * sizeof(int)));
+    prd[m] = static_cast<const int*>(up(prs[m].data(), prs[m].size() * sizeof(int)));
+    if (!offd[m] || !prd[m]) { release(); return fail(ctx, DQMC_ENOMEM, "class lists"); }
+  }
+  for (int c = 0; c < nch; ++c) {
+    const int m = ctx->chain_model[c];
+    coff[c] = offd[m];
+    cpr[c] = prd[m];
+    cnc[c] = n_class[m];
+  }
+  const int* const* coff_d = static_cast<const int* const*>(up(coff.data(), nch * sizeof(int*)));
+  const int* const* cpr_d = static_cast<const int* const*>(up(cpr.data(), nch * sizeof(int*)));
+  const int* cnc_d = static_cast<const int*>(up(cnc.data(), nch * sizeof(int)));
+  const size_t nout = (size_t)nch * max_cls * 4;
+  double2* out_d = nullptr;
+  if (!coff_d || !cpr_d || !cnc_d || cudaMalloc((void**)&out_d, nout * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(ctx, DQMC_ENOMEM, "correlation buffers");
+  }
+  tmp.push_back(out_d);
+  dqmc_status st = DQMC_OK;
+  cudaError_t e = dqmc::su2_launch_corr(ctx->chains_d, nch, coff_d, cpr_d, cnc_d, max_cls, out_d, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, out_d, nout * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) st = fail(ctx, DQMC_ECUDA, "correlations: %s", cudaGetErrorString(e));
+  if (!st) st = download(ctx);
+  release();
+  if (st) return st;
+  for (int c = 0; c < nch; ++c) {
+    phase[2 * c] = ctx->chains_h[c].P.x;
+    phase[2 * c + 1] = ctx->chains_h[c].P.y;
+  }
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_su2_get_fields(dqmc_su2_ctx* ctx, int8_t* out, uint64_t* sweep_counter) {
   if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
   if (out) {

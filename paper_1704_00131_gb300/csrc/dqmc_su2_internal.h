@@ -83,5 +83,9 @@ cudaError_t su2_launch_fresh(Su2Dev* chains, int n_chains, int mode, int only, d
 cudaError_t su2_launch_sweep(Su2Dev* chains, const Su2SweepParams& p, size_t smem, cudaStream_t st);
 cudaError_t su2_launch_copy_green(Su2Dev* chains, int chain, double2* out, cudaStream_t st);
 cudaError_t su2_launch_reset_stats(Su2Dev* chains, int n_chains, int clear_meas, cudaStream_t st);
+// per chain: CSR lists of the pair classes (off[c], pairs[c]: device pointers),
+// ncls [n_chains]; out [n_chains][max_cls][4] complex
+cudaError_t su2_launch_corr(const Su2Dev* chains, int n_chains, const int* const* off, const int* const* pairs,
+                            const int* ncls, int max_cls, double2* out, cudaStream_t st);
 
 }  // namespace dqmc

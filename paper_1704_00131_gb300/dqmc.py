@@ -24,7 +24,8 @@ PREC = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tc": 3}
 EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_greens_tau", "dqmc_measure", "dqmc_measure_tau",
             "dqmc_measure_tau_corr", "dqmc_measure_corr", "dqmc_logdet_backward", "dqmc_energy_backward", "dqmc_get_fields",
             "dqmc_set_fields", "dqmc_green_fresh_noalloc", "dqmc_last_error", "dqmc_destroy",
-            "dqmc_su2_init", "dqmc_su2_sweep", "dqmc_su2_greens", "dqmc_su2_measure", "dqmc_su2_get_fields",
+            "dqmc_su2_init", "dqmc_su2_sweep", "dqmc_su2_greens", "dqmc_su2_measure", "dqmc_su2_measure_corr",
+            "dqmc_su2_get_fields",
             "dqmc_su2_set_fields", "dqmc_su2_last_error", "dqmc_su2_destroy"]
 
 
@@ -141,6 +142,8 @@ def load() -> ctypes.CDLL:
     L.dqmc_su2_greens.restype = ctypes.c_int
     L.dqmc_su2_measure.argtypes = [vp, vp, vp, vp, i32]
     L.dqmc_su2_measure.restype = ctypes.c_int
+    L.dqmc_su2_measure_corr.argtypes = [vp, vp, vp, vp, vp]
+    L.dqmc_su2_measure_corr.restype = ctypes.c_int
     L.dqmc_su2_get_fields.argtypes = [vp, vp, vp]
     L.dqmc_su2_get_fields.restype = ctypes.c_int
     L.dqmc_su2_set_fields.argtypes = [vp, vp, u64]
@@ -534,6 +537,17 @@ class Su2Ensemble:
         nm = np.zeros(self.n_chains, dtype=np.int64)
         self._check(self._lib.dqmc_su2_measure(self._h, _p(out), _p(sg), _p(nm), int(reset)))
         return out[..., 0] + 1j * out[..., 1], sg, nm
+
+    def measure_corr(self, pair_class, n_class):
+        """Equal-time correlations per pair class of every chain's current G(0):
+        (complex [n_chains, max n_class, 4] sums of S^z S^z, n n, S^+ S^-, c^+ c;
+        complex phase P per chain).  pair_class: one [N, N] int array per model."""
+        cls = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32).ravel() for c in pair_class]))
+        nc = np.ascontiguousarray(n_class, dtype=np.int32)
+        out = np.zeros((self.n_chains, int(nc.max()), 4, 2))
+        ph = np.zeros((self.n_chains, 2))
+        self._check(self._lib.dqmc_su2_measure_corr(self._h, _p(cls), _p(nc), _p(out), _p(ph)))
+        return out[..., 0] + 1j * out[..., 1], ph[:, 0] + 1j * ph[:, 1]
 
     def get_fields(self):
         total = sum(self.model_of(c).L * self.model_of(c).MV for c in range(self.n_chains))

@@ -298,3 +298,39 @@ def test_bond_model_sampler_matches_trotter_product(dq, orc, mu):
         mean, err = A.jackknife(obs[:, q].real / n, sg / n)
         assert abs(mean - ref) < 4 * err, (q, mean, err, ref)
         assert err < 0.05 * abs(ref)
+
+
+def test_su2_correlations_match_oracle(dq, orc):
+    """Equal-time correlations per translation class (S^z S^z, n n, S^+ S^-,
+    c^+ c) from the working G(0) of chains of two lattices in one context,
+    against the oracle's correlations on its own stable G(0) for the same
+    fields; after a sweep, against the oracle's formula applied to the GPU's
+    working G."""
+    ms = [dq.Su2Model(W.square_lattice(4, 4, t=1.0, mu=0.3), U=4.0, dtau=0.1, L=40, n_wrap=10),
+          dq.Su2Model(W.square_lattice(3, 3, t=1.0), U=3.0, dtau=0.1, L=20, n_wrap=5)]
+    cl = [W.translation_classes_square(4, 4), W.translation_classes_square(3, 3)]
+    chain_model = [0, 1, 0]
+    rng = np.random.default_rng(8)
+    fields = [rng.choice([-2, -1, 1, 2], size=(ms[m].L, ms[m].N)).astype(np.int8) for m in chain_model]
+    ens = dq.Su2Ensemble(ms, chain_model, fields=fields, seed=3)
+    out, P = ens.measure_corr([c[0] for c in cl], [c[1] for c in cl])
+    for c, m in enumerate(chain_model):
+        mm, (cls, ncls, _) = ms[m], cl[m]
+        Go, _, _ = orc.su2_green_udv(mm.hopping, mm.dtau, mm.U, mm.n_wrap, fields[c], 0)
+        ref = orc.su2_correlations(Go, cls, ncls)
+        assert np.abs(out[c, :ncls] - ref).max() < 1e-9 * max(1.0, np.abs(ref).max()), c
+        assert np.all(out[c, ncls:] == 0)
+        _, _, _, Pc = ens.greens(c)
+        assert P[c] == Pc
+    ens.sweep(1)
+    out, _ = ens.measure_corr([c[0] for c in cl], [c[1] for c in cl])
+    for c, m in enumerate(chain_model):
+        G, _, _, _ = ens.greens(c)
+        ref = orc.su2_correlations(G, cl[m][0], cl[m][1])
+        assert np.abs(out[c, :cl[m][1]] - ref).max() < 1e-12 * max(1.0, np.abs(ref).max()), c
+    with pytest.raises(dq.DqmcError) as e:
+        bad = cl[0][0].copy()
+        bad[1] = cl[0][1]                   # class index out of range
+        ens.measure_corr([bad, cl[1][0]], [cl[0][1], cl[1][1]])
+    assert e.value.status == dq.DQMC_EINVAL
+    ens.close()
