@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 path")
     ap.add_argument("--peaks", action="store_true", help="measure the matmul peaks used as roofline denominators")
     ap.add_argument("--no-oracle-check", action="store_true", help="skip the max|dG| check against the oracle")
+    ap.add_argument("--gradients", action="store_true",
+                    help="time the log-det and energy adjoints of the 64-configuration 8x8, beta = 4 workload")
     ap.add_argument("--paper-example", action="store_true",
                     help="precision monitors of the paper's 4x4, U=4, beta=10 spin-z example instead of the bench")
     ap.add_argument("--run-option", action="append", default=[], metavar="KEY=VALUE",
@@ -599,8 +601,60 @@ def paper_example(args):
     print(json.dumps(out), flush=True)
 
 
+def gradients(args):
+    """The differentiation workload: d log|det(1+B(beta,0))| / d(K, U) and
+    d Ener / d(K, U) on square 8x8 (N = 64), beta = 4 (L = 40), U = 4, for 64
+    seeded field configurations, FP64 (the adjoint of Sec. 2.3's B chain,
+    checkpointed at the stabilisation points).  Prints one JSON line: configurations
+    per second for both adjoints together (device time, CUDA events, after
+    warm-up), the gradients of one configuration against the FP64 oracle, and the
+    oracle's own time for that configuration on one host core."""
+    import torch
+
+    import oracle
+    from paper_1704_00131_gb300 import build_ext, dqmc
+    build_ext.build()
+    torch.cuda.set_device(0)
+    m = W.ModelSpec(W.square_lattice(8, 8), U=4.0, dtau=0.1, L=40, n_wrap=10, name="square8x8_U4_b4")
+    f = np.stack([W.random_fields(1, m.L, m.n_vertices, seed=s) for s in range(1, 65)])
+    ens = dqmc.Ensemble([m], [0], precision="fp64")
+    for _ in range(max(1, args.warmup)):
+        ens.logdet_backward(0, f[:8])
+        ens.energy_backward(0, f[:8])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        ld, gKl, gUl = ens.logdet_backward(0, f)
+        e, gKe, gUe = ens.energy_backward(0, f)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    om = oracle.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+    t0 = time.perf_counter()
+    ldo, _, gKlo, gUlo = oracle.logdet_grad(om, f[0])
+    eo, gKeo, gUeo = oracle.energy_grad(om, f[0])
+    t_orc = time.perf_counter() - t0
+    ens.close()
+    dev = {"logdet": float(np.max(np.abs(ld[0] - ldo) / np.maximum(1.0, np.abs(ldo)))),
+           "dlogdet_dK": float(np.max(np.abs(gKl[0] - gKlo))), "dlogdet_dU": float(np.max(np.abs(gUl[0] - gUlo))),
+           "ener": float(np.max(np.abs(e[0] - eo))), "dener_dK": float(np.max(np.abs(gKe[0] - gKeo))),
+           "dener_dU": float(abs(gUe[0] - gUeo))}
+    print(json.dumps({"metric": "gradient configurations/s (log-det and energy adjoints together)",
+                      "value": 64.0 / (ms * 1e-3), "unit": "configurations/s", "ms_per_step": ms,
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": m.name + " x 64 configurations", "n_wrap": m.n_wrap},
+                      "max_abs_dev_vs_oracle_config0": dev,
+                      "cpu_baseline": {"value": 1.0 / t_orc, "unit": "configurations/s", "cores": 1,
+                                       "kind": "oracle", "sample": "both adjoints of configuration 0"}}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.gradients:
+        gradients(args)
+        return
     if args.peaks:
         measure_peaks()
         return
