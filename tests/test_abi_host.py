@@ -71,6 +71,35 @@ def test_invalid_options_rejected_before_any_device_work(lib):
         assert e.value.status == dqmc.DQMC_EINVAL, kw
 
 
+def test_su2_context_has_no_cpu_fallback_and_validates_on_the_host(lib):
+    """The complex family: without a device the context fails with DQMC_ECUDA (no
+    CPU path); invalid models, bonds and J pairs are rejected with DQMC_EINVAL
+    before any device work."""
+    import torch
+    K = W.chain_lattice(3)
+    good = dqmc.Su2Model(K, U=2.0, dtau=0.1, L=4, n_wrap=2, bonds=[(0, 1), (1, 2)], xi=0.5, h=1.0, pairs=[(0, 1)])
+    if not torch.cuda.is_available():
+        with pytest.raises(dqmc.DqmcError) as e:
+            dqmc.Su2Ensemble([good], [0])
+        assert e.value.status == dqmc.DQMC_ECUDA
+    bad = [dict(L=5), dict(bonds=[(0, 0)], h=1.0), dict(bonds=[(0, 3)], h=1.0), dict(bonds=[(0, 1)], h=0.0),
+           dict(bonds=[(0, 1)], h=1.0, pairs=[(0, 0)]), dict(pairs=[(0, 1)])]
+    for kw in bad:
+        args = dict(U=2.0, dtau=0.1, L=4, n_wrap=2, xi=0.5)
+        args.update(kw)
+        with pytest.raises(dqmc.DqmcError) as e:
+            dqmc.Su2Ensemble([dqmc.Su2Model(K, **args)], [0])
+        assert e.value.status == dqmc.DQMC_EINVAL, kw
+
+
+def test_svd_stabilisation_needs_the_fp64_path(lib):
+    m = W.ModelSpec(W.square_lattice(2, 2), U=2.0, dtau=0.1, L=4, n_wrap=2)
+    for prec in ("fp32", "mixed", "mixed_tc"):
+        with pytest.raises(dqmc.DqmcError) as e:
+            dqmc.Ensemble([m], [0], precision=prec, stab_svd=True)
+        assert e.value.status == dqmc.DQMC_EINVAL, prec
+
+
 def test_binding_lists_every_exported_entry_point(lib):
     assert set(dqmc.EXPORTED) == declared_symbols()
 
