@@ -1,7 +1,7 @@
 """Autotuner of the sweep's launch parameters on this GPU.
 
 For a batch of chains (models and the chain -> model map) it picks, in two
-rounds:
+passes:
 1. the product kernel family of the reduced-precision path: float-pair SIMT
    register tiles ("mixed") or exact-split BF16 products on the tensor cores
    ("mixed_tc"; the FP64 path has one family, "fp64"), together with the rank k
@@ -52,7 +52,7 @@ class Choice:
 
 
 def option_candidates(precision: str) -> list:
-    """Tile options tried for the winner of the first round."""
+    """Tile options tried for the winner of the first pass."""
     if precision not in ("mixed", "mixed_tc"):
         return []
     out = [{"dd_tile": t} for t in DD_TILES]

@@ -58,7 +58,7 @@ def test_tune_picks_minimum_and_uses_cache(tmp_path):
 
     cache = AT.Cache(str(tmp_path / "at.json"))
     ch = AT.tune(wl.models, wl.chain_model, "mixed", (8, 16), cache=cache, timer=fake, device="fake-gpu")
-    # round 1: family x rank; round 2: the winner's tile options
+    # first pass: family x rank; second pass: the winner's launch options
     assert (ch.precision, ch.delay_k, ch.ms, ch.cached, ch.options) == ("mixed", 16, 3.5, False, {"dd_tile": 3})
     assert len(calls) == 6 and len(ch.timings) == 6
     again = AT.tune(wl.models, wl.chain_model, "mixed", (8, 16), cache=cache, timer=fake, device="fake-gpu")
