@@ -114,6 +114,8 @@ def lib():
                                                       ctypes.c_int, vp, vp, ctypes.c_int, vp, vp, vp]
         _lib.orc_su2_correlations.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int, vp]
         _lib.orc_su2_green_udv.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
+        _lib.orc_su2_green_displaced.argtypes = [ctypes.c_int, vp, d, d, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                                                 vp, vp]
         del i32
     return _lib
 
@@ -383,6 +385,20 @@ def su2_correlations(G: np.ndarray, pair_class: np.ndarray, n_class: int) -> np.
     out = np.zeros((n_class, 4, 2))
     _check(lib().orc_su2_correlations(N, _ptr(Gi), _ptr(cls), int(n_class), _ptr(out)), "su2_correlations")
     return out[..., 0] + 1j * out[..., 1]
+
+
+def su2_green_displaced(K: np.ndarray, dtau: float, U: float, n_wrap: int, fields: np.ndarray, tau: int):
+    """G(tau,0) and G(0,tau) (complex [N, N]) of one color of the SU(2)
+    decoupling through the complex UDV chains."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    N = K.shape[0]
+    f = np.ascontiguousarray(fields, dtype=np.int8)
+    L = f.size // N
+    Gt0 = np.zeros((N, N, 2))
+    G0t = np.zeros((N, N, 2))
+    _check(lib().orc_su2_green_displaced(N, _ptr(K), float(dtau), float(U), L, int(n_wrap), _ptr(f), int(tau),
+                                         _ptr(Gt0), _ptr(G0t)), "su2_green_displaced")
+    return Gt0[..., 0] + 1j * Gt0[..., 1], G0t[..., 0] + 1j * G0t[..., 1]
 
 
 def su2_green_udv(K: np.ndarray, dtau: float, U: float, n_wrap: int, fields: np.ndarray, tau: int = 0):

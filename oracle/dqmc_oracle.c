@@ -1817,6 +1817,109 @@ int orc_su2_green_udv(int N, const double* K, double dtau, double U, int L, int 
   return st;
 }
 
+/* Time-displaced Green functions of the SU(2) decoupling on fixed fields (one
+ * color; the definitions of the real case with complex B):
+ *   G(tau,0) = B(tau,0) G(0) = (B(tau,0)^-1 + B(beta,tau))^-1,
+ *   G(0,tau) = -(1 - G(0)) B(tau,0)^-1,
+ * from the right chain R = B(tau,0) and the left chain Lf = B(beta,tau)^H with
+ * the middle matrix of cudv_green:
+ *   G(tau,0) = Q_L Db_L^-1 Mid^-1 Ds_R T_R,
+ *   G(0,tau) = -T_L^H Ds_L Mid^-1 Db_R^-1 Q_R^H.
+ * Gt0, G0t: [N][N] complex (re, im interleaved). */
+static int cudv_displaced(int N, const cudv_t* R, const cudv_t* Lf, double* Gt0, double* G0t) {
+  const size_t NN = (size_t)N * N;
+  double complex* Mid = (double complex*)calloc(NN, sizeof(double complex));
+  double complex* MI = (double complex*)calloc(NN, sizeof(double complex));
+  double complex* X = (double complex*)calloc(NN, sizeof(double complex));
+  double *dbR = dalloc(N), *dsR = dalloc(N), *dbL = dalloc(N), *dsL = dalloc(N);
+  for (int i = 0; i < N; ++i) {
+    dbR[i] = R->D[i] > 1.0 ? R->D[i] : 1.0;  dsR[i] = R->D[i] > 1.0 ? 1.0 : R->D[i];
+    dbL[i] = Lf->D[i] > 1.0 ? Lf->D[i] : 1.0; dsL[i] = Lf->D[i] > 1.0 ? 1.0 : Lf->D[i];
+  }
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double complex qq = 0.0, tt = 0.0;
+      for (int k = 0; k < N; ++k) {
+        qq += conj(R->Q[(size_t)k * N + i]) * Lf->Q[(size_t)k * N + j];
+        tt += R->T[(size_t)i * N + k] * conj(Lf->T[(size_t)j * N + k]);
+      }
+      Mid[(size_t)i * N + j] = qq / (dbR[i] * dbL[j]) + dsR[i] * tt * dsL[j];
+      MI[(size_t)i * N + j] = (i == j) ? 1.0 : 0.0;
+    }
+  /* Gauss-Jordan with partial pivoting: MI <- Mid^-1 */
+  int st = ORC_OK;
+  for (int k = 0; k < N && !st; ++k) {
+    int p = k;
+    for (int i = k + 1; i < N; ++i)
+      if (cabs(Mid[(size_t)i * N + k]) > cabs(Mid[(size_t)p * N + k])) p = i;
+    if (cabs(Mid[(size_t)p * N + k]) == 0.0) { st = ORC_ESING; break; }
+    for (int j = 0; j < N; ++j) {
+      double complex t = Mid[(size_t)k * N + j]; Mid[(size_t)k * N + j] = Mid[(size_t)p * N + j]; Mid[(size_t)p * N + j] = t;
+      t = MI[(size_t)k * N + j]; MI[(size_t)k * N + j] = MI[(size_t)p * N + j]; MI[(size_t)p * N + j] = t;
+    }
+    const double complex d = Mid[(size_t)k * N + k];
+    for (int j = 0; j < N; ++j) { Mid[(size_t)k * N + j] /= d; MI[(size_t)k * N + j] /= d; }
+    for (int i = 0; i < N; ++i) {
+      if (i == k) continue;
+      const double complex f = Mid[(size_t)i * N + k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < N; ++j) { Mid[(size_t)i * N + j] -= f * Mid[(size_t)k * N + j]; MI[(size_t)i * N + j] -= f * MI[(size_t)k * N + j]; }
+    }
+  }
+  if (!st) {
+    /* G(tau,0) = Q_L (Db_L^-1 MI Ds_R) T_R */
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) X[(size_t)i * N + j] = MI[(size_t)i * N + j] / dbL[i] * dsR[j];
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        double complex acc = 0.0;
+        for (int k = 0; k < N; ++k) {
+          double complex qx = 0.0;
+          for (int l = 0; l < N; ++l) qx += Lf->Q[(size_t)i * N + l] * X[(size_t)l * N + k];
+          acc += qx * R->T[(size_t)k * N + j];
+        }
+        Gt0[2 * ((size_t)i * N + j)] = creal(acc);
+        Gt0[2 * ((size_t)i * N + j) + 1] = cimag(acc);
+      }
+    /* G(0,tau) = -T_L^H (Ds_L MI Db_R^-1) Q_R^H */
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) X[(size_t)i * N + j] = dsL[i] * MI[(size_t)i * N + j] / dbR[j];
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        double complex acc = 0.0;
+        for (int k = 0; k < N; ++k) {
+          double complex tx = 0.0;
+          for (int l = 0; l < N; ++l) tx += conj(Lf->T[(size_t)l * N + i]) * X[(size_t)l * N + k];
+          acc += tx * conj(R->Q[(size_t)j * N + k]);
+        }
+        G0t[2 * ((size_t)i * N + j)] = -creal(acc);
+        G0t[2 * ((size_t)i * N + j) + 1] = -cimag(acc);
+      }
+  }
+  free(Mid); free(MI); free(X); free(dbR); free(dsR); free(dbL); free(dsL);
+  return st;
+}
+
+/* G(tau,0) and G(0,tau) of one color of the SU(2) decoupling through the
+ * complex UDV chains (chunks of n_wrap slices, a partial chunk closing each
+ * chain).  Gt0, G0t: [N][N] complex (re, im). */
+int orc_su2_green_displaced(int N, const double* K, double dtau, double U, int L, int n_wrap, const int8_t* fields,
+                            int tau, double* Gt0, double* G0t) {
+  if (N < 1 || L < 1 || n_wrap < 1 || tau < 0 || tau > L || !(dtau > 0.0) || !(U >= 0.0)) return ORC_EINVAL;
+  const double g = sqrt(0.5 * dtau * U);
+  double* E = dalloc((size_t)N * N);
+  orc_expm_sym(N, K, -dtau, E);
+  cudv_t R, Lf;
+  cudv_alloc(N, &R);
+  cudv_alloc(N, &Lf);
+  for (int t = 0; t < tau; t += n_wrap) cudv_step(N, E, g, fields, t, (t + n_wrap < tau) ? t + n_wrap : tau, 0, &R);
+  for (int t = L; t > tau; t -= n_wrap) cudv_step(N, E, g, fields, (t - n_wrap > tau) ? t - n_wrap : tau, t, 1, &Lf);
+  const int st = cudv_displaced(N, &R, &Lf, Gt0, G0t);
+  free(E);
+  cudv_free(&R); cudv_free(&Lf);
+  return st;
+}
+
 /* ---- SVD stabilisation (the compile-time alternative of Sec. 5, -DSTAB1) -- */
 /* The same UDV chain with the decomposition M = X D = U S V^T by one-sided     */
 /* Jacobi rotations (Hestenes): column pairs of M are rotated until mutually    */

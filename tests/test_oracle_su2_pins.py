@@ -157,3 +157,62 @@ def test_su2_correlations_enumeration_equals_fock_trace(orc, case):
     got = acc / Z
     assert np.abs(got - ref).max() < 1e-10 * max(1.0, np.abs(ref).max())
     assert np.abs(ref.imag).max() < 1e-12 and np.abs(got.imag).max() < 1e-10
+
+
+def _su2_B(K, dtau, U, fields, orc):
+    """B_t = exp(-dtau K) exp(i g eta(l_t)) of every slice, plain numpy."""
+    w, V = np.linalg.eigh(K)
+    E = (V * np.exp(-dtau * w)) @ V.T
+    g = np.sqrt(0.5 * dtau * U)
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    return [E * np.exp(1j * g * np.array([eta[int(l)] for l in f]))[None, :] for f in fields]
+
+
+def test_su2_displaced_green_matches_the_definition(orc):
+    """orc_su2_green_displaced (complex UDV chains, scale separation) against the
+    definitions G(tau,0) = B(tau,0) G(0) and G(0,tau) = -(1 - G(0)) B(tau,0)^-1
+    with plain products and a dense inverse, where both hold (beta = 2), for
+    several chunk lengths, at tau = 0 (G(0), -(1 - G(0))) and beyond."""
+    rng = np.random.default_rng(3)
+    K = W.square_lattice(4, 4, t=1.0, mu=0.2)
+    dtau, U, L = 0.1, 4.0, 20
+    f = rng.choice([-2, -1, 1, 2], size=(L, 16)).astype(np.int8)
+    Bs = _su2_B(K, dtau, U, f, orc)
+    I = np.eye(16)
+    Bb = I.astype(complex)
+    for B in Bs:
+        Bb = B @ Bb
+    G0 = np.linalg.inv(I + Bb)
+    for nw in (1, 5, 20):
+        for tau in (0, 3, 7, 20):
+            Bt = I.astype(complex)
+            for B in Bs[:tau]:
+                Bt = B @ Bt
+            Gt0, G0t = orc.su2_green_displaced(K, dtau, U, nw, f, tau)
+            assert np.abs(Gt0 - Bt @ G0).max() < 1e-10, (nw, tau)
+            assert np.abs(G0t + (I - G0) @ np.linalg.inv(Bt)).max() < 1e-10, (nw, tau)
+
+
+def test_su2_displaced_green_free_limit(orc):
+    """U = 0: G(tau,0) = e^{-tau dtau K} (1 + e^{-beta K})^-1 and
+    G(0,tau) = -(1 - G(0)) e^{tau dtau K}, in K's eigenbasis."""
+    K = W.square_lattice(4, 4, t=1.0, mu=-0.3)
+    dtau, L = 0.1, 60
+    w, V = np.linalg.eigh(K)
+    f = np.ones((L, 16), dtype=np.int8)
+    for tau in (0, 13, 60):
+        Gt0, G0t = orc.su2_green_displaced(K, dtau, 0.0, 10, f, tau)
+        nk = 1.0 / (1.0 + np.exp(-L * dtau * w))
+        hk = 1.0 / (1.0 + np.exp(L * dtau * w))      # 1 - n_k without cancellation
+        assert np.abs(Gt0 - (V * (np.exp(-tau * dtau * w) * nk)) @ V.T).max() < 1e-12
+        assert np.abs(G0t + (V * (hk * np.exp(tau * dtau * w))) @ V.T).max() < 1e-12
+
+
+def test_su2_displaced_green_is_independent_of_n_wrap_at_large_beta(orc):
+    rng = np.random.default_rng(4)
+    K = W.square_lattice(4, 4, t=1.0, mu=0.2)
+    f = rng.choice([-2, -1, 1, 2], size=(100, 16)).astype(np.int8)     # beta = 10
+    for tau in (30, 57):
+        a0, b0 = orc.su2_green_displaced(K, 0.1, 4.0, 5, f, tau)
+        a1, b1 = orc.su2_green_displaced(K, 0.1, 4.0, 10, f, tau)
+        assert np.abs(a0 - a1).max() < 1e-10 and np.abs(b0 - b1).max() < 1e-10, tau
