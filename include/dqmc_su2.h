@@ -125,6 +125,23 @@ dqmc_status dqmc_su2_greens(dqmc_su2_ctx* ctx, int32_t chain, int32_t fresh, dou
  * [n_chains].  Host buffers. */
 dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas, int32_t reset);
 
+/* Time-displaced measurement of every chain's current configuration (the tau_m
+ * step, Sec. 2.4; the time-displaced observables of Sec. 5.2): from the stable
+ * G(0), G(tau,0) = B_tau G(tau-1,0) and G(0,tau) = G(0,tau-1) B_tau^-1 for
+ * tau = 1..n_tau, both recomputed from the UDV chains at every multiple of
+ * n_wrap (G(tau,0) = (B(tau,0)^-1 + B(beta,tau))^-1, G(0,tau) =
+ * -(1 - G(0)) B(tau,0)^-1).  out (host) [n_chains][n_tau + 1][2]: (re, im) of
+ * sum_x G(tau,0)_xx; prec_tau (host, nullable) [2]: "Precision tau", the mean
+ * over chains and recompute points of the mean |wrapped - recomputed| entry
+ * of G(tau,0) and G(0,tau), and the maximum.  0 <= n_tau <= L of every chain.
+ * The chains are left as they are. */
+dqmc_status dqmc_su2_measure_tau(dqmc_su2_ctx* ctx, int32_t n_tau, double* out, double* prec_tau);
+
+/* G(tau,0) and G(0,tau) of one chain ([N][N] complex each, host), reached as
+ * dqmc_su2_measure_tau reaches them (wrapped from the last recompute point at
+ * or below tau). */
+dqmc_status dqmc_su2_greens_displaced(dqmc_su2_ctx* ctx, int32_t chain, int32_t tau, double* out_t0, double* out_0t);
+
 /* Equal-time correlation functions of every chain's current configuration from
  * its working G(0) (the paper's SpinZ, Den, SpinXY and Green observables of
  * Sec. 6, collected per class of site pairs as Obser_Latt collects them per

@@ -547,6 +547,85 @@ __device__ int z_green(const Su2Dev& C, ZUdv R, ZUdv Lf, double2* Gout, double& 
   return 0;
 }
 
+// Time-displaced Green functions from the right chain R = B(tau,0) and the
+// left chain Lf = B(beta,tau)^H, with the middle matrix of z_green:
+//   G(tau,0) = (B(tau,0)^-1 + B(beta,tau))^-1 = Q_L Db_L^-1 Mid^-1 Ds_R T_R,
+//   G(0,tau) = -(1 - G(0)) B(tau,0)^-1 = -T_L^H Ds_L Mid^-1 Db_R^-1 Q_R^H.
+// Mid^-1 by Gauss-Jordan with partial pivoting.  Returns 1 on a singular Mid.
+__device__ int z_displaced(const Su2Dev& C, ZUdv R, ZUdv Lf, double2* Gt0, double2* G0t, Sm& S) {
+  const int N = C.N, ld = C.ld, tid = threadIdx.x;
+  double *dbR = dvec(C, 4), *dsR = dvec(C, 5), *dbL = dvec(C, 6), *dsL = dvec(C, 7);
+  for (int i = tid; i < N; i += kThreads) {
+    dbR[i] = fmax(R.D[i], 1.0);
+    dsR[i] = fmin(R.D[i], 1.0);
+    dbL[i] = fmax(Lf.D[i], 1.0);
+    dsL[i] = fmin(Lf.D[i], 1.0);
+  }
+  __syncthreads();
+  double2* Mid = zmat(C, 4);
+  double2* MI = zmat(C, 5);
+  double2* X = zmat(C, 7);
+  zgemm<2, 0, false>(N, N, N, R.Q, ld, Lf.Q, ld, Mid, ld, S.gemm);  // Q_R^H Q_L
+  zgemm<0, 2, false>(N, N, N, R.T, ld, Lf.T, ld, X, ld, S.gemm);    // T_R T_L^H
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    Mid[(size_t)i * ld + j] = zadd(zscal(1.0 / (dbR[i] * dbL[j]), Mid[(size_t)i * ld + j]),
+                                   zscal(dsR[i] * dsL[j], X[(size_t)i * ld + j]));
+    MI[(size_t)i * ld + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    double bv = -1.0;
+    int bi = N;
+    for (int i = k + tid; i < N; i += kThreads) {
+      const double a = zabs(Mid[(size_t)i * ld + k]);
+      if (a > bv) { bv = a; bi = i; }
+    }
+    const int p = block_argmax(bv, bi, S.red, S.ired);
+    if (p >= N || zabs(Mid[(size_t)p * ld + k]) == 0.0) return 1;
+    if (p != k) {
+      for (int j = tid; j < N; j += kThreads) {
+        double2 t = Mid[(size_t)k * ld + j]; Mid[(size_t)k * ld + j] = Mid[(size_t)p * ld + j]; Mid[(size_t)p * ld + j] = t;
+        t = MI[(size_t)k * ld + j]; MI[(size_t)k * ld + j] = MI[(size_t)p * ld + j]; MI[(size_t)p * ld + j] = t;
+      }
+      __syncthreads();
+    }
+    const double2 dinv = zdiv(make_double2(1.0, 0.0), Mid[(size_t)k * ld + k]);
+    __syncthreads();
+    for (int j = tid; j < N; j += kThreads) {
+      Mid[(size_t)k * ld + j] = zmul(Mid[(size_t)k * ld + j], dinv);
+      MI[(size_t)k * ld + j] = zmul(MI[(size_t)k * ld + j], dinv);
+    }
+    for (int i = tid; i < N; i += kThreads) S.hv[i] = (i == k) ? make_double2(0.0, 0.0) : Mid[(size_t)i * ld + k];
+    __syncthreads();
+    for (int e = tid; e < N * N; e += kThreads) {
+      const int i = e / N, j = e - i * N;
+      if (i == k) continue;
+      const double2 f = S.hv[i];
+      Mid[(size_t)i * ld + j] = zsub(Mid[(size_t)i * ld + j], zmul(f, Mid[(size_t)k * ld + j]));
+      MI[(size_t)i * ld + j] = zsub(MI[(size_t)i * ld + j], zmul(f, MI[(size_t)k * ld + j]));
+    }
+    __syncthreads();
+  }
+  // G(tau,0) = Q_L (Db_L^-1 MI Ds_R) T_R
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    X[(size_t)i * ld + j] = zscal(dsR[j] / dbL[i], MI[(size_t)i * ld + j]);
+  }
+  __syncthreads();
+  zgemm<0, 0, false>(N, N, N, Lf.Q, ld, (const double2*)X, ld, Mid, ld, S.gemm);
+  zgemm<0, 0, false>(N, N, N, (const double2*)Mid, ld, R.T, ld, Gt0, ld, S.gemm);
+  // G(0,tau) = -T_L^H (Ds_L MI Db_R^-1) Q_R^H
+  for (int e = tid; e < N * N; e += kThreads) {
+    const int i = e / N, j = e - i * N;
+    X[(size_t)i * ld + j] = zscal(-dsL[i] / dbR[j], MI[(size_t)i * ld + j]);
+  }
+  __syncthreads();
+  zgemm<2, 0, false>(N, N, N, Lf.T, ld, (const double2*)X, ld, Mid, ld, S.gemm);
+  zgemm<0, 2, false>(N, N, N, (const double2*)Mid, ld, R.Q, ld, G0t, ld, S.gemm);
+  return 0;
+}
+
 // -g sum over every slice and site of eta(l): the phase of the bosonic factor
 // exp(-i g sum eta) of the weight
 __device__ double bosonic_phase(const Su2Dev& C, Sm& S) {
@@ -992,6 +1071,114 @@ __global__ void su2_corr_kernel(const Su2Dev* chains, int n_chains, const int* c
   }
 }
 
+// The time-displaced measurement of each chain's current configuration (the
+// tau_m step after a sweep, Sec. 2.4 / Algorithm 1, on the stored left chain):
+// starting from the stable G(0) = (1 + B(beta,0))^-1,
+//   G(tau,0) = B_tau G(tau-1,0),  G(0,tau) = G(0,tau-1) B_tau^-1,
+// and at every tau = j n_wrap both are recomputed from the right chain B(tau,0)
+// (built in place of the stored left chain's slot j, which is no longer needed)
+// and the left chain B(beta,tau)^H; the largest and the mean |wrapped - fresh|
+// entry over both is "Precision tau".  Per tau: a(tau) = sum_x G(tau,0)_xx.
+// The stored left chain is rebuilt at the end, so the chain continues as it
+// was; its working G is untouched.  only >= 0: that chain alone, and its
+// G(n_tau,0), G(0,n_tau) ([N][N] complex) into gt0 / g0t.
+__global__ void __launch_bounds__(kThreads) su2_tau_kernel(Su2Dev* chains, int n_chains, int only, int n_tau,
+                                                           double2* out_a, double* out_prec, double2* gt0,
+                                                           double2* g0t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int c = blockIdx.x;
+  if (c >= n_chains || (only >= 0 && c != only)) return;
+  Su2Dev& C = chains[c];
+  Sm S = su2_carve(smem_raw, C.N, C.MV);
+  const int N = C.N, ld = C.ld, nw = C.nw, nst = C.L / nw;
+  double2* Gt0 = zmat(C, 8);
+  double2* G0t = zmat(C, 9);
+  double2* Ft0 = zmat(C, 10);
+  double2* F0t = zmat(C, 11);
+  double la = 0.0, ar = 0.0;
+  int bad = z_green(C, z_ident(C), z_slot(C, 0), zmat(C, 6), la, ar, S);
+  const double2* G00 = zmat(C, 6);
+  for (int e = threadIdx.x; e < N * N; e += kThreads) {
+    const int x = e / N, y = e - x * N;
+    const double2 g = G00[(size_t)x * ld + y];
+    Gt0[(size_t)x * ld + y] = g;
+    G0t[(size_t)x * ld + y] = make_double2(g.x - (x == y ? 1.0 : 0.0), g.y);
+  }
+  __syncthreads();
+  double pmax = 0.0, psum = 0.0;
+  int nev = 0;
+  for (int tau = 0; tau <= n_tau && !bad; ++tau) {
+    if (tau > 0) {
+      const int8_t* f = C.fields + (size_t)(tau - 1) * C.MV;
+      double2* W = zmat(C, 0);
+      // G(tau,0) = E X_0 .. X_{nb-1} e^{V} G(tau-1,0)
+      slice_phases(C, f, +1.0, S.ph);
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        Gt0[(size_t)x * ld + y] = zmul(S.ph[x], Gt0[(size_t)x * ld + y]);
+      }
+      __syncthreads();
+      for (int b = C.nb - 1; b >= 0; --b) bond_rows(N, ld, Gt0, C.bi[b], C.bj[b], C.a0 * f[N + b]);
+      zgemm<0, 0, false>(N, N, N, C.E, ld, (const double2*)Gt0, ld, W, ld, S.gemm);
+      zcopy(N, ld, W, Gt0);
+      // G(0,tau) = G(0,tau-1) e^{-V} X_{nb-1}^-1 .. X_0^-1 E^-1
+      slice_phases(C, f, -1.0, S.ph);
+      for (int e = threadIdx.x; e < N * N; e += kThreads) {
+        const int x = e / N, y = e - x * N;
+        G0t[(size_t)x * ld + y] = zmul(G0t[(size_t)x * ld + y], S.ph[y]);
+      }
+      __syncthreads();
+      for (int b = C.nb - 1; b >= 0; --b) bond_cols(N, ld, G0t, C.bi[b], C.bj[b], -C.a0 * f[N + b]);
+      zgemm<0, 0, false>(N, N, N, (const double2*)G0t, ld, C.Einv, ld, W, ld, S.gemm);
+      zcopy(N, ld, W, G0t);
+      if (tau % nw == 0) {
+        const int j = tau / nw;
+        const ZUdv src = (j == 1) ? z_ident(C) : z_slot(C, j - 1);
+        const int dq = z_chain_step(C, (j - 1) * nw, j * nw, false, src, S);
+        const ZUdv Lf = (j == nst) ? z_ident(C) : z_slot(C, j);
+        bad = z_displaced(C, z_work(C, dq), Lf, Ft0, F0t, S);
+        if (bad) break;
+        double mx = 0.0, sm = 0.0;
+        for (int e = threadIdx.x; e < N * N; e += kThreads) {
+          const int x = e / N, y = e - x * N;
+          const size_t q = (size_t)x * ld + y;
+          const double d1 = zabs(zsub(Gt0[q], Ft0[q])), d2 = zabs(zsub(G0t[q], F0t[q]));
+          mx = fmax(mx, fmax(d1, d2));
+          sm += d1 + d2;
+          Gt0[q] = Ft0[q];
+          G0t[q] = F0t[q];
+        }
+        mx = block_max(mx, S.red);
+        sm = block_sum(sm, S.red);
+        pmax = fmax(pmax, mx);
+        psum += sm / (2.0 * N * N);
+        ++nev;
+        z_store_slot(C, j, dq);  // the right chain B(tau,0) takes slot j
+      }
+    }
+    double2 a = make_double2(0.0, 0.0);
+    for (int x = threadIdx.x; x < N; x += kThreads) a = zadd(a, Gt0[(size_t)x * ld + x]);
+    a = block_zsum(a, S.red);
+    if (threadIdx.x == 0 && out_a) out_a[(size_t)c * (n_tau + 1) + tau] = a;
+  }
+  if (only >= 0 && !bad) {
+    for (int e = threadIdx.x; e < N * N; e += kThreads) {
+      const int x = e / N, y = e - x * N;
+      gt0[e] = Gt0[(size_t)x * ld + y];
+      g0t[e] = G0t[(size_t)x * ld + y];
+    }
+  }
+  // the stored left chain again, for the next sweep
+  if (z_fill_left(C, S, la, ar)) bad = 1;
+  if (threadIdx.x == 0) {
+    if (bad) C.error |= 1;
+    if (out_prec) {
+      out_prec[2 * c] = nev ? psum / nev : 0.0;
+      out_prec[2 * c + 1] = pmax;
+    }
+  }
+}
+
 __global__ void su2_copy_green_kernel(Su2Dev* chains, int chain, double2* out) {
   const Su2Dev& C = chains[chain];
   const int N = C.N;
@@ -1075,6 +1262,14 @@ cudaError_t su2_launch_copy_green(Su2Dev* chains, int chain, double2* out, cudaS
 cudaError_t su2_launch_corr(const Su2Dev* chains, int n_chains, const int* const* off, const int* const* pairs,
                             const int* ncls, int max_cls, double2* out, cudaStream_t st) {
   su2_corr_kernel<<<n_chains, 128, 0, st>>>(chains, n_chains, off, pairs, ncls, max_cls, out);
+  return cudaGetLastError();
+}
+
+cudaError_t su2_launch_tau(Su2Dev* chains, int n_chains, int only, int n_tau, double2* out_a, double* out_prec,
+                           double2* gt0, double2* g0t, size_t smem, cudaStream_t st) {
+  cudaError_t e = su2_set_smem((const void*)su2_tau_kernel, smem);
+  if (e != cudaSuccess) return e;
+  su2_tau_kernel<<<n_chains, kThreads, smem, st>>>(chains, n_chains, only, n_tau, out_a, out_prec, gt0, g0t);
   return cudaGetLastError();
 }
 

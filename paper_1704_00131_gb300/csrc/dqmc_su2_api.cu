@@ -342,6 +342,66 @@ dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, i
   return DQMC_OK;
 }
 
+dqmc_status dqmc_su2_measure_tau(dqmc_su2_ctx* ctx, int32_t n_tau, double* out, double* prec_tau) {
+  if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
+  if (!out) return fail(ctx, DQMC_EINVAL, "null output");
+  const int nch = (int)ctx->chains_h.size();
+  for (const Su2Dev& C : ctx->chains_h)
+    if (n_tau < 0 || n_tau > C.L) return fail(ctx, DQMC_EINVAL, "n_tau must be in [0, L] of every chain");
+  double2* a_d = nullptr;
+  double* p_d = nullptr;
+  const size_t na = (size_t)nch * (n_tau + 1);
+  if (cudaMalloc((void**)&a_d, na * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&p_d, (size_t)nch * 2 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(a_d);
+    return fail(ctx, DQMC_ENOMEM, "tau measurement buffers");
+  }
+  std::vector<double> pr((size_t)nch * 2, 0.0);
+  dqmc_status st = DQMC_OK;
+  cudaError_t e = dqmc::su2_launch_tau(ctx->chains_d, nch, -1, n_tau, a_d, p_d, nullptr, nullptr, ctx->smem, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, a_d, na * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pr.data(), p_d, pr.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) st = fail(ctx, DQMC_ECUDA, "tau measurement: %s", cudaGetErrorString(e));
+  if (!st) st = download(ctx);
+  cudaFree(a_d);
+  cudaFree(p_d);
+  if (st) return st;
+  double mean = 0.0, mx = 0.0;
+  for (int c = 0; c < nch; ++c) {
+    if (ctx->chains_h[c].error) return fail(ctx, DQMC_EUNSTABLE, "chain %d: singular matrix in the tau measurement", c);
+    mean += pr[2 * c] / nch;
+    mx = std::max(mx, pr[2 * c + 1]);
+  }
+  if (prec_tau) { prec_tau[0] = mean; prec_tau[1] = mx; }
+  return DQMC_OK;
+}
+
+dqmc_status dqmc_su2_greens_displaced(dqmc_su2_ctx* ctx, int32_t chain, int32_t tau, double* out_t0, double* out_0t) {
+  if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");
+  if (chain < 0 || chain >= (int)ctx->chains_h.size() || !out_t0 || !out_0t)
+    return fail(ctx, DQMC_EINVAL, "bad chain or output");
+  const Su2Dev& H = ctx->chains_h[chain];
+  if (tau < 0 || tau > H.L) return fail(ctx, DQMC_EINVAL, "tau must be in [0, L]");
+  const size_t nn = (size_t)H.N * H.N;
+  double2* g_d = nullptr;
+  if (cudaMalloc((void**)&g_d, 2 * nn * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, DQMC_ENOMEM, "displaced Green function buffers");
+  }
+  dqmc_status st = DQMC_OK;
+  cudaError_t e = dqmc::su2_launch_tau(ctx->chains_d, (int)ctx->chains_h.size(), chain, tau, nullptr, nullptr, g_d,
+                                       g_d + nn, ctx->smem, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_t0, g_d, nn * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_0t, g_d + nn, nn * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) st = fail(ctx, DQMC_ECUDA, "displaced Green functions: %s", cudaGetErrorString(e));
+  if (!st) st = download(ctx);
+  cudaFree(g_d);
+  if (st) return st;
+  if (ctx->chains_h[chain].error) return fail(ctx, DQMC_EUNSTABLE, "chain %d: singular matrix", chain);
+  return DQMC_OK;
+}
+
 dqmc_status dqmc_su2_measure_corr(dqmc_su2_ctx* ctx, const int32_t* pair_class, const int32_t* n_class, double* out,
                                   double* phase) {
   if (!ctx || !ctx->chains_d) return fail(ctx, DQMC_ESTATE, "context not initialised");

@@ -56,7 +56,7 @@ struct Su2Dev {
   int error;              // bit 0: a singular matrix in the stabilisation
 };
 
-constexpr int kSu2Mats = 8;   // complex N x ld work matrices per chain
+constexpr int kSu2Mats = 12;  // complex N x ld work matrices per chain
 constexpr int kSu2ZVecs = 4;  // complex work vectors per chain
 constexpr int kSu2DVecs = 10; // real work vectors per chain
 
@@ -83,6 +83,11 @@ cudaError_t su2_launch_fresh(Su2Dev* chains, int n_chains, int mode, int only, d
 cudaError_t su2_launch_sweep(Su2Dev* chains, const Su2SweepParams& p, size_t smem, cudaStream_t st);
 cudaError_t su2_launch_copy_green(Su2Dev* chains, int chain, double2* out, cudaStream_t st);
 cudaError_t su2_launch_reset_stats(Su2Dev* chains, int n_chains, int clear_meas, cudaStream_t st);
+// time-displaced measurement of every chain (only < 0) or of chain `only` (with
+// its G(n_tau,0), G(0,n_tau) into gt0 / g0t): out_a [n_chains][n_tau+1] complex
+// traces of G(tau,0), out_prec [n_chains][2] (mean, max) of Precision tau
+cudaError_t su2_launch_tau(Su2Dev* chains, int n_chains, int only, int n_tau, double2* out_a, double* out_prec,
+                           double2* gt0, double2* g0t, size_t smem, cudaStream_t st);
 // per chain: CSR lists of the pair classes (off[c], pairs[c]: device pointers),
 // ncls [n_chains]; out [n_chains][max_cls][4] complex
 cudaError_t su2_launch_corr(const Su2Dev* chains, int n_chains, const int* const* off, const int* const* pairs,

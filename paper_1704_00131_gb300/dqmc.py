@@ -25,6 +25,7 @@ EXPORTED = ["dqmc_init", "dqmc_sweep", "dqmc_greens", "dqmc_greens_tau", "dqmc_m
             "dqmc_measure_tau_corr", "dqmc_measure_corr", "dqmc_logdet_backward", "dqmc_energy_backward", "dqmc_get_fields",
             "dqmc_set_fields", "dqmc_green_fresh_noalloc", "dqmc_last_error", "dqmc_destroy",
             "dqmc_su2_init", "dqmc_su2_sweep", "dqmc_su2_greens", "dqmc_su2_measure", "dqmc_su2_measure_corr",
+            "dqmc_su2_measure_tau", "dqmc_su2_greens_displaced",
             "dqmc_su2_get_fields",
             "dqmc_su2_set_fields", "dqmc_su2_last_error", "dqmc_su2_destroy"]
 
@@ -142,6 +143,10 @@ def load() -> ctypes.CDLL:
     L.dqmc_su2_greens.restype = ctypes.c_int
     L.dqmc_su2_measure.argtypes = [vp, vp, vp, vp, i32]
     L.dqmc_su2_measure.restype = ctypes.c_int
+    L.dqmc_su2_measure_tau.argtypes = [vp, i32, vp, vp]
+    L.dqmc_su2_measure_tau.restype = ctypes.c_int
+    L.dqmc_su2_greens_displaced.argtypes = [vp, i32, i32, vp, vp]
+    L.dqmc_su2_greens_displaced.restype = ctypes.c_int
     L.dqmc_su2_measure_corr.argtypes = [vp, vp, vp, vp, vp]
     L.dqmc_su2_measure_corr.restype = ctypes.c_int
     L.dqmc_su2_get_fields.argtypes = [vp, vp, vp]
@@ -537,6 +542,21 @@ class Su2Ensemble:
         nm = np.zeros(self.n_chains, dtype=np.int64)
         self._check(self._lib.dqmc_su2_measure(self._h, _p(out), _p(sg), _p(nm), int(reset)))
         return out[..., 0] + 1j * out[..., 1], sg, nm
+
+    def measure_tau(self, n_tau: int):
+        """(complex [n_chains, n_tau + 1] traces of G(tau,0); (mean, max) of Precision tau)."""
+        out = np.zeros((self.n_chains, int(n_tau) + 1, 2))
+        pt = np.zeros(2)
+        self._check(self._lib.dqmc_su2_measure_tau(self._h, int(n_tau), _p(out), _p(pt)))
+        return out[..., 0] + 1j * out[..., 1], (float(pt[0]), float(pt[1]))
+
+    def greens_displaced(self, chain: int, tau: int):
+        """(G(tau,0), G(0,tau)) of a chain, complex [N, N] each."""
+        N = self.model_of(chain).N
+        a = np.zeros((N, N, 2))
+        b = np.zeros((N, N, 2))
+        self._check(self._lib.dqmc_su2_greens_displaced(self._h, int(chain), int(tau), _p(a), _p(b)))
+        return a[..., 0] + 1j * a[..., 1], b[..., 0] + 1j * b[..., 1]
 
     def measure_corr(self, pair_class, n_class):
         """Equal-time correlations per pair class of every chain's current G(0):

@@ -334,3 +334,109 @@ def test_su2_correlations_match_oracle(dq, orc):
         ens.measure_corr([bad, cl[1][0]], [cl[0][1], cl[1][1]])
     assert e.value.status == dq.DQMC_EINVAL
     ens.close()
+
+
+@pytest.mark.parametrize("mu,L,nw", [(0.0, 20, 5), (0.3, 20, 5), (-0.4, 60, 10)])
+def test_su2_displaced_greens_match_oracle(dq, orc, mu, L, nw):
+    """G(tau,0) and G(0,tau) (Sec. 2.4) of fixed fields: wrapped slice by slice
+    from the stable G(0) and recomputed from the UDV chains at every multiple of
+    n_wrap, against the oracle's displaced functions from its own UDV chains at
+    taus on and between the recompute points; the traces of measure_tau are
+    sum_x G(tau,0)_xx; the ends reduce to G(beta,0) = 1 - G(0), G(0,beta) = -G(0)."""
+    K = W.square_lattice(4, 4, t=1.0, mu=mu)
+    dtau, U, n_ch = 0.1, 4.0, 2
+    rng = np.random.default_rng(int(L + 10 * mu) + 7)
+    fields = [rng.choice([-2, -1, 1, 2], size=(L, 16)).astype(np.int8) for _ in range(n_ch)]
+    m = dq.Su2Model(K, U=U, dtau=dtau, L=L, n_wrap=nw)
+    ens = dq.Su2Ensemble([m], [0] * n_ch, fields=fields, seed=5)
+    taus = sorted({0, 1, nw - 1, nw, nw + 3, L // 2, L - 1, L})
+    a, (pmean, pmax) = ens.measure_tau(L)
+    assert a.shape == (n_ch, L + 1)
+    assert pmax < 1e-8 and pmean <= pmax
+    for c in range(n_ch):
+        G0, _, _ = orc.su2_green_udv(K, dtau, U, nw, fields[c], 0)
+        for tau in taus:
+            Gt0, G0t = ens.greens_displaced(c, tau)
+            Ot0, O0t = orc.su2_green_displaced(K, dtau, U, nw, fields[c], tau)
+            assert np.abs(Gt0 - Ot0).max() < 1e-9, (c, tau)
+            assert np.abs(G0t - O0t).max() < 1e-9, (c, tau)
+            assert abs(a[c, tau] - np.trace(Gt0)) < 1e-12 * max(1.0, abs(a[c, tau])), (c, tau)
+            if tau == L:
+                assert np.abs(Gt0 - (np.eye(16) - G0)).max() < 1e-9
+                assert np.abs(G0t + G0).max() < 1e-9
+            if tau == 0:
+                assert np.abs(Gt0 - G0).max() < 1e-10 and np.abs(G0t - (G0 - np.eye(16))).max() < 1e-10
+    ens.close()
+
+
+def test_su2_tau_measurement_leaves_the_chain(dq):
+    """The tau measurement rebuilds the stored chain it borrows: the working
+    G(0), the phase and the next sweeps' field trajectory equal those of an
+    identical ensemble that was not measured."""
+    m = dq.Su2Model(W.square_lattice(4, 4, t=1.0, mu=0.2), U=4.0, dtau=0.1, L=40, n_wrap=10)
+    e1 = dq.Su2Ensemble([m], [0] * 3, seed=21)
+    e2 = dq.Su2Ensemble([m], [0] * 3, seed=21)
+    e1.sweep(1)
+    e2.sweep(1)
+    before = [e1.greens(c) for c in range(3)]
+    e1.measure_tau(17)
+    e1.greens_displaced(1, 23)
+    for c in range(3):
+        G, la, ar, P = e1.greens(c)
+        assert np.array_equal(G, before[c][0]) and P == before[c][3]
+    s1, s2 = e1.sweep(2), e2.sweep(2)
+    f1, _ = e1.get_fields()
+    f2, _ = e2.get_fields()
+    assert np.array_equal(f1, f2) and s1["accepted"] == s2["accepted"]
+    for c in range(3):
+        assert np.abs(e1.greens(c)[0] - e2.greens(c)[0]).max() < 1e-10
+    with pytest.raises(dq.DqmcError) as e:
+        e1.measure_tau(41)
+    assert e.value.status == dq.DQMC_EINVAL
+    with pytest.raises(dq.DqmcError) as e:
+        e1.greens_displaced(1, 41)
+    assert e.value.status == dq.DQMC_EINVAL
+    e1.close()
+    e2.close()
+
+
+def test_su2_paper_example_precision_tau(dq):
+    """4 x 4, U = 4, beta = 10, n_wrap = 10 (the paper's SU(2) example): the
+    Precision tau of the time-displaced measurement over the whole interval
+    stays at the level the paper reports for its example (mean ~1e-14, max
+    ~1e-11)."""
+    m = dq.Su2Model(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=100, n_wrap=10)
+    ens = dq.Su2Ensemble([m], [0] * 8, seed=11)
+    ens.sweep(3)
+    a, (pmean, pmax) = ens.measure_tau(100)
+    assert pmean < 1e-12 and pmax < 1e-8
+    assert np.all(np.isfinite(a)) and np.all(np.abs(a[:, 50]) < np.abs(a[:, 0]))
+    ens.close()
+
+
+def test_bond_model_displaced_greens(dq, orc):
+    """Bond model (two-site bond factors inside each slice): the ends of the
+    displaced functions against the oracle's G(0) (G(beta,0) = 1 - G(0),
+    G(0,beta) = -G(0)); at an interior tau between recompute points, the
+    identity -G(tau,0) G(0,tau) = G(tau) (1 - G(tau)) with the oracle's
+    equal-time G(tau); Precision tau at the FP64 level."""
+    Lx, L, nw = 3, 15, 5
+    T = W.square_lattice(Lx, Lx, t=1.0, mu=0.2)
+    bonds = _square_bonds(Lx, Lx)[:4]
+    rng = np.random.default_rng(41)
+    hs = [rng.choice([-2, -1, 1, 2], size=(L, 9)).astype(np.int8) for _ in range(2)]
+    ising = [rng.choice([-1, 1], size=(L, len(bonds))).astype(np.int8) for _ in range(2)]
+    m = dq.Su2Model(T, U=3.0, dtau=0.1, L=L, n_wrap=nw, bonds=bonds, xi=0.5, h=1.0, J=0.0)
+    ens = dq.Su2Ensemble([m], [0, 0], fields=[np.concatenate([hs[c], ising[c]], axis=1) for c in range(2)], seed=3)
+    _, (pmean, pmax) = ens.measure_tau(L)
+    assert pmax < 1e-9
+    for c in range(2):
+        G0, _, _ = orc.hubbard_ising_green_udv(T, bonds, 0.5, 0.1, 3.0, nw, hs[c], ising[c], 0)
+        Gt0, G0t = ens.greens_displaced(c, L)
+        assert np.abs(Gt0 - (np.eye(9) - G0)).max() < 1e-9
+        assert np.abs(G0t + G0).max() < 1e-9
+        for tau in (3, 7, 12):
+            Gt, _, _ = orc.hubbard_ising_green_udv(T, bonds, 0.5, 0.1, 3.0, nw, hs[c], ising[c], tau)
+            Gt0, G0t = ens.greens_displaced(c, tau)
+            assert np.abs(-Gt0 @ G0t - Gt @ (np.eye(9) - Gt)).max() < 1e-9, (c, tau)
+    ens.close()
