@@ -561,7 +561,9 @@ def paper_example(args):
     mixed paths over args.steps sweeps after args.warmup, with the time-displaced
     functions measured after every sweep, next to the values of the paper's info file;
     then the same for the SU(2) decoupling's example (Sec. 6.1), with its
-    "Precision Phase" and the throughput of a batch of its chains."""
+    "Precision Phase", the Precision tau of one time-displaced measurement over
+    the whole interval after the sweeps, and the throughput of a batch of its
+    chains."""
     from paper_1704_00131_gb300 import build_ext, dqmc
     build_ext.build()
     m = W.ModelSpec(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=100, n_wrap=10, name="square4x4_U4_b10")
@@ -589,12 +591,15 @@ def paper_example(args):
     ens = dqmc.Su2Ensemble([ms2], [0] * n_su2, seed=W.BASE_SEED)
     ens.sweep(args.warmup)
     st = ens.sweep(args.steps)
+    _, pt = ens.measure_tau(ms2.L)
     ens.close()
     out["su2"] = {"workload": f"su2_square4x4_U4_b10 x {n_su2} chains",
                   "paper_info_file": {"precision_green_mean_max": [1.2918865817224671e-14, 4.0983018995027644e-11],
-                                      "precision_phase_max": 5.0272908791449966e-12},
+                                      "precision_phase_max": 5.0272908791449966e-12,
+                                      "precision_tau_mean_max": [8.4596701790588625e-15, 3.5033530012121281e-11]},
                   "precision_green_mean_max": [st["prec_green_mean"], st["prec_green_max"]],
-                  "precision_phase_max": st["prec_phase_max"], "mean_sign": st["mean_sign"],
+                  "precision_phase_max": st["prec_phase_max"],
+                  "precision_tau_mean_max": [pt[0], pt[1]], "mean_sign": st["mean_sign"],
                   "acceptance": st["accepted"] / st["proposals"],
                   "proposals_per_s": st["proposals"] / (st["ms_total"] * 1e-3),
                   "ms_per_sweep": st["ms_total"] / args.steps, "dtype": "complex f64"}
