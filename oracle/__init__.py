@@ -68,7 +68,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        # DQMC_ORACLE_LIB: a prebuilt oracle library to load instead (the pin
+        # tests load builds with planted mistakes this way and must fail)
+        _lib = ctypes.CDLL(os.environ.get("DQMC_ORACLE_LIB") or build())
         d, i32, u32, u64, vp = ctypes.c_double, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
         _lib.orc_philox4x32_10.argtypes = [vp, vp, vp]
         _lib.orc_u01.argtypes = [u32, u32]

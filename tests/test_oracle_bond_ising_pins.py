@@ -180,6 +180,28 @@ def test_vertex_green_ratios_and_rank2_update(orc):
     assert worst_r < 1e-12 and worst_g < 1e-12, (worst_r, worst_g)
 
 
+def test_rank2_update_with_a_general_delta(orc):
+    """The rank-2 update against its definition for any change (1 + Delta) F of the
+    factor F seen by G~ = (1 + F R)^-1, with Delta nonzero only on the block {i, j}:
+    G~' = (1 + (1 + Delta) F R)^-1 and ratio = det(1 + (1 + Delta) F R) / det(1 + F R),
+    here with a random complex F R and a random non-symmetric complex 2 x 2 block, so
+    that a transposed or misplaced delta cannot pass."""
+    rng = np.random.default_rng(12)
+    N = 5
+    A = 0.4 * (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N)))
+    G = np.linalg.inv(np.eye(N) + A)
+    for i, j in ((1, 3), (4, 0)):
+        d = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+        D = np.zeros((N, N), dtype=complex)
+        D[np.ix_([i, j], [i, j])] = d
+        A1 = (np.eye(N) + D) @ A
+        G1_ref = np.linalg.inv(np.eye(N) + A1)
+        r_ref = np.linalg.det(np.eye(N) + A1) / np.linalg.det(np.eye(N) + A)
+        G1, r = orc.bond_rank2_update(G, i, j, d)
+        assert np.abs(G1 - G1_ref).max() < 1e-12 * max(1.0, np.abs(G1_ref).max())
+        assert abs(r - r_ref) < 1e-12 * abs(r_ref)
+
+
 @pytest.mark.parametrize("mu", [0.0, 0.3])
 def test_sampler_matches_trotter_product(orc, mu):
     from paper_1704_00131_gb300 import analysis as A

@@ -104,13 +104,17 @@ def _wrap_angle(a):
     return (a + np.pi) % (2 * np.pi) - np.pi
 
 
-def test_su2_udv_chain_matches_plain_product(orc):
+@pytest.mark.parametrize("lx", [4, 3])
+def test_su2_udv_chain_matches_plain_product(orc, lx):
     """The complex UDV chain (QR with pivoting, scale separation) against the plain
     product where both hold (beta = 2): G, log|det| and arg det for several n_wrap,
-    and G(tau) against the plain product of the cyclically rotated fields."""
+    and G(tau) against the plain product of the cyclically rotated fields.  The odd
+    3 x 3 torus gives a Householder QR of N = 9 reflections, det Q = -1, so the
+    factor det Q_R conj(det Q_L) of arg det is exercised (at tau = 0 the right
+    chain is the identity)."""
     rng = np.random.default_rng(0)
-    K = W.square_lattice(4, 4, t=1.0, mu=0.2)
-    f = rng.choice([-2, -1, 1, 2], size=(20, 16)).astype(np.int8)
+    K = W.square_lattice(lx, lx, t=1.0, mu=0.2)
+    f = rng.choice([-2, -1, 1, 2], size=(20, lx * lx)).astype(np.int8)
     Gp, la, ar, _, _, _ = orc.su2_plain(K, 0.1, 4.0, f)
     for nw in (1, 5, 20):
         Gu, lu, au = orc.su2_green_udv(K, 0.1, 4.0, nw, f, 0)
