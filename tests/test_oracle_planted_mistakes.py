@@ -148,6 +148,54 @@ PLANTS = [
     ("rank-2 update: delta transposed",
      [("Wm[2 * a + b] = Si[2 * a] * d[b] + Si[2 * a + 1] * d[2 + b];",
        "Wm[2 * a + b] = Si[2 * a] * d[2 * b] + Si[2 * a + 1] * d[2 * b + 1];")], [BOND + "::test_rank2_update_with_a_general_delta"]),
+    ('53-bit uniform from 52 bits',
+     [('return (double)(w >> 11) * (1.0 / 9007199254740992.0);', 'return (double)(w >> 12) * (1.0 / 9007199254740992.0);')],
+     [CORE + "::test_uniform_mapping"]),
+    ('initial four-valued fields drawn from three values',
+     [('int idx = (int)floor(4.0 * u);', 'int idx = (int)floor(3.0 * u);')],
+     [CORE + "::test_init_fields_distribution"]),
+    ('four-valued proposal restricted to two of the three other values',
+     [('int idx = (int)floor(3.0 * u1);\n    if (idx > 2) idx = 2;\n    fn = others[idx];', 'int idx = (int)floor(2.0 * u1);\n    if (idx > 2) idx = 2;\n    fn = others[idx];')],
+     [CORE + "::test_sampler_reproduces_exact_energies"]),
+    ('LU: sign of a negative pivot ignored',
+     [('    if (d < 0) sg = -sg;\n', '')],
+     [CORE + "::test_logdet_against_library"]),
+    ('Jacobi rotation with the wrong sign of s',
+     [('const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;', 'const double c = 1.0 / sqrt(t * t + 1.0), s = -t * c;')],
+     [CORE + "::test_eig_and_expm_against_library"]),
+    ('log-det adjoint: V-wrap of G(tau-1) with the wrong sign',
+     [('- exp(v[x] - v[y]) * G[x * N + y];', '- exp(v[y] - v[x]) * G[x * N + y];')],
+     [CORE + "::test_logdet_gradient_finite_differences"]),
+    ('log-det adjoint: E for E^-1',
+     [('mat_mul(N, S, M.Einv + s * nn, A);', 'mat_mul(N, S, M.E + s * nn, A);')],
+     [CORE + "::test_logdet_gradient_finite_differences"]),
+    ('energy adjoint: explicit delta - G^T term dropped on the diagonal',
+     [('if (x == y) g[x * N + y] = Z[x * N + y] + ex;', 'if (x == y) g[x * N + y] = Z[x * N + y];')],
+     [CORE + "::test_energy_gradient_finite_differences"]),
+    ('energy adjoint: divided difference sinh(x) for sinh(x)/x',
+     [('const double x = 0.5 * M.dtau * (w[a] - w[b]);\n          const double shc = (x == 0.0) ? 1.0 : sinh(x) / x;', 'const double x = 0.5 * M.dtau * (w[a] - w[b]);\n          const double shc = (x == 0.0) ? 1.0 : sinh(x);')],
+     [CORE + "::test_energy_gradient_finite_differences"]),
+    ("energy adjoint: the own flavor's density in dPot/dK_xx",
+     [('g -= M.U * (1.0 - G0[1 - s][x * N + x]);', 'g -= M.U * (1.0 - G0[s][x * N + x]);')],
+     [CORE + "::test_energy_gradient_finite_differences"]),
+    ('tau observables: connected density term with the wrong sign',
+     [('c -= px * py * G0t[y * N + x] * Gt0[x * N + y];', 'c += px * py * G0t[y * N + x] * Gt0[x * N + y];')],
+     [TAU]),
+    ('tau observables: density at tau taken from G(tau,0)',
+     [('p += px * (1.0 - Gtt[x * N + x]);', 'p += px * (1.0 - Gt0[x * N + x]);')],
+     [TAU]),
+    ('SU(2) correlations: S^z S^z with 1/4 X for 1/2 X',
+     [('const double complex v[4] = {0.5 * X, rx * ry + 2.0 * X, X, 2.0 * hyx};', 'const double complex v[4] = {0.25 * X, rx * ry + 2.0 * X, X, 2.0 * hyx};')],
+     [SU2 + "::test_su2_correlations_enumeration_equals_fock_trace"]),
+    ('SU(2) left chain: e^{V} for its adjoint e^{-V}',
+     [('const double complex ev = cexp(-_Complex_I * g * hs_eta(fields[(size_t)(t - 1) * N + x]));', 'const double complex ev = cexp(_Complex_I * g * hs_eta(fields[(size_t)(t - 1) * N + x]));')],
+     [SU2 + "::test_su2_udv_chain_matches_plain_product"]),
+    ('SU(2) G(0,tau) with the wrong sign',
+     [('G0t[2 * ((size_t)i * N + j)] = -creal(acc);\n        G0t[2 * ((size_t)i * N + j) + 1] = -cimag(acc);', 'G0t[2 * ((size_t)i * N + j)] = creal(acc);\n        G0t[2 * ((size_t)i * N + j) + 1] = cimag(acc);')],
+     [SU2 + "::test_su2_displaced_green_matches_the_definition"]),
+    ('SU(2) G(tau,0) with Db_R for Ds_R',
+     [('X[(size_t)i * N + j] = MI[(size_t)i * N + j] / dbL[i] * dsR[j];', 'X[(size_t)i * N + j] = MI[(size_t)i * N + j] / dbL[i] * dbR[j];')],
+     [SU2 + "::test_su2_displaced_green_matches_the_definition"]),
 ]
 
 
