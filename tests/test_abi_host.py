@@ -127,3 +127,36 @@ def test_product_and_oracle_share_no_code():
             text = open(os.path.join(root, "oracle", fn), encoding="utf-8").read()
             assert not re.search(r"^\s*(import|from)\s+paper_1704_00131_gb300\b", text, re.M), fn
             assert not re.search(r"^\s*#\s*include\s*[<\"].*(dqmc|paper_1704)", text, re.M), fn
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of the C structs have the header's size and field
+    offsets (the header compiled by gcc prints them), so a field added, removed or
+    reordered on one side only fails here on the CPU rather than as garbage
+    arguments on a GPU."""
+    import ctypes
+    import json
+    import subprocess
+    from paper_1704_00131_gb300 import dqmc as dq
+    mirrors = {"dqmc_model_desc": dq.ModelDesc, "dqmc_run_opts": dq.RunOpts, "dqmc_sweep_stats": dq.SweepStats,
+               "dqmc_su2_model_desc": dq.Su2ModelDesc, "dqmc_su2_opts": dq.Su2Opts,
+               "dqmc_su2_sweep_stats": dq.Su2SweepStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dqmc.h"', '#include "dqmc_su2.h"',
+             'int main(void) {', '  printf("{");']
+    first = True
+    for cname, py in mirrors.items():
+        fields = ", ".join(f'\\"{f}\\": %zu' for f, _ in py._fields_)
+        args = ", ".join(f"offsetof({cname}, {f})" for f, _ in py._fields_)
+        sep = "" if first else ", "
+        first = False
+        lines.append(f'  printf("{sep}\\"{cname}\\": {{\\"sizeof\\": %zu, {fields}}}", sizeof({cname}), {args});')
+    lines += ['  printf("}\\n");', '  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    c = json.loads(subprocess.check_output([str(exe)]).decode())
+    for cname, py in mirrors.items():
+        assert c[cname]["sizeof"] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert c[cname][f] == getattr(py, f).offset, (cname, f)
