@@ -207,7 +207,9 @@ dqmc_status dqmc_greens_tau(dqmc_ctx* ctx, int32_t chain, int32_t flavor, int32_
  *     out[c][1] = sum sign * Pot,  Pot  = U sum_i (1 - G^up_ii)(1 - G^dn_ii)
  *     out[c][2] = sum sign * Part, Part = sum_s sum_i (1 - G^s_ii)
  *     out[c][3] = sum sign * (Kin + Pot)
- * sign_sum[c] = sum of signs, n_meas[c] = number of measurements (host arrays). */
+ * sign_sum[c] = sum of signs, n_meas[c] = number of measurements (host arrays).
+ * Waits for the context's stream.  Errors: DQMC_EINVAL (a null output),
+ * DQMC_ECUDA. */
 dqmc_status dqmc_measure(dqmc_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas);
 
 /* Time-displaced Green functions of every chain's current configuration: the
@@ -301,7 +303,12 @@ dqmc_status dqmc_measure_corr(dqmc_ctx* ctx, const int32_t* pair_class, const in
  *     logdet  [n_cfg][n_flavors]
  *     grad_K  [n_cfg][n_flavors][N][N]: d/dK^s_xy with K_xy and K_yx varied
  *             together (x != y); d/dK_xx on the diagonal
- *     grad_U  [n_cfg][n_flavors]: d/dU through the couplings c(field). */
+ *     grad_U  [n_cfg][n_flavors]: d/dU through the couplings c(field).
+ * The workspace (one FP64 chain per configuration) is allocated and freed by
+ * the call, which waits for its work.  Errors: DQMC_EINVAL (model_index out of
+ * range, n_cfg < 1, a null pointer, an invalid field value), DQMC_ENOMEM,
+ * DQMC_ECUDA, DQMC_EUNSTABLE (a singular matrix in the stabilisation of a
+ * configuration). */
 dqmc_status dqmc_logdet_backward(dqmc_ctx* ctx, int32_t model_index, const int8_t* fields, int32_t n_cfg,
                                  double* logdet, double* grad_K, double* grad_U);
 
@@ -314,7 +321,8 @@ dqmc_status dqmc_logdet_backward(dqmc_ctx* ctx, int32_t model_index, const int8_
  * from the UDV chains).  fields: [n_cfg][L][M_V] int8 host.  Outputs (host):
  *     energy  [n_cfg][4] = Kin, Pot, Part, Ener of each configuration
  *     grad_K  [n_cfg][n_flavors][N][N]: dEner/dK^s_xy, K_xy and K_yx varied together
- *     grad_U  [n_cfg]: dEner/dU (explicit U and the couplings c(field)). */
+ *     grad_U  [n_cfg]: dEner/dU (explicit U and the couplings c(field)).
+ * Workspace, waiting and errors as dqmc_logdet_backward. */
 dqmc_status dqmc_energy_backward(dqmc_ctx* ctx, int32_t model_index, const int8_t* fields, int32_t n_cfg,
                                  double* energy, double* grad_K, double* grad_U);
 
