@@ -113,7 +113,9 @@ dqmc_status dqmc_su2_sweep(dqmc_su2_ctx* ctx, int32_t n_sweeps, dqmc_su2_sweep_s
  * (host, or device when out_is_device): fresh = 0 the working G the sweeps
  * left, fresh = 1 recomputed from the fields through the UDV chain.
  * logabs_out / arg_out (nullable): log|det(1 + B(beta,0))| and its argument
- * at the last fresh G; phase_out (nullable, [2]): the chain's phase P. */
+ * at the last fresh G; phase_out (nullable, [2]): the chain's phase P.
+ * Errors: DQMC_ESTATE (no context), DQMC_EINVAL (chain out of range, null out),
+ * DQMC_ECUDA, DQMC_EUNSTABLE (fresh = 1 met a singular matrix). */
 dqmc_status dqmc_su2_greens(dqmc_su2_ctx* ctx, int32_t chain, int32_t fresh, double* out, int32_t out_is_device,
                             double* logabs_out, double* arg_out, double* phase_out);
 
@@ -122,7 +124,8 @@ dqmc_status dqmc_su2_greens(dqmc_su2_ctx* ctx, int32_t chain, int32_t fresh, dou
  * O = Kin, Pot, Part, Ener (Sec. 6.1 estimator, both colors; Kin of the hopping
  * K alone) and the bond spins' (sum_b s_b)^2 / n_bonds averaged over the slices
  * (0 without bonds); sign_sum [n_chains] = sum of sign(Re P); n_meas
- * [n_chains].  Host buffers. */
+ * [n_chains].  Host buffers, each nullable (skipped).  Waits for the context's
+ * stream.  Errors: DQMC_ESTATE, DQMC_ECUDA. */
 dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, int64_t* n_meas, int32_t reset);
 
 /* Time-displaced measurement of every chain's current configuration (the tau_m
@@ -134,12 +137,15 @@ dqmc_status dqmc_su2_measure(dqmc_su2_ctx* ctx, double* out, double* sign_sum, i
  * sum_x G(tau,0)_xx; prec_tau (host, nullable) [2]: "Precision tau", the mean
  * over chains and recompute points of the mean |wrapped - recomputed| entry
  * of G(tau,0) and G(0,tau), and the maximum.  0 <= n_tau <= L of every chain.
- * The chains are left as they are. */
+ * The chains are left as they are.  Errors: DQMC_ESTATE, DQMC_EINVAL (null out,
+ * n_tau out of range), DQMC_ENOMEM, DQMC_ECUDA, DQMC_EUNSTABLE (a singular
+ * matrix at a recompute point). */
 dqmc_status dqmc_su2_measure_tau(dqmc_su2_ctx* ctx, int32_t n_tau, double* out, double* prec_tau);
 
 /* G(tau,0) and G(0,tau) of one chain ([N][N] complex each, host), reached as
  * dqmc_su2_measure_tau reaches them (wrapped from the last recompute point at
- * or below tau). */
+ * or below tau).  Errors: DQMC_ESTATE, DQMC_EINVAL (chain or tau out of range,
+ * a null output), DQMC_ENOMEM, DQMC_ECUDA, DQMC_EUNSTABLE. */
 dqmc_status dqmc_su2_greens_displaced(dqmc_su2_ctx* ctx, int32_t chain, int32_t tau, double* out_t0, double* out_0t);
 
 /* Equal-time correlation functions of every chain's current configuration from
@@ -159,10 +165,13 @@ dqmc_status dqmc_su2_greens_displaced(dqmc_su2_ctx* ctx, int32_t chain, int32_t 
 dqmc_status dqmc_su2_measure_corr(dqmc_su2_ctx* ctx, const int32_t* pair_class, const int32_t* n_class, double* out,
                                   double* phase);
 
-/* Fields of every chain (packed [L_c][N_c + n_bonds_c] int8) and the sweep counter. */
+/* Fields of every chain (packed [L_c][N_c + n_bonds_c] int8, host; out nullable)
+ * and the sweep counter (nullable).  Errors: DQMC_ESTATE, DQMC_ECUDA. */
 dqmc_status dqmc_su2_get_fields(dqmc_su2_ctx* ctx, int8_t* out, uint64_t* sweep_counter);
-/* Replace the fields and the sweep counter; the left chains, G(0) and the
- * phases are recomputed. */
+/* Replace the fields (host, packed as dqmc_su2_get_fields writes them) and the
+ * sweep counter; the left chains, G(0) and the phases are recomputed.  Every
+ * value is checked first; an invalid one returns DQMC_EINVAL and changes
+ * nothing.  Errors: DQMC_ESTATE, DQMC_EINVAL, DQMC_ECUDA, DQMC_EUNSTABLE. */
 dqmc_status dqmc_su2_set_fields(dqmc_su2_ctx* ctx, const int8_t* in, uint64_t sweep_counter);
 
 const char* dqmc_su2_last_error(const dqmc_su2_ctx* ctx);
