@@ -7,6 +7,14 @@
 * `rebin` and `jackknife`: error bars of sign-weighted averages
   <O> = <O s> / <s> from per-sample data, as the paper's bin analysis does
   (Sec. 5.3: bins of measurements, then jackknife over bins for ratios).
+* `reciprocal_vectors`, `k_quantisation`, `momenta`: the momentum grid of a
+  periodic Bravais lattice with unit vectors a_1, a_2 and periodicity vectors
+  L_1, L_2 (Sec. 3.2, the Lattice type: a_i . g_j = 2 pi delta_ij and the
+  quantisation k = n b_1 + m b_2 of Eq. k.quant; tilted lattices included).
+* `structure_factor` and `obser_latt`: the orbital-resolved correlation
+  function S_ab(k, tau) of an Obser_Latt observable (Sec. 5.1, Eq. s with its
+  correlated part s_corr and background part s_back) from per-class sums of a
+  multi-orbital lattice, and its sign-reweighted jackknife over bins.
 """
 from __future__ import annotations
 
@@ -49,3 +57,109 @@ def jackknife(obs_sign: np.ndarray, sign: np.ndarray):
     loo = (tot_o[None] - os_) / (tot_s - s).reshape(sh)          # leave-one-out estimates
     err = np.sqrt((n - 1) / n * ((loo - loo.mean(axis=0)) ** 2).sum(axis=0))
     return mean, err
+
+
+def reciprocal_vectors(a1, a2):
+    """g_1, g_2 with a_i . g_j = 2 pi delta_ij (two dimensions)."""
+    A = np.array([a1, a2], dtype=np.float64)
+    G = 2.0 * np.pi * np.linalg.inv(A).T          # rows g_j: A @ G.T = 2 pi 1
+    return G[0], G[1]
+
+
+def k_quantisation(L1, L2, g1, g2):
+    """b_1, b_2 of the momentum grid k = n b_1 + m b_2 allowed by the periodicity
+    vectors L_1, L_2 (e^{i k . L_i} = 1), as the paper writes them:
+        b_1 = 2 pi [(L_2.g_2) g_1 - (L_2.g_1) g_2] / D,
+        b_2 = 2 pi [(L_1.g_1) g_2 - (L_1.g_2) g_1] / D,
+        D = (L_1.g_1)(L_2.g_2) - (L_1.g_2)(L_2.g_1)."""
+    L1, L2, g1, g2 = (np.asarray(v, dtype=np.float64) for v in (L1, L2, g1, g2))
+    d = (L1 @ g1) * (L2 @ g2) - (L1 @ g2) * (L2 @ g1)
+    b1 = 2.0 * np.pi / d * ((L2 @ g2) * g1 - (L2 @ g1) * g2)
+    b2 = 2.0 * np.pi / d * ((L1 @ g1) * g2 - (L1 @ g2) * g1)
+    return b1, b2
+
+
+def momenta(a1, a2, L1, L2) -> np.ndarray:
+    """The N_unit_cell momenta of the lattice: one k = n b_1 + m b_2 per class
+    modulo the reciprocal lattice, the smallest (m, n) in lexicographic order
+    representing each class (for L_1 = l_1 a_1, L_2 = l_2 a_2 the cell-index
+    order n + l_1 m of `translation_classes_square`).  Returns [N_unit_cell, 2]."""
+    a1, a2, L1, L2 = (np.asarray(v, dtype=np.float64) for v in (a1, a2, L1, L2))
+    n_cells = int(round(abs(np.linalg.det(np.array([L1, L2]))) / abs(np.linalg.det(np.array([a1, a2])))))
+    g1, g2 = reciprocal_vectors(a1, a2)
+    b1, b2 = k_quantisation(L1, L2, g1, g2)
+    m, n = np.meshgrid(np.arange(n_cells), np.arange(n_cells), indexing="ij")
+    ks = n.reshape(-1, 1) * b1 + m.reshape(-1, 1) * b2
+    frac = np.stack([ks @ a1, ks @ a2], axis=1) / (2.0 * np.pi)     # k in units of g_1, g_2
+    key = np.round((frac % 1.0) * 1e8).astype(np.int64) % 100000000
+    _, first = np.unique(key, axis=0, return_index=True)
+    first = np.sort(first)
+    if first.size != n_cells:
+        raise ValueError(f"found {first.size} momenta for {n_cells} unit cells")
+    return ks[first]
+
+
+def _is_zero_momentum(k, a1, a2) -> np.ndarray:
+    frac = np.stack([np.asarray(k) @ np.asarray(a1, float), np.asarray(k) @ np.asarray(a2, float)], axis=-1)
+    frac = frac / (2.0 * np.pi)
+    return np.all(np.abs(frac - np.round(frac)) < 1e-9, axis=-1)
+
+
+def structure_factor(C, r_cells, a1, a2, k, n_cells: int, n_orb: int = 1, O_mean=None) -> np.ndarray:
+    """S_ab(k) = (1/N_cell) sum_d e^{i k . R_d} C(d, a, b) - N_cell <O_a><O_b> delta(k).
+
+    C: [..., n_class] sums of <O_x O_y> over the pairs of each class, classes
+    ordered as n_orb^2 d + n_orb a + b for the cell displacement d = cell(y) -
+    cell(x) and orbitals a of x, b of y (as `translation_classes_square` and
+    `translation_classes_honeycomb` number them); leading dimensions (bins,
+    tau) are kept.  With x = (i, a), y = (j, b) the phase e^{i k . R_d} is the
+    paper's e^{-i k . (i - j)} (Eq. s_corr).  r_cells: [n_class, 2] cell
+    displacement of each class in units of a_1, a_2.  k: [n_k, 2].
+    O_mean: [..., n_orb] the per-orbital means <O_a> = (1/N_cell) sum_i <O_ia>
+    (Eq. o); when given, the background N_cell <O_a><O_b> at k = 0 (Eq. s_back)
+    is subtracted.  Returns [..., n_k, n_orb, n_orb] complex."""
+    C = np.asarray(C)
+    no2 = n_orb * n_orb
+    if C.shape[-1] % no2:
+        raise ValueError("the number of classes is not a multiple of n_orb^2")
+    n_d = C.shape[-1] // no2
+    R = np.asarray(r_cells, dtype=np.float64).reshape(n_d, no2, 2)[:, 0, :]
+    Rv = R[:, :1] * np.asarray(a1, float) + R[:, 1:2] * np.asarray(a2, float)   # [n_d, 2]
+    phase = np.exp(1j * (np.asarray(k, dtype=np.float64) @ Rv.T))                # [n_k, n_d]
+    Cd = C.reshape(C.shape[:-1] + (n_d, n_orb, n_orb))
+    S = np.einsum("kd,...dab->...kab", phase, Cd) / float(n_cells)
+    if O_mean is not None:
+        O = np.asarray(O_mean)
+        back = float(n_cells) * O[..., :, None] * O[..., None, :]                 # [..., n_orb, n_orb]
+        zero = _is_zero_momentum(k, a1, a2)
+        S = S - zero[:, None, None] * back[..., None, :, :]
+    return S
+
+
+def obser_latt(C_sign, sign, r_cells, a1, a2, k, n_cells: int, n_orb: int = 1, O_sign=None):
+    """Bin analysis of an Obser_Latt observable (Sec. 5.1 and 5.3): from the
+    per-bin means of the sign-weighted class sums C s ([n_bins, ..., n_class]),
+    of the sign s ([n_bins]) and optionally of the sign-weighted per-orbital
+    means O s ([n_bins, ..., n_orb]), the estimate S_ab(k) = structure factor of
+    <C s>/<s> with the background of <O s>/<s>, and its jackknife error over
+    bins (leave-one-bin-out ratios, real and imaginary parts separately).
+    Returns (mean, err_re, err_im), each [..., n_k, n_orb, n_orb]."""
+    Cs = np.asarray(C_sign, dtype=np.float64)
+    s = np.asarray(sign, dtype=np.float64)
+    n = s.shape[0]
+    if n < 2:
+        raise ValueError("need at least two bins")
+    Os = None if O_sign is None else np.asarray(O_sign, dtype=np.float64)
+
+    def estimate(csum, osum, ssum):
+        return structure_factor(csum / ssum, r_cells, a1, a2, k, n_cells, n_orb,
+                                None if osum is None else osum / ssum)
+
+    tot_c, tot_s = Cs.sum(axis=0), s.sum()
+    tot_o = None if Os is None else Os.sum(axis=0)
+    mean = estimate(tot_c, tot_o, tot_s)
+    loo = np.stack([estimate(tot_c - Cs[b], None if Os is None else tot_o - Os[b], tot_s - s[b])
+                    for b in range(n)])
+    dev = loo - loo.mean(axis=0)
+    f = (n - 1) / n
+    return mean, np.sqrt(f * (dev.real ** 2).sum(axis=0)), np.sqrt(f * (dev.imag ** 2).sum(axis=0))

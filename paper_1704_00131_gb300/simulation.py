@@ -45,6 +45,15 @@ class Simulation:
           site and flavor) and "szz_tau" (sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)>)
     corr: (pair_class per model, n_class per model) -> "corr_zz", "corr_nn",
           "corr_pm", "corr_gf" per class
+    lattice: with `corr`, (a1, a2, L1, L2, n_orb, r_cells) of the Bravais
+          lattice (unit vectors, periodicity vectors, orbitals per cell and the
+          cell displacement of each class, as `workloads.translation_classes_*`
+          returns it) -> "corr_zz_k", "corr_nn_k", "corr_pm_k", "corr_gf_k": the
+          orbital-resolved S_ab(k) [n_k, n_orb, n_orb] of each correlation at the
+          momenta "k" (`analysis.momenta`), Eq. s of Sec. 5.1; the density's
+          background N_cell <n_a><n_b> at k = 0 is subtracted with <n_a> from the
+          local sum_s <c+ c> of the same bins.  Their error is
+          err(Re) + 1j err(Im) (jackknife over bins).
     The energy estimator ("kin", "pot", "part", "ener") comes from the ensemble's
     own measurement window (the ensemble must be created with measure=True).
     Chains of different models are pooled, so `tau` and `corr` need a single
@@ -52,9 +61,11 @@ class Simulation:
     """
 
     def __init__(self, ensemble, n_bins: int, sweeps_per_bin: int, warmup: int = 0, tau=None, corr=None,
-                 energy: bool = True):
+                 energy: bool = True, lattice=None):
         if n_bins < 2 or sweeps_per_bin < 1 or warmup < 0:
             raise ValueError("need n_bins >= 2, sweeps_per_bin >= 1, warmup >= 0")
+        if lattice is not None and corr is None:
+            raise ValueError("lattice needs corr")
         self.ens = ensemble
         self.n_bins = n_bins
         self.sweeps_per_bin = sweeps_per_bin
@@ -62,6 +73,7 @@ class Simulation:
         self.tau = tau
         self.corr = corr
         self.energy = energy
+        self.lattice = lattice
 
     def _one_bin(self):
         ens = self.ens
@@ -163,6 +175,18 @@ class Simulation:
             data = np.array([b[k] for b, _ in bins])
             sg = e_signs if k in ("kin", "pot", "part", "ener") else signs
             res.mean[k], res.error[k] = analysis.jackknife(data, sg)
+        if self.lattice is not None:
+            a1, a2, L1, L2, n_orb, r_cells = self.lattice
+            k = analysis.momenta(a1, a2, L1, L2)
+            n_cells = k.shape[0]
+            res.mean["k"] = k
+            gf = np.array([b["corr_gf"] for b, _ in bins])
+            dens = gf[:, [(n_orb + 1) * a for a in range(n_orb)]] / n_cells   # sum_i n_ia / N_cell (class d = 0, a, a)
+            for name in ("corr_zz", "corr_nn", "corr_pm", "corr_gf"):
+                data = np.array([b[name] for b, _ in bins])
+                m, er, ei = analysis.obser_latt(data, signs, r_cells, a1, a2, k, n_cells, n_orb,
+                                                O_sign=dens if name == "corr_nn" else None)
+                res.mean[name + "_k"], res.error[name + "_k"] = m, er + 1j * ei
         if self.tau is not None or self.corr is not None:
             res.mean_sign = float(signs.mean() / self.ens.n_chains)   # per chain and sweep
         else:

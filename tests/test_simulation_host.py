@@ -12,8 +12,9 @@ class _Model:
 class FakeEnsemble:
     """Deterministic stand-in with the measurement calls of dqmc.Ensemble."""
 
-    def __init__(self, n_chains=3, L=4, seed=0):
+    def __init__(self, n_chains=3, L=4, seed=0, n_class=2):
         self.n_chains = n_chains
+        self.n_class = n_class
         self.L = L
         self.seed = seed
         self.counter = 0                                # sweeps done: the random numbers follow from it
@@ -41,7 +42,7 @@ class FakeEnsemble:
                 f[rng.integers(self.L), rng.integers(4)] *= -1
             sg = np.where(rng.random((self.n_chains, 2)) < 0.9, 1, -1).astype(np.int32)
             obs = rng.random((self.n_chains, self.L + 1, 2, 3))
-            corr = rng.random((self.n_chains, 2, 4))
+            corr = rng.random((self.n_chains, self.n_class, 4))
             en = rng.random((self.n_chains, 4))
             s = np.prod(sg, axis=1)
             self.e += 2 * s[:, None] * en                   # two measurements per sweep
@@ -125,3 +126,30 @@ def test_checkpoint_of_another_run_is_rejected(tmp_path):
         Simulation(FakeEnsemble(), n_bins=4, sweeps_per_bin=2).run(checkpoint=path)
     with pytest.raises(ValueError):
         Simulation(FakeEnsemble(n_chains=2), n_bins=3, sweeps_per_bin=2).run(checkpoint=path)
+
+
+def test_lattice_resolved_structure_factors():
+    """With a lattice the bin driver turns the per-class correlation bins into
+    S_ab(k): the sign-reweighted pooled class sums through analysis.structure_factor,
+    the density's background from the local sum_s <c+ c> at d = 0."""
+    from paper_1704_00131_gb300 import analysis as A
+    from paper_1704_00131_gb300 import workloads as W
+    L1, L2 = 2, 2
+    cls, ncls, r = W.translation_classes_honeycomb(L1, L2)
+    a1, a2 = np.array([1.0, 0.0]), np.array([0.5, np.sqrt(3.0) / 2.0])
+    ens = FakeEnsemble(n_class=ncls)
+    sim = Simulation(ens, n_bins=4, sweeps_per_bin=3, corr=([cls], [ncls]), lattice=(a1, a2, L1 * a1, L2 * a2, 2, r))
+    res = sim.run()
+    s = np.array([x[0] for x in ens.log])                   # [sweeps, chains]
+    corr = np.array([x[2] for x in ens.log])                # [sweeps, chains, class, 4]
+    pooled = (s[:, :, None, None] * corr).sum(axis=(0, 1)) / s.sum()
+    k = A.momenta(a1, a2, L1 * a1, L2 * a2)
+    assert np.abs(res.mean["k"] - k).max() == 0.0
+    dens = pooled[[0, 3], 3] / (L1 * L2)
+    want_nn = A.structure_factor(pooled[:, 1], r, a1, a2, k, L1 * L2, 2, O_mean=dens)
+    want_zz = A.structure_factor(pooled[:, 0], r, a1, a2, k, L1 * L2, 2)
+    assert np.abs(res.mean["corr_nn_k"] - want_nn).max() < 1e-12
+    assert np.abs(res.mean["corr_zz_k"] - want_zz).max() < 1e-12
+    assert res.error["corr_nn_k"].shape == want_nn.shape and np.all(res.error["corr_nn_k"].real > 0)
+    with pytest.raises(ValueError):
+        Simulation(ens, n_bins=4, sweeps_per_bin=3, lattice=(a1, a2, L1 * a1, L2 * a2, 2, r))
