@@ -45,7 +45,10 @@ class Simulation:
           site and flavor) and "szz_tau" (sum_xy ph_x ph_y <S^z_x(tau) S^z_y(0)>)
     corr: (pair_class per model, n_class per model) -> "corr_zz", "corr_nn",
           "corr_pm", "corr_gf" per class
-    lattice: with `corr`, (a1, a2, L1, L2, n_orb, r_cells) of the Bravais
+    tau_corr: (n_tau, pair_class per model, n_class per model) -> "gf_tau_r",
+          "szz_tau_r", "nn_tau_r": sum_s <c_xs(tau) c+_ys(0)>, <S^z_x(tau) S^z_y(0)>
+          and <n_x(tau) n_y(0)> per tau and class (`Ensemble.measure_tau_corr`)
+    lattice: with `corr` or `tau_corr`, (a1, a2, L1, L2, n_orb, r_cells) of the Bravais
           lattice (unit vectors, periodicity vectors, orbitals per cell and the
           cell displacement of each class, as `workloads.translation_classes_*`
           returns it) -> "corr_zz_k", "corr_nn_k", "corr_pm_k", "corr_gf_k": the
@@ -53,7 +56,9 @@ class Simulation:
           momenta "k" (`analysis.momenta`), Eq. s of Sec. 5.1; the density's
           background N_cell <n_a><n_b> at k = 0 is subtracted with <n_a> from the
           local sum_s <c+ c> of the same bins.  Their error is
-          err(Re) + 1j err(Im) (jackknife over bins).
+          err(Re) + 1j err(Im) (jackknife over bins).  With `tau_corr` likewise
+          "gf_tau_k", "szz_tau_k", "nn_tau_k" [n_tau + 1, n_k, n_orb, n_orb], the
+          density's background from sum_s G(0,0)_xx = 2 - <n_x>.
     The energy estimator ("kin", "pot", "part", "ener") comes from the ensemble's
     own measurement window (the ensemble must be created with measure=True).
     Chains of different models are pooled, so `tau` and `corr` need a single
@@ -61,11 +66,11 @@ class Simulation:
     """
 
     def __init__(self, ensemble, n_bins: int, sweeps_per_bin: int, warmup: int = 0, tau=None, corr=None,
-                 energy: bool = True, lattice=None):
+                 energy: bool = True, lattice=None, tau_corr=None):
         if n_bins < 2 or sweeps_per_bin < 1 or warmup < 0:
             raise ValueError("need n_bins >= 2, sweeps_per_bin >= 1, warmup >= 0")
-        if lattice is not None and corr is None:
-            raise ValueError("lattice needs corr")
+        if lattice is not None and corr is None and tau_corr is None:
+            raise ValueError("lattice needs corr or tau_corr")
         self.ens = ensemble
         self.n_bins = n_bins
         self.sweeps_per_bin = sweeps_per_bin
@@ -74,6 +79,7 @@ class Simulation:
         self.corr = corr
         self.energy = energy
         self.lattice = lattice
+        self.tau_corr = tau_corr
 
     def _one_bin(self):
         ens = self.ens
@@ -102,6 +108,14 @@ class Simulation:
                     sign = sgc
                 for q, name in enumerate(("corr_zz", "corr_nn", "corr_pm", "corr_gf")):
                     acc[name] = acc.get(name, 0.0) + (sgc[:, None] * c[:, :, q]).sum(axis=0)
+            if self.tau_corr is not None:
+                n_tau, classes, n_class = self.tau_corr
+                o, sgt = ens.measure_tau_corr(n_tau, classes, n_class)
+                sgt = sgt.astype(np.float64)
+                if sign is None:
+                    sign = sgt
+                for q, name in enumerate(("gf_tau_r", "szz_tau_r", "nn_tau_r")):
+                    acc[name] = acc.get(name, 0.0) + (sgt[:, None, None] * o[..., q]).sum(axis=0)
             if sign is not None:
                 s_acc += sign.sum()
         out = {k: v / self.sweeps_per_bin for k, v in acc.items()}
@@ -180,14 +194,23 @@ class Simulation:
             k = analysis.momenta(a1, a2, L1, L2)
             n_cells = k.shape[0]
             res.mean["k"] = k
-            gf = np.array([b["corr_gf"] for b, _ in bins])
-            dens = gf[:, [(n_orb + 1) * a for a in range(n_orb)]] / n_cells   # sum_i n_ia / N_cell (class d = 0, a, a)
-            for name in ("corr_zz", "corr_nn", "corr_pm", "corr_gf"):
+            local = [(n_orb + 1) * a for a in range(n_orb)]                  # classes (d = 0, a, a)
+            todo = []
+            if self.corr is not None:
+                gf = np.array([b["corr_gf"] for b, _ in bins])
+                dens = gf[:, local] / n_cells                                   # sum_i n_ia / N_cell, sign-weighted
+                todo += [(name, name + "_k", dens if name == "corr_nn" else None)
+                         for name in ("corr_zz", "corr_nn", "corr_pm", "corr_gf")]
+            if self.tau_corr is not None:
+                g0 = np.array([b["gf_tau_r"] for b, _ in bins])[:, 0, :]       # tau = 0: sum_s G(0,0)_xx = 2 - n_x
+                dens_t = 2.0 * signs[:, None] - g0[:, local] / n_cells
+                todo += [(name, name[:-2] + "_k", dens_t if name == "nn_tau_r" else None)
+                         for name in ("gf_tau_r", "szz_tau_r", "nn_tau_r")]
+            for name, out, dens_b in todo:
                 data = np.array([b[name] for b, _ in bins])
-                m, er, ei = analysis.obser_latt(data, signs, r_cells, a1, a2, k, n_cells, n_orb,
-                                                O_sign=dens if name == "corr_nn" else None)
-                res.mean[name + "_k"], res.error[name + "_k"] = m, er + 1j * ei
-        if self.tau is not None or self.corr is not None:
+                m, er, ei = analysis.obser_latt(data, signs, r_cells, a1, a2, k, n_cells, n_orb, O_sign=dens_b)
+                res.mean[out], res.error[out] = m, er + 1j * ei
+        if self.tau is not None or self.corr is not None or self.tau_corr is not None:
             res.mean_sign = float(signs.mean() / self.ens.n_chains)   # per chain and sweep
         else:
             res.mean_sign = float(np.nanmean(e_signs))                 # per measurement

@@ -23,6 +23,7 @@ class FakeEnsemble:
         self.ss = np.zeros(n_chains)
         self.nm = np.zeros(n_chains, dtype=np.int64)
         self.log = []                                   # (sign, obs, corr) per sweep
+        self.log_tau = []                               # time-displaced class sums per sweep
 
     def model_of(self, c):
         return _Model()
@@ -57,6 +58,13 @@ class FakeEnsemble:
     def measure_tau(self, n_tau, phases):
         sg, obs, _ = self.cur
         return obs, sg, np.zeros(2)
+
+    def measure_tau_corr(self, n_tau, classes, n_class):
+        sg, obs, corr = self.cur
+        rng = np.random.default_rng([self.seed, self.counter, 7])
+        out = rng.random((self.n_chains, n_tau + 1, self.n_class, 3))
+        self.log_tau.append(out)
+        return out, np.prod(sg, axis=1).astype(np.int32)
 
     def measure_corr(self, classes, n_class):
         sg, _, corr = self.cur
@@ -153,3 +161,29 @@ def test_lattice_resolved_structure_factors():
     assert res.error["corr_nn_k"].shape == want_nn.shape and np.all(res.error["corr_nn_k"].real > 0)
     with pytest.raises(ValueError):
         Simulation(ens, n_bins=4, sweeps_per_bin=3, lattice=(a1, a2, L1 * a1, L2 * a2, 2, r))
+
+
+def test_time_displaced_structure_factors():
+    """tau_corr with a lattice: S_ab(k, tau) of the three time-displaced
+    correlations from the pooled class sums; the density's background from
+    sum_s G(0,0)_xx = 2 - <n_x> at tau = 0."""
+    from paper_1704_00131_gb300 import analysis as A
+    from paper_1704_00131_gb300 import workloads as W
+    L1, L2, n_tau = 2, 2, 3
+    cls, ncls, r = W.translation_classes_honeycomb(L1, L2)
+    a1, a2 = np.array([1.0, 0.0]), np.array([0.5, np.sqrt(3.0) / 2.0])
+    ens = FakeEnsemble(n_class=ncls)
+    sim = Simulation(ens, n_bins=3, sweeps_per_bin=2, energy=False, tau_corr=(n_tau, [cls], [ncls]),
+                     lattice=(a1, a2, L1 * a1, L2 * a2, 2, r))
+    res = sim.run()
+    s = np.array([x[0] for x in ens.log])                   # [sweeps, chains]
+    o = np.array(ens.log_tau)                               # [sweeps, chains, tau, class, 3]
+    pooled = (s[:, :, None, None, None] * o).sum(axis=(0, 1)) / s.sum()
+    k = A.momenta(a1, a2, L1 * a1, L2 * a2)
+    dens = 2.0 - pooled[0, [0, 3], 0] / (L1 * L2)
+    want_nn = A.structure_factor(pooled[..., 2], r, a1, a2, k, L1 * L2, 2, O_mean=dens)
+    want_gf = A.structure_factor(pooled[..., 0], r, a1, a2, k, L1 * L2, 2)
+    assert res.mean["nn_tau_k"].shape == (n_tau + 1, L1 * L2, 2, 2)
+    assert np.abs(res.mean["nn_tau_k"] - want_nn).max() < 1e-12
+    assert np.abs(res.mean["gf_tau_k"] - want_gf).max() < 1e-12
+    assert "szz_tau_k" in res.error and res.mean_sign != 0.0
