@@ -4,9 +4,10 @@
   displacement class, S(q) = (1/N) sum_r e^{i q.r} C(r) with C(r) the sum over
   the pairs of the class (the R -> K transform the paper's analysis programs
   apply to Obser_Latt data, Sec. 5.3).
-* `rebin` and `jackknife`: error bars of sign-weighted averages
-  <O> = <O s> / <s> from per-sample data, as the paper's bin analysis does
-  (Sec. 5.3: bins of measurements, then jackknife over bins for ratios).
+* `rebin`, `skip_and_rebin` and `jackknife`: error bars of sign-weighted
+  averages <O> = <O s> / <s> from per-bin data, as the paper's bin analysis
+  does (Sec. 5.3: n_skip and N_rebin, then the delete-1 jackknife over bins,
+  Eqs. jack_mean and jack_error).
 * `reciprocal_vectors`, `k_quantisation`, `momenta`: the momentum grid of a
   periodic Bravais lattice with unit vectors a_1, a_2 and periodicity vectors
   L_1, L_2 (Sec. 3.2, the Lattice type: a_i . g_j = 2 pi delta_ij and the
@@ -44,7 +45,10 @@ def rebin(x: np.ndarray, n_bins: int) -> np.ndarray:
 
 
 def jackknife(obs_sign: np.ndarray, sign: np.ndarray):
-    """Sign-reweighted mean <O> = sum(O s) / sum(s) and its jackknife error.
+    """Sign-reweighted <O> = <O s> / <s> by the delete-1 jackknife over bins
+    (Sec. 5.3): with f_(i) the ratio of the means without bin i, the estimate is
+    f_(.) = (1/N) sum_i f_(i) (Eq. jack_mean) and its error
+    sqrt((N-1)/N sum_i (f_(i) - f_(.))^2) (Eq. jack_error).
     obs_sign: per-bin means of O * s, shape [n_bins, ...]; sign: per-bin means of s."""
     os_ = np.asarray(obs_sign, dtype=np.float64)
     s = np.asarray(sign, dtype=np.float64)
@@ -53,10 +57,24 @@ def jackknife(obs_sign: np.ndarray, sign: np.ndarray):
         raise ValueError("need at least two bins")
     sh = (n,) + (1,) * (os_.ndim - 1)
     tot_o, tot_s = os_.sum(axis=0), s.sum()
-    mean = tot_o / tot_s
-    loo = (tot_o[None] - os_) / (tot_s - s).reshape(sh)          # leave-one-out estimates
-    err = np.sqrt((n - 1) / n * ((loo - loo.mean(axis=0)) ** 2).sum(axis=0))
+    loo = (tot_o[None] - os_) / (tot_s - s).reshape(sh)          # f_(i)
+    mean = loo.mean(axis=0)                                        # f_(.)
+    err = np.sqrt((n - 1) / n * ((loo - mean) ** 2).sum(axis=0))
     return mean, err
+
+
+def skip_and_rebin(bins: np.ndarray, n_skip: int = 0, n_rebin: int = 1) -> np.ndarray:
+    """The analysis parameters n_skip and N_rebin of Sec. 5.3: drop the first
+    n_skip bins (warm-up), then merge every n_rebin consecutive bins into one
+    (their mean; a tail that does not fill a merged bin is dropped)."""
+    b = np.asarray(bins, dtype=np.float64)
+    if n_skip < 0 or n_rebin < 1:
+        raise ValueError("need n_skip >= 0 and n_rebin >= 1")
+    b = b[n_skip:]
+    m = b.shape[0] // n_rebin
+    if m < 1:
+        raise ValueError("no bins left after n_skip and n_rebin")
+    return b[: m * n_rebin].reshape((m, n_rebin) + b.shape[1:]).mean(axis=1)
 
 
 def reciprocal_vectors(a1, a2):
@@ -136,14 +154,22 @@ def structure_factor(C, r_cells, a1, a2, k, n_cells: int, n_orb: int = 1, O_mean
     return S
 
 
-def obser_latt(C_sign, sign, r_cells, a1, a2, k, n_cells: int, n_orb: int = 1, O_sign=None):
+def obser_latt(C_sign, sign, r_cells, a1, a2, k, n_cells: int, n_orb: int = 1, O_sign=None, cov: bool = False):
     """Bin analysis of an Obser_Latt observable (Sec. 5.1 and 5.3): from the
     per-bin means of the sign-weighted class sums C s ([n_bins, ..., n_class]),
     of the sign s ([n_bins]) and optionally of the sign-weighted per-orbital
-    means O s ([n_bins, ..., n_orb]), the estimate S_ab(k) = structure factor of
-    <C s>/<s> with the background of <O s>/<s>, and its jackknife error over
-    bins (leave-one-bin-out ratios, real and imaginary parts separately).
-    Returns (mean, err_re, err_im), each [..., n_k, n_orb, n_orb]."""
+    means O s ([n_bins, ..., n_orb]), the structure factor S_ab(k) of <C s>/<s>
+    with the background of <O s>/<s>, by the delete-1 jackknife over bins: the
+    mean of the leave-one-bin-out estimates f_(i) and the error
+    sqrt((N-1)/N sum_i (f_(i) - f_(.))^2), real and imaginary parts separately.
+    Returns (mean, err_re, err_im), each [..., n_k, n_orb, n_orb]; with cov and a
+    leading tau axis (C_sign [n_bins, n_tau, n_class]) also the covariance of
+    Re S between imaginary times (the N_Cov option of Sec. 5.3),
+    COV[t, t'] = (N-1)/N sum_i (f_(i)(t) - f_(.)(t)) (f_(i)(t') - f_(.)(t')),
+    [n_tau, n_tau, n_k, n_orb, n_orb]; its diagonal is err_re^2, and for a
+    plain mean it is the paper's (1/N_bin) <(S(t) - <S(t)>)(S(t') - <S(t')>)>
+    with the average over bins taken with the bias correction of Eq. jack_error
+    (1/(N_bin - 1)), so that the diagonal is the squared jackknife error."""
     Cs = np.asarray(C_sign, dtype=np.float64)
     s = np.asarray(sign, dtype=np.float64)
     n = s.shape[0]
@@ -157,9 +183,15 @@ def obser_latt(C_sign, sign, r_cells, a1, a2, k, n_cells: int, n_orb: int = 1, O
 
     tot_c, tot_s = Cs.sum(axis=0), s.sum()
     tot_o = None if Os is None else Os.sum(axis=0)
-    mean = estimate(tot_c, tot_o, tot_s)
     loo = np.stack([estimate(tot_c - Cs[b], None if Os is None else tot_o - Os[b], tot_s - s[b])
-                    for b in range(n)])
-    dev = loo - loo.mean(axis=0)
+                    for b in range(n)])                                     # f_(i)
+    mean = loo.mean(axis=0)                                                  # f_(.)
+    dev = loo - mean
     f = (n - 1) / n
-    return mean, np.sqrt(f * (dev.real ** 2).sum(axis=0)), np.sqrt(f * (dev.imag ** 2).sum(axis=0))
+    out = (mean, np.sqrt(f * (dev.real ** 2).sum(axis=0)), np.sqrt(f * (dev.imag ** 2).sum(axis=0)))
+    if cov:
+        if Cs.ndim != 3:
+            raise ValueError("cov needs C_sign of shape [n_bins, n_tau, n_class]")
+        d = dev.real                                                         # [n_bins, n_tau, n_k, a, b]
+        out = out + (f * np.einsum("itkab,iukab->tukab", d, d),)
+    return out

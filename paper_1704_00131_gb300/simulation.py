@@ -59,6 +59,8 @@ class Simulation:
           err(Re) + 1j err(Im) (jackknife over bins).  With `tau_corr` likewise
           "gf_tau_k", "szz_tau_k", "nn_tau_k" [n_tau + 1, n_k, n_orb, n_orb], the
           density's background from sum_s G(0,0)_xx = 2 - <n_x>.
+    n_skip, n_rebin: the analysis drops the first n_skip bins and merges every
+          n_rebin consecutive bins (the paper's n_skip and N_rebin, Sec. 5.3).
     The energy estimator ("kin", "pot", "part", "ener") comes from the ensemble's
     own measurement window (the ensemble must be created with measure=True).
     Chains of different models are pooled, so `tau` and `corr` need a single
@@ -66,9 +68,11 @@ class Simulation:
     """
 
     def __init__(self, ensemble, n_bins: int, sweeps_per_bin: int, warmup: int = 0, tau=None, corr=None,
-                 energy: bool = True, lattice=None, tau_corr=None):
+                 energy: bool = True, lattice=None, tau_corr=None, n_skip: int = 0, n_rebin: int = 1):
         if n_bins < 2 or sweeps_per_bin < 1 or warmup < 0:
             raise ValueError("need n_bins >= 2, sweeps_per_bin >= 1, warmup >= 0")
+        if n_skip < 0 or n_rebin < 1 or (n_bins - n_skip) // n_rebin < 2:
+            raise ValueError("need n_skip >= 0, n_rebin >= 1 and two bins left after them")
         if lattice is not None and corr is None and tau_corr is None:
             raise ValueError("lattice needs corr or tau_corr")
         self.ens = ensemble
@@ -80,6 +84,8 @@ class Simulation:
         self.energy = energy
         self.lattice = lattice
         self.tau_corr = tau_corr
+        self.n_skip = n_skip
+        self.n_rebin = n_rebin
 
     def _one_bin(self):
         ens = self.ens
@@ -180,13 +186,17 @@ class Simulation:
 
     def _analyse(self, bins) -> Result:
         res = Result(self.n_bins, self.sweeps_per_bin, 0.0, complete=len(bins) == self.n_bins)
-        if len(bins) < 2:
+        if (len(bins) - self.n_skip) // self.n_rebin < 2:
             return res
+
+        def col(values):                       # per-bin values after n_skip and N_rebin
+            return analysis.skip_and_rebin(np.array(values), self.n_skip, self.n_rebin)
+
         names = sorted({k for b, _ in bins for k in b if not k.startswith("_")})
-        signs = np.array([s for _, s in bins])
-        e_signs = np.array([b.get("_sign_energy", np.nan) for b, _ in bins])
+        signs = col([s for _, s in bins])
+        e_signs = col([b.get("_sign_energy", np.nan) for b, _ in bins])
         for k in names:
-            data = np.array([b[k] for b, _ in bins])
+            data = col([b[k] for b, _ in bins])
             sg = e_signs if k in ("kin", "pot", "part", "ener") else signs
             res.mean[k], res.error[k] = analysis.jackknife(data, sg)
         if self.lattice is not None:
@@ -197,17 +207,17 @@ class Simulation:
             local = [(n_orb + 1) * a for a in range(n_orb)]                  # classes (d = 0, a, a)
             todo = []
             if self.corr is not None:
-                gf = np.array([b["corr_gf"] for b, _ in bins])
+                gf = col([b["corr_gf"] for b, _ in bins])
                 dens = gf[:, local] / n_cells                                   # sum_i n_ia / N_cell, sign-weighted
                 todo += [(name, name + "_k", dens if name == "corr_nn" else None)
                          for name in ("corr_zz", "corr_nn", "corr_pm", "corr_gf")]
             if self.tau_corr is not None:
-                g0 = np.array([b["gf_tau_r"] for b, _ in bins])[:, 0, :]       # tau = 0: sum_s G(0,0)_xx = 2 - n_x
+                g0 = col([b["gf_tau_r"] for b, _ in bins])[:, 0, :]            # tau = 0: sum_s G(0,0)_xx = 2 - n_x
                 dens_t = 2.0 * signs[:, None] - g0[:, local] / n_cells
                 todo += [(name, name[:-2] + "_k", dens_t if name == "nn_tau_r" else None)
                          for name in ("gf_tau_r", "szz_tau_r", "nn_tau_r")]
             for name, out, dens_b in todo:
-                data = np.array([b[name] for b, _ in bins])
+                data = col([b[name] for b, _ in bins])
                 m, er, ei = analysis.obser_latt(data, signs, r_cells, a1, a2, k, n_cells, n_orb, O_sign=dens_b)
                 res.mean[out], res.error[out] = m, er + 1j * ei
         if self.tau is not None or self.corr is not None or self.tau_corr is not None:

@@ -36,7 +36,11 @@ def test_jackknife_sign_reweighting():
     o = rng.standard_normal(4000) + 1.0
     ob, sb = A.rebin(o * s, 40), A.rebin(s, 40)
     mean, err = A.jackknife(ob[:, None], sb)
-    assert mean[0] == pytest.approx((o * s).sum() / s.sum(), rel=1e-12)
+    # Eq. jack_mean: the mean over i of the ratio without bin i
+    loo = [(ob.sum() - ob[i]) / (sb.sum() - sb[i]) for i in range(40)]
+    assert mean[0] == pytest.approx(np.mean(loo), rel=1e-12)
+    assert err[0] == pytest.approx(np.sqrt(39 / 40 * np.sum((np.array(loo) - np.mean(loo)) ** 2)), rel=1e-12)
+    assert mean[0] == pytest.approx((o * s).sum() / s.sum(), rel=1e-2)
     assert 0 < err[0] < 1.0
     with pytest.raises(ValueError):
         A.rebin(o, 5000)
@@ -171,12 +175,47 @@ def test_obser_latt_jackknife():
                                 O_sign=np.tile(O, (5, 1)) * 0.5)
     assert np.abs(mean - A.structure_factor(C, r, A1, A2H, k, ncell, 2, O_mean=O)).max() < 1e-12
     assert er.max() < 1e-12 and ei.max() < 1e-12
-    # sign-reweighted bins: the mean is the structure factor of sum(C s) / sum(s)
+    # sign-reweighted bins: the mean of the leave-one-bin-out structure factors (Eq. jack_mean)
     s = np.where(rng.random(20) < 0.8, 1.0, -1.0) * (0.5 + rng.random(20))
     Cb = rng.standard_normal((20, ncls)) * s[:, None]
     mean, er, ei = A.obser_latt(Cb, s, r, A1, A2H, k, ncell, 2)
-    ref = A.structure_factor(Cb.sum(0) / s.sum(), r, A1, A2H, k, ncell, 2)
-    assert np.abs(mean - ref).max() < 1e-12
+    loo = np.array([A.structure_factor((Cb.sum(0) - Cb[i]) / (s.sum() - s[i]), r, A1, A2H, k, ncell, 2)
+                    for i in range(20)])
+    assert np.abs(mean - loo.mean(axis=0)).max() < 1e-12
+    assert np.abs(er - np.sqrt(19 / 20 * ((loo.real - loo.real.mean(0)) ** 2).sum(0))).max() < 1e-12
     assert er.max() > 0 and np.isfinite(er).all() and np.isfinite(ei).all()
     with pytest.raises(ValueError):
         A.obser_latt(Cb[:1], s[:1], r, A1, A2H, k, ncell, 2)
+
+
+def test_covariance_between_imaginary_times():
+    """N_Cov: for plain means (unit signs) the jackknife covariance of S(k, tau)
+    is the paper's (1/N_bin) <(S(tau) - <S>)(S(tau') - <S>)> over bins, with the
+    bin average bias-corrected (1/(N_bin - 1)) as in the jackknife error, so its
+    diagonal is the squared error."""
+    L1, L2, n_tau, nb = 2, 2, 3, 12
+    ncell = L1 * L2
+    cls, ncls, r = W.translation_classes_honeycomb(L1, L2)
+    k = A.momenta(A1, A2H, L1 * A1, L2 * A2H)
+    rng = np.random.default_rng(8)
+    base = rng.standard_normal((n_tau + 1, ncls))
+    Cb = base[None] + 0.1 * rng.standard_normal((nb, 1, ncls)) + 0.05 * rng.standard_normal((nb, n_tau + 1, ncls))
+    mean, er, ei, cov = A.obser_latt(Cb, np.ones(nb), r, A1, A2H, k, ncell, 2, cov=True)
+    Sb = A.structure_factor(Cb, r, A1, A2H, k, ncell, 2).real            # per bin [nb, tau, k, a, b]
+    dev = Sb - Sb.mean(axis=0)
+    want = np.einsum("itkab,iukab->tukab", dev, dev) / nb / (nb - 1)      # covariance of the bin mean
+    assert np.abs(cov - want).max() < 1e-12 * max(1.0, np.abs(want).max())
+    assert np.abs(np.einsum("ttkab->tkab", cov) - er ** 2).max() < 1e-12
+    assert np.abs(mean.real - Sb.mean(axis=0)).max() < 1e-12
+    with pytest.raises(ValueError):
+        A.obser_latt(Cb[:, 0], np.ones(nb), r, A1, A2H, k, ncell, 2, cov=True)
+
+
+def test_skip_and_rebin():
+    x = np.arange(11.0)
+    assert np.array_equal(A.skip_and_rebin(x, n_skip=2, n_rebin=3), np.array([3.0, 6.0, 9.0]))
+    assert np.array_equal(A.skip_and_rebin(x), x)
+    with pytest.raises(ValueError):
+        A.skip_and_rebin(x, n_skip=11)
+    with pytest.raises(ValueError):
+        A.skip_and_rebin(x, n_rebin=0)

@@ -5,6 +5,20 @@ import pytest
 from paper_1704_00131_gb300.simulation import Simulation
 
 
+def _jack_mean(num, den, n_bins, f=lambda x: x):
+    """Eq. jack_mean written out: the per-sweep sign-weighted sums num [sweeps, ...]
+    and signs den [sweeps] grouped into n_bins consecutive bins, then the mean over
+    i of f(sum_{b != i} num_b / sum_{b != i} den_b)."""
+    nb = np.array_split(np.asarray(num, dtype=np.float64), n_bins)
+    db = np.array_split(np.asarray(den, dtype=np.float64), n_bins)
+    out = []
+    for i in range(n_bins):
+        N = sum(x.sum(axis=0) for b, x in enumerate(nb) if b != i)
+        D = sum(x.sum() for b, x in enumerate(db) if b != i)
+        out.append(f(N / D))
+    return np.mean(out, axis=0)
+
+
 class _Model:
     N = 4
 
@@ -79,17 +93,20 @@ def test_bins_pool_chains_and_reweight_by_sign():
     s = np.array([x[0] for x in log])                   # [sweeps, chains]
     corr = np.array([x[2] for x in log])                # [sweeps, chains, class, 4]
     en = np.array([x[3] for x in log])
-    want_zz = (s[:, :, None] * corr[:, :, :, 0]).sum(axis=(0, 1)) / s.sum()
+    ss = s.sum(axis=1)                                  # sign summed over chains, per sweep
+    want_zz = _jack_mean((s[:, :, None] * corr[:, :, :, 0]).sum(axis=1), ss, 4)
     assert res.mean["corr_zz"] == pytest.approx(want_zz, rel=1e-12)
-    want_kin = (s * en[:, :, 0]).sum() / s.sum()
+    # a bin's reweighted ratio sits close to the pooled one (the estimate differs by the jackknife's O(1/N_bin))
+    assert res.mean["corr_zz"] == pytest.approx((s[:, :, None] * corr[:, :, :, 0]).sum(axis=(0, 1)) / s.sum(), rel=0.05)
+    want_kin = _jack_mean((s * en[:, :, 0]).sum(axis=1), ss, 4)
     assert res.mean["kin"] == pytest.approx(want_kin, rel=1e-12)
     obs = np.array([x[1] for x in log])                 # [sweeps, chains, tau, fl, 3]
     m = obs[..., 0, 2] - obs[..., 1, 2]
     szz = (m * m[..., :1] + obs[..., 0, 1] + obs[..., 1, 1]) / 4.0
-    want_szz = (s[:, :, None] * szz).sum(axis=(0, 1)) / s.sum()
+    want_szz = _jack_mean((s[:, :, None] * szz).sum(axis=1), ss, 4)
     assert res.mean["szz_tau"] == pytest.approx(want_szz, rel=1e-12)
     gl = obs[..., 0].sum(axis=3) / (2 * 4)
-    assert res.mean["gloc_tau"] == pytest.approx((s[:, :, None] * gl).sum(axis=(0, 1)) / s.sum(), rel=1e-12)
+    assert res.mean["gloc_tau"] == pytest.approx(_jack_mean((s[:, :, None] * gl).sum(axis=1), ss, 4), rel=1e-12)
     assert all(np.all(np.asarray(res.error[k]) > 0) for k in res.mean)
     assert res.mean_sign == pytest.approx(s.mean(), rel=1e-12)
     assert res.n_bins == 4 and res.sweeps_per_bin == 5
@@ -150,12 +167,12 @@ def test_lattice_resolved_structure_factors():
     res = sim.run()
     s = np.array([x[0] for x in ens.log])                   # [sweeps, chains]
     corr = np.array([x[2] for x in ens.log])                # [sweeps, chains, class, 4]
-    pooled = (s[:, :, None, None] * corr).sum(axis=(0, 1)) / s.sum()
     k = A.momenta(a1, a2, L1 * a1, L2 * a2)
     assert np.abs(res.mean["k"] - k).max() == 0.0
-    dens = pooled[[0, 3], 3] / (L1 * L2)
-    want_nn = A.structure_factor(pooled[:, 1], r, a1, a2, k, L1 * L2, 2, O_mean=dens)
-    want_zz = A.structure_factor(pooled[:, 0], r, a1, a2, k, L1 * L2, 2)
+    num = (s[:, :, None, None] * corr).sum(axis=1)
+    want_nn = _jack_mean(num, s.sum(axis=1), 4, lambda p: A.structure_factor(
+        p[:, 1], r, a1, a2, k, L1 * L2, 2, O_mean=p[[0, 3], 3] / (L1 * L2)))
+    want_zz = _jack_mean(num, s.sum(axis=1), 4, lambda p: A.structure_factor(p[:, 0], r, a1, a2, k, L1 * L2, 2))
     assert np.abs(res.mean["corr_nn_k"] - want_nn).max() < 1e-12
     assert np.abs(res.mean["corr_zz_k"] - want_zz).max() < 1e-12
     assert res.error["corr_nn_k"].shape == want_nn.shape and np.all(res.error["corr_nn_k"].real > 0)
@@ -178,12 +195,27 @@ def test_time_displaced_structure_factors():
     res = sim.run()
     s = np.array([x[0] for x in ens.log])                   # [sweeps, chains]
     o = np.array(ens.log_tau)                               # [sweeps, chains, tau, class, 3]
-    pooled = (s[:, :, None, None, None] * o).sum(axis=(0, 1)) / s.sum()
     k = A.momenta(a1, a2, L1 * a1, L2 * a2)
-    dens = 2.0 - pooled[0, [0, 3], 0] / (L1 * L2)
-    want_nn = A.structure_factor(pooled[..., 2], r, a1, a2, k, L1 * L2, 2, O_mean=dens)
-    want_gf = A.structure_factor(pooled[..., 0], r, a1, a2, k, L1 * L2, 2)
+    num = (s[:, :, None, None, None] * o).sum(axis=1)
+    want_nn = _jack_mean(num, s.sum(axis=1), 3, lambda p: A.structure_factor(
+        p[..., 2], r, a1, a2, k, L1 * L2, 2, O_mean=2.0 - p[0, [0, 3], 0] / (L1 * L2)))
+    want_gf = _jack_mean(num, s.sum(axis=1), 3, lambda p: A.structure_factor(p[..., 0], r, a1, a2, k, L1 * L2, 2))
     assert res.mean["nn_tau_k"].shape == (n_tau + 1, L1 * L2, 2, 2)
     assert np.abs(res.mean["nn_tau_k"] - want_nn).max() < 1e-12
     assert np.abs(res.mean["gf_tau_k"] - want_gf).max() < 1e-12
     assert "szz_tau_k" in res.error and res.mean_sign != 0.0
+
+
+def test_skip_and_rebin_bins():
+    """n_skip drops the first bins and n_rebin merges consecutive ones before the
+    jackknife: 6 bins of 2 sweeps with n_skip = 2, n_rebin = 2 analyse as 2 bins of
+    4 sweeps starting at the fifth sweep."""
+    ens = FakeEnsemble()
+    res = Simulation(ens, n_bins=6, sweeps_per_bin=2, corr=([None], [2]), n_skip=2, n_rebin=2, energy=False).run()
+    log = ens.log[4:]
+    s = np.array([x[0] for x in log])
+    corr = np.array([x[2] for x in log])
+    want = _jack_mean((s[:, :, None] * corr[:, :, :, 1]).sum(axis=1), s.sum(axis=1), 2)
+    assert res.mean["corr_nn"] == pytest.approx(want, rel=1e-12)
+    with pytest.raises(ValueError):
+        Simulation(ens, n_bins=4, sweeps_per_bin=2, n_skip=1, n_rebin=2)
