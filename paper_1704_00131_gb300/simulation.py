@@ -26,6 +26,26 @@ import numpy as np
 from . import analysis
 
 
+def _sum_over_ranks(raw: dict) -> dict:
+    """Sum each array of `raw` over the ranks of the default process group (one
+    all-reduce of the concatenated float64 values; CUDA tensors under NCCL)."""
+    import torch
+    import torch.distributed as dist
+    keys = sorted(raw)
+    shapes = [np.shape(raw[k]) for k in keys]
+    flat = np.concatenate([np.asarray(raw[k], dtype=np.float64).ravel() for k in keys])
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.from_numpy(flat).to(dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    flat = t.cpu().numpy()
+    out, off = {}, 0
+    for k, sh in zip(keys, shapes):
+        n = int(np.prod(sh)) if sh else 1
+        out[k] = flat[off:off + n].reshape(sh) if sh else np.float64(flat[off])
+        off += n
+    return out
+
+
 @dataclass
 class Result:
     """Jackknife mean and error over bins of each sign-reweighted observable."""
@@ -61,6 +81,12 @@ class Simulation:
           density's background from sum_s G(0,0)_xx = 2 - <n_x>.
     n_skip, n_rebin: the analysis drops the first n_skip bins and merges every
           n_rebin consecutive bins (the paper's n_skip and N_rebin, Sec. 5.3).
+    distributed: one process per GPU, each with its own ensemble (independent
+          walkers, the paper's one walker per MPI task): at the end of every bin
+          the bin's sums over sweeps and chains are added over all ranks of the
+          default torch.distributed group (one all-reduce per bin, the only
+          exchange), so every rank analyses the same bins of all chains.  Each
+          rank checkpoints its own fields (give each its own path).
     The energy estimator ("kin", "pot", "part", "ener") comes from the ensemble's
     own measurement window (the ensemble must be created with measure=True).
     Chains of different models are pooled, so `tau` and `corr` need a single
@@ -68,7 +94,8 @@ class Simulation:
     """
 
     def __init__(self, ensemble, n_bins: int, sweeps_per_bin: int, warmup: int = 0, tau=None, corr=None,
-                 energy: bool = True, lattice=None, tau_corr=None, n_skip: int = 0, n_rebin: int = 1):
+                 energy: bool = True, lattice=None, tau_corr=None, n_skip: int = 0, n_rebin: int = 1,
+                 distributed: bool = False):
         if n_bins < 2 or sweeps_per_bin < 1 or warmup < 0:
             raise ValueError("need n_bins >= 2, sweeps_per_bin >= 1, warmup >= 0")
         if n_skip < 0 or n_rebin < 1 or (n_bins - n_skip) // n_rebin < 2:
@@ -86,6 +113,11 @@ class Simulation:
         self.tau_corr = tau_corr
         self.n_skip = n_skip
         self.n_rebin = n_rebin
+        self.distributed = distributed
+        if distributed:
+            import torch.distributed as dist
+            if not (dist.is_available() and dist.is_initialized()):
+                raise ValueError("distributed needs an initialised torch.distributed process group")
 
     def _one_bin(self):
         ens = self.ens
@@ -124,18 +156,28 @@ class Simulation:
                     acc[name] = acc.get(name, 0.0) + (sgt[:, None, None] * o[..., q]).sum(axis=0)
             if sign is not None:
                 s_acc += sign.sum()
-        out = {k: v / self.sweeps_per_bin for k, v in acc.items()}
-        s_bin = s_acc / self.sweeps_per_bin
+        raw = dict(acc)                        # sums over the bin's sweeps and this process's chains
+        raw["_s"] = np.float64(s_acc)
         if self.energy:
             e1, ss1, n1 = ens.measure()
-            nm = float((n1 - n0).sum())
-            if nm > 0:
-                de = (e1 - e0).sum(axis=0) / nm                  # sum over chains of sign * O per measurement
-                ds = float((ss1 - ss0).sum()) / nm
-                for q, name in enumerate(("kin", "pot", "part", "ener")):
-                    out[name] = de[q]
-                out["_sign_energy"] = ds
+            raw["_e"] = (e1 - e0).sum(axis=0)
+            raw["_es"] = np.float64((ss1 - ss0).sum())
+            raw["_nm"] = np.float64((n1 - n0).sum())
+        if self.distributed:
+            raw = _sum_over_ranks(raw)         # the chains of every rank in one bin
+        out = {k: v / self.sweeps_per_bin for k, v in raw.items() if not k.startswith("_")}
+        s_bin = float(raw["_s"]) / self.sweeps_per_bin
+        if self.energy and raw["_nm"] > 0:
+            de = raw["_e"] / raw["_nm"]                          # sum over chains of sign * O per measurement
+            for q, name in enumerate(("kin", "pot", "part", "ener")):
+                out[name] = de[q]
+            out["_sign_energy"] = float(raw["_es"] / raw["_nm"])
         return out, s_bin
+
+    def _chains_total(self) -> int:
+        if not self.distributed:
+            return self.ens.n_chains
+        return int(round(float(_sum_over_ranks({"n": np.float64(self.ens.n_chains)})["n"])))
 
     def _save(self, path: str, bins) -> None:
         fields, ctr = self.ens.get_fields()
@@ -221,7 +263,7 @@ class Simulation:
                 m, er, ei = analysis.obser_latt(data, signs, r_cells, a1, a2, k, n_cells, n_orb, O_sign=dens_b)
                 res.mean[out], res.error[out] = m, er + 1j * ei
         if self.tau is not None or self.corr is not None or self.tau_corr is not None:
-            res.mean_sign = float(signs.mean() / self.ens.n_chains)   # per chain and sweep
+            res.mean_sign = float(signs.mean() / self._chains_total())  # per chain and sweep
         else:
             res.mean_sign = float(np.nanmean(e_signs))                 # per measurement
         return res
