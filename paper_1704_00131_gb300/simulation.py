@@ -55,6 +55,7 @@ class Result:
     mean_sign: float
     mean: dict = field(default_factory=dict)
     error: dict = field(default_factory=dict)
+    cov: dict = field(default_factory=dict)   # N_Cov: covariance of Re S(k, tau) between imaginary times
     complete: bool = True          # False when a time budget stopped the run early
 
 
@@ -78,7 +79,9 @@ class Simulation:
           local sum_s <c+ c> of the same bins.  Their error is
           err(Re) + 1j err(Im) (jackknife over bins).  With `tau_corr` likewise
           "gf_tau_k", "szz_tau_k", "nn_tau_k" [n_tau + 1, n_k, n_orb, n_orb], the
-          density's background from sum_s G(0,0)_xx = 2 - <n_x>.
+          density's background from sum_s G(0,0)_xx = 2 - <n_x>; with n_cov also
+          their covariance between imaginary times in `Result.cov`
+          [n_tau + 1, n_tau + 1, n_k, n_orb, n_orb] (the paper's N_Cov).
     n_skip, n_rebin: the analysis drops the first n_skip bins and merges every
           n_rebin consecutive bins (the paper's n_skip and N_rebin, Sec. 5.3).
     distributed: one process per GPU, each with its own ensemble (independent
@@ -95,7 +98,7 @@ class Simulation:
 
     def __init__(self, ensemble, n_bins: int, sweeps_per_bin: int, warmup: int = 0, tau=None, corr=None,
                  energy: bool = True, lattice=None, tau_corr=None, n_skip: int = 0, n_rebin: int = 1,
-                 distributed: bool = False):
+                 distributed: bool = False, n_cov: bool = False):
         if n_bins < 2 or sweeps_per_bin < 1 or warmup < 0:
             raise ValueError("need n_bins >= 2, sweeps_per_bin >= 1, warmup >= 0")
         if n_skip < 0 or n_rebin < 1 or (n_bins - n_skip) // n_rebin < 2:
@@ -114,6 +117,7 @@ class Simulation:
         self.n_skip = n_skip
         self.n_rebin = n_rebin
         self.distributed = distributed
+        self.n_cov = n_cov
         if distributed:
             import torch.distributed as dist
             if not (dist.is_available() and dist.is_initialized()):
@@ -260,8 +264,11 @@ class Simulation:
                          for name in ("gf_tau_r", "szz_tau_r", "nn_tau_r")]
             for name, out, dens_b in todo:
                 data = col([b[name] for b, _ in bins])
-                m, er, ei = analysis.obser_latt(data, signs, r_cells, a1, a2, k, n_cells, n_orb, O_sign=dens_b)
-                res.mean[out], res.error[out] = m, er + 1j * ei
+                want_cov = self.n_cov and name.endswith("_tau_r")
+                r = analysis.obser_latt(data, signs, r_cells, a1, a2, k, n_cells, n_orb, O_sign=dens_b, cov=want_cov)
+                res.mean[out], res.error[out] = r[0], r[1] + 1j * r[2]
+                if want_cov:
+                    res.cov[out] = r[3]
         if self.tau is not None or self.corr is not None or self.tau_corr is not None:
             res.mean_sign = float(signs.mean() / self._chains_total())  # per chain and sweep
         else:

@@ -191,7 +191,7 @@ def test_time_displaced_structure_factors():
     a1, a2 = np.array([1.0, 0.0]), np.array([0.5, np.sqrt(3.0) / 2.0])
     ens = FakeEnsemble(n_class=ncls)
     sim = Simulation(ens, n_bins=3, sweeps_per_bin=2, energy=False, tau_corr=(n_tau, [cls], [ncls]),
-                     lattice=(a1, a2, L1 * a1, L2 * a2, 2, r))
+                     lattice=(a1, a2, L1 * a1, L2 * a2, 2, r), n_cov=True)
     res = sim.run()
     s = np.array([x[0] for x in ens.log])                   # [sweeps, chains]
     o = np.array(ens.log_tau)                               # [sweeps, chains, tau, class, 3]
@@ -204,6 +204,9 @@ def test_time_displaced_structure_factors():
     assert np.abs(res.mean["nn_tau_k"] - want_nn).max() < 1e-12
     assert np.abs(res.mean["gf_tau_k"] - want_gf).max() < 1e-12
     assert "szz_tau_k" in res.error and res.mean_sign != 0.0
+    c = res.cov["nn_tau_k"]
+    assert c.shape == (n_tau + 1, n_tau + 1, L1 * L2, 2, 2)
+    assert np.abs(np.einsum("ttkab->tkab", c) - res.error["nn_tau_k"].real ** 2).max() < 1e-12
 
 
 def test_skip_and_rebin_bins():
