@@ -196,6 +196,30 @@ PLANTS = [
     ('SU(2) G(tau,0) with Db_R for Ds_R',
      [('X[(size_t)i * N + j] = MI[(size_t)i * N + j] / dbL[i] * dsR[j];', 'X[(size_t)i * N + j] = MI[(size_t)i * N + j] / dbL[i] * dbR[j];')],
      [SU2 + "::test_su2_displaced_green_matches_the_definition"]),
+    ('SU(2) acceptance with |R| instead of the phase-reweighted |Re(P R)| / |Re P|',
+     [('const double ratio = fabs(creal(P * R)) / fabs(creal(P));', 'const double ratio = cabs(R);')],
+     [SU2 + "::test_su2_sampler_matches_trotter_energy"]),
+    ('SU(2) initial phase with arg det for 2 arg det (one color)',
+     [('P = cexp(_Complex_I * (ph + 2.0 * ar));   /* prod', 'P = cexp(_Complex_I * (ph + ar));   /* prod')],
+     [SU2 + "::test_su2_phase_carried_equals_recomputed"]),
+    ('bond model: site ratio not squared (one color)',
+     [('          R = hs_gamma(fn) / hs_gamma(f) * cexp(-_Complex_I * dth) * r1 * r1;', '          R = hs_gamma(fn) / hs_gamma(f) * cexp(-_Complex_I * dth) * r1;')],
+     [BOND + "::test_sampler_matches_trotter_product"]),
+    ('bond flip: delta of the flip from a for 2a',
+     [('const double delta[8] = {cosh(2.0 * a) - 1.0, 0.0, -sinh(2.0 * a), 0.0,\n                                   -sinh(2.0 * a), 0.0, cosh(2.0 * a) - 1.0, 0.0};', 'const double delta[8] = {cosh(a) - 1.0, 0.0, -sinh(a), 0.0,\n                                   -sinh(a), 0.0, cosh(a) - 1.0, 0.0};')],
+     [BOND + "::test_sampler_matches_trotter_product"]),
+    ('n(tau) n(0): exchange term with the wrong sign',
+     [('o[2] += (nxu + nxd) * (nyu + nyd) + X0 + X1;', 'o[2] += (nxu + nxd) * (nyu + nyd) - X0 - X1;')],
+     [TAUC + "::test_enumeration_equals_fock_trace"]),
+    ("SU(2) n n correlation with one color's exchange term",
+     [('const double complex v[4] = {0.5 * X, rx * ry + 2.0 * X, X, 2.0 * hyx};', 'const double complex v[4] = {0.5 * X, rx * ry + X, X, 2.0 * hyx};')],
+     [SU2 + "::test_su2_correlations_enumeration_equals_fock_trace"]),
+    ('four-valued eta(2) equal to eta(1)',
+     [('case 2: return sqrt(2.0 * (3.0 + s6));', 'case 2: return sqrt(2.0 * (3.0 - s6));')],
+     [CORE + "::test_hs4_constants_match_paper_identity"]),
+    ('B_tau = e^V E instead of E e^V (equal-time G shifted by a similarity)',
+     [('  slice_potential(M, f, s, tau, v);\n  for (int i = 0; i < N; ++i) {\n    const double e = exp(v[i]);\n    for (int j = 0; j < N; ++j) X[i * N + j] *= e;\n  }\n  mat_mul(N, M->E + (size_t)s * N * N, X, X);', '  slice_potential(M, f, s, tau, v);\n  mat_mul(N, M->E + (size_t)s * N * N, X, X);\n  for (int i = 0; i < N; ++i) {\n    const double e = exp(v[i]);\n    for (int j = 0; j < N; ++j) X[i * N + j] *= e;\n  }')],
+     [TAU + "::test_tau_enumeration_equals_fock_trace"]),
 ]
 
 

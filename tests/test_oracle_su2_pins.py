@@ -104,6 +104,27 @@ def _wrap_angle(a):
     return (a + np.pi) % (2 * np.pi) - np.pi
 
 
+def test_su2_phase_carried_equals_recomputed(orc):
+    """The phase P of e^{-S} that the chain carries through its accepted updates
+    (P <- P R / |R|, Sec. 2.2 with W = |Re e^{-S}|) equals, after every sweep, the
+    phase recomputed from scratch on the chain's fields, exp(i (-g sum eta +
+    2 arg det(1 + B))) (both colors).  Away from half filling on a 3-site chain the
+    phases are far from real, so a dropped or halved term shows."""
+    K, U, dtau, L = W.chain_lattice(3, t=1.0, mu=0.5), 4.0, 0.25, 4
+    worst, spread = 0.0, 0.0
+    for c in range(4):
+        ch = orc.Su2Chain(K, dtau, U, orc.init_fields(2, L, 3, 13, c), seed=13, chain=c)
+        for _ in range(5):
+            ch.sweep()
+            _, _, ar, ph, _, _ = orc.su2_plain(K, dtau, U, ch.fields.reshape(L, 3))
+            P = complex(ch.phase[0], ch.phase[1])
+            want = np.exp(1j * (ph + 2.0 * ar))
+            worst = max(worst, abs(P / abs(P) - want))
+            spread = max(spread, abs(np.angle(want)))
+    assert worst < 1e-10
+    assert spread > 0.3                                  # the pin has power: phases well off the real axis
+
+
 @pytest.mark.parametrize("lx", [4, 3])
 def test_su2_udv_chain_matches_plain_product(orc, lx):
     """The complex UDV chain (QR with pivoting, scale separation) against the plain
