@@ -220,6 +220,15 @@ PLANTS = [
     ('B_tau = e^V E instead of E e^V (equal-time G shifted by a similarity)',
      [('  slice_potential(M, f, s, tau, v);\n  for (int i = 0; i < N; ++i) {\n    const double e = exp(v[i]);\n    for (int j = 0; j < N; ++j) X[i * N + j] *= e;\n  }\n  mat_mul(N, M->E + (size_t)s * N * N, X, X);', '  slice_potential(M, f, s, tau, v);\n  mat_mul(N, M->E + (size_t)s * N * N, X, X);\n  for (int i = 0; i < N; ++i) {\n    const double e = exp(v[i]);\n    for (int j = 0; j < N; ++j) X[i * N + j] *= e;\n  }')],
      [TAU + "::test_tau_enumeration_equals_fock_trace"]),
+    ('complex Householder reflection without the conjugate',
+     [('for (int i = k; i < N; ++i) s += conj(v[i]) * X[(size_t)i * N + j];', 'for (int i = k; i < N; ++i) s += v[i] * X[(size_t)i * N + j];')],
+     [SU2 + "::test_su2_udv_chain_matches_plain_product"]),
+    ('complex QR: reflections not counted in det Q',
+     [('betas[k] = 2.0 / vhv;\n    dq = -dq;', 'betas[k] = 2.0 / vhv;')],
+     [SU2 + "::test_su2_udv_chain_matches_plain_product"]),
+    ('complex chain: pivot permutation left out of T',
+     [('acc += X[(size_t)i * N + k] * u->T[(size_t)perm[k] * N + j];', 'acc += X[(size_t)i * N + k] * u->T[(size_t)k * N + j];')],
+     [SU2 + "::test_su2_udv_chain_matches_plain_product"]),
 ]
 
 
