@@ -361,6 +361,10 @@ def time_path(wl, precision, args, stream, seed, world, local_rank, delay_k=None
             "traffic_note": ("ncu capture on these kernel sources" if traffic is not None else
                              f"no ncu capture on these kernel sources (sha {srchash})"),
             "kernel": kern, "peak_source": src}
+    if precision == "mixed_tc" and pk.get("fp32_simt_tflops"):
+        # the same launch against the double-word peak of the FP32 pipes, where
+        # everything but the N^3 products runs
+        roof["frac_double_word"] = achieved / (pk["fp32_simt_tflops"] / DW_OPS_PER_FMA)
     return {"ens": ens, "st": st, "ms_step": ms_step, "value": value, "roofline": roof, "clocks": clk.summary(),
             "algorithmic_tflop_per_step": flops_per_step / 1e12}
 
