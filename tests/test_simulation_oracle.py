@@ -5,7 +5,8 @@ correlations per pair class) are served here by chains of the FP64 oracle,
 which is test infrastructure: this checks the host pipeline -- bins over chains
 and sweeps, sign reweighting, the delete-1 jackknife and the R -> K transform
 with its background -- on Monte Carlo data, against exact diagonalisation of
-the Trotterised density matrix of the 2 x 2 plaquette.  The reference S(k) is
+the Trotterised density matrix of the 2 x 2 plaquette and of a 2 x 1 honeycomb
+(two orbitals per cell, 2 x 2 matrices S_ab(k)).  The reference S(k) is
 the plain definition (1/N) sum_xy e^{i k (R_y - R_x)} (<O_x O_y> - <O_x><O_y>)
 over all site pairs, not the per-class path the driver takes.
 """
@@ -46,9 +47,10 @@ class OracleEnsemble:
         return out, sign
 
 
-def _ed_structure_factors(K, U, dtau, L, pos, k):
-    """S^zz(k) and S^nn(k) (background subtracted) of the Trotterised density
-    matrix, from the expectation of every site pair."""
+def _ed_structure_factors(K, U, dtau, L, cell_pos, n_orb, k):
+    """S^zz_ab(k) and S^nn_ab(k) (background subtracted) of the Trotterised density
+    matrix, from the expectation of every site pair: site x = n_orb cell + orbital,
+    S_ab(k) = (1/N_cell) sum_ij e^{i k (R_j - R_i)} (<O_ia O_jb> - <O_ia><O_jb>)."""
     N = K.shape[0]
     F = Fock(N)
     rho = F.trotter_ising(K, U, dtau, L)
@@ -59,34 +61,49 @@ def _ed_structure_factors(K, U, dtau, L, pos, k):
     Mzz = np.array([[ev(sz[x] @ sz[y]) for y in range(N)] for x in range(N)])
     n1 = np.array([ev(nn[x]) for x in range(N)])
     Mnn = np.array([[ev(nn[x] @ nn[y]) for y in range(N)] for x in range(N)]) - np.outer(n1, n1)
-    ph = np.exp(1j * (k @ pos.T))                                       # [n_k, N]: e^{i k R_x}
-    S = lambda M: np.einsum("kx,xy,ky->k", ph.conj(), M, ph) / N       # (1/N) sum_xy e^{i k (R_y - R_x)} M_xy
+    n_cells = N // n_orb
+    ph = np.exp(1j * (k @ cell_pos.T))                                  # [n_k, N_cell]: e^{i k R_i}
+
+    def S(M):
+        Mc = M.reshape(n_cells, n_orb, n_cells, n_orb)                  # [i, a, j, b]
+        return np.einsum("ki,iajb,kj->kab", ph.conj(), Mc, ph) / n_cells
+
     return S(Mzz), S(Mnn)
 
 
-def test_bin_driver_structure_factors_match_exact_diagonalisation(orc):
-    K = W.square_lattice(2, 2, t=1.0)
+A1, A2SQ, A2H = np.array([1.0, 0.0]), np.array([0.0, 1.0]), np.array([0.5, np.sqrt(3.0) / 2.0])
+CASES = {
+    # name: (hopping, classes, unit vectors, periodicity in cells, orbitals)
+    "square2x2": (lambda: W.square_lattice(2, 2, t=1.0), lambda: W.translation_classes_square(2, 2), A2SQ, (2, 2), 1),
+    "honeycomb2x1": (lambda: W.honeycomb_lattice(2, 1, t=1.0), lambda: W.translation_classes_honeycomb(2, 1), A2H,
+                     (2, 1), 2),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_bin_driver_structure_factors_match_exact_diagonalisation(orc, case):
+    hop, classes, a2, (l1, l2), n_orb = CASES[case]
+    K = hop()
     U, dtau, L = 4.0, 0.125, 8
     m = W.ModelSpec(K, U=U, dtau=dtau, L=L, n_wrap=4)
-    cls, ncls, r = W.translation_classes_square(2, 2)
-    a1, a2 = np.array([1.0, 0.0]), np.array([0.0, 1.0])
+    cls, ncls, r = classes()
     ens = OracleEnsemble(orc, m, n_chains=64, seed=91)
     res = Simulation(ens, n_bins=12, sweeps_per_bin=20, warmup=20, corr=([cls], [ncls]),
-                     lattice=(a1, a2, 2 * a1, 2 * a2, 1, r)).run()
+                     lattice=(A1, a2, l1 * A1, l2 * a2, n_orb, r)).run()
     k = res.mean["k"]
-    pos = np.array([[x % 2, x // 2] for x in range(4)], dtype=float)
-    zz_ed, nn_ed = _ed_structure_factors(K, U, dtau, L, pos, k)
+    n_cells = l1 * l2
+    cell_pos = np.array([(c % l1) * A1 + (c // l1) * a2 for c in range(n_cells)])
+    zz_ed, nn_ed = _ed_structure_factors(K, U, dtau, L, cell_pos, n_orb, k)
     assert res.mean_sign == pytest.approx(1.0)
-    F = Fock(4)
+    F = Fock(K.shape[0])
     rho = F.trotter_ising(K, U, dtau, L)
     kin_ed = np.trace(F.hopping(K) @ rho) / np.trace(rho)
     assert abs(res.mean["kin"] - kin_ed) < 5 * res.error["kin"]
     for name, ed in (("corr_zz_k", zz_ed), ("corr_nn_k", nn_ed)):
-        mc, err = res.mean[name][:, 0, 0], res.error[name][:, 0, 0]
-        assert np.abs(mc.imag).max() < 1e-12 and np.abs(ed.imag).max() < 1e-12
-        z = np.abs(mc.real - ed.real) / (err.real + 1e-12)
-        assert (z < 5.0).all(), (name, mc.real, err.real, ed.real)
-    # the power of the check: S^zz at (pi, pi) is the largest and well resolved
-    q = int(np.argmin(np.abs(k - np.pi).sum(axis=1)))
-    assert res.mean["corr_zz_k"][q, 0, 0].real > 5 * res.error["corr_zz_k"][q, 0, 0].real
-    assert zz_ed[q].real == max(zz_ed.real)
+        mc, err = res.mean[name], res.error[name]
+        for part, e in ((np.real, err.real), (np.imag, err.imag)):
+            z = np.abs(part(mc) - part(ed)) / (e + 1e-12)
+            assert (z < 5.0).all(), (name, mc, err, ed)
+    # the power of the check: the largest S^zz component is resolved
+    q, a, b = np.unravel_index(np.argmax(zz_ed.real), zz_ed.shape)
+    assert res.mean["corr_zz_k"][q, a, b].real > 5 * res.error["corr_zz_k"][q, a, b].real
