@@ -26,6 +26,7 @@ class OracleEnsemble:
         self.orc = orc
         self.m = m
         om = orc.Model(m.hopping, m.vertex_site, m.vertex_sign, m.U, m.dtau, m.L, m.n_wrap, m.field_type)
+        self.om = om
         self.chains = [orc.Chain(om, None, seed=seed, chain=c, measure=True) for c in range(n_chains)]
         self.n_chains = n_chains
 
@@ -39,6 +40,12 @@ class OracleEnsemble:
     def measure(self):
         r = [ch.measure() for ch in self.chains]
         return (np.array([x[0] for x in r]), np.array([x[1] for x in r]), np.array([x[2] for x in r]))
+
+    def measure_tau_corr(self, n_tau, classes, n_class):
+        cls, nc = classes[0], int(n_class[0])
+        out = np.stack([self.orc.tau_correlations(self.om, ch.fields()[0], n_tau, cls, nc) for ch in self.chains])
+        sign = np.array([ch.fields()[2] for ch in self.chains], dtype=np.int32)
+        return out, sign
 
     def measure_corr(self, classes, n_class):
         cls, nc = classes[0], int(n_class[0])
@@ -107,3 +114,39 @@ def test_bin_driver_structure_factors_match_exact_diagonalisation(orc, case):
     # the power of the check: the largest S^zz component is resolved
     q, a, b = np.unravel_index(np.argmax(zz_ed.real), zz_ed.shape)
     assert res.mean["corr_zz_k"][q, a, b].real > 5 * res.error["corr_zz_k"][q, a, b].real
+
+
+def test_bin_driver_time_displaced_structure_factors_match_exact_diagonalisation(orc):
+    """tau_corr: S^zz(k, tau) and the background-subtracted S^nn(k, tau) of the 2 x 2
+    plaquette for every tau against <A(tau) B(0)> = Tr[T^(L-tau) A T^tau B] / Tr[T^L]
+    of every site pair, T the Trotter factor of one slice."""
+    from scipy.linalg import expm
+    K = W.square_lattice(2, 2, t=1.0)
+    U, dtau, L = 4.0, 0.125, 8
+    m = W.ModelSpec(K, U=U, dtau=dtau, L=L, n_wrap=4)
+    cls, ncls, r = W.translation_classes_square(2, 2)
+    ens = OracleEnsemble(orc, m, n_chains=64, seed=92)
+    res = Simulation(ens, n_bins=12, sweeps_per_bin=20, warmup=20, tau_corr=(L, [cls], [ncls]), energy=False,
+                     lattice=(A1, A2SQ, 2 * A1, 2 * A2SQ, 1, r), n_cov=True).run()
+    k = res.mean["k"]
+    N = 4
+    F = Fock(N)
+    T = expm(-dtau * F.hopping(K)) @ expm(-dtau * F.hubbard_ph(U))
+    Z = np.trace(np.linalg.matrix_power(T, L))
+    sz = [0.5 * (F.n(0, x) - F.n(1, x)) for x in range(N)]
+    nn = [F.n(0, x) + F.n(1, x) for x in range(N)]
+    n1 = np.array([np.trace(np.linalg.matrix_power(T, L) @ nn[x]) / Z for x in range(N)])
+    pos = np.array([[x % 2, x // 2] for x in range(N)], dtype=float)
+    ph = np.exp(1j * (k @ pos.T))
+    for tau in range(L + 1):
+        Aa, Bb = np.linalg.matrix_power(T, L - tau), np.linalg.matrix_power(T, tau)
+        Mzz = np.array([[np.trace(Aa @ sz[x] @ Bb @ sz[y]) / Z for y in range(N)] for x in range(N)])
+        Mnn = np.array([[np.trace(Aa @ nn[x] @ Bb @ nn[y]) / Z for y in range(N)] for x in range(N)]) - np.outer(n1, n1)
+        for name, M in (("szz_tau_k", Mzz), ("nn_tau_k", Mnn)):
+            ed = np.einsum("kx,xy,ky->k", ph.conj(), M, ph) / N
+            mc, err = res.mean[name][tau, :, 0, 0], res.error[name][tau, :, 0, 0]
+            z = np.abs(mc.real - ed.real) / (err.real + 1e-12)
+            assert (z < 5.0).all(), (name, tau, mc.real, err.real, ed.real)
+    # neighbouring imaginary times are correlated: positive covariance between tau and tau + 1
+    c = res.cov["szz_tau_k"][:, :, 3, 0, 0]
+    assert c[4, 5] > 0 and np.allclose(np.diag(c), res.error["szz_tau_k"][:, 3, 0, 0].real ** 2)
