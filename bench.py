@@ -155,6 +155,7 @@ def oracle_sample(wl: W.Workload, n_threads: int, per_class: int):
         chains.append((oracle.Chain(om, None, seed=W.BASE_SEED, chain=c), 2 * m.L * m.n_vertices))
     idx = [0]
     lock = threading.Lock()
+    errors = []
 
     def worker():
         while True:
@@ -163,7 +164,12 @@ def oracle_sample(wl: W.Workload, n_threads: int, per_class: int):
                     return
                 i = idx[0]
                 idx[0] += 1
-            chains[i][0].sweep(1)
+            try:
+                chains[i][0].sweep(1)
+            except BaseException as e:       # a failed chain must not be counted as swept
+                with lock:
+                    errors.append(e)
+                return
 
     t0 = time.perf_counter()
     n_threads = max(1, min(n_threads, len(chains)))       # threads that get work
@@ -173,6 +179,8 @@ def oracle_sample(wl: W.Workload, n_threads: int, per_class: int):
     for t in th:
         t.join()
     dt = time.perf_counter() - t0
+    if errors:
+        raise RuntimeError(f"oracle baseline: {len(errors)} of {len(chains)} chain sweeps failed") from errors[0]
     props = sum(p for _, p in chains)
     desc = (f"1 sweep each of {len(chains)} chains ({per_class} per model class of the workload: "
             + ", ".join(f"{wl.models[mi].name}" for mi in sorted(classes)) + f") on {n_threads} threads")
@@ -394,10 +402,15 @@ def oracle_checks(wl, ens, n_threads):
                            m.field_type)
         jobs.append((om, om2, fields[c], c, m.L // 2 - 1))
     res = [None] * len(jobs)
+    errors = []
 
     def work(i):
         om, om2, f, c, ti = jobs[i]
-        res[i] = (oracle.green_udv(om, f, 0, 0)[0], oracle.green_udv(om, f, 0, ti)[0], oracle.green_udv(om2, f, 0, ti)[0])
+        try:
+            res[i] = (oracle.green_udv(om, f, 0, 0)[0], oracle.green_udv(om, f, 0, ti)[0],
+                      oracle.green_udv(om2, f, 0, ti)[0])
+        except BaseException as e:
+            errors.append(e)
 
     ths = []
     for i in range(len(jobs)):
@@ -410,6 +423,8 @@ def oracle_checks(wl, ens, n_threads):
             ths = []
     for t in ths:
         t.join()
+    if errors:
+        raise RuntimeError(f"oracle accuracy check: {len(errors)} of {len(jobs)} oracle recomputes failed") from errors[0]
     fresh = wrapped = delta = 0.0
     for i, (_, _, _, c, ti) in enumerate(jobs):
         G0, Gt, Gt2 = res[i]

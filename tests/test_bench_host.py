@@ -69,3 +69,35 @@ def test_reference_arm_under_torchrun_prints_on_rank0_only():
     lines = _json_lines(r.stdout)
     assert len(lines) == 1
     assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2 and lines[0]["value"] > 0
+
+
+def test_oracle_baseline_fails_loudly_when_a_worker_dies(monkeypatch):
+    """A host thread of the oracle baseline whose chain raises (the failure is
+    injected on the host) stops the run with an error instead of counting that
+    chain's proposals as done."""
+    import threading
+    import bench
+    import oracle
+    oracle.build()
+    real = oracle.Chain.sweep
+    calls = {"n": 0}
+    lock = threading.Lock()
+
+    def flaky(self, n=1):
+        with lock:
+            calls["n"] += 1
+            k = calls["n"]
+        if k == 2:
+            raise RuntimeError("injected worker failure")
+        return real(self, n)
+
+    import numpy as np
+    from paper_1704_00131_gb300 import workloads as W
+    monkeypatch.setattr(oracle.Chain, "sweep", flaky)
+    m = W.ModelSpec(W.square_lattice(4, 4), U=4.0, dtau=0.1, L=20, n_wrap=10, name="square4x4")
+    wl = W.Workload("square 4x4 x4 chains", [m], np.zeros(4, dtype=np.int32), "fp64", 8)
+    with pytest.raises(RuntimeError, match="chain sweeps failed"):
+        bench.oracle_sample(wl, 2, 4)
+    monkeypatch.setattr(oracle.Chain, "sweep", real)
+    props, dt, desc, used = bench.oracle_sample(bench.workload("c1"), 2, 1)
+    assert props == bench.workload("c1").proposals_per_sweep() and dt > 0 and used == 1
