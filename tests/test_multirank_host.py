@@ -121,3 +121,44 @@ def test_simulation_bins_are_summed_over_ranks():
         for k in ref.mean:
             assert np.allclose(mean[k], ref.mean[k], rtol=1e-12, atol=1e-14), k
             assert np.allclose(err[k], ref.error[k], rtol=1e-10, atol=1e-14), k
+
+
+def _failing_rank(rank, world, port, out):
+    import datetime
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    from paper_1704_00131_gb300.simulation import Simulation
+    from tests.test_simulation_host import FakeEnsemble
+
+    class Dies(FakeEnsemble):
+        def sweep(self, n, stats=False):
+            if self.counter >= 4:                       # the fifth sweep: inside the second bin
+                raise RuntimeError("injected failure of this rank's chains")
+            return super().sweep(n, stats)
+
+    ens = Dies(n_chains=3, seed=rank) if rank == 1 else FakeEnsemble(n_chains=3, seed=rank)
+    try:
+        Simulation(ens, n_bins=4, sweeps_per_bin=3, corr=([None], [2]), distributed=True).run()
+        out[rank] = "finished"
+    except Exception as e:                              # noqa: BLE001 - the outcome is what the test checks
+        out[rank] = type(e).__name__ + ": " + str(e)[:200]
+    # rank 1 leaves between its own steps, with no collective in flight; rank 0 is
+    # waiting in the bin's all-reduce and must get an error, not hang
+
+
+def test_distributed_bins_report_a_lost_rank():
+    """A rank whose chains fail leaves the run between steps; the other rank's
+    next per-bin all-reduce ends with an error (peer gone, or the process group's
+    20 s timeout) instead of waiting forever.  The failure is injected on the host."""
+    import time
+    port = _free_port()
+    manager = mp.Manager()
+    out = manager.dict()
+    t0 = time.monotonic()
+    mp.spawn(_failing_rank, args=(2, port, out), nprocs=2, join=True)
+    assert out[1].startswith("RuntimeError: injected failure")
+    assert out[0] != "finished"
+    assert time.monotonic() - t0 < 120
