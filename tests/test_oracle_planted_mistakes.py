@@ -229,6 +229,12 @@ PLANTS = [
     ('complex chain: pivot permutation left out of T',
      [('acc += X[(size_t)i * N + k] * u->T[(size_t)perm[k] * N + j];', 'acc += X[(size_t)i * N + k] * u->T[(size_t)k * N + j];')],
      [SU2 + "::test_su2_udv_chain_matches_plain_product"]),
+    ("stable G(tau): the right chain's last chunk overshoots tau",
+     [('  for (int t = 0; t < tau; t += nw) udv_right_step(&M, fields, s, t, (t + nw < tau) ? t + nw : tau, &R);\n  for (int t = M.L; t > tau; t -= nw) udv_left_step(&M, fields, s, (t - nw > tau) ? t - nw : tau, t, &Lf);\n  st = green_from_udv(', '  for (int t = 0; t < tau; t += nw) udv_right_step(&M, fields, s, t, t + nw, &R);\n  for (int t = M.L; t > tau; t -= nw) udv_left_step(&M, fields, s, (t - nw > tau) ? t - nw : tau, t, &Lf);\n  st = green_from_udv(')],
+     [CORE + "::test_udv_agrees_with_plain_product"]),
+    ("stable G(tau): the left chain's last chunk stops short of tau",
+     [('  for (int t = 0; t < tau; t += nw) udv_right_step(&M, fields, s, t, (t + nw < tau) ? t + nw : tau, &R);\n  for (int t = M.L; t > tau; t -= nw) udv_left_step(&M, fields, s, (t - nw > tau) ? t - nw : tau, t, &Lf);\n  st = green_from_udv(', '  for (int t = 0; t < tau; t += nw) udv_right_step(&M, fields, s, t, (t + nw < tau) ? t + nw : tau, &R);\n  for (int t = M.L; t > tau; t -= nw) udv_left_step(&M, fields, s, (t - nw > tau) ? t - nw : tau + 1, t, &Lf);\n  st = green_from_udv(')],
+     [CORE + "::test_udv_agrees_with_plain_product"]),
 ]
 
 
