@@ -85,3 +85,44 @@ def test_translation_classes_partition_pairs():
     assert cls[0] == 0 and all(cls[i * N + i] == 0 for i in range(N))
     clsh, nh, _ = W.translation_classes_honeycomb(3, 2)
     assert nh == 24 and (np.bincount(clsh, minlength=nh) == 6).all()
+
+
+def test_single_configuration_per_ordered_pair_equals_fock_trace(orc):
+    """One field configuration, every ordered pair its own class, on a 3-site
+    chain without reflection symmetry: the Wick values of orc_correlations on the
+    configuration's G(0) equal Tr[O U_C] / Tr[U_C], U_C = U_L ... U_1 with
+    U_tau = exp(-dtau H_T) exp(sum_s sum_i v^s_i,tau n_i,s) the configuration's
+    Fock-space propagator (its G(0) = (1 + B(beta,0))^-1 is <c c+> of U_C).  Per
+    configuration <S^+_x S^-_y> and <S^+_y S^-_x> differ, so this fixes the order
+    of the two sites in each estimator, which the averages over all fields (real
+    and symmetric) cannot."""
+    from scipy.linalg import expm
+    N, U, dtau, L = 3, 4.0, 0.2, 4
+    K = W.chain_lattice(N, t=1.0, mu=0.2)
+    K[0, 0] -= 0.4
+    K[1, 2] = K[2, 1] = -0.7
+    om = make_model(orc, K, U, dtau, L, 2)
+    lam = math.acosh(math.exp(0.5 * dtau * U))
+    F = Fock(N)
+    ET = expm(-dtau * F.hopping(K))
+    cls = np.arange(N * N, dtype=np.int32)
+    for seed in (1, 2):
+        f = np.where(np.random.default_rng(seed).random((L, N)) < 0.5, -1, 1).astype(np.int8)
+        Uc = np.eye(F.dim)
+        for t in range(L):
+            V = sum(lam * f[t, i] * (F.n(0, i) - F.n(1, i)) for i in range(N))
+            Uc = ET @ expm(V) @ Uc
+        Z = np.trace(Uc)
+        G = np.stack([orc.green_udv(om, f, s, 0)[0] for s in (0, 1)])
+        got = orc.correlations(G, cls, N * N)
+        cu = [F.c[F.mode(0, x)] for x in range(N)]
+        cd = [F.c[F.mode(1, x)] for x in range(N)]
+        for x in range(N):
+            for y in range(N):
+                szx, szy = 0.5 * (F.n(0, x) - F.n(1, x)), 0.5 * (F.n(0, y) - F.n(1, y))
+                nx, ny = F.n(0, x) + F.n(1, x), F.n(0, y) + F.n(1, y)
+                ops = (szx @ szy, nx @ ny, cu[x].T @ cd[x] @ cd[y].T @ cu[y], cu[x].T @ cu[y] + cd[x].T @ cd[y])
+                want = [np.trace(O @ Uc) / Z for O in ops]
+                assert np.abs(got[x * N + y] - want).max() < 1e-10, (seed, x, y, got[x * N + y], want)
+        # the pin has power: per configuration the S^+ S^- estimator is not symmetric in x, y
+        assert abs(got[0 * N + 2, 2] - got[2 * N + 0, 2]) > 1e-3

@@ -235,6 +235,12 @@ PLANTS = [
     ("stable G(tau): the left chain's last chunk stops short of tau",
      [('  for (int t = 0; t < tau; t += nw) udv_right_step(&M, fields, s, t, (t + nw < tau) ? t + nw : tau, &R);\n  for (int t = M.L; t > tau; t -= nw) udv_left_step(&M, fields, s, (t - nw > tau) ? t - nw : tau, t, &Lf);\n  st = green_from_udv(', '  for (int t = 0; t < tau; t += nw) udv_right_step(&M, fields, s, t, (t + nw < tau) ? t + nw : tau, &R);\n  for (int t = M.L; t > tau; t -= nw) udv_left_step(&M, fields, s, (t - nw > tau) ? t - nw : tau + 1, t, &Lf);\n  st = green_from_udv(')],
      [CORE + "::test_udv_agrees_with_plain_product"]),
+    ('S^+_x S^-_y with x and y exchanged',
+     [('out[c * 4 + 2] += (dxy - G0[y * N + x]) * G1[x * N + y];', 'out[c * 4 + 2] += (dxy - G0[x * N + y]) * G1[y * N + x];')],
+     [CORR + "::test_single_configuration_per_ordered_pair_equals_fock_trace"]),
+    ('SU(2) correlations with x and y exchanged',
+     [('      const double complex hyx = dxy - GZ(y, x);\n      const double complex X = hyx * GZ(x, y);', '      const double complex hyx = dxy - GZ(x, y);\n      const double complex X = hyx * GZ(y, x);')],
+     [SU2 + "::test_su2_single_configuration_per_ordered_pair_equals_fock_trace"]),
 ]
 
 

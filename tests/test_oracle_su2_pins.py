@@ -241,3 +241,45 @@ def test_su2_displaced_green_is_independent_of_n_wrap_at_large_beta(orc):
         a0, b0 = orc.su2_green_displaced(K, 0.1, 4.0, 5, f, tau)
         a1, b1 = orc.su2_green_displaced(K, 0.1, 4.0, 10, f, tau)
         assert np.abs(a0 - a1).max() < 1e-10 and np.abs(b0 - b1).max() < 1e-10, tau
+
+
+def test_su2_single_configuration_per_ordered_pair_equals_fock_trace(orc):
+    """One four-valued field configuration of the SU(2) decoupling, every ordered
+    pair its own class, on a 3-site chain without reflection symmetry: the Wick
+    values of orc_su2_correlations on the configuration's complex G(0) equal
+    Tr[O U_C] / Tr[U_C], U_C = U_L ... U_1, U_tau = exp(-dtau H_T)
+    exp(i g sum_x eta(l_x,tau) n_x) on both colors (the constant -i g sum eta of
+    (n_x - 1) cancels in the ratio).  This fixes the order of the two sites in the
+    Green-function estimator per configuration, which the averages over all fields
+    cannot."""
+    from scipy.linalg import expm
+    N, U, dtau, L = 3, 4.0, 0.25, 3
+    K = W.chain_lattice(N, t=1.0, mu=0.3)
+    K[0, 0] -= 0.4
+    K[1, 2] = K[2, 1] = -0.7
+    g = np.sqrt(0.5 * dtau * U)
+    eta = {l: orc.field_coupling(2, 1.0, 2.0, l) for l in (-2, -1, 1, 2)}
+    F = Fock(N)
+    ET = expm(-dtau * F.hopping(K))
+    cls = np.arange(N * N, dtype=np.int32)
+    cu = [F.c[F.mode(0, x)] for x in range(N)]
+    cd = [F.c[F.mode(1, x)] for x in range(N)]
+    for seed in (3, 4):
+        f = np.random.default_rng(seed).choice([-2, -1, 1, 2], size=(L, N)).astype(np.int8)
+        Uc = np.eye(F.dim, dtype=complex)
+        for t in range(L):
+            V = sum(1j * g * eta[int(f[t, x])] * (F.n(0, x) + F.n(1, x)) for x in range(N))
+            Uc = ET @ expm(V) @ Uc
+        Z = np.trace(Uc)
+        G = orc.su2_plain(K, dtau, U, f)[0]
+        got = orc.su2_correlations(G, cls, N * N)
+        for x in range(N):
+            for y in range(N):
+                szx, szy = 0.5 * (F.n(0, x) - F.n(1, x)), 0.5 * (F.n(0, y) - F.n(1, y))
+                nx, ny = F.n(0, x) + F.n(1, x), F.n(0, y) + F.n(1, y)
+                ops = (szx @ szy, nx @ ny, cu[x].T @ cd[x] @ cd[y].T @ cu[y], cu[x].T @ cu[y] + cd[x].T @ cd[y])
+                want = np.array([np.trace(O @ Uc) / Z for O in ops])
+                assert np.abs(got[x * N + y] - want).max() < 1e-10, (seed, x, y, got[x * N + y], want)
+        # with one G for both colors the two-body terms are symmetric in x, y, but
+        # sum_s <c+_x c_y> = 2 (delta - G_yx) is not: the pin fixes the order there
+        assert abs(got[0 * N + 2, 3] - got[2 * N + 0, 3]) > 1e-3
