@@ -241,6 +241,24 @@ PLANTS = [
     ('SU(2) correlations with x and y exchanged',
      [('      const double complex hyx = dxy - GZ(y, x);\n      const double complex X = hyx * GZ(x, y);', '      const double complex hyx = dxy - GZ(x, y);\n      const double complex X = hyx * GZ(y, x);')],
      [SU2 + "::test_su2_single_configuration_per_ordered_pair_equals_fock_trace"]),
+    ('bond model left chain: e^{V} for its adjoint',
+     [('          const double complex ev = cexp(-_Complex_I * m->g * hs_eta(m->hs[(size_t)(t - 1) * N + x]));', '          const double complex ev = cexp(_Complex_I * m->g * hs_eta(m->hs[(size_t)(t - 1) * N + x]));')],
+     [BOND]),
+    ("bond model left chain: factors in the right chain's order",
+     [('      const int part = left ? m->nb + 1 - q : q;', '      const int part = q;')],
+     [BOND]),
+    ('log-det adjoint dU with G_ii for 1 - G_ii',
+     [('        gU += (1.0 - G[i * N + i]) * M.sgn[s * M.MV + k] *', '        gU += G[i * N + i] * M.sgn[s * M.MV + k] *')],
+     [CORE + "::test_logdet_gradient_finite_differences"]),
+    ('energy adjoint dU without the flavor sign sigma_s',
+     [('          gu += acc * M.sgn[s * M.MV + k] *', '          gu += acc *')],
+     [CORE + "::test_energy_gradient_finite_differences"]),
+    ('particle number from G_ii for 1 - G_ii',
+     [('    for (int i = 0; i < N; ++i) part += 1.0 - G[s][i * N + i];', '    for (int i = 0; i < N; ++i) part += G[s][i * N + i];')],
+     [CORE]),
+    ('local G(tau) from G(0,tau) for G(tau,0)',
+     [('        a += Gt0[x * N + x];', '        a += G0t[x * N + x];')],
+     [TAU]),
 ]
 
 
