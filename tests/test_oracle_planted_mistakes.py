@@ -259,6 +259,9 @@ PLANTS = [
     ('local G(tau) from G(0,tau) for G(tau,0)',
      [('        a += Gt0[x * N + x];', '        a += G0t[x * N + x];')],
      [TAU]),
+    ('measurements not weighted by the sign',
+     [('for (int q = 0; q < 4; ++q) c->meas[q] += (double)c->sign * e[q];', 'for (int q = 0; q < 4; ++q) c->meas[q] += e[q];')],
+     [CORE + "::test_sampler_with_negative_weights_matches_exact_energies"]),
 ]
 
 
