@@ -262,6 +262,18 @@ PLANTS = [
     ('measurements not weighted by the sign',
      [('for (int q = 0; q < 4; ++q) c->meas[q] += (double)c->sign * e[q];', 'for (int q = 0; q < 4; ++q) c->meas[q] += e[q];')],
      [CORE + "::test_sampler_with_negative_weights_matches_exact_energies"]),
+    ('ratio without the flavor sign sigma_s',
+     [('delta[s] = exp(M->sgn[s * M->MV + k] * dc) - 1.0;', 'delta[s] = exp(dc) - 1.0;')],
+     [CORE + "::test_wrapped_sherman_morrison_matches_fresh"]),
+    ('V-unwrap of the down pass with the up sign',
+     [('    for (int s = 0; s < nfl; ++s) v_wrap(c, s, tau, -1.0);', '    for (int s = 0; s < nfl; ++s) v_wrap(c, s, tau, +1.0);')],
+     [CORE + "::test_wrapped_sherman_morrison_matches_fresh"]),
+    ('up-pass stabilisation with the left chain of the previous point',
+     [('        fresh_replace(c, s, &chain, (j == nst) ? &ident : &c->slot[s][j], &fs);', '        fresh_replace(c, s, &chain, (j == nst) ? &ident : &c->slot[s][j - 1], &fs);')],
+     [CORE + "::test_free_fermion_closed_form"]),
+    ('down-pass stabilisation from the wrong stored slot',
+     [('        udv_copy(N, (j + 1 == nst) ? &ident : &c->slot[s][j + 1], &chain);', '        udv_copy(N, (j + 1 == nst) ? &ident : &c->slot[s][j], &chain);')],
+     [CORE + "::test_free_fermion_closed_form"]),
 ]
 
 
