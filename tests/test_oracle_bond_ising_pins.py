@@ -271,3 +271,68 @@ def test_udv_chain_low_temperature(orc):
     for tau in (0, 30, 55, 100):
         _, la, ar = orc.hubbard_ising_green_udv(K, bonds, xi, dtau, U, 10, hs, z, tau)
         assert la == pytest.approx(ref[1], rel=1e-11) and abs(np.angle(np.exp(1j * (ar - ref[2])))) < 1e-9
+
+
+def _uniforms(orc, seed, chain, sweep, tau, direction, vertex):
+    """The two uniforms of one proposal: Philox4x32-10 with counter
+    (sweep_lo, 2 tau + dir, vertex, sweep_hi) and key (seed_lo, seed_hi ^ chain)."""
+    ctr = [sweep & 0xFFFFFFFF, 2 * tau + direction, vertex, sweep >> 32]
+    key = [seed & 0xFFFFFFFF, ((seed >> 32) ^ chain) & 0xFFFFFFFF]
+    o = orc.philox4x32_10(ctr, key)
+    return orc.u01(int(o[0]), int(o[1])), orc.u01(int(o[2]), int(o[3]))
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.6])
+def test_sweep_equals_brute_force_metropolis_on_full_weights(orc, mu):
+    """The chain over HS fields and bond spins, replayed proposal by proposal with
+    the Metropolis rule on W = |Re e^{-S}| (Sec. 2.2), each weight recomputed from
+    scratch: prod gamma(l)/4 e^{-i g sum eta} det(1 + B)^2 (plain product, both
+    colors) times the bond spins' weight e^{S0}.  The oracle's sweep -- which
+    takes its ratios from the Green function at the vertex and the rank-1 / rank-2
+    determinant formulas, and carries the phase -- must make the same decisions:
+    fields, spins and carried phase equal after every sweep.  Away from half
+    filling the weights are complex, so sampling |e^{-S}| instead of |Re e^{-S}|
+    changes decisions."""
+    K, U, dtau, L = W.chain_lattice(3, t=1.0, mu=mu), 4.0, 0.25, 4
+    K[0, 0] -= 0.3
+    bonds, pairs = [(0, 1), (1, 2)], [(0, 1)]
+    xi, h, J = 0.7, 0.8, 0.4
+    N, nb = 3, 2
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+
+    def full_weight(hs, z):
+        _, la, ar, ph, _ = orc.hubbard_ising_plain(K, bonds, xi, dtau, U, hs, z)
+        g = np.prod([gam[int(l)] / 4.0 for l in hs.ravel()])
+        return g * np.exp(1j * ph) * np.exp(2.0 * (la + 1j * ar)) * np.exp(orc.ising_bond_logweight(z, dtau, h, J, pairs))
+
+    seed, n_sweeps, decisions = 4321, 3, 0
+    for chain in range(3):
+        rng = np.random.default_rng(chain)
+        hs, z = random_config(rng, L, N, nb)
+        ch = orc.HubbardIsingChain(K, bonds, xi, h, J, pairs, dtau, U, hs, z, seed=seed, chain=chain)
+        hs, z = hs.copy(), z.copy()
+        w = full_weight(hs, z)
+        for sweep in range(n_sweeps):
+            for direction in (0, 1):
+                for step in range(L):
+                    tau = L - step if direction else step + 1
+                    for q in range(N + nb):
+                        v = N + nb - 1 - q if direction else q
+                        hs1, z1 = hs.copy(), z.copy()
+                        if v < N:
+                            u1, u2 = _uniforms(orc, seed, chain, sweep, tau, direction, v)
+                            others = [l for l in (-2, -1, 1, 2) if l != hs[tau - 1, v]]
+                            hs1[tau - 1, v] = others[min(int(np.floor(3.0 * u1)), 2)]
+                        else:
+                            b = nb - 1 - (v - N)
+                            u1, u2 = _uniforms(orc, seed, chain, sweep, tau, direction, N + b)
+                            z1[tau - 1, b] = -z1[tau - 1, b]
+                        w1 = full_weight(hs1, z1)
+                        if u2 < min(1.0, abs(w1.real) / abs(w.real)):
+                            hs, z, w = hs1, z1, w1
+                        decisions += 1
+            ch.sweep()
+            assert np.array_equal(ch.hs.reshape(L, N), hs) and np.array_equal(ch.ising.reshape(L, nb), z), (chain, sweep)
+            P = complex(ch.phase[0], ch.phase[1])
+            assert abs(P / abs(P) - w / abs(w)) < 1e-9, (chain, sweep, P, w)
+    assert decisions == 3 * n_sweeps * 2 * L * (N + nb)

@@ -198,7 +198,7 @@ PLANTS = [
      [SU2 + "::test_su2_displaced_green_matches_the_definition"]),
     ('SU(2) acceptance with |R| instead of the phase-reweighted |Re(P R)| / |Re P|',
      [('const double ratio = fabs(creal(P * R)) / fabs(creal(P));', 'const double ratio = cabs(R);')],
-     [SU2 + "::test_su2_sampler_matches_trotter_energy"]),
+     [SU2 + "::test_su2_sweep_equals_brute_force_metropolis_on_full_weights"]),
     ('SU(2) initial phase with arg det for 2 arg det (one color)',
      [('P = cexp(_Complex_I * (ph + 2.0 * ar));   /* prod', 'P = cexp(_Complex_I * (ph + ar));   /* prod')],
      [SU2 + "::test_su2_phase_carried_equals_recomputed"]),
@@ -274,6 +274,18 @@ PLANTS = [
     ('down-pass stabilisation from the wrong stored slot',
      [('        udv_copy(N, (j + 1 == nst) ? &ident : &c->slot[s][j + 1], &chain);', '        udv_copy(N, (j + 1 == nst) ? &ident : &c->slot[s][j], &chain);')],
      [CORE + "::test_free_fermion_closed_form"]),
+    ('bond model: initial phase with one arg det',
+     [('    P = cexp(_Complex_I * (ph + 2.0 * ar));\n  }\n  int acc = 0;\n  const int nv', '    P = cexp(_Complex_I * (ph + ar));\n  }\n  int acc = 0;\n  const int nv')],
+     [BOND + "::test_sweep_equals_brute_force_metropolis_on_full_weights"]),
+    ('bond model: site acceptance without the phase reweighting',
+     [('          R = hs_gamma(fn) / hs_gamma(f) * cexp(-_Complex_I * dth) * r1 * r1;\n          const double rr = fabs(creal(P * R)) / fabs(creal(P));', '          R = hs_gamma(fn) / hs_gamma(f) * cexp(-_Complex_I * dth) * r1 * r1;\n          const double rr = cabs(R);')],
+     [BOND + "::test_sweep_equals_brute_force_metropolis_on_full_weights"]),
+    ('bond model: bond acceptance without the phase reweighting',
+     [('          R = rf * rf * exp(lw1 - lw0);\n          const double rr = fabs(creal(P * R)) / fabs(creal(P));', '          R = rf * rf * exp(lw1 - lw0);\n          const double rr = cabs(R);')],
+     [BOND + "::test_sweep_equals_brute_force_metropolis_on_full_weights"]),
+    ('bond spins: J coupling with the wrong sign',
+     [('lw += dtau * J * (double)(s[pairs[2 * q]] * s[pairs[2 * q + 1]]);', 'lw -= dtau * J * (double)(s[pairs[2 * q]] * s[pairs[2 * q + 1]]);')],
+     [BOND + "::test_enumeration_equals_trotter_trace_two_bonds_interacting"]),
 ]
 
 

@@ -283,3 +283,49 @@ def test_su2_single_configuration_per_ordered_pair_equals_fock_trace(orc):
         # with one G for both colors the two-body terms are symmetric in x, y, but
         # sum_s <c+_x c_y> = 2 (delta - G_yx) is not: the pin fixes the order there
         assert abs(got[0 * N + 2, 3] - got[2 * N + 0, 3]) > 1e-3
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.5])
+def test_su2_sweep_equals_brute_force_metropolis_on_full_weights(orc, mu):
+    """The SU(2) chain replayed proposal by proposal with the Metropolis rule on
+    W = |Re e^{-S}| (Sec. 2.2), every weight recomputed from scratch as
+    prod gamma(l)/4 e^{-i g sum eta} det(1 + B)^2 (plain product): the oracle's
+    sweep (ratios from the Green function at the vertex, carried phase) makes the
+    same decisions, so the fields and the carried phase agree after every sweep."""
+    K, U, dtau, L = W.chain_lattice(3, t=1.0, mu=mu), 4.0, 0.25, 4
+    K[0, 0] -= 0.3
+    N = 3
+    gam = {l: orc.field_gamma(2, l) for l in (-2, -1, 1, 2)}
+
+    def full_weight(f):
+        _, la, ar, ph, _, _ = orc.su2_plain(K, dtau, U, f)
+        return np.prod([gam[int(l)] / 4.0 for l in f.ravel()]) * np.exp(1j * ph) * np.exp(2.0 * (la + 1j * ar))
+
+    def uniforms(seed, chain, sweep, tau, direction, vertex):
+        o = orc.philox4x32_10([sweep & 0xFFFFFFFF, 2 * tau + direction, vertex, sweep >> 32],
+                              [seed & 0xFFFFFFFF, ((seed >> 32) ^ chain) & 0xFFFFFFFF])
+        return orc.u01(int(o[0]), int(o[1])), orc.u01(int(o[2]), int(o[3]))
+
+    seed = 2468
+    for chain in range(3):
+        f = orc.init_fields(2, L, N, seed, chain).reshape(L, N)
+        ch = orc.Su2Chain(K, dtau, U, f, seed=seed, chain=chain)
+        f = f.copy()
+        w = full_weight(f)
+        for sweep in range(3):
+            for direction in (0, 1):
+                for step in range(L):
+                    tau = L - step if direction else step + 1
+                    for q in range(N):
+                        x = N - 1 - q if direction else q
+                        u1, u2 = uniforms(seed, chain, sweep, tau, direction, x)
+                        others = [l for l in (-2, -1, 1, 2) if l != f[tau - 1, x]]
+                        f1 = f.copy()
+                        f1[tau - 1, x] = others[min(int(np.floor(3.0 * u1)), 2)]
+                        w1 = full_weight(f1)
+                        if u2 < min(1.0, abs(w1.real) / abs(w.real)):
+                            f, w = f1, w1
+            ch.sweep()
+            assert np.array_equal(ch.fields.reshape(L, N), f), (chain, sweep)
+            P = complex(ch.phase[0], ch.phase[1])
+            assert abs(P / abs(P) - w / abs(w)) < 1e-9, (chain, sweep, P, w)
