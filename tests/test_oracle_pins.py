@@ -550,3 +550,56 @@ def test_energy_gradient_finite_differences(orc):
             assert gK[:, x, y].sum() == pytest.approx(fd, rel=1e-6, abs=1e-8), (ft, x, y)
         fdU = (ener(K, U + h) - ener(K, U - h)) / (2 * h)
         assert gU == pytest.approx(fdU, rel=1e-6, abs=1e-8)
+
+
+@pytest.mark.parametrize("ft", [1, 2])
+def test_sweep_equals_brute_force_metropolis_on_full_weights(orc, ft):
+    """The spin-z chain replayed proposal by proposal with the Metropolis rule on
+    |w| (Sec. 2.2), each weight recomputed from scratch as prod_s det(1 + B_s)
+    through the stabilised chain (times prod gamma(l) for the four-valued
+    field; beta = 4 is beyond the plain product's reach at U = 8): the
+    oracle's chain -- ratios from the wrapped Green function, Sherman-Morrison
+    updates, stabilisations -- makes the same decisions and carries the same sign,
+    on a frustrated triangle away from half filling where weights go negative."""
+    N, mu, U, dtau, L = 3, 0.8, 8.0, 0.125, 32
+    K = W.chain_lattice(N, t=1.0, mu=mu, periodic=True)
+    m = make_model(orc, K, U, dtau, L, 4, ft=ft)
+
+    def log_weight(f):
+        lds = [orc.green_udv(m, f, s, 0)[1:] for s in (0, 1)]
+        lg = sum(math.log(orc.field_gamma(ft, int(l))) for l in f.ravel())
+        return sum(ld for ld, _ in lds) + lg, lds[0][1] * lds[1][1]
+
+    def uniforms(seed, chain, sweep, tau, direction, vertex):
+        o = orc.philox4x32_10([sweep & 0xFFFFFFFF, 2 * tau + direction, vertex, sweep >> 32],
+                              [seed & 0xFFFFFFFF, ((seed >> 32) ^ chain) & 0xFFFFFFFF])
+        return orc.u01(int(o[0]), int(o[1])), orc.u01(int(o[2]), int(o[3]))
+
+    seed, negative = 97, 0
+    for chain in range(4):
+        f = orc.init_fields(ft, L, N, seed, chain).reshape(L, N)
+        ch = orc.Chain(m, f, seed=seed, chain=chain)
+        f = f.copy()
+        lw, sg = log_weight(f)
+        for sweep in range(3):
+            for direction in (0, 1):
+                for step in range(L):
+                    tau = L - step if direction else step + 1
+                    for q in range(N):
+                        k = N - 1 - q if direction else q
+                        u1, u2 = uniforms(seed, chain, sweep, tau, direction, k)
+                        f1 = f.copy()
+                        if ft == 1:
+                            f1[tau - 1, k] = -f[tau - 1, k]
+                        else:
+                            others = [l for l in (-2, -1, 1, 2) if l != f[tau - 1, k]]
+                            f1[tau - 1, k] = others[min(int(math.floor(3.0 * u1)), 2)]
+                        lw1, sg1 = log_weight(f1)
+                        if u2 < min(1.0, math.exp(lw1 - lw)):
+                            f, lw, sg = f1, lw1, sg1
+                            negative += sg < 0
+            ch.sweep(1)
+            fo, _, so = ch.fields()
+            assert np.array_equal(fo, f), (chain, sweep)
+            assert so == sg, (chain, sweep, so, sg)
+    assert negative > 0                                  # the sign was exercised
