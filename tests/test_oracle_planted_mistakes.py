@@ -286,6 +286,15 @@ PLANTS = [
     ('bond spins: J coupling with the wrong sign',
      [('lw += dtau * J * (double)(s[pairs[2 * q]] * s[pairs[2 * q + 1]]);', 'lw -= dtau * J * (double)(s[pairs[2 * q]] * s[pairs[2 * q + 1]]);')],
      [BOND + "::test_enumeration_equals_trotter_trace_two_bonds_interacting"]),
+    ('bond factor of part p taken as bond p',
+     [('    const int b = m->nb - part;', '    const int b = part - 1;')],
+     [BOND]),
+    ('Green function seen by a factor taken before it acts',
+     [('  const int f = (tau - 1) * P + part;', '  const int f = (tau - 1) * P + part - 1;')],
+     [BOND]),
+    ('bond model: site ratio with G_xx for 1 - G_xx',
+     [('          const double complex r1 = 1.0 + (cexp(_Complex_I * dth) - 1.0) * (1.0 - Gt[(size_t)x * N + x]);', '          const double complex r1 = 1.0 + (cexp(_Complex_I * dth) - 1.0) * Gt[(size_t)x * N + x];')],
+     [BOND]),
 ]
 
 
